@@ -1,0 +1,18 @@
+"""FP64 CPU oracle for the collocation BEM operators (test infrastructure only).
+
+Only the tests, the smoke check and the bench's CPU-baseline leg import this
+package.  It shares no code with the CUDA library.
+"""
+from .oracle import (  # noqa: F401
+    FLAG_NO_HALF,
+    FLAG_NO_REFINE,
+    FLAG_RULE1,
+    adjoint,
+    apply,
+    assemble,
+    entries,
+    eval_points,
+    geometry,
+    lu_solve,
+    num_threads,
+)

@@ -1,0 +1,117 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the boundary element method itself: it only
+makes surface meshes (vertex coordinates + triangle connectivity) and random
+complex densities, exactly as a user of the library would before calling it.
+Both the CPU oracle and the CUDA path take these arrays as plain inputs.
+
+Conventions (Section 2.1 of the paper, "n is the exterior normal of the elastic
+region"): every triangle (a, b, c) is ordered so that (b - a) x (c - a) points
+out of the scatterer, into the fluid.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "icosphere",
+    "translate_scale",
+    "merge_meshes",
+    "random_density",
+    "plane_wave",
+    "large_multibody",
+]
+
+
+def _icosahedron():
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = np.array(
+        [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+         [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    f = np.array(
+        [[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+         [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+         [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+         [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    return v / np.linalg.norm(v, axis=1, keepdims=True), f
+
+
+def _orient_outward(v, f, centre):
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    flip = np.einsum("ij,ij->i", nrm, (a + b + c) / 3.0 - centre) < 0
+    f = f.copy()
+    f[flip, 1], f[flip, 2] = f[flip, 2], f[flip, 1].copy()
+    return f
+
+
+def icosphere(level: int, radius: float = 1.0, centre=(0.0, 0.0, 0.0)):
+    """Icosahedron subdivided `level` times (20 * 4**level triangles), projected
+    onto the sphere of the given radius. Returns (vertices float64 [nv,3],
+    triangles int32 [nt,3]) with outward orientation."""
+    v, f = _icosahedron()
+    for _ in range(level):
+        nv = v.shape[0]
+        e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]], axis=0)
+        e = np.sort(e, axis=1)
+        key = e[:, 0] * (nv + 1) + e[:, 1]
+        ukey, inv = np.unique(key, return_inverse=True)
+        ua, ub = ukey // (nv + 1), ukey % (nv + 1)
+        mid = v[ua] + v[ub]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        nf = f.shape[0]
+        m01 = nv + inv[0:nf]
+        m12 = nv + inv[nf:2 * nf]
+        m20 = nv + inv[2 * nf:3 * nf]
+        v = np.concatenate([v, mid], axis=0)
+        f = np.concatenate([
+            np.stack([f[:, 0], m01, m20], axis=1),
+            np.stack([m01, f[:, 1], m12], axis=1),
+            np.stack([m20, m12, f[:, 2]], axis=1),
+            np.stack([m01, m12, m20], axis=1)], axis=0)
+    f = _orient_outward(v, f, np.zeros(3))
+    v = v * float(radius) + np.asarray(centre, dtype=np.float64)[None, :]
+    return np.ascontiguousarray(v), np.ascontiguousarray(f.astype(np.int32))
+
+
+def translate_scale(vertices, scale=1.0, shift=(0.0, 0.0, 0.0)):
+    return np.ascontiguousarray(vertices * float(scale) + np.asarray(shift, dtype=np.float64)[None, :])
+
+
+def merge_meshes(parts):
+    """Concatenate several (vertices, triangles) meshes into one."""
+    vs, fs, off = [], [], 0
+    for v, f in parts:
+        vs.append(v)
+        fs.append(f.astype(np.int64) + off)
+        off += v.shape[0]
+    return (np.ascontiguousarray(np.concatenate(vs, axis=0)),
+            np.ascontiguousarray(np.concatenate(fs, axis=0).astype(np.int32)))
+
+
+def large_multibody(big_level: int = 7, small_level: int = 6):
+    """Unit icosphere (level 7: 327,680 triangles) plus 8 icospheres of radius
+    0.3 (level 6: 81,920 triangles each) centred at (+-1.5, +-1.5, +-1.5)."""
+    parts = [icosphere(big_level, 1.0)]
+    for sx in (-1.5, 1.5):
+        for sy in (-1.5, 1.5):
+            for sz in (-1.5, 1.5):
+                parts.append(icosphere(small_level, 0.3, (sx, sy, sz)))
+    return merge_meshes(parts)
+
+
+def random_density(n: int, nrhs: int = 1, seed: int = 0, stream: int = 0, dtype=np.complex128):
+    """Complex density with real and imaginary parts i.i.d. N(0,1), drawn from
+    numpy's PCG64 seeded with (seed, stream). Shape [nrhs, n]."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), int(stream)]))
+    re = rng.standard_normal((nrhs, n))
+    im = rng.standard_normal((nrhs, n))
+    return np.ascontiguousarray((re + 1j * im).astype(dtype))
+
+
+def plane_wave(points, k: float, direction=(0.0, 0.0, 1.0)):
+    """exp(i k d.x) sampled at the given points (e.g. triangle centroids)."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    return np.exp(1j * float(k) * (np.asarray(points) @ d))

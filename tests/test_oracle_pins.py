@@ -1,0 +1,204 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each test names what fixes the expected value: a closed form (sphere
+eigenvalues, Mie series), an identity (Gauss, reciprocity), a library routine
+(numpy.linalg.solve, scipy adaptive quadrature), or brute force.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from oracle import closed_forms as cf
+from paper_1606_02383_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def sphere3():
+    return inputs.icosphere(3)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+# --- self term: closed form + polar remainder vs 2-D adaptive quadrature ------
+
+def _self_adaptive(V, k):
+    """int_T exp(ikr)/(4 pi r) dA at the centroid, by scipy's adaptive dblquad in
+    polar coordinates about the centroid (the 1/r cancels the Jacobian)."""
+    c = V.mean(axis=0)
+    e1 = V[1] - V[0]
+    nrm = np.cross(e1, V[2] - V[0])
+    nrm /= np.linalg.norm(nrm)
+    u = e1 / np.linalg.norm(e1)
+    w = np.cross(nrm, u)
+    P = np.array([[(v - c) @ u, (v - c) @ w] for v in V])
+    tot = 0.0 + 0.0j
+    for e in range(3):
+        A, B = P[e], P[(e + 1) % 3]
+        ta, tb = np.arctan2(A[1], A[0]), np.arctan2(B[1], B[0])
+        if tb < ta:
+            tb += 2 * np.pi
+        d = B - A
+
+        def rmax(t):
+            uu = np.array([np.cos(t), np.sin(t)])
+            # solve rho*uu = A + s*d
+            M = np.array([[uu[0], -d[0]], [uu[1], -d[1]]])
+            return np.linalg.solve(M, A)[0]
+
+        re = integrate.dblquad(lambda r, t: np.cos(k * r) / (4 * np.pi), ta, tb, 0.0, rmax, epsabs=1e-14, epsrel=1e-13)[0]
+        im = integrate.dblquad(lambda r, t: np.sin(k * r) / (4 * np.pi), ta, tb, 0.0, rmax, epsabs=1e-14, epsrel=1e-13)[0]
+        tot += re + 1j * im
+    return tot
+
+
+@pytest.mark.parametrize("k", [0.0, 1.0, 7.5])
+def test_self_term_matches_adaptive_quadrature(k):
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        V = rng.normal(size=(3, 3)) * 0.3
+        T = np.array([[0, 1, 2]], dtype=np.int32)
+        s, d = oracle.entries(V, T, k, [0], [0])
+        ref = _self_adaptive(V, k)
+        assert abs(s[0] - ref) <= 1e-11 * abs(ref), (s[0], ref)
+        assert d[0] == 0.0
+
+
+# --- single layer: sphere eigenvalues (closed form), O(h^2) convergence ------
+
+@pytest.mark.parametrize("k", [1.0, 3.0])
+def test_single_layer_sphere_eigenvalues_converge(k):
+    errs = []
+    for lev in (2, 3):
+        V, T = inputs.icosphere(lev)
+        c, _, _, _ = oracle.geometry(V, T)
+        e = []
+        for n in (0, 1, 2):
+            yn = cf.zonal_harmonic(c, n)[None, :].astype(complex)
+            z = oracle.apply(V, T, k, y=yn)[0]
+            lam = cf.sphere_single_layer_eigenvalue(n, k, 1.0)
+            e.append(np.linalg.norm(z - lam * yn[0]) / np.linalg.norm(yn[0]))
+        errs.append(max(e))
+    assert errs[1] < 0.01
+    assert errs[0] / errs[1] > 2.5  # observed order >= ~1.3 per halving of h
+
+
+@pytest.mark.parametrize("k", [1.0, 3.0])
+def test_double_layer_sphere_eigenvalues_converge(k):
+    errs = []
+    for lev in (2, 3):
+        V, T = inputs.icosphere(lev)
+        c, _, _, _ = oracle.geometry(V, T)
+        e = []
+        for n in (0, 1, 2):
+            xn = cf.zonal_harmonic(c, n)[None, :].astype(complex)
+            z = -oracle.apply(V, T, k, x=xn, flags=oracle.FLAG_NO_HALF)[0]   # = D x
+            lam = cf.sphere_double_layer_eigenvalue(n, k, 1.0)
+            e.append(np.linalg.norm(z - lam * xn[0]) / np.linalg.norm(xn[0]))
+        errs.append(max(e))
+    assert errs[1] < 0.0025 * (1.0 + k * k)   # discretisation error grows like (k h)^2
+    assert errs[0] / errs[1] > 2.5
+
+
+def test_double_layer_static_limit_eigenvalues(sphere3):
+    V, T = sphere3
+    c, _, _, _ = oracle.geometry(V, T)
+    for n in (0, 1, 3):
+        xn = cf.zonal_harmonic(c, n)[None, :].astype(complex)
+        z = -oracle.apply(V, T, 0.0, x=xn, flags=oracle.FLAG_NO_HALF)[0]
+        assert np.linalg.norm(z - cf.sphere_double_layer_static(n) * xn[0]) / np.linalg.norm(xn[0]) < 5e-3
+
+
+# --- Gauss identity for the double layer at k = 0 ---------------------------
+
+def test_gauss_identity(sphere3):
+    V, T = sphere3
+    nt = T.shape[0]
+    ones = np.ones((1, nt), complex)
+    on = -oracle.apply(V, T, 0.0, x=ones, flags=oracle.FLAG_NO_HALF)[0]       # D 1 at centroids
+    assert np.max(np.abs(on + 0.5)) < 1e-4
+    # with the 1/2 term: (1/2 I - D) 1 = 1 on the surface
+    assert np.max(np.abs(oracle.apply(V, T, 0.0, x=ones)[0] - 1.0)) < 1e-4
+    pts_in = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1], [0.0, 0.5, -0.5]])
+    pts_out = np.array([[2.0, 0.0, 0.0], [1.5, 1.5, -1.0], [0.0, 0.0, -3.0]])
+    w_in = -oracle.eval_points(V, T, 0.0, pts_in, x=ones)[0]    # = sum_j D(p, j)
+    w_out = -oracle.eval_points(V, T, 0.0, pts_out, x=ones)[0]
+    assert np.max(np.abs(w_in + 1.0)) < 2e-5    # quadrature error of R_0 at distance ~h/0.1
+    assert np.max(np.abs(w_out)) < 1e-6
+
+
+# --- reciprocity of the single-layer kernel (1-point centroid rule) ---------
+
+def test_single_layer_reciprocity():
+    V, T = inputs.icosphere(2)
+    _, area, _, _ = oracle.geometry(V, T)
+    rng = np.random.default_rng(7)
+    ii = rng.integers(0, T.shape[0], 200)
+    jj = rng.integers(0, T.shape[0], 200)
+    keep = ii != jj
+    ii, jj = ii[keep], jj[keep]
+    k = 2.0
+    sij, dij = oracle.entries(V, T, k, ii, jj, flags=oracle.FLAG_RULE1)
+    sji, dji = oracle.entries(V, T, k, jj, ii, flags=oracle.FLAG_RULE1)
+    np.testing.assert_allclose(sij / area[jj], sji / area[ii], rtol=1e-13)
+    # the double layer is not symmetric: a transposed operand would make it so
+    assert np.max(np.abs(dij / area[jj] - dji / area[ii])) > 1e-3
+
+
+# --- dense LU vs numpy.linalg.solve ----------------------------------------
+
+def test_lu_matches_numpy(sphere3):
+    V, T = sphere3
+    k = 1.0
+    S, D = oracle.assemble(V, T, k)
+    A = 0.5 * np.eye(T.shape[0]) - D + 0.3 * S
+    b = inputs.random_density(T.shape[0], 2, seed=1)
+    x = oracle.lu_solve(A, b)
+    ref = np.linalg.solve(A, b.T).T
+    assert _rel(x, ref) < 1e-12
+
+
+# --- apply/assemble/adjoint consistency (loops and conjugation) --------------
+
+def test_apply_adjoint_dot_product(sphere3):
+    V, T = sphere3
+    k = 2.0
+    nt = T.shape[0]
+    x = inputs.random_density(nt, 1, seed=2)
+    y = inputs.random_density(nt, 1, seed=3)
+    g = inputs.random_density(nt, 1, seed=4)
+    z = oracle.apply(V, T, k, x=x, y=y)
+    gx, gy = oracle.adjoint(V, T, k, g)
+    lhs = np.vdot(g, z)
+    rhs = np.vdot(gx, x) + np.vdot(gy, y)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(z) * np.linalg.norm(g)
+    S, D = oracle.assemble(V, T, k)
+    z2 = (0.5 * x[0] - D @ x[0] + S @ y[0])
+    assert _rel(z[0], z2) < 1e-14
+
+
+# --- Mie series for the rigid sphere (the sound-hard limit, Section 3.3) ------
+
+def test_mie_rigid_sphere_solution_converges():
+    k = 1.0
+    errs = []
+    for lev in (2, 3):
+        V, T = inputs.icosphere(lev)
+        c, _, _, _ = oracle.geometry(V, T)
+        S, D = oracle.assemble(V, T, k)
+        A = 0.5 * np.eye(T.shape[0]) - D
+        b = inputs.plane_wave(c, k)[None, :]
+        p = oracle.lu_solve(A, b)[0]
+        ref = cf.mie_rigid_sphere_surface(k, 1.0, c[:, 2] / np.linalg.norm(c, axis=1))
+        errs.append(_rel(p, ref))
+    assert errs[1] < 5e-3
+    assert errs[0] / errs[1] > 2.5
+
+
+def test_mie_series_truncation_independent():
+    ct = np.linspace(-1, 1, 17)
+    a = cf.mie_rigid_sphere_surface(5.0, 1.0, ct)
+    b = cf.mie_rigid_sphere_surface(5.0, 1.0, ct, nmax=60)
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
