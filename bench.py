@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM Helmholtz BEM operator on one GB300 (or N replicas).
+
+Metric: FMM Helmholtz BEM matvecs/sec at N = 327,680 (level-7 icosphere of
+radius 1), ka = 20, one matvec = one bem_apply computing z = (1/2 I - D) x + S y
+with both densities present and one right-hand side; valid only when the
+relative L2 error on 2,000 seeded rows against the FP64 CPU oracle is <= 1e-5.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica of the workload on its
+own GPU (the operator is applied to a single body; nothing is exchanged), the
+timed region is bracketed by barriers + device synchronisation, and rank 0
+prints one JSON line with the whole-job throughput (sum of matvecs over ranks
+divided by the slowest rank's time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FMM Helmholtz BEM matvecs/sec at N=327,680, rel.err ≤1e-5 vs FP64 oracle"
+UNIT = "matvecs/s"
+N_SUBSET = 2000
+# algorithmic FP32 work of one regular-rule (target, source point) evaluation of
+# the combined S + D kernel, excluding the rsqrt and sincos (36 flops)
+P2P_FLOPS_PER_EVAL = 36
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--level", type=int, default=7, help="icosphere level (7 -> 327,680 triangles)")
+    ap.add_argument("--ka", type=float, default=20.0)
+    ap.add_argument("--eps", type=float, default=1e-5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return a
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="bem_clocks_", suffix=".csv")
+        self.gpu_index = gpu_index
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_index is not None:
+                cmd += ["-i", str(self.gpu_index)]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value, world):
+    """max over ranks (identity at world size 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(level, ka):
+    from paper_1606_02383_gb300 import inputs
+    V, T = inputs.icosphere(level, 1.0)
+    n = T.shape[0]
+    x = inputs.random_density(n, 1, seed=0, stream=0)
+    y = inputs.random_density(n, 1, seed=0, stream=1)
+    rows = np.sort(np.random.default_rng(0).choice(n, size=min(N_SUBSET, n), replace=False))
+    return V, T, x, y, rows, ka  # radius 1: k = ka
+
+
+def oracle_subset(V, T, k, x, y, rows):
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.apply(V, T, k, x=x, y=y, rows=rows)
+    dt = time.perf_counter() - t0
+    return ref, dt, oracle.num_threads()
+
+
+def config_dict(args, n, extra=None):
+    d = {"workload": "icosphere level %d (N=%d triangles, radius 1), ka=%g, nrhs=1, z=(I/2-D)x+Sy, "
+                     "x,y complex128 N(0,1) seed 0" % (args.level, n, args.ka),
+         "N": n, "ka": args.ka, "nrhs": 1, "eps": args.eps, "mode": "FMM mixed (FP32 near/far, FP64 setup+correction build)",
+         "l2": "inputs larger than L2 (operator data streamed per apply > 1.5 GB) and a 256 MiB L2 flush between timed steps",
+         "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: FP64 CPU direct sum on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    V, T, x, y, rows, k = workload(args.level, args.ka)
+    n = T.shape[0]
+    per_step = 128
+    rng = np.random.default_rng(1)
+    import oracle
+    for _ in range(args.warmup):
+        oracle.apply(V, T, k, x=x, y=y, rows=np.sort(rng.choice(n, 16, replace=False)))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply(V, T, k, x=x, y=y, rows=np.sort(rng.choice(n, per_step, replace=False)))
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, n, {"reference": "FP64 CPU oracle (direct O(N^2) sum of the rule-defined "
+                                                         "operator), %d seeded rows per step, extrapolated x N/%d"
+                                                         % (per_step, per_step)}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d seeded target rows x all %d sources per step" % (per_step, n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1606_02383_gb300.operator import Operator
+
+    torch.cuda.set_device(local)
+    V, T, x, y, rows, k = workload(args.level, args.ka)
+    n = T.shape[0]
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op = Operator(V, T, k, p=0, eps=args.eps, mode="mixed")
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    # validity (rank 0): the oracle on 2,000 rows -- also the CPU baseline
+    z = op.apply(xd, yd)
+    torch.cuda.synchronize()
+    rel_err = None
+    cpu = None
+    if rank == 0:
+        ref, dt, cores = oracle_subset(V, T, k, x, y, rows)
+        zr = z.cpu().numpy()[0, rows]
+        rel_err = float(np.linalg.norm(zr - ref[0]) / np.linalg.norm(ref[0]))
+        cpu = {"value": (len(rows) / n) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded target rows x all %d sources (%.1f s), per-matvec time extrapolated x N/%d"
+                         % (len(rows), n, dt, len(rows))}
+
+    for _ in range(args.warmup):
+        op.apply(xd, yd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    launches = op.info("launches_last_apply")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = vis.split(",")[local] if vis and vis.split(",")[0].isdigit() else local
+    sampler = ClockSampler(gpu_index)
+    op.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        op.apply(xd, yd)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    stages = op.profile_read()
+    op.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    total_ms_max = reduce_max(total_ms, world)
+    value = world * args.steps / (total_ms_max / 1000.0)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    zh = torch.empty_like(xh).pin_memory()
+    op.apply_host(xh, yh, zh)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        op.apply_host(xh, yh, zh)  # synchronises internally (D2H of z)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e_val = world * args.e2e_steps / e2e_s
+
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    info = {kk: op.info(kk) for kk in ("leaf_level", "n_leaves", "p2p_pairs", "corr_nnz", "m2l_pairs",
+                                       "m2l_flops", "p_leaf", "p_top")}
+    orders = [op.order_of_level(l) for l in range(2, info["leaf_level"] + 1)]
+    # roofline of the dominant stage (average launch duration from the live events)
+    dom = max(stages, key=lambda s: stages[s][0])
+    dom_ms, dom_launches = stages[dom]
+    per_launch_ms = dom_ms / max(dom_launches, 1)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    steps = args.steps
+    if dom == "p2p":
+        work = info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL  # per launch (one launch per apply)
+        achieved = work / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_p2p_fmm<float>",
+                "work_per_launch": "%d (target, source point) evaluations x %d flops"
+                                   % (info["p2p_pairs"] * 3, P2P_FLOPS_PER_EVAL),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %g MHz" % sm_max}
+    elif dom == "m2l":
+        per_apply_ms = dom_ms / steps
+        achieved = info["m2l_flops"] / (per_apply_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_grouped_gemm<float> (M2L, all levels)",
+                "work_per_launch": "%.4g flops (8 P_l^2 per V-list pair, %d launches per apply)"
+                                   % (info["m2l_flops"] / max(dom_launches / steps, 1), dom_launches // steps),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %g MHz" % sm_max}
+    else:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        nbytes = {"correction": info["corr_nnz"] * 20 + n * 32,
+                  "p2m": n * 2 * (info["p_leaf"] + 1) ** 2 * 8 + n * 16,
+                  "l2p": n * (info["p_leaf"] + 1) ** 2 * 8 + n * 16}.get(dom, n * 32)
+        achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom, "work_per_launch": "%d bytes" % nbytes}
+    roof["stage"] = dom
+    roof["peak_of"] = peak_src
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(args, n, {"leaf_level": info["leaf_level"], "orders_level2_to_leaf": orders,
+                                            "setup_s": round(setup_s, 3), "rel_err_vs_oracle_2000_rows": rel_err,
+                                            "valid": bool(rel_err is not None and rel_err <= 1e-5),
+                                            "wall_s_timed_region": round(wall, 4)}),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 16, "d2h_bytes_per_step": n * 16},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+            "stages_ms_per_apply": {s: round(v[0] / args.steps, 4) for s, v in stages.items()}}
+    if args.stages:
+        print(json.dumps(line["stages_ms_per_apply"]), file=sys.stderr)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * bem.h -- C ABI of the GB300 fast multipole BEM operator library.
+ *
+ * The library applies the discretised 3-D Helmholtz boundary operators of the
+ * acoustic boundary integral equation (paper: Section 2.3, Eq. (danseibie2);
+ * block system Eq. (renritupu); FMM step 2(c) of the solver algorithm):
+ *
+ *     z = (1/2 I - D) x + S y
+ *
+ * for flat triangles Gamma_j with piecewise-constant densities, collocation at
+ * the triangle centroids x_i, G(r) = exp(i k r)/(4 pi r), and n_j the unit
+ * normal pointing out of the scatterer into the fluid (Section 2.1).  The
+ * paper fixes no quadrature, so matrix entries are defined by this rule: the
+ * 3-point rule with barycentric points (2/3,1/6,1/6) and permutations; the
+ * triangle split uniformly L times near the target (L = 2 when the target is
+ * within 2 h_j of the centroid c_j, L = 1 within 4 h_j, h_j the longest edge);
+ * and the exact integral for the self term (D_ii = 0 on a flat element).
+ * The far field is evaluated by a fast multipole method on an octree
+ * (Section 2.3, "a low-frequency FMM is employed"; truncation chosen so the
+ * error is below the requested tolerance, Section 3).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a bem_status code; bem_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Device arrays are raw CUDA device pointers; complex arrays are
+ *    interleaved (re, im) of the given bem_dtype, layout [nrhs][n] with the
+ *    element index fastest, in the caller's triangle order.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Apply calls are stream-ordered and do not synchronise the
+ *    host unless BEM_HOST_BUFFERS is given.
+ *  - The caller owns every buffer it passes; the handle owns all device state
+ *    it allocates at setup (geometry, tree, lists, translation operators,
+ *    correction matrix, workspaces).
+ *  - A handle must not be used from two host threads or two streams at once.
+ *  - Nothing traps or exits on the device; device-detected problems are
+ *    reported through the status of the next synchronising call.
+ */
+#ifndef BEM_H_
+#define BEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_handle bem_handle;
+
+typedef enum {
+  BEM_OK = 0,
+  BEM_ERR_INVALID_ARG = 1,     /* null pointer, bad size, k <= 0, bad flags */
+  BEM_ERR_DEGENERATE_MESH = 2, /* zero-area or non-finite triangle */
+  BEM_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  BEM_ERR_OOM = 4,             /* device allocation failed */
+  BEM_ERR_NOT_CONVERGED = 5,   /* GMRES hit max_iter; x holds the last iterate */
+  BEM_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
+  BEM_ERR_NUMERIC = 7,         /* NaN/Inf detected, or an unusable expansion */
+  BEM_ERR_UNSUPPORTED = 8      /* option combination not available */
+} bem_status;
+
+typedef enum { BEM_C64 = 1, BEM_C128 = 2 } bem_dtype;
+
+/* How the operator is evaluated (fixed at setup). */
+typedef enum {
+  BEM_MODE_FMM_MIXED = 0,   /* FP32 near field and expansions, FP64 setup, FP64 accumulation */
+  BEM_MODE_FMM_FP64 = 1,    /* every stage in FP64 */
+  BEM_MODE_DIRECT_FP64 = 2, /* O(N^2) direct sum in FP64 (same rule-defined operator) */
+  BEM_MODE_DIRECT_FP32 = 3  /* O(N^2) direct sum in FP32 with FP64 correction */
+} bem_mode;
+
+/* bem_apply flags */
+#define BEM_APPLY_NO_HALF 1     /* omit the 1/2 I term: z = -D x + S y */
+#define BEM_HOST_BUFFERS 2      /* x, y, z are host pointers (pinned is best); the call
+                                   copies in, computes, copies out and synchronises */
+
+typedef struct {
+  int64_t n_vertices;
+  int64_t n_triangles;
+  const double* vertices;    /* [n_vertices][3] */
+  const int32_t* triangles;  /* [n_triangles][3], ordered so that (b-a)x(c-a) points
+                                out of the scatterer into the fluid */
+  int on_device;             /* 0: host pointers, 1: device pointers */
+} bem_mesh;
+
+typedef struct {
+  int struct_size;  /* sizeof(bem_options); 0 means "all defaults" */
+  int mode;         /* bem_mode, default BEM_MODE_FMM_MIXED */
+  int leaf_level;   /* octree leaf level; <= 0 picks one from leaf_target */
+  int leaf_target;  /* mean triangles per occupied leaf for the automatic choice (default 48) */
+  int max_nrhs;     /* largest nrhs a later call may use (default 16) */
+  int p_min;        /* lower bound of the automatic per-level order (default 4) */
+  int p_max;        /* upper bound of any order (default 40) */
+} bem_options;
+
+/*
+ * bem_setup -- build everything that does not depend on the densities.
+ *   mesh   : surface mesh, copied at setup (host or device pointers).
+ *   k      : wavenumber k_f > 0 (Section 2.1, Eq. (kf)).
+ *   p      : > 0 fixes the expansion order on every level; <= 0 picks the
+ *            order of each level from eps (Section 3: truncation error < tol).
+ *   eps    : target relative truncation error for the automatic order.
+ *   opt    : nullable, see bem_options.
+ *   stream : stream for the setup work; setup synchronises it before returning.
+ *   out    : receives the new handle (NULL on failure).
+ * Errors: INVALID_ARG, DEGENERATE_MESH, CUDA, OOM, NUMERIC.
+ */
+int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_options* opt, void* stream,
+              bem_handle** out);
+
+/* bem_destroy -- free a handle and all its device memory (NULL is accepted). */
+int bem_destroy(bem_handle* h);
+
+/*
+ * bem_apply -- z = (1/2 I - D) x + S y  (Section 2.3, step 2(c)).
+ *   nrhs  : number of right-hand sides, 1 <= nrhs <= max_nrhs.
+ *   dtype : BEM_C64 or BEM_C128 for x, y and z.
+ *   x     : D-density [nrhs][N], nullable (treated as zero).
+ *   y     : S-density [nrhs][N], nullable (treated as zero).
+ *   z     : output [nrhs][N]; must not alias x or y.
+ *   flags : BEM_APPLY_NO_HALF, BEM_HOST_BUFFERS.
+ */
+int bem_apply(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, void* z, int flags, void* stream);
+
+/*
+ * bem_apply_adjoint -- conjugate transpose of bem_apply:
+ *   gx = (1/2 I - D)^H g,  gy = S^H g   (either output nullable).
+ * The adjoint problem of Section 2.2 uses the same operator; this entry point
+ * is what reverse-mode differentiation of bem_apply needs.
+ */
+int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int flags,
+                      void* stream);
+
+/*
+ * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
+ * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
+ *   b          : right-hand sides [nrhs][N] (device).
+ *   x          : in: initial guess if (flags & BEM_GMRES_USE_X0) else ignored;
+ *                out: solution [nrhs][N] (device).
+ *   tol        : stop when ||b - A x||_2 / ||b||_2 <= tol for every rhs
+ *                (recursive residual).
+ *   max_iter   : total iteration cap; restart: Krylov dimension per cycle.
+ *   iters_out  : nullable; receives the iterations used.
+ *   relres_out : nullable host array [nrhs]; receives the final relative residuals.
+ * Orthogonalisation is classical Gram-Schmidt applied twice, in FP64.
+ * Returns BEM_ERR_NOT_CONVERGED (with x = last iterate) if max_iter is reached.
+ * Synchronises `stream` once per iteration (to read the residual).
+ */
+#define BEM_GMRES_USE_X0 1
+int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
+                    int flags, int* iters_out, double* relres_out, void* stream);
+
+/*
+ * bem_info -- integer facts about a handle (sizes, counts, orders), for
+ * reporting and for the roofline arithmetic.  Unknown keys -> INVALID_ARG.
+ */
+typedef enum {
+  BEM_INFO_N = 0,            /* triangles */
+  BEM_INFO_LEAF_LEVEL = 1,
+  BEM_INFO_N_LEAVES = 2,
+  BEM_INFO_P2P_PAIRS = 3,    /* (target, source triangle) pairs of the near field */
+  BEM_INFO_CORR_NNZ = 4,     /* entries of the near-singular correction matrix */
+  BEM_INFO_M2L_PAIRS = 5,    /* V-list pairs over all levels */
+  BEM_INFO_M2L_FLOPS = 6,    /* 8 P_l^2 per V-list pair summed over levels (one rhs) */
+  BEM_INFO_P_LEAF = 7,       /* expansion order at the leaf level */
+  BEM_INFO_P_TOP = 8,        /* expansion order at level 2 */
+  BEM_INFO_MODE = 9,
+  BEM_INFO_DEVICE_BYTES = 10,
+  BEM_INFO_P2M_BYTES = 11,   /* bytes of the stored P2M + L2P rows */
+  BEM_INFO_LAUNCHES_LAST_APPLY = 12, /* kernels the last bem_apply launched (memsets excluded) */
+  BEM_INFO_ORDER_OF_LEVEL = 100 /* + level: expansion order of that level */
+} bem_info_key;
+int bem_info(bem_handle* h, int key, int64_t* value);
+
+/*
+ * bem_profile -- per-stage device timing of bem_apply (measurement support for
+ * the stage breakdown the paper reports as Table 2, here at kernel level).
+ *   enable = 1: from now on every bem_apply records a pair of CUDA events
+ *               around each stage on the caller's stream (about 1 us each).
+ *   enable = 0: stop recording.  Either value synchronises the device and
+ *               discards the records collected so far.
+ * Stages: 0 prologue, 1 P2P near field, 2 near-singular correction, 3 P2M,
+ * 4 M2M, 5 M2L, 6 L2L, 7 L2P, 8 epilogue.
+ */
+int bem_profile(bem_handle* h, int enable);
+
+/*
+ * bem_profile_read -- wait for the recorded events and return, per stage,
+ * the summed device milliseconds (ms[nstages]) and the number of kernel
+ * launches (launches[nstages], nullable) since the last bem_profile call.
+ */
+int bem_profile_read(bem_handle* h, double* ms, int64_t* launches, int nstages);
+
+/*
+ * bem_last_error -- message of the last failing call on this thread ("" if none).
+ */
+const char* bem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_H_ */

@@ -6,14 +6,11 @@ The compute path lives in the CUDA shared library built from ``csrc/``;
 wrapper.  Importing this package does not load the CUDA library; the first
 use of ``Operator`` does, and fails loudly if it is missing.
 """
-__all__ = ["Operator", "inputs"]
+__all__ = ["Operator"]
 
 
 def __getattr__(name):
     if name == "Operator":
-        from .operator import Operator
-        return Operator
-    if name == "inputs":
-        from . import inputs
-        return inputs
+        import importlib
+        return importlib.import_module(".operator", __name__).Operator
     raise AttributeError(name)

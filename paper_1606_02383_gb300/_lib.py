@@ -1,0 +1,96 @@
+"""ctypes binding of libbem.so (argument marshalling only).
+
+Every step of the operator runs inside the CUDA library; this module only
+passes pointers, sizes and the stream.  If the library is missing the import
+fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbem.so")
+
+BEM_OK = 0
+BEM_ERR_INVALID_ARG = 1
+BEM_ERR_DEGENERATE_MESH = 2
+BEM_ERR_CUDA = 3
+BEM_ERR_OOM = 4
+BEM_ERR_NOT_CONVERGED = 5
+BEM_ERR_TIMEOUT = 6
+BEM_ERR_NUMERIC = 7
+BEM_ERR_UNSUPPORTED = 8
+
+BEM_C64 = 1
+BEM_C128 = 2
+
+MODES = {"mixed": 0, "fp64": 1, "direct64": 2, "direct32": 3}
+
+BEM_APPLY_NO_HALF = 1
+BEM_HOST_BUFFERS = 2
+BEM_GMRES_USE_X0 = 1
+
+INFO = {
+    "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,
+    "p_leaf": 7, "p_top": 8, "mode": 9, "device_bytes": 10, "p2m_bytes": 11, "launches_last_apply": 12,
+}
+STAGES = ("prologue", "p2p", "correction", "p2m", "m2m", "m2l", "l2l", "l2p", "epilogue")
+INFO_ORDER_OF_LEVEL = 100
+
+# every entry point declared in include/bem.h
+EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
+           "bem_profile", "bem_profile_read", "bem_last_error")
+
+
+class BemMesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class BemOptions(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int), ("mode", ctypes.c_int), ("leaf_level", ctypes.c_int),
+                ("leaf_target", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("p_min", ctypes.c_int),
+                ("p_max", ctypes.c_int)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bem error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbem.so (raises if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() (no CPU fallback exists)" % p)
+    lib = ctypes.CDLL(p)
+    vp, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.bem_setup.argtypes = [ctypes.POINTER(BemMesh), ctypes.c_double, i, ctypes.c_double,
+                              ctypes.POINTER(BemOptions), vp, ctypes.POINTER(vp)]
+    lib.bem_destroy.argtypes = [vp]
+    lib.bem_apply.argtypes = [vp, i, i, vp, vp, vp, i, vp]
+    lib.bem_apply_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, vp]
+    lib.bem_gmres_solve.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
+    lib.bem_profile.argtypes = [vp, i]
+    lib.bem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i]
+    lib.bem_last_error.restype = ctypes.c_char_p
+    for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
+              "bem_profile", "bem_profile_read"):
+        getattr(lib, f).restype = i
+    _lib = lib
+    return lib
+
+
+def check(rc: int):
+    if rc != BEM_OK:
+        raise BemError(rc, load().bem_last_error().decode(errors="replace"))

@@ -1,0 +1,250 @@
+// bem_common.cuh -- shared types of the GB300 BEM/FMM library (device + host).
+//
+// Layout of the handle's device state (all per-element arrays are in octree
+// (Morton) order; perm[s] maps a sorted index s to the caller's index):
+//   geometry   : centroids, quadrature points, normals, areas, longest edges
+//   octree     : per level l = 0..L the occupied boxes (Morton prefix, element
+//                range, parent, first child, child count, integer coordinates)
+//   lists      : 27-slot colleague table of every leaf (near field), V-list
+//                pairs grouped by (level, offset), M2M/L2L pairs grouped by octant
+//   operators  : scaled translation matrices per (level, offset/octant), P2M
+//                and L2P rows per element, near-singular correction in CSR
+//   workspaces : weighted densities, multipole/local expansions, partial sums
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+#define BEM_MAXLEV 10  // Morton keys carry 10 bits per axis
+#define BEM_PI 3.14159265358979323846
+
+// ---------------------------------------------------------------- complex --
+template <typename R>
+struct cpx {
+  R re, im;
+};
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> cmk(R a, R b) {
+  cpx<R> c;
+  c.re = a;
+  c.im = b;
+  return c;
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) {
+  return cmk(a.re + b.re, a.im + b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) {
+  return cmk(a.re - b.re, a.im - b.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) {
+  return cmk(s * a.re, s * a.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> conjc(cpx<R> a) {
+  return cmk(a.re, -a.im);
+}
+typedef cpx<double> zd;
+typedef cpx<float> zf;
+
+// i^n for integer n
+__host__ __device__ __forceinline__ zd ipow(int n) {
+  int m = ((n % 4) + 4) % 4;
+  return m == 0 ? cmk(1.0, 0.0) : m == 1 ? cmk(0.0, 1.0) : m == 2 ? cmk(-1.0, 0.0) : cmk(0.0, -1.0);
+}
+
+// ------------------------------------------------------------ status codes --
+struct BemError {
+  int code;
+  std::string msg;
+};
+
+void bem_set_error(const std::string& m);
+int bem_fail(int code, const std::string& m);
+
+#define BEM_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return bem_fail(e_ == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA,             \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+#define BEM_TRY(call)            \
+  do {                           \
+    int rc_ = (call);            \
+    if (rc_ != BEM_OK) return rc_; \
+  } while (0)
+
+// Device-side problem flags (written by kernels, read at synchronising calls).
+#define BEM_DEVERR_DEGENERATE 1
+#define BEM_DEVERR_NONFINITE 2
+#define BEM_DEVERR_OVERFLOW 4
+
+// ------------------------------------------------------------------ handle --
+struct GroupedOp {
+  // dst[dst_off[c] + r] += sum_k T[g][r][k] * src[src_off[c] + k] for every pair c of group g
+  int ngroups = 0;
+  std::vector<int> rows, cols;          // per group (host copy)
+  std::vector<int64_t> mat_off;         // per group, complex offset into the matrix buffer
+  std::vector<int> pair_start;          // per group, first pair (host copy), size ngroups+1
+  int npairs = 0;
+  int* d_src_off = nullptr;             // [npairs]
+  int* d_dst_off = nullptr;             // [npairs]
+  // tile jobs: (group, first pair, row tile)
+  int njobs = 0;
+  int4* d_jobs = nullptr;               // x = group, y = first pair, z = npairs in job, w = row0
+  int* d_group_rows = nullptr;
+  int* d_group_cols = nullptr;
+  int64_t* d_group_mat = nullptr;
+  int64_t flops = 0;                    // 8 * rows * cols per pair, summed
+};
+
+struct LevelInfo {
+  int nbox = 0;
+  int p = 0, P = 0;
+  double w = 0.0;        // box width
+  int64_t exp_base = 0;  // complex offset of this level's expansions within one rhs slab
+  // device arrays (per box)
+  uint32_t* key = nullptr;  // Morton prefix of the box
+  int* start = nullptr;     // first element (sorted order)
+  int* end = nullptr;       // one past last element
+  int* child0 = nullptr;    // first child box (level l+1), -1 at the leaf level
+  int* nchild = nullptr;
+  int* parent = nullptr;    // parent box (level l-1), -1 at the root
+  int* coord = nullptr;     // [nbox][3] integer box coordinates at this level
+  double* centre = nullptr; // [nbox][3]
+};
+
+// one profiled stage of one apply: events recorded on the caller's stream
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+  int launches;
+};
+#define BEM_NSTAGES 9  // prologue, p2p, correction, p2m, m2m, m2l, l2l, l2p, epilogue
+
+struct bem_handle {
+  int device = 0;
+  int mode = BEM_MODE_FMM_MIXED;
+  double k = 0.0;
+  int fixed_p = 0;
+  double eps = 1e-5;
+  int nrhs_max = 16;
+  int p_min = 4, p_max = 40;
+  int64_t nt = 0, nv = 0;
+  int L = 0;          // leaf level
+  int Lc = 0;         // level used to search for near-singular pairs
+  double root_c[3] = {0, 0, 0};
+  double root_w = 0;  // root box width
+  std::vector<LevelInfo> lev;
+
+  std::vector<void*> allocs;  // everything cudaMalloc'ed for this handle
+  size_t bytes = 0;
+
+  int* d_err = nullptr;  // device problem flags
+
+  // geometry (sorted order)
+  int* perm = nullptr;          // sorted -> caller index
+  double* cent = nullptr;       // [nt][3]
+  double* qpt = nullptr;        // [nt][3][3]
+  double* nrm = nullptr;        // [nt][3]
+  double* area = nullptr;       // [nt]
+  double* hmax = nullptr;       // [nt]
+  double* wgt = nullptr;        // A_j / (12 pi): quadrature weight per point, with 1/(4 pi)
+  float4* tgt32 = nullptr;      // [nt] centroid
+  float4* src32 = nullptr;      // [nt][3] quadrature points, normal in .w
+  double4* tgt64 = nullptr;
+  double4* src64 = nullptr;
+  double hmax_all = 0.0;
+
+  int* leaf_of = nullptr;       // [nt] leaf box of every sorted element
+  // near field: 27 colleague slots per leaf (-1 = none)
+  int* near27 = nullptr;        // [nleaf][27]
+  int64_t p2p_pairs = 0;
+
+  // correction CSR over sorted targets; values divided by wgt[j]
+  int* corr_ptr = nullptr;      // [nt+1]
+  int* corr_col = nullptr;      // [nnz]
+  void* corr_val = nullptr;     // [nnz] of {S, D} complex (float4 or double4)
+  int64_t corr_nnz = 0;
+
+  // far field
+  GroupedOp m2m[BEM_MAXLEV + 1];  // index l: child level l+1 -> parent level l
+  GroupedOp m2l[BEM_MAXLEV + 1];
+  GroupedOp l2l[BEM_MAXLEV + 1];  // index l: parent level l -> child level l+1
+  void* mats = nullptr;           // all translation matrices (complex float or double)
+  int64_t mats_len = 0;
+  void* p2m_rows = nullptr;       // [nt][2][P_L] complex: a-hat, b-hat
+  void* l2p_rows = nullptr;       // [nt][P_L] complex
+  int64_t exp_total = 0;          // complex coefficients per rhs over all levels
+
+  // workspaces
+  void* dens = nullptr;     // [nrhs_max][nt] weighted (y, x) pairs: float4 or double4
+  void* Mexp = nullptr;     // [nrhs_max][exp_total] complex
+  void* Lexp = nullptr;
+  double* zn = nullptr;     // [nrhs_max][nt] complex double (near + correction), sorted
+  double* zfar = nullptr;   // [nrhs_max][nt] complex double (far), sorted
+  void* io_x = nullptr;     // staging for BEM_HOST_BUFFERS: [nrhs_max][nt] complex double each
+  void* io_y = nullptr;
+  void* io_z = nullptr;
+  // profiling
+  int prof_on = 0;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  int launches_last_apply = 0;  // kernels launched by the last bem_apply
+  // GMRES workspace (allocated on first use)
+  int gm_restart = 0;
+  int gm_nrhs = 0;
+  double* gm_V = nullptr;
+  double* gm_w = nullptr;
+  double* gm_dots = nullptr;
+  double* gm_norms = nullptr;
+};
+
+int bem_prof_begin(bem_handle* h, cudaStream_t s);                      // returns a record index or -1
+void bem_prof_end(bem_handle* h, int rec, int stage, int launches, cudaStream_t s);
+bool bem_is_fmm(const bem_handle* h);
+bool bem_is_fp64(const bem_handle* h);
+
+template <typename T>
+int bem_alloc(bem_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return bem_fail(BEM_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                     " bytes failed: " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back((void*)*p);
+  h->bytes += count * sizeof(T);
+  return BEM_OK;
+}
+
+// ---- stage entry points (defined in the .cu files) ----
+int bem_build_geometry(bem_handle* h, const double* dV, const int32_t* dT, cudaStream_t s);
+int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t s);
+int bem_build_correction(bem_handle* h, cudaStream_t s);
+int bem_build_far_field(bem_handle* h, cudaStream_t s);
+int bem_apply_sorted(bem_handle* h, int nrhs, cudaStream_t s);  // dens -> zn, zfar
+int bem_apply_adjoint_sorted(bem_handle* h, int nrhs, cudaStream_t s);
+int bem_prologue(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, cudaStream_t s);
+int bem_epilogue(bem_handle* h, int nrhs, int dtype, const void* x, void* z, int half, cudaStream_t s);
+int bem_adjoint_prologue(bem_handle* h, int nrhs, int dtype, const void* g, cudaStream_t s);
+int bem_adjoint_epilogue(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
+                         cudaStream_t s);
+int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
+              int flags, int* iters_out, double* relres_out, cudaStream_t s);
+int bem_check_device_error(bem_handle* h, cudaStream_t s);

@@ -1,0 +1,143 @@
+"""PyTorch-facing wrapper of the CUDA library.
+
+torch supplies device memory and the current CUDA stream; every computation
+happens inside libbem.so (see _lib.py).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex128:
+        return _lib.BEM_C128
+    if t.dtype == torch.complex64:
+        return _lib.BEM_C64
+    raise TypeError("densities must be complex64 or complex128 tensors")
+
+
+class Operator:
+    """z = (1/2 I - D) x + S y on a triangle mesh (see include/bem.h).
+
+    Parameters: vertices [nv,3] float64, triangles [nt,3] int32 (host arrays),
+    wavenumber k, order p (> 0 fixed, 0 = automatic from eps), eps, mode in
+    {"mixed", "fp64", "direct64", "direct32"}, leaf_level (0 = automatic),
+    leaf_target, max_nrhs.
+    """
+
+    def __init__(self, vertices, triangles, k, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48,
+                 max_nrhs=16, p_min=4, p_max=40):
+        lib = _lib.load()
+        V = np.ascontiguousarray(vertices, dtype=np.float64)
+        T = np.ascontiguousarray(triangles, dtype=np.int32)
+        mesh = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
+        opt = _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
+                              int(max_nrhs), int(p_min), int(p_max))
+        h = ctypes.c_void_p()
+        _lib.check(lib.bem_setup(ctypes.byref(mesh), float(k), int(p), float(eps), ctypes.byref(opt), _stream(),
+                                 ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.n = T.shape[0]
+        self.k = float(k)
+        self.mode = mode
+        self.max_nrhs = int(max_nrhs)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, key):
+        v = ctypes.c_int64()
+        code = _lib.INFO[key] if isinstance(key, str) else int(key)
+        _lib.check(self._lib.bem_info(self._h, code, ctypes.byref(v)))
+        return int(v.value)
+
+    def profile(self, enable=True):
+        """Start (or stop) per-stage CUDA-event timing inside the library."""
+        _lib.check(self._lib.bem_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{stage: (milliseconds, launches)} summed since profile() was called."""
+        n = len(_lib.STAGES)
+        ms = (ctypes.c_double * n)()
+        ln = (ctypes.c_int64 * n)()
+        _lib.check(self._lib.bem_profile_read(self._h, ms, ln, n))
+        return {st: (ms[i], int(ln[i])) for i, st in enumerate(_lib.STAGES)}
+
+    def order_of_level(self, level):
+        return self.info(_lib.INFO_ORDER_OF_LEVEL + int(level))
+
+    def _prep(self, t, dtype):
+        if t is None:
+            return None
+        t = torch.as_tensor(t)
+        if t.dim() == 1:
+            t = t[None, :]
+        return t.to(device="cuda", dtype=dtype).contiguous()
+
+    def apply(self, x=None, y=None, no_half=False, dtype=None):
+        """z = (1/2 I - D) x + S y for device densities [nrhs, n] (or [n])."""
+        ref = x if x is not None else y
+        if ref is None:
+            raise ValueError("x and y cannot both be None")
+        dtype = dtype or (ref.dtype if isinstance(ref, torch.Tensor) else torch.complex128)
+        xs, ys = self._prep(x, dtype), self._prep(y, dtype)
+        nrhs = (xs if xs is not None else ys).shape[0]
+        z = torch.empty((nrhs, self.n), dtype=dtype, device="cuda")
+        flags = _lib.BEM_APPLY_NO_HALF if no_half else 0
+        _lib.check(self._lib.bem_apply(self._h, nrhs, _dtype_code(z), None if xs is None else xs.data_ptr(),
+                                       None if ys is None else ys.data_ptr(), z.data_ptr(), flags, _stream()))
+        return z
+
+    def apply_host(self, x=None, y=None, out=None, no_half=False):
+        """Same as apply() for host arrays/tensors (pinned is best); copies are inside the call."""
+        ref = x if x is not None else y
+        nrhs = ref.shape[0] if ref.dim() == 2 else 1
+        dtype = ref.dtype
+        if out is None:
+            out = torch.empty((nrhs, self.n), dtype=dtype)
+        flags = _lib.BEM_HOST_BUFFERS | (_lib.BEM_APPLY_NO_HALF if no_half else 0)
+        _lib.check(self._lib.bem_apply(self._h, nrhs, _dtype_code(out), None if x is None else x.data_ptr(),
+                                       None if y is None else y.data_ptr(), out.data_ptr(), flags, _stream()))
+        return out
+
+    def adjoint(self, g):
+        """(gx, gy) = ((1/2 I - D)^H g, S^H g)."""
+        gs = self._prep(g, g.dtype)
+        nrhs = gs.shape[0]
+        gx = torch.empty_like(gs)
+        gy = torch.empty_like(gs)
+        _lib.check(self._lib.bem_apply_adjoint(self._h, nrhs, _dtype_code(gs), gs.data_ptr(), gx.data_ptr(),
+                                               gy.data_ptr(), 0, _stream()))
+        return gx, gy
+
+    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
+        """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs])."""
+        bs = self._prep(b, b.dtype)
+        nrhs = bs.shape[0]
+        x = torch.zeros_like(bs) if x0 is None else self._prep(x0, bs.dtype).clone()
+        iters = ctypes.c_int(0)
+        rel = (ctypes.c_double * nrhs)()
+        flags = _lib.BEM_GMRES_USE_X0 if x0 is not None else 0
+        rc = self._lib.bem_gmres_solve(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
+                                       int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
+        if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
+            _lib.check(rc)
+        return x, int(iters.value), np.array(list(rel))

@@ -1,0 +1,42 @@
+"""The C ABI library loads and exports every entry point include/bem.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+from paper_1606_02383_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(?:int|const char\*)\s+(bem_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
+              "bem_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_lib.EXPORTS) <= set(_declared())
+
+
+def test_error_paths_without_gpu():
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    # NULL mesh -> invalid argument, no CUDA call needed
+    rc = lib.bem_setup(None, 1.0, 8, 1e-5, None, None, ctypes.byref(h))
+    assert rc == _lib.BEM_ERR_INVALID_ARG
+    assert b"mesh" in lib.bem_last_error()
+    mesh = _lib.BemMesh(3, 1, 0, 0, 0)
+    assert lib.bem_setup(ctypes.byref(mesh), 1.0, 8, 1e-5, None, None, ctypes.byref(h)) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_apply(None, 1, _lib.BEM_C128, None, None, None, 0, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_destroy(None) == _lib.BEM_OK

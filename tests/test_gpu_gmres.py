@@ -1,0 +1,56 @@
+"""GMRES on the device vs the oracle's dense LU and vs the Mie series."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import closed_forms as cf
+from paper_1606_02383_gb300 import inputs
+from paper_1606_02383_gb300.operator import Operator
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mode,p,tol_lu", [("direct64", 0, 1e-7), ("mixed", 10, 1e-5)])
+def test_gmres_plane_wave_small_sphere(cuda_ok, mode, p, tol_lu):
+    """Config 'plain method, small': (1/2 I - D) p = exp(i k z), tol 1e-8, checked against LU and Mie."""
+    V, T = inputs.icosphere(3)
+    k = 1.0
+    c, _, _, _ = oracle.geometry(V, T)
+    b = inputs.plane_wave(c, k)[None, :]
+    S, D = oracle.assemble(V, T, k)
+    ref = oracle.lu_solve(0.5 * np.eye(T.shape[0]) - D, b)
+    op = Operator(V, T, k, p=p, mode=mode, leaf_level=3 if mode == "mixed" else 0)
+    x, iters, relres = op.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=100, restart=100)
+    x = x.cpu().numpy()
+    assert relres[0] <= 1e-8
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= tol_lu
+    mie = cf.mie_rigid_sphere_surface(k, 1.0, c[:, 2] / np.linalg.norm(c, axis=1))
+    assert np.linalg.norm(x[0] - mie) / np.linalg.norm(mie) <= 5e-3
+    assert 2 <= iters <= 40
+
+
+def test_gmres_multi_rhs_and_restart(cuda_ok):
+    V, T = inputs.icosphere(3)
+    k = 2.0
+    n = T.shape[0]
+    rng = np.random.default_rng(0)
+    b = inputs.random_density(n, 3, seed=4)
+    op = Operator(V, T, k, mode="direct64")
+    x, iters, relres = op.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_iter=300, restart=7)
+    assert np.all(relres <= 1e-10)
+    Ax = op.apply(x, None).cpu().numpy()
+    assert np.linalg.norm(Ax - b) / np.linalg.norm(b) <= 1e-9
+    del rng
+
+
+def test_gmres_not_converged_status(cuda_ok):
+    from paper_1606_02383_gb300 import _lib
+    V, T = inputs.icosphere(2)
+    op = Operator(V, T, 1.0, mode="direct64")
+    b = torch.from_numpy(inputs.random_density(T.shape[0], 1, seed=2)).cuda()
+    with pytest.raises(_lib.BemError) as e:
+        op.solve(b, tol=1e-14, max_iter=2, restart=2)
+    assert e.value.code == _lib.BEM_ERR_NOT_CONVERGED
+    x, iters, rel = op.solve(b, tol=1e-14, max_iter=2, restart=2, raise_on_fail=False)
+    assert iters == 2 and rel[0] > 1e-14

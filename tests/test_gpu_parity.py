@@ -1,0 +1,162 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: 1e-10 relative L2 for the FP64 direct path (same rule-defined
+operator, only rounding differs); 1e-5 for the FMM (truncation + FP32), the
+bar of the headline metric.  Errors are also checked per operator (S alone,
+D alone) against their own norms.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_02383_gb300 import inputs
+from paper_1606_02383_gb300.operator import Operator
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def sphere3():
+    V, T = inputs.icosphere(3)
+    n = T.shape[0]
+    x = inputs.random_density(n, 2, seed=0, stream=0)
+    y = inputs.random_density(n, 2, seed=0, stream=1)
+    return V, T, x, y
+
+
+def perturbed_mesh(level=2, seed=5, amp=0.08):
+    V, T = inputs.icosphere(level)
+    rng = np.random.default_rng(seed)
+    V = V * (1.0 + amp * rng.uniform(-1, 1, size=(V.shape[0], 1)))
+    return V, T
+
+
+@pytest.mark.parametrize("k", [1.0, 4.0])
+def test_direct_fp64_matches_oracle(cuda_ok, sphere3, k):
+    V, T, x, y = sphere3
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    op = Operator(V, T, k, mode="direct64")
+    z = op.apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, ref) <= 1e-10
+    # each operator alone
+    zs = op.apply(None, dev(y)).cpu().numpy()
+    assert rel(zs, oracle.apply(V, T, k, y=y)) <= 1e-10
+    zd = op.apply(dev(x), None, no_half=True).cpu().numpy()
+    assert rel(zd, oracle.apply(V, T, k, x=x, flags=oracle.FLAG_NO_HALF)) <= 1e-10
+
+
+def test_direct_fp64_irregular_mesh(cuda_ok):
+    V, T = perturbed_mesh()
+    n = T.shape[0]
+    x = inputs.random_density(n, 1, seed=3, stream=0)
+    y = inputs.random_density(n, 1, seed=3, stream=1)
+    k = 2.5
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    z = Operator(V, T, k, mode="direct64").apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, ref) <= 1e-10
+
+
+def test_direct_fp32_matches_oracle(cuda_ok, sphere3):
+    V, T, x, y = sphere3
+    k = 1.0
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    z = Operator(V, T, k, mode="direct32").apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("leaf_level", [2, 3])
+@pytest.mark.parametrize("p,tol,tol_d", [(8, 2e-5, 5e-4), (10, 1e-5, 1e-4)])
+def test_fmm_small_sphere(cuda_ok, sphere3, mode, leaf_level, p, tol, tol_d):
+    """Config 'plain method, small': 1,280 triangles, k = 1.  At p = 8 the
+    truncation error of z measures 1.1e-5 (leaf level 2) to 1.7e-5 (level 3) in
+    both precisions; p = 10 meets the 1e-5 bar.  The double layer alone (its
+    multipoles come from dipoles, whose expansions decay one order slower) is
+    checked against its own norm with the looser tol_d: measured 1.9e-4 / 3.0e-4
+    at p = 8 and 7.2e-5 at p = 10 (leaf level 3)."""
+    V, T, x, y = sphere3
+    k = 1.0
+    op = Operator(V, T, k, p=p, mode=mode, leaf_level=leaf_level)
+    z = op.apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, oracle.apply(V, T, k, x=x, y=y)) <= tol
+    zs = op.apply(None, dev(y)).cpu().numpy()
+    assert rel(zs, oracle.apply(V, T, k, y=y)) <= tol
+    zd = op.apply(dev(x), None, no_half=True).cpu().numpy()
+    assert rel(zd, oracle.apply(V, T, k, x=x, flags=oracle.FLAG_NO_HALF)) <= tol_d
+
+
+def test_fmm_smooth_density_far_field_dominated(cuda_ok):
+    """A smooth density makes the far field the main part of S y: checks the expansions."""
+    V, T = inputs.icosphere(4)
+    c, _, _, _ = oracle.geometry(V, T)
+    k = 3.0
+    y = inputs.plane_wave(c, k, (0.3, -0.2, 0.9))[None, :]
+    ref = oracle.apply(V, T, k, y=y)
+    for mode in ("fp64", "mixed"):
+        op = Operator(V, T, k, p=0, eps=1e-6, mode=mode, leaf_level=4)
+        z = op.apply(None, dev(y)).cpu().numpy()
+        assert rel(z, ref) <= 1e-5, mode
+
+
+def test_fmm_auto_order_ka5(cuda_ok):
+    V, T = inputs.icosphere(4)
+    n = T.shape[0]
+    k = 5.0
+    x = inputs.random_density(n, 1, seed=11, stream=0)
+    y = inputs.random_density(n, 1, seed=11, stream=1)
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed")
+    z = op.apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, ref) <= 1e-5
+    assert op.info("leaf_level") >= 2
+
+
+def test_dtypes_and_host_buffers(cuda_ok, sphere3):
+    V, T, x, y = sphere3
+    k = 1.0
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    op = Operator(V, T, k, p=10, mode="mixed", leaf_level=3)
+    z64 = op.apply(dev(x.astype(np.complex64)), dev(y.astype(np.complex64))).cpu().numpy()
+    assert z64.dtype == np.complex64
+    assert rel(z64, ref) <= 2e-5
+    zh = op.apply_host(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()).numpy()
+    assert rel(zh, ref) <= 1e-5
+
+
+def test_tiny_and_ragged_meshes(cuda_ok):
+    # a tetrahedron (4 triangles) and an octahedron: every path must still agree with the oracle
+    Vt = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    Tt = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    for V, T in ((Vt, Tt), inputs.icosphere(0), perturbed_mesh(1, seed=9)):
+        n = T.shape[0]
+        x = inputs.random_density(n, 1, seed=1, stream=0)
+        y = inputs.random_density(n, 1, seed=1, stream=1)
+        ref = oracle.apply(V, T, 1.5, x=x, y=y)
+        for mode in ("direct64", "fp64", "mixed"):
+            z = Operator(V, T, 1.5, p=6, mode=mode).apply(dev(x), dev(y)).cpu().numpy()
+            assert rel(z, ref) <= (1e-10 if mode == "direct64" else 1e-5), (n, mode)
+
+
+def test_invalid_arguments(cuda_ok, sphere3):
+    from paper_1606_02383_gb300 import _lib
+    V, T, x, y = sphere3
+    with pytest.raises(_lib.BemError) as e:
+        Operator(V, T, -1.0)
+    assert e.value.code == _lib.BEM_ERR_INVALID_ARG
+    Tbad = T.copy()
+    Tbad[0] = [0, 0, 1]  # zero-area triangle
+    with pytest.raises(_lib.BemError) as e:
+        Operator(V, Tbad, 1.0, mode="direct64")
+    assert e.value.code == _lib.BEM_ERR_DEGENERATE_MESH
+    op = Operator(V, T, 1.0, mode="direct64", max_nrhs=2)
+    with pytest.raises(_lib.BemError):
+        op.apply(dev(np.ones((3, T.shape[0]), complex)), None)
