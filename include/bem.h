@@ -122,6 +122,39 @@ int bem_destroy(bem_handle* h);
 int bem_apply(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, void* z, int flags, void* stream);
 
 /*
+ * bem_apply_noalloc -- bem_apply for callers that cannot allocate device
+ * memory.  (No counterpart in the paper: this is an interface convenience.)
+ *
+ * Who needs it: programs whose device memory belongs to an allocator or pool
+ * that already holds the whole GPU, so a cudaMalloc would fail or fragment the
+ * pool, and latency-critical loops that must stay out of the driver's
+ * allocation path (cudaMalloc/cudaFree may synchronise the device).
+ *
+ * It computes exactly what bem_apply computes, with the same arguments, on
+ * device buffers only (flags: BEM_APPLY_NO_HALF; BEM_HOST_BUFFERS is
+ * rejected).  The per-call scratch (weighted densities, near/far partial sums,
+ * expansions) lives in one fixed library array of BEM_NOALLOC_SCRATCH_BYTES
+ * on each device instead of the handle's workspaces, and the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  The caller still passes x, y
+ * and z; the handle comes from bem_setup, which did allocate.
+ *  - Limit: the scratch needed is about nrhs * (48 N + 16 E) bytes in the
+ *    mixed modes (80 N + 32 E in the FP64 modes), E the number of expansion
+ *    coefficients of the tree; a call that needs more than the array returns
+ *    BEM_ERR_INVALID_ARG with the byte counts in bem_last_error().  At
+ *    N = 327,680 (mixed) one call fits two right-hand sides.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *    first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents: the
+ *    call zeroes what must start at zero itself, and calls that overlap on the
+ *    GPU (two streams, two threads, two handles) race on it.
+ */
+#define BEM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int bem_apply_noalloc(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, void* z, int flags,
+                      void* stream);
+
+/*
  * bem_apply_adjoint -- conjugate transpose of bem_apply:
  *   gx = (1/2 I - D)^H g,  gy = S^H g   (either output nullable).
  * The adjoint problem of Section 2.2 uses the same operator; this entry point
