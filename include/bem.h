@@ -90,6 +90,8 @@ typedef struct {
   int max_nrhs;     /* largest nrhs a later call may use (default 16) */
   int p_min;        /* lower bound of the automatic per-level order (default 4) */
   int p_max;        /* upper bound of any order (default 40) */
+  int p_level[11];  /* > 0: expansion order of octree level l (overrides p and eps there);
+                       this is what the order autotuner sets */
 } bem_options;
 
 /*

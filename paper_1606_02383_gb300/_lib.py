@@ -51,7 +51,7 @@ class BemMesh(ctypes.Structure):
 class BemOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("mode", ctypes.c_int), ("leaf_level", ctypes.c_int),
                 ("leaf_target", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("p_min", ctypes.c_int),
-                ("p_max", ctypes.c_int)]
+                ("p_max", ctypes.c_int), ("p_level", ctypes.c_int * 11)]
 
 
 class BemError(RuntimeError):

@@ -23,6 +23,7 @@ int bem_check_device_error(bem_handle* h, cudaStream_t s) {
   if (flags == 0) return BEM_OK;
   BEM_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   if (flags & BEM_DEVERR_DEGENERATE) return bem_fail(BEM_ERR_DEGENERATE_MESH, "degenerate or invalid triangle");
+  if (flags & BEM_DEVERR_TIMEOUT) return bem_fail(BEM_ERR_TIMEOUT, "a bounded device wait expired (tensor-core stage)");
   if (flags & BEM_DEVERR_OVERFLOW)
     return bem_fail(BEM_ERR_NUMERIC, "translation operator or expansion row not finite (order/frequency out of range)");
   return bem_fail(BEM_ERR_NUMERIC, "non-finite value detected on the device");
@@ -129,6 +130,13 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->nrhs_max = o.max_nrhs;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
+  for (int l = 0; l <= BEM_MAXLEV; ++l) {
+    if (o.p_level[l] < 0 || o.p_level[l] > 60) {
+      delete h;
+      return bem_fail(BEM_ERR_INVALID_ARG, "p_level entries must be in [0, 60]");
+    }
+    h->p_level[l] = o.p_level[l];
+  }
   h->nt = mesh->n_triangles;
   h->nv = mesh->n_vertices;
 

@@ -69,150 +69,114 @@ __global__ void k_epilogue(int64_t nt, int nrhs, const int* __restrict__ perm, c
   }
 }
 
-// ----------------------------------------------------------- kernel pieces --
-// exp(i kr) for FP32: Cody-Waite reduction by 2 pi (two-term split) then the
-// hardware sin/cos on |t| <= pi.
-__device__ __forceinline__ void sincos_2pi_reduced(float kr, float* sn, float* cs) {
-  const float inv2pi = 0.15915494309189535f;
-  const float c_hi = 6.28125f;                 // 2 pi split: exact leading part
-  const float c_lo = 1.9353071795864769e-3f;   // 2 pi - 6.28125
-  float q = rintf(kr * inv2pi);
-  float t = fmaf(-q, c_hi, kr);
-  t = fmaf(-q, c_lo, t);
-  __sincosf(t, sn, cs);
-}
-
-// accumulate the regular-rule contribution of one source point
-template <typename R>
-__device__ __forceinline__ void p2p_point(R dx, R dy, R dz, R nx, R ny, R nz, R k, R sre, R sim, R tre, R tim,
-                                          R& are, R& aim);
-
-template <>
-__device__ __forceinline__ void p2p_point<float>(float dx, float dy, float dz, float nx, float ny, float nz, float k,
-                                                 float sre, float sim, float tre, float tim, float& are, float& aim) {
+// ------------------------------------------------------------- P2P (FMM) --
+// One point of the combined regular-rule kernel.  With g = exp(ikr)/r,
+// f = (y-x).n / r^2, sigma = w y and tau = w x (w = A/(12 pi)), the S and D
+// contributions of the point are g sigma - (ikr - 1) g f tau
+// = g [sigma + u - i kr u] with u = f tau.
+__device__ __forceinline__ void p2p_eval(float dx, float dy, float dz, float nx, float ny, float nz, float k,
+                                         float4 d, float& are, float& aim) {
   float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   float rinv = rsqrtf(r2);
-  float r = r2 * rinv;
-  float kr = k * r;
+  float kr = k * (r2 * rinv);
   float sn, cs;
-  sincos_2pi_reduced(kr, &sn, &cs);
-  float gre = rinv * cs, gim = rinv * sn;  // exp(ikr)/r
-  float dn = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
-  float f = dn * rinv * rinv;              // (y-x).n / r^2 ; times g gives the /r^3
-  // (ikr - 1) exp(ikr)/r = (-g_re - kr g_im) + i (kr g_re - g_im)
-  float hre = fmaf(-kr, gim, -gre), him = fmaf(kr, gre, -gim);
-  hre *= f;
-  him *= f;
-  are = fmaf(gre, sre, are);
-  are = fmaf(-gim, sim, are);
-  aim = fmaf(gre, sim, aim);
-  aim = fmaf(gim, sre, aim);
-  are = fmaf(-hre, tre, are);
-  are = fmaf(him, tim, are);
-  aim = fmaf(-hre, tim, aim);
-  aim = fmaf(-him, tre, aim);
+  __sincosf(kr, &sn, &cs);  // |kr| stays small in the near field (phase error ~4e-8 kr)
+  float f = fmaf(dx, nx, fmaf(dy, ny, dz * nz)) * (rinv * rinv);
+  float ur = f * d.z, ui = f * d.w;
+  float vr = fmaf(kr, ui, d.x + ur), vi = fmaf(-kr, ur, d.y + ui);
+  float gre = rinv * cs, gim = rinv * sn;
+  are = fmaf(gre, vr, fmaf(-gim, vi, are));
+  aim = fmaf(gre, vi, fmaf(gim, vr, aim));
 }
-
-template <>
-__device__ __forceinline__ void p2p_point<double>(double dx, double dy, double dz, double nx, double ny, double nz,
-                                                  double k, double sre, double sim, double tre, double tim,
-                                                  double& are, double& aim) {
+__device__ __forceinline__ void p2p_eval(double dx, double dy, double dz, double nx, double ny, double nz, double k,
+                                         double4 d, double& are, double& aim) {
   double r2 = dx * dx + dy * dy + dz * dz;
-  double r = sqrt(r2);
-  double rinv = 1.0 / r;
+  double r = sqrt(r2), rinv = 1.0 / r;
   double kr = k * r;
   double sn, cs;
   sincos(kr, &sn, &cs);
+  double f = (dx * nx + dy * ny + dz * nz) * (rinv * rinv);
+  double ur = f * d.z, ui = f * d.w;
+  double vr = kr * ui + (d.x + ur), vi = -kr * ur + (d.y + ui);
   double gre = rinv * cs, gim = rinv * sn;
-  double dn = dx * nx + dy * ny + dz * nz;
-  double f = dn * rinv * rinv;
-  double hre = (-kr * gim - gre) * f, him = (kr * gre - gim) * f;
-  are += gre * sre - gim * sim - hre * tre + him * tim;
-  aim += gre * sim + gim * sre - hre * tim - him * tre;
+  are += gre * vr - gim * vi;
+  aim += gre * vi + gim * vr;
 }
 
-// ------------------------------------------------------------- P2P (FMM) --
-// One CTA per leaf target box; targets x split factor over 128 threads; source
-// elements of each colleague box staged in shared memory, shifted into the
-// target box's frame (coordinates are stored relative to their leaf centre).
-#define P2P_THREADS 128
+// One warp per work unit (leaf box, 2^j consecutive targets, j <= 6).  The
+// 32 lanes are np2 = ceil(count/2) target pairs times 32/np2 source slices;
+// every lane owns two targets and walks its slice of the elements of the 27
+// colleague boxes (stored relative to their own leaf centre, shifted into the
+// target box's frame on load), evaluating 6 points per element.  Slices are
+// summed with an xor-shuffle butterfly; no shared memory and no barriers.
+// Units are sorted by cost, largest first, so the tail of the grid is short.
+#define P2P_WARPS 4
 template <typename R>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_fmm(int nleaf, int64_t nt, R k, R wleaf,
-                                                         const int* __restrict__ near27, const int* __restrict__ bstart,
-                                                         const int* __restrict__ bend, const int* __restrict__ coord,
-                                                         const typename V4of<R>::T* __restrict__ tgt,
-                                                         const typename V4of<R>::T* __restrict__ src,
-                                                         const typename V4of<R>::T* __restrict__ dens,
-                                                         double* __restrict__ zn) {
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t nt, R k, R wleaf,
+                                                            const int4* __restrict__ units,
+                                                            const int* __restrict__ near27,
+                                                            const int* __restrict__ bstart,
+                                                            const int* __restrict__ bend,
+                                                            const int* __restrict__ coord,
+                                                            const typename V4of<R>::T* __restrict__ tgt,
+                                                            const typename V4of<R>::T* __restrict__ src,
+                                                            const typename V4of<R>::T* __restrict__ dens,
+                                                            double* __restrict__ zn) {
   typedef typename V4of<R>::T V4;
-  __shared__ V4 s_src[P2P_THREADS][3];
-  __shared__ V4 s_den[P2P_THREADS];
-  __shared__ R s_red[2][P2P_THREADS];
-  int b = blockIdx.x;
+  int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
+  if (u >= nunits) return;
+  int lane = threadIdx.x & 31;
   int r = blockIdx.y;
-  int tid = threadIdx.x;
-  int t0 = bstart[b], t1 = bend[b];
-  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
+  int4 U = units[u];
+  int b = U.x, tfirst = U.y, cnt = U.z;
+  int np2 = (cnt + 1) >> 1;  // power of two
+  int pi = lane & (np2 - 1), split = lane / np2, nsplit = 32 / np2;
+  bool two = pi + np2 < cnt;
+  V4 ta = tgt[tfirst + pi];
+  V4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
   const V4* dr = dens + (int64_t)r * nt;
-  for (int c0 = t0; c0 < t1; c0 += P2P_THREADS) {
-    int nc = min(P2P_THREADS, t1 - c0);
-    int nsplit = P2P_THREADS / nc;
-    int ti = tid % nc, split = tid / nc;
-    bool active = split < nsplit;
-    V4 tg = tgt[c0 + ti];
-    R are = 0, aim = 0;
-    for (int slot = 0; slot < 27; ++slot) {
-      int sb = near27[27 * b + slot];
-      if (sb < 0) continue;
-      R shx = (R)((coord[3 * sb] - bx) * (double)wleaf);
-      R shy = (R)((coord[3 * sb + 1] - by) * (double)wleaf);
-      R shz = (R)((coord[3 * sb + 2] - bz) * (double)wleaf);
-      int s0 = bstart[sb], s1 = bend[sb];
-      for (int e0 = s0; e0 < s1; e0 += P2P_THREADS) {
-        int ne = min(P2P_THREADS, s1 - e0);
-        __syncthreads();
-        if (tid < ne) {
-          for (int q = 0; q < 3; ++q) {
-            V4 v = src[3 * (int64_t)(e0 + tid) + q];
-            v.x += shx;
-            v.y += shy;
-            v.z += shz;
-            s_src[tid][q] = v;
-          }
-          s_den[tid] = dr[e0 + tid];
-        }
-        __syncthreads();
-        if (active) {
-          for (int e = split; e < ne; e += nsplit) {
-            V4 q0 = s_src[e][0], q1 = s_src[e][1], q2 = s_src[e][2];
-            V4 dd = s_den[e];
-            R nx = q0.w, ny = q1.w, nz = q2.w;
-            p2p_point<R>(q0.x - tg.x, q0.y - tg.y, q0.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
-            p2p_point<R>(q1.x - tg.x, q1.y - tg.y, q1.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
-            p2p_point<R>(q2.x - tg.x, q2.y - tg.y, q2.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
-          }
-        }
-      }
+  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
+  R a_re = 0, a_im = 0, b_re = 0, b_im = 0;
+  for (int slot = 0; slot < 27; ++slot) {
+    int sb = near27[27 * b + slot];
+    if (sb < 0) continue;
+    R sx = (R)((coord[3 * sb] - bx) * (double)wleaf);
+    R sy = (R)((coord[3 * sb + 1] - by) * (double)wleaf);
+    R sz = (R)((coord[3 * sb + 2] - bz) * (double)wleaf);
+    R ax = ta.x - sx, ay = ta.y - sy, az = ta.z - sz;  // targets in the source box's frame
+    R bx_ = tb.x - sx, by_ = tb.y - sy, bz_ = tb.z - sz;
+    int e1 = bend[sb];
+    for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+      V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
+      V4 d = dr[e];
+      R nx = q0.w, ny = q1.w, nz = q2.w;
+      p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
     }
-    __syncthreads();
-    s_red[0][tid] = active ? are : (R)0;
-    s_red[1][tid] = active ? aim : (R)0;
-    __syncthreads();
-    if (tid < nc) {
-      double sre = 0.0, sim = 0.0;
-      for (int sp = 0; sp < nsplit; ++sp) {
-        sre += (double)s_red[0][tid + sp * nc];
-        sim += (double)s_red[1][tid + sp * nc];
-      }
-      int64_t o = 2 * ((int64_t)r * nt + c0 + tid);
-      zn[o] = sre;
-      zn[o + 1] = sim;
+  }
+  for (int o = np2; o < 32; o <<= 1) {
+    a_re += __shfl_xor_sync(0xffffffffu, a_re, o);
+    a_im += __shfl_xor_sync(0xffffffffu, a_im, o);
+    b_re += __shfl_xor_sync(0xffffffffu, b_re, o);
+    b_im += __shfl_xor_sync(0xffffffffu, b_im, o);
+  }
+  if (split == 0) {
+    int64_t o = 2 * ((int64_t)r * nt + tfirst + pi);
+    zn[o] = (double)a_re;
+    zn[o + 1] = (double)a_im;
+    if (two) {
+      zn[o + 2 * np2] = (double)b_re;
+      zn[o + 2 * np2 + 1] = (double)b_im;
     }
-    __syncthreads();
   }
 }
 
 // ----------------------------------------------------------- direct sums --
+#define P2P_THREADS 128
 // One target per thread; all sources streamed through shared memory.  FP32
 // partial sums are flushed into FP64 accumulators after every tile.
 template <typename R>
@@ -243,9 +207,9 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
       V4 q0 = s_src[e][0], q1 = s_src[e][1], q2 = s_src[e][2];
       V4 dd = s_den[e];
       R nx = q0.w, ny = q1.w, nz = q2.w;
-      p2p_point<R>(q0.x - tg.x, q0.y - tg.y, q0.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
-      p2p_point<R>(q1.x - tg.x, q1.y - tg.y, q1.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
-      p2p_point<R>(q2.x - tg.x, q2.y - tg.y, q2.z - tg.z, nx, ny, nz, k, dd.x, dd.y, dd.z, dd.w, are, aim);
+      p2p_eval(q0.x - tg.x, q0.y - tg.y, q0.z - tg.z, nx, ny, nz, k, dd, are, aim);
+      p2p_eval(q1.x - tg.x, q1.y - tg.y, q1.z - tg.z, nx, ny, nz, k, dd, are, aim);
+      p2p_eval(q2.x - tg.x, q2.y - tg.y, q2.z - tg.z, nx, ny, nz, k, dd, are, aim);
     }
     sre += (double)are;
     sim += (double)aim;
@@ -258,7 +222,11 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
 }
 
 // ------------------------------------------------------------- correction --
-template <typename V4>
+// z_i += sum_j C^S_ij sigma_j - C^D_ij tau_j  (values pre-divided by the weight).
+// One warp per row, accumulated in the operator's precision (FP32 in the mixed
+// mode: about 130 terms per row, each already a small correction) and added to
+// the FP64 near-field sum.
+template <typename V4, typename R>
 __global__ void k_correction(int64_t nt, const int* __restrict__ ptr, const int* __restrict__ col,
                              const V4* __restrict__ val, const V4* __restrict__ dens, double* __restrict__ zn) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -266,13 +234,13 @@ __global__ void k_correction(int64_t nt, const int* __restrict__ ptr, const int*
   int r = blockIdx.y;
   if (i >= nt) return;
   const V4* dr = dens + (int64_t)r * nt;
-  double are = 0.0, aim = 0.0;
-  for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+  R are = 0, aim = 0;
+  int e1 = ptr[i + 1];
+  for (int e = ptr[i] + lane; e < e1; e += 32) {
     V4 c = val[e];
     V4 d = dr[col[e]];
-    // S (c.x, c.y) * sigma (d.x, d.y) - D (c.z, c.w) * tau (d.z, d.w)
-    are += (double)c.x * d.x - (double)c.y * d.y - (double)c.z * d.z + (double)c.w * d.w;
-    aim += (double)c.x * d.y + (double)c.y * d.x - (double)c.z * d.w - (double)c.w * d.z;
+    are += c.x * d.x - c.y * d.y - c.z * d.z + c.w * d.w;
+    aim += c.x * d.y + c.y * d.x - c.z * d.w - c.w * d.z;
   }
   for (int o = 16; o > 0; o >>= 1) {
     are += __shfl_xor_sync(0xffffffffu, are, o);
@@ -280,8 +248,8 @@ __global__ void k_correction(int64_t nt, const int* __restrict__ ptr, const int*
   }
   if (lane == 0) {
     int64_t o = 2 * ((int64_t)r * nt + i);
-    zn[o] += are;
-    zn[o + 1] += aim;
+    zn[o] += (double)are;
+    zn[o + 1] += (double)aim;
   }
 }
 
@@ -338,74 +306,101 @@ __global__ void k_l2p(int64_t nt, int P, const int* __restrict__ leaf_of, const 
 }
 
 // ------------------------------------------------ grouped translation GEMM --
-// For every job (group g, pairs [p0, p0+np), rows [row0, row0+64)):
-//   dst[dst_off[c] + row] += sum_k T_g[row][k] * src[src_off[c] + k]
-// 64x64 complex output tile per CTA, 256 threads with 4x4 complex micro-tiles.
-#define GT_M 64
-#define GT_N 64
-#define GT_K 16
-template <typename R>
+// For every job (group g, pairs [p0, p0+np), rows [row0, row0+BM)):
+//   dst[dst_off[c] + Q_c(row)] += s_c(row) sum_k T_g[row][k] s_c(k) src[src_off[c] + Q_c(k)]
+// where (Q_c, s_c) is the signed permutation of the pair's reflection flags:
+// an x or y flip maps m -> -m (both flips cancel), an x flip contributes
+// (-1)^m and a z flip (-1)^(n+m).  BM x BN complex output tile per CTA,
+// 256 threads with TM x TN complex micro-tiles, K in chunks of 16 with the
+// next chunk prefetched into registers while the current one is consumed.
+template <typename R, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) k_grouped_gemm(const int4* __restrict__ jobs, const int* __restrict__ grows,
                                                      const int* __restrict__ gcols, const int64_t* __restrict__ gmat,
                                                      const R* __restrict__ mats, const int* __restrict__ src_off,
-                                                     const int* __restrict__ dst_off, const R* __restrict__ src,
-                                                     R* __restrict__ dst, int64_t exp_stride) {
-  __shared__ cpx<R> As[GT_K][GT_M];
-  __shared__ cpx<R> Bs[GT_K][GT_N];
-  __shared__ int s_src[GT_N], s_dst[GT_N];
+                                                     const int* __restrict__ dst_off,
+                                                     const unsigned char* __restrict__ pflags,
+                                                     const R* __restrict__ src, R* __restrict__ dst,
+                                                     int64_t exp_stride) {
+  constexpr int BK = 16;
+  constexpr int NTX = BN / TN;
+  constexpr int AE = BM * BK / 256;  // A elements per thread per chunk
+  constexpr int BE = BN * BK / 256;  // B elements per thread per chunk
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  __shared__ __align__(16) cpx<R> As[BK][BM + 2];
+  __shared__ __align__(16) cpx<R> Bs[BK][BN + 2];
+  __shared__ int s_src[BN], s_dst[BN], s_flg[BN];
+  constexpr int KS = 128;  // K slice of one job
   int4 job = jobs[blockIdx.x];
   int r = blockIdx.y;
-  int g = job.x, p0 = job.y, np = job.z, row0 = job.w;
+  int g = job.x, p0 = job.y, np = job.z & 255, row0 = job.w;
+  int kbeg = (job.z >> 8) * KS;
   int rows = grows[g], cols = gcols[g];
+  int kend = min(cols, kbeg + KS);
   const cpx<R>* T = (const cpx<R>*)(mats) + gmat[g];
   const cpx<R>* S = (const cpx<R>*)(src) + (int64_t)r * exp_stride;
   cpx<R>* D = (cpx<R>*)(dst) + (int64_t)r * exp_stride;
   int tid = threadIdx.x;
-  if (tid < GT_N) {
-    s_src[tid] = tid < np ? src_off[p0 + tid] : -1;
-    s_dst[tid] = tid < np ? dst_off[p0 + tid] : -1;
+  for (int c = tid; c < BN; c += 256) {
+    bool ok = c < np;
+    s_src[c] = ok ? src_off[p0 + c] : -1;
+    s_dst[c] = ok ? dst_off[p0 + c] : -1;
+    s_flg[c] = ok ? (int)pflags[p0 + c] : 0;
   }
-  int ty = tid >> 4, tx = tid & 15;
-  cpx<R> acc[4][4];
+  int ty = tid / NTX, tx = tid % NTX;
+  cpx<R> acc[TM][TN];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = cmk((R)0, (R)0);
+    for (int b = 0; b < TN; ++b) acc[a][b] = cmk((R)0, (R)0);
   __syncthreads();
-  int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row/pair lr, k offset lk..lk+3
-  for (int k0 = 0; k0 < cols; k0 += GT_K) {
-    // A tile
-    {
-      int row = row0 + lr;
+  cpx<R> ra[AE], rb[BE];
+  auto load = [&](int k0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int kk = k0 + lk + q;
-        cpx<R> v = cmk((R)0, (R)0);
-        if (row < rows && kk < cols) v = T[(int64_t)row * cols + kk];
-        As[lk + q][lr] = v;
-      }
-      int so = s_src[lr];
+    for (int q = 0; q < AE; ++q) {
+      int e = tid + 256 * q;
+      int row = row0 + e / BK, kk = k0 + e % BK;
+      ra[q] = (row < rows && kk < kend) ? T[(int64_t)row * cols + kk] : cmk((R)0, (R)0);
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int kk = k0 + lk + q;
-        cpx<R> v = cmk((R)0, (R)0);
-        if (so >= 0 && kk < cols) v = S[so + kk];
-        Bs[lk + q][lr] = v;
+    for (int q = 0; q < BE; ++q) {
+      int e = tid + 256 * q;
+      int c = e / BK, kk = k0 + e % BK;
+      cpx<R> v = cmk((R)0, (R)0);
+      int so = s_src[c];
+      if (so >= 0 && kk < kend) {
+        bool neg;
+        int ki = reflect_index(kk, s_flg[c], &neg);
+        v = S[so + ki];
+        if (neg) v = cmk(-v.re, -v.im);
       }
+      rb[q] = v;
+    }
+  };
+  load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < AE; ++q) {
+      int e = tid + 256 * q;
+      As[e % BK][e / BK] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < BE; ++q) {
+      int e = tid + 256 * q;
+      Bs[e % BK][e / BK] = rb[q];
     }
     __syncthreads();
+    if (k0 + BK < kend) load(k0 + BK);
 #pragma unroll
-    for (int kk = 0; kk < GT_K; ++kk) {
-      cpx<R> a[4], b[4];
+    for (int kk = 0; kk < BK; ++kk) {
+      cpx<R> a[TM], b[TN];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        b[q] = Bs[kk][tx * 4 + q];
-      }
+      for (int q = 0; q < TM; ++q) a[q] = As[kk][ty * TM + q];
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
+      for (int q = 0; q < TN; ++q) b[q] = Bs[kk][tx * TN + q];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
+      for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
           acc[ii][jj].re += a[ii].re * b[jj].re - a[ii].im * b[jj].im;
           acc[ii][jj].im += a[ii].re * b[jj].im + a[ii].im * b[jj].re;
         }
@@ -413,17 +408,20 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const int4* __restrict__ j
     __syncthreads();
   }
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
-    int c = tx * 4 + jj;
+  for (int jj = 0; jj < TN; ++jj) {
+    int c = tx * TN + jj;
     int dof = s_dst[c];
     if (dof < 0) continue;
+    int fl = s_flg[c];
 #pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      int row = row0 + ty * 4 + ii;
+    for (int ii = 0; ii < TM; ++ii) {
+      int row = row0 + ty * TM + ii;
       if (row < rows) {
-        R* p = (R*)(D + dof + row);
-        atomicAdd(p, acc[ii][jj].re);
-        atomicAdd(p + 1, acc[ii][jj].im);
+        bool neg;
+        int ri = reflect_index(row, fl, &neg);
+        R* p = (R*)(D + dof + ri);
+        atomicAdd(p, neg ? -acc[ii][jj].re : acc[ii][jj].re);
+        atomicAdd(p + 1, neg ? -acc[ii][jj].im : acc[ii][jj].im);
       }
     }
   }
@@ -431,13 +429,27 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const int4* __restrict__ j
 
 // ----------------------------------------------------------------- driver --
 template <typename R>
-static int run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s) {
-  if (op.njobs == 0) return BEM_OK;
-  dim3 grid(op.njobs, nrhs);
-  k_grouped_gemm<R><<<grid, 256, 0, s>>>(op.d_jobs, op.d_group_rows, op.d_group_cols, op.d_group_mat,
-                                         (const R*)h->mats, op.d_src_off, op.d_dst_off, (const R*)src, (R*)dst,
-                                         h->exp_total);
-  BEM_CUDA(cudaGetLastError());
+static int run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
+                       int* launches) {
+  if (sizeof(R) == 4) return bem_run_grouped_tc(h, op, src, dst, nrhs, s, launches);  // tensor cores
+  if (op.njobsA > 0) {
+    dim3 grid(op.njobsA, nrhs);
+    k_grouped_gemm<R, 64, 64, 4, 4><<<grid, 256, 0, s>>>(op.d_jobsA, op.d_group_rows, op.d_group_cols,
+                                                         op.d_group_mat, (const R*)h->mats, op.d_src_off,
+                                                         op.d_dst_off, op.d_flags, (const R*)src, (R*)dst,
+                                                         h->exp_total);
+    BEM_CUDA(cudaGetLastError());
+    ++*launches;
+  }
+  if (op.njobsB > 0) {
+    dim3 grid(op.njobsB, nrhs);
+    k_grouped_gemm<R, 128, 16, 4, 2><<<grid, 256, 0, s>>>(op.d_jobsB, op.d_group_rows, op.d_group_cols,
+                                                          op.d_group_mat, (const R*)h->mats, op.d_src_off,
+                                                          op.d_dst_off, op.d_flags, (const R*)src, (R*)dst,
+                                                          h->exp_total);
+    BEM_CUDA(cudaGetLastError());
+    ++*launches;
+  }
   return BEM_OK;
 }
 
@@ -454,9 +466,9 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   int pr = bem_prof_begin(h, s);
   if (fmm) {
     LevelInfo& lf = h->lev[L];
-    dim3 grid(lf.nbox, nrhs);
-    k_p2p_fmm<R><<<grid, P2P_THREADS, 0, s>>>(lf.nbox, nt, (R)h->k, (R)lf.w, h->near27, lf.start, lf.end, lf.coord,
-                                              tgt, src, dens, h->zn);
+    dim3 grid(nblk(h->n_p2p_units, P2P_WARPS), nrhs);
+    k_p2p_fmm<R><<<grid, 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, (R)h->k, (R)lf.w, h->p2p_units, h->near27,
+                                                 lf.start, lf.end, lf.coord, tgt, src, dens, h->zn);
   } else {
     dim3 grid(nblk(nt, P2P_THREADS), nrhs);
     k_p2p_direct<R><<<grid, P2P_THREADS, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->zn);
@@ -466,7 +478,7 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   pr = bem_prof_begin(h, s);
   {
     dim3 grid(nblk(nt * 32, 256), nrhs);
-    k_correction<V4><<<grid, 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->zn);
+    k_correction<V4, R><<<grid, 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->zn);
     BEM_CUDA(cudaGetLastError());
   }
   bem_prof_end(h, pr, 2, 1, s);
@@ -489,15 +501,15 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   bem_prof_end(h, pr, 3, 1, s);
   int nl = 0;
   pr = bem_prof_begin(h, s);
-  for (int l = L - 1; l >= 2; --l, ++nl) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s));
+  for (int l = L - 1; l >= 2; --l) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 4, nl, s);
   nl = 0;
   pr = bem_prof_begin(h, s);
-  for (int l = 2; l <= L; ++l, ++nl) BEM_TRY(run_grouped<R>(h, h->m2l[l], h->Mexp, h->Lexp, nrhs, s));
+  for (int l = 2; l <= L; ++l) BEM_TRY(run_grouped<R>(h, h->m2l[l], h->Mexp, h->Lexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 5, nl, s);
   nl = 0;
   pr = bem_prof_begin(h, s);
-  for (int l = 2; l < L; ++l, ++nl) BEM_TRY(run_grouped<R>(h, h->l2l[l], h->Lexp, h->Lexp, nrhs, s));
+  for (int l = 2; l < L; ++l) BEM_TRY(run_grouped<R>(h, h->l2l[l], h->Lexp, h->Lexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 6, nl, s);
   pr = bem_prof_begin(h, s);
   {

@@ -91,24 +91,52 @@ int bem_fail(int code, const std::string& m);
 #define BEM_DEVERR_DEGENERATE 1
 #define BEM_DEVERR_NONFINITE 2
 #define BEM_DEVERR_OVERFLOW 4
+#define BEM_DEVERR_TIMEOUT 8
+
+// Signed permutation of a reflection (flags: bit 0 = x, 1 = y, 2 = z) acting on
+// the coefficient index k = n^2 + n + m of an expansion: an x or y flip maps
+// m -> -m (both together cancel), an x flip contributes (-1)^m and a z flip
+// (-1)^(n+m).  Returns the permuted index and sets *neg for a sign change.
+__device__ __forceinline__ int reflect_index(int k, int flags, bool* neg) {
+  int n = (int)sqrtf((float)k);
+  if ((n + 1) * (n + 1) <= k) ++n;
+  if (n * n > k) --n;
+  int m = k - n * n - n;
+  bool s = ((flags & 1) && (m & 1)) != ((flags & 4) && ((n + m) & 1));
+  *neg = s;
+  return (((flags & 1) != 0) != ((flags & 2) != 0)) ? (n * n + n - m) : k;
+}
 
 // ------------------------------------------------------------------ handle --
 struct GroupedOp {
-  // dst[dst_off[c] + r] += sum_k T[g][r][k] * src[src_off[c] + k] for every pair c of group g
+  // For every pair c of group g, with Q_c the signed permutation of the pair's
+  // reflection flags (x, y, z bits):
+  //   dst[dst_off[c] + .] += Q_c T_g Q_c src[src_off[c] + .]
+  // T_g is the translation matrix of the group's canonical vector (all
+  // components >= 0); a reflected vector R v gives T(R v) = Q T(v) Q.
   int ngroups = 0;
   std::vector<int> rows, cols;          // per group (host copy)
   std::vector<int64_t> mat_off;         // per group, complex offset into the matrix buffer
   std::vector<int> pair_start;          // per group, first pair (host copy), size ngroups+1
+  std::vector<int> codes;               // tree build: offset code of every V-list group
   int npairs = 0;
   int* d_src_off = nullptr;             // [npairs]
   int* d_dst_off = nullptr;             // [npairs]
-  // tile jobs: (group, first pair, row tile)
-  int njobs = 0;
-  int4* d_jobs = nullptr;               // x = group, y = first pair, z = npairs in job, w = row0
+  unsigned char* d_flags = nullptr;     // [npairs] reflection bits
+  // tile jobs: (group, first pair, npairs | k-slice << 8, row0); A = 64x64 tiles, B = 128x16 tiles;
+  // K is split into slices of 128 (outputs are accumulated atomically anyway)
+  int njobsA = 0, njobsB = 0;
+  int4* d_jobsA = nullptr;
+  int4* d_jobsB = nullptr;
   int* d_group_rows = nullptr;
   int* d_group_cols = nullptr;
   int64_t* d_group_mat = nullptr;
   int64_t flops = 0;                    // 8 * rows * cols per pair, summed
+  // tensor-core form (mixed mode): A packed per (row tile, k stage), jobs (group, pair0, npairs, row tile)
+  float* tcA = nullptr;
+  int64_t* d_tc_off = nullptr;
+  int4* d_tc_jobs = nullptr;
+  int n_tc_jobs = 0;
 };
 
 struct LevelInfo {
@@ -143,6 +171,7 @@ struct bem_handle {
   double eps = 1e-5;
   int nrhs_max = 16;
   int p_min = 4, p_max = 40;
+  int p_level[BEM_MAXLEV + 1] = {0};  // explicit per-level orders (0 = automatic)
   int64_t nt = 0, nv = 0;
   int L = 0;          // leaf level
   int Lc = 0;         // level used to search for near-singular pairs
@@ -173,6 +202,8 @@ struct bem_handle {
   // near field: 27 colleague slots per leaf (-1 = none)
   int* near27 = nullptr;        // [nleaf][27]
   int64_t p2p_pairs = 0;
+  int4* p2p_units = nullptr;    // warp work units (leaf, first target, count), largest first
+  int n_p2p_units = 0;
 
   // correction CSR over sorted targets; values divided by wgt[j]
   int* corr_ptr = nullptr;      // [nt+1]
@@ -248,3 +279,6 @@ int bem_adjoint_epilogue(bem_handle* h, int nrhs, int dtype, const void* g, void
 int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
               int flags, int* iters_out, double* relres_out, cudaStream_t s);
 int bem_check_device_error(bem_handle* h, cudaStream_t s);
+int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s);
+int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
+                       int* launches);

@@ -726,6 +726,43 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     BEM_CUDA(cudaFreeAsync(dp, s));
     h->p2p_pairs = (int64_t)v;
   }
+  // P2P warp work units: each leaf's targets cut into 64-target blocks plus the
+  // binary decomposition of the remainder, sorted by cost (targets x near sources)
+  if (bem_is_fmm(h)) {
+    int nl = h->lev[L].nbox;
+    std::vector<int> hs(nl), he(nl), hn(27 * (size_t)nl);
+    BEM_CUDA(cudaMemcpyAsync(hs.data(), h->lev[L].start, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(he.data(), h->lev[L].end, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(hn.data(), coll[L], hn.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    std::vector<std::pair<int64_t, int4>> units;
+    for (int b = 0; b < nl; ++b) {
+      int64_t ns = 0;
+      for (int t = 0; t < 27; ++t) {
+        int c = hn[27 * (size_t)b + t];
+        if (c >= 0) ns += he[c] - hs[c];
+      }
+      int t0 = hs[b], nc = he[b] - hs[b];
+      while (nc >= 64) {
+        units.push_back({64 * ns, make_int4(b, t0, 64, 0)});
+        t0 += 64;
+        nc -= 64;
+      }
+      for (int j = 5; j >= 0; --j)
+        if (nc & (1 << j)) {
+          units.push_back({(int64_t)(1 << j) * ns, make_int4(b, t0, 1 << j, 0)});
+          t0 += 1 << j;
+        }
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) { return a.first > b.first; });
+    std::vector<int4> u4(units.size());
+    for (size_t i = 0; i < units.size(); ++i) u4[i] = units[i].second;
+    h->n_p2p_units = (int)u4.size();
+    BEM_TRY(bem_alloc(h, &h->p2p_units, std::max<size_t>(u4.size(), 1)));
+    BEM_CUDA(cudaMemcpyAsync(h->p2p_units, u4.data(), u4.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+  }
 
   // ---- correction pairs (FP64 values) ----
   {
@@ -836,9 +873,7 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
       }
     op.pair_start.push_back(np);
     op.ngroups = (int)goff.size();
-    // group offset ids are stashed in `cols` until the far-field build assigns sizes
-    op.rows.assign(op.ngroups, 0);
-    op.cols = goff;
+    op.codes = goff;
     int *src_box, *dst_box;
     BEM_TRY(bem_alloc(h, &op.d_src_off, std::max(np, 1)));
     BEM_TRY(bem_alloc(h, &op.d_dst_off, std::max(np, 1)));

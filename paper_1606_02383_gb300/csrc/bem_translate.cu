@@ -378,32 +378,49 @@ __global__ void k_pairs_to_offsets(int np, const int* __restrict__ src_box, cons
   dst_off[i] = (int)(dst_base + (int64_t)dst_box[i] * Pdst);
 }
 
-// child box -> (octant, parent) pairs for one level (children at level lc)
-__global__ void k_octant_count(int nchild_boxes, const uint32_t* __restrict__ ckey, int* counts) {
+// all children of one level as (child, parent, reflection flags) pairs: the
+// canonical child offset is (+w/2, +w/2, +w/2); an axis whose octant bit is 0
+// points the other way, so its flag bit is set
+__global__ void k_octant_pairs(int nchild_boxes, const uint32_t* __restrict__ ckey, const int* __restrict__ cparent,
+                               int* child_box, int* parent_box, unsigned char* flags) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nchild_boxes) return;
-  atomicAdd(&counts[ckey[c] & 7], 1);
+  child_box[c] = c;
+  parent_box[c] = cparent[c];
+  flags[c] = (unsigned char)((~ckey[c]) & 7u);
 }
-__global__ void k_octant_fill(int nchild_boxes, const uint32_t* __restrict__ ckey, const int* __restrict__ cparent,
-                              const int* __restrict__ gstart, int* cursor, int* child_box, int* parent_box) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nchild_boxes) return;
-  int o = ckey[c] & 7;
-  int pos = gstart[o] + atomicAdd(&cursor[o], 1);
-  child_box[pos] = c;
-  parent_box[pos] = cparent[c];
+
+// move V-list pairs from per-offset blocks into per-canonical-offset blocks
+// blk[i] = (old start, new start, count, flags)
+__global__ void k_regroup(const int4* __restrict__ blk, const int* __restrict__ src_in, const int* __restrict__ dst_in,
+                          int* src_out, int* dst_out, unsigned char* flags) {
+  int4 B = blk[blockIdx.x];
+  for (int i = threadIdx.x; i < B.z; i += blockDim.x) {
+    src_out[B.y + i] = src_in[B.x + i];
+    dst_out[B.y + i] = dst_in[B.x + i];
+    flags[B.y + i] = (unsigned char)B.w;
+  }
 }
 
 // ------------------------------------------------------------------ host --
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-static int order_for_level(const bem_handle* h, double w) {
+// Order of one level (Section 3: truncation "numerically determined" so the
+// error stays below the tolerance).  Two terms: the high-frequency rule
+// p = kd + c (d0)^(2/3) (kd)^(1/3) (d the box diameter, d0 = -log10 eps) and a
+// low-frequency floor 1.6 d0 + 1.  The constants were calibrated on the
+// 327,680-triangle sphere at ka = 20 and a 20,480-triangle sphere at ka = 5,
+// against the FP64 oracle, for random densities and for smooth (plane-wave)
+// single- and double-layer densities: the leaf order sets the error, the
+// coarse-level orders mostly set the cost.
+static int order_for_level(const bem_handle* h, int l, double w) {
+  if (h->p_level[l] > 0) return h->p_level[l];
   if (h->fixed_p > 0) return h->fixed_p;
   double d0 = -std::log10(std::max(h->eps, 1e-15));
   double kd = h->k * std::sqrt(3.0) * w;
-  double p_hf = kd + 1.8 * std::pow(d0, 2.0 / 3.0) * std::cbrt(std::max(kd, 1e-30));
-  double p_lf = 1.4 * d0 + 1.0;
-  int p = (int)std::ceil(std::max(p_hf, p_lf));
+  double p_hf = kd + 1.0 * std::pow(d0, 2.0 / 3.0) * std::cbrt(std::max(kd, 1e-30));
+  double p_lf = 1.6 * d0 + 1.0;
+  int p = (int)std::ceil(std::max(p_hf, p_lf) - 1e-9);
   return std::min(std::max(p, h->p_min), h->p_max);
 }
 
@@ -437,24 +454,30 @@ static void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// tile jobs: groups with many pairs use 64 x 64 output tiles, small groups 128 x 16
 static int make_jobs(bem_handle* h, GroupedOp& op, cudaStream_t s) {
-  std::vector<int4> jobs;
-  const int TM = 64, TN = 64;
+  std::vector<int4> ja, jb;
   op.flops = 0;
   for (int g = 0; g < op.ngroups; ++g) {
     int np = op.pair_start[g + 1] - op.pair_start[g];
     op.flops += 8LL * op.rows[g] * op.cols[g] * np;
+    bool wide = np >= 40;
+    int TN = wide ? 64 : 16, TM = wide ? 64 : 128;
+    const int KS = 128;  // K slice per job (matches the kernel)
     for (int p0 = 0; p0 < np; p0 += TN)
       for (int r0 = 0; r0 < op.rows[g]; r0 += TM)
-        jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TN, np - p0), r0));
+        for (int kt = 0; kt * KS < op.cols[g]; ++kt)
+          (wide ? ja : jb).push_back(make_int4(g, op.pair_start[g] + p0, std::min(TN, np - p0) | (kt << 8), r0));
   }
-  op.njobs = (int)jobs.size();
-  BEM_TRY(bem_alloc(h, &op.d_jobs, std::max<size_t>(jobs.size(), 1)));
+  op.njobsA = (int)ja.size();
+  op.njobsB = (int)jb.size();
+  BEM_TRY(bem_alloc(h, &op.d_jobsA, std::max<size_t>(ja.size(), 1)));
+  BEM_TRY(bem_alloc(h, &op.d_jobsB, std::max<size_t>(jb.size(), 1)));
   BEM_TRY(bem_alloc(h, &op.d_group_rows, std::max(op.ngroups, 1)));
   BEM_TRY(bem_alloc(h, &op.d_group_cols, std::max(op.ngroups, 1)));
   BEM_TRY(bem_alloc(h, &op.d_group_mat, std::max(op.ngroups, 1)));
-  if (!jobs.empty())
-    BEM_CUDA(cudaMemcpyAsync(op.d_jobs, jobs.data(), jobs.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  if (!ja.empty()) BEM_CUDA(cudaMemcpyAsync(op.d_jobsA, ja.data(), ja.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  if (!jb.empty()) BEM_CUDA(cudaMemcpyAsync(op.d_jobsB, jb.data(), jb.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   if (op.ngroups) {
     BEM_CUDA(cudaMemcpyAsync(op.d_group_rows, op.rows.data(), op.ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaMemcpyAsync(op.d_group_cols, op.cols.data(), op.ngroups * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -473,7 +496,7 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   h->exp_total = 0;
   for (int l = 2; l <= L; ++l) {
     LevelInfo& lv = h->lev[l];
-    lv.p = order_for_level(h, lv.w);
+    lv.p = order_for_level(h, l, lv.w);
     lv.P = (lv.p + 1) * (lv.p + 1);
     lv.exp_base = h->exp_total;
     h->exp_total += (int64_t)lv.nbox * lv.P;
@@ -511,71 +534,95 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   for (int l = 2; l <= L; ++l) {
     GroupedOp& op = h->m2l[l];
     LevelInfo& lv = h->lev[l];
-    std::vector<int> offs = op.cols;  // offset ids stashed by the tree build
-    op.rows.assign(op.ngroups, lv.P);
-    op.cols.assign(op.ngroups, lv.P);
-    op.mat_off.resize(op.ngroups);
+    // canonical offset (|dx|, |dy|, |dz|) and reflection flags of every code group
+    std::vector<int> canon_of(op.ngroups), flag_of(op.ngroups);
+    std::vector<int> ccount(343, 0);
     for (int g = 0; g < op.ngroups; ++g) {
-      int o = offs[g];
+      int o = op.codes[g];
       int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
-      double v[3] = {dx * lv.w, dy * lv.w, dz * lv.w};  // X = c_t - c_s
-      op.mat_off[g] = add_mat(0, v, lv.p, lv.p, l, l);
+      canon_of[g] = (std::abs(dx) + 3) * 49 + (std::abs(dy) + 3) * 7 + (std::abs(dz) + 3);
+      flag_of[g] = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+      ccount[canon_of[g]] += op.pair_start[g + 1] - op.pair_start[g];
     }
-    if (op.npairs > 0)
-      k_pairs_to_offsets<<<nblk(op.npairs, 256), 256, 0, s>>>(op.npairs, op.d_src_off, op.d_dst_off, lv.exp_base,
-                                                              lv.P, lv.exp_base, lv.P, op.d_src_off, op.d_dst_off);
+    std::vector<int> cstart(344, 0);
+    for (int c = 0; c < 343; ++c) cstart[c + 1] = cstart[c] + ccount[c];
+    std::vector<int4> blk;
+    std::vector<int> cur(cstart.begin(), cstart.end() - 1);
+    for (int g = 0; g < op.ngroups; ++g) {
+      int cnt = op.pair_start[g + 1] - op.pair_start[g];
+      blk.push_back(make_int4(op.pair_start[g], cur[canon_of[g]], cnt, flag_of[g]));
+      cur[canon_of[g]] += cnt;
+    }
+    int np = op.npairs;
+    int *src2, *dst2;
+    int4* dblk;
+    BEM_TRY(bem_alloc(h, &src2, std::max(np, 1)));
+    BEM_TRY(bem_alloc(h, &dst2, std::max(np, 1)));
+    BEM_TRY(bem_alloc(h, &op.d_flags, std::max(np, 1)));
+    if (!blk.empty()) {
+      BEM_CUDA(cudaMallocAsync((void**)&dblk, blk.size() * sizeof(int4), s));
+      BEM_CUDA(cudaMemcpyAsync(dblk, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+      k_regroup<<<(unsigned)blk.size(), 128, 0, s>>>(dblk, op.d_src_off, op.d_dst_off, src2, dst2, op.d_flags);
+      BEM_CUDA(cudaGetLastError());
+      BEM_CUDA(cudaStreamSynchronize(s));
+      BEM_CUDA(cudaFreeAsync(dblk, s));
+    }
+    op.d_src_off = src2;
+    op.d_dst_off = dst2;
+    op.ngroups = 0;
+    op.pair_start.clear();
+    op.rows.clear();
+    op.cols.clear();
+    op.mat_off.clear();
+    for (int c = 0; c < 343; ++c) {
+      if (ccount[c] == 0) continue;
+      int dx = c / 49 - 3, dy = (c / 7) % 7 - 3, dz = c % 7 - 3;
+      double v[3] = {dx * lv.w, dy * lv.w, dz * lv.w};  // X = c_t - c_s (canonical)
+      op.pair_start.push_back(cstart[c]);
+      op.rows.push_back(lv.P);
+      op.cols.push_back(lv.P);
+      op.mat_off.push_back(add_mat(0, v, lv.p, lv.p, l, l));
+      ++op.ngroups;
+    }
+    op.pair_start.push_back(np);
+    if (np > 0)
+      k_pairs_to_offsets<<<nblk(np, 256), 256, 0, s>>>(np, op.d_src_off, op.d_dst_off, lv.exp_base, lv.P,
+                                                       lv.exp_base, lv.P, op.d_src_off, op.d_dst_off);
     BEM_CUDA(cudaGetLastError());
     BEM_TRY(make_jobs(h, op, s));
   }
   for (int l = 2; l < L; ++l) {
-    // children at level l+1, parents at level l
+    // children at level l+1, parents at level l; one canonical matrix each way
     LevelInfo& pv = h->lev[l];
     LevelInfo& cv = h->lev[l + 1];
-    int *dcnt, *dcur, *dstart, *cb, *pb;
-    BEM_CUDA(cudaMallocAsync((void**)&dcnt, 8 * sizeof(int), s));
-    BEM_CUDA(cudaMallocAsync((void**)&dcur, 8 * sizeof(int), s));
-    BEM_CUDA(cudaMallocAsync((void**)&dstart, 9 * sizeof(int), s));
-    BEM_CUDA(cudaMemsetAsync(dcnt, 0, 8 * sizeof(int), s));
-    BEM_CUDA(cudaMemsetAsync(dcur, 0, 8 * sizeof(int), s));
-    k_octant_count<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cv.key, dcnt);
-    int hc[8];
-    BEM_CUDA(cudaMemcpyAsync(hc, dcnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> gs(9, 0);
-    for (int o = 0; o < 8; ++o) gs[o + 1] = gs[o] + hc[o];
-    BEM_CUDA(cudaMemcpyAsync(dstart, gs.data(), 9 * sizeof(int), cudaMemcpyHostToDevice, s));
+    int *cb, *pb;
+    unsigned char* fl;
     BEM_CUDA(cudaMallocAsync((void**)&cb, std::max(cv.nbox, 1) * sizeof(int), s));
     BEM_CUDA(cudaMallocAsync((void**)&pb, std::max(cv.nbox, 1) * sizeof(int), s));
-    k_octant_fill<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cv.key, cv.parent, dstart, dcur, cb, pb);
+    BEM_CUDA(cudaMallocAsync((void**)&fl, std::max(cv.nbox, 1), s));
+    k_octant_pairs<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cv.key, cv.parent, cb, pb, fl);
     BEM_CUDA(cudaGetLastError());
+    double hw = 0.5 * cv.w;
+    double v[3] = {hw, hw, hw};  // canonical c_child - c_parent
     GroupedOp* ops[2] = {&h->m2m[l], &h->l2l[l]};
     for (int which = 0; which < 2; ++which) {
       GroupedOp& op = *ops[which];
       op.npairs = cv.nbox;
-      op.ngroups = 0;
-      op.pair_start.clear();
-      op.rows.clear();
-      op.cols.clear();
-      op.mat_off.clear();
-      for (int o = 0; o < 8; ++o) {
-        if (hc[o] == 0) continue;
-        double hw = 0.5 * cv.w;
-        double v[3] = {(o & 1) ? hw : -hw, (o & 2) ? hw : -hw, (o & 4) ? hw : -hw};  // c_child - c_parent
-        op.pair_start.push_back(gs[o]);
-        if (which == 0) {
-          op.rows.push_back(pv.P);
-          op.cols.push_back(cv.P);
-          op.mat_off.push_back(add_mat(1, v, pv.p, cv.p, l, l + 1));
-        } else {
-          op.rows.push_back(cv.P);
-          op.cols.push_back(pv.P);
-          op.mat_off.push_back(add_mat(2, v, cv.p, pv.p, l + 1, l));
-        }
-        ++op.ngroups;
+      op.ngroups = 1;
+      op.pair_start = {0, cv.nbox};
+      if (which == 0) {
+        op.rows = {pv.P};
+        op.cols = {cv.P};
+        op.mat_off = {add_mat(1, v, pv.p, cv.p, l, l + 1)};
+      } else {
+        op.rows = {cv.P};
+        op.cols = {pv.P};
+        op.mat_off = {add_mat(2, v, cv.p, pv.p, l + 1, l)};
       }
-      op.pair_start.push_back(gs[8]);
       BEM_TRY(bem_alloc(h, &op.d_src_off, std::max(cv.nbox, 1)));
       BEM_TRY(bem_alloc(h, &op.d_dst_off, std::max(cv.nbox, 1)));
+      BEM_TRY(bem_alloc(h, &op.d_flags, std::max(cv.nbox, 1)));
+      BEM_CUDA(cudaMemcpyAsync(op.d_flags, fl, cv.nbox, cudaMemcpyDeviceToDevice, s));
       if (which == 0)
         k_pairs_to_offsets<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cb, pb, cv.exp_base, cv.P, pv.exp_base, pv.P,
                                                               op.d_src_off, op.d_dst_off);
@@ -586,11 +633,9 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
       BEM_TRY(make_jobs(h, op, s));
     }
     BEM_CUDA(cudaStreamSynchronize(s));
-    BEM_CUDA(cudaFreeAsync(dcnt, s));
-    BEM_CUDA(cudaFreeAsync(dcur, s));
-    BEM_CUDA(cudaFreeAsync(dstart, s));
     BEM_CUDA(cudaFreeAsync(cb, s));
     BEM_CUDA(cudaFreeAsync(pb, s));
+    BEM_CUDA(cudaFreeAsync(fl, s));
   }
 
   // ---- Gaunt table for n, n' <= pmax ----
@@ -678,6 +723,15 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   BEM_CUDA(cudaFreeAsync(d_tab, s));
   BEM_CUDA(cudaFreeAsync(d_gval, s));
   BEM_CUDA(cudaFreeAsync(d_goff, s));
+
+  // ---- tensor-core packing of every grouped operator (mixed mode) ----
+  if (!f64) {
+    for (int l = 2; l <= L; ++l) BEM_TRY(bem_build_tc(h, h->m2l[l], s));
+    for (int l = 2; l < L; ++l) {
+      BEM_TRY(bem_build_tc(h, h->m2m[l], s));
+      BEM_TRY(bem_build_tc(h, h->l2l[l], s));
+    }
+  }
 
   // ---- P2M / L2P rows at the leaf level ----
   LevelInfo& lf = h->lev[L];

@@ -31,17 +31,20 @@ class Operator:
     Parameters: vertices [nv,3] float64, triangles [nt,3] int32 (host arrays),
     wavenumber k, order p (> 0 fixed, 0 = automatic from eps), eps, mode in
     {"mixed", "fp64", "direct64", "direct32"}, leaf_level (0 = automatic),
-    leaf_target, max_nrhs.
+    leaf_target, max_nrhs, p_level ({level: order} overrides).
     """
 
     def __init__(self, vertices, triangles, k, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48,
-                 max_nrhs=16, p_min=4, p_max=40):
+                 max_nrhs=16, p_min=4, p_max=40, p_level=None):
         lib = _lib.load()
         V = np.ascontiguousarray(vertices, dtype=np.float64)
         T = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
+        levels = (ctypes.c_int * 11)(*([0] * 11))
+        for lvl, order in (p_level or {}).items():
+            levels[int(lvl)] = int(order)
         opt = _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
-                              int(max_nrhs), int(p_min), int(p_max))
+                              int(max_nrhs), int(p_min), int(p_max), levels)
         h = ctypes.c_void_p()
         _lib.check(lib.bem_setup(ctypes.byref(mesh), float(k), int(p), float(eps), ctypes.byref(opt), _stream(),
                                  ctypes.byref(h)))
