@@ -10,8 +10,8 @@
 // A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (hi = x rounded to TF32, lo = x - hi),
 // all accumulated in FP32 in tensor memory.
 //
-// One CTA (128 threads) computes a 128-row x 64-pair output tile over the
-// whole K range, in stages of 32 real K:
+// One CTA (256 threads) computes a 128-row x 64-pair output tile over a slice
+// of at most 8 stages of 32 real K (longer K is split across CTAs):
 //   - the A stage (hi and lo, packed at setup in the K-major, no-swizzle core
 //     matrix layout) arrives by one bulk asynchronous copy on an mbarrier;
 //   - the B stage is gathered by the threads (source expansion of each pair,
@@ -19,7 +19,8 @@
 //     stored in the same layout, then made visible to the async proxy;
 //   - one thread issues 4 k-steps x 3 tcgen05.mma (M=128, N=64, K=8) and
 //     commits them to an mbarrier that releases the stage;
-//   - two stages overlap the gather of stage s+1 with the MMAs of stage s.
+//   - two stages, and the next stage's B gather is in flight (in registers)
+//     while the current stage multiplies.
 // The epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes)
 // and scatters with atomic adds, applying the output reflection.
 // Every wait is bounded: on expiry the CTA records BEM_DEVERR_TIMEOUT, stops
@@ -120,14 +121,23 @@ __global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, 
 }
 
 // ------------------------------------------------------------------ kernel --
-__global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ jobs, const int* __restrict__ grows,
-                                                      const int* __restrict__ gcols,
-                                                      const int64_t* __restrict__ tcoff,
-                                                      const float* __restrict__ tcA, const int* __restrict__ src_off,
-                                                      const int* __restrict__ dst_off,
-                                                      const unsigned char* __restrict__ pflags,
-                                                      const float* __restrict__ src, float* __restrict__ dst,
-                                                      int64_t exp_stride, int* err) {
+#define TC_THREADS 256
+#define TC_KSLICE 8  // K stages per job (longer K is split; outputs are accumulated atomically)
+
+// B element held by thread `tid` in register slot q of a stage: a warp covers
+// one 8-pair x 4-k core-matrix row block (rr = lane / 4 pairs, e = lane % 4 k),
+// so its 32 shared-memory stores hit 32 different banks.
+__device__ __forceinline__ void b_slot(int tid, int q, int* c, int* kk) {
+  int lane = tid & 31, G = (tid >> 5) + 8 * q;  // G in [0, 64)
+  *c = (G & 7) * 8 + (lane >> 2);
+  *kk = (G >> 3) * 4 + (lane & 3);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
+    const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
+    const int64_t* __restrict__ tcoff, const float* __restrict__ tcA, const int* __restrict__ src_off,
+    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ src,
+    float* __restrict__ dst, int64_t exp_stride, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_a[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -137,9 +147,10 @@ __global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ 
 
   const int4 job = jobs[blockIdx.x];
   const int r = blockIdx.y;
-  const int g = job.x, p0 = job.y, np = job.z, rt = job.w;
+  const int g = job.x, p0 = job.y, np = job.z & 255, rt = job.w;
   const int Po = grows[g], Pi = gcols[g];
   const int nks = (2 * Pi + TC_KS - 1) / TC_KS;
+  const int ks0 = (job.z >> 8) * TC_KSLICE, ks1 = min(nks, ks0 + TC_KSLICE);
   const float* Ag = tcA + tcoff[g] + (int64_t)rt * nks * (2 * TC_M * TC_KS);
   const float* S = src + 2 * (int64_t)r * exp_stride;
   float* D = dst + 2 * (int64_t)r * exp_stride;
@@ -169,16 +180,38 @@ __global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = instr_desc();
-  int issued_a = 0;  // bulk copies issued by thread 0 (only thread 0 tracks these)
-  int committed = 0; // MMA commits issued by thread 0
+  int issued_a = 0, committed = 0;  // tracked by thread 0 only
 
-  for (int ks = 0; ks < nks; ++ks) {
-    const int st = ks & 1;
+  // gather of one B stage into registers (reflection applied)
+  float pre[8];
+  auto gather = [&](int ks) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int c, kk;
+      b_slot(tid, q, &c, &kk);
+      int realk = ks * TC_KS + kk;
+      int k = realk >> 1, part = realk & 1;
+      float v = 0.f;
+      int so = s_src[c];
+      if (so >= 0 && k < Pi) {
+        bool neg;
+        int ki = reflect_index(k, s_flg[c], &neg);
+        v = S[2 * ((int64_t)so + ki) + part];
+        if (neg) v = -v;
+      }
+      pre[q] = v;
+    }
+  };
+  gather(ks0);
+
+  for (int ks = ks0; ks < ks1; ++ks) {
+    const int it = ks - ks0;
+    const int st = it & 1;
     unsigned char* sA = smem + st * TC_STAGE_BYTES;
     unsigned char* sBh = sA + TC_ABYTES;
     unsigned char* sBl = sBh + TC_BBYTES;
     // the MMAs that last read this stage must be done before it is rewritten
-    if (ks >= 2 && !mbar_wait(smem_u32(&bar_m[st]), ((ks >> 1) - 1) & 1)) atomicExch(&s_abort, 1);
+    if (tid == 0 && it >= 2 && !mbar_wait(smem_u32(&bar_m[st]), ((it >> 1) - 1) & 1)) s_abort = 1;
     __syncthreads();
     if (s_abort) break;
     if (tid == 0) {
@@ -190,38 +223,31 @@ __global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ 
                    : "memory");
       ++issued_a;
     }
-    // gather B: column c = pair, 32 real K values of this stage
-    for (int idx = tid; idx < TC_N * TC_KS; idx += 128) {
-      int c = idx / TC_KS, kk = idx % TC_KS;
-      int realk = ks * TC_KS + kk;
-      int k = realk >> 1, part = realk & 1;
-      float v = 0.f;
-      int so = s_src[c];
-      if (so >= 0 && k < Pi) {
-        bool neg;
-        int ki = reflect_index(k, s_flg[c], &neg);
-        v = S[2 * ((int64_t)so + ki) + part];
-        if (neg) v = -v;
-      }
-      float hi = tf32_round(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int c, kk;
+      b_slot(tid, q, &c, &kk);
+      float v = pre[q], hi = tf32_round(v);
       uint32_t o = core_off(c, kk, TC_N);
       *(float*)(sBh + o) = hi;
       *(float*)(sBl + o) = v - hi;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (ks + 1 < ks1) gather(ks + 1);  // in flight while this stage multiplies
     __syncthreads();
     if (tid == 0) {
-      if (!mbar_wait(smem_u32(&bar_a[st]), (ks >> 1) & 1)) {
-        atomicExch(&s_abort, 1);
+      if (!mbar_wait(smem_u32(&bar_a[st]), (it >> 1) & 1)) {
+        s_abort = 1;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t a0 = smem_u32(sA), b0 = smem_u32(sBh), b1 = smem_u32(sBl);
+#pragma unroll
         for (int j = 0; j < TC_KS / 8; ++j) {
           uint64_t ah = smem_desc(a0 + j * (TC_M / 8) * 256);
           uint64_t al = smem_desc(a0 + TC_M * TC_KS * 4 + j * (TC_M / 8) * 256);
           uint64_t bh = smem_desc(b0 + j * (TC_N / 8) * 256);
           uint64_t bl = smem_desc(b1 + j * (TC_N / 8) * 256);
-          mma_tf32(tmem, ah, bh, idesc, (ks > 0 || j > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
           mma_tf32(tmem, ah, bl, idesc, 1u);
           mma_tf32(tmem, al, bh, idesc, 1u);
         }
@@ -232,29 +258,27 @@ __global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ 
       }
     }
   }
-  // wait for the last commit (it covers every MMA this thread issued)
-  __syncthreads();
-  bool ok = !s_abort;
+  // the last commit covers every MMA this thread issued
   if (tid == 0 && committed > 0) {
-    int last = committed - 1;  // commits alternate stages 0,1,0,1,...
-    if (!mbar_wait(smem_u32(&bar_m[last & 1]), (last >> 1) & 1)) atomicExch(&s_abort, 1);
+    int last = committed - 1;
+    if (!mbar_wait(smem_u32(&bar_m[last & 1]), (last >> 1) & 1)) s_abort = 1;
   }
-  if (tid == 0 && issued_a > committed) {
-    // a copy was issued but its MMAs were not: let it land before leaving
+  if (tid == 0 && issued_a > committed) {  // a copy landed without its MMAs: let it finish
     int st = (issued_a - 1) & 1;
     mbar_wait(smem_u32(&bar_a[st]), ((issued_a - 1) >> 1) & 1);
   }
   __syncthreads();
-  ok = ok && !s_abort;
+  const bool ok = !s_abort;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    const int rowl = 32 * warp + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns [32 (w / 4), + 32)
+    const int rowl = 32 * (warp & 3) + lane;
     const int R = rt * TC_M + rowl;
     const int q = R >> 1, part = R & 1;
     const bool vrow = q < Po;
-    for (int c0 = 0; c0 < TC_N; c0 += 16) {
+    for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32; c0 += 16) {
       uint32_t v[16];
-      uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
@@ -283,8 +307,6 @@ __global__ void __launch_bounds__(128, 1) k_grouped_tc(const int4* __restrict__ 
 }
 
 // -------------------------------------------------------------------- host --
-static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
 int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
   if (op.ngroups == 0) return BEM_OK;
   std::vector<int64_t> off(op.ngroups);
@@ -305,8 +327,11 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
   for (int g = 0; g < op.ngroups; ++g) {
     int np = op.pair_start[g + 1] - op.pair_start[g];
     int nrt = (2 * op.rows[g] + TC_M - 1) / TC_M;
+    int nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
     for (int p0 = 0; p0 < np; p0 += TC_N)
-      for (int rt = 0; rt < nrt; ++rt) jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_N, np - p0), rt));
+      for (int rt = 0; rt < nrt; ++rt)
+        for (int sl = 0; sl * TC_KSLICE < nks; ++sl)
+          jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_N, np - p0) | (sl << 8), rt));
   }
   op.n_tc_jobs = (int)jobs.size();
   BEM_TRY(bem_alloc(h, &op.d_tc_jobs, std::max<size_t>(jobs.size(), 1)));
@@ -323,7 +348,7 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   if (op.n_tc_jobs == 0) return BEM_OK;
   BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   dim3 grid(op.n_tc_jobs, nrhs);
-  k_grouped_tc<<<grid, 128, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
+  k_grouped_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
                                           op.d_src_off, op.d_dst_off, op.d_flags, (const float*)src, (float*)dst,
                                           h->exp_total, h->d_err);
   BEM_CUDA(cudaGetLastError());
