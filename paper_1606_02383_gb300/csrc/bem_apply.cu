@@ -103,6 +103,61 @@ __device__ __forceinline__ void p2p_eval(double dx, double dy, double dz, double
   aim += gre * vi + gim * vr;
 }
 
+// ---- packed FP32 pairs (Blackwell f32x2 instructions): one lane evaluates the
+// same source point for its two targets in one instruction per operation ----
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// The point kernel of p2p_eval for two targets at once (packed pairs).
+// nt = (-t_a, -t_b) per axis; n, sigma, tau as broadcast pairs; k2 = (k, k),
+// nk2 = (-k, -k), m1 = (-1, -1).
+__device__ __forceinline__ void p2p_eval_pair(float qx, float qy, float qz, f32x2 ntx, f32x2 nty, f32x2 ntz,
+                                              f32x2 nx, f32x2 ny, f32x2 nz, f32x2 sre, f32x2 sim, f32x2 tre,
+                                              f32x2 tim, f32x2 k2, f32x2 nk2, f32x2 m1, f32x2& are, f32x2& aim) {
+  f32x2 dx = add2(pk2(qx, qx), ntx), dy = add2(pk2(qy, qy), nty), dz = add2(pk2(qz, qz), ntz);
+  f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  float r2a, r2b;
+  upk2(r2, r2a, r2b);
+  f32x2 ri = pk2(rsqrtf(r2a), rsqrtf(r2b));
+  f32x2 r = mul2(r2, ri);
+  f32x2 kr = mul2(k2, r);
+  f32x2 nkr = mul2(nk2, r);
+  float kra, krb, sa, ca, sb, cb;
+  upk2(kr, kra, krb);
+  __sincosf(kra, &sa, &ca);  // |kr| stays small in the near field (phase error ~4e-8 kr)
+  __sincosf(krb, &sb, &cb);
+  f32x2 f = mul2(fma2(dx, nx, fma2(dy, ny, mul2(dz, nz))), mul2(ri, ri));
+  f32x2 ur = mul2(f, tre), ui = mul2(f, tim);
+  f32x2 vr = fma2(kr, ui, add2(sre, ur));
+  f32x2 vi = fma2(nkr, ur, add2(sim, ui));
+  f32x2 wi = mul2(vi, m1);
+  f32x2 gre = mul2(ri, pk2(ca, cb)), gim = mul2(ri, pk2(sa, sb));
+  are = fma2(gre, vr, fma2(gim, wi, are));
+  aim = fma2(gre, vi, fma2(gim, vr, aim));
+}
+
 // One warp per work unit (leaf box, 2^j consecutive targets, j <= 6).  The
 // 32 lanes are np2 = ceil(count/2) target pairs times 32/np2 source slices;
 // every lane owns two targets and walks its slice of the elements of the 27
@@ -137,6 +192,9 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t 
   const V4* dr = dens + (int64_t)r * nt;
   int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
   R a_re = 0, a_im = 0, b_re = 0, b_im = 0;
+  // packed accumulators and constants (used by the FP32 instantiation)
+  f32x2 pa_re = pk2(0.f, 0.f), pa_im = pk2(0.f, 0.f);
+  const f32x2 pk_k = pk2((float)k, (float)k), pk_nk = pk2(-(float)k, -(float)k), pk_m1 = pk2(-1.f, -1.f);
   for (int slot = 0; slot < 27; ++slot) {
     int sb = near27[27 * b + slot];
     if (sb < 0) continue;
@@ -146,17 +204,42 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t 
     R ax = ta.x - sx, ay = ta.y - sy, az = ta.z - sz;  // targets in the source box's frame
     R bx_ = tb.x - sx, by_ = tb.y - sy, bz_ = tb.z - sz;
     int e1 = bend[sb];
-    for (int e = bstart[sb] + split; e < e1; e += nsplit) {
-      V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
-      V4 d = dr[e];
-      R nx = q0.w, ny = q1.w, nz = q2.w;
-      p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-      p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-      p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+    if constexpr (sizeof(R) == 4) {
+      f32x2 ntx = pk2(-ax, -bx_), nty = pk2(-ay, -by_), ntz = pk2(-az, -bz_);
+      for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+        V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
+        V4 d = dr[e];
+        f32x2 nx = pk2(q0.w, q0.w), ny = pk2(q1.w, q1.w), nz = pk2(q2.w, q2.w);
+        f32x2 sre = pk2(d.x, d.x), sim = pk2(d.y, d.y), tre = pk2(d.z, d.z), tim = pk2(d.w, d.w);
+        p2p_eval_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
+                      pa_im);
+        p2p_eval_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
+                      pa_im);
+        p2p_eval_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
+                      pa_im);
+      }
+    } else {
+      for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+        V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
+        V4 d = dr[e];
+        R nx = q0.w, ny = q1.w, nz = q2.w;
+        p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
+        p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
+        p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
+        p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+        p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+        p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      }
     }
+  }
+  if constexpr (sizeof(R) == 4) {
+    float lo, hi;
+    upk2(pa_re, lo, hi);
+    a_re += lo;
+    b_re += hi;
+    upk2(pa_im, lo, hi);
+    a_im += lo;
+    b_im += hi;
   }
   for (int o = np2; o < 32; o <<= 1) {
     a_re += __shfl_xor_sync(0xffffffffu, a_re, o);

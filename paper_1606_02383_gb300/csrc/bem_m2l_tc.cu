@@ -5,38 +5,40 @@
 // gathered expansions (Section 2.3's FMM, translation step).  The complex
 // product is written as a real one with interleaved (re, im) rows and columns,
 //     [Re out; Im out] = [[Tr, -Ti], [Ti, Tr]] [Re in; Im in],
-// so an expansion stored as interleaved complex64 is already a real column of
+// so an expansion stored as interleaved complex64 is already a real vector of
 // length 2 P_in.  FP32 accuracy comes from the 3xTF32 split
 // A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi (hi = x rounded to TF32, lo = x - hi),
 // all accumulated in FP32 in tensor memory.
 //
-// One CTA (256 threads) computes a 128-row x 64-pair output tile over a slice
-// of at most 8 stages of 32 real K (longer K is split across CTAs):
-//   - the A stage (hi and lo, packed at setup in the K-major, no-swizzle core
+// The MMA is D[pairs x rows] += E[pairs x K] . T_real[rows x K]^T: M = 128
+// pairs of one group, N = up to 256 real output rows, K in stages of 16:
+//   - the T stage (hi and lo, packed at setup in the K-major, no-swizzle core
 //     matrix layout) arrives by one bulk asynchronous copy on an mbarrier;
-//   - the B stage is gathered by the threads (source expansion of each pair,
+//   - the E stage is gathered by the threads (source expansion of every pair,
 //     with the pair's reflection permutation and signs), split into hi/lo and
-//     stored in the same layout, then made visible to the async proxy;
-//   - one thread issues 4 k-steps x 3 tcgen05.mma (M=128, N=64, K=8) and
-//     commits them to an mbarrier that releases the stage;
-//   - two stages, and the next stage's B gather is in flight (in registers)
-//     while the current stage multiplies.
-// The epilogue reads the accumulator with tcgen05.ld (each warp its 32 lanes)
-// and scatters with atomic adds, applying the output reflection.
-// Every wait is bounded: on expiry the CTA records BEM_DEVERR_TIMEOUT, stops
-// issuing work, waits (bounded) for its own copies and MMAs, frees its tensor
-// memory and returns.
+//     stored in the same layout, then made visible to the async proxy; the
+//     next stage's gather is in flight in registers while this one multiplies;
+//   - one thread issues 2 k-steps x 3 tcgen05.mma (M=128, N<=256, K=8) and
+//     commits them to an mbarrier that releases the stage (two stages);
+//   - long K is split across CTAs (outputs are accumulated atomically).
+// In the epilogue every thread owns one pair (its TMEM lane) and adds that
+// pair's outputs to the destination expansion with (re, im) vector atomics,
+// applying the output reflection.  Every wait is bounded: on expiry the CTA
+// records BEM_DEVERR_TIMEOUT, stops issuing work, waits (bounded) for its own
+// copies and MMAs, frees its tensor memory and returns.
 #include <algorithm>
 #include <vector>
 
 #include "bem_common.cuh"
 
-#define TC_N 64         // pairs per tile (MMA N)
-#define TC_M 128        // real rows per tile (MMA M)
-#define TC_KS 32        // real K per stage (4 MMA k-steps of 8)
-#define TC_ABYTES (2 * TC_M * TC_KS * 4)  // hi + lo A stage
-#define TC_BBYTES (TC_N * TC_KS * 4)      // one of hi / lo B stage
-#define TC_STAGE_BYTES (TC_ABYTES + 2 * TC_BBYTES)
+#define TC_M 128        // pairs per tile (MMA M)
+#define TC_NMAX 256     // real output rows per tile (MMA N, multiple of 16)
+#define TC_KS 16        // real K per stage (2 MMA k-steps of 8)
+#define TC_KSLICE 16    // stages per job
+#define TC_THREADS 256
+#define TC_EBYTES (TC_M * TC_KS * 4)                     // one of hi / lo gathered stage
+#define TC_TBYTES_MAX (TC_NMAX * TC_KS * 4)             // one of hi / lo matrix stage
+#define TC_STAGE_BYTES (2 * TC_EBYTES + 2 * TC_TBYTES_MAX)
 #define TC_SMEM (2 * TC_STAGE_BYTES)
 
 // ----------------------------------------------------------- PTX helpers --
@@ -79,9 +81,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TC_N
-__device__ __forceinline__ uint32_t instr_desc() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+// instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -92,20 +94,27 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       : "memory");
 }
 
-// offset (bytes) of element (row, k) in a stage block of `rows` rows x 32 K
+// offset (bytes) of element (row, k) in a stage block of `rows` rows x TC_KS K
 __device__ __forceinline__ uint32_t core_off(int row, int kk, int rows) {
   int j = kk >> 3, kg = (kk >> 2) & 1, e = kk & 3;
   return (uint32_t)(j * (rows / 8) * 256 + (row >> 3) * 256 + kg * 128 + (row & 7) * 16 + e * 4);
 }
 
 // --------------------------------------------------------- setup packing --
-// A_real of group g, packed per (row tile, k stage): [hi block | lo block].
-__global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, float* out) {
-  int rt = blockIdx.x / nks, ks = blockIdx.x % nks;
-  float* blk = out + (int64_t)blockIdx.x * (2 * TC_M * TC_KS);
-  for (int idx = threadIdx.x; idx < TC_M * TC_KS; idx += blockDim.x) {
+// Rows of n-tile nt: real output rows [256 nt, 256 nt + N) with N the tile's
+// width rounded up to 16; per k stage a block [hi N x 16 | lo N x 16].
+__host__ __device__ __forceinline__ int tc_ntile_width(int rows_real, int nt) {
+  int w = min(TC_NMAX, rows_real - nt * TC_NMAX);
+  return (w + 15) & ~15;
+}
+
+__global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, int nnt, float* out) {
+  int nt = blockIdx.x / nks, ks = blockIdx.x % nks;
+  int N = tc_ntile_width(2 * Po, nt);
+  float* blk = out + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS) + (int64_t)ks * (2 * N * TC_KS);
+  for (int idx = threadIdx.x; idx < N * TC_KS; idx += blockDim.x) {
     int row = idx / TC_KS, kk = idx % TC_KS;
-    int R = rt * TC_M + row, C = ks * TC_KS + kk;
+    int R = nt * TC_NMAX + row, C = ks * TC_KS + kk;
     int q = R >> 1, k = C >> 1;
     float v = 0.f;
     if (q < Po && k < Pi) {
@@ -114,49 +123,49 @@ __global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, 
       v = (pr == pc) ? tr : (pr == 0 ? -ti : ti);
     }
     float hi = tf32_round(v);
-    uint32_t o = core_off(row, kk, TC_M) >> 2;
+    uint32_t o = core_off(row, kk, N) >> 2;
     blk[o] = hi;
-    blk[TC_M * TC_KS + o] = v - hi;
+    blk[N * TC_KS + o] = v - hi;
   }
+  (void)nnt;
 }
 
 // ------------------------------------------------------------------ kernel --
-#define TC_THREADS 256
-#define TC_KSLICE 8  // K stages per job (longer K is split; outputs are accumulated atomically)
-
-// B element held by thread `tid` in register slot q of a stage: a warp covers
-// one 8-pair x 4-k core-matrix row block (rr = lane / 4 pairs, e = lane % 4 k),
+// gathered element held by thread `tid` in register slot q of a stage: a warp
+// covers one 8-pair x 4-k core-matrix row block (lane / 4 pairs, lane % 4 k),
 // so its 32 shared-memory stores hit 32 different banks.
-__device__ __forceinline__ void b_slot(int tid, int q, int* c, int* kk) {
-  int lane = tid & 31, G = (tid >> 5) + 8 * q;  // G in [0, 64)
-  *c = (G & 7) * 8 + (lane >> 2);
-  *kk = (G >> 3) * 4 + (lane & 3);
+__device__ __forceinline__ void e_slot(int tid, int q, int* c, int* kk) {
+  int lane = tid & 31, G = (tid >> 5) + 8 * q;  // G in [0, 64): 16 row groups x 4 k groups
+  *c = (G & 15) * 8 + (lane >> 2);
+  *kk = (G >> 4) * 4 + (lane & 3);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
-    const int64_t* __restrict__ tcoff, const float* __restrict__ tcA, const int* __restrict__ src_off,
+    const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ src_off,
     const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ src,
     float* __restrict__ dst, int64_t exp_stride, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_a[2];
+  __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ int s_src[TC_N], s_dst[TC_N], s_flg[TC_N];
+  __shared__ int s_src[TC_M], s_dst[TC_M], s_flg[TC_M];
 
   const int4 job = jobs[blockIdx.x];
   const int r = blockIdx.y;
-  const int g = job.x, p0 = job.y, np = job.z & 255, rt = job.w;
+  const int g = job.x, p0 = job.y, np = job.z & 255, nt = job.w;
   const int Po = grows[g], Pi = gcols[g];
+  const int N = tc_ntile_width(2 * Po, nt);
   const int nks = (2 * Pi + TC_KS - 1) / TC_KS;
   const int ks0 = (job.z >> 8) * TC_KSLICE, ks1 = min(nks, ks0 + TC_KSLICE);
-  const float* Ag = tcA + tcoff[g] + (int64_t)rt * nks * (2 * TC_M * TC_KS);
+  const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
+  const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
   const float* S = src + 2 * (int64_t)r * exp_stride;
   float* D = dst + 2 * (int64_t)r * exp_stride;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (tid < TC_N) {
+  if (tid < TC_M) {
     bool ok = tid < np;
     s_src[tid] = ok ? src_off[p0 + tid] : -1;
     s_dst[tid] = ok ? dst_off[p0 + tid] : -1;
@@ -164,13 +173,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(TC_N));
+                 "r"(TC_NMAX));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     s_abort = 0;
     for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_a[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_t[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_m[i])));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -179,16 +188,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = instr_desc();
-  int issued_a = 0, committed = 0;  // tracked by thread 0 only
+  const uint32_t idesc = instr_desc(N);
+  int issued_t = 0, committed = 0;  // tracked by thread 0 only
 
-  // gather of one B stage into registers (reflection applied)
   float pre[8];
   auto gather = [&](int ks) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int c, kk;
-      b_slot(tid, q, &c, &kk);
+      e_slot(tid, q, &c, &kk);
       int realk = ks * TC_KS + kk;
       int k = realk >> 1, part = realk & 1;
       float v = 0.f;
@@ -202,51 +210,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
       pre[q] = v;
     }
   };
+  __syncthreads();  // s_src visible
   gather(ks0);
 
   for (int ks = ks0; ks < ks1; ++ks) {
     const int it = ks - ks0;
     const int st = it & 1;
-    unsigned char* sA = smem + st * TC_STAGE_BYTES;
-    unsigned char* sBh = sA + TC_ABYTES;
-    unsigned char* sBl = sBh + TC_BBYTES;
-    // the MMAs that last read this stage must be done before it is rewritten
+    unsigned char* sEh = smem + st * TC_STAGE_BYTES;
+    unsigned char* sEl = sEh + TC_EBYTES;
+    unsigned char* sT = sEl + TC_EBYTES;  // [hi N x 16 | lo N x 16]
     if (tid == 0 && it >= 2 && !mbar_wait(smem_u32(&bar_m[st]), ((it >> 1) - 1) & 1)) s_abort = 1;
     __syncthreads();
     if (s_abort) break;
     if (tid == 0) {
-      uint32_t bar = smem_u32(&bar_a[st]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(TC_ABYTES) : "memory");
+      uint32_t bar = smem_u32(&bar_t[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tbytes) : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(sA)),
-                   "l"(Ag + (int64_t)ks * (2 * TC_M * TC_KS)), "r"(TC_ABYTES), "r"(bar)
+                       smem_u32(sT)),
+                   "l"(Tg + (int64_t)ks * (2 * N * TC_KS)), "r"(tbytes), "r"(bar)
                    : "memory");
-      ++issued_a;
+      ++issued_t;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int c, kk;
-      b_slot(tid, q, &c, &kk);
+      e_slot(tid, q, &c, &kk);
       float v = pre[q], hi = tf32_round(v);
-      uint32_t o = core_off(c, kk, TC_N);
-      *(float*)(sBh + o) = hi;
-      *(float*)(sBl + o) = v - hi;
+      uint32_t o = core_off(c, kk, TC_M);
+      *(float*)(sEh + o) = hi;
+      *(float*)(sEl + o) = v - hi;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ks + 1 < ks1) gather(ks + 1);  // in flight while this stage multiplies
+    if (ks + 1 < ks1) gather(ks + 1);
     __syncthreads();
     if (tid == 0) {
-      if (!mbar_wait(smem_u32(&bar_a[st]), (it >> 1) & 1)) {
+      if (!mbar_wait(smem_u32(&bar_t[st]), (it >> 1) & 1)) {
         s_abort = 1;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint32_t a0 = smem_u32(sA), b0 = smem_u32(sBh), b1 = smem_u32(sBl);
+        uint32_t e0 = smem_u32(sEh), e1 = smem_u32(sEl), t0 = smem_u32(sT);
 #pragma unroll
         for (int j = 0; j < TC_KS / 8; ++j) {
-          uint64_t ah = smem_desc(a0 + j * (TC_M / 8) * 256);
-          uint64_t al = smem_desc(a0 + TC_M * TC_KS * 4 + j * (TC_M / 8) * 256);
-          uint64_t bh = smem_desc(b0 + j * (TC_N / 8) * 256);
-          uint64_t bl = smem_desc(b1 + j * (TC_N / 8) * 256);
+          uint64_t ah = smem_desc(e0 + j * (TC_M / 8) * 256);
+          uint64_t al = smem_desc(e1 + j * (TC_M / 8) * 256);
+          uint64_t bh = smem_desc(t0 + j * (N / 8) * 256);
+          uint64_t bl = smem_desc(t0 + N * TC_KS * 4 + j * (N / 8) * 256);
           mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
           mma_tf32(tmem, ah, bl, idesc, 1u);
           mma_tf32(tmem, al, bh, idesc, 1u);
@@ -258,43 +266,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
       }
     }
   }
-  // the last commit covers every MMA this thread issued
   if (tid == 0 && committed > 0) {
     int last = committed - 1;
     if (!mbar_wait(smem_u32(&bar_m[last & 1]), (last >> 1) & 1)) s_abort = 1;
   }
-  if (tid == 0 && issued_a > committed) {  // a copy landed without its MMAs: let it finish
-    int st = (issued_a - 1) & 1;
-    mbar_wait(smem_u32(&bar_a[st]), ((issued_a - 1) >> 1) & 1);
+  if (tid == 0 && issued_t > committed) {
+    int st = (issued_t - 1) & 1;
+    mbar_wait(smem_u32(&bar_t[st]), ((issued_t - 1) >> 1) & 1);
   }
   __syncthreads();
   const bool ok = !s_abort;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns [32 (w / 4), + 32)
-    const int rowl = 32 * (warp & 3) + lane;
-    const int R = rt * TC_M + rowl;
-    const int q = R >> 1, part = R & 1;
-    const bool vrow = q < Po;
-    for (int c0 = 32 * (warp >> 2); c0 < 32 * (warp >> 2) + 32; c0 += 16) {
-      uint32_t v[16];
-      uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
+    // warp w: TMEM lanes (pairs) 32 (w % 4) .. + 31, columns [w/4 * N/2, + N/2)
+    const int c = 32 * (warp & 3) + lane;
+    const int dof = s_dst[c], fl = s_flg[c];
+    const int half = N >> 1;
+    for (int col0 = (warp >> 2) * half; col0 < (warp >> 2) * half + half; col0 += 8) {
+      uint32_t v[8];
+      uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col0;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (vrow) {
+      if (dof >= 0) {
 #pragma unroll
-        for (int cc = 0; cc < 16; ++cc) {
-          int c = c0 + cc;
-          int dof = s_dst[c];
-          if (dof < 0) continue;
-          bool neg;
-          int qi = reflect_index(q, s_flg[c], &neg);
-          float val = __uint_as_float(v[cc]);
-          atomicAdd(D + 2 * ((int64_t)dof + qi) + part, neg ? -val : val);
+        for (int e = 0; e < 4; ++e) {
+          int q = (nt * TC_NMAX + col0) / 2 + e;
+          if (q < Po) {
+            bool neg;
+            int qi = reflect_index(q, fl, &neg);
+            float re = __uint_as_float(v[2 * e]), im = __uint_as_float(v[2 * e + 1]);
+            if (neg) {
+              re = -re;
+              im = -im;
+            }
+            atomicAdd((float2*)(D + 2 * ((int64_t)dof + qi)), make_float2(re, im));
+          }
         }
       }
     }
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
 }
 
 // -------------------------------------------------------------------- host --
@@ -312,26 +320,26 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
   std::vector<int64_t> off(op.ngroups);
   int64_t tot = 0;
   for (int g = 0; g < op.ngroups; ++g) {
-    int nrt = (2 * op.rows[g] + TC_M - 1) / TC_M, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
+    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
     off[g] = tot;
-    tot += (int64_t)nrt * nks * 2 * TC_M * TC_KS;
+    tot += (int64_t)nnt * nks * 2 * TC_NMAX * TC_KS;
   }
   BEM_TRY(bem_alloc(h, &op.tcA, std::max<int64_t>(tot, 4)));
   for (int g = 0; g < op.ngroups; ++g) {
-    int nrt = (2 * op.rows[g] + TC_M - 1) / TC_M, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
-    k_tc_pack<<<nrt * nks, 256, 0, s>>>((const float*)h->mats + 2 * op.mat_off[g], op.rows[g], op.cols[g], nks,
-                                        op.tcA + off[g]);
+    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
+    k_tc_pack<<<nnt * nks, 256, 0, s>>>((const float*)h->mats + 2 * op.mat_off[g], op.rows[g], op.cols[g], nks,
+                                        nnt, op.tcA + off[g]);
     BEM_CUDA(cudaGetLastError());
   }
   std::vector<int4> jobs;
   for (int g = 0; g < op.ngroups; ++g) {
     int np = op.pair_start[g + 1] - op.pair_start[g];
-    int nrt = (2 * op.rows[g] + TC_M - 1) / TC_M;
+    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX;
     int nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
-    for (int p0 = 0; p0 < np; p0 += TC_N)
-      for (int rt = 0; rt < nrt; ++rt)
+    for (int p0 = 0; p0 < np; p0 += TC_M)
+      for (int nt = 0; nt < nnt; ++nt)
         for (int sl = 0; sl * TC_KSLICE < nks; ++sl)
-          jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_N, np - p0) | (sl << 8), rt));
+          jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_M, np - p0) | (sl << 8), nt));
   }
   op.n_tc_jobs = (int)jobs.size();
   BEM_TRY(bem_alloc(h, &op.d_tc_jobs, std::max<size_t>(jobs.size(), 1)));
