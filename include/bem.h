@@ -158,9 +158,17 @@ int bem_apply_noalloc(bem_handle* h, int nrhs, int dtype, const void* x, const v
 
 /*
  * bem_apply_adjoint -- conjugate transpose of bem_apply:
- *   gx = (1/2 I - D)^H g,  gy = S^H g   (either output nullable).
+ *   gx = (1/2 I - D)^H g,  gy = S^H g   (either output nullable, not both).
  * The adjoint problem of Section 2.2 uses the same operator; this entry point
- * is what reverse-mode differentiation of bem_apply needs.
+ * is what reverse-mode differentiation of bem_apply needs (PyTorch's complex
+ * convention: the gradient of a linear map A is A^H applied to the output
+ * gradient).  Every part of the apply is transposed exactly (near field,
+ * correction, each FMM translation), so <A x, g> = <x, A^H g> holds to
+ * rounding, not only to the FMM tolerance.
+ *   g     : [nrhs][N] device buffer; gx, gy: [nrhs][N] device buffers.
+ *   flags : BEM_APPLY_NO_HALF (gx = -D^H g).  Host buffers are not accepted.
+ * The first call builds the transposed translation operators (allocation,
+ * synchronising); later calls are stream-ordered like bem_apply.
  */
 int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int flags,
                       void* stream);

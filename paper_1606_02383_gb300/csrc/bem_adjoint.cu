@@ -1,0 +1,375 @@
+// bem_adjoint.cu -- conjugate-transpose apply: gx = (1/2 I - D)^H g, gy = S^H g.
+//
+// The adjoint problem of Section 2.2 is solved with the same matrix as the
+// state problem; this is the operator reverse-mode differentiation of
+// bem_apply needs.  With h = conj(g) the two products are the plain
+// transposes u = S^T h, v = D^T h, and gy = conj(u), gx = 1/2 g - conj(v).
+// Every part of the forward operator is transposed:
+//   near field   u_j += sum_i h_i sum_q G(y_jq - x_i),  v_j += ... dG/dn_y(x_i, y_jq)
+//                (the quadrature points of element j are now the evaluation
+//                points and the centroids the sources; weight w_j at the end)
+//   correction   C^T, scattered with atomic adds
+//   far field    the forward chain L2P . L2L . M2L . M2M . P2M reversed with
+//                every factor transposed: L2P^T (leaf sums of the L2P rows),
+//                L2L^T upward, M2L^T across, M2M^T downward, P2M^T (dot
+//                products with the P2M rows).
+#include "bem_common.cuh"
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename R>
+struct AV4;
+template <>
+struct AV4<float> {
+  typedef float4 T;
+};
+template <>
+struct AV4<double> {
+  typedef double4 T;
+};
+
+// h = conj(g) in octree order, stored in the density workspace (.x, .y)
+template <typename Rin, typename V4>
+__global__ void k_adj_prologue(int64_t nt, int nrhs, const int* __restrict__ perm, const Rin* __restrict__ g,
+                               V4* dens) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nt) return;
+  int64_t o = perm[s];
+  for (int r = 0; r < nrhs; ++r) {
+    int64_t io = 2 * ((int64_t)r * nt + o);
+    V4 d;
+    d.x = g[io];
+    d.y = -g[io + 1];
+    d.z = 0;
+    d.w = 0;
+    dens[(int64_t)r * nt + s] = d;
+  }
+}
+
+template <typename Rout>
+__global__ void k_adj_epilogue(int64_t nt, int nrhs, const int* __restrict__ perm, const double* __restrict__ wgt,
+                               const Rout* __restrict__ g, const double4* __restrict__ uv, int half, Rout* gx,
+                               Rout* gy) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nt) return;
+  int64_t o = perm[s];
+  double w = wgt[s];
+  for (int r = 0; r < nrhs; ++r) {
+    double4 a = uv[(int64_t)r * nt + s];
+    int64_t io = 2 * ((int64_t)r * nt + o);
+    if (gy) {
+      gy[io] = (Rout)(w * a.x);
+      gy[io + 1] = (Rout)(-w * a.y);
+    }
+    if (gx) {
+      double re = -w * a.z, im = w * a.w;  // -conj(v)
+      if (half) {
+        re += 0.5 * (double)g[io];
+        im += 0.5 * (double)g[io + 1];
+      }
+      gx[io] = (Rout)re;
+      gx[io + 1] = (Rout)im;
+    }
+  }
+}
+
+// contribution of the source centroid x (complex weight h) at one quadrature
+// point y of an element with normal n:  u += h e^{ikr}/r,
+// v += h (ikr - 1) e^{ikr}/r^3 (y - x).n   (dx = y - x)
+template <typename R>
+__device__ __forceinline__ void adj_point(R dx, R dy, R dz, R nx, R ny, R nz, R k, R hre, R him, R& ure, R& uim,
+                                          R& vre, R& vim) {
+  R r2 = dx * dx + dy * dy + dz * dz;
+  R rinv, sn, cs;
+  if (sizeof(R) == 4) {
+    float ri = rsqrtf((float)r2);
+    float s_, c_;
+    __sincosf((float)k * (float)r2 * ri, &s_, &c_);
+    rinv = (R)ri;
+    sn = (R)s_;
+    cs = (R)c_;
+  } else {
+    double rr = sqrt((double)r2);
+    rinv = (R)(1.0 / rr);
+    double s_, c_;
+    sincos((double)k * rr, &s_, &c_);
+    sn = (R)s_;
+    cs = (R)c_;
+  }
+  R kr = k * r2 * rinv;
+  R gre = rinv * cs, gim = rinv * sn;
+  R f = (dx * nx + dy * ny + dz * nz) * rinv * rinv;
+  R dre = f * (-gre - kr * gim), dim = f * (kr * gre - gim);
+  ure += gre * hre - gim * him;
+  uim += gre * him + gim * hre;
+  vre += dre * hre - dim * him;
+  vim += dre * him + dim * hre;
+}
+
+// near field, transposed: one warp per unit (leaf, 2^j elements j); lanes =
+// element pairs x source slices, as in the forward kernel
+#define ADJ_WARPS 4
+template <typename R>
+__global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t nt, R k, R wleaf,
+                                                            const int4* __restrict__ units,
+                                                            const int* __restrict__ near27,
+                                                            const int* __restrict__ bstart,
+                                                            const int* __restrict__ bend,
+                                                            const int* __restrict__ coord,
+                                                            const typename AV4<R>::T* __restrict__ tgt,
+                                                            const typename AV4<R>::T* __restrict__ src,
+                                                            const typename AV4<R>::T* __restrict__ dens,
+                                                            double4* __restrict__ uv) {
+  typedef typename AV4<R>::T V4;
+  int u = blockIdx.x * ADJ_WARPS + (threadIdx.x >> 5);
+  if (u >= nunits) return;
+  int lane = threadIdx.x & 31;
+  int r = blockIdx.y;
+  int4 U = units[u];
+  int b = U.x, first = U.y, cnt = U.z;
+  int np2 = (cnt + 1) >> 1;
+  int pi = lane & (np2 - 1), split = lane / np2, nsplit = 32 / np2;
+  bool two = pi + np2 < cnt;
+  int ja = first + pi, jb = first + (two ? pi + np2 : pi);
+  V4 qa[3], qb[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    qa[q] = src[3 * (int64_t)ja + q];
+    qb[q] = src[3 * (int64_t)jb + q];
+  }
+  const V4* dr = dens + (int64_t)r * nt;
+  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
+  R ua_re = 0, ua_im = 0, va_re = 0, va_im = 0, ub_re = 0, ub_im = 0, vb_re = 0, vb_im = 0;
+  for (int slot = 0; slot < 27; ++slot) {
+    int sb = near27[27 * b + slot];
+    if (sb < 0) continue;
+    R sx = (R)((coord[3 * sb] - bx) * (double)wleaf);
+    R sy = (R)((coord[3 * sb + 1] - by) * (double)wleaf);
+    R sz = (R)((coord[3 * sb + 2] - bz) * (double)wleaf);
+    int e1 = bend[sb];
+    for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+      V4 x = tgt[e];
+      V4 d = dr[e];
+      R xx = x.x + sx, xy = x.y + sy, xz = x.z + sz;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        adj_point<R>(qa[q].x - xx, qa[q].y - xy, qa[q].z - xz, qa[0].w, qa[1].w, qa[2].w, k, d.x, d.y, ua_re, ua_im,
+                     va_re, va_im);
+        adj_point<R>(qb[q].x - xx, qb[q].y - xy, qb[q].z - xz, qb[0].w, qb[1].w, qb[2].w, k, d.x, d.y, ub_re, ub_im,
+                     vb_re, vb_im);
+      }
+    }
+  }
+  for (int o = np2; o < 32; o <<= 1) {
+    ua_re += __shfl_xor_sync(0xffffffffu, ua_re, o);
+    ua_im += __shfl_xor_sync(0xffffffffu, ua_im, o);
+    va_re += __shfl_xor_sync(0xffffffffu, va_re, o);
+    va_im += __shfl_xor_sync(0xffffffffu, va_im, o);
+    ub_re += __shfl_xor_sync(0xffffffffu, ub_re, o);
+    ub_im += __shfl_xor_sync(0xffffffffu, ub_im, o);
+    vb_re += __shfl_xor_sync(0xffffffffu, vb_re, o);
+    vb_im += __shfl_xor_sync(0xffffffffu, vb_im, o);
+  }
+  if (split == 0) {
+    uv[(int64_t)r * nt + ja] = make_double4(ua_re, ua_im, va_re, va_im);
+    if (two) uv[(int64_t)r * nt + jb] = make_double4(ub_re, ub_im, vb_re, vb_im);
+  }
+}
+
+// direct (all pairs), transposed: one element per thread, every centroid a source
+template <typename R>
+__global__ void __launch_bounds__(128) k_p2p_adj_direct(int64_t nt, R k, const typename AV4<R>::T* __restrict__ tgt,
+                                                       const typename AV4<R>::T* __restrict__ src,
+                                                       const typename AV4<R>::T* __restrict__ dens,
+                                                       double4* __restrict__ uv) {
+  typedef typename AV4<R>::T V4;
+  __shared__ V4 s_x[128], s_h[128];
+  int r = blockIdx.y;
+  int64_t j = blockIdx.x * (int64_t)128 + threadIdx.x;
+  const V4* dr = dens + (int64_t)r * nt;
+  V4 q[3];
+  int64_t jj = j < nt ? j : 0;
+  for (int a = 0; a < 3; ++a) q[a] = src[3 * jj + a];
+  double u0 = 0, u1 = 0, v0 = 0, v1 = 0;
+  for (int64_t e0 = 0; e0 < nt; e0 += 128) {
+    int ne = (int)min((int64_t)128, nt - e0);
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      s_x[threadIdx.x] = tgt[e0 + threadIdx.x];
+      s_h[threadIdx.x] = dr[e0 + threadIdx.x];
+    }
+    __syncthreads();
+    R ure = 0, uim = 0, vre = 0, vim = 0;
+    for (int e = 0; e < ne; ++e) {
+      V4 x = s_x[e], h = s_h[e];
+      for (int a = 0; a < 3; ++a)
+        adj_point<R>(q[a].x - x.x, q[a].y - x.y, q[a].z - x.z, q[0].w, q[1].w, q[2].w, k, h.x, h.y, ure, uim, vre,
+                     vim);
+    }
+    u0 += ure;
+    u1 += uim;
+    v0 += vre;
+    v1 += vim;
+  }
+  if (j < nt) uv[(int64_t)r * nt + j] = make_double4(u0, u1, v0, v1);
+}
+
+// correction, transposed: warp per row i, entries scattered into their columns
+template <typename V4>
+__global__ void k_corr_adj(int64_t nt, const int* __restrict__ ptr, const int* __restrict__ col,
+                           const V4* __restrict__ val, const V4* __restrict__ dens, double4* __restrict__ uv) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int r = blockIdx.y;
+  if (i >= nt) return;
+  V4 h = dens[(int64_t)r * nt + i];
+  double hr = h.x, hi = h.y;
+  for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+    V4 c = val[e];
+    double* t = (double*)(uv + (int64_t)r * nt + col[e]);
+    atomicAdd(t + 0, (double)c.x * hr - (double)c.y * hi);
+    atomicAdd(t + 1, (double)c.x * hi + (double)c.y * hr);
+    atomicAdd(t + 2, (double)c.z * hr - (double)c.w * hi);
+    atomicAdd(t + 3, (double)c.z * hi + (double)c.w * hr);
+  }
+}
+
+// L2P^T: Lambda_b = sum_{i in b} rows_r[i] h_i  (leaf level)
+template <typename R>
+__global__ void k_l2p_t(int nleaf, int64_t nt, int P, const int* __restrict__ bstart, const int* __restrict__ bend,
+                        const R* __restrict__ rows_r, const typename AV4<R>::T* __restrict__ dens, int64_t exp_base,
+                        int64_t exp_stride, R* __restrict__ Lam) {
+  typedef typename AV4<R>::T V4;
+  int b = blockIdx.x, r = blockIdx.y;
+  const V4* dr = dens + (int64_t)r * nt;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    R are = 0, aim = 0;
+    for (int i = bstart[b]; i < bend[b]; ++i) {
+      const R* row = rows_r + 2 * ((int64_t)i * P);
+      R xr = row[2 * e], xi = row[2 * e + 1];
+      V4 h = dr[i];
+      are += xr * h.x - xi * h.y;
+      aim += xr * h.y + xi * h.x;
+    }
+    R* out = Lam + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P + e);
+    out[0] = are;
+    out[1] = aim;
+  }
+}
+
+// P2M^T: u_j += a_j . Mu_b, v_j += b_j . Mu_b   (warp per element, leaf level)
+template <typename R>
+__global__ void k_p2m_t(int64_t nt, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_ab,
+                        const R* __restrict__ Mu, int64_t exp_base, int64_t exp_stride, double4* __restrict__ uv) {
+  int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int r = blockIdx.y;
+  if (j >= nt) return;
+  int b = leaf_of[j];
+  const R* ab = rows_ab + 2 * ((int64_t)j * 2 * P);
+  const R* M = Mu + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P);
+  R ure = 0, uim = 0, vre = 0, vim = 0;
+  for (int e = lane; e < P; e += 32) {
+    R mr = M[2 * e], mi = M[2 * e + 1];
+    R ar = ab[2 * e], ai = ab[2 * e + 1], br = ab[2 * (P + e)], bi = ab[2 * (P + e) + 1];
+    ure += ar * mr - ai * mi;
+    uim += ar * mi + ai * mr;
+    vre += br * mr - bi * mi;
+    vim += br * mi + bi * mr;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ure += __shfl_xor_sync(0xffffffffu, ure, o);
+    uim += __shfl_xor_sync(0xffffffffu, uim, o);
+    vre += __shfl_xor_sync(0xffffffffu, vre, o);
+    vim += __shfl_xor_sync(0xffffffffu, vim, o);
+  }
+  if (lane == 0) {
+    double4* t = uv + (int64_t)r * nt + j;
+    double4 a = *t;
+    a.x += ure;
+    a.y += uim;
+    a.z += vre;
+    a.w += vim;
+    *t = a;
+  }
+}
+
+template <typename R>
+static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
+  typedef typename AV4<R>::T V4;
+  int64_t nt = h->nt;
+  const V4* dens = (const V4*)h->dens;
+  const V4* tgt = (const V4*)(sizeof(R) == 4 ? (const void*)h->tgt32 : (const void*)h->tgt64);
+  const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
+  bool fmm = bem_is_fmm(h);
+  int L = h->L;
+  if (fmm) {
+    LevelInfo& lf = h->lev[L];
+    dim3 grid(nblk(h->n_p2p_units, ADJ_WARPS), nrhs);
+    k_p2p_adj<R><<<grid, 32 * ADJ_WARPS, 0, s>>>(h->n_p2p_units, nt, (R)h->k, (R)lf.w, h->p2p_units, h->near27,
+                                                 lf.start, lf.end, lf.coord, tgt, src, dens, h->uv);
+  } else {
+    dim3 grid(nblk(nt, 128), nrhs);
+    k_p2p_adj_direct<R><<<grid, 128, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->uv);
+  }
+  BEM_CUDA(cudaGetLastError());
+  {
+    dim3 grid(nblk(nt * 32, 256), nrhs);
+    k_corr_adj<V4><<<grid, 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->uv);
+    BEM_CUDA(cudaGetLastError());
+  }
+  if (!fmm || L < 2) return BEM_OK;
+  size_t esz = 2 * sizeof(R);
+  LevelInfo& lf = h->lev[L];
+  BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
+  BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
+  {
+    dim3 grid(lf.nbox, nrhs);
+    k_l2p_t<R><<<grid, 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->l2p_rows, dens, lf.exp_base,
+                                    h->exp_total, (R*)h->Lexp);
+    BEM_CUDA(cudaGetLastError());
+  }
+  int nl = 0;
+  for (int l = L - 1; l >= 2; --l) BEM_TRY(bem_run_grouped(h, h->l2l_T[l], h->Lexp, h->Lexp, nrhs, s, &nl));
+  for (int l = 2; l <= L; ++l) BEM_TRY(bem_run_grouped(h, h->m2l_T[l], h->Lexp, h->Mexp, nrhs, s, &nl));
+  for (int l = 2; l < L; ++l) BEM_TRY(bem_run_grouped(h, h->m2m_T[l], h->Mexp, h->Mexp, nrhs, s, &nl));
+  {
+    dim3 grid(nblk(nt * 32, 256), nrhs);
+    k_p2m_t<R><<<grid, 256, 0, s>>>(nt, lf.P, h->leaf_of, (const R*)h->p2m_rows, (const R*)h->Mexp, lf.exp_base,
+                                    h->exp_total, h->uv);
+    BEM_CUDA(cudaGetLastError());
+  }
+  return BEM_OK;
+}
+
+int bem_adjoint_sorted(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
+                       cudaStream_t s) {
+  BEM_TRY(bem_build_adjoint(h, s));
+  int64_t nt = h->nt;
+  unsigned gb = nblk(nt, 256);
+  bool f64 = bem_is_fp64(h);
+  if (dtype == BEM_C128) {
+    if (f64)
+      k_adj_prologue<double, double4><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, (const double*)g, (double4*)h->dens);
+    else
+      k_adj_prologue<double, float4><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, (const double*)g, (float4*)h->dens);
+  } else {
+    if (f64)
+      k_adj_prologue<float, double4><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, (const float*)g, (double4*)h->dens);
+    else
+      k_adj_prologue<float, float4><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, (const float*)g, (float4*)h->dens);
+  }
+  BEM_CUDA(cudaGetLastError());
+  if (f64)
+    BEM_TRY(adjoint_impl<double>(h, nrhs, s));
+  else
+    BEM_TRY(adjoint_impl<float>(h, nrhs, s));
+  if (dtype == BEM_C128)
+    k_adj_epilogue<double><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, h->wgt, (const double*)g, h->uv, half, (double*)gx,
+                                              (double*)gy);
+  else
+    k_adj_epilogue<float><<<gb, 256, 0, s>>>(nt, nrhs, h->perm, h->wgt, (const float*)g, h->uv, half, (float*)gx,
+                                             (float*)gy);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}

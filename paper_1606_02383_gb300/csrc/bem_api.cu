@@ -306,11 +306,13 @@ int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* g
                       void* stream) {
   g_last_error.clear();
   BEM_TRY(check_apply_args(h, nrhs, dtype, flags));
-  (void)g;
-  (void)gx;
-  (void)gy;
-  (void)stream;
-  return bem_fail(BEM_ERR_UNSUPPORTED, "adjoint apply not available yet");
+  if (flags & BEM_HOST_BUFFERS) return bem_fail(BEM_ERR_INVALID_ARG, "bem_apply_adjoint takes device buffers only");
+  if (!g) return bem_fail(BEM_ERR_INVALID_ARG, "g is NULL");
+  if (!gx && !gy) return bem_fail(BEM_ERR_INVALID_ARG, "gx and gy are both NULL");
+  if (gx == g || gy == g || (gx && gx == gy)) return bem_fail(BEM_ERR_INVALID_ARG, "outputs must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  int half = (flags & BEM_APPLY_NO_HALF) ? 0 : 1;
+  return bem_adjoint_sorted(h, nrhs, dtype, g, gx, gy, half, s);
 }
 
 int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,

@@ -518,7 +518,7 @@ static int run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   if (op.njobsA > 0) {
     dim3 grid(op.njobsA, nrhs);
     k_grouped_gemm<R, 64, 64, 4, 4><<<grid, 256, 0, s>>>(op.d_jobsA, op.d_group_rows, op.d_group_cols,
-                                                         op.d_group_mat, (const R*)h->mats, op.d_src_off,
+                                                         op.d_group_mat, (const R*)op.mats_base, op.d_src_off,
                                                          op.d_dst_off, op.d_flags, (const R*)src, (R*)dst,
                                                          h->exp_total);
     BEM_CUDA(cudaGetLastError());
@@ -527,7 +527,7 @@ static int run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   if (op.njobsB > 0) {
     dim3 grid(op.njobsB, nrhs);
     k_grouped_gemm<R, 128, 16, 4, 2><<<grid, 256, 0, s>>>(op.d_jobsB, op.d_group_rows, op.d_group_cols,
-                                                          op.d_group_mat, (const R*)h->mats, op.d_src_off,
+                                                          op.d_group_mat, (const R*)op.mats_base, op.d_src_off,
                                                           op.d_dst_off, op.d_flags, (const R*)src, (R*)dst,
                                                           h->exp_total);
     BEM_CUDA(cudaGetLastError());
@@ -603,6 +603,12 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   }
   bem_prof_end(h, pr, 7, 1, s);
   return BEM_OK;
+}
+
+int bem_run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
+                    int* launches) {
+  if (bem_is_fp64(h)) return run_grouped<double>(h, op, src, dst, nrhs, s, launches);
+  return run_grouped<float>(h, op, src, dst, nrhs, s, launches);
 }
 
 int bem_apply_sorted(bem_handle* h, int nrhs, cudaStream_t s) {

@@ -119,6 +119,7 @@ struct GroupedOp {
   std::vector<int64_t> mat_off;         // per group, complex offset into the matrix buffer
   std::vector<int> pair_start;          // per group, first pair (host copy), size ngroups+1
   std::vector<int> codes;               // tree build: offset code of every V-list group
+  const void* mats_base = nullptr;      // matrix buffer the group offsets refer to
   int npairs = 0;
   int* d_src_off = nullptr;             // [npairs]
   int* d_dst_off = nullptr;             // [npairs]
@@ -221,6 +222,14 @@ struct bem_handle {
   void* l2p_rows = nullptr;       // [nt][P_L] complex
   int64_t exp_total = 0;          // complex coefficients per rhs over all levels
 
+  // adjoint (conjugate-transpose) apply, built on first use
+  bool adj_ready = false;
+  GroupedOp m2m_T[BEM_MAXLEV + 1];  // index l: parent level l -> child level l+1 (transpose of m2m[l])
+  GroupedOp m2l_T[BEM_MAXLEV + 1];  // target level-l Lambda -> source level-l Mu (transpose of m2l[l])
+  GroupedOp l2l_T[BEM_MAXLEV + 1];  // child level l+1 -> parent level l (transpose of l2l[l])
+  void* mats_T = nullptr;
+  double4* uv = nullptr;            // [nrhs_max][nt]: (u = S^T h, v = D^T h) before the weight, sorted
+
   // workspaces
   void* dens = nullptr;     // [nrhs_max][nt] weighted (y, x) pairs: float4 or double4
   void* Mexp = nullptr;     // [nrhs_max][exp_total] complex
@@ -280,5 +289,10 @@ int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double
               int flags, int* iters_out, double* relres_out, cudaStream_t s);
 int bem_check_device_error(bem_handle* h, cudaStream_t s);
 int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s);
+int bem_build_adjoint(bem_handle* h, cudaStream_t s);
+int bem_adjoint_sorted(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
+                       cudaStream_t s);
+int bem_run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
+                    int* launches);
 int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
                        int* launches);

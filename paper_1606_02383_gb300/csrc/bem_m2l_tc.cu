@@ -327,7 +327,7 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
   BEM_TRY(bem_alloc(h, &op.tcA, std::max<int64_t>(tot, 4)));
   for (int g = 0; g < op.ngroups; ++g) {
     int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
-    k_tc_pack<<<nnt * nks, 256, 0, s>>>((const float*)h->mats + 2 * op.mat_off[g], op.rows[g], op.cols[g], nks,
+    k_tc_pack<<<nnt * nks, 256, 0, s>>>((const float*)op.mats_base + 2 * op.mat_off[g], op.rows[g], op.cols[g], nks,
                                         nnt, op.tcA + off[g]);
     BEM_CUDA(cudaGetLastError());
   }

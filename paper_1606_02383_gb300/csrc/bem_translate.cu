@@ -724,6 +724,11 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   BEM_CUDA(cudaFreeAsync(d_gval, s));
   BEM_CUDA(cudaFreeAsync(d_goff, s));
 
+  for (int l = 2; l <= L; ++l) h->m2l[l].mats_base = h->mats;
+  for (int l = 2; l < L; ++l) {
+    h->m2m[l].mats_base = h->mats;
+    h->l2l[l].mats_base = h->mats;
+  }
   // ---- tensor-core packing of every grouped operator (mixed mode) ----
   if (!f64) {
     for (int l = 2; l <= L; ++l) BEM_TRY(bem_build_tc(h, h->m2l[l], s));
@@ -770,4 +775,69 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   BEM_CUDA(cudaFreeAsync(scr, s));
   (void)csz;
   return bem_check_device_error(h, s);
+}
+
+// ------------------------------------------------------- adjoint operators --
+// Plain transpose (no conjugation) of every group matrix: out[c][r] = in[r][c].
+template <typename R>
+__global__ void k_transpose_group(const R* __restrict__ in, R* __restrict__ out, int rows, int cols, int64_t off) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)rows * cols) return;
+  int r = (int)(e / cols), c = (int)(e % cols);
+  out[2 * (off + (int64_t)c * rows + r)] = in[2 * (off + e)];
+  out[2 * (off + (int64_t)c * rows + r) + 1] = in[2 * (off + e) + 1];
+}
+
+// The transpose of a grouped operator: same pairs with source and destination
+// swapped, transposed matrices, same reflection flags ((Q T Q)^T = Q T^T Q).
+static int make_transposed(bem_handle* h, const GroupedOp& op, GroupedOp& t, cudaStream_t s) {
+  t.ngroups = op.ngroups;
+  t.rows = op.cols;
+  t.cols = op.rows;
+  t.mat_off = op.mat_off;
+  t.pair_start = op.pair_start;
+  t.npairs = op.npairs;
+  t.d_src_off = op.d_dst_off;
+  t.d_dst_off = op.d_src_off;
+  t.d_flags = op.d_flags;
+  t.mats_base = h->mats_T;
+  bool f64 = bem_is_fp64(h);
+  for (int g = 0; g < op.ngroups; ++g) {
+    int64_t n = (int64_t)op.rows[g] * op.cols[g];
+    if (f64)
+      k_transpose_group<double><<<nblk(n, 256), 256, 0, s>>>((const double*)h->mats, (double*)h->mats_T, op.rows[g],
+                                                             op.cols[g], op.mat_off[g]);
+    else
+      k_transpose_group<float><<<nblk(n, 256), 256, 0, s>>>((const float*)h->mats, (float*)h->mats_T, op.rows[g],
+                                                            op.cols[g], op.mat_off[g]);
+    BEM_CUDA(cudaGetLastError());
+  }
+  BEM_TRY(make_jobs(h, t, s));
+  if (!f64) BEM_TRY(bem_build_tc(h, t, s));
+  return BEM_OK;
+}
+
+int bem_build_adjoint(bem_handle* h, cudaStream_t s) {
+  if (h->adj_ready) return BEM_OK;
+  int64_t nt = h->nt;
+  BEM_TRY(bem_alloc(h, &h->uv, (size_t)nt * h->nrhs_max));
+  if (bem_is_fmm(h) && h->L >= 2) {
+    if (bem_is_fp64(h)) {
+      double* m;
+      BEM_TRY(bem_alloc(h, &m, 2 * std::max<int64_t>(h->mats_len, 1)));
+      h->mats_T = m;
+    } else {
+      float* m;
+      BEM_TRY(bem_alloc(h, &m, 2 * std::max<int64_t>(h->mats_len, 1)));
+      h->mats_T = m;
+    }
+    for (int l = 2; l <= h->L; ++l) BEM_TRY(make_transposed(h, h->m2l[l], h->m2l_T[l], s));
+    for (int l = 2; l < h->L; ++l) {
+      BEM_TRY(make_transposed(h, h->m2m[l], h->m2m_T[l], s));
+      BEM_TRY(make_transposed(h, h->l2l[l], h->l2l_T[l], s));
+    }
+  }
+  BEM_CUDA(cudaStreamSynchronize(s));
+  h->adj_ready = true;
+  return BEM_OK;
 }

@@ -121,15 +121,20 @@ class Operator:
                                        None if y is None else y.data_ptr(), out.data_ptr(), flags, _stream()))
         return out
 
-    def adjoint(self, g):
+    def adjoint(self, g, no_half=False):
         """(gx, gy) = ((1/2 I - D)^H g, S^H g)."""
         gs = self._prep(g, g.dtype)
         nrhs = gs.shape[0]
         gx = torch.empty_like(gs)
         gy = torch.empty_like(gs)
+        flags = _lib.BEM_APPLY_NO_HALF if no_half else 0
         _lib.check(self._lib.bem_apply_adjoint(self._h, nrhs, _dtype_code(gs), gs.data_ptr(), gx.data_ptr(),
-                                               gy.data_ptr(), 0, _stream()))
+                                               gy.data_ptr(), flags, _stream()))
         return gx, gy
+
+    def __call__(self, x, y):
+        """Differentiable z = (1/2 I - D) x + S y (torch.autograd; backward = bem_apply_adjoint)."""
+        return BemApplyFn.apply(self, x, y)
 
     def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
         """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs])."""
@@ -144,3 +149,21 @@ class Operator:
         if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
             _lib.check(rc)
         return x, int(iters.value), np.array(list(rel))
+
+
+class BemApplyFn(torch.autograd.Function):
+    """z = (1/2 I - D) x + S y with the conjugate-transpose apply as its backward.
+
+    For a linear map z = A u PyTorch's complex gradient convention gives
+    grad_u = A^H grad_z, which is exactly bem_apply_adjoint.
+    """
+
+    @staticmethod
+    def forward(ctx, op, x, y):
+        ctx.op = op
+        return op.apply(x, y)
+
+    @staticmethod
+    def backward(ctx, gz):
+        gx, gy = ctx.op.adjoint(gz.contiguous())
+        return None, gx.reshape(gz.shape), gy.reshape(gz.shape)
