@@ -174,6 +174,25 @@ int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* g
                       void* stream);
 
 /*
+ * bem_grad -- derivative of a real loss L with respect to the wavenumber k,
+ * given the upstream gradient g = dL/dz of z = bem_apply(x, y) (PyTorch's
+ * convention for complex outputs: g = dL/dRe z + i dL/dIm z):
+ *     dk = sum over rhs of Re < g, (dA/dk) u >,
+ * where dA/dk differentiates every rule-defined entry: the smooth kernels
+ * dG/dk = i exp(ikr)/(4 pi) and d(dG/dn)/dk = -k exp(ikr) (y-x).n/(4 pi r),
+ * the refined near-singular rules and the exact self term.  The gradients
+ * with respect to x and y are bem_apply_adjoint.
+ *   g, x, y   : [nrhs][N] device buffers (x or y may be NULL, not both).
+ *   dvertices : must be NULL (vertex gradients are not provided; the call
+ *               returns BEM_ERR_UNSUPPORTED otherwise).
+ *   dk        : host pointer to one double.
+ * Cost: an FP64 direct sum over all pairs (O(N^2)) plus the correction
+ * pairs; it allocates per-call scratch and synchronises `stream`.
+ */
+int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, const void* y, double* dvertices,
+             double* dk, void* stream);
+
+/*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
  * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
  *   b          : right-hand sides [nrhs][N] (device).

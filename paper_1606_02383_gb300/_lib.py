@@ -40,7 +40,7 @@ INFO_ORDER_OF_LEVEL = 100
 
 # every entry point declared in include/bem.h
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
-           "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_last_error")
+           "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_last_error")
 
 
 class BemMesh(ctypes.Structure):
@@ -79,6 +79,8 @@ def load(path: str | None = None):
     lib.bem_apply.argtypes = [vp, i, i, vp, vp, vp, i, vp]
     lib.bem_apply_adjoint.argtypes = [vp, i, i, vp, vp, vp, i, vp]
     lib.bem_apply_noalloc.argtypes = [vp, i, i, vp, vp, vp, i, vp]
+    lib.bem_grad.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             vp]
     lib.bem_gmres_solve.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
                                     ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
@@ -86,7 +88,7 @@ def load(path: str | None = None):
     lib.bem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
-              "bem_profile", "bem_profile_read", "bem_apply_noalloc"):
+              "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

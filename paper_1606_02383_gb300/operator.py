@@ -132,9 +132,25 @@ class Operator:
                                                gy.data_ptr(), flags, _stream()))
         return gx, gy
 
-    def __call__(self, x, y):
-        """Differentiable z = (1/2 I - D) x + S y (torch.autograd; backward = bem_apply_adjoint)."""
-        return BemApplyFn.apply(self, x, y)
+    def grad_k(self, g, x=None, y=None):
+        """dL/dk = sum Re <g, (dA/dk) u> for the upstream gradient g of z = apply(x, y)."""
+        gs = self._prep(g, g.dtype)
+        xs, ys = self._prep(x, g.dtype), self._prep(y, g.dtype)
+        dk = ctypes.c_double(0.0)
+        _lib.check(self._lib.bem_grad(self._h, gs.shape[0], _dtype_code(gs), gs.data_ptr(),
+                                      None if xs is None else xs.data_ptr(), None if ys is None else ys.data_ptr(),
+                                      None, ctypes.byref(dk), _stream()))
+        return float(dk.value)
+
+    def __call__(self, x, y, k=None):
+        """Differentiable z = (1/2 I - D) x + S y (torch.autograd).
+
+        Backward: dL/dx, dL/dy from bem_apply_adjoint; if a real tensor `k`
+        (equal to the operator's wavenumber) is passed, dL/dk from bem_grad.
+        """
+        if k is None:
+            k = torch.tensor(self.k, dtype=torch.float64)
+        return BemApplyFn.apply(self, x, y, k)
 
     def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
         """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs])."""
@@ -159,11 +175,19 @@ class BemApplyFn(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, op, x, y):
+    def forward(ctx, op, x, y, k):
+        if abs(float(k) - op.k) > 1e-12 * max(1.0, abs(op.k)):
+            raise ValueError("k must equal the wavenumber the operator was set up with")
         ctx.op = op
+        ctx.save_for_backward(x, y)
         return op.apply(x, y)
 
     @staticmethod
     def backward(ctx, gz):
-        gx, gy = ctx.op.adjoint(gz.contiguous())
-        return None, gx.reshape(gz.shape), gy.reshape(gz.shape)
+        x, y = ctx.saved_tensors
+        gz = gz.contiguous()
+        gx, gy = ctx.op.adjoint(gz)
+        gk = None
+        if ctx.needs_input_grad[3]:
+            gk = torch.tensor(ctx.op.grad_k(gz, x, y), dtype=torch.float64)
+        return None, gx.reshape(gz.shape), gy.reshape(gz.shape), gk

@@ -54,3 +54,24 @@ def test_gmres_not_converged_status(cuda_ok):
     assert e.value.code == _lib.BEM_ERR_NOT_CONVERGED
     x, iters, rel = op.solve(b, tol=1e-14, max_iter=2, restart=2, raise_on_fail=False)
     assert iters == 2 and rel[0] > 1e-14
+
+
+def test_state_and_adjoint_rhs_in_one_solve(cuda_ok):
+    """State (plane wave) and adjoint (point sources at the observation points,
+    Section 2.2: same matrix, right-hand side sum_m G(x - x_obs,m)) solved
+    together as nrhs = 2, each checked against the oracle's LU solve."""
+    V, T = inputs.icosphere(3)
+    k = 2.0
+    c, _, _, _ = oracle.geometry(V, T)
+    obs = np.array([[5.0, 0, 0], [-5.0, 0, 0], [0, 0, 5.0], [0, 0, -5.0]])
+    r = np.linalg.norm(c[:, None, :] - obs[None, :, :], axis=2)
+    adj = np.sum(np.exp(1j * k * r) / (4 * np.pi * r), axis=1)
+    b = np.stack([inputs.plane_wave(c, k), adj])
+    S, D = oracle.assemble(V, T, k)
+    ref = oracle.lu_solve(0.5 * np.eye(T.shape[0]) - D, b)
+    op = Operator(V, T, k, p=10, mode="mixed", leaf_level=3)
+    x, iters, relres = op.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=100, restart=100)
+    x = x.cpu().numpy()
+    assert np.all(relres <= 1e-8)
+    for q in range(2):
+        assert np.linalg.norm(x[q] - ref[q]) / np.linalg.norm(ref[q]) <= 1e-5
