@@ -212,6 +212,42 @@ int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, 
                     int flags, int* iters_out, double* relres_out, void* stream);
 
 /*
+ * Batches of independent problems (many scatterers, each with its own mesh
+ * and wavenumber: the state and adjoint solves of Section 2.5 repeated over a
+ * population of designs).  Every problem keeps its own octree and operators;
+ * a batch apply runs all of them from one captured CUDA graph whose branches
+ * (problems spread over 8 forked streams) execute concurrently.
+ */
+typedef struct bem_batch bem_batch;
+
+/*
+ * bem_setup_batch -- bem_setup for `count` meshes with wavenumbers ks[count]
+ * (same p, eps and options for all).  Synchronises `stream`.
+ */
+int bem_setup_batch(const bem_mesh* meshes, const double* ks, int count, int p, double eps, const bem_options* opt,
+                    void* stream, bem_batch** out);
+
+/*
+ * bem_apply_batch -- z = (1/2 I - D) x + S y for every problem at once.
+ *   x, y, z : device buffers [nrhs][N_total] where N_total is the sum of the
+ *             problems' triangle counts; problem b owns the columns
+ *             [N_0 + ... + N_{b-1}, + N_b) of every rhs row.
+ *   flags   : BEM_APPLY_NO_HALF.
+ * The first call for a given (nrhs, flags) captures the graph (host work);
+ * later calls are two small staging kernels and one graph launch on `stream`.
+ */
+int bem_apply_batch(bem_batch* b, int nrhs, int dtype, const void* x, const void* y, void* z, int flags, void* stream);
+
+/*
+ * bem_batch_info -- problem = -1: key 0 -> N_total, key 1 -> number of
+ * problems; problem >= 0: bem_info of that problem's handle.
+ */
+int bem_batch_info(bem_batch* b, int problem, int key, int64_t* value);
+
+/* bem_destroy_batch -- free a batch and every handle in it (NULL accepted). */
+int bem_destroy_batch(bem_batch* b);
+
+/*
  * bem_info -- integer facts about a handle (sizes, counts, orders), for
  * reporting and for the roofline arithmetic.  Unknown keys -> INVALID_ARG.
  */

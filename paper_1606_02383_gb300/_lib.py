@@ -40,7 +40,8 @@ INFO_ORDER_OF_LEVEL = 100
 
 # every entry point declared in include/bem.h
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
-           "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_last_error")
+           "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
+           "bem_batch_info", "bem_destroy_batch", "bem_last_error")
 
 
 class BemMesh(ctypes.Structure):
@@ -86,9 +87,15 @@ def load(path: str | None = None):
     lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
     lib.bem_profile.argtypes = [vp, i]
     lib.bem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i]
+    lib.bem_setup_batch.argtypes = [ctypes.POINTER(BemMesh), ctypes.POINTER(ctypes.c_double), i, i, ctypes.c_double,
+                                    ctypes.POINTER(BemOptions), vp, ctypes.POINTER(vp)]
+    lib.bem_apply_batch.argtypes = [vp, i, i, vp, vp, vp, i, vp]
+    lib.bem_batch_info.argtypes = [vp, i, i, ctypes.POINTER(i64)]
+    lib.bem_destroy_batch.argtypes = [vp]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
-              "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad"):
+              "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
+              "bem_apply_batch", "bem_batch_info", "bem_destroy_batch"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
 // -------------------------------------------------------------------- host --
 int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
   if (op.ngroups == 0) return BEM_OK;
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   std::vector<int64_t> off(op.ngroups);
   int64_t tot = 0;
   for (int g = 0; g < op.ngroups; ++g) {
@@ -354,7 +355,6 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
 int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
                        int* launches) {
   if (op.n_tc_jobs == 0) return BEM_OK;
-  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   dim3 grid(op.n_tc_jobs, nrhs);
   k_grouped_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
                                           op.d_src_off, op.d_dst_off, op.d_flags, (const float*)src, (float*)dst,

@@ -15,6 +15,9 @@ import numpy as np
 
 __all__ = [
     "icosphere",
+    "ellipsoid",
+    "torus",
+    "batch_bodies",
     "translate_scale",
     "merge_meshes",
     "random_density",
@@ -73,6 +76,92 @@ def icosphere(level: int, radius: float = 1.0, centre=(0.0, 0.0, 0.0)):
     f = _orient_outward(v, f, np.zeros(3))
     v = v * float(radius) + np.asarray(centre, dtype=np.float64)[None, :]
     return np.ascontiguousarray(v), np.ascontiguousarray(f.astype(np.int32))
+
+
+def _orient_by_direction(v, f, outward):
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    flip = np.einsum("ij,ij->i", nrm, outward) < 0
+    f = f.copy()
+    f[flip, 1], f[flip, 2] = f[flip, 2], f[flip, 1].copy()
+    return f
+
+
+def ellipsoid(n: int, axes=(1.0, 1.0, 1.0), centre=(0.0, 0.0, 0.0)):
+    """Cube-sphere: each cube face split into n x n squares (two triangles
+    each, 12 n^2 triangles), projected onto the unit sphere and scaled by the
+    semi-axes."""
+    g = np.linspace(-1.0, 1.0, n + 1)
+    U, W = np.meshgrid(g, g, indexing="ij")
+    verts, faces, off = [], [], 0
+    for axis in range(3):
+        for sign in (-1.0, 1.0):
+            P = np.zeros((n + 1, n + 1, 3))
+            P[..., axis] = sign
+            P[..., (axis + 1) % 3] = U
+            P[..., (axis + 2) % 3] = W
+            verts.append(P.reshape(-1, 3))
+            idx = np.arange((n + 1) * (n + 1)).reshape(n + 1, n + 1) + off
+            a, b, c, d = idx[:-1, :-1], idx[1:, :-1], idx[1:, 1:], idx[:-1, 1:]
+            faces.append(np.stack([a, b, c], -1).reshape(-1, 3))
+            faces.append(np.stack([a, c, d], -1).reshape(-1, 3))
+            off += (n + 1) * (n + 1)
+    v = np.concatenate(verts)
+    f = np.concatenate(faces)
+    key = np.round(v * 1e9).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    v = v[first]
+    f = inv.reshape(-1)[f]
+    v = v / np.linalg.norm(v, axis=1, keepdims=True)
+    f = _orient_by_direction(v, f, (v[f[:, 0]] + v[f[:, 1]] + v[f[:, 2]]) / 3.0)
+    v = v * np.asarray(axes, dtype=np.float64)[None, :] + np.asarray(centre, dtype=np.float64)[None, :]
+    return np.ascontiguousarray(v), np.ascontiguousarray(f.astype(np.int32))
+
+
+def torus(nu: int, nv: int, R: float = 1.0, r: float = 0.3, centre=(0.0, 0.0, 0.0)):
+    """Torus of major radius R and minor radius r on an nu x nv (u, v) grid
+    (2 nu nv triangles), oriented away from the tube's centre line."""
+    u = 2 * np.pi * np.arange(nu) / nu
+    w = 2 * np.pi * np.arange(nv) / nv
+    Uu, Ww = np.meshgrid(u, w, indexing="ij")
+    v = np.stack([(R + r * np.cos(Ww)) * np.cos(Uu), (R + r * np.cos(Ww)) * np.sin(Uu), r * np.sin(Ww)], -1)
+    v = v.reshape(-1, 3)
+    idx = np.arange(nu * nv).reshape(nu, nv)
+    a = idx
+    b = np.roll(idx, -1, axis=0)
+    c = np.roll(np.roll(idx, -1, axis=0), -1, axis=1)
+    d = np.roll(idx, -1, axis=1)
+    f = np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)])
+    cen = (v[f[:, 0]] + v[f[:, 1]] + v[f[:, 2]]) / 3.0
+    ring = cen.copy()
+    ring[:, 2] = 0.0
+    ring = R * ring / np.linalg.norm(ring, axis=1, keepdims=True)
+    f = _orient_by_direction(v, f, cen - ring)
+    v = v + np.asarray(centre, dtype=np.float64)[None, :]
+    return np.ascontiguousarray(v), np.ascontiguousarray(f.astype(np.int32))
+
+
+def batch_bodies(count: int = 64, seed: int = 0, n_min: int = 2000, n_max: int = 50000):
+    """The batching workload: `count` independent scatterers, half ellipsoids
+    (semi-axes uniform in [0.5, 2]) and half tori (R = 1, r uniform in
+    [0.2, 0.5]), triangle counts log-uniform in [n_min, n_max], wavenumbers
+    uniform in [1, 8].  Returns a list of (vertices, triangles, k)."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 3]))
+    out = []
+    for b in range(count):
+        target = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        k = float(rng.uniform(1.0, 8.0))
+        if b % 2 == 0:
+            axes = rng.uniform(0.5, 2.0, size=3)
+            n = max(2, int(round(np.sqrt(target / 12.0))))
+            V, T = ellipsoid(n, axes)
+        else:
+            r = float(rng.uniform(0.2, 0.5))
+            nv = max(3, int(round(np.sqrt(target / 2.0 * r))))
+            nu = max(3, int(round(target / (2.0 * nv))))
+            V, T = torus(nu, nv, 1.0, r)
+        out.append((V, T, k))
+    return out
 
 
 def translate_scale(vertices, scale=1.0, shift=(0.0, 0.0, 0.0)):

@@ -191,3 +191,62 @@ class BemApplyFn(torch.autograd.Function):
         if ctx.needs_input_grad[3]:
             gk = torch.tensor(ctx.op.grad_k(gz, x, y), dtype=torch.float64)
         return None, gx.reshape(gz.shape), gy.reshape(gz.shape), gk
+
+
+class Batch:
+    """Many independent problems (meshes with their own wavenumbers) applied together.
+
+    problems: list of (vertices, triangles, k).  Densities are concatenated
+    along the element axis in problem order: [nrhs, sum N_b].
+    """
+
+    def __init__(self, problems, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48, max_nrhs=4):
+        lib = _lib.load()
+        self._keep = []
+        meshes = (_lib.BemMesh * len(problems))()
+        ks = (ctypes.c_double * len(problems))()
+        for i, (V, T, k) in enumerate(problems):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            T = np.ascontiguousarray(T, dtype=np.int32)
+            self._keep += [V, T]
+            meshes[i] = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
+            ks[i] = float(k)
+        opt = _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
+                              int(max_nrhs), 4, 40, (ctypes.c_int * 11)())
+        h = ctypes.c_void_p()
+        _lib.check(lib.bem_setup_batch(meshes, ks, len(problems), int(p), float(eps), ctypes.byref(opt), _stream(),
+                                       ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.sizes = [int(T.shape[0]) for _, T, _ in problems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bem_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, problem, key):
+        v = ctypes.c_int64()
+        code = _lib.INFO[key] if isinstance(key, str) else int(key)
+        _lib.check(self._lib.bem_batch_info(self._h, int(problem), code, ctypes.byref(v)))
+        return int(v.value)
+
+    def apply(self, x=None, y=None, no_half=False):
+        ref = x if x is not None else y
+        dtype = ref.dtype
+        xs = None if x is None else (x if x.dim() == 2 else x[None]).to("cuda", dtype).contiguous()
+        ys = None if y is None else (y if y.dim() == 2 else y[None]).to("cuda", dtype).contiguous()
+        nrhs = (xs if xs is not None else ys).shape[0]
+        z = torch.empty((nrhs, self.n), dtype=dtype, device="cuda")
+        _lib.check(self._lib.bem_apply_batch(self._h, nrhs, _dtype_code(z), None if xs is None else xs.data_ptr(),
+                                             None if ys is None else ys.data_ptr(), z.data_ptr(),
+                                             _lib.BEM_APPLY_NO_HALF if no_half else 0, _stream()))
+        return z
