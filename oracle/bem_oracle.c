@@ -30,7 +30,8 @@
  *         interior point, int 1/r dA = sum_edges d ln((R+ + s+)/(R- + s-)),
  *         plus the bounded remainder int (exp(ikr)-1)/r dA done in polar
  *         coordinates about x_i, where the radial integral is analytic and the
- *         angle integral uses 64-point Gauss-Legendre per edge.
+ *         angle integral is adaptive Gauss-Legendre (16-point panels halved
+ *         until the halves agree to 1e-15) per edge.
  *
  * A 1-point (centroid) rule without near refinement is available through
  * flags; it exists for the reciprocity pin (S_ij/A_j = S_ji/A_i exactly).
@@ -133,7 +134,7 @@ static void rule_rl(const double* x, const double* a, const double* b, const dou
 }
 
 /* ---- Gauss-Legendre nodes (Newton iteration on P_n) --------------------- */
-#define OR_GL_N 64
+#define OR_GL_N 16
 static double gl_x[OR_GL_N], gl_w[OR_GL_N];
 static int gl_ready = 0;
 
@@ -168,6 +169,31 @@ static void gl_init(void) {
 }
 
 /* ---- exact self term S_ii --------------------------------------------- */
+/* Remainder integrand in polar coordinates about the centroid, for the edge
+ * at distance `dist`: the radial integral of (exp(ikr)-1)/r r dr from 0 to
+ * rho = dist / cos(phi) is (exp(ik rho)-1)/(ik) - rho. */
+static cplx smooth_radial(double dist, double phi, double k) {
+  double rho = dist / cos(phi);
+  if (k == 0.0) return 0.0;
+  double sh = sin(0.5 * k * rho);
+  return (sin(k * rho) / k - rho) + I * (2.0 * sh * sh / k);
+}
+
+static cplx gl_panel(double dist, double a, double b, double k) {
+  double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+  cplx s = 0.0;
+  for (int q = 0; q < OR_GL_N; ++q) s += gl_w[q] * smooth_radial(dist, mid + half * gl_x[q], k);
+  return half * s;
+}
+
+/* adaptive: bisect a panel until its two halves agree with it */
+static cplx gl_adaptive(double dist, double a, double b, double k, cplx whole, int depth) {
+  double m = 0.5 * (a + b);
+  cplx l = gl_panel(dist, a, m, k), r = gl_panel(dist, m, b, k);
+  if (depth >= 40 || cabs(l + r - whole) <= 1e-15 * (1.0 + cabs(l + r)) * (b - a)) return l + r;
+  return gl_adaptive(dist, a, m, k, l, depth + 1) + gl_adaptive(dist, m, b, k, r, depth + 1);
+}
+
 /* Returns S_ii for the triangle t at its own centroid.  See file header. */
 static cplx self_single_layer(const tri_t* t, double k) {
   const double* x = t->c;
@@ -193,21 +219,7 @@ static cplx self_single_layer(const tri_t* t, double k) {
     double Rp = norm3(bx), Rm = norm3(xa);
     s_static += dist * log((Rp + sp) / (Rm + sm));
     double phip = atan2(sp, dist), phim = atan2(sm, dist);
-    double half = 0.5 * (phip - phim), mid = 0.5 * (phip + phim);
-    for (int q = 0; q < OR_GL_N; ++q) {
-      double phi = mid + half * gl_x[q];
-      double rho = dist / cos(phi);
-      double re, im;
-      if (k == 0.0) {
-        re = 0.0;
-        im = 0.0;
-      } else {
-        double sh = sin(0.5 * k * rho);
-        re = sin(k * rho) / k - rho;
-        im = 2.0 * sh * sh / k;
-      }
-      s_smooth += half * gl_w[q] * (re + I * im);
-    }
+    s_smooth += gl_adaptive(dist, phim, phip, k, gl_panel(dist, phim, phip, k), 0);
   }
   return (s_static + s_smooth) / (4.0 * OR_PI);
 }

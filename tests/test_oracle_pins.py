@@ -57,8 +57,9 @@ def _self_adaptive(V, k):
 @pytest.mark.parametrize("k", [0.0, 1.0, 7.5])
 def test_self_term_matches_adaptive_quadrature(k):
     rng = np.random.default_rng(3)
-    for _ in range(3):
-        V = rng.normal(size=(3, 3)) * 0.3
+    slivers = [np.array([[0.0, 0, 0], [0.2, 0, 0], [0.1, 0.002, 0.0]]),           # aspect ~ 1e-2
+               np.array([[0.0, 0, 0], [0.05, 0.001, 0.0005], [0.3, 0.0, 0.0]])]   # long and thin
+    for V in [rng.normal(size=(3, 3)) * 0.3 for _ in range(3)] + slivers:
         T = np.array([[0, 1, 2]], dtype=np.int32)
         s, d = oracle.entries(V, T, k, [0], [0])
         ref = _self_adaptive(V, k)
