@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
+    ap.add_argument("--workload", choices=["headline", "precision", "batching", "large", "differentiation"],
+                    default="headline", help="headline = the metric above; the others are the remaining "
+                    "configurations (one JSON line each, not the headline metric)")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -332,11 +335,181 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _resonance_safe_k(k0, radii, width=0.2, nmax=40):
+    """k in [k0 - width, k0 + width] keeping every sphere (radius a) away from
+    the interior Dirichlet eigenvalues: maximise min_n |j_n(k a)| / max|j_n|."""
+    from scipy import special as sp
+    best, bk = -1.0, k0
+    for k in np.linspace(k0 - width, k0 + width, 81):
+        m = min(np.min(np.abs(sp.spherical_jn(np.arange(nmax), k * a)) /
+                       np.maximum(1e-300, np.max(np.abs(sp.spherical_jn(np.arange(nmax), np.linspace(0.5, 1.5, 21)[:, None] * k * a)), axis=0)))
+                for a in radii)
+        if m > best:
+            best, bk = m, k
+    return float(bk)
+
+
+def run_other(args):
+    """The configurations besides the headline, one JSON line each."""
+    import torch
+    import oracle
+    from paper_1606_02383_gb300 import inputs
+    from paper_1606_02383_gb300.operator import Batch, Operator
+
+    w = args.workload
+    steps, warm = args.steps, args.warmup
+    line = {"workload": w, "data": "synthetic", "n_gpus": 1, "steps": steps, "warmup": warm}
+    if w == "precision":
+        V, T = inputs.icosphere(5)
+        n, k = T.shape[0], 5.0
+        c, _, _, _ = oracle.geometry(V, T)
+        pw = inputs.plane_wave(c, k)[None, :]
+        dens = np.concatenate([pw, inputs.random_density(n, 16, seed=2)]).astype(np.complex64)
+        rows = np.sort(np.random.default_rng(0).choice(n, 2000, replace=False))
+        ref_s = oracle.apply(V, T, k, y=dens.astype(np.complex128), rows=rows)
+        ref_d = oracle.apply(V, T, k, x=dens.astype(np.complex128), rows=rows)
+        res = {}
+        for mode in ("mixed", "fp64"):
+            op = Operator(V, T, k, p=0, eps=1e-5, mode=mode, max_nrhs=17)
+            yd = torch.from_numpy(dens).cuda()
+            zs = op.apply(None, yd).cpu().numpy()[:, rows]
+            zd = op.apply(yd, None).cpu().numpy()[:, rows]
+            ms = _timed(lambda: op.apply(yd, yd), steps, warm)
+            b = torch.from_numpy(pw).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xs, iters, relres = op.solve(b, tol=1e-6, max_iter=300, restart=300)
+            torch.cuda.synchronize()
+            ts = time.perf_counter() - t0
+            r_true = oracle.apply(V, T, k, x=xs.cpu().numpy(), rows=rows)[0] - pw[0, rows]
+            res[mode] = {"apply_ms_17rhs": ms, "rhs_matvecs_per_s": 17e3 / ms,
+                         "rel_err_S_per_rhs_max": max(_rel(zs[q], ref_s[q]) for q in range(17)),
+                         "rel_err_z_per_rhs_max": max(_rel(zd[q], ref_d[q]) for q in range(17)),
+                         "gmres_iters": iters, "gmres_s": ts, "gmres_relres": float(relres[0]),
+                         "true_residual_2000_rows": float(np.linalg.norm(r_true) / np.linalg.norm(pw[0, rows]))}
+            op.close()
+        line.update({"metric": "rhs-matvecs/sec, 20,480-triangle sphere ka=5, plane wave + 16 complex64 densities",
+                     "value": res["mixed"]["rhs_matvecs_per_s"], "unit": "rhs-matvecs/s",
+                     "mixed_over_fp64": res["fp64"]["apply_ms_17rhs"] / res["mixed"]["apply_ms_17rhs"],
+                     "modes": res})
+    elif w == "batching":
+        probs = inputs.batch_bodies(64, seed=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        n = bt.n
+        x = torch.from_numpy(inputs.random_density(n, 2, seed=0, stream=0)).cuda()
+        y = torch.from_numpy(inputs.random_density(n, 2, seed=0, stream=1)).cuda()
+        ms = _timed(lambda: bt.apply(x, y), steps, warm)
+        z = bt.apply(x, y).cpu().numpy()
+        errs = []
+        for pb in (0, 1, 2, 3):
+            V, T, k = probs[pb]
+            a, e = bt.offsets[pb], bt.offsets[pb + 1]
+            rows = np.sort(np.random.default_rng(pb).choice(e - a, 500, replace=False))
+            ref = oracle.apply(V, T, k, x=x[:, a:e].cpu().numpy(), y=y[:, a:e].cpu().numpy(), rows=rows)
+            errs.append(_rel(z[:, a:e][:, rows], ref))
+        line.update({"metric": "batch applies/sec, 64 ellipsoids/tori (775,312 triangles, k in [1,8]), nrhs=2",
+                     "value": 1e3 / ms, "unit": "batch-applies/s", "ms_per_step": ms,
+                     "triangle_rhs_per_s": 2 * n / ms * 1e3, "setup_s": setup, "rel_err_bodies_0_3": errs})
+    elif w == "large":
+        V, T = inputs.large_multibody()
+        n = T.shape[0]
+        k = _resonance_safe_k(20.0, [1.0, 0.3])
+        c, _, _, _ = oracle.geometry(V, T)
+        x = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=0)).cuda()
+        y = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=1)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed")
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        ms = _timed(lambda: op.apply(x, y), steps, warm)
+        rows = np.sort(np.random.default_rng(0).choice(n, 2000, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.apply(V, T, k, x=x.cpu().numpy(), y=y.cpu().numpy(), rows=rows)
+        tor = time.perf_counter() - t0
+        err = _rel(op.apply(x, y).cpu().numpy()[:, rows], ref)
+        b = torch.from_numpy(inputs.plane_wave(c, k)[None, :]).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, iters, relres = op.solve(b, tol=1e-5, max_iter=400, restart=400, raise_on_fail=False)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        line.update({"metric": "FMM BEM matvecs/sec, 983,040 triangles (unit sphere + 8 spheres r=0.3), ka~20",
+                     "value": 1e3 / ms, "unit": "matvecs/s", "ms_per_step": ms, "k": k, "N": n, "setup_s": setup,
+                     "rel_err_vs_oracle_2000_rows": err, "orders": [op.order_of_level(l) for l in
+                                                                    range(2, op.info("leaf_level") + 1)],
+                     "gmres": {"tol": 1e-5, "iters": iters, "relres": float(relres[0]), "seconds": ts},
+                     "cpu_baseline": {"value": (2000 / n) / tor, "unit": "matvecs/s", "kind": "oracle",
+                                      "cores": oracle.num_threads(), "sample": "2,000 rows, extrapolated"}})
+    else:  # differentiation
+        V, T = inputs.level_set_mesh(0)
+        n, k = T.shape[0], 3.0
+        x0 = inputs.random_density(n, 1, seed=0, stream=0)
+        y0 = inputs.random_density(n, 1, seed=0, stream=1)
+        t0_ = inputs.random_density(n, 1, seed=0, stream=2)
+        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed")
+        kt = torch.tensor(k, dtype=torch.float64, requires_grad=True)
+        xt = torch.from_numpy(x0).cuda().requires_grad_(True)
+        yt = torch.from_numpy(y0).cuda().requires_grad_(True)
+        tt = torch.from_numpy(t0_).cuda()
+
+        def step():
+            kt.grad = xt.grad = yt.grad = None
+            loss = (op(xt, yt, kt) - tt).abs().pow(2).sum()
+            loss.backward()
+            return loss
+
+        ms = _timed(step, steps, warm)
+        loss = step()
+        hk = 1e-6
+        rows = None
+
+        def oloss(kk):
+            return float(np.sum(np.abs(oracle.apply(V, T, kk, x=x0, y=y0) - t0_) ** 2))
+
+        fd = (oloss(k + hk) - oloss(k - hk)) / (2 * hk)
+        z = oracle.apply(V, T, k, x=x0, y=y0)
+        gx_ref, gy_ref = oracle.adjoint(V, T, k, 2.0 * (z - t0_))
+        line.update({"metric": "forward+backward steps/sec (apply, adjoint, dL/dk), 30,004-triangle level-set "
+                               "surface, k=3", "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "N": n,
+                     "dk": float(kt.grad), "dk_central_difference_oracle": fd,
+                     "dk_rel_err": abs(float(kt.grad) - fd) / abs(fd),
+                     "dx_rel_err_vs_oracle": _rel(xt.grad.cpu().numpy(), gx_ref),
+                     "dy_rel_err_vs_oracle": _rel(yt.grad.cpu().numpy(), gy_ref)})
+        del rows, loss
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload != "headline":
+        if rank == 0:
+            run_other(args)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -18,6 +18,7 @@ __all__ = [
     "ellipsoid",
     "torus",
     "batch_bodies",
+    "level_set_mesh",
     "translate_scale",
     "merge_meshes",
     "random_density",
@@ -162,6 +163,115 @@ def batch_bodies(count: int = 64, seed: int = 0, n_min: int = 2000, n_max: int =
             V, T = torus(nu, nv, 1.0, r)
         out.append((V, T, k))
     return out
+
+
+def _marching_tets(phi, lo, h, t):
+    """Iso-surface phi = t of a grid function by marching tetrahedra.
+
+    Every cube splits into the 6 tetrahedra that run from corner (0,0,0) to
+    (1,1,1) along the 6 orders of the axes (a conforming split).  A tetrahedron
+    with 1 or 3 corners inside (phi > t) contributes one triangle, with 2 a
+    quadrilateral cut into two; cut points sit on the crossing edges at the
+    linear-interpolation zero and are shared through their grid edge, so the
+    surface is closed.  Triangles face from the inside corners to the outside
+    ones, i.e. out of the region phi > t.  Cut points are kept 2% of an edge
+    away from the grid vertices so that no triangle degenerates."""
+    n0, n1, n2 = phi.shape
+    I, J, K = np.meshgrid(np.arange(n0 - 1), np.arange(n1 - 1), np.arange(n2 - 1), indexing="ij")
+    base = np.stack([I.ravel(), J.ravel(), K.ravel()], -1)
+    unit = np.eye(3, dtype=np.int64)
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        c0 = np.zeros(3, np.int64)
+        c1 = unit[perm[0]]
+        c2 = c1 + unit[perm[1]]
+        c3 = c2 + unit[perm[2]]
+        tets.append(np.stack([base + c for c in (c0, c1, c2, c3)], 1))
+    tet = np.concatenate(tets)                                        # [ntet, 4, 3]
+    gid = (tet[..., 0] * n1 + tet[..., 1]) * n2 + tet[..., 2]        # [ntet, 4]
+    val = phi.ravel()[gid]
+    inside = val > t
+    nin = inside.sum(1)
+    keep = (nin > 0) & (nin < 4)
+    tet, gid, val, inside, nin = tet[keep], gid[keep], val[keep], inside[keep], nin[keep]
+    pos = lo + tet.astype(np.float64) * h
+    verts_key, verts_xyz, faces = {}, [], []
+
+    def cut(i, a, b):  # point on edge (a, b) of tetrahedron i
+        ga, gb = gid[i, a], gid[i, b]
+        key = (min(ga, gb), max(ga, gb))
+        idx = verts_key.get(key)
+        if idx is None:
+            fa, fb = val[i, a], val[i, b]
+            # kept away from the grid vertices so no cut edge degenerates
+            s_ = min(max((t - fa) / (fb - fa), 0.02), 0.98)
+            verts_xyz.append(pos[i, a] + s_ * (pos[i, b] - pos[i, a]))
+            idx = len(verts_xyz) - 1
+            verts_key[key] = idx
+        return idx
+
+    for i in range(tet.shape[0]):
+        ins = [a for a in range(4) if inside[i, a]]
+        out = [a for a in range(4) if not inside[i, a]]
+        if len(ins) == 1 or len(ins) == 3:
+            lone, rest = (ins[0], out) if len(ins) == 1 else (out[0], ins)
+            tri = [cut(i, lone, r) for r in rest]
+            faces.append((tri, ins, out, i))
+        else:
+            a, b = ins
+            c, d = out
+            q = [cut(i, a, c), cut(i, a, d), cut(i, b, d), cut(i, b, c)]
+            faces.append(([q[0], q[1], q[2]], ins, out, i))
+            faces.append(([q[0], q[2], q[3]], ins, out, i))
+    V = np.asarray(verts_xyz)
+    F = np.asarray([f[0] for f in faces], dtype=np.int64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    area2 = np.linalg.norm(nrm, axis=1)
+    away = np.asarray([pos[f[3], f[2]].mean(0) - pos[f[3], f[1]].mean(0) for f in faces])
+    flip = np.einsum("ij,ij->i", nrm, away) < 0
+    F[flip, 1], F[flip, 2] = F[flip, 2], F[flip, 1].copy()
+    del area2
+    return V, F
+
+
+def level_set_mesh(seed: int = 0, n_gauss: int = 20, grid: int = 64, target: int = 30000):
+    """The differentiation workload's surface: the level set of
+    phi(x) = sum_i exp(-|x - c_i|^2 / (2 w_i^2)) (c_i uniform in [-1,1]^3,
+    w_i uniform in [0.2, 0.5]) on a grid^3 lattice over [-2,2]^3, at the
+    iso-level (found by bisection) that gives about `target` triangles."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 4]))
+    c = rng.uniform(-1.0, 1.0, size=(n_gauss, 3))
+    w = rng.uniform(0.2, 0.5, size=n_gauss)
+    x = np.linspace(-2.0, 2.0, grid)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    P = np.stack([X, Y, Z], -1)
+    phi = np.zeros(X.shape)
+    for i in range(n_gauss):
+        phi += np.exp(-np.sum((P - c[i]) ** 2, -1) / (2.0 * w[i] ** 2))
+    h = x[1] - x[0]
+
+    def count(t):  # triangles of the iso-surface at level t, without building it
+        n0 = grid
+        I, J, K = np.meshgrid(np.arange(n0 - 1), np.arange(n0 - 1), np.arange(n0 - 1), indexing="ij")
+        base = np.stack([I.ravel(), J.ravel(), K.ravel()], -1)
+        unit = np.eye(3, dtype=np.int64)
+        tot = 0
+        for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+            cs = [np.zeros(3, np.int64), unit[perm[0]], unit[perm[0]] + unit[perm[1]], np.ones(3, np.int64)]
+            nin = sum((phi[tuple((base + cc).T)] > t).astype(np.int64) for cc in cs)
+            tot += int(np.sum((nin == 1) | (nin == 3)) + 2 * np.sum(nin == 2))
+        return tot
+
+    lo_t, hi_t = 1e-3, float(phi.max()) * 0.999
+    for _ in range(40):
+        mid = 0.5 * (lo_t + hi_t)
+        if count(mid) > target:
+            lo_t = mid
+        else:
+            hi_t = mid
+    V, F = _marching_tets(phi, np.array([-2.0, -2.0, -2.0]), h, 0.5 * (lo_t + hi_t))
+    return np.ascontiguousarray(V), np.ascontiguousarray(F.astype(np.int32))
 
 
 def translate_scale(vertices, scale=1.0, shift=(0.0, 0.0, 0.0)):
