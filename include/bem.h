@@ -65,7 +65,9 @@ typedef enum {
   BEM_MODE_FMM_MIXED = 0,   /* FP32 near field and expansions, FP64 setup, FP64 accumulation */
   BEM_MODE_FMM_FP64 = 1,    /* every stage in FP64 */
   BEM_MODE_DIRECT_FP64 = 2, /* O(N^2) direct sum in FP64 (same rule-defined operator) */
-  BEM_MODE_DIRECT_FP32 = 3  /* O(N^2) direct sum in FP32 with FP64 correction */
+  BEM_MODE_DIRECT_FP32 = 3, /* O(N^2) direct sum in FP32 with FP64 correction */
+  BEM_MODE_FMM_TF32 = 4     /* diagnostic: as MIXED but the translations use one plain TF32
+                               product instead of the 3xTF32 split (shows what the split buys) */
 } bem_mode;
 
 /* bem_apply flags */

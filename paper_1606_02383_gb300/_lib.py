@@ -25,7 +25,7 @@ BEM_ERR_UNSUPPORTED = 8
 BEM_C64 = 1
 BEM_C128 = 2
 
-MODES = {"mixed": 0, "fp64": 1, "direct64": 2, "direct32": 3}
+MODES = {"mixed": 0, "fp64": 1, "direct64": 2, "direct32": 3, "tf32": 4}
 
 BEM_APPLY_NO_HALF = 1
 BEM_HOST_BUFFERS = 2

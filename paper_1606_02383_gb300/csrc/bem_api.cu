@@ -13,7 +13,9 @@ int bem_fail(int code, const std::string& m) {
   return code;
 }
 
-bool bem_is_fmm(const bem_handle* h) { return h->mode == BEM_MODE_FMM_MIXED || h->mode == BEM_MODE_FMM_FP64; }
+bool bem_is_fmm(const bem_handle* h) {
+  return h->mode == BEM_MODE_FMM_MIXED || h->mode == BEM_MODE_FMM_FP64 || h->mode == BEM_MODE_FMM_TF32;
+}
 bool bem_is_fp64(const bem_handle* h) { return h->mode == BEM_MODE_FMM_FP64 || h->mode == BEM_MODE_DIRECT_FP64; }
 
 int bem_check_device_error(bem_handle* h, cudaStream_t s) {
@@ -115,7 +117,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
     if (o.p_min <= 0) o.p_min = 4;
     if (o.p_max <= 0) o.p_max = 40;
   }
-  if (o.mode < 0 || o.mode > 3) return bem_fail(BEM_ERR_INVALID_ARG, "unknown mode");
+  if (o.mode < 0 || o.mode > 4) return bem_fail(BEM_ERR_INVALID_ARG, "unknown mode");
   if (o.max_nrhs > 1024) return bem_fail(BEM_ERR_INVALID_ARG, "max_nrhs above 1024");
   if (o.leaf_level > BEM_MAXLEV) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level above 10");
   if (o.p_min > o.p_max || o.p_max > 60) return bem_fail(BEM_ERR_INVALID_ARG, "bad order bounds");

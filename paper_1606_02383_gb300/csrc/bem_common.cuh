@@ -134,6 +134,9 @@ struct GroupedOp {
   int64_t* d_group_mat = nullptr;
   int64_t flops = 0;                    // 8 * rows * cols per pair, summed
   // tensor-core form (mixed mode): A packed per (row tile, k stage), jobs (group, pair0, npairs, row tile)
+  // source level of the pairs (its expansions are prepared, reflected and split, before every launch)
+  int src_level = -1;
+  int* d_prep_row = nullptr;            // [npairs] row (flag * nbox + box) of the prepared source
   float* tcA = nullptr;
   int64_t* d_tc_off = nullptr;
   int4* d_tc_jobs = nullptr;
@@ -228,6 +231,8 @@ struct bem_handle {
   GroupedOp m2l_T[BEM_MAXLEV + 1];  // target level-l Lambda -> source level-l Mu (transpose of m2l[l])
   GroupedOp l2l_T[BEM_MAXLEV + 1];  // child level l+1 -> parent level l (transpose of l2l[l])
   void* mats_T = nullptr;
+  float* prep = nullptr;            // reflected, TF32-split source expansions of one level (tensor-core path)
+  int64_t prep_len = 0;
   double4* uv = nullptr;            // [nrhs_max][nt]: (u = S^T h, v = D^T h) before the weight, sorted
 
   // workspaces
@@ -288,7 +293,7 @@ int bem_adjoint_epilogue(bem_handle* h, int nrhs, int dtype, const void* g, void
 int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
               int flags, int* iters_out, double* relres_out, cudaStream_t s);
 int bem_check_device_error(bem_handle* h, cudaStream_t s);
-int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s);
+int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s);
 int bem_build_adjoint(bem_handle* h, cudaStream_t s);
 int bem_adjoint_sorted(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
                        cudaStream_t s);

@@ -131,20 +131,11 @@ __global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, 
 }
 
 // ------------------------------------------------------------------ kernel --
-// gathered element held by thread `tid` in register slot q of a stage: a warp
-// covers one 8-pair x 4-k core-matrix row block (lane / 4 pairs, lane % 4 k),
-// so its 32 shared-memory stores hit 32 different banks.
-__device__ __forceinline__ void e_slot(int tid, int q, int* c, int* kk) {
-  int lane = tid & 31, G = (tid >> 5) + 8 * q;  // G in [0, 64): 16 row groups x 4 k groups
-  *c = (G & 15) * 8 + (lane >> 2);
-  *kk = (G >> 4) * 4 + (lane & 3);
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
-    const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ src_off,
-    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ src,
-    float* __restrict__ dst, int64_t exp_stride, int* err) {
+    const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
+    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep, int R2,
+    float* __restrict__ dst, int64_t exp_stride, int nprod, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -161,13 +152,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const int ks0 = (job.z >> 8) * TC_KSLICE, ks1 = min(nks, ks0 + TC_KSLICE);
   const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
   const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
-  const float* S = src + 2 * (int64_t)r * exp_stride;
   float* D = dst + 2 * (int64_t)r * exp_stride;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid < TC_M) {
     bool ok = tid < np;
-    s_src[tid] = ok ? src_off[p0 + tid] : -1;
+    s_src[tid] = ok ? prep_row[p0 + tid] : -1;
     s_dst[tid] = ok ? dst_off[p0 + tid] : -1;
     s_flg[tid] = ok ? (int)pflags[p0 + tid] : 0;
   }
@@ -191,23 +181,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const uint32_t idesc = instr_desc(N);
   int issued_t = 0, committed = 0;  // tracked by thread 0 only
 
-  float pre[8];
+  // gather of one E stage from the prepared rows: per pair a hi and a lo row of
+  // R2 floats (reflection and split already applied); thread slot q covers
+  // (pair c, k-quad) with the 32 lanes of a warp on 32 consecutive pairs, so
+  // 16-byte loads and conflict-free 16-byte shared stores
+  float4 pre_h[2], pre_l[2];
   auto gather = [&](int ks) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int c, kk;
-      e_slot(tid, q, &c, &kk);
-      int realk = ks * TC_KS + kk;
-      int k = realk >> 1, part = realk & 1;
-      float v = 0.f;
-      int so = s_src[c];
-      if (so >= 0 && k < Pi) {
-        bool neg;
-        int ki = reflect_index(k, s_flg[c], &neg);
-        v = S[2 * ((int64_t)so + ki) + part];
-        if (neg) v = -v;
+    for (int q = 0; q < 2; ++q) {
+      int item = tid + TC_THREADS * q;  // 0..511
+      int quad = item >> 7, c = item & 127;
+      int row = s_src[c];
+      float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
+      if (row >= 0) {
+        const float* rp = prep + (int64_t)row * (2 * R2) + ks * TC_KS + quad * 4;
+        vh = *(const float4*)rp;
+        vl = *(const float4*)(rp + R2);
       }
-      pre[q] = v;
+      pre_h[q] = vh;
+      pre_l[q] = vl;
     }
   };
   __syncthreads();  // s_src visible
@@ -232,13 +224,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
       ++issued_t;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int c, kk;
-      e_slot(tid, q, &c, &kk);
-      float v = pre[q], hi = tf32_round(v);
-      uint32_t o = core_off(c, kk, TC_M);
-      *(float*)(sEh + o) = hi;
-      *(float*)(sEl + o) = v - hi;
+    for (int q = 0; q < 2; ++q) {
+      int item = tid + TC_THREADS * q;
+      int quad = item >> 7, c = item & 127;
+      uint32_t o = core_off(c, quad * 4, TC_M);
+      *(float4*)(sEh + o) = pre_h[q];
+      *(float4*)(sEl + o) = pre_l[q];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (ks + 1 < ks1) gather(ks + 1);
@@ -256,8 +247,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
           uint64_t bh = smem_desc(t0 + j * (N / 8) * 256);
           uint64_t bl = smem_desc(t0 + N * TC_KS * 4 + j * (N / 8) * 256);
           mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
-          mma_tf32(tmem, ah, bl, idesc, 1u);
-          mma_tf32(tmem, al, bh, idesc, 1u);
+          if (nprod == 3) {
+            mma_tf32(tmem, ah, bl, idesc, 1u);
+            mma_tf32(tmem, al, bh, idesc, 1u);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&bar_m[st]))
@@ -314,9 +307,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
 }
 
+// ------------------------------------------------------ source preparation --
+// For every box of the source level and every reflection f (8), a hi and a lo
+// row of R2 floats: row (f * nbox + b) holds s_f(k) M_b[Q_f(k)] as interleaved
+// (re, im), rounded to TF32 (hi) plus the remainder (lo), zero-padded to R2.
+__global__ void k_prep(const float* __restrict__ src, int64_t base, int nbox, int P, int R2, int nrhs_slab,
+                       int64_t exp_stride, float* __restrict__ out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t rows = (int64_t)8 * nbox;
+  if (idx >= rows * R2) return;
+  int64_t row = idx / R2;
+  int kr = (int)(idx % R2);
+  int f = (int)(row / nbox), b = (int)(row % nbox);
+  float v = 0.f;
+  if (kr < 2 * P) {
+    int k = kr >> 1, part = kr & 1;
+    bool neg;
+    int ki = reflect_index(k, f, &neg);
+    v = src[2 * ((int64_t)nrhs_slab * exp_stride + base + (int64_t)b * P + ki) + part];
+    if (neg) v = -v;
+  }
+  float hi = tf32_round(v);
+  out[row * (2 * (int64_t)R2) + kr] = hi;
+  out[row * (2 * (int64_t)R2) + R2 + kr] = v - hi;
+}
+
+__global__ void k_prep_rows(int np, const int* __restrict__ src_off, const unsigned char* __restrict__ flags,
+                            int64_t base, int P, int nbox, int* rows) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int b = (int)((src_off[i] - base) / P);
+  rows[i] = (int)flags[i] * nbox + b;
+}
+
 // -------------------------------------------------------------------- host --
-int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
+static inline int prep_stride(int P) { return ((2 * P + TC_KS - 1) / TC_KS) * TC_KS; }
+
+int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
   if (op.ngroups == 0) return BEM_OK;
+  op.src_level = src_level;
+  {
+    LevelInfo& sl = h->lev[src_level];
+    int64_t need = (int64_t)8 * sl.nbox * 2 * prep_stride(sl.P);
+    if (need > h->prep_len) {
+      float* p;
+      BEM_TRY(bem_alloc(h, &p, need));  // grows monotonically; older buffers stay in the handle's list
+      h->prep = p;
+      h->prep_len = need;
+    }
+    BEM_TRY(bem_alloc(h, &op.d_prep_row, std::max(op.npairs, 1)));
+    if (op.npairs > 0)
+      k_prep_rows<<<(op.npairs + 255) / 256, 256, 0, s>>>(op.npairs, op.d_src_off, op.d_flags, sl.exp_base, sl.P,
+                                                          sl.nbox, op.d_prep_row);
+    BEM_CUDA(cudaGetLastError());
+  }
   BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   std::vector<int64_t> off(op.ngroups);
   int64_t tot = 0;
@@ -355,11 +399,21 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, cudaStream_t s) {
 int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst, int nrhs, cudaStream_t s,
                        int* launches) {
   if (op.n_tc_jobs == 0) return BEM_OK;
-  dim3 grid(op.n_tc_jobs, nrhs);
-  k_grouped_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
-                                          op.d_src_off, op.d_dst_off, op.d_flags, (const float*)src, (float*)dst,
-                                          h->exp_total, h->d_err);
-  BEM_CUDA(cudaGetLastError());
-  ++*launches;
+  LevelInfo& sl = h->lev[op.src_level];
+  int R2 = prep_stride(sl.P);
+  for (int r = 0; r < nrhs; ++r) {
+    int64_t n = (int64_t)8 * sl.nbox * R2;
+    k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r,
+                                                        h->exp_total, h->prep);
+    BEM_CUDA(cudaGetLastError());
+    // one rhs at a time: the prepared buffer holds one source level of one rhs
+    dim3 grid(op.n_tc_jobs, 1);
+    k_grouped_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off,
+                                                   op.tcA, op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, R2,
+                                                   (float*)dst + 2 * (int64_t)r * h->exp_total, h->exp_total,
+                                                   h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, h->d_err);
+    BEM_CUDA(cudaGetLastError());
+    *launches += 2;
+  }
   return BEM_OK;
 }

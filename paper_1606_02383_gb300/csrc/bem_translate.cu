@@ -731,10 +731,10 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   }
   // ---- tensor-core packing of every grouped operator (mixed mode) ----
   if (!f64) {
-    for (int l = 2; l <= L; ++l) BEM_TRY(bem_build_tc(h, h->m2l[l], s));
+    for (int l = 2; l <= L; ++l) BEM_TRY(bem_build_tc(h, h->m2l[l], l, s));
     for (int l = 2; l < L; ++l) {
-      BEM_TRY(bem_build_tc(h, h->m2m[l], s));
-      BEM_TRY(bem_build_tc(h, h->l2l[l], s));
+      BEM_TRY(bem_build_tc(h, h->m2m[l], l + 1, s));
+      BEM_TRY(bem_build_tc(h, h->l2l[l], l, s));
     }
   }
 
@@ -790,7 +790,7 @@ __global__ void k_transpose_group(const R* __restrict__ in, R* __restrict__ out,
 
 // The transpose of a grouped operator: same pairs with source and destination
 // swapped, transposed matrices, same reflection flags ((Q T Q)^T = Q T^T Q).
-static int make_transposed(bem_handle* h, const GroupedOp& op, GroupedOp& t, cudaStream_t s) {
+static int make_transposed(bem_handle* h, const GroupedOp& op, GroupedOp& t, int src_level, cudaStream_t s) {
   t.ngroups = op.ngroups;
   t.rows = op.cols;
   t.cols = op.rows;
@@ -813,7 +813,7 @@ static int make_transposed(bem_handle* h, const GroupedOp& op, GroupedOp& t, cud
     BEM_CUDA(cudaGetLastError());
   }
   BEM_TRY(make_jobs(h, t, s));
-  if (!f64) BEM_TRY(bem_build_tc(h, t, s));
+  if (!f64) BEM_TRY(bem_build_tc(h, t, src_level, s));
   return BEM_OK;
 }
 
@@ -831,10 +831,10 @@ int bem_build_adjoint(bem_handle* h, cudaStream_t s) {
       BEM_TRY(bem_alloc(h, &m, 2 * std::max<int64_t>(h->mats_len, 1)));
       h->mats_T = m;
     }
-    for (int l = 2; l <= h->L; ++l) BEM_TRY(make_transposed(h, h->m2l[l], h->m2l_T[l], s));
+    for (int l = 2; l <= h->L; ++l) BEM_TRY(make_transposed(h, h->m2l[l], h->m2l_T[l], l, s));
     for (int l = 2; l < h->L; ++l) {
-      BEM_TRY(make_transposed(h, h->m2m[l], h->m2m_T[l], s));
-      BEM_TRY(make_transposed(h, h->l2l[l], h->l2l_T[l], s));
+      BEM_TRY(make_transposed(h, h->m2m[l], h->m2m_T[l], l, s));      // parent level -> children
+      BEM_TRY(make_transposed(h, h->l2l[l], h->l2l_T[l], l + 1, s));  // children -> parent level
     }
   }
   BEM_CUDA(cudaStreamSynchronize(s));

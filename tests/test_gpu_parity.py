@@ -175,3 +175,19 @@ def test_level_set_surface_with_slivers(cuda_ok):
     assert rel(z, ref) <= 1e-10
     z = Operator(V, T, k, p=0, eps=1e-5, mode="mixed").apply(dev(x), dev(y)).cpu().numpy()
     assert rel(z, ref) <= 1e-5
+
+
+def test_plain_tf32_translations_lose_accuracy(cuda_ok):
+    """The diagnostic mode with one TF32 product per translation is measurably
+    less accurate than the 3xTF32 split on a far-field-dominated product (a
+    smooth single-layer density), which is why the mixed mode splits."""
+    V, T = inputs.icosphere(4)
+    c, _, _, _ = oracle.geometry(V, T)
+    k = 3.0
+    y = inputs.plane_wave(c, k, (0.3, -0.2, 0.9))[None, :]
+    ref = oracle.apply(V, T, k, y=y)
+    e_mixed = rel(Operator(V, T, k, p=10, mode="mixed", leaf_level=4).apply(None, dev(y)).cpu().numpy(), ref)
+    e_tf32 = rel(Operator(V, T, k, p=10, mode="tf32", leaf_level=4).apply(None, dev(y)).cpu().numpy(), ref)
+    assert e_mixed <= 1e-5
+    assert e_tf32 > 3 * e_mixed
+    assert e_tf32 < 1e-2
