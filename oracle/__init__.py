@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     entries,
     eval_points,
     geometry,
+    grad,
     lu_solve,
     num_threads,
 )

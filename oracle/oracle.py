@@ -28,7 +28,7 @@ def _load():
     if _lib is not None:
         return _lib
     path = _build.LIB
-    if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_build.SRC):
+    if _build.stale():
         path = _build.build()
     lib = ctypes.CDLL(path)
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -41,8 +41,10 @@ def _load():
                                        _D, _i64, _D]
     lib.oracle_assemble.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, _D, _D]
     lib.oracle_lu_solve.argtypes = [_i64, _D, ctypes.c_int, _D]
+    lib.oracle_grad.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                                _I64, _i64, _D, _D]
     for f in (lib.oracle_geometry, lib.oracle_entries, lib.oracle_apply, lib.oracle_apply_adjoint,
-              lib.oracle_eval_points, lib.oracle_assemble, lib.oracle_lu_solve):
+              lib.oracle_eval_points, lib.oracle_assemble, lib.oracle_lu_solve, lib.oracle_grad):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -125,6 +127,35 @@ def adjoint(V, T, k, g, flags=0):
                                       _dp(ga), gx.ctypes.data_as(_D), gy.ctypes.data_as(_D))
     assert rc == 0
     return gx, gy
+
+
+def grad(V, T, k, g, x=None, y=None, vertices=None, flags=0):
+    """Gradient of the real loss L with dL = sum Re(conj(g) dz), z = (1/2 I - D) x + S y.
+
+    Returns (dV, dk): dV [nv, 3] and dk (float) for every vertex; with
+    `vertices` given, dV [len(vertices), 3] for those vertices only (computed
+    from the pairs that touch them) and dk None.  Forward-mode dual arithmetic
+    over every rule-defined entry (bem_oracle_grad.c)."""
+    V, T = _mesh(V, T)
+    nt = T.shape[0]
+    ga, ng = _cplx(g, nt)
+    xa, nx = _cplx(x, nt)
+    ya, ny = _cplx(y, nt)
+    assert ng > 0 and nx in (0, ng) and ny in (0, ng)
+    if vertices is None:
+        dV = np.empty((V.shape[0], 3))
+        dk = np.empty(1)
+        sel, nsel = None, 0
+    else:
+        sel = np.ascontiguousarray(vertices, dtype=np.int64)
+        nsel = sel.size
+        dV = np.empty((nsel, 3))
+        dk = None
+    rc = _load().oracle_grad(_dp(V), V.shape[0], T.ctypes.data_as(_I32), nt, float(k), int(flags), ng, _dp(ga),
+                             _dp(xa), _dp(ya), None if sel is None else sel.ctypes.data_as(_I64), nsel, _dp(dV),
+                             _dp(dk))
+    assert rc == 0
+    return dV, (None if dk is None else float(dk[0]))
 
 
 def eval_points(V, T, k, pts, x=None, y=None, flags=0):

@@ -203,3 +203,93 @@ def test_mie_series_truncation_independent():
     a = cf.mie_rigid_sphere_surface(5.0, 1.0, ct)
     b = cf.mie_rigid_sphere_surface(5.0, 1.0, ct, nmax=60)
     assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
+
+
+# --- vertex / wavenumber gradient (forward-mode duals over every entry) ------
+
+def _loss(V, T, k, g, x, y):
+    """L = sum Re(conj(g) z), z = (1/2 I - D) x + S y: the loss whose upstream gradient is g."""
+    z = oracle.apply(V, T, k, x, y)
+    return float(np.sum((np.conj(g) * z).real))
+
+
+def _grad_case(mesh, k, nrhs=2, seed=5):
+    V, T = mesh
+    nt = T.shape[0]
+    rng = np.random.default_rng(seed)
+    draw = lambda: rng.standard_normal((nrhs, nt)) + 1j * rng.standard_normal((nrhs, nt))
+    return V, T, k, draw(), draw(), draw()
+
+
+def _jittered_icosphere():
+    V, T = inputs.icosphere(1)
+    rng = np.random.default_rng(3)
+    return V * (1.0 + 0.08 * rng.standard_normal((V.shape[0], 1))), T
+
+
+@pytest.mark.parametrize("which", ["icosphere1_jittered", "level_set_slivers"])
+def test_gradient_matches_central_differences(which):
+    """Pin: the derivative is the limit of the difference quotient of the pinned
+    apply.  Coarse meshes put most pairs inside the refined rules R_1, R_2 and
+    every self term on the path; the level-set mesh adds sliver triangles."""
+    mesh = _jittered_icosphere() if which == "icosphere1_jittered" else inputs.level_set_mesh(seed=1, grid=16, target=300)
+    V, T, k, g, x, y = _grad_case(mesh, 2.3)
+    dV, dk = oracle.grad(V, T, k, g, x, y)
+    h = 1e-6
+    rng = np.random.default_rng(11)
+    for v in rng.choice(V.shape[0], 6, replace=False):
+        for d in range(3):
+            Vp, Vm = V.copy(), V.copy()
+            Vp[v, d] += h
+            Vm[v, d] -= h
+            fd = (_loss(Vp, T, k, g, x, y) - _loss(Vm, T, k, g, x, y)) / (2 * h)
+            assert abs(dV[v, d] - fd) <= 1e-6 * max(1.0, abs(fd)), (v, d, dV[v, d], fd)
+    fdk = (_loss(V, T, k + h, g, x, y) - _loss(V, T, k - h, g, x, y)) / (2 * h)
+    assert abs(dk - fdk) <= 1e-6 * max(1.0, abs(fdk))
+
+
+@pytest.mark.parametrize("sliver", [False, True])
+def test_self_term_gradient_matches_central_differences(sliver):
+    """One triangle: L = Re(conj(g) S_11 y) is the exact self term alone (D_11 = 0)."""
+    V = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.3, 0.8, 0.2]])
+    if sliver:
+        V[2] = [0.5, 0.03, 0.01]
+    T = np.array([[0, 1, 2]], dtype=np.int32)
+    g, x, y = np.array([[0.7 - 0.4j]]), np.array([[0.3 + 0.9j]]), np.array([[1.1 + 0.2j]])
+    k = 4.0
+    dV, dk = oracle.grad(V, T, k, g, x, y)
+    h = 1e-6
+    for v in range(3):
+        for d in range(3):
+            Vp, Vm = V.copy(), V.copy()
+            Vp[v, d] += h
+            Vm[v, d] -= h
+            fd = (_loss(Vp, T, k, g, x, y) - _loss(Vm, T, k, g, x, y)) / (2 * h)
+            assert abs(dV[v, d] - fd) <= 1e-7 * max(1.0, abs(fd)), (v, d, dV[v, d], fd)
+    fdk = (_loss(V, T, k + h, g, x, y) - _loss(V, T, k - h, g, x, y)) / (2 * h)
+    assert abs(dk - fdk) <= 1e-7 * max(1.0, abs(fdk))
+
+
+def test_gradient_invariances_and_scaling_identity():
+    """Pins from the symmetries of the operator, exact for the rule-defined entries:
+    - translating the mesh changes no entry: sum_v dL/dV_v = 0;
+    - rotating it changes none: sum_v V_v x dL/dV_v = 0;
+    - scaling: S(lam V, k) = lam S(V, lam k) and D(lam V, k) = D(V, lam k), so
+      sum_v V_v . dL/dV_v = Re<g, S y> + k dL/dk."""
+    V, T, k, g, x, y = _grad_case(inputs.level_set_mesh(seed=2, grid=16, target=300), 3.1)
+    V = V + np.array([0.4, -0.2, 0.9])  # away from the origin, so rotation and scaling are not trivial
+    dV, dk = oracle.grad(V, T, k, g, x, y)
+    scale = np.abs(V).sum(axis=1) @ np.abs(dV).sum(axis=1)
+    assert np.abs(dV.sum(axis=0)).max() <= 1e-12 * np.abs(dV).sum()
+    assert np.abs(np.cross(V, dV).sum(axis=0)).max() <= 1e-12 * scale
+    sy = float(np.sum((np.conj(g) * oracle.apply(V, T, k, None, y)).real))
+    assert abs(np.sum(V * dV) - (sy + k * dk)) <= 1e-12 * scale
+
+
+def test_gradient_of_selected_vertices_equals_full():
+    V, T, k, g, x, y = _grad_case(_jittered_icosphere(), 1.7)
+    dV, _ = oracle.grad(V, T, k, g, x, y)
+    sel = np.array([0, 7, 33, 41])
+    dVs, dks = oracle.grad(V, T, k, g, x, y, vertices=sel)
+    assert dks is None
+    np.testing.assert_allclose(dVs, dV[sel], rtol=1e-13, atol=1e-13 * np.abs(dV).max())
