@@ -176,20 +176,29 @@ int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* g
                       void* stream);
 
 /*
- * bem_grad -- derivative of a real loss L with respect to the wavenumber k,
- * given the upstream gradient g = dL/dz of z = bem_apply(x, y) (PyTorch's
- * convention for complex outputs: g = dL/dRe z + i dL/dIm z):
- *     dk = sum over rhs of Re < g, (dA/dk) u >,
- * where dA/dk differentiates every rule-defined entry: the smooth kernels
- * dG/dk = i exp(ikr)/(4 pi) and d(dG/dn)/dk = -k exp(ikr) (y-x).n/(4 pi r),
- * the refined near-singular rules and the exact self term.  The gradients
- * with respect to x and y are bem_apply_adjoint.
+ * bem_grad -- derivatives of a real loss L with respect to the vertex
+ * positions and the wavenumber k, given the upstream gradient g = dL/dz of
+ * z = bem_apply(x, y) (PyTorch's convention for complex outputs:
+ * g = dL/dRe z + i dL/dIm z), so that dL = sum over rhs of Re <g, dz>:
+ *     dvertices[v] = sum over rhs of Re < g, (dA/dV_v) u >,
+ *     dk           = sum over rhs of Re < g, (dA/dk) u >,
+ * where A u = (1/2 I - D) x + S y and every rule-defined entry is
+ * differentiated: the collocation point (the centroid) and the quadrature
+ * points move with the vertices, the weight with the area and D with the unit
+ * normal; the refined near-singular rules are differentiated point by point
+ * (their refinement level is piecewise constant); the exact self term S_ii
+ * in closed radial form (D_ii = 0 for every vertex position).  The k-kernels
+ * are dG/dk = i exp(ikr)/(4 pi) and d(dG/dn)/dk = -k exp(ikr) (y-x).n/(4 pi r).
+ * The gradients with respect to x and y are bem_apply_adjoint.
  *   g, x, y   : [nrhs][N] device buffers (x or y may be NULL, not both).
- *   dvertices : must be NULL (vertex gradients are not provided; the call
- *               returns BEM_ERR_UNSUPPORTED otherwise).
- *   dk        : host pointer to one double.
- * Cost: an FP64 direct sum over all pairs (O(N^2)) plus the correction
- * pairs; it allocates per-call scratch and synchronises `stream`.
+ *   dvertices : nullable host array [nv][3], the caller's vertex order
+ *               (BEM_ERR_INVALID_ARG for a device pointer).
+ *   dk        : nullable host pointer to one double; not both NULL.
+ * Cost: direct sums over all pairs (O(N^2)): FP64 in the FP64 modes; in the
+ * mixed modes the vertex terms run in FP32 with FP64 accumulation, and FP64
+ * for pairs within 4.5 longest edges, while dk stays FP64.  The correction
+ * pairs are FP64.  The call allocates per-call scratch and synchronises
+ * `stream`.
  */
 int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, const void* y, double* dvertices,
              double* dk, void* stream);

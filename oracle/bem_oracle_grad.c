@@ -27,7 +27,8 @@
  *     of int 1/r dA plus the polar-coordinate remainder int (exp(ikr)-1)/r dA
  *     with adaptive Gauss-Legendre in the angle.  The panels' end points are
  *     functions of the vertices and carry tangents; panels are halved until
- *     the value and every tangent of the two halves agree with the whole.
+ *     the value and every tangent of the two halves agree with the whole
+ *     (tolerances at dclose).
  * x_i is the centroid, so a tangent of x_i moves each vertex of Gamma_i by 1/3.
  * The derivative with respect to k requires k > 0.
  */
@@ -262,19 +263,25 @@ static dual dgl_panel(dual dist, dual a, dual b, dual k) {
   return dmul(half, s);
 }
 
-static int dclose(dual lr, dual whole, double width) {
+/* A panel is accepted when its halves agree with it: the value to the tolerance
+ * bem_oracle.c uses, each tangent to 1e-13 of the whole edge integral's
+ * tangent (floored at 1) per unit of angle.  A budget of panels per edge bounds
+ * the recursion where rounding keeps the tangents from settling. */
+static int dclose(dual lr, dual whole, const dual* top, double width) {
   if (cabs(lr.v - whole.v) > 1e-15 * (1.0 + cabs(lr.v)) * width) return 0;
   for (int t = 0; t < GR_ND; ++t)
-    if (cabs(lr.d[t] - whole.d[t]) > 1e-13 * (1.0 + cabs(lr.d[t])) * width) return 0;
+    if (cabs(lr.d[t] - whole.d[t]) > 1e-13 * (1.0 + cabs(top->d[t])) * width) return 0;
   return 1;
 }
 
-static dual dgl_adaptive(dual dist, dual a, dual b, dual k, dual whole, int depth) {
+static dual dgl_adaptive(dual dist, dual a, dual b, dual k, dual whole, const dual* top, int depth, int* budget) {
   dual m = dscale(dadd(a, b), 0.5);
   dual l = dgl_panel(dist, a, m, k), r = dgl_panel(dist, m, b, k);
   dual lr = dadd(l, r);
-  if (depth >= 40 || dclose(lr, whole, creal(b.v) - creal(a.v))) return lr;
-  return dadd(dgl_adaptive(dist, a, m, k, l, depth + 1), dgl_adaptive(dist, m, b, k, r, depth + 1));
+  *budget -= 2;
+  if (depth >= 40 || *budget <= 0 || dclose(lr, whole, top, creal(b.v) - creal(a.v))) return lr;
+  dual left = dgl_adaptive(dist, a, m, k, l, top, depth + 1, budget);
+  return dadd(left, dgl_adaptive(dist, m, b, k, r, top, depth + 1, budget));
 }
 
 /* S_ii of the triangle v at its own centroid */
@@ -301,7 +308,9 @@ static dual dself(const dual v[3][3], dual k) {
     dual Rp = vnorm(bx), Rm = vnorm(xa);
     s_static = dadd(s_static, dmul(dist, dlog(ddiv(dadd(Rp, sp), dadd(Rm, sm)))));
     dual phip = datan2(sp, dist), phim = datan2(sm, dist);
-    s_smooth = dadd(s_smooth, dgl_adaptive(dist, phim, phip, k, dgl_panel(dist, phim, phip, k), 0));
+    dual top = dgl_panel(dist, phim, phip, k);
+    int budget = 1 << 22;
+    s_smooth = dadd(s_smooth, dgl_adaptive(dist, phim, phip, k, top, &top, 0, &budget));
   }
   return dscale(dadd(s_static, s_smooth), 1.0 / (4.0 * GR_PI));
 }

@@ -196,6 +196,7 @@ struct bem_handle {
   double* area = nullptr;       // [nt]
   double* hmax = nullptr;       // [nt]
   double* wgt = nullptr;        // A_j / (12 pi): quadrature weight per point, with 1/(4 pi)
+  int* tri = nullptr;           // [nt][3] caller's vertex indices of every sorted element
   float4* tgt32 = nullptr;      // [nt] centroid
   float4* src32 = nullptr;      // [nt][3] quadrature points, normal in .w
   double4* tgt64 = nullptr;
@@ -262,6 +263,13 @@ int bem_prof_begin(bem_handle* h, cudaStream_t s);                      // retur
 void bem_prof_end(bem_handle* h, int rec, int stage, int launches, cudaStream_t s);
 bool bem_is_fmm(const bem_handle* h);
 bool bem_is_fp64(const bem_handle* h);
+// n-point Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n), host side
+void bem_gl_host(int n, double* x, double* w);
+// vertex gradient of the loss (bem_grad_vertices.cu); yx, gs: unweighted
+// densities (y, x) and the upstream gradient in octree order, FP64;
+// dvertices: host array [nv][3], written when `s` completes
+int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices,
+                      cudaStream_t s);
 
 template <typename T>
 int bem_alloc(bem_handle* h, T** p, size_t count) {

@@ -255,7 +255,7 @@ __global__ void k_grad_k_corr(int64_t nt, int nrhs, double k, const double* __re
   if (lane == 0 && part != 0.0) atomicAdd(out, part);
 }
 
-static void gl_host(int n, double* x, double* w) {
+void bem_gl_host(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
     double z = cos(BEM_PI * (i + 0.75) / (n + 0.5));
     for (int it = 0; it < 200; ++it) {
@@ -292,8 +292,12 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
   if (nrhs < 1 || nrhs > h->nrhs_max) return bem_fail(BEM_ERR_INVALID_ARG, "nrhs out of [1, max_nrhs]");
   if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
   if (!g || (!x && !y)) return bem_fail(BEM_ERR_INVALID_ARG, "g and at least one of x, y are required");
-  if (dvertices) return bem_fail(BEM_ERR_UNSUPPORTED, "vertex gradients are not available; pass dvertices = NULL");
-  if (!dk) return bem_fail(BEM_ERR_INVALID_ARG, "dk is NULL");
+  if (!dk && !dvertices) return bem_fail(BEM_ERR_INVALID_ARG, "dk and dvertices are both NULL");
+  cudaPointerAttributes pa;
+  if (dvertices && (cudaPointerGetAttributes(&pa, dvertices) != cudaSuccess || pa.type == cudaMemoryTypeDevice)) {
+    cudaGetLastError();
+    return bem_fail(BEM_ERR_INVALID_ARG, "dvertices must be a host pointer");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   int64_t nt = h->nt;
   double4* yx;
@@ -311,8 +315,16 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
     k_grad_prologue<float><<<nblk(nt, 256), 256, 0, s>>>(nt, nrhs, h->perm, (const float*)g, (const float*)x,
                                                          (const float*)y, yx, gs);
   BEM_CUDA(cudaGetLastError());
+  if (dvertices) BEM_TRY(bem_grad_vertices(h, nrhs, yx, gs, dvertices, s));
+  if (!dk) {
+    BEM_CUDA(cudaFreeAsync(yx, s));
+    BEM_CUDA(cudaFreeAsync(gs, s));
+    BEM_CUDA(cudaFreeAsync(acc, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    return bem_check_device_error(h, s);
+  }
   double glx[32], glw[32];
-  gl_host(32, glx, glw);
+  bem_gl_host(32, glx, glw);
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
   {

@@ -1,0 +1,617 @@
+// bem_grad_vertices.cu -- derivative of a real loss with respect to the vertex
+// positions of the mesh (the shape gradient the topology optimisation of
+// Section 2.5 needs, restricted here to the boundary operators of Section 2.3).
+//
+// For z = (1/2 I - D) x + S y and the upstream gradient g (PyTorch's complex
+// convention), dL = sum_rhs sum_i Re(conj(g_i) dz_i).  The 1/2 I term does not
+// move with the mesh, so per pair (i, j), with cy = sum_rhs conj(g_i) y_j and
+// cx = sum_rhs conj(g_i) x_j, the loss holds l_ij = Re(cy S_ij - cx D_ij).
+//
+// One point y of weight w on Gamma_j seen from the collocation point x:
+//   d = y - x, r = |d|, E = exp(ikr)/(4 pi)
+//   G = E/r                         (the single-layer kernel)
+//   F = E (ikr - 1)/r^3             grad_y G = F d,  dG/dn_y = F (d.n)
+//   H = E (3 - 3ikr - k^2 r^2)/r^5  grad_y F = H d
+//   grad_y (dG/dn_y) = H (d.n) d + F n;  grad_x = -grad_y for both kernels.
+// The entry also moves through the weight (w = A/(3 4^L), A the area) and the
+// unit normal n.  With e_a = V_{a+1} - V_{a+2} (cyclic vertex order) and
+// P = I - n n^T:
+//   dA/dV_a = (1/2) e_a x n,     d(u.n)/dV_a = e_a x (P u) / (2 A),
+// and the point y = sum_a beta_a V_a moves with the vertices by beta_a.  The
+// collocation point is the centroid, so it moves by 1/3 with each vertex of
+// its own triangle.
+//
+// Pieces, all on the stream:
+//   regular rule R_0 over every pair: one target-major pass gives the centroid
+//     gradients, one source-major pass the point / area / normal gradients.
+//     FP64 in the FP64 modes; otherwise FP32 with block-relative coordinates
+//     and FP64 accumulation after every tile, except pairs closer than 4.5
+//     longest edges, which stay FP64.
+//   corrections (FP64): for every pair of the correction matrix, the
+//     derivative of the refined rule R_L, or of the exact self term, minus
+//     that of R_0.  The exact self term S_ii (D_ii = 0 for every vertex
+//     position) differentiates in closed radial form: with lambda_a the
+//     barycentric coordinates and polar coordinates (rho, u) about the centroid,
+//       dS_ii/dV_a = (dA/dV_a) S_ii / A
+//                  + (1/4 pi) int u (u . grad lambda_a) K(R(phi)) dphi,
+//       K(R) = int_0^R exp(ik rho)(ik rho - 1) d rho = R exp(ikR) - 2 (exp(ikR) - 1)/(ik),
+//     integrated per edge with the substitution tan(phi) = sinh(t) and 32-point
+//     Gauss-Legendre on panels of length <= 4 in t.
+//   finish: per element, everything mapped onto its three vertices and added
+//     into the caller's vertex order.
+#include "bem_common.cuh"
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// sin/cos in the precision of the pair evaluation
+__device__ __forceinline__ void sc(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sc(double a, double* s, double* c) { sincos(a, s, c); }
+
+// G, F, H of one point at separation d (|d| > 0)
+template <typename R>
+__device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F, cpx<R>& H) {
+  R r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  R r = sqrt(r2);
+  R ir = R(1) / r;
+  R ir2 = ir * ir;
+  R kr = k * r;
+  R sn, cs;
+  sc(kr, &sn, &cs);
+  const R c4 = R(1.0 / (4.0 * BEM_PI));
+  cpx<R> E = cmk(cs * c4, sn * c4);
+  G = ir * E;
+  // F = E (ikr - 1) / r^3
+  F = (ir * ir2) * (E * cmk(R(-1), kr));
+  // H = E (3 - k^2 r^2 - 3ikr) / r^5
+  H = (ir2 * ir2 * ir) * (E * cmk(R(3) - kr * kr, R(-3) * kr));
+}
+
+// ------------------------------------------------------ regular rule R_0 --
+// In the FP32 passes, sources within NEAR64 h_j of the target (centroid to
+// centroid, h_j the longest edge) are evaluated in FP64 from the FP64
+// geometry: their kernels are the largest and FP32 rounding of the short
+// separations would dominate the error.  Which pass takes a pair changes only
+// its rounding, not the rule, so the FP32 distance test needs no margin of
+// consistency with the correction matrix.
+#define NEAR64 4.5
+
+// the target-pass terms of one pair in FP64: acc += sum_q w [-F d y_j + (H (d.n) d + F n) x_j]
+__device__ void near_target64(const double* __restrict__ xi, int64_t j, double k, const double* __restrict__ qpt,
+                              const double* __restrict__ nrm, const double* __restrict__ area,
+                              const double4* __restrict__ u, double* acc) {
+  const double w = area[j] / 3.0;
+  const double4 v = u[j];
+  const zd wy = cmk(w * v.x, w * v.y), wx = cmk(w * v.z, w * v.w);
+  const double n0 = nrm[3 * j], n1 = nrm[3 * j + 1], n2 = nrm[3 * j + 2];
+  for (int q = 0; q < 3; ++q) {
+    const double d0 = qpt[9 * j + 3 * q] - xi[0], d1 = qpt[9 * j + 3 * q + 1] - xi[1],
+                 d2 = qpt[9 * j + 3 * q + 2] - xi[2];
+    zd G, F, H;
+    ghf(d0, d1, d2, k, G, F, H);
+    const double dn = d0 * n0 + d1 * n1 + d2 * n2;
+    const zd a = dn * (H * wx) - F * wy;
+    const zd b = F * wx;
+    acc[0] += d0 * a.re + n0 * b.re;
+    acc[1] += d0 * a.im + n0 * b.im;
+    acc[2] += d1 * a.re + n1 * b.re;
+    acc[3] += d1 * a.im + n1 * b.im;
+    acc[4] += d2 * a.re + n2 * b.re;
+    acc[5] += d2 * a.im + n2 * b.im;
+  }
+}
+
+// Target-major pass: for every collocation point x_i,
+//   gx_i += Re( conj(g_i) sum_j sum_q w_j [ -F d y_j + (H (d.n) d + F n) x_j ] ),
+// the gradient of l_i = sum_j l_ij with respect to x_i (w_j = A_j/3).  One
+// thread per target, sources streamed through shared memory; coordinates are
+// taken relative to the block's first centroid before rounding to R.
+template <typename R>
+__global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const double* __restrict__ cent,
+                                                   const double* __restrict__ qpt, const double* __restrict__ nrm,
+                                                   const double* __restrict__ area, const double* __restrict__ hmax,
+                                                   const double4* __restrict__ yx, const double2* __restrict__ gs,
+                                                   double* __restrict__ gx) {
+  __shared__ R s_q[128][9];
+  __shared__ R s_n[128][3];
+  __shared__ cpx<R> s_y[128], s_x[128];
+  __shared__ R s_c[128][3];  // FP32 only: source centroid and squared near radius
+  __shared__ R s_h2[128];
+  const int r = blockIdx.y;
+  const int64_t i0 = blockIdx.x * (int64_t)128;
+  const int64_t i = i0 + threadIdx.x;
+  double ref[3];
+  for (int d = 0; d < 3; ++d) ref[d] = cent[3 * i0 + d];
+  R x[3] = {R(0), R(0), R(0)};
+  if (i < nt)
+    for (int d = 0; d < 3; ++d) x[d] = R(cent[3 * i + d] - ref[d]);
+  const double4* u = yx + (int64_t)r * nt;
+  const R kk = R(k);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e0 = 0; e0 < nt; e0 += 128) {
+    const int ne = (int)min((int64_t)128, nt - e0);
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      const int64_t j = e0 + threadIdx.x;
+      for (int q = 0; q < 3; ++q)
+        for (int d = 0; d < 3; ++d) s_q[threadIdx.x][3 * q + d] = R(qpt[9 * j + 3 * q + d] - ref[d]);
+      for (int d = 0; d < 3; ++d) s_n[threadIdx.x][d] = R(nrm[3 * j + d]);
+      const double w = area[j] / 3.0;
+      const double4 v = u[j];
+      s_y[threadIdx.x] = cmk(R(w * v.x), R(w * v.y));
+      s_x[threadIdx.x] = cmk(R(w * v.z), R(w * v.w));
+      if (sizeof(R) == 4) {
+        for (int d = 0; d < 3; ++d) s_c[threadIdx.x][d] = R(cent[3 * j + d] - ref[d]);
+        const double rn = NEAR64 * hmax[j];
+        s_h2[threadIdx.x] = R(rn * rn);
+      }
+    }
+    __syncthreads();
+    if (i < nt) {
+      cpx<R> T0 = cmk(R(0), R(0)), T1 = T0, T2 = T0;
+      for (int e = 0; e < ne; ++e) {
+        if (sizeof(R) == 4) {
+          const R c0 = s_c[e][0] - x[0], c1 = s_c[e][1] - x[1], c2 = s_c[e][2] - x[2];
+          if (c0 * c0 + c1 * c1 + c2 * c2 < s_h2[e]) {
+            near_target64(cent + 3 * i, e0 + e, k, qpt, nrm, area, u, acc);
+            continue;
+          }
+        }
+        const cpx<R> wy = s_y[e], wx = s_x[e];
+        const R n0 = s_n[e][0], n1 = s_n[e][1], n2 = s_n[e][2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const R d0 = s_q[e][3 * q] - x[0], d1 = s_q[e][3 * q + 1] - x[1], d2 = s_q[e][3 * q + 2] - x[2];
+          cpx<R> G, F, H;
+          ghf(d0, d1, d2, kk, G, F, H);
+          const R dn = d0 * n0 + d1 * n1 + d2 * n2;
+          const cpx<R> a = dn * (H * wx) - F * wy;
+          const cpx<R> b = F * wx;
+          T0 = T0 + d0 * a + n0 * b;
+          T1 = T1 + d1 * a + n1 * b;
+          T2 = T2 + d2 * a + n2 * b;
+        }
+      }
+      acc[0] += T0.re;
+      acc[1] += T0.im;
+      acc[2] += T1.re;
+      acc[3] += T1.im;
+      acc[4] += T2.re;
+      acc[5] += T2.im;
+    }
+  }
+  if (i < nt) {
+    const double2 g = gs[(int64_t)r * nt + i];
+    for (int d = 0; d < 3; ++d) atomicAdd(&gx[3 * i + d], g.x * acc[2 * d] + g.y * acc[2 * d + 1]);
+  }
+}
+
+// the source-pass sums of one pair in FP64 (c = conj(g_i))
+__device__ void near_source64(const double* __restrict__ yq, const double* __restrict__ n,
+                              const double* __restrict__ xi, double2 g, double k, double* PS, double* QH, double* Fs,
+                              double* GS, double* GD) {
+  const double d0 = yq[0] - xi[0], d1 = yq[1] - xi[1], d2 = yq[2] - xi[2];
+  zd G, F, H;
+  ghf(d0, d1, d2, k, G, F, H);
+  const double dn = d0 * n[0] + d1 * n[1] + d2 * n[2];
+  const zd c = cmk(g.x, -g.y);
+  const zd cF = c * F, cH = dn * (c * H), cG = c * G;
+  const double d[3] = {d0, d1, d2};
+  for (int m = 0; m < 3; ++m) {
+    PS[2 * m] += d[m] * cF.re;
+    PS[2 * m + 1] += d[m] * cF.im;
+    QH[2 * m] += d[m] * cH.re;
+    QH[2 * m + 1] += d[m] * cH.im;
+  }
+  Fs[0] += cF.re;
+  Fs[1] += cF.im;
+  GS[0] += cG.re;
+  GS[1] += cG.im;
+  GD[0] += dn * cF.re;
+  GD[1] += dn * cF.im;
+}
+
+// Source-major pass: one thread per quadrature point p = 3 j + q of the regular
+// rule, all collocation points streamed through shared memory.  With
+// c_i = conj(g_i) it sums PS = sum c F d, QH = sum c H (d.n) d, Fs = sum c F,
+// GS = sum c G, GD = sum c F (d.n) and leaves
+//   gq[p] = Re( w (y_j PS - x_j (QH + Fs n)) )   (gradient w.r.t. the point)
+//   ga[j] += Re( y_j GS - x_j GD ) / 3           (w.r.t. the area, w/A = 1/3)
+//   gn[j] += -Re( w x_j PS )                     (w.r.t. the unit normal)
+template <typename R>
+__global__ void __launch_bounds__(128) k_gv_source(int64_t nt, double k, const double* __restrict__ cent,
+                                                   const double* __restrict__ qpt, const double* __restrict__ nrm,
+                                                   const double* __restrict__ area, const double* __restrict__ hmax,
+                                                   const double4* __restrict__ yx, const double2* __restrict__ gs,
+                                                   double* __restrict__ gq, double* __restrict__ ga,
+                                                   double* __restrict__ gn) {
+  __shared__ R s_x[128][3];
+  __shared__ cpx<R> s_g[128];
+  const int r = blockIdx.y;
+  const int64_t p0 = blockIdx.x * (int64_t)128;
+  const int64_t p = p0 + threadIdx.x;
+  const bool act = p < 3 * nt;
+  const int64_t j = act ? p / 3 : 0;
+  const int q = (int)(p % 3);
+  double ref[3];
+  for (int d = 0; d < 3; ++d) ref[d] = cent[3 * (p0 / 3) + d];
+  R y[3], n[3];
+  for (int d = 0; d < 3; ++d) {
+    y[d] = R(qpt[9 * j + 3 * q + d] - ref[d]);
+    n[d] = R(nrm[3 * j + d]);
+  }
+  const R kk = R(k);
+  const double2* gr = gs + (int64_t)r * nt;
+  double PS[6] = {0, 0, 0, 0, 0, 0}, QH[6] = {0, 0, 0, 0, 0, 0}, Fs[2] = {0, 0}, GS[2] = {0, 0}, GD[2] = {0, 0};
+  // FP32 only: this element's centroid and squared near radius (FP64 pairs)
+  R cj[3] = {R(0), R(0), R(0)}, h2 = R(0);
+  if (sizeof(R) == 4) {
+    for (int d = 0; d < 3; ++d) cj[d] = R(cent[3 * j + d] - ref[d]);
+    const double rn = NEAR64 * hmax[j];
+    h2 = R(rn * rn);
+  }
+  for (int64_t e0 = 0; e0 < nt; e0 += 128) {
+    const int ne = (int)min((int64_t)128, nt - e0);
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      const int64_t i = e0 + threadIdx.x;
+      for (int d = 0; d < 3; ++d) s_x[threadIdx.x][d] = R(cent[3 * i + d] - ref[d]);
+      const double2 g = gr[i];
+      s_g[threadIdx.x] = cmk(R(g.x), R(-g.y));
+    }
+    __syncthreads();
+    if (act) {
+      cpx<R> ps0 = cmk(R(0), R(0)), ps1 = ps0, ps2 = ps0, qh0 = ps0, qh1 = ps0, qh2 = ps0, fs = ps0, gsum = ps0,
+             gd = ps0;
+      for (int e = 0; e < ne; ++e) {
+        if (sizeof(R) == 4) {
+          const R c0 = cj[0] - s_x[e][0], c1 = cj[1] - s_x[e][1], c2 = cj[2] - s_x[e][2];
+          if (c0 * c0 + c1 * c1 + c2 * c2 < h2) {
+            near_source64(qpt + 9 * j + 3 * q, nrm + 3 * j, cent + 3 * (e0 + e), gr[e0 + e], k, PS, QH, Fs, GS, GD);
+            continue;
+          }
+        }
+        const R d0 = y[0] - s_x[e][0], d1 = y[1] - s_x[e][1], d2 = y[2] - s_x[e][2];
+        cpx<R> G, F, H;
+        ghf(d0, d1, d2, kk, G, F, H);
+        const R dn = d0 * n[0] + d1 * n[1] + d2 * n[2];
+        const cpx<R> c = s_g[e];
+        const cpx<R> cF = c * F;
+        const cpx<R> cH = dn * (c * H);
+        ps0 = ps0 + d0 * cF;
+        ps1 = ps1 + d1 * cF;
+        ps2 = ps2 + d2 * cF;
+        qh0 = qh0 + d0 * cH;
+        qh1 = qh1 + d1 * cH;
+        qh2 = qh2 + d2 * cH;
+        fs = fs + cF;
+        gsum = gsum + c * G;
+        gd = gd + dn * cF;
+      }
+      PS[0] += ps0.re; PS[1] += ps0.im; PS[2] += ps1.re; PS[3] += ps1.im; PS[4] += ps2.re; PS[5] += ps2.im;
+      QH[0] += qh0.re; QH[1] += qh0.im; QH[2] += qh1.re; QH[3] += qh1.im; QH[4] += qh2.re; QH[5] += qh2.im;
+      Fs[0] += fs.re; Fs[1] += fs.im;
+      GS[0] += gsum.re; GS[1] += gsum.im;
+      GD[0] += gd.re; GD[1] += gd.im;
+    }
+  }
+  if (!act) return;
+  const double w = area[j] / 3.0;
+  const double4 v = yx[(int64_t)r * nt + j];
+  const zd yj = cmk(v.x, v.y), xj = cmk(v.z, v.w);
+  const zd fsz = cmk(Fs[0], Fs[1]);
+  for (int d = 0; d < 3; ++d) {
+    const zd ps = cmk(PS[2 * d], PS[2 * d + 1]);
+    const zd qh = cmk(QH[2 * d], QH[2 * d + 1]) + nrm[3 * j + d] * fsz;
+    const zd t = yj * ps - xj * qh;
+    atomicAdd(&gq[3 * p + d], w * t.re);
+    atomicAdd(&gn[3 * j + d], -w * (xj * ps).re);
+  }
+  const zd ar = yj * cmk(GS[0], GS[1]) - xj * cmk(GD[0], GD[1]);
+  atomicAdd(&ga[j], ar.re / 3.0);
+}
+
+// ------------------------------------------------------------ corrections --
+struct VTri {
+  double v[3][3], n[3], c[3], area, h;
+};
+
+__device__ void vload(const double* __restrict__ qpt, const double* __restrict__ nrm, const double* __restrict__ cent,
+                      const double* __restrict__ area, const double* __restrict__ hmax, int64_t j, VTri& t) {
+  for (int d = 0; d < 3; ++d) {
+    t.c[d] = cent[3 * j + d];
+    t.n[d] = nrm[3 * j + d];
+  }
+  // the rule's point a is (2/3) V_a + (1/6)(V_b + V_c) = (V_a + 3 c)/2
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) t.v[a][d] = 2.0 * qpt[9 * j + 3 * a + d] - t.c[d];
+  t.area = area[j];
+  t.h = hmax[j];
+}
+
+__device__ __forceinline__ void cross(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// adds dL/dA (scalar) and dL/dn (vector) of triangle t onto its vertices
+__device__ void map_area_normal(const VTri& t, double gA, const double* gN, double* g9) {
+  double nn = gN[0] * t.n[0] + gN[1] * t.n[1] + gN[2] * t.n[2];
+  double pg[3] = {gN[0] - nn * t.n[0], gN[1] - nn * t.n[1], gN[2] - nn * t.n[2]};
+  for (int a = 0; a < 3; ++a) {
+    const double* b = t.v[(a + 1) % 3];
+    const double* c = t.v[(a + 2) % 3];
+    double e[3] = {b[0] - c[0], b[1] - c[1], b[2] - c[2]};
+    double ea[3], en[3];
+    cross(e, t.n, ea);
+    cross(e, pg, en);
+    for (int d = 0; d < 3; ++d) g9[3 * a + d] += 0.5 * gA * ea[d] + en[d] / (2.0 * t.area);
+  }
+}
+
+// sign * d/d(geometry) of Re(cy S_ij - cx D_ij) under rule R_L on triangle t:
+// the collocation point's gradient goes to tgt, the vertices' to g9.
+__device__ void rule_grad(const double* x, const VTri& t, int L, double k, zd cy, zd cx, double sign, double* tgt,
+                          double* g9) {
+  const int npieces = 1 << (2 * L);
+  const double w = t.area / (3.0 * npieces);
+  double gA = 0.0, gN[3] = {0.0, 0.0, 0.0};
+  double g9l[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tl[3] = {0, 0, 0};
+  for (int piece = 0; piece < npieces; ++piece) {
+    // barycentric coordinates (rows: the piece's corners, columns: V_0..V_2)
+    double B[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    int code = piece;
+    for (int lvl = 0; lvl < L; ++lvl) {
+      const int child = code & 3;
+      code >>= 2;
+      double ab[3], bc[3], ca[3];
+      for (int a = 0; a < 3; ++a) {
+        ab[a] = 0.5 * (B[0][a] + B[1][a]);
+        bc[a] = 0.5 * (B[1][a] + B[2][a]);
+        ca[a] = 0.5 * (B[2][a] + B[0][a]);
+      }
+      for (int a = 0; a < 3; ++a) {
+        if (child == 0) {
+          B[1][a] = ab[a];
+          B[2][a] = ca[a];
+        } else if (child == 1) {
+          B[0][a] = ab[a];
+          B[2][a] = bc[a];
+        } else if (child == 2) {
+          B[0][a] = ca[a];
+          B[1][a] = bc[a];
+        } else {
+          B[0][a] = ab[a];
+          B[1][a] = bc[a];
+          B[2][a] = ca[a];
+        }
+      }
+    }
+    for (int q = 0; q < 3; ++q) {
+      double beta[3], d[3];
+      for (int a = 0; a < 3; ++a) {
+        beta[a] = 0.0;
+        for (int c = 0; c < 3; ++c) beta[a] += (c == q ? 2.0 / 3.0 : 1.0 / 6.0) * B[c][a];
+      }
+      for (int dd = 0; dd < 3; ++dd)
+        d[dd] = beta[0] * t.v[0][dd] + beta[1] * t.v[1][dd] + beta[2] * t.v[2][dd] - x[dd];
+      zd G, F, H;
+      ghf(d[0], d[1], d[2], k, G, F, H);
+      const double dn = d[0] * t.n[0] + d[1] * t.n[1] + d[2] * t.n[2];
+      const zd a = cy * F - dn * (cx * H);
+      const zd b = cx * F;
+      for (int dd = 0; dd < 3; ++dd) {
+        const double pg = w * (a.re * d[dd] - b.re * t.n[dd]);
+        tl[dd] -= pg;
+        for (int c = 0; c < 3; ++c) g9l[3 * c + dd] += beta[c] * pg;
+        gN[dd] -= w * b.re * d[dd];
+      }
+      gA += (cy * G - dn * (cx * F)).re;
+    }
+  }
+  map_area_normal(t, gA * w / t.area, gN, g9l);
+  for (int m = 0; m < 9; ++m) g9[m] += sign * g9l[m];
+  for (int dd = 0; dd < 3; ++dd) tgt[dd] += sign * tl[dd];
+}
+
+__constant__ double c_vgl_x[32];
+__constant__ double c_vgl_w[32];
+
+// int_0^1 exp(i a s) ds = (exp(ia) - 1)/(ia)
+__device__ zd moment0(double a) {
+  if (fabs(a) < 0.5) {
+    zd acc = cmk(0.0, 0.0), term = cmk(1.0, 0.0);  // (ia)^n / n!
+    for (int n = 0; n < 24; ++n) {
+      acc = acc + (1.0 / (n + 1.0)) * term;
+      term = (1.0 / (n + 1.0)) * (term * cmk(0.0, a));
+    }
+    return acc;
+  }
+  double sn, cs;
+  sincos(a, &sn, &cs);
+  // (cs - 1 + i sn) / (i a) = (sn - i (cs - 1)) / a
+  return cmk(sn / a, (1.0 - cs) / a);
+}
+
+// d/dV of Re(cy S_ii) for the exact self term (closed radial form, file header)
+__device__ void self_grad(const VTri& t, double k, zd cy, double* g9) {
+  double gl[3][3];  // grad lambda_a = (e_a x n) / (2A), e_a = V_{a+1} - V_{a+2}
+  double dA[3][3];  // dA/dV_a = (1/2) e_a x n
+  for (int a = 0; a < 3; ++a) {
+    const double* b = t.v[(a + 1) % 3];
+    const double* c = t.v[(a + 2) % 3];
+    double e[3] = {b[0] - c[0], b[1] - c[1], b[2] - c[2]}, en[3];
+    cross(e, t.n, en);
+    for (int d = 0; d < 3; ++d) {
+      gl[a][d] = en[d] / (2.0 * t.area);
+      dA[a][d] = 0.5 * en[d];
+    }
+  }
+  zd S = cmk(0.0, 0.0);
+  zd J[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) J[a][d] = cmk(0.0, 0.0);
+  for (int e = 0; e < 3; ++e) {
+    const double* a = t.v[e];
+    const double* b = t.v[(e + 1) % 3];
+    double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double len = sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+    double tv[3] = {ab[0] / len, ab[1] / len, ab[2] / len};
+    double xa[3] = {t.c[0] - a[0], t.c[1] - a[1], t.c[2] - a[2]};
+    double pr = xa[0] * tv[0] + xa[1] * tv[1] + xa[2] * tv[2];
+    double fx[3] = {xa[0] - pr * tv[0], xa[1] - pr * tv[1], xa[2] - pr * tv[2]};
+    double dist = sqrt(fx[0] * fx[0] + fx[1] * fx[1] + fx[2] * fx[2]);
+    double fh[3] = {-fx[0] / dist, -fx[1] / dist, -fx[2] / dist};  // centroid -> foot of the edge
+    const double u0 = asinh(-pr / dist), u1 = asinh((len - pr) / dist);
+    // the direction's tanh(u) has poles at u = +-i pi/2: panels of length <= 4
+    // keep 32-point Gauss-Legendre at rounding level on slivers, whose u-range
+    // grows like 2 log(edge / height)
+    const int npan = max(1, (int)ceil((u1 - u0) / 4.0));
+    const double plen = (u1 - u0) / npan;
+    for (int qq = 0; qq < 32 * npan; ++qq) {
+      const int q = qq & 31;
+      const double half = 0.5 * plen, mid = u0 + plen * ((qq >> 5) + 0.5);
+      const double u = mid + half * c_vgl_x[q];
+      const double ch = cosh(u), sh = sinh(u);
+      const double R = dist * ch;
+      const double wq = half * c_vgl_w[q] / ch;  // d phi = du / cosh(u)
+      const zd m0 = moment0(k * R);
+      double sn, cs;
+      sincos(k * R, &sn, &cs);
+      S = S + (wq * R) * m0;
+      const zd K = R * (cmk(cs, sn) - 2.0 * m0);
+      double dir[3];
+      for (int d = 0; d < 3; ++d) dir[d] = (fh[d] + sh * tv[d]) / ch;
+      for (int va = 0; va < 3; ++va) {
+        const double s = dir[0] * gl[va][0] + dir[1] * gl[va][1] + dir[2] * gl[va][2];
+        for (int d = 0; d < 3; ++d) J[va][d] = J[va][d] + (wq * s * dir[d]) * K;
+      }
+    }
+  }
+  const double c4 = 1.0 / (4.0 * BEM_PI);
+  for (int va = 0; va < 3; ++va)
+    for (int d = 0; d < 3; ++d) {
+      const zd dS = (c4 * dA[va][d] / t.area) * S + c4 * J[va][d];
+      g9[3 * va + d] += (cy * dS).re;
+    }
+}
+
+// One warp per row i of the correction matrix: for every (i, j) the refined
+// rule (or, for j == i, the exact self term) minus R_0.  Collocation-point
+// gradients are summed over the warp into gx; vertex gradients of Gamma_j go
+// to gel[j] (9 doubles: V_0, V_1, V_2).
+__global__ void k_gv_corr(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+                          const double* __restrict__ qpt, const double* __restrict__ nrm,
+                          const double* __restrict__ area, const double* __restrict__ hmax,
+                          const int* __restrict__ ptr, const int* __restrict__ col, const double4* __restrict__ yx,
+                          const double2* __restrict__ gs, double* __restrict__ gx, double* __restrict__ gel) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  double tg[3] = {0.0, 0.0, 0.0};
+  if (i < nt) {
+    const double x[3] = {cent[3 * i], cent[3 * i + 1], cent[3 * i + 2]};
+    for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+      const int64_t j = col[e];
+      VTri t;
+      vload(qpt, nrm, cent, area, hmax, j, t);
+      int L = 0;
+      if (j != i) {
+        const double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
+        const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+        if (L == 0) continue;  // the rules agree: no correction
+      }
+      zd cy = cmk(0.0, 0.0), cx = cmk(0.0, 0.0);
+      for (int r = 0; r < nrhs; ++r) {
+        const double2 g = gs[(int64_t)r * nt + i];
+        const double4 v = yx[(int64_t)r * nt + j];
+        const zd cg = cmk(g.x, -g.y);
+        cy = cy + cg * cmk(v.x, v.y);
+        cx = cx + cg * cmk(v.z, v.w);
+      }
+      double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
+      rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
+      if (j == i) {
+        self_grad(t, k, cy, g9);
+        // the collocation point is this triangle's own centroid
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) g9[3 * a + d] += tt[d] / 3.0;
+      } else {
+        rule_grad(x, t, L, k, cy, cx, 1.0, tt, g9);
+        for (int d = 0; d < 3; ++d) tg[d] += tt[d];
+      }
+      for (int m = 0; m < 9; ++m) atomicAdd(&gel[9 * j + m], g9[m]);
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) tg[d] += __shfl_xor_sync(0xffffffffu, tg[d], o);
+  if (i < nt && lane == 0)
+    for (int d = 0; d < 3; ++d) atomicAdd(&gx[3 * i + d], tg[d]);
+}
+
+// Per element: regular-rule point, area and normal gradients and the
+// collocation-point gradient mapped onto the three vertices, plus the
+// corrections; added into the caller's vertex order.
+__global__ void k_gv_finish(int64_t nt, const double* __restrict__ cent, const double* __restrict__ qpt,
+                            const double* __restrict__ nrm, const double* __restrict__ area,
+                            const double* __restrict__ hmax, const int* __restrict__ tri,
+                            const double* __restrict__ gx, const double* __restrict__ gq,
+                            const double* __restrict__ ga, const double* __restrict__ gn,
+                            const double* __restrict__ gel, double* __restrict__ dV) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  VTri t;
+  vload(qpt, nrm, cent, area, hmax, j, t);
+  double g9[9];
+  for (int m = 0; m < 9; ++m) g9[m] = gel[9 * j + m];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) {
+      double s = gx[3 * j + d] / 3.0;
+      for (int q = 0; q < 3; ++q) s += (q == a ? 2.0 / 3.0 : 1.0 / 6.0) * gq[9 * j + 3 * q + d];
+      g9[3 * a + d] += s;
+    }
+  const double gN[3] = {gn[3 * j], gn[3 * j + 1], gn[3 * j + 2]};
+  map_area_normal(t, ga[j], gN, g9);
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) atomicAdd(&dV[3 * (int64_t)tri[3 * j + a] + d], g9[3 * a + d]);
+}
+
+int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices,
+                      cudaStream_t s) {
+  const int64_t nt = h->nt, nv = h->nv;
+  double *gx, *gq, *ga, *gn, *gel, *dV;
+  const size_t nd = (size_t)nt * (3 + 9 + 1 + 3 + 9) + (size_t)nv * 3;
+  double* buf;
+  BEM_CUDA(cudaMallocAsync((void**)&buf, nd * sizeof(double), s));
+  BEM_CUDA(cudaMemsetAsync(buf, 0, nd * sizeof(double), s));
+  gx = buf;
+  gq = gx + 3 * nt;
+  ga = gq + 9 * nt;
+  gn = ga + nt;
+  gel = gn + 3 * nt;
+  dV = gel + 9 * nt;
+  const dim3 gt(nblk(nt, 128), nrhs), gsrc(nblk(3 * nt, 128), nrhs);
+  if (bem_is_fp64(h)) {
+    k_gv_target<double><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx);
+    k_gv_source<double><<<gsrc, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gq, ga,
+                                             gn);
+  } else {
+    k_gv_target<float><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx);
+    k_gv_source<float><<<gsrc, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gq, ga,
+                                            gn);
+  }
+  BEM_CUDA(cudaGetLastError());
+  double glx[32], glw[32];
+  bem_gl_host(32, glx, glw);
+  BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
+  k_gv_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
+                                               h->corr_ptr, h->corr_col, yx, gs, gx, gel);
+  BEM_CUDA(cudaGetLastError());
+  k_gv_finish<<<nblk(nt, 128), 128, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->tri, gx, gq, ga, gn,
+                                            gel, dV);
+  BEM_CUDA(cudaGetLastError());
+  BEM_CUDA(cudaMemcpyAsync(dvertices, dV, (size_t)nv * 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA(cudaFreeAsync(buf, s));
+  return BEM_OK;
+}

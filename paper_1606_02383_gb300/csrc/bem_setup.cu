@@ -149,11 +149,13 @@ __global__ void k_count_levels(const uint32_t* __restrict__ keys, int64_t nt, un
 
 // gather per-element geometry into sorted order
 __global__ void k_permute_geometry(const int* __restrict__ perm, int64_t nt, const double* cent_o, const double* qpt_o,
-                                   const double* nrm_o, const double* area_o, const double* hmax_o, double* cent,
-                                   double* qpt, double* nrm, double* area, double* hmax, double* wgt) {
+                                   const double* nrm_o, const double* area_o, const double* hmax_o,
+                                   const int32_t* __restrict__ tri_o, double* cent, double* qpt, double* nrm,
+                                   double* area, double* hmax, double* wgt, int* tri) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nt) return;
   int64_t o = perm[s];
+  for (int a = 0; a < 3; ++a) tri[3 * s + a] = tri_o[3 * o + a];
   for (int d = 0; d < 3; ++d) {
     cent[3 * s + d] = cent_o[3 * o + d];
     nrm[3 * s + d] = nrm_o[3 * o + d];
@@ -594,8 +596,9 @@ int bem_build_geometry(bem_handle* h, const double* dV, const int32_t* dT, cudaS
   BEM_TRY(bem_alloc(h, &h->area, nt));
   BEM_TRY(bem_alloc(h, &h->hmax, nt));
   BEM_TRY(bem_alloc(h, &h->wgt, nt));
-  k_permute_geometry<<<nblk(nt, 256), 256, 0, s>>>(h->perm, nt, cent_o, qpt_o, nrm_o, area_o, hmax_o, h->cent, h->qpt,
-                                                   h->nrm, h->area, h->hmax, h->wgt);
+  BEM_TRY(bem_alloc(h, &h->tri, nt * 3));
+  k_permute_geometry<<<nblk(nt, 256), 256, 0, s>>>(h->perm, nt, cent_o, qpt_o, nrm_o, area_o, hmax_o, dT, h->cent,
+                                                   h->qpt, h->nrm, h->area, h->hmax, h->wgt, h->tri);
   BEM_CUDA(cudaGetLastError());
   // longest edge over the mesh
   {

@@ -51,6 +51,7 @@ class Operator:
         self._h = h
         self._lib = lib
         self.n = T.shape[0]
+        self.vertices = V.copy()
         self.k = float(k)
         self.mode = mode
         self.max_nrhs = int(max_nrhs)
@@ -142,15 +143,33 @@ class Operator:
                                       None, ctypes.byref(dk), _stream()))
         return float(dk.value)
 
-    def __call__(self, x, y, k=None):
+    def grad(self, g, x=None, y=None, vertices=True, k=True):
+        """Gradients of the real loss with upstream gradient g of z = apply(x, y).
+
+        Returns (dV, dk): dV a float64 array [nv, 3] of dL/dvertices (None when
+        vertices=False) and dk = dL/dk (None when k=False), from one bem_grad call."""
+        gs = self._prep(g, g.dtype)
+        xs, ys = self._prep(x, g.dtype), self._prep(y, g.dtype)
+        dV = np.zeros(self.vertices.shape, dtype=np.float64) if vertices else None
+        dk = ctypes.c_double(0.0)
+        _lib.check(self._lib.bem_grad(self._h, gs.shape[0], _dtype_code(gs), gs.data_ptr(),
+                                      None if xs is None else xs.data_ptr(), None if ys is None else ys.data_ptr(),
+                                      None if dV is None else dV.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.byref(dk) if k else None,
+                                      _stream()))
+        return dV, (float(dk.value) if k else None)
+
+    def __call__(self, x, y, k=None, vertices=None):
         """Differentiable z = (1/2 I - D) x + S y (torch.autograd).
 
-        Backward: dL/dx, dL/dy from bem_apply_adjoint; if a real tensor `k`
-        (equal to the operator's wavenumber) is passed, dL/dk from bem_grad.
+        Backward: dL/dx, dL/dy from bem_apply_adjoint.  If a real tensor `k`
+        (equal to the operator's wavenumber) or a float64 tensor `vertices`
+        (equal to the mesh the operator was set up with) is passed, dL/dk and
+        dL/dvertices come from bem_grad.
         """
         if k is None:
             k = torch.tensor(self.k, dtype=torch.float64)
-        return BemApplyFn.apply(self, x, y, k)
+        return BemApplyFn.apply(self, x, y, k, vertices)
 
     def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
         """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs])."""
@@ -175,9 +194,11 @@ class BemApplyFn(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, op, x, y, k):
+    def forward(ctx, op, x, y, k, vertices=None):
         if abs(float(k) - op.k) > 1e-12 * max(1.0, abs(op.k)):
             raise ValueError("k must equal the wavenumber the operator was set up with")
+        if vertices is not None and not np.array_equal(vertices.detach().cpu().numpy(), op.vertices):
+            raise ValueError("vertices must equal the mesh the operator was set up with")
         ctx.op = op
         ctx.save_for_backward(x, y)
         return op.apply(x, y)
@@ -187,10 +208,13 @@ class BemApplyFn(torch.autograd.Function):
         x, y = ctx.saved_tensors
         gz = gz.contiguous()
         gx, gy = ctx.op.adjoint(gz)
-        gk = None
-        if ctx.needs_input_grad[3]:
-            gk = torch.tensor(ctx.op.grad_k(gz, x, y), dtype=torch.float64)
-        return None, gx.reshape(gz.shape), gy.reshape(gz.shape), gk
+        gk = gv = None
+        want_k, want_v = ctx.needs_input_grad[3], len(ctx.needs_input_grad) > 4 and ctx.needs_input_grad[4]
+        if want_k or want_v:
+            dV, dk = ctx.op.grad(gz, x, y, vertices=want_v, k=want_k)
+            gk = torch.tensor(dk, dtype=torch.float64) if want_k else None
+            gv = torch.from_numpy(dV) if want_v else None
+        return None, gx.reshape(gz.shape), gy.reshape(gz.shape), gk, gv
 
 
 class Batch:
