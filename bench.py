@@ -282,7 +282,7 @@ def run_ours(args, world, rank, local):
         return
     peaks, peak_src = measured_peaks()
     info = {kk: op.info(kk) for kk in ("leaf_level", "n_leaves", "p2p_pairs", "corr_nnz", "m2l_pairs",
-                                       "m2l_flops", "p_leaf", "p_top")}
+                                       "m2l_flops", "p_leaf", "p_top", "device_bytes")}
     orders = [op.order_of_level(l) for l in range(2, info["leaf_level"] + 1)]
     # roofline of the dominant stage (average launch duration from the live events)
     dom = max(stages, key=lambda s: stages[s][0])
@@ -322,7 +322,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(args, n, {"leaf_level": info["leaf_level"], "orders_level2_to_leaf": orders,
-                                            "setup_s": round(setup_s, 3), "rel_err_vs_oracle_2000_rows": rel_err,
+                                            "setup_s": round(setup_s, 3), "device_bytes": info["device_bytes"],
+                                            "rel_err_vs_oracle_2000_rows": rel_err,
                                             "valid": bool(rel_err is not None and rel_err <= 1e-5),
                                             "wall_s_timed_region": round(wall, 4)}),
             "roofline": roof,
@@ -505,6 +506,10 @@ def run_other(args):
                                "level-set surface, k=3", "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "N": n,
                      "dvertices_rel_err_vs_oracle_8_vertices": _rel(Vt.grad.numpy()[sel], dV_ref),
                      "dk": float(kt.grad), "dk_oracle_richardson_central_difference_h1e-3": fd,
+                     # the same dk with the upstream gradient built from the oracle's z: separates the
+                     # FP64 derivative from the FMM error of the forward apply carried by g = 2 (z - t)
+                     "dk_rel_err_with_oracle_upstream": abs(op.grad_k(torch.from_numpy(2.0 * (z - t0_)).cuda(),
+                                                                      xt.detach(), yt.detach()) - fd) / abs(fd),
                      "dk_rel_err": abs(float(kt.grad) - fd) / abs(fd),
                      "dx_rel_err_vs_oracle": _rel(xt.grad.cpu().numpy(), gx_ref),
                      "dy_rel_err_vs_oracle": _rel(yt.grad.cpu().numpy(), gy_ref)})
