@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
     const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
     const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep, int R2,
-    float* __restrict__ dst, int64_t exp_stride, int nprod, int* err) {
+    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   __shared__ int s_abort;
   __shared__ int s_src[TC_M], s_dst[TC_M], s_flg[TC_M];
 
-  const int4 job = jobs[blockIdx.x];
-  const int r = blockIdx.y;
+  // blocks walk (job, rhs) with the rhs fastest, so the CTAs that read one
+  // matrix stage run together and share it through L2
+  const int4 job = jobs[blockIdx.x / nchunk];
+  const int r = blockIdx.x % nchunk;
   const int g = job.x, p0 = job.y, np = job.z & 255, nt = job.w;
   const int Po = grows[g], Pi = gcols[g];
   const int N = tc_ntile_width(2 * Po, nt);
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
 
   if (tid < TC_M) {
     bool ok = tid < np;
-    s_src[tid] = ok ? prep_row[p0 + tid] : -1;
+    s_src[tid] = ok ? prep_row[p0 + tid] + r * rows_per_rhs : -1;
     s_dst[tid] = ok ? dst_off[p0 + tid] : -1;
     s_flg[tid] = ok ? (int)pflags[p0 + tid] : 0;
   }
@@ -181,58 +183,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const uint32_t idesc = instr_desc(N);
   int issued_t = 0, committed = 0;  // tracked by thread 0 only
 
-  // gather of one E stage from the prepared rows: per pair a hi and a lo row of
-  // R2 floats (reflection and split already applied); thread slot q covers
-  // (pair c, k-quad) with the 32 lanes of a warp on 32 consecutive pairs, so
-  // 16-byte loads and conflict-free 16-byte shared stores
-  float4 pre_h[2], pre_l[2];
-  auto gather = [&](int ks) {
+  // gather of one E stage from the prepared rows (reflection and hi/lo split
+  // already applied; per stage a pair's row holds [hi 16 | lo 16]).  Item
+  // bits: pair (3 low bits), quad (2), pair group (4), half hi/lo (1): a warp
+  // covers 8 pairs x 4 quads of one half, i.e. 8 requests of 64 contiguous
+  // bytes, and its 16-byte shared stores fill 4 whole 128-byte lines
+  auto gather = [&](float4(&pre)[4], int ks) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int item = tid + TC_THREADS * q;  // 0..511
-      int quad = item >> 7, c = item & 127;
-      int row = s_src[c];
-      float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
-      if (row >= 0) {
-        const float* rp = prep + (int64_t)row * (2 * R2) + ks * TC_KS + quad * 4;
-        vh = *(const float4*)rp;
-        vl = *(const float4*)(rp + R2);
-      }
-      pre_h[q] = vh;
-      pre_l[q] = vl;
+    for (int q = 0; q < 4; ++q) {
+      const int item = tid + TC_THREADS * q;  // 0..1023
+      const int c = ((item >> 5) & 15) * 8 + (item & 7), quad = (item >> 3) & 3, part = item >> 9;
+      const int row = s_src[c];
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row >= 0) v = *(const float4*)(prep + (int64_t)row * (2 * R2) + ks * (2 * TC_KS) + part * TC_KS + quad * 4);
+      pre[q] = v;
     }
   };
+  // one bulk copy of matrix stage `it` into buffer it & 1 (thread 0)
+  auto issue_t = [&](int it) {
+    const uint32_t bar = smem_u32(&bar_t[it & 1]);
+    unsigned char* sT = smem + (it & 1) * TC_STAGE_BYTES + 2 * TC_EBYTES;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tbytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(sT)),
+                 "l"(Tg + (int64_t)(ks0 + it) * (2 * N * TC_KS)), "r"(tbytes), "r"(bar)
+                 : "memory");
+    ++issued_t;
+  };
   __syncthreads();  // s_src visible
-  gather(ks0);
-
-  for (int ks = ks0; ks < ks1; ++ks) {
-    const int it = ks - ks0;
+  // Pipeline (two smem buffers, stage it in buffer it & 1): the gather runs two
+  // stages ahead in registers (sets pA / pB alternate), and the matrix copy of
+  // stage it + 1 is issued as soon as MMA(it - 1) has released its buffer, so
+  // a copy has a whole stage of MMA work to land behind.
+  const int nstage = ks1 - ks0;
+  float4 pA[4], pB[4];
+  gather(pA, ks0);
+  if (nstage > 1) gather(pB, ks0 + 1);
+  if (tid == 0) issue_t(0);
+  auto body = [&](float4(&cur)[4], int it) -> bool {
     const int st = it & 1;
     unsigned char* sEh = smem + st * TC_STAGE_BYTES;
     unsigned char* sEl = sEh + TC_EBYTES;
     unsigned char* sT = sEl + TC_EBYTES;  // [hi N x 16 | lo N x 16]
-    if (tid == 0 && it >= 2 && !mbar_wait(smem_u32(&bar_m[st]), ((it >> 1) - 1) & 1)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) break;
-    if (tid == 0) {
-      uint32_t bar = smem_u32(&bar_t[st]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tbytes) : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(sT)),
-                   "l"(Tg + (int64_t)ks * (2 * N * TC_KS)), "r"(tbytes), "r"(bar)
-                   : "memory");
-      ++issued_t;
-    }
+    __syncthreads();  // buffer st is free: thread 0 saw MMA(it - 2) complete
+    if (s_abort) return false;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int item = tid + TC_THREADS * q;
-      int quad = item >> 7, c = item & 127;
-      uint32_t o = core_off(c, quad * 4, TC_M);
-      *(float4*)(sEh + o) = pre_h[q];
-      *(float4*)(sEl + o) = pre_l[q];
+    for (int q = 0; q < 4; ++q) {
+      const int item = tid + TC_THREADS * q;
+      const int c = ((item >> 5) & 15) * 8 + (item & 7), quad = (item >> 3) & 3, part = item >> 9;
+      *(float4*)((part ? sEl : sEh) + core_off(c, quad * 4, TC_M)) = cur[q];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ks + 1 < ks1) gather(ks + 1);
+    if (it + 2 < nstage) gather(cur, ks0 + it + 2);
     __syncthreads();
     if (tid == 0) {
       if (!mbar_wait(smem_u32(&bar_t[st]), (it >> 1) & 1)) {
@@ -256,8 +258,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
                          smem_u32(&bar_m[st]))
                      : "memory");
         ++committed;
+        if (it + 1 < nstage) {
+          // buffer st ^ 1 held stage it - 1: wait for its MMAs, then refill it
+          if (it >= 1 && !mbar_wait(smem_u32(&bar_m[st ^ 1]), ((it - 1) >> 1) & 1))
+            s_abort = 1;
+          else
+            issue_t(it + 1);
+        }
       }
     }
+    return true;
+  };
+  for (int it = 0; it < nstage; it += 2) {
+    if (!body(pA, it)) break;
+    if (it + 1 < nstage && !body(pB, it + 1)) break;
   }
   if (tid == 0 && committed > 0) {
     int last = committed - 1;
@@ -308,28 +322,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
 }
 
 // ------------------------------------------------------ source preparation --
-// For every box of the source level and every reflection f (8), a hi and a lo
-// row of R2 floats: row (f * nbox + b) holds s_f(k) M_b[Q_f(k)] as interleaved
-// (re, im), rounded to TF32 (hi) plus the remainder (lo), zero-padded to R2.
-__global__ void k_prep(const float* __restrict__ src, int64_t base, int nbox, int P, int R2, int nrhs_slab,
+// For rhs r0 + rc (rc < nchunk), every box of the source level and every
+// reflection f (8), a row of 2 R2 floats: row ((rc * 8 + f) * nbox + b) holds
+// s_f(k) M_b[Q_f(k)] as interleaved (re, im), zero-padded to R2, rounded to
+// TF32 (hi) plus the remainder (lo), stored per K stage of 16 as
+// [hi 16 | lo 16], so that one stage of one pair is 128 contiguous bytes.
+#define TC_RHS_CHUNK 4  // right-hand sides per translation launch
+
+__global__ void k_prep(const float* __restrict__ src, int64_t base, int nbox, int P, int R2, int r0, int nchunk,
                        int64_t exp_stride, float* __restrict__ out) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t rows = (int64_t)8 * nbox;
-  if (idx >= rows * R2) return;
-  int64_t row = idx / R2;
-  int kr = (int)(idx % R2);
-  int f = (int)(row / nbox), b = (int)(row % nbox);
-  float v = 0.f;
-  if (kr < 2 * P) {
-    int k = kr >> 1, part = kr & 1;
-    bool neg;
-    int ki = reflect_index(k, f, &neg);
-    v = src[2 * ((int64_t)nrhs_slab * exp_stride + base + (int64_t)b * P + ki) + part];
-    if (neg) v = -v;
+  // one thread per 4 consecutive floats of a row (one float4 of hi, one of lo)
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per_rhs = (int64_t)8 * nbox;
+  const int R4 = R2 / 4;
+  if (idx >= nchunk * per_rhs * R4) return;
+  const int64_t row = idx / R4;
+  const int kr0 = 4 * (int)(idx % R4);
+  const int rc = (int)(row / per_rhs);
+  const int f = (int)((row % per_rhs) / nbox), b = (int)(row % nbox);
+  const float* sb = src + 2 * ((int64_t)(r0 + rc) * exp_stride + base + (int64_t)b * P);
+  float v[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int kr = kr0 + e;
+    v[e] = 0.f;
+    if (kr < 2 * P) {
+      bool neg;
+      const int ki = reflect_index(kr >> 1, f, &neg);
+      v[e] = sb[2 * ki + (kr & 1)];
+      if (neg) v[e] = -v[e];
+    }
   }
-  float hi = tf32_round(v);
-  out[row * (2 * (int64_t)R2) + kr] = hi;
-  out[row * (2 * (int64_t)R2) + R2 + kr] = v - hi;
+  float4 hi, lo;
+  hi.x = tf32_round(v[0]);
+  hi.y = tf32_round(v[1]);
+  hi.z = tf32_round(v[2]);
+  hi.w = tf32_round(v[3]);
+  lo = make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+  float* o = out + row * (2 * (int64_t)R2) + (kr0 / TC_KS) * (2 * TC_KS) + (kr0 % TC_KS);
+  *(float4*)o = hi;
+  *(float4*)(o + TC_KS) = lo;
 }
 
 __global__ void k_prep_rows(int np, const int* __restrict__ src_off, const unsigned char* __restrict__ flags,
@@ -348,7 +380,8 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
   op.src_level = src_level;
   {
     LevelInfo& sl = h->lev[src_level];
-    int64_t need = (int64_t)8 * sl.nbox * 2 * prep_stride(sl.P);
+    const int chunk = std::min(h->nrhs_max, TC_RHS_CHUNK);
+    int64_t need = (int64_t)chunk * 8 * sl.nbox * 2 * prep_stride(sl.P);
     if (need > h->prep_len) {
       float* p;
       BEM_TRY(bem_alloc(h, &p, need));  // grows monotonically; older buffers stay in the handle's list
@@ -401,17 +434,18 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   if (op.n_tc_jobs == 0) return BEM_OK;
   LevelInfo& sl = h->lev[op.src_level];
   int R2 = prep_stride(sl.P);
-  for (int r = 0; r < nrhs; ++r) {
-    int64_t n = (int64_t)8 * sl.nbox * R2;
-    k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r,
+  const int chunk = std::min(h->nrhs_max, TC_RHS_CHUNK);
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    // up to `chunk` right-hand sides per launch share each matrix stage via L2
+    const int nc = std::min(chunk, nrhs - r0);
+    const int64_t n = (int64_t)nc * 8 * sl.nbox * (R2 / 4);
+    k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r0, nc,
                                                         h->exp_total, h->prep);
     BEM_CUDA(cudaGetLastError());
-    // one rhs at a time: the prepared buffer holds one source level of one rhs
-    dim3 grid(op.n_tc_jobs, 1);
-    k_grouped_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off,
-                                                   op.tcA, op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, R2,
-                                                   (float*)dst + 2 * (int64_t)r * h->exp_total, h->exp_total,
-                                                   h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, h->d_err);
+    k_grouped_tc<<<op.n_tc_jobs * nc, TC_THREADS, TC_SMEM, s>>>(
+        op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA, op.d_prep_row, op.d_dst_off, op.d_flags,
+        h->prep, R2, nc, 8 * sl.nbox, (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total,
+        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, h->d_err);
     BEM_CUDA(cudaGetLastError());
     *launches += 2;
   }
