@@ -23,9 +23,10 @@
 //   - long K is split across CTAs (outputs are accumulated atomically).
 // In the epilogue every thread owns one pair (its TMEM lane) and adds that
 // pair's outputs to the destination expansion with (re, im) vector atomics,
-// applying the output reflection.  Every wait is bounded: on expiry the CTA
-// records BEM_DEVERR_TIMEOUT, stops issuing work, waits (bounded) for its own
-// copies and MMAs, frees its tensor memory and returns.
+// applying the output reflection.  Every wait is bounded (about one second of
+// SM clocks): on expiry the CTA records BEM_DEVERR_TIMEOUT, stops issuing work,
+// waits (bounded) for its own copies and MMAs, frees its tensor memory and
+// returns.
 #include <algorithm>
 #include <vector>
 
@@ -50,23 +51,26 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(u);
 }
 
+// try_wait suspends the thread in hardware until the phase completes or a
+// system-defined time window passes, so polling it costs no issue slots
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
-// bounded wait: about 2^21 polls with a short sleep (well under a second)
+// bounded wait: gives up after about 2^31 SM clocks (about one second)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 21); ++it) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
     if (mbar_try(bar, parity)) return true;
-    __nanosleep(64);
+    if (clock64() - t0 > (1LL << 31)) return false;
   }
-  return false;
 }
 
 // K-major, no-swizzle shared-memory matrix descriptor: core matrices of
