@@ -293,28 +293,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int c = 32 * (warp & 3) + lane;
     const int dof = s_dst[c], fl = s_flg[c];
     const int half = N >> 1;
-    for (int col0 = (warp >> 2) * half; col0 < (warp >> 2) * half + half; col0 += 8) {
+    const int cbeg = (warp >> 2) * half;
+    const bool mflip = ((fl & 1) != 0) != ((fl & 2) != 0);
+    // output coefficient q = n^2 + n + m, tracked incrementally from the first column
+    int q = (nt * TC_NMAX + cbeg) / 2;
+    int n = (int)sqrtf((float)q);
+    if ((n + 1) * (n + 1) <= q) ++n;
+    if (n * n > q) --n;
+    int m = q - n * n - n;
+    for (int col0 = cbeg; col0 < cbeg + half; col0 += 8) {
       uint32_t v[8];
       uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col0;
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                    : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (dof >= 0) {
+      // the 4 coefficients of this load: destination index (after the output
+      // reflection) and signed value; -1 marks padding rows
+      int qi[4];
+      float re[4], im[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int q = (nt * TC_NMAX + col0) / 2 + e;
-          if (q < Po) {
-            bool neg;
-            int qi = reflect_index(q, fl, &neg);
-            float re = __uint_as_float(v[2 * e]), im = __uint_as_float(v[2 * e + 1]);
-            if (neg) {
-              re = -re;
-              im = -im;
-            }
-            atomicAdd((float2*)(D + 2 * ((int64_t)dof + qi)), make_float2(re, im));
+      for (int e = 0; e < 4; ++e) {
+        const bool neg = ((fl & 1) && (m & 1)) != ((fl & 4) && ((n + m) & 1));
+        qi[e] = (dof >= 0 && q < Po) ? (mflip ? n * n + n - m : q) : -1;
+        re[e] = neg ? -__uint_as_float(v[2 * e]) : __uint_as_float(v[2 * e]);
+        im[e] = neg ? -__uint_as_float(v[2 * e + 1]) : __uint_as_float(v[2 * e + 1]);
+        ++q;
+        if (++m > n) {
+          ++n;
+          m = -n;
+        }
+      }
+      // two coefficients that land next to each other on a 16-byte boundary go
+      // as one float4 atomic, the others as float2 atomics
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (qi[e] < 0) continue;
+        if (e < 3 && qi[e + 1] >= 0 && (qi[e + 1] == qi[e] + 1 || qi[e + 1] == qi[e] - 1)) {
+          const int lo = min(qi[e], qi[e + 1]);
+          float* a = D + 2 * ((int64_t)dof + lo);
+          if (((uintptr_t)a & 15) == 0) {
+            const bool up = qi[e + 1] > qi[e];
+            atomicAdd((float4*)a, up ? make_float4(re[e], im[e], re[e + 1], im[e + 1])
+                                     : make_float4(re[e + 1], im[e + 1], re[e], im[e]));
+            qi[e + 1] = -1;
+            continue;
           }
         }
+        atomicAdd((float2*)(D + 2 * ((int64_t)dof + qi[e])), make_float2(re[e], im[e]));
       }
     }
   } else if (tid == 0) {
