@@ -360,6 +360,64 @@ __global__ void k_p2m(int nleaf, int64_t nt, int P, const int* __restrict__ bsta
   }
 }
 
+// FP32: one thread per coefficient pair (2t, 2t+1) with 16-byte loads of the
+// element rows, elements in rounds of 4 so that their loads are in flight
+// together.  A row [a (P complex) | b (P complex)] starts on a 16-byte
+// boundary; b does too when P is even, otherwise it is read as two float2.
+__global__ void k_p2m_v(int nleaf, int64_t nt, int P, const int* __restrict__ bstart, const int* __restrict__ bend,
+                        const float* __restrict__ rows_ab, const float4* __restrict__ dens, int64_t exp_base,
+                        int64_t exp_stride, float* __restrict__ M) {
+  const int b = blockIdx.x, r = blockIdx.y;
+  const int e0 = 2 * threadIdx.x;
+  if (e0 >= P) return;
+  const bool two = e0 + 1 < P, peven = (P & 1) == 0;
+  const float4* dr = dens + (int64_t)r * nt;
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+  const int j0 = bstart[b], j1 = bend[b];
+  for (int jb = j0; jb < j1; jb += 4) {
+    float4 A[4], B[4], D[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + u;
+      if (j >= j1) {
+        A[u] = B[u] = D[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const float* ab = rows_ab + 4 * (int64_t)j * P;
+      const float* bb = ab + 2 * P;
+      if (two) {
+        A[u] = *(const float4*)(ab + 2 * e0);
+      } else {
+        const float2 a2 = *(const float2*)(ab + 2 * e0);
+        A[u] = make_float4(a2.x, a2.y, 0.f, 0.f);
+      }
+      if (peven) {
+        B[u] = *(const float4*)(bb + 2 * e0);
+      } else {
+        const float2 b0 = *(const float2*)(bb + 2 * e0);
+        const float2 b1 = two ? *(const float2*)(bb + 2 * e0 + 2) : make_float2(0.f, 0.f);
+        B[u] = make_float4(b0.x, b0.y, b1.x, b1.y);
+      }
+      D[u] = dr[j];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 a = A[u], bq = B[u], d = D[u];
+      acc0.x += a.x * d.x - a.y * d.y - bq.x * d.z + bq.y * d.w;
+      acc0.y += a.x * d.y + a.y * d.x - bq.x * d.w - bq.y * d.z;
+      acc1.x += a.z * d.x - a.w * d.y - bq.z * d.z + bq.w * d.w;
+      acc1.y += a.z * d.y + a.w * d.x - bq.z * d.w - bq.w * d.z;
+    }
+  }
+  float* out = M + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P + e0);
+  out[0] = acc0.x;
+  out[1] = acc0.y;
+  if (two) {
+    out[2] = acc1.x;
+    out[3] = acc1.y;
+  }
+}
+
 // -------------------------------------------------------------------- L2P --
 template <typename R>
 __global__ void k_l2p(int64_t nt, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
@@ -372,10 +430,21 @@ __global__ void k_l2p(int64_t nt, int P, const int* __restrict__ leaf_of, const 
   const R* row = rows_r + 2 * (i * P);
   const R* Lb = Lexp + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P);
   R are = 0, aim = 0;
-  for (int e = lane; e < P; e += 32) {
-    R x = row[2 * e], y = row[2 * e + 1], lr = Lb[2 * e], li = Lb[2 * e + 1];
-    are += x * lr - y * li;
-    aim += x * li + y * lr;
+  if (sizeof(R) == 4 && (P & 1) == 0) {
+    // P even: the row starts on a 16-byte boundary, two coefficients per load
+    for (int e2 = lane; 2 * e2 < P; e2 += 32) {
+      const float4 x = *(const float4*)((const float*)row + 4 * e2);
+      const float2 l0 = *(const float2*)((const float*)Lb + 4 * e2);
+      const float2 l1 = *(const float2*)((const float*)Lb + 4 * e2 + 2);
+      are += x.x * l0.x - x.y * l0.y + x.z * l1.x - x.w * l1.y;
+      aim += x.x * l0.y + x.y * l0.x + x.z * l1.y + x.w * l1.x;
+    }
+  } else {
+    for (int e = lane; e < P; e += 32) {
+      R x = row[2 * e], y = row[2 * e + 1], lr = Lb[2 * e], li = Lb[2 * e + 1];
+      are += x * lr - y * li;
+      aim += x * li + y * lr;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     are += __shfl_xor_sync(0xffffffffu, are, o);
@@ -577,8 +646,13 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
   {
     dim3 grid(lf.nbox, nrhs);
-    k_p2m<R><<<grid, 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens, lf.exp_base,
-                                  h->exp_total, (R*)h->Mexp);
+    if constexpr (sizeof(R) == 4)
+      k_p2m_v<<<grid, ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end,
+                                                               (const float*)h->p2m_rows, (const float4*)dens,
+                                                               lf.exp_base, h->exp_total, (float*)h->Mexp);
+    else
+      k_p2m<R><<<grid, 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens, lf.exp_base,
+                                    h->exp_total, (R*)h->Mexp);
     BEM_CUDA(cudaGetLastError());
   }
   bem_prof_end(h, pr, 3, 1, s);
