@@ -216,7 +216,9 @@ int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, c
  *   relres_out : nullable host array [nrhs]; receives the final relative residuals.
  * Orthogonalisation is classical Gram-Schmidt applied twice, in FP64.
  * Returns BEM_ERR_NOT_CONVERGED (with x = last iterate) if max_iter is reached.
- * Synchronises `stream` once per iteration (to read the residual).
+ * Synchronises `stream` once per iteration (to read the residual).  The call
+ * allocates about (min(restart, max_iter) + 4) * nrhs * N * 16 bytes of
+ * stream-ordered scratch for its Krylov basis and frees it before returning.
  */
 #define BEM_GMRES_USE_X0 1
 int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
@@ -254,6 +256,21 @@ int bem_apply_batch(bem_batch* b, int nrhs, int dtype, const void* x, const void
  * problems; problem >= 0: bem_info of that problem's handle.
  */
 int bem_batch_info(bem_batch* b, int problem, int key, int64_t* value);
+
+/*
+ * bem_gmres_solve_batch -- bem_gmres_solve for every problem of a batch at
+ * once: (1/2 I - D_p) x_p = b_p for every problem p and right-hand side.
+ *   rhs, x     : [nrhs][N_total] device buffers in the batch's concatenated
+ *                layout (problem p owns its contiguous segment of each rhs).
+ *   relres_out : nullable host array [nrhs][number of problems].
+ * Every (rhs, problem) segment is its own GMRES system with its own Krylov
+ * space, tolerance test and residual; all of them advance in lockstep, and
+ * each iteration is one bem_apply_batch of the whole batch.  iters_out gets the
+ * lockstep iteration count (the largest over the systems).  Other arguments,
+ * the errors and the scratch are as for bem_gmres_solve with N = N_total.
+ */
+int bem_gmres_solve_batch(bem_batch* b, int nrhs, int dtype, const void* rhs, void* x, double tol, int max_iter,
+                          int restart, int flags, int* iters_out, double* relres_out, void* stream);
 
 /* bem_destroy_batch -- free a batch and every handle in it (NULL accepted). */
 int bem_destroy_batch(bem_batch* b);

@@ -41,7 +41,7 @@ INFO_ORDER_OF_LEVEL = 100
 # every entry point declared in include/bem.h
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
-           "bem_batch_info", "bem_destroy_batch", "bem_last_error")
+           "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error")
 
 
 class BemMesh(ctypes.Structure):
@@ -84,6 +84,8 @@ def load(path: str | None = None):
                              vp]
     lib.bem_gmres_solve.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.bem_gmres_solve_batch.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
+                                          ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
     lib.bem_profile.argtypes = [vp, i]
     lib.bem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i]
@@ -95,7 +97,7 @@ def load(path: str | None = None):
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
-              "bem_apply_batch", "bem_batch_info", "bem_destroy_batch"):
+              "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

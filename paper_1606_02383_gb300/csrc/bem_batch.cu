@@ -242,3 +242,43 @@ extern "C" int bem_batch_info(bem_batch* b, int problem, int key, int64_t* value
   if (problem < 0 || problem >= (int)b->h.size()) return bem_fail(BEM_ERR_INVALID_ARG, "problem index out of range");
   return bem_info(b->h[problem], key, value);
 }
+
+// ------------------------------------------------------------ batch solve --
+// GMRES for every problem and right-hand side of the batch at once: column
+// (r, p) is problem p's segment of right-hand side r in the caller's
+// [nrhs][ntot] layout, and each iteration is one graph-replayed batch apply of
+// (1/2 I - D).  Columns converge independently (each has its own Krylov space).
+namespace {
+struct BatchOp {
+  bem_batch* b;
+  int nrhs;
+};
+int batch_apply(void* ctx, const double* in, double* out, cudaStream_t s) {
+  BatchOp* o = (BatchOp*)ctx;
+  return bem_apply_batch(o->b, o->nrhs, BEM_C128, in, nullptr, out, 0, (void*)s);
+}
+}  // namespace
+
+extern "C" int bem_gmres_solve_batch(bem_batch* b, int nrhs, int dtype, const void* rhs, void* x, double tol,
+                                     int max_iter, int restart, int flags, int* iters_out, double* relres_out,
+                                     void* stream) {
+  bem_set_error("");
+  if (!b) return bem_fail(BEM_ERR_INVALID_ARG, "batch is NULL");
+  if (nrhs < 1 || nrhs > b->nrhs_max) return bem_fail(BEM_ERR_INVALID_ARG, "nrhs out of [1, max_nrhs]");
+  if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
+  if (!rhs || !x) return bem_fail(BEM_ERR_INVALID_ARG, "rhs and x are required");
+  if (!(tol > 0.0) || max_iter < 1 || restart < 1)
+    return bem_fail(BEM_ERR_INVALID_ARG, "tol must be > 0, max_iter and restart >= 1");
+  if (flags & ~BEM_GMRES_USE_X0) return bem_fail(BEM_ERR_INVALID_ARG, "flags: only BEM_GMRES_USE_X0");
+  const int np = (int)b->h.size();
+  const int ncol = nrhs * np;
+  std::vector<int64_t> off(ncol), len(ncol);
+  for (int r = 0; r < nrhs; ++r)
+    for (int p = 0; p < np; ++p) {
+      off[r * np + p] = (int64_t)r * b->ntot + b->off[p];
+      len[r * np + p] = b->off[p + 1] - b->off[p];
+    }
+  BatchOp ctx{b, nrhs};
+  return bem_gmres_core(batch_apply, &ctx, ncol, (int64_t)nrhs * b->ntot, off.data(), len.data(), dtype, rhs, x, tol,
+                        max_iter, restart, flags, iters_out, relres_out, (cudaStream_t)stream);
+}

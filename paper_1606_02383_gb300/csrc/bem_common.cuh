@@ -250,13 +250,6 @@ struct bem_handle {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   int launches_last_apply = 0;  // kernels launched by the last bem_apply
-  // GMRES workspace (allocated on first use)
-  int gm_restart = 0;
-  int gm_nrhs = 0;
-  double* gm_V = nullptr;
-  double* gm_w = nullptr;
-  double* gm_dots = nullptr;
-  double* gm_norms = nullptr;
 };
 
 int bem_prof_begin(bem_handle* h, cudaStream_t s);                      // returns a record index or -1
@@ -298,6 +291,13 @@ int bem_epilogue(bem_handle* h, int nrhs, int dtype, const void* x, void* z, int
 int bem_adjoint_prologue(bem_handle* h, int nrhs, int dtype, const void* g, cudaStream_t s);
 int bem_adjoint_epilogue(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
                          cudaStream_t s);
+// apply callback of the GMRES core: out = A in, both block vectors of complex FP64
+typedef int (*bem_gm_apply_fn)(void* ctx, const double* in, double* out, cudaStream_t s);
+// restarted GMRES on ncol independent systems in lockstep; column c is the
+// segment [off[c], off[c] + len[c]) of a block vector of M complex entries
+int bem_gmres_core(bem_gm_apply_fn apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
+                   int dtype, const void* b, void* x, double tol, int max_iter, int restart, int flags,
+                   int* iters_out, double* relres_out, cudaStream_t s);
 int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
               int flags, int* iters_out, double* relres_out, cudaStream_t s);
 int bem_check_device_error(bem_handle* h, cudaStream_t s);

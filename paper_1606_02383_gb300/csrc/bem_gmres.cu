@@ -1,11 +1,14 @@
 // bem_gmres.cu -- restarted GMRES for (1/2 I - D) x = b (Section 2.3, Eq. (GMRES)
 // without the FEM coupling term; Section 3: GMRES with a relative tolerance).
 //
-// All right-hand sides run in lockstep so every iteration makes one multi-rhs
-// operator apply.  Krylov vectors, dot products and updates are FP64 on the
-// device; orthogonalisation is classical Gram-Schmidt applied twice (CGS2).
-// The small Hessenberg least-squares problem (Givens rotations) is solved on
-// the host, which reads j+2 coefficients per rhs after every iteration.
+// The core solves `ncol` independent systems in lockstep: column c is the
+// complex segment [off[c], off[c] + len[c]) of one block vector of length M,
+// and every iteration makes one apply of the whole block (a multi-rhs apply of
+// one operator, or one batch apply of many operators).  Krylov vectors, dot
+// products and updates are FP64 on the device; orthogonalisation is classical
+// Gram-Schmidt applied twice (CGS2).  The small Hessenberg least-squares
+// problem (Givens rotations) of every column is solved on the host, which reads
+// j+2 coefficients per column after every iteration.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -18,14 +21,24 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 
 #define GM_CHUNKS 128
 
-// partial[(r*(nv) + i)*GM_CHUNKS + chunk] = sum over the chunk of conj(V_i[r]) w[r]
-__global__ void k_gm_dots(int64_t n, int nv, int nrhs, const double* __restrict__ V, int64_t vstride,
-                          const double* __restrict__ w, double* partial) {
-  int chunk = blockIdx.x, i = blockIdx.y, r = blockIdx.z;
+// colof[off[c] + e] = c for every element of every column
+__global__ void k_gm_colof(const int64_t* __restrict__ off, const int64_t* __restrict__ len, int* colof) {
+  const int c = blockIdx.y;
+  const int64_t n = len[c], o = off[c];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    colof[o + e] = c;
+}
+
+// partial[(c*nv + i)*GM_CHUNKS + chunk] = sum over the chunk of conj(V_i[c]) w[c]
+__global__ void k_gm_dots(int nv, const int64_t* __restrict__ off, const int64_t* __restrict__ len,
+                          const double* __restrict__ V, int64_t vstride, const double* __restrict__ w,
+                          double* partial) {
+  int chunk = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
+  const int64_t n = len[c];
   int64_t per = (n + GM_CHUNKS - 1) / GM_CHUNKS;
   int64_t a = chunk * per, b = min(n, a + per);
-  const double* v = V + i * vstride + 2 * (int64_t)r * n;
-  const double* ww = w + 2 * (int64_t)r * n;
+  const double* v = V + i * vstride + 2 * off[c];
+  const double* ww = w + 2 * off[c];
   double sre = 0.0, sim = 0.0;
   for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
     double vr = v[2 * e], vi = v[2 * e + 1], wr = ww[2 * e], wi = ww[2 * e + 1];
@@ -44,72 +57,67 @@ __global__ void k_gm_dots(int64_t n, int nv, int nrhs, const double* __restrict_
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    int64_t o = ((int64_t)r * nv + i) * GM_CHUNKS + chunk;
+    int64_t o = ((int64_t)c * nv + i) * GM_CHUNKS + chunk;
     partial[2 * o] = sh[0][0];
     partial[2 * o + 1] = sh[1][0];
   }
 }
 
-// out[r*nv + i] (+)= sum over chunks
-__global__ void k_gm_reduce(int nv, int nrhs, const double* __restrict__ partial, double* out, int accumulate) {
+// out[c*nv + i] = sum over chunks
+__global__ void k_gm_reduce(int nv, int ncol, const double* __restrict__ partial, double* out) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nv * nrhs) return;
+  if (t >= nv * ncol) return;
   double sre = 0.0, sim = 0.0;
   for (int c = 0; c < GM_CHUNKS; ++c) {
     sre += partial[2 * ((int64_t)t * GM_CHUNKS + c)];
     sim += partial[2 * ((int64_t)t * GM_CHUNKS + c) + 1];
   }
-  if (accumulate) {
-    out[2 * t] += sre;
-    out[2 * t + 1] += sim;
-  } else {
-    out[2 * t] = sre;
-    out[2 * t + 1] = sim;
-  }
+  out[2 * t] = sre;
+  out[2 * t + 1] = sim;
 }
 
-// w[r] -= sum_i coef[r*nv + i] V_i[r]   (coef from the latest dot round)
-__global__ void k_gm_orth(int64_t n, int nv, int nrhs, const double* __restrict__ V, int64_t vstride,
-                          const double* __restrict__ coef, double* w) {
+// w -= sum_i coef[c*nv + i] V_i   on every element e of column c = colof[e]
+__global__ void k_gm_orth(int64_t M, int nv, const int* __restrict__ colof, const double* __restrict__ V,
+                          int64_t vstride, const double* __restrict__ coef, double* w) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
-  if (e >= n) return;
-  double wr = w[2 * ((int64_t)r * n + e)], wi = w[2 * ((int64_t)r * n + e) + 1];
+  if (e >= M) return;
+  const int c = colof[e];
+  double wr = w[2 * e], wi = w[2 * e + 1];
   for (int i = 0; i < nv; ++i) {
-    double cr = coef[2 * (r * nv + i)], ci = coef[2 * (r * nv + i) + 1];
-    const double* v = V + i * vstride + 2 * ((int64_t)r * n + e);
+    double cr = coef[2 * (c * nv + i)], ci = coef[2 * (c * nv + i) + 1];
+    const double* v = V + i * vstride + 2 * e;
     wr -= cr * v[0] - ci * v[1];
     wi -= cr * v[1] + ci * v[0];
   }
-  w[2 * ((int64_t)r * n + e)] = wr;
-  w[2 * ((int64_t)r * n + e) + 1] = wi;
+  w[2 * e] = wr;
+  w[2 * e + 1] = wi;
 }
 
-// dst[r] = src[r] * scale[r] (complex src, real scale)
-__global__ void k_gm_scale(int64_t n, const double* __restrict__ src, const double* __restrict__ scale, double* dst) {
+// dst = src * scale[column] (complex src, real scale)
+__global__ void k_gm_scale(int64_t M, const int* __restrict__ colof, const double* __restrict__ src,
+                           const double* __restrict__ scale, double* dst) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
-  if (e >= n) return;
-  double s = scale[r];
-  dst[2 * ((int64_t)r * n + e)] = src[2 * ((int64_t)r * n + e)] * s;
-  dst[2 * ((int64_t)r * n + e) + 1] = src[2 * ((int64_t)r * n + e) + 1] * s;
+  if (e >= M) return;
+  double s = scale[colof[e]];
+  dst[2 * e] = src[2 * e] * s;
+  dst[2 * e + 1] = src[2 * e + 1] * s;
 }
 
-// x[r] += sum_i y[r][i] V_i[r]
-__global__ void k_gm_update_x(int64_t n, int nv, const double* __restrict__ V, int64_t vstride,
-                              const double* __restrict__ y, double* x) {
+// x += sum_i y[c][i] V_i
+__global__ void k_gm_update_x(int64_t M, int nv, const int* __restrict__ colof, const double* __restrict__ V,
+                              int64_t vstride, const double* __restrict__ y, double* x) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
-  if (e >= n) return;
-  double xr = x[2 * ((int64_t)r * n + e)], xi = x[2 * ((int64_t)r * n + e) + 1];
+  if (e >= M) return;
+  const int c = colof[e];
+  double xr = x[2 * e], xi = x[2 * e + 1];
   for (int i = 0; i < nv; ++i) {
-    double yr = y[2 * (r * nv + i)], yi = y[2 * (r * nv + i) + 1];
-    const double* v = V + i * vstride + 2 * ((int64_t)r * n + e);
+    double yr = y[2 * (c * nv + i)], yi = y[2 * (c * nv + i) + 1];
+    const double* v = V + i * vstride + 2 * e;
     xr += yr * v[0] - yi * v[1];
     xi += yr * v[1] + yi * v[0];
   }
-  x[2 * ((int64_t)r * n + e)] = xr;
-  x[2 * ((int64_t)r * n + e) + 1] = xi;
+  x[2 * e] = xr;
+  x[2 * e + 1] = xi;
 }
 
 // r = b - z  (all complex double)
@@ -128,165 +136,184 @@ __global__ void k_c128_to_c64(int64_t m, const double* __restrict__ a, float* b)
   if (e < m) b[e] = (float)a[e];
 }
 
-struct Gm {
-  bem_handle* h;
-  int nrhs;
-  int64_t n;
+namespace {
+
+// stream-ordered scratch of one solve, released on every return path
+struct GmScratch {
   cudaStream_t s;
-  double *V, *w, *partial, *coef, *coef2, *nrm, *scale, *y, *tmp;
-  int64_t vstride;
+  std::vector<void*> p;
+  ~GmScratch() {
+    for (void* q : p) cudaFreeAsync(q, s);
+  }
+  template <typename T>
+  int get(T** out, size_t count) {
+    void* q = nullptr;
+    BEM_CUDA(cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s));
+    p.push_back(q);
+    *out = (T*)q;
+    return BEM_OK;
+  }
 };
 
-static int gm_apply(Gm& g, const double* in, double* out) {
-  BEM_TRY(bem_prologue(g.h, g.nrhs, BEM_C128, in, nullptr, g.s));
-  BEM_TRY(bem_apply_sorted(g.h, g.nrhs, g.s));
-  BEM_TRY(bem_epilogue(g.h, g.nrhs, BEM_C128, in, out, 1, g.s));
-  return BEM_OK;
-}
+struct GmCore {
+  bem_gm_apply_fn apply;
+  void* ctx;
+  int ncol;
+  int64_t M;
+  cudaStream_t s;
+  double *V, *w, *bb, *xx, *partial, *coef, *coef2, *y, *nrm, *scale;
+  int64_t vstride;
+  int64_t *d_off, *d_len;
+  int* colof;
+};
 
-// squared norms of the nrhs vectors in `w` into host array
-static int gm_norms(Gm& g, const double* w, std::vector<double>& out) {
-  dim3 grid(GM_CHUNKS, 1, g.nrhs);
-  k_gm_dots<<<grid, 256, 0, g.s>>>(g.n, 1, g.nrhs, w, 0, w, g.partial);
-  k_gm_reduce<<<nblk(g.nrhs, 128), 128, 0, g.s>>>(1, g.nrhs, g.partial, g.nrm, 0);
-  std::vector<double> t(2 * g.nrhs);
-  BEM_CUDA(cudaMemcpyAsync(t.data(), g.nrm, 2 * g.nrhs * sizeof(double), cudaMemcpyDeviceToHost, g.s));
+// norms of the ncol columns of `w` into a host array (synchronises)
+int gm_norms(GmCore& g, const double* w, std::vector<double>& out) {
+  dim3 grid(GM_CHUNKS, 1, g.ncol);
+  k_gm_dots<<<grid, 256, 0, g.s>>>(1, g.d_off, g.d_len, w, 0, w, g.partial);
+  k_gm_reduce<<<nblk(g.ncol, 128), 128, 0, g.s>>>(1, g.ncol, g.partial, g.nrm);
+  std::vector<double> t(2 * (size_t)g.ncol);
+  BEM_CUDA(cudaMemcpyAsync(t.data(), g.nrm, t.size() * sizeof(double), cudaMemcpyDeviceToHost, g.s));
   BEM_CUDA(cudaStreamSynchronize(g.s));
-  out.resize(g.nrhs);
-  for (int r = 0; r < g.nrhs; ++r) out[r] = std::sqrt(std::max(0.0, t[2 * r]));
+  out.resize(g.ncol);
+  for (int c = 0; c < g.ncol; ++c) out[c] = std::sqrt(std::max(0.0, t[2 * c]));
   return BEM_OK;
 }
 
-int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out, double tol, int max_iter,
-              int restart, int flags, int* iters_out, double* relres_out, cudaStream_t s) {
-  int64_t n = h->nt;
-  int m = std::min(restart, max_iter);
-  Gm g;
-  g.h = h;
-  g.nrhs = nrhs;
-  g.n = n;
+}  // namespace
+
+int bem_gmres_core(bem_gm_apply_fn apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
+                   int dtype, const void* b_in, void* x_out, double tol, int max_iter, int restart, int flags,
+                   int* iters_out, double* relres_out, cudaStream_t s) {
+  const int m = std::max(1, std::min(restart, max_iter));
+  GmScratch sc_{s, {}};
+  GmCore g;
+  g.apply = apply;
+  g.ctx = ctx;
+  g.ncol = ncol;
+  g.M = M;
   g.s = s;
-  // workspace (re)allocation
-  if (!h->gm_V || h->gm_restart < m || h->gm_nrhs < nrhs) {
-    BEM_TRY(bem_alloc(h, &h->gm_V, (size_t)(m + 1) * nrhs * n * 2));
-    BEM_TRY(bem_alloc(h, &h->gm_w, (size_t)nrhs * n * 2 * 3));
-    BEM_TRY(bem_alloc(h, &h->gm_dots, (size_t)nrhs * (m + 1) * GM_CHUNKS * 2 + 4 * (size_t)nrhs * (m + 1) * 2 + 2 * nrhs));
-    h->gm_restart = m;
-    h->gm_nrhs = nrhs;
-  }
-  g.vstride = (int64_t)nrhs * n * 2;
-  g.V = h->gm_V;
-  g.w = h->gm_w;
-  double* bb = h->gm_w + (size_t)nrhs * n * 2;      // b in C128
-  double* xx = bb + (size_t)nrhs * n * 2;           // x in C128
-  g.partial = h->gm_dots;
-  g.coef = g.partial + (size_t)nrhs * (m + 1) * GM_CHUNKS * 2;
-  g.coef2 = g.coef + (size_t)nrhs * (m + 1) * 2;
-  g.y = g.coef2 + (size_t)nrhs * (m + 1) * 2;
-  g.nrm = g.y + (size_t)nrhs * (m + 1) * 2;
-  g.scale = g.nrm + (size_t)nrhs * (m + 1) * 2;
-  int64_t tot = 2 * (int64_t)nrhs * n;
+  g.vstride = 2 * M;
+  BEM_TRY(sc_.get(&g.V, (size_t)(m + 1) * 2 * M));
+  BEM_TRY(sc_.get(&g.w, 2 * (size_t)M));
+  BEM_TRY(sc_.get(&g.bb, 2 * (size_t)M));
+  BEM_TRY(sc_.get(&g.xx, 2 * (size_t)M));
+  BEM_TRY(sc_.get(&g.partial, (size_t)ncol * (m + 1) * GM_CHUNKS * 2));
+  BEM_TRY(sc_.get(&g.coef, (size_t)ncol * (m + 1) * 2));
+  BEM_TRY(sc_.get(&g.coef2, (size_t)ncol * (m + 1) * 2));
+  BEM_TRY(sc_.get(&g.y, (size_t)ncol * (m + 1) * 2));
+  BEM_TRY(sc_.get(&g.nrm, (size_t)ncol * 2));
+  BEM_TRY(sc_.get(&g.scale, (size_t)ncol));
+  BEM_TRY(sc_.get(&g.d_off, (size_t)ncol));
+  BEM_TRY(sc_.get(&g.d_len, (size_t)ncol));
+  BEM_TRY(sc_.get(&g.colof, (size_t)M));
+  BEM_CUDA(cudaMemcpyAsync(g.d_off, off, ncol * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(g.d_len, len, ncol * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  k_gm_colof<<<dim3(64, ncol), 256, 0, s>>>(g.d_off, g.d_len, g.colof);
+  const int64_t tot = 2 * M;
   if (dtype == BEM_C128) {
-    BEM_CUDA(cudaMemcpyAsync(bb, b_in, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (flags & BEM_GMRES_USE_X0) BEM_CUDA(cudaMemcpyAsync(xx, x_out, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(g.bb, b_in, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (flags & BEM_GMRES_USE_X0)
+      BEM_CUDA(cudaMemcpyAsync(g.xx, x_out, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
-    k_c64_to_c128<<<nblk(tot, 256), 256, 0, s>>>(tot, (const float*)b_in, bb);
-    if (flags & BEM_GMRES_USE_X0) k_c64_to_c128<<<nblk(tot, 256), 256, 0, s>>>(tot, (const float*)x_out, xx);
+    k_c64_to_c128<<<nblk(tot, 256), 256, 0, s>>>(tot, (const float*)b_in, g.bb);
+    if (flags & BEM_GMRES_USE_X0) k_c64_to_c128<<<nblk(tot, 256), 256, 0, s>>>(tot, (const float*)x_out, g.xx);
   }
-  if (!(flags & BEM_GMRES_USE_X0)) BEM_CUDA(cudaMemsetAsync(xx, 0, tot * sizeof(double), s));
+  if (!(flags & BEM_GMRES_USE_X0)) BEM_CUDA(cudaMemsetAsync(g.xx, 0, tot * sizeof(double), s));
+  BEM_CUDA(cudaGetLastError());
 
   std::vector<double> bnorm;
-  BEM_TRY(gm_norms(g, bb, bnorm));
-  std::vector<double> relres(nrhs, 1.0);
+  BEM_TRY(gm_norms(g, g.bb, bnorm));
+  std::vector<double> relres(ncol, 1.0);
   int it_total = 0;
   bool all_conv = false;
-  dim3 gvec(nblk(n, 256), nrhs);
+  const unsigned gvec = nblk(M, 256);
   while (it_total < max_iter && !all_conv) {
     // r0 = b - A x
-    BEM_TRY(gm_apply(g, xx, g.w));
-    k_gm_sub<<<nblk(tot, 256), 256, 0, s>>>(tot, bb, g.w, g.w);
+    BEM_TRY(g.apply(g.ctx, g.xx, g.w, s));
+    k_gm_sub<<<nblk(tot, 256), 256, 0, s>>>(tot, g.bb, g.w, g.w);
     std::vector<double> beta;
     BEM_TRY(gm_norms(g, g.w, beta));
-    std::vector<double> sc(nrhs);
-    std::vector<bool> active(nrhs);
+    std::vector<double> sc(ncol);
+    std::vector<bool> active(ncol);
     all_conv = true;
-    for (int r = 0; r < nrhs; ++r) {
-      double bn = bnorm[r] > 0 ? bnorm[r] : 1.0;
-      relres[r] = beta[r] / bn;
-      active[r] = relres[r] > tol && beta[r] > 0.0;
-      if (active[r]) all_conv = false;
-      sc[r] = active[r] ? 1.0 / beta[r] : 0.0;
+    for (int c = 0; c < ncol; ++c) {
+      double bn = bnorm[c] > 0 ? bnorm[c] : 1.0;
+      relres[c] = beta[c] / bn;
+      active[c] = relres[c] > tol && beta[c] > 0.0;
+      if (active[c]) all_conv = false;
+      sc[c] = active[c] ? 1.0 / beta[c] : 0.0;
     }
     if (all_conv) break;
-    BEM_CUDA(cudaMemcpyAsync(g.scale, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-    k_gm_scale<<<gvec, 256, 0, s>>>(n, g.w, g.scale, g.V);
-    // per-rhs small problem
-    std::vector<std::vector<hz>> H(nrhs, std::vector<hz>((size_t)(m + 1) * m, 0.0));
-    std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m, 0.0));
-    std::vector<std::vector<hz>> sn(nrhs, std::vector<hz>(m, 0.0));
-    std::vector<std::vector<hz>> gg(nrhs, std::vector<hz>(m + 1, 0.0));
-    std::vector<int> ncols(nrhs, 0);
-    for (int r = 0; r < nrhs; ++r) gg[r][0] = beta[r];
+    BEM_CUDA(cudaMemcpyAsync(g.scale, sc.data(), ncol * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_gm_scale<<<gvec, 256, 0, s>>>(M, g.colof, g.w, g.scale, g.V);
+    // per-column small problem
+    std::vector<std::vector<hz>> H(ncol, std::vector<hz>((size_t)(m + 1) * m, 0.0));
+    std::vector<std::vector<double>> cs(ncol, std::vector<double>(m, 0.0));
+    std::vector<std::vector<hz>> sn(ncol, std::vector<hz>(m, 0.0));
+    std::vector<std::vector<hz>> gg(ncol, std::vector<hz>(m + 1, 0.0));
+    std::vector<int> ncols(ncol, 0);
+    for (int c = 0; c < ncol; ++c) gg[c][0] = beta[c];
     int j = 0;
     for (; j < m && it_total < max_iter; ++j) {
       double* vj = g.V + j * g.vstride;
-      BEM_TRY(gm_apply(g, vj, g.w));
+      BEM_TRY(g.apply(g.ctx, vj, g.w, s));
       int nv = j + 1;
       // CGS2
-      dim3 gd(GM_CHUNKS, nv, nrhs);
-      k_gm_dots<<<gd, 256, 0, s>>>(n, nv, nrhs, g.V, g.vstride, g.w, g.partial);
-      k_gm_reduce<<<nblk(nv * nrhs, 128), 128, 0, s>>>(nv, nrhs, g.partial, g.coef, 0);
-      k_gm_orth<<<gvec, 256, 0, s>>>(n, nv, nrhs, g.V, g.vstride, g.coef, g.w);
-      k_gm_dots<<<gd, 256, 0, s>>>(n, nv, nrhs, g.V, g.vstride, g.w, g.partial);
-      k_gm_reduce<<<nblk(nv * nrhs, 128), 128, 0, s>>>(nv, nrhs, g.partial, g.coef2, 0);
-      k_gm_orth<<<gvec, 256, 0, s>>>(n, nv, nrhs, g.V, g.vstride, g.coef2, g.w);
+      dim3 gd(GM_CHUNKS, nv, ncol);
+      k_gm_dots<<<gd, 256, 0, s>>>(nv, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
+      k_gm_reduce<<<nblk(nv * ncol, 128), 128, 0, s>>>(nv, ncol, g.partial, g.coef);
+      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, g.colof, g.V, g.vstride, g.coef, g.w);
+      k_gm_dots<<<gd, 256, 0, s>>>(nv, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
+      k_gm_reduce<<<nblk(nv * ncol, 128), 128, 0, s>>>(nv, ncol, g.partial, g.coef2);
+      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, g.colof, g.V, g.vstride, g.coef2, g.w);
       BEM_CUDA(cudaGetLastError());
-      std::vector<double> hc(2 * nv * nrhs), hc2(2 * nv * nrhs);
+      std::vector<double> hc(2 * (size_t)nv * ncol), hc2(2 * (size_t)nv * ncol);
       BEM_CUDA(cudaMemcpyAsync(hc.data(), g.coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       BEM_CUDA(cudaMemcpyAsync(hc2.data(), g.coef2, hc2.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       std::vector<double> wn;
       BEM_TRY(gm_norms(g, g.w, wn));  // synchronises
       ++it_total;
       bool any = false;
-      for (int r = 0; r < nrhs; ++r) {
-        if (!active[r]) {
-          sc[r] = 0.0;
+      for (int c = 0; c < ncol; ++c) {
+        if (!active[c]) {
+          sc[c] = 0.0;
           continue;
         }
-        std::vector<hz>& Hr = H[r];
+        std::vector<hz>& Hc = H[c];
         for (int i = 0; i < nv; ++i)
-          Hr[(size_t)i * m + j] = hz(hc[2 * (r * nv + i)] + hc2[2 * (r * nv + i)],
-                                     hc[2 * (r * nv + i) + 1] + hc2[2 * (r * nv + i) + 1]);
-        double hn = wn[r];
-        Hr[(size_t)(j + 1) * m + j] = hn;
+          Hc[(size_t)i * m + j] = hz(hc[2 * (c * nv + i)] + hc2[2 * (c * nv + i)],
+                                     hc[2 * (c * nv + i) + 1] + hc2[2 * (c * nv + i) + 1]);
+        double hn = wn[c];
+        Hc[(size_t)(j + 1) * m + j] = hn;
         for (int i = 0; i < j; ++i) {  // previous rotations
-          hz a = Hr[(size_t)i * m + j], bq = Hr[(size_t)(i + 1) * m + j];
-          Hr[(size_t)i * m + j] = cs[r][i] * a + sn[r][i] * bq;
-          Hr[(size_t)(i + 1) * m + j] = -std::conj(sn[r][i]) * a + cs[r][i] * bq;
+          hz a = Hc[(size_t)i * m + j], bq = Hc[(size_t)(i + 1) * m + j];
+          Hc[(size_t)i * m + j] = cs[c][i] * a + sn[c][i] * bq;
+          Hc[(size_t)(i + 1) * m + j] = -std::conj(sn[c][i]) * a + cs[c][i] * bq;
         }
-        hz a = Hr[(size_t)j * m + j];
-        double bq = std::abs(Hr[(size_t)(j + 1) * m + j]);
+        hz a = Hc[(size_t)j * m + j];
+        double bq = std::abs(Hc[(size_t)(j + 1) * m + j]);
         double rho = std::hypot(std::abs(a), bq);
         if (std::abs(a) == 0.0) {
-          cs[r][j] = 0.0;
-          sn[r][j] = 1.0;
+          cs[c][j] = 0.0;
+          sn[c][j] = 1.0;
         } else {
-          cs[r][j] = std::abs(a) / rho;
-          sn[r][j] = (a / std::abs(a)) * bq / rho;
+          cs[c][j] = std::abs(a) / rho;
+          sn[c][j] = (a / std::abs(a)) * bq / rho;
         }
-        Hr[(size_t)j * m + j] = cs[r][j] * a + sn[r][j] * bq;
-        Hr[(size_t)(j + 1) * m + j] = 0.0;
-        gg[r][j + 1] = -std::conj(sn[r][j]) * gg[r][j];
-        gg[r][j] = cs[r][j] * gg[r][j];
-        ncols[r] = j + 1;
-        double bn = bnorm[r] > 0 ? bnorm[r] : 1.0;
-        relres[r] = std::abs(gg[r][j + 1]) / bn;
-        bool breakdown = !(hn > 1e-14 * std::abs(Hr[(size_t)j * m + j]));
-        if (relres[r] <= tol || breakdown) {
-          active[r] = false;
-          sc[r] = 0.0;
+        Hc[(size_t)j * m + j] = cs[c][j] * a + sn[c][j] * bq;
+        Hc[(size_t)(j + 1) * m + j] = 0.0;
+        gg[c][j + 1] = -std::conj(sn[c][j]) * gg[c][j];
+        gg[c][j] = cs[c][j] * gg[c][j];
+        ncols[c] = j + 1;
+        double bn = bnorm[c] > 0 ? bnorm[c] : 1.0;
+        relres[c] = std::abs(gg[c][j + 1]) / bn;
+        bool breakdown = !(hn > 1e-14 * std::abs(Hc[(size_t)j * m + j]));
+        if (relres[c] <= tol || breakdown) {
+          active[c] = false;
+          sc[c] = 0.0;
         } else {
-          sc[r] = 1.0 / hn;
+          sc[c] = 1.0 / hn;
           any = true;
         }
       }
@@ -294,45 +321,70 @@ int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out,
         ++j;
         break;
       }
-      BEM_CUDA(cudaMemcpyAsync(g.scale, sc.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
-      k_gm_scale<<<gvec, 256, 0, s>>>(n, g.w, g.scale, g.V + (j + 1) * g.vstride);
+      BEM_CUDA(cudaMemcpyAsync(g.scale, sc.data(), ncol * sizeof(double), cudaMemcpyHostToDevice, s));
+      k_gm_scale<<<gvec, 256, 0, s>>>(M, g.colof, g.w, g.scale, g.V + (j + 1) * g.vstride);
     }
     // solve the triangular systems and update x
     int nvmax = 0;
-    for (int r = 0; r < nrhs; ++r) nvmax = std::max(nvmax, ncols[r]);
+    for (int c = 0; c < ncol; ++c) nvmax = std::max(nvmax, ncols[c]);
     if (nvmax > 0) {
-      std::vector<double> yv(2 * (size_t)nrhs * nvmax, 0.0);
-      for (int r = 0; r < nrhs; ++r) {
-        int k = ncols[r];
+      std::vector<double> yv(2 * (size_t)ncol * nvmax, 0.0);
+      for (int c = 0; c < ncol; ++c) {
+        int k = ncols[c];
         std::vector<hz> yy(k);
         for (int i = k - 1; i >= 0; --i) {
-          hz acc = gg[r][i];
-          for (int q = i + 1; q < k; ++q) acc -= H[r][(size_t)i * m + q] * yy[q];
-          yy[i] = acc / H[r][(size_t)i * m + i];
+          hz acc = gg[c][i];
+          for (int q = i + 1; q < k; ++q) acc -= H[c][(size_t)i * m + q] * yy[q];
+          yy[i] = acc / H[c][(size_t)i * m + i];
         }
         for (int i = 0; i < k; ++i) {
-          yv[2 * (r * nvmax + i)] = yy[i].real();
-          yv[2 * (r * nvmax + i) + 1] = yy[i].imag();
+          yv[2 * (c * nvmax + i)] = yy[i].real();
+          yv[2 * (c * nvmax + i) + 1] = yy[i].imag();
         }
       }
       BEM_CUDA(cudaMemcpyAsync(g.y, yv.data(), yv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      k_gm_update_x<<<gvec, 256, 0, s>>>(n, nvmax, g.V, g.vstride, g.y, xx);
+      k_gm_update_x<<<gvec, 256, 0, s>>>(M, nvmax, g.colof, g.V, g.vstride, g.y, g.xx);
       BEM_CUDA(cudaGetLastError());
       BEM_CUDA(cudaStreamSynchronize(s));
     }
     all_conv = true;
-    for (int r = 0; r < nrhs; ++r)
-      if (relres[r] > tol) all_conv = false;
+    for (int c = 0; c < ncol; ++c)
+      if (relres[c] > tol) all_conv = false;
   }
   if (dtype == BEM_C128)
-    BEM_CUDA(cudaMemcpyAsync(x_out, xx, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(x_out, g.xx, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
   else
-    k_c128_to_c64<<<nblk(tot, 256), 256, 0, s>>>(tot, xx, (float*)x_out);
+    k_c128_to_c64<<<nblk(tot, 256), 256, 0, s>>>(tot, g.xx, (float*)x_out);
   BEM_CUDA(cudaStreamSynchronize(s));
   if (iters_out) *iters_out = it_total;
   if (relres_out)
-    for (int r = 0; r < nrhs; ++r) relres_out[r] = relres[r];
-  for (int r = 0; r < nrhs; ++r)
-    if (!(relres[r] <= tol)) return bem_fail(BEM_ERR_NOT_CONVERGED, "GMRES reached max_iter before tol");
+    for (int c = 0; c < ncol; ++c) relres_out[c] = relres[c];
+  for (int c = 0; c < ncol; ++c)
+    if (!(relres[c] <= tol)) return bem_fail(BEM_ERR_NOT_CONVERGED, "GMRES reached max_iter before tol");
   return BEM_OK;
+}
+
+// ---------------------------------------------------------- one operator --
+namespace {
+struct OneOp {
+  bem_handle* h;
+  int nrhs;
+};
+int one_op_apply(void* ctx, const double* in, double* out, cudaStream_t s) {
+  OneOp* o = (OneOp*)ctx;
+  BEM_TRY(bem_prologue(o->h, o->nrhs, BEM_C128, in, nullptr, s));
+  BEM_TRY(bem_apply_sorted(o->h, o->nrhs, s));
+  BEM_TRY(bem_epilogue(o->h, o->nrhs, BEM_C128, in, out, 1, s));
+  return BEM_OK;
+}
+}  // namespace
+
+// the nrhs right-hand sides of one operator: column r is [r N, (r + 1) N)
+int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out, double tol, int max_iter,
+              int restart, int flags, int* iters_out, double* relres_out, cudaStream_t s) {
+  std::vector<int64_t> off(nrhs), len(nrhs, h->nt);
+  for (int r = 0; r < nrhs; ++r) off[r] = (int64_t)r * h->nt;
+  OneOp ctx{h, nrhs};
+  return bem_gmres_core(one_op_apply, &ctx, nrhs, (int64_t)nrhs * h->nt, off.data(), len.data(), dtype, b_in, x_out,
+                        tol, max_iter, restart, flags, iters_out, relres_out, s);
 }

@@ -274,3 +274,20 @@ class Batch:
                                              None if ys is None else ys.data_ptr(), z.data_ptr(),
                                              _lib.BEM_APPLY_NO_HALF if no_half else 0, _stream()))
         return z
+
+    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
+        """GMRES for (1/2 I - D_p) x_p = b_p on every problem p at once (each with its
+        own Krylov space).  b: [nrhs, N_total].  Returns (x, iterations,
+        relres[nrhs, number of problems])."""
+        bs = (b if b.dim() == 2 else b[None]).to("cuda").contiguous()
+        nrhs = bs.shape[0]
+        x = torch.zeros_like(bs) if x0 is None else (x0 if x0.dim() == 2 else x0[None]).to("cuda", bs.dtype).clone()
+        iters = ctypes.c_int(0)
+        nprob = len(self.sizes)
+        rel = (ctypes.c_double * (nrhs * nprob))()
+        flags = _lib.BEM_GMRES_USE_X0 if x0 is not None else 0
+        rc = self._lib.bem_gmres_solve_batch(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
+                                             int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
+        if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
+            _lib.check(rc)
+        return x, int(iters.value), np.array(list(rel)).reshape(nrhs, nprob)

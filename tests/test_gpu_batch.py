@@ -43,3 +43,50 @@ def test_batch_generators_are_closed_surfaces():
         c, area, nrm, _ = oracle.geometry(V, T)
         assert np.max(np.abs((area[:, None] * nrm).sum(0))) < 1e-12
         assert 1.0 <= k <= 8.0
+
+
+def state_and_adjoint_rhs(V, T, k):
+    """The two right-hand sides of a body: the plane wave e^{ikz} and the adjoint
+    source sum_m G(x - x_obs,m), x_obs at distance 5 along +-x and +-z from the
+    body's centre (G = e^{ikr}/(4 pi r))."""
+    c, _, _, _ = oracle.geometry(V, T)
+    pw = inputs.plane_wave(c, k)
+    centre = 0.5 * (V.min(axis=0) + V.max(axis=0))
+    adj = np.zeros(c.shape[0], dtype=np.complex128)
+    for o in ((5, 0, 0), (-5, 0, 0), (0, 0, 5), (0, 0, -5)):
+        r = np.linalg.norm(c - (centre + np.array(o, float)), axis=1)
+        adj += np.exp(1j * k * r) / (4 * np.pi * r)
+    return np.stack([pw, adj])
+
+
+def test_batch_solve_state_and_adjoint(cuda_ok):
+    """GMRES on every body of a batch at once (two right-hand sides each): per
+    system the recursive residual reaches tol, the solution agrees with the
+    single-body solve, and the oracle's true residual on 300 rows per body is
+    at the apply accuracy."""
+    probs = small_bodies()
+    batch = Batch(probs, p=10, mode="mixed", max_nrhs=2)
+    b = np.concatenate([state_and_adjoint_rhs(V, T, k) for V, T, k in probs], axis=1)
+    tol = 1e-8
+    x, iters, relres = batch.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=200, restart=200)
+    x = x.cpu().numpy()
+    assert relres.shape == (2, len(probs)) and np.all(relres <= tol) and iters >= 2
+    for p, (V, T, k) in enumerate(probs):
+        a, e = batch.offsets[p], batch.offsets[p + 1]
+        op = Operator(V, T, k, p=10, mode="mixed", max_nrhs=2)
+        xs, _, _ = op.solve(torch.from_numpy(b[:, a:e].copy()).cuda(), tol=tol)
+        assert rel(x[:, a:e], xs.cpu().numpy()) <= 1e-5
+        rows = np.sort(np.random.default_rng(p).choice(e - a, min(300, e - a), replace=False))
+        res = b[:, a:e][:, rows] - oracle.apply(V, T, k, x=x[:, a:e], rows=rows)
+        assert np.linalg.norm(res) / np.linalg.norm(b[:, a:e][:, rows]) <= 1e-5
+
+
+def test_batch_solve_rejects_bad_arguments(cuda_ok):
+    from paper_1606_02383_gb300 import _lib
+    batch = Batch(small_bodies()[:2], p=8, mode="mixed", max_nrhs=1)
+    b = torch.zeros((3, batch.n), dtype=torch.complex128, device="cuda")
+    with pytest.raises(RuntimeError):
+        batch.solve(b)  # nrhs above max_nrhs
+    rc = batch._lib.bem_gmres_solve_batch(batch._h, 1, _lib.BEM_C128, b.data_ptr(), None, 1e-6, 10, 10, 0, None, None,
+                                          None)
+    assert rc == _lib.BEM_ERR_INVALID_ARG
