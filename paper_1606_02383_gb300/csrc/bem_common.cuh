@@ -260,8 +260,9 @@ bool bem_is_fp64(const bem_handle* h);
 void bem_gl_host(int n, double* x, double* w);
 // vertex gradient of the loss (bem_grad_vertices.cu); yx, gs: unweighted
 // densities (y, x) and the upstream gradient in octree order, FP64;
-// dvertices: host array [nv][3], written when `s` completes
-int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices,
+// dvertices: nullable host array [nv][3], written when `s` completes;
+// dk: nullable device double to which the regular-rule part of dL/dk is added
+int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices, double* dk,
                       cudaStream_t s);
 
 template <typename T>

@@ -8,8 +8,10 @@
 //   dS_ii/dk = (1/4 pi) int_T i exp(ikr) dA.
 // For an upstream gradient g (PyTorch convention for complex outputs) the loss
 // derivative is dk = sum_rhs Re < g, (dA/dk) u >.  The regular rule R_0 over
-// all pairs is an FP64 direct sum; the near-singular / self corrections add
-// d/dk of (rule R_L or exact) - R_0 for the pairs of the correction matrix.
+// all pairs is summed by the target-major pass of the vertex gradient
+// (bem_grad_vertices.cu: FP64 in the FP64 modes, FP32 with FP64 near pairs
+// otherwise); the near-singular / self corrections add, in FP64, d/dk of
+// (rule R_L or exact) - R_0 for the pairs of the correction matrix.
 #include "bem_common.cuh"
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -161,57 +163,6 @@ __device__ zd dk_self(const GTri& t, double k) {
   return (1.0 / (4.0 * BEM_PI)) * acc;
 }
 
-// regular rule over all pairs: out[block] = sum_i Re conj(g_i) sum_j dA_ij u_j  (per rhs, all rhs summed)
-__global__ void __launch_bounds__(128) k_grad_k_regular(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
-                                                        const double* __restrict__ qpt,
-                                                        const double* __restrict__ nrm,
-                                                        const double* __restrict__ area,
-                                                        const double4* __restrict__ yx,
-                                                        const double2* __restrict__ gs, double* out) {
-  __shared__ double s_q[128][9];
-  __shared__ double s_n[128][3];
-  __shared__ double s_w[128];
-  __shared__ double s_red[128];
-  int64_t i = blockIdx.x * (int64_t)128 + threadIdx.x;
-  int r = blockIdx.y;
-  double x[3] = {0, 0, 0};
-  if (i < nt)
-    for (int d = 0; d < 3; ++d) x[d] = cent[3 * i + d];
-  const double4* u = yx + (int64_t)r * nt;
-  zd acc = cmk(0.0, 0.0);
-  for (int64_t e0 = 0; e0 < nt; e0 += 128) {
-    int ne = (int)min((int64_t)128, nt - e0);
-    __syncthreads();
-    if (threadIdx.x < ne) {
-      int64_t j = e0 + threadIdx.x;
-      for (int d = 0; d < 9; ++d) s_q[threadIdx.x][d] = qpt[9 * j + d];
-      for (int d = 0; d < 3; ++d) s_n[threadIdx.x][d] = nrm[3 * j + d];
-      s_w[threadIdx.x] = area[j] / 3.0;
-    }
-    __syncthreads();
-    if (i < nt) {
-      for (int e = 0; e < ne; ++e) {
-        zd ds = cmk(0.0, 0.0), dd = cmk(0.0, 0.0);
-        for (int q = 0; q < 3; ++q) dk_point(x, &s_q[e][3 * q], s_n[e], s_w[e], k, ds, dd);
-        double4 uy = u[e0 + e];
-        acc = acc + ds * cmk(uy.x, uy.y) - dd * cmk(uy.z, uy.w);
-      }
-    }
-  }
-  double part = 0.0;
-  if (i < nt) {
-    double2 g = gs[(int64_t)r * nt + i];
-    part = g.x * acc.re + g.y * acc.im;  // Re(conj(g) acc)
-  }
-  s_red[threadIdx.x] = part;
-  __syncthreads();
-  for (int st = 64; st > 0; st >>= 1) {
-    if (threadIdx.x < st) s_red[threadIdx.x] += s_red[threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) atomicAdd(out, s_red[0]);
-}
-
 // corrections: (d/dk of the refined / exact entry) - (d/dk of R_0) for every correction pair
 __global__ void k_grad_k_corr(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
                               const double* __restrict__ qpt, const double* __restrict__ nrm,
@@ -315,7 +266,9 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
     k_grad_prologue<float><<<nblk(nt, 256), 256, 0, s>>>(nt, nrhs, h->perm, (const float*)g, (const float*)x,
                                                          (const float*)y, yx, gs);
   BEM_CUDA(cudaGetLastError());
-  if (dvertices) BEM_TRY(bem_grad_vertices(h, nrhs, yx, gs, dvertices, s));
+  // regular rule over all pairs: vertex terms and the regular part of dL/dk in
+  // one target-major pass (plus the source-major pass for the vertices)
+  BEM_TRY(bem_grad_vertices(h, nrhs, yx, gs, dvertices, dk ? acc : nullptr, s));
   if (!dk) {
     BEM_CUDA(cudaFreeAsync(yx, s));
     BEM_CUDA(cudaFreeAsync(gs, s));
@@ -327,11 +280,6 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
   bem_gl_host(32, glx, glw);
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
-  {
-    dim3 grid(nblk(nt, 128), nrhs);
-    k_grad_k_regular<<<grid, 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, yx, gs, acc);
-    BEM_CUDA(cudaGetLastError());
-  }
   k_grad_k_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                    h->corr_ptr, h->corr_col, yx, gs, acc);
   BEM_CUDA(cudaGetLastError());

@@ -49,9 +49,9 @@ __device__ __forceinline__ void sc(double a, double* s, double* c) { sincos(a, s
 
 // G, F, H of one point at separation d (|d| > 0)
 template <typename R>
-__device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F, cpx<R>& H) {
+__device__ __forceinline__ void ghfr(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F, cpx<R>& H, R& r) {
   R r2 = d0 * d0 + d1 * d1 + d2 * d2;
-  R r = sqrt(r2);
+  r = sqrt(r2);
   R ir = R(1) / r;
   R ir2 = ir * ir;
   R kr = k * r;
@@ -64,6 +64,11 @@ __device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F,
   F = (ir * ir2) * (E * cmk(R(-1), kr));
   // H = E (3 - k^2 r^2 - 3ikr) / r^5
   H = (ir2 * ir2 * ir) * (E * cmk(R(3) - kr * kr, R(-3) * kr));
+}
+template <typename R>
+__device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F, cpx<R>& H) {
+  R r;
+  ghfr(d0, d1, d2, k, G, F, H, r);
 }
 
 // ------------------------------------------------------ regular rule R_0 --
@@ -78,7 +83,7 @@ __device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F,
 // the target-pass terms of one pair in FP64: acc += sum_q w [-F d y_j + (H (d.n) d + F n) x_j]
 __device__ void near_target64(const double* __restrict__ xi, int64_t j, double k, const double* __restrict__ qpt,
                               const double* __restrict__ nrm, const double* __restrict__ area,
-                              const double4* __restrict__ u, double* acc) {
+                              const double4* __restrict__ u, double* acc, double* kacc) {
   const double w = area[j] / 3.0;
   const double4 v = u[j];
   const zd wy = cmk(w * v.x, w * v.y), wx = cmk(w * v.z, w * v.w);
@@ -87,10 +92,15 @@ __device__ void near_target64(const double* __restrict__ xi, int64_t j, double k
     const double d0 = qpt[9 * j + 3 * q] - xi[0], d1 = qpt[9 * j + 3 * q + 1] - xi[1],
                  d2 = qpt[9 * j + 3 * q + 2] - xi[2];
     zd G, F, H;
-    ghf(d0, d1, d2, k, G, F, H);
+    double r;
+    ghfr(d0, d1, d2, k, G, F, H, r);
     const double dn = d0 * n0 + d1 * n1 + d2 * n2;
     const zd a = dn * (H * wx) - F * wy;
     const zd b = F * wx;
+    // d/dk: dG/dk = i r G, d(dG/dn)/dk = -k (d.n) G
+    const zd kt = G * (cmk(-r * wy.im, r * wy.re) + (k * dn) * wx);
+    kacc[0] += kt.re;
+    kacc[1] += kt.im;
     acc[0] += d0 * a.re + n0 * b.re;
     acc[1] += d0 * a.im + n0 * b.im;
     acc[2] += d1 * a.re + n1 * b.re;
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
                                                    const double* __restrict__ qpt, const double* __restrict__ nrm,
                                                    const double* __restrict__ area, const double* __restrict__ hmax,
                                                    const double4* __restrict__ yx, const double2* __restrict__ gs,
-                                                   double* __restrict__ gx) {
+                                                   double* __restrict__ gx, double* __restrict__ dk) {
   __shared__ R s_q[128][9];
   __shared__ R s_n[128][3];
   __shared__ cpx<R> s_y[128], s_x[128];
@@ -127,6 +137,7 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
   const double4* u = yx + (int64_t)r * nt;
   const R kk = R(k);
   double acc[6] = {0, 0, 0, 0, 0, 0};
+  double kacc[2] = {0, 0};  // sum of w [dS/dk y_j - dD/dk x_j] over the pairs of this target
   for (int64_t e0 = 0; e0 < nt; e0 += 128) {
     const int ne = (int)min((int64_t)128, nt - e0);
     __syncthreads();
@@ -147,12 +158,12 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
     }
     __syncthreads();
     if (i < nt) {
-      cpx<R> T0 = cmk(R(0), R(0)), T1 = T0, T2 = T0;
+      cpx<R> T0 = cmk(R(0), R(0)), T1 = T0, T2 = T0, KT = T0;
       for (int e = 0; e < ne; ++e) {
         if (sizeof(R) == 4) {
           const R c0 = s_c[e][0] - x[0], c1 = s_c[e][1] - x[1], c2 = s_c[e][2] - x[2];
           if (c0 * c0 + c1 * c1 + c2 * c2 < s_h2[e]) {
-            near_target64(cent + 3 * i, e0 + e, k, qpt, nrm, area, u, acc);
+            near_target64(cent + 3 * i, e0 + e, k, qpt, nrm, area, u, acc, kacc);
             continue;
           }
         }
@@ -162,10 +173,12 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
         for (int q = 0; q < 3; ++q) {
           const R d0 = s_q[e][3 * q] - x[0], d1 = s_q[e][3 * q + 1] - x[1], d2 = s_q[e][3 * q + 2] - x[2];
           cpx<R> G, F, H;
-          ghf(d0, d1, d2, kk, G, F, H);
+          R rr;
+          ghfr(d0, d1, d2, kk, G, F, H, rr);
           const R dn = d0 * n0 + d1 * n1 + d2 * n2;
           const cpx<R> a = dn * (H * wx) - F * wy;
           const cpx<R> b = F * wx;
+          KT = KT + G * (cmk(-rr * wy.im, rr * wy.re) + (kk * dn) * wx);
           T0 = T0 + d0 * a + n0 * b;
           T1 = T1 + d1 * a + n1 * b;
           T2 = T2 + d2 * a + n2 * b;
@@ -177,11 +190,25 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
       acc[3] += T1.im;
       acc[4] += T2.re;
       acc[5] += T2.im;
+      kacc[0] += KT.re;
+      kacc[1] += KT.im;
     }
   }
+  double kpart = 0.0;
   if (i < nt) {
     const double2 g = gs[(int64_t)r * nt + i];
     for (int d = 0; d < 3; ++d) atomicAdd(&gx[3 * i + d], g.x * acc[2 * d] + g.y * acc[2 * d + 1]);
+    kpart = g.x * kacc[0] + g.y * kacc[1];  // Re(conj(g_i) K_i)
+  }
+  if (dk) {
+    __shared__ double s_red[128];
+    s_red[threadIdx.x] = kpart;
+    __syncthreads();
+    for (int st = 64; st > 0; st >>= 1) {
+      if (threadIdx.x < st) s_red[threadIdx.x] += s_red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(dk, s_red[0]);
   }
 }
 
@@ -576,11 +603,11 @@ __global__ void k_gv_finish(int64_t nt, const double* __restrict__ cent, const d
     for (int d = 0; d < 3; ++d) atomicAdd(&dV[3 * (int64_t)tri[3 * j + a] + d], g9[3 * a + d]);
 }
 
-int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices,
+int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2* gs, double* dvertices, double* dk,
                       cudaStream_t s) {
   const int64_t nt = h->nt, nv = h->nv;
   double *gx, *gq, *ga, *gn, *gel, *dV;
-  const size_t nd = (size_t)nt * (3 + 9 + 1 + 3 + 9) + (size_t)nv * 3;
+  const size_t nd = dvertices ? (size_t)nt * (3 + 9 + 1 + 3 + 9) + (size_t)nv * 3 : (size_t)nt * 3;
   double* buf;
   BEM_CUDA(cudaMallocAsync((void**)&buf, nd * sizeof(double), s));
   BEM_CUDA(cudaMemsetAsync(buf, 0, nd * sizeof(double), s));
@@ -591,15 +618,23 @@ int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2*
   gel = gn + 3 * nt;
   dV = gel + 9 * nt;
   const dim3 gt(nblk(nt, 128), nrhs), gsrc(nblk(3 * nt, 128), nrhs);
-  if (bem_is_fp64(h)) {
-    k_gv_target<double><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx);
+  const bool f64 = bem_is_fp64(h);
+  if (f64)
+    k_gv_target<double><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx, dk);
+  else
+    k_gv_target<float><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx, dk);
+  BEM_CUDA(cudaGetLastError());
+  if (!dvertices) {
+    // only the regular-rule part of dL/dk was asked for
+    BEM_CUDA(cudaFreeAsync(buf, s));
+    return BEM_OK;
+  }
+  if (f64)
     k_gv_source<double><<<gsrc, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gq, ga,
                                              gn);
-  } else {
-    k_gv_target<float><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gx);
+  else
     k_gv_source<float><<<gsrc, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gq, ga,
                                             gn);
-  }
   BEM_CUDA(cudaGetLastError());
   double glx[32], glw[32];
   bem_gl_host(32, glx, glw);
