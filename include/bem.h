@@ -195,9 +195,8 @@ int bem_apply_adjoint(bem_handle* h, int nrhs, int dtype, const void* g, void* g
  *               (BEM_ERR_INVALID_ARG for a device pointer).
  *   dk        : nullable host pointer to one double; not both NULL.
  * Cost: direct sums over all pairs (O(N^2)): FP64 in the FP64 modes; in the
- * mixed modes the vertex terms run in FP32 with FP64 accumulation, and FP64
- * for pairs within 4.5 longest edges, while dk stays FP64.  The correction
- * pairs are FP64.  The call allocates per-call scratch and synchronises
+ * mixed modes FP32 with FP64 accumulation, and FP64 for pairs within 4.5
+ * longest edges.  The correction pairs are FP64.  The call allocates per-call scratch and synchronises
  * `stream`.
  */
 int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, const void* y, double* dvertices,
