@@ -361,6 +361,75 @@ __device__ void rule_refined(const double* x, const Tri64& t, int L, double k, z
 __constant__ double c_gl_x[32];
 __constant__ double c_gl_w[32];
 
+// FP32 versions for the mixed modes, with the triangle in coordinates
+// relative to the target (so the point differences stay accurate in FP32)
+struct Tri32 {
+  float v[3][3];
+  float n[3];
+  float area;
+};
+
+__device__ __forceinline__ void kern32(const float* y, const float* n, float w, float k, zf& s, zf& d) {
+  const float r = sqrtf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+  float sn, cs;
+  sincosf(k * r, &sn, &cs);
+  const float g = w / (4.0f * (float)BEM_PI * r);
+  s.re += g * cs;
+  s.im += g * sn;
+  const float rn = y[0] * n[0] + y[1] * n[1] + y[2] * n[2];
+  const float f = w * rn / (4.0f * (float)BEM_PI * r * r * r);
+  d.re += f * (-cs - k * r * sn);
+  d.im += f * (k * r * cs - sn);
+}
+
+// R_L on a target-relative triangle (same pieces and points as rule_refined)
+__device__ void rule_refined32(const Tri32& t, int L, float k, zf& s, zf& d) {
+  const int npieces = 1 << (2 * L);
+  const float w = t.area / (3.0f * npieces);
+  for (int piece = 0; piece < npieces; ++piece) {
+    float a[3], b[3], c[3];
+    for (int dd = 0; dd < 3; ++dd) {
+      a[dd] = t.v[0][dd];
+      b[dd] = t.v[1][dd];
+      c[dd] = t.v[2][dd];
+    }
+    int code = piece;
+    for (int lvl = 0; lvl < L; ++lvl) {
+      const int child = code & 3;
+      code >>= 2;
+      float ab[3], bc[3], ca[3];
+      for (int dd = 0; dd < 3; ++dd) {
+        ab[dd] = 0.5f * (a[dd] + b[dd]);
+        bc[dd] = 0.5f * (b[dd] + c[dd]);
+        ca[dd] = 0.5f * (c[dd] + a[dd]);
+      }
+      for (int dd = 0; dd < 3; ++dd) {
+        if (child == 0) {
+          b[dd] = ab[dd];
+          c[dd] = ca[dd];
+        } else if (child == 1) {
+          a[dd] = ab[dd];
+          c[dd] = bc[dd];
+        } else if (child == 2) {
+          a[dd] = ca[dd];
+          b[dd] = bc[dd];
+        } else {
+          a[dd] = ab[dd];
+          b[dd] = bc[dd];
+          c[dd] = ca[dd];
+        }
+      }
+    }
+    const float b0 = 2.0f / 3.0f, b1 = 1.0f / 6.0f;
+    for (int q = 0; q < 3; ++q) {
+      float y[3];
+      for (int dd = 0; dd < 3; ++dd)
+        y[dd] = (q == 0 ? b0 : b1) * a[dd] + (q == 1 ? b0 : b1) * b[dd] + (q == 2 ? b0 : b1) * c[dd];
+      kern32(y, t.n, w, k, s, d);
+    }
+  }
+}
+
 __device__ zd self_single_layer(const Tri64& t, double k) {
   zd acc = cmk(0.0, 0.0);
   for (int e = 0; e < 3; ++e) {
@@ -437,7 +506,9 @@ __global__ void k_corr_pairs(int64_t nt, const double* __restrict__ cent, const 
   if (!pass) count[i] = n;
 }
 
-// correction values, one warp per target row; values divided by wgt[j]
+// correction values, one warp per target row; values divided by wgt[j].  In the
+// FP64 modes everything is FP64; in the mixed modes (FP32 values) the rules of
+// non-self pairs are summed in FP32 relative to the target, the self term in FP64.
 template <typename V4>
 __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ cent, const double* __restrict__ qpt,
                               const double* __restrict__ nrm, const double* __restrict__ area,
@@ -451,6 +522,32 @@ __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ c
     int j = col[e];
     Tri64 t;
     load_tri64(qpt, nrm, cent, area, hmax, j, t);
+    if (sizeof(V4) == sizeof(float4) && (int64_t)j != i) {
+      // mixed modes (values stored in FP32): both rules in FP32, target-relative
+      double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
+      double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+      int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+      V4 o;
+      if (L == 0) {
+        o.x = o.y = o.z = o.w = 0;
+      } else {
+        Tri32 tf;
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) tf.v[a][c] = (float)(t.v[a][c] - x[c]);
+        for (int c = 0; c < 3; ++c) tf.n[c] = (float)t.n[c];
+        tf.area = (float)t.area;
+        zf s0f = cmk(0.f, 0.f), d0f = s0f, s1f = s0f, d1f = s0f;
+        rule_refined32(tf, 0, (float)k, s0f, d0f);
+        rule_refined32(tf, L, (float)k, s1f, d1f);
+        const float iwf = (float)(1.0 / wgt[j]);
+        o.x = (s1f.re - s0f.re) * iwf;
+        o.y = (s1f.im - s0f.im) * iwf;
+        o.z = (d1f.re - d0f.re) * iwf;
+        o.w = (d1f.im - d0f.im) * iwf;
+      }
+      val[e] = o;
+      continue;
+    }
     zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0), s1 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
     rule_refined(x, t, 0, k, s0, d0);  // what the regular rule contributes
     if ((int64_t)j == i) {
