@@ -211,6 +211,7 @@ def run_reference(args, world, rank):
 
 def run_ours(args, world, rank, local):
     import torch
+    from paper_1606_02383_gb300 import inputs
     from paper_1606_02383_gb300.operator import Operator
 
     torch.cuda.set_device(local)
@@ -278,6 +279,40 @@ def run_ours(args, world, rank, local):
     e2e_s = reduce_max(time.perf_counter() - t0, world)
     e2e_val = world * args.e2e_steps / e2e_s
 
+    # also reported on rank 0: multi-rhs throughput of the same operator and the
+    # GMRES solve of the plane wave on this sphere (resonance-checked ka)
+    also = None
+    if rank == 0:
+        multi = {}
+        for m in (2, 16):
+            xm = torch.from_numpy(inputs.random_density(n, m, seed=2, stream=0)).cuda()
+            ym = torch.from_numpy(inputs.random_density(n, m, seed=2, stream=1)).cuda()
+            for _ in range(2):
+                op.apply(xm, ym)
+            reps, tot = 5, 0.0
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                op.apply(xm, ym)
+                b.record()
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            multi["nrhs%d" % m] = {"ms_per_apply": tot / reps, "rhs_matvecs_per_s": m * reps * 1e3 / tot}
+            del xm, ym
+        ks = _resonance_safe_k(args.ka, [1.0])
+        ops = Operator(V, T, ks, p=0, eps=args.eps, mode="mixed")
+        cen = V[T].mean(axis=1)
+        bpw = torch.from_numpy(inputs.plane_wave(cen, ks)[None, :]).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, relres = ops.solve(bpw, tol=1e-5, max_iter=300, restart=300, raise_on_fail=False)
+        torch.cuda.synchronize()
+        gm_s = time.perf_counter() - t0
+        ops.close()
+        also = {"multi_rhs": multi, "gmres_plane_wave": {"ka": ks, "tol": 1e-5, "iterations": iters,
+                                                         "relres": float(relres[0]), "seconds": gm_s}}
+
     if rank != 0:
         return
     peaks, peak_src = measured_peaks()
@@ -340,6 +375,7 @@ def run_ours(args, world, rank, local):
                                             "wall_s_timed_region": round(wall, 4)}),
             "roofline": roof,
             "roofline_m2l": roof_m2l,
+            "also": also,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 16, "d2h_bytes_per_step": n * 16},
             "gpu_launches": launches * args.steps,

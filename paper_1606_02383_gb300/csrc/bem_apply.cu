@@ -11,6 +11,7 @@
 //   L2P       : far field at the centroids from the stored per-element rows
 //   epilogue  : z = 1/2 x + near + far, back to the caller's order and dtype
 #include <algorithm>
+#include <type_traits>
 
 #include "bem_common.cuh"
 
@@ -130,32 +131,41 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
   return r;
 }
 
-// The point kernel of p2p_eval for two targets at once (packed pairs).
-// nt = (-t_a, -t_b) per axis; n, sigma, tau as broadcast pairs; k2 = (k, k),
-// nk2 = (-k, -k), m1 = (-1, -1).
-__device__ __forceinline__ void p2p_eval_pair(float qx, float qy, float qz, f32x2 ntx, f32x2 nty, f32x2 ntz,
-                                              f32x2 nx, f32x2 ny, f32x2 nz, f32x2 sre, f32x2 sim, f32x2 tre,
-                                              f32x2 tim, f32x2 k2, f32x2 nk2, f32x2 m1, f32x2& are, f32x2& aim) {
+// The point kernel of p2p_eval for two targets at once (packed pairs), split
+// into the part every right-hand side shares (g = exp(ikr)/r, f and kr f) and
+// the per-density update.  nt = (-t_a, -t_b) per axis; n as broadcast pairs;
+// k2 = (k, k), m1 = (-1, -1).
+struct P2PPoint {
+  f32x2 gre, gim, ngim, f, fk, nfk;
+};
+__device__ __forceinline__ P2PPoint p2p_point_pair(float qx, float qy, float qz, f32x2 ntx, f32x2 nty, f32x2 ntz,
+                                                   f32x2 nx, f32x2 ny, f32x2 nz, f32x2 k2, f32x2 m1) {
+  P2PPoint g;
   f32x2 dx = add2(pk2(qx, qx), ntx), dy = add2(pk2(qy, qy), nty), dz = add2(pk2(qz, qz), ntz);
   f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
   float r2a, r2b;
   upk2(r2, r2a, r2b);
   f32x2 ri = pk2(rsqrtf(r2a), rsqrtf(r2b));
-  f32x2 r = mul2(r2, ri);
-  f32x2 kr = mul2(k2, r);
-  f32x2 nkr = mul2(nk2, r);
+  f32x2 kr = mul2(k2, mul2(r2, ri));
   float kra, krb, sa, ca, sb, cb;
   upk2(kr, kra, krb);
   __sincosf(kra, &sa, &ca);  // |kr| stays small in the near field (phase error ~4e-8 kr)
   __sincosf(krb, &sb, &cb);
-  f32x2 f = mul2(fma2(dx, nx, fma2(dy, ny, mul2(dz, nz))), mul2(ri, ri));
-  f32x2 ur = mul2(f, tre), ui = mul2(f, tim);
-  f32x2 vr = fma2(kr, ui, add2(sre, ur));
-  f32x2 vi = fma2(nkr, ur, add2(sim, ui));
-  f32x2 wi = mul2(vi, m1);
-  f32x2 gre = mul2(ri, pk2(ca, cb)), gim = mul2(ri, pk2(sa, sb));
-  are = fma2(gre, vr, fma2(gim, wi, are));
-  aim = fma2(gre, vi, fma2(gim, vr, aim));
+  g.f = mul2(fma2(dx, nx, fma2(dy, ny, mul2(dz, nz))), mul2(ri, ri));
+  g.fk = mul2(g.f, kr);
+  g.nfk = mul2(g.fk, m1);
+  g.gre = mul2(ri, pk2(ca, cb));
+  g.gim = mul2(ri, pk2(sa, sb));
+  g.ngim = mul2(g.gim, m1);
+  return g;
+}
+// a += g [sigma + u - i kr u], u = f tau, for the density d = (sigma, tau)
+__device__ __forceinline__ void p2p_acc_pair(const P2PPoint& g, float4 d, f32x2& are, f32x2& aim) {
+  f32x2 sre = pk2(d.x, d.x), sim = pk2(d.y, d.y), tre = pk2(d.z, d.z), tim = pk2(d.w, d.w);
+  f32x2 vr = fma2(g.fk, tim, fma2(g.f, tre, sre));
+  f32x2 vi = fma2(g.nfk, tre, fma2(g.f, tim, sim));
+  are = fma2(g.gre, vr, fma2(g.ngim, vi, are));
+  aim = fma2(g.gre, vi, fma2(g.gim, vr, aim));
 }
 
 // One warp per work unit (leaf box, 2^j consecutive targets, j <= 6).  The
@@ -166,18 +176,98 @@ __device__ __forceinline__ void p2p_eval_pair(float qx, float qy, float qz, f32x
 // summed with an xor-shuffle butterfly; no shared memory and no barriers.
 // Units are sorted by cost, largest first, so the tail of the grid is short.
 #define P2P_WARPS 4
-template <typename R>
-__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t nt, R k, R wleaf,
-                                                            const int4* __restrict__ units,
-                                                            const int* __restrict__ near27,
-                                                            const int* __restrict__ bstart,
-                                                            const int* __restrict__ bend,
-                                                            const int* __restrict__ coord,
-                                                            const typename V4of<R>::T* __restrict__ tgt,
-                                                            const typename V4of<R>::T* __restrict__ src,
-                                                            const typename V4of<R>::T* __restrict__ dens,
-                                                            double* __restrict__ zn) {
-  typedef typename V4of<R>::T V4;
+#define P2P_NR_MAX 4  // right-hand sides per FP32 P2P warp
+// FP32: NR right-hand sides r0 + NR blockIdx.y + [0, NR) per warp, sharing
+// the kernel values of every point (packed f32x2 arithmetic, two targets per
+// lane).
+template <int NR>
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k, float wleaf,
+                                                              const int4* __restrict__ units,
+                                                              const int* __restrict__ near27,
+                                                              const int* __restrict__ bstart,
+                                                              const int* __restrict__ bend,
+                                                              const int* __restrict__ coord,
+                                                              const float4* __restrict__ tgt,
+                                                              const float4* __restrict__ src,
+                                                              const float4* __restrict__ dens,
+                                                              double* __restrict__ zn) {
+  int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
+  if (u >= nunits) return;
+  int lane = threadIdx.x & 31;
+  int r = r0 + blockIdx.y * NR;
+  int4 U = units[u];
+  int b = U.x, tfirst = U.y, cnt = U.z;
+  int np2 = (cnt + 1) >> 1;  // power of two
+  int pi = lane & (np2 - 1), split = lane / np2, nsplit = 32 / np2;
+  bool two = pi + np2 < cnt;
+  float4 ta = tgt[tfirst + pi];
+  float4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
+  const float4* dr = dens + (int64_t)r * nt;
+  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
+  f32x2 are[NR], aim[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) are[j] = aim[j] = pk2(0.f, 0.f);
+  const f32x2 pk_k = pk2(k, k), pk_m1 = pk2(-1.f, -1.f);
+  for (int slot = 0; slot < 27; ++slot) {
+    int sb = near27[27 * b + slot];
+    if (sb < 0) continue;
+    float sx = (float)((coord[3 * sb] - bx) * (double)wleaf);
+    float sy = (float)((coord[3 * sb + 1] - by) * (double)wleaf);
+    float sz = (float)((coord[3 * sb + 2] - bz) * (double)wleaf);
+    // targets in the source box's frame, negated
+    f32x2 ntx = pk2(sx - ta.x, sx - tb.x), nty = pk2(sy - ta.y, sy - tb.y), ntz = pk2(sz - ta.z, sz - tb.z);
+    int e1 = bend[sb];
+    for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+      float4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
+      float4 d[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) d[j] = dr[(int64_t)j * nt + e];
+      f32x2 nx = pk2(q0.w, q0.w), ny = pk2(q1.w, q1.w), nz = pk2(q2.w, q2.w);
+      P2PPoint g = p2p_point_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+      g = p2p_point_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+      g = p2p_point_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    float a_re, b_re, a_im, b_im;
+    upk2(are[j], a_re, b_re);
+    upk2(aim[j], a_im, b_im);
+    for (int o = np2; o < 32; o <<= 1) {
+      a_re += __shfl_xor_sync(0xffffffffu, a_re, o);
+      a_im += __shfl_xor_sync(0xffffffffu, a_im, o);
+      b_re += __shfl_xor_sync(0xffffffffu, b_re, o);
+      b_im += __shfl_xor_sync(0xffffffffu, b_im, o);
+    }
+    if (split == 0) {
+      int64_t o = 2 * ((int64_t)(r + j) * nt + tfirst + pi);
+      zn[o] = (double)a_re;
+      zn[o + 1] = (double)a_im;
+      if (two) {
+        zn[o + 2 * np2] = (double)b_re;
+        zn[o + 2 * np2 + 1] = (double)b_im;
+      }
+    }
+  }
+}
+
+// FP64: one right-hand side per warp (grid.y), scalar arithmetic.
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm64(int nunits, int64_t nt, double k, double wleaf,
+                                                              const int4* __restrict__ units,
+                                                              const int* __restrict__ near27,
+                                                              const int* __restrict__ bstart,
+                                                              const int* __restrict__ bend,
+                                                              const int* __restrict__ coord,
+                                                              const double4* __restrict__ tgt,
+                                                              const double4* __restrict__ src,
+                                                              const double4* __restrict__ dens,
+                                                              double* __restrict__ zn) {
   int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
   if (u >= nunits) return;
   int lane = threadIdx.x & 31;
@@ -187,59 +277,31 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t 
   int np2 = (cnt + 1) >> 1;  // power of two
   int pi = lane & (np2 - 1), split = lane / np2, nsplit = 32 / np2;
   bool two = pi + np2 < cnt;
-  V4 ta = tgt[tfirst + pi];
-  V4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
-  const V4* dr = dens + (int64_t)r * nt;
+  double4 ta = tgt[tfirst + pi];
+  double4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
+  const double4* dr = dens + (int64_t)r * nt;
   int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
-  R a_re = 0, a_im = 0, b_re = 0, b_im = 0;
-  // packed accumulators and constants (used by the FP32 instantiation)
-  f32x2 pa_re = pk2(0.f, 0.f), pa_im = pk2(0.f, 0.f);
-  const f32x2 pk_k = pk2((float)k, (float)k), pk_nk = pk2(-(float)k, -(float)k), pk_m1 = pk2(-1.f, -1.f);
+  double a_re = 0, a_im = 0, b_re = 0, b_im = 0;
   for (int slot = 0; slot < 27; ++slot) {
     int sb = near27[27 * b + slot];
     if (sb < 0) continue;
-    R sx = (R)((coord[3 * sb] - bx) * (double)wleaf);
-    R sy = (R)((coord[3 * sb + 1] - by) * (double)wleaf);
-    R sz = (R)((coord[3 * sb + 2] - bz) * (double)wleaf);
-    R ax = ta.x - sx, ay = ta.y - sy, az = ta.z - sz;  // targets in the source box's frame
-    R bx_ = tb.x - sx, by_ = tb.y - sy, bz_ = tb.z - sz;
+    double sx = (coord[3 * sb] - bx) * wleaf;
+    double sy = (coord[3 * sb + 1] - by) * wleaf;
+    double sz = (coord[3 * sb + 2] - bz) * wleaf;
+    double ax = ta.x - sx, ay = ta.y - sy, az = ta.z - sz;  // targets in the source box's frame
+    double bx_ = tb.x - sx, by_ = tb.y - sy, bz_ = tb.z - sz;
     int e1 = bend[sb];
-    if constexpr (sizeof(R) == 4) {
-      f32x2 ntx = pk2(-ax, -bx_), nty = pk2(-ay, -by_), ntz = pk2(-az, -bz_);
-      for (int e = bstart[sb] + split; e < e1; e += nsplit) {
-        V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
-        V4 d = dr[e];
-        f32x2 nx = pk2(q0.w, q0.w), ny = pk2(q1.w, q1.w), nz = pk2(q2.w, q2.w);
-        f32x2 sre = pk2(d.x, d.x), sim = pk2(d.y, d.y), tre = pk2(d.z, d.z), tim = pk2(d.w, d.w);
-        p2p_eval_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
-                      pa_im);
-        p2p_eval_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
-                      pa_im);
-        p2p_eval_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, sre, sim, tre, tim, pk_k, pk_nk, pk_m1, pa_re,
-                      pa_im);
-      }
-    } else {
-      for (int e = bstart[sb] + split; e < e1; e += nsplit) {
-        V4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
-        V4 d = dr[e];
-        R nx = q0.w, ny = q1.w, nz = q2.w;
-        p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
-        p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
-        p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
-        p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-        p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-        p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-      }
+    for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+      double4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
+      double4 d = dr[e];
+      double nx = q0.w, ny = q1.w, nz = q2.w;
+      p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
+      p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
     }
-  }
-  if constexpr (sizeof(R) == 4) {
-    float lo, hi;
-    upk2(pa_re, lo, hi);
-    a_re += lo;
-    b_re += hi;
-    upk2(pa_im, lo, hi);
-    a_im += lo;
-    b_im += hi;
   }
   for (int o = np2; o < 32; o <<= 1) {
     a_re += __shfl_xor_sync(0xffffffffu, a_re, o);
@@ -249,11 +311,11 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm(int nunits, int64_t 
   }
   if (split == 0) {
     int64_t o = 2 * ((int64_t)r * nt + tfirst + pi);
-    zn[o] = (double)a_re;
-    zn[o + 1] = (double)a_im;
+    zn[o] = a_re;
+    zn[o + 1] = a_im;
     if (two) {
-      zn[o + 2 * np2] = (double)b_re;
-      zn[o + 2 * np2 + 1] = (double)b_im;
+      zn[o + 2 * np2] = b_re;
+      zn[o + 2 * np2 + 1] = b_im;
     }
   }
 }
@@ -308,31 +370,41 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
 // z_i += sum_j C^S_ij sigma_j - C^D_ij tau_j  (values pre-divided by the weight).
 // One warp per row, accumulated in the operator's precision (FP32 in the mixed
 // mode: about 130 terms per row, each already a small correction) and added to
-// the FP64 near-field sum.
-template <typename V4, typename R>
-__global__ void k_correction(int64_t nt, const int* __restrict__ ptr, const int* __restrict__ col,
+// the FP64 near-field sum.  NR right-hand sides r0 + NR blockIdx.y + [0, NR)
+// share each loaded value pair.
+template <typename V4, typename R, int NR>
+__global__ void k_correction(int64_t nt, int r0, const int* __restrict__ ptr, const int* __restrict__ col,
                              const V4* __restrict__ val, const V4* __restrict__ dens, double* __restrict__ zn) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  int r = blockIdx.y;
+  int r = r0 + blockIdx.y * NR;
   if (i >= nt) return;
   const V4* dr = dens + (int64_t)r * nt;
-  R are = 0, aim = 0;
+  R are[NR], aim[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) are[j] = aim[j] = 0;
   int e1 = ptr[i + 1];
   for (int e = ptr[i] + lane; e < e1; e += 32) {
     V4 c = val[e];
-    V4 d = dr[col[e]];
-    are += c.x * d.x - c.y * d.y - c.z * d.z + c.w * d.w;
-    aim += c.x * d.y + c.y * d.x - c.z * d.w - c.w * d.z;
+    int64_t cj = col[e];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      V4 d = dr[(int64_t)j * nt + cj];
+      are[j] += c.x * d.x - c.y * d.y - c.z * d.z + c.w * d.w;
+      aim[j] += c.x * d.y + c.y * d.x - c.z * d.w - c.w * d.z;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    are += __shfl_xor_sync(0xffffffffu, are, o);
-    aim += __shfl_xor_sync(0xffffffffu, aim, o);
-  }
-  if (lane == 0) {
-    int64_t o = 2 * ((int64_t)r * nt + i);
-    zn[o] += (double)are;
-    zn[o + 1] += (double)aim;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    for (int o = 16; o > 0; o >>= 1) {
+      are[j] += __shfl_xor_sync(0xffffffffu, are[j], o);
+      aim[j] += __shfl_xor_sync(0xffffffffu, aim[j], o);
+    }
+    if (lane == 0) {
+      int64_t o = 2 * ((int64_t)(r + j) * nt + i);
+      zn[o] += (double)are[j];
+      zn[o + 1] += (double)aim[j];
+    }
   }
 }
 
@@ -362,25 +434,32 @@ __global__ void k_p2m(int nleaf, int64_t nt, int P, const int* __restrict__ bsta
 
 // FP32: one thread per coefficient pair (2t, 2t+1) with 16-byte loads of the
 // element rows, elements in rounds of 4 so that their loads are in flight
-// together.  A row [a (P complex) | b (P complex)] starts on a 16-byte
-// boundary; b does too when P is even, otherwise it is read as two float2.
-__global__ void k_p2m_v(int nleaf, int64_t nt, int P, const int* __restrict__ bstart, const int* __restrict__ bend,
-                        const float* __restrict__ rows_ab, const float4* __restrict__ dens, int64_t exp_base,
-                        int64_t exp_stride, float* __restrict__ M) {
-  const int b = blockIdx.x, r = blockIdx.y;
+// together; NR right-hand sides r0 + NR blockIdx.y + [0, NR) share each row.
+// A row [a (P complex) | b (P complex)] starts on a 16-byte boundary; b does
+// too when P is even, otherwise it is read as two float2.
+template <int NR>
+__global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restrict__ bstart,
+                        const int* __restrict__ bend, const float* __restrict__ rows_ab,
+                        const float4* __restrict__ dens, int64_t exp_base, int64_t exp_stride,
+                        float* __restrict__ M) {
+  const int b = blockIdx.x, r = r0 + blockIdx.y * NR;
   const int e0 = 2 * threadIdx.x;
   if (e0 >= P) return;
   const bool two = e0 + 1 < P, peven = (P & 1) == 0;
   const float4* dr = dens + (int64_t)r * nt;
-  float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+  float2 acc0[NR], acc1[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc0[q] = acc1[q] = make_float2(0.f, 0.f);
   const int j0 = bstart[b], j1 = bend[b];
   for (int jb = j0; jb < j1; jb += 4) {
-    float4 A[4], B[4], D[4];
+    float4 A[4], B[4], D[4][NR];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = jb + u;
       if (j >= j1) {
-        A[u] = B[u] = D[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A[u] = B[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) D[u][q] = A[u];
         continue;
       }
       const float* ab = rows_ab + 4 * (int64_t)j * P;
@@ -398,62 +477,86 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int P, const int* __restrict__ bs
         const float2 b1 = two ? *(const float2*)(bb + 2 * e0 + 2) : make_float2(0.f, 0.f);
         B[u] = make_float4(b0.x, b0.y, b1.x, b1.y);
       }
-      D[u] = dr[j];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) D[u][q] = dr[(int64_t)q * nt + j];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float4 a = A[u], bq = B[u], d = D[u];
-      acc0.x += a.x * d.x - a.y * d.y - bq.x * d.z + bq.y * d.w;
-      acc0.y += a.x * d.y + a.y * d.x - bq.x * d.w - bq.y * d.z;
-      acc1.x += a.z * d.x - a.w * d.y - bq.z * d.z + bq.w * d.w;
-      acc1.y += a.z * d.y + a.w * d.x - bq.z * d.w - bq.w * d.z;
+      const float4 a = A[u], bq = B[u];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const float4 d = D[u][q];
+        acc0[q].x += a.x * d.x - a.y * d.y - bq.x * d.z + bq.y * d.w;
+        acc0[q].y += a.x * d.y + a.y * d.x - bq.x * d.w - bq.y * d.z;
+        acc1[q].x += a.z * d.x - a.w * d.y - bq.z * d.z + bq.w * d.w;
+        acc1[q].y += a.z * d.y + a.w * d.x - bq.z * d.w - bq.w * d.z;
+      }
     }
   }
-  float* out = M + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P + e0);
-  out[0] = acc0.x;
-  out[1] = acc0.y;
-  if (two) {
-    out[2] = acc1.x;
-    out[3] = acc1.y;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    float* out = M + 2 * ((int64_t)(r + q) * exp_stride + exp_base + (int64_t)b * P + e0);
+    out[0] = acc0[q].x;
+    out[1] = acc0[q].y;
+    if (two) {
+      out[2] = acc1[q].x;
+      out[3] = acc1[q].y;
+    }
   }
 }
 
 // -------------------------------------------------------------------- L2P --
-template <typename R>
-__global__ void k_l2p(int64_t nt, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
+// One warp per target; NR right-hand sides r0 + NR blockIdx.y + [0, NR)
+// share each loaded row.
+template <typename R, int NR>
+__global__ void k_l2p(int64_t nt, int r0, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
                       const R* __restrict__ Lexp, int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  int r = blockIdx.y;
+  int r = r0 + blockIdx.y * NR;
   if (i >= nt) return;
   int b = leaf_of[i];
   const R* row = rows_r + 2 * (i * P);
   const R* Lb = Lexp + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P);
-  R are = 0, aim = 0;
+  const int64_t ls = 2 * exp_stride;  // between right-hand sides
+  R are[NR], aim[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) are[q] = aim[q] = 0;
   if (sizeof(R) == 4 && (P & 1) == 0) {
     // P even: the row starts on a 16-byte boundary, two coefficients per load
     for (int e2 = lane; 2 * e2 < P; e2 += 32) {
       const float4 x = *(const float4*)((const float*)row + 4 * e2);
-      const float2 l0 = *(const float2*)((const float*)Lb + 4 * e2);
-      const float2 l1 = *(const float2*)((const float*)Lb + 4 * e2 + 2);
-      are += x.x * l0.x - x.y * l0.y + x.z * l1.x - x.w * l1.y;
-      aim += x.x * l0.y + x.y * l0.x + x.z * l1.y + x.w * l1.x;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const float* Lq = (const float*)Lb + q * ls;
+        const float2 l0 = *(const float2*)(Lq + 4 * e2);
+        const float2 l1 = *(const float2*)(Lq + 4 * e2 + 2);
+        are[q] += x.x * l0.x - x.y * l0.y + x.z * l1.x - x.w * l1.y;
+        aim[q] += x.x * l0.y + x.y * l0.x + x.z * l1.y + x.w * l1.x;
+      }
     }
   } else {
     for (int e = lane; e < P; e += 32) {
-      R x = row[2 * e], y = row[2 * e + 1], lr = Lb[2 * e], li = Lb[2 * e + 1];
-      are += x * lr - y * li;
-      aim += x * li + y * lr;
+      R x = row[2 * e], y = row[2 * e + 1];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        R lr = Lb[q * ls + 2 * e], li = Lb[q * ls + 2 * e + 1];
+        are[q] += x * lr - y * li;
+        aim[q] += x * li + y * lr;
+      }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    are += __shfl_xor_sync(0xffffffffu, are, o);
-    aim += __shfl_xor_sync(0xffffffffu, aim, o);
-  }
-  if (lane == 0) {
-    int64_t o = 2 * ((int64_t)r * nt + i);
-    zfar[o] = (double)are;
-    zfar[o + 1] = (double)aim;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      are[q] += __shfl_xor_sync(0xffffffffu, are[q], o);
+      aim[q] += __shfl_xor_sync(0xffffffffu, aim[q], o);
+    }
+    if (lane == 0) {
+      int64_t o = 2 * ((int64_t)(r + q) * nt + i);
+      zfar[o] = (double)are[q];
+      zfar[o + 1] = (double)aim[q];
+    }
   }
 }
 
@@ -605,6 +708,19 @@ static int run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   return BEM_OK;
 }
 
+// Calls f(NR, r0, nchunk) for the right-hand sides [0, nrhs): chunks of
+// P2P_NR_MAX, then one chunk of the remainder.  Returns the launch count.
+template <typename F>
+static int by_rhs_chunks(int nrhs, F&& f) {
+  static_assert(P2P_NR_MAX == 4, "remainder cases below assume chunks of 4");
+  const int full = nrhs / 4, rem = nrhs - 4 * full;
+  if (full) f(std::integral_constant<int, 4>(), 0, full);
+  if (rem == 1) f(std::integral_constant<int, 1>(), 4 * full, 1);
+  if (rem == 2) f(std::integral_constant<int, 2>(), 4 * full, 1);
+  if (rem == 3) f(std::integral_constant<int, 3>(), 4 * full, 1);
+  return (full > 0) + (rem > 0);
+}
+
 template <typename R>
 static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   typedef typename V4of<R>::T V4;
@@ -616,24 +732,34 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   int L = h->L;
   // near field
   int pr = bem_prof_begin(h, s);
+  int nl = 1;
   if (fmm) {
     LevelInfo& lf = h->lev[L];
-    dim3 grid(nblk(h->n_p2p_units, P2P_WARPS), nrhs);
-    k_p2p_fmm<R><<<grid, 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, (R)h->k, (R)lf.w, h->p2p_units, h->near27,
-                                                 lf.start, lf.end, lf.coord, tgt, src, dens, h->zn);
+    const unsigned gx = nblk(h->n_p2p_units, P2P_WARPS);
+    if constexpr (sizeof(R) == 4) {
+      nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+        k_p2p_fmm32<decltype(nr)::value><<<dim3(gx, nchunk), 32 * P2P_WARPS, 0, s>>>(
+            h->n_p2p_units, nt, r0, (float)h->k, (float)lf.w, h->p2p_units, h->near27, lf.start, lf.end, lf.coord,
+            (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
+      });
+    } else {
+      k_p2p_fmm64<<<dim3(gx, nrhs), 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, h->k, lf.w, h->p2p_units,
+                                                          h->near27, lf.start, lf.end, lf.coord, (const double4*)tgt,
+                                                          (const double4*)src, (const double4*)dens, h->zn);
+    }
   } else {
     dim3 grid(nblk(nt, P2P_THREADS), nrhs);
     k_p2p_direct<R><<<grid, P2P_THREADS, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->zn);
   }
   BEM_CUDA(cudaGetLastError());
-  bem_prof_end(h, pr, 1, 1, s);
+  bem_prof_end(h, pr, 1, nl, s);
   pr = bem_prof_begin(h, s);
-  {
-    dim3 grid(nblk(nt * 32, 256), nrhs);
-    k_correction<V4, R><<<grid, 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->zn);
-    BEM_CUDA(cudaGetLastError());
-  }
-  bem_prof_end(h, pr, 2, 1, s);
+  nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+    k_correction<V4, R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(
+        nt, r0, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->zn);
+  });
+  BEM_CUDA(cudaGetLastError());
+  bem_prof_end(h, pr, 2, nl, s);
   if (!fmm || L < 2) {
     BEM_CUDA(cudaMemsetAsync(h->zfar, 0, sizeof(double) * 2 * nt * nrhs, s));
     return BEM_OK;
@@ -644,19 +770,20 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   pr = bem_prof_begin(h, s);
   BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
   BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
-  {
-    dim3 grid(lf.nbox, nrhs);
-    if constexpr (sizeof(R) == 4)
-      k_p2m_v<<<grid, ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end,
-                                                               (const float*)h->p2m_rows, (const float4*)dens,
-                                                               lf.exp_base, h->exp_total, (float*)h->Mexp);
-    else
-      k_p2m<R><<<grid, 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens, lf.exp_base,
-                                    h->exp_total, (R*)h->Mexp);
-    BEM_CUDA(cudaGetLastError());
+  if constexpr (sizeof(R) == 4) {
+    nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+      k_p2m_v<decltype(nr)::value><<<dim3(lf.nbox, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
+          lf.nbox, nt, r0, lf.P, lf.start, lf.end, (const float*)h->p2m_rows, (const float4*)dens, lf.exp_base,
+          h->exp_total, (float*)h->Mexp);
+    });
+  } else {
+    nl = 1;
+    k_p2m<R><<<dim3(lf.nbox, nrhs), 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens,
+                                                 lf.exp_base, h->exp_total, (R*)h->Mexp);
   }
-  bem_prof_end(h, pr, 3, 1, s);
-  int nl = 0;
+  BEM_CUDA(cudaGetLastError());
+  bem_prof_end(h, pr, 3, nl, s);
+  nl = 0;
   pr = bem_prof_begin(h, s);
   for (int l = L - 1; l >= 2; --l) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 4, nl, s);
@@ -669,13 +796,12 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   for (int l = 2; l < L; ++l) BEM_TRY(run_grouped<R>(h, h->l2l[l], h->Lexp, h->Lexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 6, nl, s);
   pr = bem_prof_begin(h, s);
-  {
-    dim3 grid(nblk(nt * 32, 256), nrhs);
-    k_l2p<R><<<grid, 256, 0, s>>>(nt, lf.P, h->leaf_of, (const R*)h->l2p_rows, (const R*)h->Lexp, lf.exp_base,
-                                  h->exp_total, h->zfar);
-    BEM_CUDA(cudaGetLastError());
-  }
-  bem_prof_end(h, pr, 7, 1, s);
+  nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+    k_l2p<R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(
+        nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows, (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
+  });
+  BEM_CUDA(cudaGetLastError());
+  bem_prof_end(h, pr, 7, nl, s);
   return BEM_OK;
 }
 
