@@ -213,13 +213,22 @@ int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, c
  *   max_iter   : total iteration cap; restart: Krylov dimension per cycle.
  *   iters_out  : nullable; receives the iterations used.
  *   relres_out : nullable host array [nrhs]; receives the final relative residuals.
+ *   flags      : BEM_GMRES_USE_X0; BEM_GMRES_HOST_LOOP runs the Arnoldi steps
+ *                from the host; BEM_GMRES_GRAPH_ONLY makes a failure to build
+ *                the graph an error instead of falling back to the host loop.
  * Orthogonalisation is classical Gram-Schmidt applied twice, in FP64.
  * Returns BEM_ERR_NOT_CONVERGED (with x = last iterate) if max_iter is reached.
- * Synchronises `stream` once per iteration (to read the residual).  The call
- * allocates about (min(restart, max_iter) + 4) * nrhs * N * 16 bytes of
- * stream-ordered scratch for its Krylov basis and frees it before returning.
+ * By default every restart cycle is one CUDA graph (built once per call):
+ * the Arnoldi steps run in a conditional WHILE node, the Givens rotations of
+ * the small least-squares problems run on the device, and `stream` is
+ * synchronised once per cycle to read the residuals.  The host loop
+ * synchronises once per iteration.  The call allocates about
+ * (min(restart, max_iter) + 5) * nrhs * N * 16 bytes of stream-ordered
+ * scratch for its Krylov basis and frees it before returning.
  */
 #define BEM_GMRES_USE_X0 1
+#define BEM_GMRES_HOST_LOOP 2
+#define BEM_GMRES_GRAPH_ONLY 4
 int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
                     int flags, int* iters_out, double* relres_out, void* stream);
 

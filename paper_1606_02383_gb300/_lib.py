@@ -30,6 +30,8 @@ MODES = {"mixed": 0, "fp64": 1, "direct64": 2, "direct32": 3, "tf32": 4}
 BEM_APPLY_NO_HALF = 1
 BEM_HOST_BUFFERS = 2
 BEM_GMRES_USE_X0 = 1
+BEM_GMRES_HOST_LOOP = 2
+BEM_GMRES_GRAPH_ONLY = 4
 
 INFO = {
     "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,

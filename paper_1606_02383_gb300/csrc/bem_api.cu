@@ -323,6 +323,8 @@ int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, 
   BEM_TRY(check_apply_args(h, nrhs, dtype, 0));
   if (!b || !x) return bem_fail(BEM_ERR_INVALID_ARG, "b or x is NULL");
   if (!(tol > 0.0) || max_iter < 1 || restart < 1) return bem_fail(BEM_ERR_INVALID_ARG, "bad tol/max_iter/restart");
+  if (flags & ~(BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY))
+    return bem_fail(BEM_ERR_INVALID_ARG, "flags: BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY");
   return bem_gmres(h, nrhs, dtype, b, x, tol, max_iter, restart, flags, iters_out, relres_out, (cudaStream_t)stream);
 }
 

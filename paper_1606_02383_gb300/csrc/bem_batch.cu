@@ -149,27 +149,41 @@ extern "C" int bem_setup_batch(const bem_mesh* meshes, const double* ks, int cou
   return BEM_OK;
 }
 
-// capture the applies of all problems (staging buffers in, staging buffer out)
-static int capture(bem_batch* b, int nrhs, int half, cudaGraphExec_t* exec) {
-  cudaStream_t s = b->cs;
-  BEM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+// the applies of all problems (staging buffers in, staging buffer out),
+// forked over the batch's streams and joined back into `s`; the stage timers
+// (events) stay off, so that the work can be captured
+static int issue_batch(bem_batch* b, int nrhs, int half, cudaStream_t s) {
   int rc = BEM_OK;
-  cudaEventRecord(b->ev_fork, s);
-  for (int i = 0; i < BEM_BATCH_STREAMS; ++i) cudaStreamWaitEvent(b->fork[i], b->ev_fork, 0);
+  BEM_CUDA(cudaEventRecord(b->ev_fork, s));
+  for (int i = 0; i < BEM_BATCH_STREAMS; ++i) BEM_CUDA(cudaStreamWaitEvent(b->fork[i], b->ev_fork, 0));
   for (size_t p = 0; p < b->h.size() && rc == BEM_OK; ++p) {
     bem_handle* h = b->h[p];
     cudaStream_t fs = b->fork[p % BEM_BATCH_STREAMS];
     const double* x = b->sx + 2 * nrhs * b->off[p];
     const double* y = b->sy + 2 * nrhs * b->off[p];
     double* z = b->sz + 2 * nrhs * b->off[p];
+    const int prof = h->prof_on;
+    h->prof_on = 0;
     rc = bem_prologue(h, nrhs, BEM_C128, x, y, fs);
     if (rc == BEM_OK) rc = bem_apply_sorted(h, nrhs, fs);
     if (rc == BEM_OK) rc = bem_epilogue(h, nrhs, BEM_C128, x, z, half, fs);
+    h->prof_on = prof;
   }
+  // join every forked stream, also after a failure, so that no stream is left
+  // waiting outside a capture that ends
   for (int i = 0; i < BEM_BATCH_STREAMS; ++i) {
-    cudaEventRecord(b->ev_join[i], b->fork[i]);
-    cudaStreamWaitEvent(s, b->ev_join[i], 0);
+    cudaError_t e = cudaEventRecord(b->ev_join[i], b->fork[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[i], 0);
+    if (e != cudaSuccess && rc == BEM_OK) rc = bem_fail(BEM_ERR_CUDA, std::string("batch join: ") + cudaGetErrorString(e));
   }
+  return rc;
+}
+
+// capture the applies of all problems into an executable graph
+static int capture(bem_batch* b, int nrhs, int half, cudaGraphExec_t* exec) {
+  cudaStream_t s = b->cs;
+  BEM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = issue_batch(b, nrhs, half, s);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc != BEM_OK) {
@@ -246,8 +260,9 @@ extern "C" int bem_batch_info(bem_batch* b, int problem, int key, int64_t* value
 // ------------------------------------------------------------ batch solve --
 // GMRES for every problem and right-hand side of the batch at once: column
 // (r, p) is problem p's segment of right-hand side r in the caller's
-// [nrhs][ntot] layout, and each iteration is one graph-replayed batch apply of
-// (1/2 I - D).  Columns converge independently (each has its own Krylov space).
+// [nrhs][ntot] layout, and each iteration is one batch apply of (1/2 I - D):
+// captured into the solver's cycle graph, or graph-replayed from the host
+// loop.  Columns converge independently (each has its own Krylov space).
 namespace {
 struct BatchOp {
   bem_batch* b;
@@ -256,6 +271,19 @@ struct BatchOp {
 int batch_apply(void* ctx, const double* in, double* out, cudaStream_t s) {
   BatchOp* o = (BatchOp*)ctx;
   return bem_apply_batch(o->b, o->nrhs, BEM_C128, in, nullptr, out, 0, (void*)s);
+}
+// the same work issued directly into `s` (for capture into a solver graph)
+int batch_apply_capture(void* ctx, const double* in, double* out, cudaStream_t s) {
+  BatchOp* o = (BatchOp*)ctx;
+  bem_batch* b = o->b;
+  const int np = (int)b->h.size();
+  const unsigned g = nblk(b->ntot, 256);
+  k_batch_gather<double><<<g, 256, 0, s>>>(b->ntot, o->nrhs, np, b->doff, in, b->sx);
+  BEM_CUDA(cudaMemsetAsync(b->sy, 0, 2 * (size_t)b->ntot * o->nrhs * sizeof(double), s));
+  BEM_TRY(issue_batch(b, o->nrhs, 1, s));
+  k_batch_scatter<double><<<g, 256, 0, s>>>(b->ntot, o->nrhs, np, b->doff, b->sz, out);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
 }
 }  // namespace
 
@@ -269,7 +297,8 @@ extern "C" int bem_gmres_solve_batch(bem_batch* b, int nrhs, int dtype, const vo
   if (!rhs || !x) return bem_fail(BEM_ERR_INVALID_ARG, "rhs and x are required");
   if (!(tol > 0.0) || max_iter < 1 || restart < 1)
     return bem_fail(BEM_ERR_INVALID_ARG, "tol must be > 0, max_iter and restart >= 1");
-  if (flags & ~BEM_GMRES_USE_X0) return bem_fail(BEM_ERR_INVALID_ARG, "flags: only BEM_GMRES_USE_X0");
+  if (flags & ~(BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY))
+    return bem_fail(BEM_ERR_INVALID_ARG, "flags: BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY");
   const int np = (int)b->h.size();
   const int ncol = nrhs * np;
   std::vector<int64_t> off(ncol), len(ncol);
@@ -279,6 +308,6 @@ extern "C" int bem_gmres_solve_batch(bem_batch* b, int nrhs, int dtype, const vo
       len[r * np + p] = b->off[p + 1] - b->off[p];
     }
   BatchOp ctx{b, nrhs};
-  return bem_gmres_core(batch_apply, &ctx, ncol, (int64_t)nrhs * b->ntot, off.data(), len.data(), dtype, rhs, x, tol,
+  return bem_gmres_core(batch_apply, batch_apply_capture, &ctx, ncol, (int64_t)nrhs * b->ntot, off.data(), len.data(), dtype, rhs, x, tol,
                         max_iter, restart, flags, iters_out, relres_out, (cudaStream_t)stream);
 }

@@ -295,8 +295,11 @@ int bem_adjoint_epilogue(bem_handle* h, int nrhs, int dtype, const void* g, void
 // apply callback of the GMRES core: out = A in, both block vectors of complex FP64
 typedef int (*bem_gm_apply_fn)(void* ctx, const double* in, double* out, cudaStream_t s);
 // restarted GMRES on ncol independent systems in lockstep; column c is the
-// segment [off[c], off[c] + len[c]) of a block vector of M complex entries
-int bem_gmres_core(bem_gm_apply_fn apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
+// segment [off[c], off[c] + len[c]) of a block vector of M complex entries.
+// capture_apply (nullable) issues the same work as apply on the given stream
+// with nothing that breaks stream capture (no synchronisation, allocation or
+// events); with it the restart cycles run as CUDA graphs.
+int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
                    int dtype, const void* b, void* x, double tol, int max_iter, int restart, int flags,
                    int* iters_out, double* relres_out, cudaStream_t s);
 int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,

@@ -6,9 +6,15 @@
 // and every iteration makes one apply of the whole block (a multi-rhs apply of
 // one operator, or one batch apply of many operators).  Krylov vectors, dot
 // products and updates are FP64 on the device; orthogonalisation is classical
-// Gram-Schmidt applied twice (CGS2).  The small Hessenberg least-squares
-// problem (Givens rotations) of every column is solved on the host, which reads
-// j+2 coefficients per column after every iteration.
+// Gram-Schmidt applied twice (CGS2).
+//
+// Two drivers share the arithmetic.  By default a restart cycle is one CUDA
+// graph: the Arnoldi steps run in a conditional WHILE node, the small
+// Hessenberg least-squares problems (Givens rotations) are solved on the device
+// and the host reads the residuals once per cycle.  The host-driven loop
+// (BEM_GMRES_HOST_LOOP, and the fallback when no graph can be built) solves the
+// small problems on the host and reads j+2 coefficients per column after every
+// iteration.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -136,6 +142,281 @@ __global__ void k_c128_to_c64(int64_t m, const double* __restrict__ a, float* b)
   if (e < m) b[e] = (float)a[e];
 }
 
+// ------------------------------------------------ device-resident cycles --
+// One restart cycle as one CUDA graph: the residual, its norm and the start
+// of the cycle; a conditional WHILE node whose body is one Arnoldi step
+// (apply, CGS2, norm, Givens rotations of every column); then the triangular
+// solves and the update of x.  Every kernel of the body reads the step j from
+// a control block in device memory, so one captured body serves every j, and
+// the Givens kernel decides on the device whether the loop goes on.  The host
+// reads the residuals once per cycle.
+struct GmCtl {
+  int j;     // Arnoldi step within the cycle: V_0 .. V_j exist
+  int jlim;  // steps allowed in this cycle: min(restart, max_iter - it)
+  int it;    // iterations over all cycles
+  int any;   // some column still active
+};
+
+#define GM_VSPLIT 8
+
+__device__ __forceinline__ int gmd_nv(int fixed_nv, const GmCtl* ctl) { return fixed_nv > 0 ? fixed_nv : ctl->j + 1; }
+
+// partial[(c*mp1 + i)*GM_CHUNKS + chunk] = chunk sum of conj(V_i[c]) w[c],
+// i < nv (nv = fixed_nv, or j + 1 from the control block)
+__global__ void k_gmd_dots(int fixed_nv, const GmCtl* __restrict__ ctl, int mp1, const int64_t* __restrict__ off,
+                           const int64_t* __restrict__ len, const double* __restrict__ V, int64_t vstride,
+                           const double* __restrict__ w, double* partial) {
+  const int nv = gmd_nv(fixed_nv, ctl);
+  const int chunk = blockIdx.x, c = blockIdx.z;
+  const int64_t n = len[c];
+  const int64_t per = (n + GM_CHUNKS - 1) / GM_CHUNKS;
+  const int64_t a = chunk * per, b = min(n, a + per);
+  const double* ww = w + 2 * off[c];
+  __shared__ double sh[2][256];
+  for (int i = blockIdx.y; i < nv; i += GM_VSPLIT) {
+    const double* v = V + i * vstride + 2 * off[c];
+    double sre = 0.0, sim = 0.0;
+    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+      double vr = v[2 * e], vi = v[2 * e + 1], wr = ww[2 * e], wi = ww[2 * e + 1];
+      sre += vr * wr + vi * wi;
+      sim += vr * wi - vi * wr;
+    }
+    sh[0][threadIdx.x] = sre;
+    sh[1][threadIdx.x] = sim;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+        sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      int64_t o = ((int64_t)c * mp1 + i) * GM_CHUNKS + chunk;
+      partial[2 * o] = sh[0][0];
+      partial[2 * o + 1] = sh[1][0];
+    }
+    __syncthreads();
+  }
+}
+
+// out[c*mp1 + i] = sum over chunks, i < nv
+__global__ void k_gmd_reduce(int fixed_nv, const GmCtl* __restrict__ ctl, int ncol, int mp1,
+                             const double* __restrict__ partial, double* out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncol * mp1 || t % mp1 >= gmd_nv(fixed_nv, ctl)) return;
+  double sre = 0.0, sim = 0.0;
+  for (int c = 0; c < GM_CHUNKS; ++c) {
+    sre += partial[2 * ((int64_t)t * GM_CHUNKS + c)];
+    sim += partial[2 * ((int64_t)t * GM_CHUNKS + c) + 1];
+  }
+  out[2 * t] = sre;
+  out[2 * t + 1] = sim;
+}
+
+// w -= sum_{i <= j} coef[c*mp1 + i] V_i
+__global__ void k_gmd_orth(int64_t M, const GmCtl* __restrict__ ctl, int mp1, const int* __restrict__ colof,
+                           const double* __restrict__ V, int64_t vstride, const double* __restrict__ coef, double* w) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  const int c = colof[e], nv = ctl->j + 1;
+  double wr = w[2 * e], wi = w[2 * e + 1];
+  for (int i = 0; i < nv; ++i) {
+    double cr = coef[2 * (c * mp1 + i)], ci = coef[2 * (c * mp1 + i) + 1];
+    const double* v = V + i * vstride + 2 * e;
+    wr -= cr * v[0] - ci * v[1];
+    wi -= cr * v[1] + ci * v[0];
+  }
+  w[2 * e] = wr;
+  w[2 * e + 1] = wi;
+}
+
+// dst = V_j (the apply's input)
+__global__ void k_gmd_copy_vj(int64_t n, const GmCtl* __restrict__ ctl, const double* __restrict__ V, int64_t vstride,
+                              double* dst) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = V[(int64_t)ctl->j * vstride + e];
+}
+
+// V_j = w * scale[column]
+__global__ void k_gmd_scale(int64_t M, const GmCtl* __restrict__ ctl, const int* __restrict__ colof,
+                            const double* __restrict__ w, const double* __restrict__ scale, double* V,
+                            int64_t vstride) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  double s = scale[colof[e]];
+  double* d = V + (int64_t)ctl->j * vstride;
+  d[2 * e] = w[2 * e] * s;
+  d[2 * e + 1] = w[2 * e + 1] * s;
+}
+
+__device__ __forceinline__ double gmd_bnorm(const double* nrm_b, int c) {
+  double bn = sqrt(fmax(0.0, nrm_b[2 * c]));
+  return bn > 0.0 ? bn : 1.0;
+}
+
+// Start of a cycle (one block): beta = |r0| per column, the active columns,
+// 1 / beta for V_0, g = beta e_1; j = 0 and the step limit; the loop runs if
+// some column is active.
+__global__ void k_gmd_start(int ncol, int m, int max_iter, double tol, const double* __restrict__ nrm_r,
+                            const double* __restrict__ nrm_b, GmCtl* ctl, int* active, int* ncols, double* relres,
+                            double* scale, double* gg, int mp1, cudaGraphConditionalHandle cond) {
+  __shared__ int any_s;
+  if (threadIdx.x == 0) any_s = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const double beta = sqrt(fmax(0.0, nrm_r[2 * c]));
+    relres[c] = beta / gmd_bnorm(nrm_b, c);
+    const int act = relres[c] > tol && beta > 0.0;
+    active[c] = act;
+    ncols[c] = 0;
+    scale[c] = act ? 1.0 / beta : 0.0;
+    gg[2 * (int64_t)c * mp1] = beta;
+    gg[2 * (int64_t)c * mp1 + 1] = 0.0;
+    if (act) any_s = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int jlim = min(m, max_iter - ctl->it);
+    ctl->j = 0;
+    ctl->jlim = jlim;
+    ctl->any = any_s;
+    cudaGraphSetConditional(cond, (any_s && jlim > 0) ? 1u : 0u);
+  }
+}
+
+// One Arnoldi step's small problem for every active column (one block, a
+// thread per column): Hessenberg column j = coef + coef2 and |w|, the earlier
+// rotations, a new rotation zeroing H[j+1][j], g updated; the column stops on
+// |g[j+1]| / |b| <= tol or on breakdown.  Then j advances and the loop goes on
+// while a column is active and j < jlim.
+__global__ void k_gmd_givens(int ncol, int m, int mp1, double tol, const double* __restrict__ coef,
+                             const double* __restrict__ coef2, const double* __restrict__ nrm_w,
+                             const double* __restrict__ nrm_b, GmCtl* ctl, double* H, double* cs, double* sn,
+                             double* gg, int* active, int* ncols, double* relres, double* scale,
+                             cudaGraphConditionalHandle cond) {
+  __shared__ int any_s;
+  const int j = ctl->j;
+  if (threadIdx.x == 0) any_s = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    if (!active[c]) {
+      scale[c] = 0.0;
+      continue;
+    }
+    double* Hc = H + 2 * (int64_t)c * mp1 * m;
+    double* csc = cs + (int64_t)c * m;
+    double* snc = sn + 2 * (int64_t)c * m;
+    double* g = gg + 2 * (int64_t)c * mp1;
+#define HR(i, q) Hc[2 * ((int64_t)(i) * m + (q))]
+#define HI(i, q) Hc[2 * ((int64_t)(i) * m + (q)) + 1]
+    for (int i = 0; i <= j; ++i) {
+      HR(i, j) = coef[2 * (c * mp1 + i)] + coef2[2 * (c * mp1 + i)];
+      HI(i, j) = coef[2 * (c * mp1 + i) + 1] + coef2[2 * (c * mp1 + i) + 1];
+    }
+    const double hn = sqrt(fmax(0.0, nrm_w[2 * c]));
+    HR(j + 1, j) = hn;
+    HI(j + 1, j) = 0.0;
+    for (int i = 0; i < j; ++i) {  // earlier rotations
+      const double ar = HR(i, j), ai = HI(i, j), br = HR(i + 1, j), bi = HI(i + 1, j);
+      const double c_ = csc[i], sr = snc[2 * i], si = snc[2 * i + 1];
+      HR(i, j) = c_ * ar + (sr * br - si * bi);
+      HI(i, j) = c_ * ai + (sr * bi + si * br);
+      HR(i + 1, j) = -(sr * ar + si * ai) + c_ * br;  // -conj(s) a + c b
+      HI(i + 1, j) = -(sr * ai - si * ar) + c_ * bi;
+    }
+    const double ar = HR(j, j), ai = HI(j, j);
+    const double bq = hypot(HR(j + 1, j), HI(j + 1, j));
+    const double aa = hypot(ar, ai);
+    const double rho = hypot(aa, bq);
+    double cj, sjr, sji;
+    if (aa == 0.0) {
+      cj = 0.0;
+      sjr = 1.0;
+      sji = 0.0;
+    } else {
+      cj = aa / rho;
+      sjr = (ar / aa) * bq / rho;
+      sji = (ai / aa) * bq / rho;
+    }
+    csc[j] = cj;
+    snc[2 * j] = sjr;
+    snc[2 * j + 1] = sji;
+    HR(j, j) = cj * ar + sjr * bq;
+    HI(j, j) = cj * ai + sji * bq;
+    HR(j + 1, j) = 0.0;
+    HI(j + 1, j) = 0.0;
+    const double gr = g[2 * j], gi = g[2 * j + 1];
+    g[2 * (j + 1)] = -(sjr * gr + sji * gi);  // -conj(s) g_j
+    g[2 * (j + 1) + 1] = -(sjr * gi - sji * gr);
+    g[2 * j] = cj * gr;
+    g[2 * j + 1] = cj * gi;
+    ncols[c] = j + 1;
+    relres[c] = hypot(g[2 * (j + 1)], g[2 * (j + 1) + 1]) / gmd_bnorm(nrm_b, c);
+    const bool breakdown = !(hn > 1e-14 * hypot(HR(j, j), HI(j, j)));
+#undef HR
+#undef HI
+    if (relres[c] <= tol || breakdown) {
+      active[c] = 0;
+      scale[c] = 0.0;
+    } else {
+      scale[c] = 1.0 / hn;
+      any_s = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int jn = j + 1;
+    ctl->j = jn;
+    ctl->it += 1;
+    ctl->any = any_s;
+    cudaGraphSetConditional(cond, (any_s && jn < ctl->jlim) ? 1u : 0u);
+  }
+}
+
+// y = R^-1 g per column (back substitution over its ncols columns); zeros up
+// to the cycle's step count
+__global__ void k_gmd_backsub(int ncol, int m, int mp1, const GmCtl* __restrict__ ctl, const double* __restrict__ H,
+                              const double* __restrict__ gg, const int* __restrict__ ncols, double* y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  const int k = ncols[c], jmax = ctl->j;
+  const double* Hc = H + 2 * (int64_t)c * mp1 * m;
+  const double* g = gg + 2 * (int64_t)c * mp1;
+  double* yc = y + 2 * (int64_t)c * mp1;
+  for (int i = k - 1; i >= 0; --i) {
+    double accr = g[2 * i], acci = g[2 * i + 1];
+    for (int q = i + 1; q < k; ++q) {
+      const double hr = Hc[2 * ((int64_t)i * m + q)], hi = Hc[2 * ((int64_t)i * m + q) + 1];
+      accr -= hr * yc[2 * q] - hi * yc[2 * q + 1];
+      acci -= hr * yc[2 * q + 1] + hi * yc[2 * q];
+    }
+    const double dr = Hc[2 * ((int64_t)i * m + i)], di = Hc[2 * ((int64_t)i * m + i) + 1];
+    const double den = dr * dr + di * di;
+    yc[2 * i] = (accr * dr + acci * di) / den;
+    yc[2 * i + 1] = (acci * dr - accr * di) / den;
+  }
+  for (int i = k; i < jmax; ++i) yc[2 * i] = yc[2 * i + 1] = 0.0;
+}
+
+// x += sum_{i < j} y[c][i] V_i
+__global__ void k_gmd_update_x(int64_t M, const GmCtl* __restrict__ ctl, int mp1, const int* __restrict__ colof,
+                               const double* __restrict__ V, int64_t vstride, const double* __restrict__ y,
+                               double* x) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  const int c = colof[e], nv = ctl->j;
+  double xr = x[2 * e], xi = x[2 * e + 1];
+  for (int i = 0; i < nv; ++i) {
+    double yr = y[2 * (c * mp1 + i)], yi = y[2 * (c * mp1 + i) + 1];
+    const double* v = V + i * vstride + 2 * e;
+    xr += yr * v[0] - yi * v[1];
+    xi += yr * v[1] + yi * v[0];
+  }
+  x[2 * e] = xr;
+  x[2 * e + 1] = xi;
+}
+
 namespace {
 
 // stream-ordered scratch of one solve, released on every return path
@@ -182,8 +463,119 @@ int gm_norms(GmCore& g, const double* w, std::vector<double>& out) {
 
 }  // namespace
 
-int bem_gmres_core(bem_gm_apply_fn apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
-                   int dtype, const void* b_in, void* x_out, double tol, int max_iter, int restart, int flags,
+// device arrays of the graph-resident cycles
+struct GmDev {
+  GmCtl* ctl;
+  double *H, *cs, *sn, *gg, *relres, *nrmb, *vin;
+  int *active, *ncols;
+};
+
+// Captures one restart cycle into an executable graph (see the kernels above).
+// `capply` must issue its work on the stream it is given without
+// synchronising or allocating; it may fork onto other streams and join them
+// back.  The cycle's outer part (residual, start, WHILE node, update of x) is
+// captured first and its capture ended before the loop body is captured into
+// the WHILE node's child graph, so that streams joined by one capture are free
+// again for the other.  Every capture is closed on every return path.
+static int gm_graph_build(GmCore& g, GmDev& d, bem_gm_apply_fn capply, int m, int max_iter, double tol,
+                          cudaStream_t cs, cudaStream_t cs2, cudaGraphExec_t* exec) {
+  const int ncol = g.ncol, mp1 = m + 1;
+  const int64_t M = g.M, tot = 2 * M;
+  const unsigned gvec = nblk(M, 256);
+  cudaGraph_t body = nullptr;
+  cudaGraphConditionalHandle cond;
+  // outer part
+  BEM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  auto outer = [&]() -> int {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    BEM_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr));
+    BEM_CUDA(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+    // r0 = b - A x, |r0|, start of the cycle, V_0
+    BEM_TRY(capply(g.ctx, g.xx, g.w, cs));
+    k_gm_sub<<<nblk(tot, 256), 256, 0, cs>>>(tot, g.bb, g.w, g.w);
+    k_gmd_dots<<<dim3(GM_CHUNKS, 1, ncol), 256, 0, cs>>>(1, d.ctl, 1, g.d_off, g.d_len, g.w, 0, g.w, g.partial);
+    k_gmd_reduce<<<nblk(ncol, 128), 128, 0, cs>>>(1, d.ctl, ncol, 1, g.partial, g.nrm);
+    k_gmd_start<<<1, 256, 0, cs>>>(ncol, m, max_iter, tol, g.nrm, d.nrmb, d.ctl, d.active, d.ncols, d.relres,
+                                   g.scale, d.gg, mp1, cond);
+    k_gmd_scale<<<gvec, 256, 0, cs>>>(M, d.ctl, g.colof, g.w, g.scale, g.V, g.vstride);
+    BEM_CUDA(cudaGetLastError());
+    // the Arnoldi loop: a WHILE node after everything captured so far
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    BEM_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    BEM_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+    body = cp.conditional.phGraph_out[0];
+    BEM_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // x += V y
+    k_gmd_backsub<<<nblk(ncol, 64), 64, 0, cs>>>(ncol, m, mp1, d.ctl, d.H, d.gg, d.ncols, g.y);
+    k_gmd_update_x<<<gvec, 256, 0, cs>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.y, g.xx);
+    BEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  };
+  int rc = outer();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc == BEM_OK && e != cudaSuccess)
+    rc = bem_fail(BEM_ERR_CUDA, std::string("GMRES graph capture: ") + cudaGetErrorString(e));
+  // the loop body, captured into the WHILE node's graph
+  if (rc == BEM_OK) {
+    e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = bem_fail(BEM_ERR_CUDA, std::string("GMRES body capture: ") + cudaGetErrorString(e));
+  }
+  if (rc == BEM_OK) {
+    auto inner = [&]() -> int {
+      k_gmd_copy_vj<<<nblk(tot, 256), 256, 0, cs2>>>(tot, d.ctl, g.V, g.vstride, d.vin);
+      BEM_TRY(capply(g.ctx, d.vin, g.w, cs2));
+      const dim3 gd(GM_CHUNKS, GM_VSPLIT, ncol);
+      const unsigned gr = nblk((int64_t)ncol * mp1, 128);
+      k_gmd_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, mp1, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
+      k_gmd_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.partial, g.coef);
+      k_gmd_orth<<<gvec, 256, 0, cs2>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef, g.w);
+      k_gmd_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, mp1, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
+      k_gmd_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.partial, g.coef2);
+      k_gmd_orth<<<gvec, 256, 0, cs2>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef2, g.w);
+      k_gmd_dots<<<dim3(GM_CHUNKS, 1, ncol), 256, 0, cs2>>>(1, d.ctl, 1, g.d_off, g.d_len, g.w, 0, g.w, g.partial);
+      k_gmd_reduce<<<nblk(ncol, 128), 128, 0, cs2>>>(1, d.ctl, ncol, 1, g.partial, g.nrm);
+      k_gmd_givens<<<1, 256, 0, cs2>>>(ncol, m, mp1, tol, g.coef, g.coef2, g.nrm, d.nrmb, d.ctl, d.H, d.cs, d.sn,
+                                       d.gg, d.active, d.ncols, d.relres, g.scale, cond);
+      k_gmd_scale<<<gvec, 256, 0, cs2>>>(M, d.ctl, g.colof, g.w, g.scale, g.V, g.vstride);
+      BEM_CUDA(cudaGetLastError());
+      return BEM_OK;
+    };
+    rc = inner();
+    cudaGraph_t bg = nullptr;
+    e = cudaStreamEndCapture(cs2, &bg);
+    if (rc == BEM_OK && e != cudaSuccess)
+      rc = bem_fail(BEM_ERR_CUDA, std::string("GMRES body capture: ") + cudaGetErrorString(e));
+  }
+  if (rc == BEM_OK) {
+    e = cudaGraphInstantiate(exec, graph, 0);
+    if (e != cudaSuccess) rc = bem_fail(BEM_ERR_CUDA, std::string("GMRES graph instantiate: ") + cudaGetErrorString(e));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != BEM_OK) cudaGetLastError();  // leave no launch error behind for the host-loop fallback
+  return rc;
+}
+
+struct GmStreams {
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~GmStreams() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cs) cudaStreamDestroy(cs);
+    if (cs2) cudaStreamDestroy(cs2);
+  }
+};
+
+int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* ctx, int ncol, int64_t M,
+                   const int64_t* off, const int64_t* len, int dtype, const void* b_in, void* x_out, double tol, int max_iter, int restart, int flags,
                    int* iters_out, double* relres_out, cudaStream_t s) {
   const int m = std::max(1, std::min(restart, max_iter));
   GmScratch sc_{s, {}};
@@ -228,7 +620,49 @@ int bem_gmres_core(bem_gm_apply_fn apply, void* ctx, int ncol, int64_t M, const 
   int it_total = 0;
   bool all_conv = false;
   const unsigned gvec = nblk(M, 256);
-  while (it_total < max_iter && !all_conv) {
+  bool graph_done = false;
+  if (capture_apply && !(flags & BEM_GMRES_HOST_LOOP)) {
+    // device-resident cycles: one graph launch and one small read per cycle
+    GmDev d;
+    const int mp1 = m + 1;
+    BEM_TRY(sc_.get(&d.ctl, 1));
+    BEM_TRY(sc_.get(&d.H, (size_t)ncol * mp1 * m * 2));
+    BEM_TRY(sc_.get(&d.cs, (size_t)ncol * m));
+    BEM_TRY(sc_.get(&d.sn, (size_t)ncol * m * 2));
+    BEM_TRY(sc_.get(&d.gg, (size_t)ncol * mp1 * 2));
+    BEM_TRY(sc_.get(&d.relres, (size_t)ncol));
+    BEM_TRY(sc_.get(&d.nrmb, (size_t)ncol * 2));
+    BEM_TRY(sc_.get(&d.vin, 2 * (size_t)M));
+    BEM_TRY(sc_.get(&d.active, (size_t)ncol));
+    BEM_TRY(sc_.get(&d.ncols, (size_t)ncol));
+    BEM_CUDA(cudaMemcpyAsync(d.nrmb, g.nrm, 2 * ncol * sizeof(double), cudaMemcpyDeviceToDevice, s));  // |b|^2
+    BEM_CUDA(cudaMemsetAsync(d.ctl, 0, sizeof(GmCtl), s));
+    BEM_CUDA(cudaStreamSynchronize(s));  // the scratch is ready before the captured work can run
+    GmStreams gs;
+    BEM_CUDA(cudaStreamCreateWithFlags(&gs.cs, cudaStreamNonBlocking));
+    BEM_CUDA(cudaStreamCreateWithFlags(&gs.cs2, cudaStreamNonBlocking));
+    int rc = gm_graph_build(g, d, capture_apply, m, max_iter, tol, gs.cs, gs.cs2, &gs.exec);
+    if (rc != BEM_OK && (flags & BEM_GMRES_GRAPH_ONLY)) return rc;
+    if (rc == BEM_OK) {
+      std::vector<double> rr(ncol);
+      while (it_total < max_iter && !all_conv) {
+        BEM_CUDA(cudaGraphLaunch(gs.exec, s));
+        GmCtl hc;
+        BEM_CUDA(cudaMemcpyAsync(&hc, d.ctl, sizeof(GmCtl), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaMemcpyAsync(rr.data(), d.relres, ncol * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        it_total = hc.it;
+        all_conv = true;
+        for (int c = 0; c < ncol; ++c) {
+          relres[c] = rr[c];
+          if (!(rr[c] <= tol)) all_conv = false;
+        }
+        if (hc.j == 0) break;  // no column could take a step (non-finite residual)
+      }
+      graph_done = true;
+    }
+  }
+  while (!graph_done && it_total < max_iter && !all_conv) {
     // r0 = b - A x
     BEM_TRY(g.apply(g.ctx, g.xx, g.w, s));
     k_gm_sub<<<nblk(tot, 256), 256, 0, s>>>(tot, g.bb, g.w, g.w);
@@ -377,6 +811,15 @@ int one_op_apply(void* ctx, const double* in, double* out, cudaStream_t s) {
   BEM_TRY(bem_epilogue(o->h, o->nrhs, BEM_C128, in, out, 1, s));
   return BEM_OK;
 }
+// the same work for stream capture: the stage timers (events) stay off
+int one_op_apply_capture(void* ctx, const double* in, double* out, cudaStream_t s) {
+  OneOp* o = (OneOp*)ctx;
+  const int prof = o->h->prof_on;
+  o->h->prof_on = 0;
+  const int rc = one_op_apply(ctx, in, out, s);
+  o->h->prof_on = prof;
+  return rc;
+}
 }  // namespace
 
 // the nrhs right-hand sides of one operator: column r is [r N, (r + 1) N)
@@ -385,6 +828,6 @@ int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out,
   std::vector<int64_t> off(nrhs), len(nrhs, h->nt);
   for (int r = 0; r < nrhs; ++r) off[r] = (int64_t)r * h->nt;
   OneOp ctx{h, nrhs};
-  return bem_gmres_core(one_op_apply, &ctx, nrhs, (int64_t)nrhs * h->nt, off.data(), len.data(), dtype, b_in, x_out,
+  return bem_gmres_core(one_op_apply, one_op_apply_capture, &ctx, nrhs, (int64_t)nrhs * h->nt, off.data(), len.data(), dtype, b_in, x_out,
                         tol, max_iter, restart, flags, iters_out, relres_out, s);
 }

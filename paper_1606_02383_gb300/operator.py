@@ -171,19 +171,29 @@ class Operator:
             k = torch.tensor(self.k, dtype=torch.float64)
         return BemApplyFn.apply(self, x, y, k, vertices)
 
-    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
-        """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs])."""
+    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True, driver="graph"):
+        """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs]).
+        driver: "graph" (each restart cycle one CUDA graph, falling back to the
+        host loop if no graph can be built), "graph_only" (no fallback) or
+        "host" (the Arnoldi steps driven from the host)."""
         bs = self._prep(b, b.dtype)
         nrhs = bs.shape[0]
         x = torch.zeros_like(bs) if x0 is None else self._prep(x0, bs.dtype).clone()
         iters = ctypes.c_int(0)
         rel = (ctypes.c_double * nrhs)()
-        flags = _lib.BEM_GMRES_USE_X0 if x0 is not None else 0
+        flags = (_lib.BEM_GMRES_USE_X0 if x0 is not None else 0) | _gmres_driver_flags(driver)
         rc = self._lib.bem_gmres_solve(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
                                        int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
         if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
             _lib.check(rc)
         return x, int(iters.value), np.array(list(rel))
+
+
+def _gmres_driver_flags(driver):
+    flags = {"graph": 0, "graph_only": _lib.BEM_GMRES_GRAPH_ONLY, "host": _lib.BEM_GMRES_HOST_LOOP}
+    if driver not in flags:
+        raise ValueError("driver must be 'graph', 'graph_only' or 'host'")
+    return flags[driver]
 
 
 class BemApplyFn(torch.autograd.Function):
@@ -275,17 +285,17 @@ class Batch:
                                              _lib.BEM_APPLY_NO_HALF if no_half else 0, _stream()))
         return z
 
-    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True):
+    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True, driver="graph"):
         """GMRES for (1/2 I - D_p) x_p = b_p on every problem p at once (each with its
         own Krylov space).  b: [nrhs, N_total].  Returns (x, iterations,
-        relres[nrhs, number of problems])."""
+        relres[nrhs, number of problems]).  driver as for Operator.solve."""
         bs = (b if b.dim() == 2 else b[None]).to("cuda").contiguous()
         nrhs = bs.shape[0]
         x = torch.zeros_like(bs) if x0 is None else (x0 if x0.dim() == 2 else x0[None]).to("cuda", bs.dtype).clone()
         iters = ctypes.c_int(0)
         nprob = len(self.sizes)
         rel = (ctypes.c_double * (nrhs * nprob))()
-        flags = _lib.BEM_GMRES_USE_X0 if x0 is not None else 0
+        flags = (_lib.BEM_GMRES_USE_X0 if x0 is not None else 0) | _gmres_driver_flags(driver)
         rc = self._lib.bem_gmres_solve_batch(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
                                              int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
         if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):

@@ -71,6 +71,10 @@ def test_batch_solve_state_and_adjoint(cuda_ok):
     x, iters, relres = batch.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=200, restart=200)
     x = x.cpu().numpy()
     assert relres.shape == (2, len(probs)) and np.all(relres <= tol) and iters >= 2
+    # the host-driven loop reaches the same solutions (applies agree to FP32 rounding)
+    xh, ih, rh = batch.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=200, restart=200, driver="host")
+    assert abs(ih - iters) <= 1 and np.all(rh <= tol)
+    assert rel(x, xh.cpu().numpy()) <= 1e-5
     for p, (V, T, k) in enumerate(probs):
         a, e = batch.offsets[p], batch.offsets[p + 1]
         op = Operator(V, T, k, p=10, mode="mixed", max_nrhs=2)
