@@ -304,6 +304,7 @@ def run_ours(args, world, rank, local):
         ops = Operator(V, T, ks, p=0, eps=args.eps, mode="mixed")
         cen = V[T].mean(axis=1)
         bpw = torch.from_numpy(inputs.plane_wave(cen, ks)[None, :]).cuda()
+        _warm_solve(ops, bpw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, iters, relres = ops.solve(bpw, tol=1e-5, max_iter=300, restart=300, raise_on_fail=False)
@@ -330,7 +331,7 @@ def run_ours(args, world, rank, local):
         work = info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL  # per launch (one launch per apply)
         achieved = work / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_p2p_fmm<float>",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": "k_p2p_fmm32<1>",
                 "work_per_launch": "%d (target, source point) evaluations x %d flops"
                                    % (info["p2p_pairs"] * 3, P2P_FLOPS_PER_EVAL),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %g MHz" % sm_max}
@@ -404,6 +405,13 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
+def _warm_solve(op, b):
+    """One untimed two-step solve before a timed one: the first graph-driven
+    solve of a process pays a one-time cost (about 0.25 s) that later solves
+    do not."""
+    op.solve(b, tol=1e-30, max_iter=2, restart=2, raise_on_fail=False)
+
+
 def _resonance_safe_k(k0, radii, width=0.2, nmax=40):
     """k in [k0 - width, k0 + width] keeping every sphere (radius a) away from
     the interior Dirichlet eigenvalues: maximise min_n |j_n(k a)| / max|j_n|."""
@@ -445,6 +453,7 @@ def run_other(args):
             zd = op.apply(yd, None).cpu().numpy()[:, rows]
             ms = _timed(lambda: op.apply(yd, yd), steps, warm)
             b = torch.from_numpy(pw).cuda()
+            _warm_solve(op, b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             xs, iters, relres = op.solve(b, tol=1e-6, max_iter=300, restart=300)
@@ -491,6 +500,7 @@ def run_other(args):
                 adj += np.exp(1j * k * r) / (4 * np.pi * r)
             rhs.append(np.stack([inputs.plane_wave(c, k), adj]))
         bt_rhs = torch.from_numpy(np.concatenate(rhs, axis=1)).cuda()
+        _warm_solve(bt, bt_rhs)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         xs, iters, relres = bt.solve(bt_rhs, tol=1e-5, max_iter=300, restart=300)
@@ -531,6 +541,7 @@ def run_other(args):
         tor = time.perf_counter() - t0
         err = _rel(op.apply(x, y).cpu().numpy()[:, rows], ref)
         b = torch.from_numpy(inputs.plane_wave(c, k)[None, :]).cuda()
+        _warm_solve(op, b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         xs, iters, relres = op.solve(b, tol=1e-5, max_iter=400, restart=400, raise_on_fail=False)

@@ -509,8 +509,9 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
 // One warp per target; NR right-hand sides r0 + NR blockIdx.y + [0, NR)
 // share each loaded row.
 template <typename R, int NR>
-__global__ void k_l2p(int64_t nt, int r0, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
-                      const R* __restrict__ Lexp, int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
+__device__ __forceinline__ void l2p_body(int64_t nt, int r0, int P, const int* __restrict__ leaf_of,
+                                         const R* __restrict__ rows_r, const R* __restrict__ Lexp, int64_t exp_base,
+                                         int64_t exp_stride, double* __restrict__ zfar) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   int r = r0 + blockIdx.y * NR;
@@ -558,6 +559,19 @@ __global__ void k_l2p(int64_t nt, int r0, int P, const int* __restrict__ leaf_of
       zfar[o + 1] = (double)aim[q];
     }
   }
+}
+
+template <typename R, int NR>
+__global__ void k_l2p(int64_t nt, int r0, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
+                      const R* __restrict__ Lexp, int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
+  l2p_body<R, NR>(nt, r0, P, leaf_of, rows_r, Lexp, exp_base, exp_stride, zfar);
+}
+// FP32 with one right-hand side: eight blocks per SM (32 registers), since the
+// kernel is latency-bound on its row loads
+__global__ void __launch_bounds__(256, 8) k_l2p_f1(int64_t nt, int r0, int P, const int* __restrict__ leaf_of,
+                                                   const float* __restrict__ rows_r, const float* __restrict__ Lexp,
+                                                   int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
+  l2p_body<float, 1>(nt, r0, P, leaf_of, rows_r, Lexp, exp_base, exp_stride, zfar);
 }
 
 // ------------------------------------------------ grouped translation GEMM --
@@ -797,8 +811,13 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   bem_prof_end(h, pr, 6, nl, s);
   pr = bem_prof_begin(h, s);
   nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-    k_l2p<R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(
-        nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows, (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
+    const dim3 grid(nblk(nt * 32, 256), nchunk);
+    if constexpr (sizeof(R) == 4 && decltype(nr)::value == 1)
+      k_l2p_f1<<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const float*)h->l2p_rows, (const float*)h->Lexp,
+                                    lf.exp_base, h->exp_total, h->zfar);
+    else
+      k_l2p<R, decltype(nr)::value><<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows,
+                                                         (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
   });
   BEM_CUDA(cudaGetLastError());
   bem_prof_end(h, pr, 7, nl, s);

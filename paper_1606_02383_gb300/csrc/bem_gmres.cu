@@ -25,7 +25,23 @@
 typedef std::complex<double> hz;
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-#define GM_CHUNKS 128
+#define GM_TILE 2048      // elements per dot-product work item, at least
+#define GM_MAX_ITEMS 256  // dot-product work items per column, at most
+#define GM_VSPLIT 8       // Krylov vectors are spread over this many blocks per work item
+
+// Control block of the graph-resident cycles (below), read by the kernels of
+// the captured Arnoldi step so that one captured body serves every step j.
+struct GmCtl {
+  int j;     // Arnoldi step within the cycle: V_0 .. V_j exist
+  int jlim;  // steps allowed in this cycle: min(restart, max_iter - it)
+  int it;    // iterations over all cycles
+  int any;   // some column still active
+};
+
+// a count given by the host (fixed > 0) or the control block's j + add
+__device__ __forceinline__ int gm_count(int fixed, const GmCtl* ctl, int add) {
+  return fixed > 0 ? fixed : ctl->j + add;
+}
 
 // colof[off[c] + e] = c for every element of every column
 __global__ void k_gm_colof(const int64_t* __restrict__ off, const int64_t* __restrict__ len, int* colof) {
@@ -35,68 +51,94 @@ __global__ void k_gm_colof(const int64_t* __restrict__ off, const int64_t* __res
     colof[o + e] = c;
 }
 
-// partial[(c*nv + i)*GM_CHUNKS + chunk] = sum over the chunk of conj(V_i[c]) w[c]
-__global__ void k_gm_dots(int nv, const int64_t* __restrict__ off, const int64_t* __restrict__ len,
-                          const double* __restrict__ V, int64_t vstride, const double* __restrict__ w,
-                          double* partial) {
-  int chunk = blockIdx.x, i = blockIdx.y, c = blockIdx.z;
-  const int64_t n = len[c];
-  int64_t per = (n + GM_CHUNKS - 1) / GM_CHUNKS;
-  int64_t a = chunk * per, b = min(n, a + per);
-  const double* v = V + i * vstride + 2 * off[c];
-  const double* ww = w + 2 * off[c];
-  double sre = 0.0, sim = 0.0;
-  for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
-    double vr = v[2 * e], vi = v[2 * e + 1], wr = ww[2 * e], wi = ww[2 * e + 1];
-    sre += vr * wr + vi * wi;
-    sim += vr * wi - vi * wr;
-  }
-  __shared__ double sh[2][256];
-  sh[0][threadIdx.x] = sre;
-  sh[1][threadIdx.x] = sim;
-  __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if (threadIdx.x < st) {
-      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
-      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+// Dot products conj(V_i) . w per column, i < nv.  Work item t is chunk
+// item_k[t] of the nch[c] equal chunks of column c = item_col[t] (chunks of at
+// least GM_TILE elements, so that short columns are not split into blocks that
+// do little but reduce); partial[i * nitems + t] gets its sum.
+__global__ void __launch_bounds__(256) k_gm_dots(int fixed_nv, const GmCtl* __restrict__ ctl, int nitems,
+                                                 const int* __restrict__ item_col, const int* __restrict__ item_k,
+                                                 const int* __restrict__ nch, const int64_t* __restrict__ off,
+                                                 const int64_t* __restrict__ len, const double* __restrict__ V,
+                                                 int64_t vstride, const double* __restrict__ w, double* partial) {
+  const int nv = gm_count(fixed_nv, ctl, 1);
+  const int t = blockIdx.x, c = item_col[t], k = item_k[t];
+  const int64_t n = len[c], per = (n + nch[c] - 1) / nch[c];
+  const int64_t a = k * per, b = min(n, a + per);
+  const double2* ww = (const double2*)(w + 2 * off[c]);
+  __shared__ double sh[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = blockIdx.y; i < nv; i += GM_VSPLIT) {
+    const double2* v = (const double2*)(V + i * vstride + 2 * off[c]);
+    double sre = 0.0, sim = 0.0;
+#pragma unroll 4
+    for (int64_t e = a + threadIdx.x; e < b; e += 256) {
+      const double2 vv = v[e], x = ww[e];
+      sre += vv.x * x.x + vv.y * x.y;
+      sim += vv.x * x.y - vv.y * x.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sre += __shfl_xor_sync(0xffffffffu, sre, o);
+      sim += __shfl_xor_sync(0xffffffffu, sim, o);
+    }
+    if (lane == 0) {
+      sh[0][warp] = sre;
+      sh[1][warp] = sim;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int q = 0; q < 8; ++q) {
+        tr += sh[0][q];
+        ti += sh[1][q];
+      }
+      partial[2 * ((int64_t)i * nitems + t)] = tr;
+      partial[2 * ((int64_t)i * nitems + t) + 1] = ti;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    int64_t o = ((int64_t)c * nv + i) * GM_CHUNKS + chunk;
-    partial[2 * o] = sh[0][0];
-    partial[2 * o + 1] = sh[1][0];
-  }
 }
 
-// out[c*nv + i] = sum over chunks
-__global__ void k_gm_reduce(int nv, int ncol, const double* __restrict__ partial, double* out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nv * ncol) return;
+// out[c*mp1 + i] = sum over column c's work items, i < nv; one warp per (c, i)
+__global__ void k_gm_reduce(int fixed_nv, const GmCtl* __restrict__ ctl, int ncol, int mp1, int nitems,
+                            const int* __restrict__ item0, const int* __restrict__ nch,
+                            const double* __restrict__ partial, double* out) {
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)ncol * mp1) return;
+  const int c = (int)(wid / mp1), i = (int)(wid % mp1);
+  if (i >= gm_count(fixed_nv, ctl, 1)) return;
+  const double* p = partial + 2 * ((int64_t)i * nitems + item0[c]);
   double sre = 0.0, sim = 0.0;
-  for (int c = 0; c < GM_CHUNKS; ++c) {
-    sre += partial[2 * ((int64_t)t * GM_CHUNKS + c)];
-    sim += partial[2 * ((int64_t)t * GM_CHUNKS + c) + 1];
+  for (int t = lane; t < nch[c]; t += 32) {
+    sre += p[2 * t];
+    sim += p[2 * t + 1];
   }
-  out[2 * t] = sre;
-  out[2 * t + 1] = sim;
+  for (int o = 16; o > 0; o >>= 1) {
+    sre += __shfl_xor_sync(0xffffffffu, sre, o);
+    sim += __shfl_xor_sync(0xffffffffu, sim, o);
+  }
+  if (lane == 0) {
+    out[2 * wid] = sre;
+    out[2 * wid + 1] = sim;
+  }
 }
 
-// w -= sum_i coef[c*nv + i] V_i   on every element e of column c = colof[e]
-__global__ void k_gm_orth(int64_t M, int nv, const int* __restrict__ colof, const double* __restrict__ V,
-                          int64_t vstride, const double* __restrict__ coef, double* w) {
+// w -= sum_{i < nv} coef[c*mp1 + i] V_i   on every element e of column c = colof[e]
+__global__ void k_gm_orth(int64_t M, int fixed_nv, const GmCtl* __restrict__ ctl, int mp1,
+                          const int* __restrict__ colof, const double* __restrict__ V, int64_t vstride,
+                          const double* __restrict__ coef, double* w) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M) return;
-  const int c = colof[e];
-  double wr = w[2 * e], wi = w[2 * e + 1];
+  const int c = colof[e], nv = gm_count(fixed_nv, ctl, 1);
+  const double2* cf = (const double2*)coef + (int64_t)c * mp1;
+  double2 x = ((const double2*)w)[e];
+#pragma unroll 4
   for (int i = 0; i < nv; ++i) {
-    double cr = coef[2 * (c * nv + i)], ci = coef[2 * (c * nv + i) + 1];
-    const double* v = V + i * vstride + 2 * e;
-    wr -= cr * v[0] - ci * v[1];
-    wi -= cr * v[1] + ci * v[0];
+    const double2 q = cf[i], v = ((const double2*)(V + i * vstride))[e];
+    x.x -= q.x * v.x - q.y * v.y;
+    x.y -= q.x * v.y + q.y * v.x;
   }
-  w[2 * e] = wr;
-  w[2 * e + 1] = wi;
+  ((double2*)w)[e] = x;
 }
 
 // dst = src * scale[column] (complex src, real scale)
@@ -109,21 +151,22 @@ __global__ void k_gm_scale(int64_t M, const int* __restrict__ colof, const doubl
   dst[2 * e + 1] = src[2 * e + 1] * s;
 }
 
-// x += sum_i y[c][i] V_i
-__global__ void k_gm_update_x(int64_t M, int nv, const int* __restrict__ colof, const double* __restrict__ V,
-                              int64_t vstride, const double* __restrict__ y, double* x) {
+// x += sum_{i < nv} y[c*mp1 + i] V_i
+__global__ void k_gm_update_x(int64_t M, int fixed_nv, const GmCtl* __restrict__ ctl, int mp1,
+                              const int* __restrict__ colof, const double* __restrict__ V, int64_t vstride,
+                              const double* __restrict__ y, double* x) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= M) return;
-  const int c = colof[e];
-  double xr = x[2 * e], xi = x[2 * e + 1];
+  const int c = colof[e], nv = gm_count(fixed_nv, ctl, 0);
+  const double2* yc = (const double2*)y + (int64_t)c * mp1;
+  double2 acc = ((const double2*)x)[e];
+#pragma unroll 4
   for (int i = 0; i < nv; ++i) {
-    double yr = y[2 * (c * nv + i)], yi = y[2 * (c * nv + i) + 1];
-    const double* v = V + i * vstride + 2 * e;
-    xr += yr * v[0] - yi * v[1];
-    xi += yr * v[1] + yi * v[0];
+    const double2 q = yc[i], v = ((const double2*)(V + i * vstride))[e];
+    acc.x += q.x * v.x - q.y * v.y;
+    acc.y += q.x * v.y + q.y * v.x;
   }
-  x[2 * e] = xr;
-  x[2 * e + 1] = xi;
+  ((double2*)x)[e] = acc;
 }
 
 // r = b - z  (all complex double)
@@ -150,87 +193,6 @@ __global__ void k_c128_to_c64(int64_t m, const double* __restrict__ a, float* b)
 // a control block in device memory, so one captured body serves every j, and
 // the Givens kernel decides on the device whether the loop goes on.  The host
 // reads the residuals once per cycle.
-struct GmCtl {
-  int j;     // Arnoldi step within the cycle: V_0 .. V_j exist
-  int jlim;  // steps allowed in this cycle: min(restart, max_iter - it)
-  int it;    // iterations over all cycles
-  int any;   // some column still active
-};
-
-#define GM_VSPLIT 8
-
-__device__ __forceinline__ int gmd_nv(int fixed_nv, const GmCtl* ctl) { return fixed_nv > 0 ? fixed_nv : ctl->j + 1; }
-
-// partial[(c*mp1 + i)*GM_CHUNKS + chunk] = chunk sum of conj(V_i[c]) w[c],
-// i < nv (nv = fixed_nv, or j + 1 from the control block)
-__global__ void k_gmd_dots(int fixed_nv, const GmCtl* __restrict__ ctl, int mp1, const int64_t* __restrict__ off,
-                           const int64_t* __restrict__ len, const double* __restrict__ V, int64_t vstride,
-                           const double* __restrict__ w, double* partial) {
-  const int nv = gmd_nv(fixed_nv, ctl);
-  const int chunk = blockIdx.x, c = blockIdx.z;
-  const int64_t n = len[c];
-  const int64_t per = (n + GM_CHUNKS - 1) / GM_CHUNKS;
-  const int64_t a = chunk * per, b = min(n, a + per);
-  const double* ww = w + 2 * off[c];
-  __shared__ double sh[2][256];
-  for (int i = blockIdx.y; i < nv; i += GM_VSPLIT) {
-    const double* v = V + i * vstride + 2 * off[c];
-    double sre = 0.0, sim = 0.0;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
-      double vr = v[2 * e], vi = v[2 * e + 1], wr = ww[2 * e], wi = ww[2 * e + 1];
-      sre += vr * wr + vi * wi;
-      sim += vr * wi - vi * wr;
-    }
-    sh[0][threadIdx.x] = sre;
-    sh[1][threadIdx.x] = sim;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) {
-        sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
-        sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      int64_t o = ((int64_t)c * mp1 + i) * GM_CHUNKS + chunk;
-      partial[2 * o] = sh[0][0];
-      partial[2 * o + 1] = sh[1][0];
-    }
-    __syncthreads();
-  }
-}
-
-// out[c*mp1 + i] = sum over chunks, i < nv
-__global__ void k_gmd_reduce(int fixed_nv, const GmCtl* __restrict__ ctl, int ncol, int mp1,
-                             const double* __restrict__ partial, double* out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncol * mp1 || t % mp1 >= gmd_nv(fixed_nv, ctl)) return;
-  double sre = 0.0, sim = 0.0;
-  for (int c = 0; c < GM_CHUNKS; ++c) {
-    sre += partial[2 * ((int64_t)t * GM_CHUNKS + c)];
-    sim += partial[2 * ((int64_t)t * GM_CHUNKS + c) + 1];
-  }
-  out[2 * t] = sre;
-  out[2 * t + 1] = sim;
-}
-
-// w -= sum_{i <= j} coef[c*mp1 + i] V_i
-__global__ void k_gmd_orth(int64_t M, const GmCtl* __restrict__ ctl, int mp1, const int* __restrict__ colof,
-                           const double* __restrict__ V, int64_t vstride, const double* __restrict__ coef, double* w) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= M) return;
-  const int c = colof[e], nv = ctl->j + 1;
-  double wr = w[2 * e], wi = w[2 * e + 1];
-  for (int i = 0; i < nv; ++i) {
-    double cr = coef[2 * (c * mp1 + i)], ci = coef[2 * (c * mp1 + i) + 1];
-    const double* v = V + i * vstride + 2 * e;
-    wr -= cr * v[0] - ci * v[1];
-    wi -= cr * v[1] + ci * v[0];
-  }
-  w[2 * e] = wr;
-  w[2 * e + 1] = wi;
-}
-
 // dst = V_j (the apply's input)
 __global__ void k_gmd_copy_vj(int64_t n, const GmCtl* __restrict__ ctl, const double* __restrict__ V, int64_t vstride,
                               double* dst) {
@@ -399,24 +361,6 @@ __global__ void k_gmd_backsub(int ncol, int m, int mp1, const GmCtl* __restrict_
   for (int i = k; i < jmax; ++i) yc[2 * i] = yc[2 * i + 1] = 0.0;
 }
 
-// x += sum_{i < j} y[c][i] V_i
-__global__ void k_gmd_update_x(int64_t M, const GmCtl* __restrict__ ctl, int mp1, const int* __restrict__ colof,
-                               const double* __restrict__ V, int64_t vstride, const double* __restrict__ y,
-                               double* x) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= M) return;
-  const int c = colof[e], nv = ctl->j;
-  double xr = x[2 * e], xi = x[2 * e + 1];
-  for (int i = 0; i < nv; ++i) {
-    double yr = y[2 * (c * mp1 + i)], yi = y[2 * (c * mp1 + i) + 1];
-    const double* v = V + i * vstride + 2 * e;
-    xr += yr * v[0] - yi * v[1];
-    xi += yr * v[1] + yi * v[0];
-  }
-  x[2 * e] = xr;
-  x[2 * e + 1] = xi;
-}
-
 namespace {
 
 // stream-ordered scratch of one solve, released on every return path
@@ -446,13 +390,17 @@ struct GmCore {
   int64_t vstride;
   int64_t *d_off, *d_len;
   int* colof;
+  int mp1;                             // restart + 1: row stride of coef and y
+  int nitems;                          // dot-product work items over all columns
+  int *item_col, *item_k, *nch, *item0;  // per item: column, chunk; per column: chunks, first item
 };
 
 // norms of the ncol columns of `w` into a host array (synchronises)
 int gm_norms(GmCore& g, const double* w, std::vector<double>& out) {
-  dim3 grid(GM_CHUNKS, 1, g.ncol);
-  k_gm_dots<<<grid, 256, 0, g.s>>>(1, g.d_off, g.d_len, w, 0, w, g.partial);
-  k_gm_reduce<<<nblk(g.ncol, 128), 128, 0, g.s>>>(1, g.ncol, g.partial, g.nrm);
+  k_gm_dots<<<g.nitems, 256, 0, g.s>>>(1, nullptr, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, w, 0, w,
+                                      g.partial);
+  k_gm_reduce<<<nblk(32 * (int64_t)g.ncol, 128), 128, 0, g.s>>>(1, nullptr, g.ncol, 1, g.nitems, g.item0, g.nch,
+                                                                 g.partial, g.nrm);
   std::vector<double> t(2 * (size_t)g.ncol);
   BEM_CUDA(cudaMemcpyAsync(t.data(), g.nrm, t.size() * sizeof(double), cudaMemcpyDeviceToHost, g.s));
   BEM_CUDA(cudaStreamSynchronize(g.s));
@@ -494,8 +442,10 @@ static int gm_graph_build(GmCore& g, GmDev& d, bem_gm_apply_fn capply, int m, in
     // r0 = b - A x, |r0|, start of the cycle, V_0
     BEM_TRY(capply(g.ctx, g.xx, g.w, cs));
     k_gm_sub<<<nblk(tot, 256), 256, 0, cs>>>(tot, g.bb, g.w, g.w);
-    k_gmd_dots<<<dim3(GM_CHUNKS, 1, ncol), 256, 0, cs>>>(1, d.ctl, 1, g.d_off, g.d_len, g.w, 0, g.w, g.partial);
-    k_gmd_reduce<<<nblk(ncol, 128), 128, 0, cs>>>(1, d.ctl, ncol, 1, g.partial, g.nrm);
+    k_gm_dots<<<g.nitems, 256, 0, cs>>>(1, nullptr, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.w, 0,
+                                        g.w, g.partial);
+    k_gm_reduce<<<nblk(32 * (int64_t)ncol, 128), 128, 0, cs>>>(1, nullptr, ncol, 1, g.nitems, g.item0, g.nch,
+                                                               g.partial, g.nrm);
     k_gmd_start<<<1, 256, 0, cs>>>(ncol, m, max_iter, tol, g.nrm, d.nrmb, d.ctl, d.active, d.ncols, d.relres,
                                    g.scale, d.gg, mp1, cond);
     k_gmd_scale<<<gvec, 256, 0, cs>>>(M, d.ctl, g.colof, g.w, g.scale, g.V, g.vstride);
@@ -515,7 +465,7 @@ static int gm_graph_build(GmCore& g, GmDev& d, bem_gm_apply_fn capply, int m, in
     BEM_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     // x += V y
     k_gmd_backsub<<<nblk(ncol, 64), 64, 0, cs>>>(ncol, m, mp1, d.ctl, d.H, d.gg, d.ncols, g.y);
-    k_gmd_update_x<<<gvec, 256, 0, cs>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.y, g.xx);
+    k_gm_update_x<<<gvec, 256, 0, cs>>>(M, 0, d.ctl, mp1, g.colof, g.V, g.vstride, g.y, g.xx);
     BEM_CUDA(cudaGetLastError());
     return BEM_OK;
   };
@@ -533,16 +483,20 @@ static int gm_graph_build(GmCore& g, GmDev& d, bem_gm_apply_fn capply, int m, in
     auto inner = [&]() -> int {
       k_gmd_copy_vj<<<nblk(tot, 256), 256, 0, cs2>>>(tot, d.ctl, g.V, g.vstride, d.vin);
       BEM_TRY(capply(g.ctx, d.vin, g.w, cs2));
-      const dim3 gd(GM_CHUNKS, GM_VSPLIT, ncol);
-      const unsigned gr = nblk((int64_t)ncol * mp1, 128);
-      k_gmd_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, mp1, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
-      k_gmd_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.partial, g.coef);
-      k_gmd_orth<<<gvec, 256, 0, cs2>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef, g.w);
-      k_gmd_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, mp1, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
-      k_gmd_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.partial, g.coef2);
-      k_gmd_orth<<<gvec, 256, 0, cs2>>>(M, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef2, g.w);
-      k_gmd_dots<<<dim3(GM_CHUNKS, 1, ncol), 256, 0, cs2>>>(1, d.ctl, 1, g.d_off, g.d_len, g.w, 0, g.w, g.partial);
-      k_gmd_reduce<<<nblk(ncol, 128), 128, 0, cs2>>>(1, d.ctl, ncol, 1, g.partial, g.nrm);
+      const dim3 gd(g.nitems, GM_VSPLIT);
+      const unsigned gr = nblk(32 * (int64_t)ncol * mp1, 128);
+      k_gm_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.V,
+                                     g.vstride, g.w, g.partial);
+      k_gm_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.nitems, g.item0, g.nch, g.partial, g.coef);
+      k_gm_orth<<<gvec, 256, 0, cs2>>>(M, 0, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef, g.w);
+      k_gm_dots<<<gd, 256, 0, cs2>>>(0, d.ctl, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.V,
+                                     g.vstride, g.w, g.partial);
+      k_gm_reduce<<<gr, 128, 0, cs2>>>(0, d.ctl, ncol, mp1, g.nitems, g.item0, g.nch, g.partial, g.coef2);
+      k_gm_orth<<<gvec, 256, 0, cs2>>>(M, 0, d.ctl, mp1, g.colof, g.V, g.vstride, g.coef2, g.w);
+      k_gm_dots<<<g.nitems, 256, 0, cs2>>>(1, nullptr, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.w, 0,
+                                          g.w, g.partial);
+      k_gm_reduce<<<nblk(32 * (int64_t)ncol, 128), 128, 0, cs2>>>(1, nullptr, ncol, 1, g.nitems, g.item0, g.nch,
+                                                                 g.partial, g.nrm);
       k_gmd_givens<<<1, 256, 0, cs2>>>(ncol, m, mp1, tol, g.coef, g.coef2, g.nrm, d.nrmb, d.ctl, d.H, d.cs, d.sn,
                                        d.gg, d.active, d.ncols, d.relres, g.scale, cond);
       k_gmd_scale<<<gvec, 256, 0, cs2>>>(M, d.ctl, g.colof, g.w, g.scale, g.V, g.vstride);
@@ -590,7 +544,23 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
   BEM_TRY(sc_.get(&g.w, 2 * (size_t)M));
   BEM_TRY(sc_.get(&g.bb, 2 * (size_t)M));
   BEM_TRY(sc_.get(&g.xx, 2 * (size_t)M));
-  BEM_TRY(sc_.get(&g.partial, (size_t)ncol * (m + 1) * GM_CHUNKS * 2));
+  // dot-product work items: chunks of at least GM_TILE elements, at most GM_MAX_ITEMS per column
+  std::vector<int> nch(ncol), item0(ncol), item_col, item_k;
+  for (int c = 0; c < ncol; ++c) {
+    nch[c] = (int)std::min<int64_t>(GM_MAX_ITEMS, std::max<int64_t>(1, (len[c] + GM_TILE - 1) / GM_TILE));
+    item0[c] = (int)item_col.size();
+    for (int k = 0; k < nch[c]; ++k) {
+      item_col.push_back(c);
+      item_k.push_back(k);
+    }
+  }
+  g.mp1 = m + 1;
+  g.nitems = (int)item_col.size();
+  BEM_TRY(sc_.get(&g.item_col, (size_t)g.nitems));
+  BEM_TRY(sc_.get(&g.item_k, (size_t)g.nitems));
+  BEM_TRY(sc_.get(&g.nch, (size_t)ncol));
+  BEM_TRY(sc_.get(&g.item0, (size_t)ncol));
+  BEM_TRY(sc_.get(&g.partial, (size_t)g.nitems * (m + 1) * 2));
   BEM_TRY(sc_.get(&g.coef, (size_t)ncol * (m + 1) * 2));
   BEM_TRY(sc_.get(&g.coef2, (size_t)ncol * (m + 1) * 2));
   BEM_TRY(sc_.get(&g.y, (size_t)ncol * (m + 1) * 2));
@@ -601,6 +571,10 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
   BEM_TRY(sc_.get(&g.colof, (size_t)M));
   BEM_CUDA(cudaMemcpyAsync(g.d_off, off, ncol * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyAsync(g.d_len, len, ncol * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(g.item_col, item_col.data(), g.nitems * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(g.item_k, item_k.data(), g.nitems * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(g.nch, nch.data(), ncol * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(g.item0, item0.data(), ncol * sizeof(int), cudaMemcpyHostToDevice, s));
   k_gm_colof<<<dim3(64, ncol), 256, 0, s>>>(g.d_off, g.d_len, g.colof);
   const int64_t tot = 2 * M;
   if (dtype == BEM_C128) {
@@ -694,15 +668,18 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
       BEM_TRY(g.apply(g.ctx, vj, g.w, s));
       int nv = j + 1;
       // CGS2
-      dim3 gd(GM_CHUNKS, nv, ncol);
-      k_gm_dots<<<gd, 256, 0, s>>>(nv, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
-      k_gm_reduce<<<nblk(nv * ncol, 128), 128, 0, s>>>(nv, ncol, g.partial, g.coef);
-      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, g.colof, g.V, g.vstride, g.coef, g.w);
-      k_gm_dots<<<gd, 256, 0, s>>>(nv, g.d_off, g.d_len, g.V, g.vstride, g.w, g.partial);
-      k_gm_reduce<<<nblk(nv * ncol, 128), 128, 0, s>>>(nv, ncol, g.partial, g.coef2);
-      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, g.colof, g.V, g.vstride, g.coef2, g.w);
+      const dim3 gd(g.nitems, GM_VSPLIT);
+      const unsigned gr = nblk(32 * (int64_t)ncol * g.mp1, 128);
+      k_gm_dots<<<gd, 256, 0, s>>>(nv, nullptr, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.V,
+                                   g.vstride, g.w, g.partial);
+      k_gm_reduce<<<gr, 128, 0, s>>>(nv, nullptr, ncol, g.mp1, g.nitems, g.item0, g.nch, g.partial, g.coef);
+      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, nullptr, g.mp1, g.colof, g.V, g.vstride, g.coef, g.w);
+      k_gm_dots<<<gd, 256, 0, s>>>(nv, nullptr, g.nitems, g.item_col, g.item_k, g.nch, g.d_off, g.d_len, g.V,
+                                   g.vstride, g.w, g.partial);
+      k_gm_reduce<<<gr, 128, 0, s>>>(nv, nullptr, ncol, g.mp1, g.nitems, g.item0, g.nch, g.partial, g.coef2);
+      k_gm_orth<<<gvec, 256, 0, s>>>(M, nv, nullptr, g.mp1, g.colof, g.V, g.vstride, g.coef2, g.w);
       BEM_CUDA(cudaGetLastError());
-      std::vector<double> hc(2 * (size_t)nv * ncol), hc2(2 * (size_t)nv * ncol);
+      std::vector<double> hc(2 * (size_t)g.mp1 * ncol), hc2(2 * (size_t)g.mp1 * ncol);
       BEM_CUDA(cudaMemcpyAsync(hc.data(), g.coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       BEM_CUDA(cudaMemcpyAsync(hc2.data(), g.coef2, hc2.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       std::vector<double> wn;
@@ -716,8 +693,8 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
         }
         std::vector<hz>& Hc = H[c];
         for (int i = 0; i < nv; ++i)
-          Hc[(size_t)i * m + j] = hz(hc[2 * (c * nv + i)] + hc2[2 * (c * nv + i)],
-                                     hc[2 * (c * nv + i) + 1] + hc2[2 * (c * nv + i) + 1]);
+          Hc[(size_t)i * m + j] = hz(hc[2 * (c * g.mp1 + i)] + hc2[2 * (c * g.mp1 + i)],
+                                     hc[2 * (c * g.mp1 + i) + 1] + hc2[2 * (c * g.mp1 + i) + 1]);
         double hn = wn[c];
         Hc[(size_t)(j + 1) * m + j] = hn;
         for (int i = 0; i < j; ++i) {  // previous rotations
@@ -762,7 +739,7 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
     int nvmax = 0;
     for (int c = 0; c < ncol; ++c) nvmax = std::max(nvmax, ncols[c]);
     if (nvmax > 0) {
-      std::vector<double> yv(2 * (size_t)ncol * nvmax, 0.0);
+      std::vector<double> yv(2 * (size_t)ncol * g.mp1, 0.0);
       for (int c = 0; c < ncol; ++c) {
         int k = ncols[c];
         std::vector<hz> yy(k);
@@ -772,12 +749,12 @@ int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* c
           yy[i] = acc / H[c][(size_t)i * m + i];
         }
         for (int i = 0; i < k; ++i) {
-          yv[2 * (c * nvmax + i)] = yy[i].real();
-          yv[2 * (c * nvmax + i) + 1] = yy[i].imag();
+          yv[2 * (c * g.mp1 + i)] = yy[i].real();
+          yv[2 * (c * g.mp1 + i) + 1] = yy[i].imag();
         }
       }
       BEM_CUDA(cudaMemcpyAsync(g.y, yv.data(), yv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      k_gm_update_x<<<gvec, 256, 0, s>>>(M, nvmax, g.colof, g.V, g.vstride, g.y, g.xx);
+      k_gm_update_x<<<gvec, 256, 0, s>>>(M, nvmax, nullptr, g.mp1, g.colof, g.V, g.vstride, g.y, g.xx);
       BEM_CUDA(cudaGetLastError());
       BEM_CUDA(cudaStreamSynchronize(s));
     }
