@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
 // mode: about 130 terms per row, each already a small correction) and added to
 // the FP64 near-field sum.  NR right-hand sides r0 + NR blockIdx.y + [0, NR)
 // share each loaded value pair.
+#define CORR_U 2
 template <typename V4, typename R, int NR>
 __global__ void k_correction(int64_t nt, int r0, const int* __restrict__ ptr, const int* __restrict__ col,
                              const V4* __restrict__ val, const V4* __restrict__ dens, double* __restrict__ zn) {
@@ -383,15 +384,29 @@ __global__ void k_correction(int64_t nt, int r0, const int* __restrict__ ptr, co
   R are[NR], aim[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) are[j] = aim[j] = 0;
-  int e1 = ptr[i + 1];
-  for (int e = ptr[i] + lane; e < e1; e += 32) {
-    V4 c = val[e];
-    int64_t cj = col[e];
+  // the value and column loads of CORR_U entries per lane go out before any of
+  // their density gathers (a row holds about 130 entries: two or three rounds)
+  const int e1 = ptr[i + 1];
+  for (int eb = ptr[i] + lane; eb < e1; eb += 32 * CORR_U) {
+    V4 c[CORR_U];
+    int cj[CORR_U];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      V4 d = dr[(int64_t)j * nt + cj];
-      are[j] += c.x * d.x - c.y * d.y - c.z * d.z + c.w * d.w;
-      aim[j] += c.x * d.y + c.y * d.x - c.z * d.w - c.w * d.z;
+    for (int u = 0; u < CORR_U; ++u) {
+      const int e = eb + 32 * u;
+      if (e < e1) {
+        c[u] = val[e];
+        cj[u] = col[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CORR_U; ++u) {
+      if (eb + 32 * u >= e1) break;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        V4 d = dr[(int64_t)j * nt + cj[u]];
+        are[j] += c[u].x * d.x - c[u].y * d.y - c[u].z * d.z + c[u].w * d.w;
+        aim[j] += c[u].x * d.y + c[u].y * d.x - c[u].z * d.w - c[u].w * d.z;
+      }
     }
   }
 #pragma unroll
@@ -433,7 +448,7 @@ __global__ void k_p2m(int nleaf, int64_t nt, int P, const int* __restrict__ bsta
 }
 
 // FP32: one thread per coefficient pair (2t, 2t+1) with 16-byte loads of the
-// element rows, elements in rounds of 4 so that their loads are in flight
+// element rows, elements in rounds of P2M_U so that their loads are in flight
 // together; NR right-hand sides r0 + NR blockIdx.y + [0, NR) share each row.
 // A row [a (P complex) | b (P complex)] starts on a 16-byte boundary; b does
 // too when P is even, otherwise it is read as two float2.
@@ -451,10 +466,11 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc0[q] = acc1[q] = make_float2(0.f, 0.f);
   const int j0 = bstart[b], j1 = bend[b];
-  for (int jb = j0; jb < j1; jb += 4) {
-    float4 A[4], B[4], D[4][NR];
+  constexpr int P2M_U = NR == 1 ? 8 : 4;  // elements per round
+  for (int jb = j0; jb < j1; jb += P2M_U) {
+    float4 A[P2M_U], B[P2M_U], D[P2M_U][NR];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < P2M_U; ++u) {
       const int j = jb + u;
       if (j >= j1) {
         A[u] = B[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -481,7 +497,7 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
       for (int q = 0; q < NR; ++q) D[u][q] = dr[(int64_t)q * nt + j];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < P2M_U; ++u) {
       const float4 a = A[u], bq = B[u];
 #pragma unroll
       for (int q = 0; q < NR; ++q) {
@@ -524,7 +540,9 @@ __device__ __forceinline__ void l2p_body(int64_t nt, int r0, int P, const int* _
 #pragma unroll
   for (int q = 0; q < NR; ++q) are[q] = aim[q] = 0;
   if (sizeof(R) == 4 && (P & 1) == 0) {
-    // P even: the row starts on a 16-byte boundary, two coefficients per load
+    // P even: the row starts on a 16-byte boundary, two coefficients per load;
+    // two rounds unrolled so that their loads are in flight together
+#pragma unroll 2
     for (int e2 = lane; 2 * e2 < P; e2 += 32) {
       const float4 x = *(const float4*)((const float*)row + 4 * e2);
 #pragma unroll

@@ -136,6 +136,13 @@ struct GroupedOp {
   // tensor-core form (mixed mode): A packed per (row tile, k stage), jobs (group, pair0, npairs, row tile)
   // source level of the pairs (its expansions are prepared, reflected and split, before every launch)
   int src_level = -1;
+  int tc_kslice = 16;  // K stages per tensor-core job
+  // a second job list with shorter K slices, for launches with too few CTAs
+  // for the SMs (small operators at one right-hand side)
+  int4* d_tc_jobs_split = nullptr;
+  int n_tc_jobs_split = 0;
+  int tc_kslice_split = 16;
+  int64_t tc_want = 0;  // CTAs that give every SM two
   int* d_prep_row = nullptr;            // [npairs] row (flag * nbox + box) of the prepared source
   float* tcA = nullptr;
   int64_t* d_tc_off = nullptr;

@@ -35,7 +35,7 @@
 #define TC_M 128        // pairs per tile (MMA M)
 #define TC_NMAX 256     // real output rows per tile (MMA N, multiple of 16)
 #define TC_KS 16        // real K per stage (2 MMA k-steps of 8)
-#define TC_KSLICE 16    // stages per job
+#define TC_KSLICE 16    // stages per job, at most
 #define TC_THREADS 256
 #define TC_EBYTES (TC_M * TC_KS * 4)                     // one of hi / lo gathered stage
 #define TC_TBYTES_MAX (TC_NMAX * TC_KS * 4)             // one of hi / lo matrix stage
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
     const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
     const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep, int R2,
-    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int* err) {
+    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const int Po = grows[g], Pi = gcols[g];
   const int N = tc_ntile_width(2 * Po, nt);
   const int nks = (2 * Pi + TC_KS - 1) / TC_KS;
-  const int ks0 = (job.z >> 8) * TC_KSLICE, ks1 = min(nks, ks0 + TC_KSLICE);
+  const int ks0 = (job.z >> 8) * kslice, ks1 = min(nks, ks0 + kslice);
   const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
   const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
   float* D = dst + 2 * (int64_t)r * exp_stride;
@@ -439,15 +439,47 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
                                         nnt, op.tcA + off[g]);
     BEM_CUDA(cudaGetLastError());
   }
-  std::vector<int4> jobs;
+  // K stages per job: TC_KSLICE.  When the operator has too few (pair tile,
+  // row tile) jobs to give every SM two CTAs, a second job list with shorter
+  // slices (down to 2 stages) lets the small translations (M2M, L2L, the
+  // upper M2L levels) spread their stage-by-stage latency over more CTAs; only
+  // single-rhs launches use it.
+  int64_t base = 0;
+  int nks_max = 1;
   for (int g = 0; g < op.ngroups; ++g) {
     int np = op.pair_start[g + 1] - op.pair_start[g];
-    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX;
-    int nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
-    for (int p0 = 0; p0 < np; p0 += TC_M)
-      for (int nt = 0; nt < nnt; ++nt)
-        for (int sl = 0; sl * TC_KSLICE < nks; ++sl)
-          jobs.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_M, np - p0) | (sl << 8), nt));
+    base += (int64_t)((np + TC_M - 1) / TC_M) * ((2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX);
+    nks_max = std::max(nks_max, (2 * op.cols[g] + TC_KS - 1) / TC_KS);
+  }
+  int nsm = 0;
+  BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+  op.tc_want = 2 * (int64_t)std::max(nsm, 1);
+  int ksplit = TC_KSLICE;
+  if (base > 0 && base * ((nks_max + TC_KSLICE - 1) / TC_KSLICE) < op.tc_want) {
+    const int64_t slices = (op.tc_want + base - 1) / base;
+    ksplit = (int)std::max<int64_t>(2, std::min<int64_t>(TC_KSLICE, (nks_max + slices - 1) / slices));
+  }
+  auto make_jobs = [&](int kslice) {
+    std::vector<int4> js;
+    for (int g = 0; g < op.ngroups; ++g) {
+      int np = op.pair_start[g + 1] - op.pair_start[g];
+      int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX;
+      int nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
+      for (int p0 = 0; p0 < np; p0 += TC_M)
+        for (int nt = 0; nt < nnt; ++nt)
+          for (int sl = 0; sl * kslice < nks; ++sl)
+            js.push_back(make_int4(g, op.pair_start[g] + p0, std::min(TC_M, np - p0) | (sl << 8), nt));
+    }
+    return js;
+  };
+  std::vector<int4> jobs = make_jobs(TC_KSLICE);
+  op.tc_kslice = TC_KSLICE;
+  if (ksplit < TC_KSLICE) {
+    std::vector<int4> js = make_jobs(ksplit);
+    op.tc_kslice_split = ksplit;
+    op.n_tc_jobs_split = (int)js.size();
+    BEM_TRY(bem_alloc(h, &op.d_tc_jobs_split, js.size()));
+    BEM_CUDA(cudaMemcpyAsync(op.d_tc_jobs_split, js.data(), js.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   }
   op.n_tc_jobs = (int)jobs.size();
   BEM_TRY(bem_alloc(h, &op.d_tc_jobs, std::max<size_t>(jobs.size(), 1)));
@@ -472,10 +504,14 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
     k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r0, nc,
                                                         h->exp_total, h->prep);
     BEM_CUDA(cudaGetLastError());
-    k_grouped_tc<<<op.n_tc_jobs * nc, TC_THREADS, TC_SMEM, s>>>(
-        op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA, op.d_prep_row, op.d_dst_off, op.d_flags,
-        h->prep, R2, nc, 8 * sl.nbox, (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total,
-        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, h->d_err);
+    // one right-hand side and too few CTAs for the SMs: the job list with
+    // shorter K slices (with 2-4 right-hand sides per launch the extra
+    // slices' atomics cost more than the added CTAs give back)
+    const bool split = nc == 1 && op.n_tc_jobs_split > 0;
+    k_grouped_tc<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, TC_SMEM, s>>>(
+        split ? op.d_tc_jobs_split : op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
+        op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, R2, nc, 8 * sl.nbox, (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total,
+        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, split ? op.tc_kslice_split : op.tc_kslice, h->d_err);
     BEM_CUDA(cudaGetLastError());
     *launches += 2;
   }
