@@ -209,6 +209,44 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def stage_rooflines(stages, steps, info, n, fp32_peak, tensor_peak, hbm_peak, apply_ms):
+    """Every stage against its own bound (live CUDA-event times per apply), and
+    the apply against the sum of the stages' lower bounds.  Algorithmic work:
+    P2P 36 flops per (target, source point); translations 8 P_out P_in flops
+    per pair; stream stages their compulsory bytes (rows, values, densities and
+    results read or written once)."""
+    P = (info["p_leaf"] + 1) ** 2
+    work = {
+        "p2p": ("alu", info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL, fp32_peak * 1e12),
+        "m2m": ("tensor", info["m2m_flops"], tensor_peak * 1e12),
+        "m2l": ("tensor", info["m2l_flops"], tensor_peak * 1e12),
+        "l2l": ("tensor", info["l2l_flops"], tensor_peak * 1e12),
+        # value (16 B) + column (4 B) per entry, densities once, near sum read and written
+        "correction": ("hbm", info["corr_nnz"] * 20 + n * 16 + n * 32, hbm_peak * 1e9),
+        # 2 P complex64 rows per element, densities, leaf multipoles written
+        "p2m": ("hbm", n * 2 * P * 8 + n * 16 + info["n_leaves"] * P * 8, hbm_peak * 1e9),
+        # P complex64 row per element, leaf locals, far sum written
+        "l2p": ("hbm", n * P * 8 + info["n_leaves"] * P * 8 + n * 16, hbm_peak * 1e9),
+        # x and y in, permutation and weights, densities out
+        "prologue": ("hbm", n * (2 * 16 + 12 + 16), hbm_peak * 1e9),
+        # near and far sums and x in, permutation, z out
+        "epilogue": ("hbm", n * (3 * 16 + 4 + 16), hbm_peak * 1e9),
+    }
+    out, bound_ms = {}, 0.0
+    for st, (bound, w, peak) in work.items():
+        if st not in stages or stages[st][0] <= 0:
+            continue
+        ms = stages[st][0] / steps
+        unit = "GB/s" if bound == "hbm" else "TFLOP/s"
+        scale = 1e9 if bound == "hbm" else 1e12
+        out[st] = {"bound": bound, "ms": round(ms, 4), "achieved": w / (ms * 1e-3) / scale, "peak": peak / scale,
+                   "unit": unit, "frac": w / (ms * 1e-3) / peak, "work": w}
+        bound_ms += w / peak * 1e3
+    out["apply"] = {"sum_of_stage_bounds_ms": round(bound_ms, 4), "measured_ms": round(apply_ms, 4),
+                    "frac": bound_ms / apply_ms}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1606_02383_gb300 import inputs
@@ -313,12 +351,40 @@ def run_ours(args, world, rank, local):
         ops.close()
         also = {"multi_rhs": multi, "gmres_plane_wave": {"ka": ks, "tol": 1e-5, "iterations": iters,
                                                          "relres": float(relres[0]), "seconds": gm_s}}
+        # the same sphere at ka = 1 and 5 (mixed), and the all-FP64 FMM at the headline ka:
+        # throughput, setup and the error on 500 oracle rows
+        import oracle
+        rows500 = rows[:500]
+        ref500 = oracle.apply(V, T, k, x=x, y=y, rows=rows500)
+        for tag, kk, mode, reps in (("ka1", 1.0, "mixed", 20), ("ka5", 5.0, "mixed", 20), ("fp64_fmm", k, "fp64", 3)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            o2 = Operator(V, T, kk, p=0, eps=args.eps, mode=mode)
+            torch.cuda.synchronize()
+            su = time.perf_counter() - t0
+            zz = o2.apply(xd, yd)
+            o2.apply(xd, yd)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                zz = o2.apply(xd, yd)
+                b.record()
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            rf = ref500 if kk == k else oracle.apply(V, T, kk, x=x, y=y, rows=rows500)
+            err = float(np.linalg.norm(zz.cpu().numpy()[0, rows500] - rf[0]) / np.linalg.norm(rf[0]))
+            also[tag] = {"ka": kk, "mode": mode, "ms_per_apply": tot / reps, "matvecs_per_s": reps * 1e3 / tot,
+                         "setup_s": round(su, 3), "rel_err_vs_oracle_500_rows": err,
+                         "orders_level2_to_leaf": [o2.order_of_level(l) for l in range(2, o2.info("leaf_level") + 1)]}
+            o2.close()
 
     if rank != 0:
         return
     peaks, peak_src = measured_peaks()
     info = {kk: op.info(kk) for kk in ("leaf_level", "n_leaves", "p2p_pairs", "corr_nnz", "m2l_pairs",
-                                       "m2l_flops", "p_leaf", "p_top", "device_bytes")}
+                                       "m2l_flops", "m2m_flops", "l2l_flops", "p_leaf", "p_top", "device_bytes")}
     orders = [op.order_of_level(l) for l in range(2, info["leaf_level"] + 1)]
     # roofline of the dominant stage (average launch duration from the live events)
     dom = max(stages, key=lambda s: stages[s][0])
@@ -366,6 +432,8 @@ def run_ours(args, world, rank, local):
                 "work_per_apply": "%.4g flops (8 P_l^2 per V-list pair)" % info["m2l_flops"],
                 "peak_source": "%s BF16 %.0f TFLOP/s x 1.1/2.25 = TF32 %.0f, / 3 for 3xTF32"
                                % (peak_src, float(peaks.get("bf16_tflops", 1900.0)), tf32_peak)}
+    roof_stages = stage_rooflines(stages, steps, info, n, fp32_peak, tf32_peak / 3.0, float(peaks.get("hbm_gbs", 6800.0)),
+                                  total_ms_max / args.steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -376,6 +444,7 @@ def run_ours(args, world, rank, local):
                                             "wall_s_timed_region": round(wall, 4)}),
             "roofline": roof,
             "roofline_m2l": roof_m2l,
+            "roofline_stages": roof_stages,
             "also": also,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 16, "d2h_bytes_per_step": n * 16},

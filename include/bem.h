@@ -301,6 +301,8 @@ typedef enum {
   BEM_INFO_DEVICE_BYTES = 10,
   BEM_INFO_P2M_BYTES = 11,   /* bytes of the stored P2M + L2P rows */
   BEM_INFO_LAUNCHES_LAST_APPLY = 12, /* kernels the last bem_apply launched (memsets excluded) */
+  BEM_INFO_M2M_FLOPS = 13,   /* 8 P_child P_parent per child box summed over levels (one rhs) */
+  BEM_INFO_L2L_FLOPS = 14,   /* 8 P_parent P_child per child box summed over levels (one rhs) */
   BEM_INFO_ORDER_OF_LEVEL = 100 /* + level: expansion order of that level */
 } bem_info_key;
 int bem_info(bem_handle* h, int key, int64_t* value);

@@ -355,6 +355,13 @@ int bem_info(bem_handle* h, int key, int64_t* value) {
     case BEM_INFO_MODE: *value = h->mode; return BEM_OK;
     case BEM_INFO_DEVICE_BYTES: *value = (int64_t)h->bytes; return BEM_OK;
     case BEM_INFO_LAUNCHES_LAST_APPLY: *value = h->launches_last_apply; return BEM_OK;
+    case BEM_INFO_M2M_FLOPS:
+    case BEM_INFO_L2L_FLOPS: {
+      int64_t v = 0;
+      for (int l = 2; l < L; ++l) v += (key == BEM_INFO_M2M_FLOPS ? h->m2m[l] : h->l2l[l]).flops;
+      *value = v;
+      return BEM_OK;
+    }
     case BEM_INFO_P2M_BYTES: {
       int64_t P = (L >= 2) ? h->lev[L].P : 0;
       *value = h->nt * 3 * P * (bem_is_fp64(h) ? 16 : 8);
