@@ -540,9 +540,7 @@ __device__ __forceinline__ void l2p_body(int64_t nt, int r0, int P, const int* _
 #pragma unroll
   for (int q = 0; q < NR; ++q) are[q] = aim[q] = 0;
   if (sizeof(R) == 4 && (P & 1) == 0) {
-    // P even: the row starts on a 16-byte boundary, two coefficients per load;
-    // two rounds unrolled so that their loads are in flight together
-#pragma unroll 2
+    // P even: the row starts on a 16-byte boundary, two coefficients per load
     for (int e2 = lane; 2 * e2 < P; e2 += 32) {
       const float4 x = *(const float4*)((const float*)row + 4 * e2);
 #pragma unroll
