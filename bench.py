@@ -432,6 +432,15 @@ def run_ours(args, world, rank, local):
                 "work_per_apply": "%.4g flops (8 P_l^2 per V-list pair)" % info["m2l_flops"],
                 "peak_source": "%s BF16 %.0f TFLOP/s x 1.1/2.25 = TF32 %.0f, / 3 for 3xTF32"
                                % (peak_src, float(peaks.get("bf16_tflops", 1900.0)), tf32_peak)}
+    # the library's own probes of the FP32 and TF32 pipes, reported beside the
+    # rule-based peaks (derived FP32; measured BF16 x the nominal TF32 ratio)
+    from paper_1606_02383_gb300 import peaks as pk
+    probe_fp32, probe_tf32 = pk.measure("fp32"), pk.measure("tf32")
+    roof_m2l.update({"probe_peak": probe_tf32 / 3.0, "probe_frac": m2l_achieved / (probe_tf32 / 3.0),
+                     "probe": "bem_peak_probe: tcgen05 TF32 MMAs, M=128 N=256 K=8, %.0f TFLOP/s, / 3" % probe_tf32})
+    if roof["bound"] == "alu":
+        roof.update({"probe_peak": probe_fp32, "probe_frac": roof["achieved"] / probe_fp32,
+                     "probe": "bem_peak_probe: f32x2 FMA chains"})
     roof_stages = stage_rooflines(stages, steps, info, n, fp32_peak, tf32_peak / 3.0, float(peaks.get("hbm_gbs", 6800.0)),
                                   total_ms_max / args.steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

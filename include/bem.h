@@ -331,6 +331,23 @@ int bem_profile_read(bem_handle* h, double* ms, int64_t* launches, int nstages);
  */
 const char* bem_last_error(void);
 
+/*
+ * bem_peak_probe -- microbenchmark of a compute pipe, for roofline
+ * denominators that no vendor figure fixes on this part (the paper has no
+ * counterpart; it is a measuring tool of this library).
+ *   which  : 0 = FP32 through packed f32x2 FMAs (8 independent chains per
+ *            thread, 8 blocks of 256 threads per SM);
+ *            1 = dense TF32 through tcgen05.mma (M = 128, N = 256, K = 8,
+ *            operands resident in shared memory, one TMEM accumulator per CTA,
+ *            2 CTAs per SM).
+ *   iters  : iterations per thread (0) or MMAs per CTA (1), 1 .. 2^20.
+ *   tflops : receives the rate of the second of two launches, in TFLOP/s
+ *            (an FMA counts 2 flops).
+ * Allocates two small stream-ordered buffers and synchronises `stream`.
+ * A bounded device wait that expires returns BEM_ERR_TIMEOUT.
+ */
+int bem_peak_probe(int which, int iters, double* tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -517,3 +517,132 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   }
   return BEM_OK;
 }
+
+// ------------------------------------------------------ peak microbenchmarks --
+// Roofline denominators that no driver measurement covers: the dense TF32
+// tensor rate of tcgen05 (the translations' 3xTF32 runs three products per
+// algorithmic flop) and the FP32 rate of packed f32x2 FMAs (the P2P's pipe).
+
+// Every CTA issues `iters` back-to-back M = 128, N = 256, K = 8 TF32 MMAs
+// from one thread into one TMEM accumulator, with both operands resident in
+// shared memory, then commits once and waits (bounded) for completion.
+__global__ void __launch_bounds__(128, 1) k_peak_tc(int iters, int* err, float* sink) {
+  __shared__ __align__(1024) unsigned char ops[TC_M * 8 * 4 + TC_NMAX * 8 * 4];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < (int)(sizeof(ops) / 4); i += blockDim.x) ((float*)ops)[i] = tf32_round(1.0f + 1e-3f * (i & 7));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TC_NMAX));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands written by threads, read by the MMA
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  bool ok = true;
+  if (tid == 0) {
+    const uint64_t a = smem_desc(smem_u32(ops)), b = smem_desc(smem_u32(ops + TC_M * 8 * 4));
+    const uint32_t idesc = instr_desc(TC_NMAX);
+    for (int i = 0; i < iters; ++i) mma_tf32(tmem, a, b, idesc, i > 0 ? 1u : 0u);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar))
+                 : "memory");
+    ok = mbar_wait(smem_u32(&bar), 0);
+    if (!ok) atomicOr(err, BEM_DEVERR_TIMEOUT);
+    s_ok = ok ? 1 : 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {  // one accumulator value leaves the kernel, so the work cannot be dropped
+    uint32_t v;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(tmem) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (tid == 0 && s_ok) sink[blockIdx.x] = __uint_as_float(v);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
+}
+
+// Every thread runs 8 independent chains of packed f32x2 FMAs (4 flops each).
+__global__ void __launch_bounds__(256) k_peak_fp32(int iters, float* sink) {
+  unsigned long long acc[8];
+  const float s = 1.0f + 1e-7f * threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float v = s + j;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(acc[j]) : "f"(v), "f"(v));
+  }
+  unsigned long long m, c;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(m) : "f"(0.9999999f), "f"(0.9999999f));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(1e-7f), "f"(1e-7f));
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(acc[j]) : "l"(m), "l"(c));
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[j]));
+    t += lo + hi;
+  }
+  if (t == 12345.f) sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+extern "C" int bem_peak_probe(int which, int iters, double* tflops, void* stream) {
+  bem_set_error("");
+  if (!tflops || iters < 1 || iters > (1 << 20) || (which != 0 && which != 1))
+    return bem_fail(BEM_ERR_INVALID_ARG, "which must be 0 (FP32) or 1 (TF32), 1 <= iters <= 2^20, tflops non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  BEM_CUDA(cudaGetDevice(&dev));
+  BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = which == 1 ? 2 * nsm : 8 * nsm, threads = which == 1 ? 128 : 256;
+  float* sink = nullptr;
+  int* err = nullptr;
+  BEM_CUDA(cudaMallocAsync((void**)&sink, sizeof(float) * blocks * threads, s));
+  BEM_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = BEM_OK;
+  float ms = 0.f;
+  int herr = 0;
+  auto run = [&]() -> int {
+    BEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up, the second is timed
+      BEM_CUDA(cudaEventRecord(e0, s));
+      if (which == 1)
+        k_peak_tc<<<blocks, threads, 0, s>>>(iters, err, sink);
+      else
+        k_peak_fp32<<<blocks, threads, 0, s>>>(iters, sink);
+      BEM_CUDA(cudaGetLastError());
+      BEM_CUDA(cudaEventRecord(e1, s));
+    }
+    BEM_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    BEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return BEM_OK;
+  };
+  rc = run();
+  cudaFreeAsync(sink, s);
+  cudaFreeAsync(err, s);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BEM_OK) return rc;
+  if (herr) return bem_fail(BEM_ERR_TIMEOUT, "a bounded wait of the tensor-core probe expired");
+  const double flops = which == 1 ? (double)blocks * iters * 2.0 * TC_M * TC_NMAX * 8
+                                  : (double)blocks * threads * iters * 8 * 4;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return BEM_OK;
+}
