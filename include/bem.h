@@ -203,6 +203,28 @@ int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, c
              double* dk, void* stream);
 
 /*
+ * bem_eval_points -- the field of the densities at points off the surface:
+ *   u(p) = sum_j S(p, j) y_j - D(p, j) x_j
+ * (the representation formula's layer potentials, Section 2.1, at field
+ * points instead of collocation points; the same rule-defined entries: R_2
+ * within 2 h_j of element j's centroid, R_1 within 4 h_j, R_0 beyond; no
+ * free term and no self term).
+ *   x, y     : densities [nrhs][N] (device, dtype), either may be NULL.
+ *   points   : [npoints][3] FP64 coordinates (device).  They must not lie on
+ *              the surface.  Consecutive points should be close to each other
+ *              (a lattice in its natural order, or points sorted along a
+ *              curve): each block of 128 points shares one FP32 origin.
+ *   out      : [nrhs][npoints] complex (device, dtype).
+ *   flags    : 0.
+ * Cost: a direct sum over all elements for every point (O(npoints N)), in the
+ * handle's precision: FP32 sums with FP64 between tiles in the mixed modes,
+ * FP64 in the FP64 modes; pairs within 4 h_j take the refined rule from the
+ * FP64 geometry.  Stream-ordered; no allocation, no host synchronisation.
+ */
+int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
+                    int64_t npoints, void* out, int flags, void* stream);
+
+/*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
  * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
  *   b          : right-hand sides [nrhs][N] (device).

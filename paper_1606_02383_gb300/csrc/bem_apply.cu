@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "bem_common.cuh"
+#include "bem_rules.cuh"
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -364,6 +365,158 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
     zn[o] = sre;
     zn[o + 1] = sim;
   }
+}
+
+// ------------------------------------------------- off-surface evaluation --
+// u(p) = sum_j S(p, j) y_j - D(p, j) x_j at points p off the surface, with the
+// entries' rules: R_L (L = 2 within 2 h_j, 1 within 4 h_j of the centroid),
+// R_0 beyond.  One point per thread; all elements stream through shared
+// memory, relative to the block's first point (subtracted in FP64 once per
+// element and block), so that the R_0 sums run in the operator's precision.
+// A pair within 4 h_j instead takes the refined rule from the FP64 geometry,
+// relative to its point.  FP32 partial sums go into FP64 after every tile.
+#define EV_THREADS 128
+template <typename R>
+__device__ __forceinline__ void eval_near(const double* X, int j, double k, const double* __restrict__ cent,
+                                          const double* __restrict__ qpt, const double* __restrict__ nrm,
+                                          const double* __restrict__ area, const double* __restrict__ hmax,
+                                          const double* __restrict__ wgt, const typename V4of<R>::T& dd, R& are,
+                                          R& aim) {
+  Tri64 t;
+  load_tri64(qpt, nrm, cent, area, hmax, j, t);
+  const double c0 = t.c[0] - X[0], c1 = t.c[1] - X[1], c2 = t.c[2] - X[2];
+  const double dist = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  const int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+  const double iw = 1.0 / wgt[j];
+  if constexpr (sizeof(R) == 4) {
+    Tri32 tf;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) tf.v[a][c] = (float)(t.v[a][c] - X[c]);
+    for (int c = 0; c < 3; ++c) tf.n[c] = (float)t.n[c];
+    tf.area = (float)t.area;
+    zf sv = cmk(0.f, 0.f), dv = sv;
+    rule_refined32(tf, L, (float)k, sv, dv);
+    const float w = (float)iw;
+    const float yr = dd.x * w, yi = dd.y * w, xr = dd.z * w, xi = dd.w * w;
+    are += sv.re * yr - sv.im * yi - (dv.re * xr - dv.im * xi);
+    aim += sv.re * yi + sv.im * yr - (dv.re * xi + dv.im * xr);
+  } else {
+    zd sv = cmk(0.0, 0.0), dv = sv;
+    rule_refined(X, t, L, k, sv, dv);
+    const double yr = dd.x * iw, yi = dd.y * iw, xr = dd.z * iw, xi = dd.w * iw;
+    are += sv.re * yr - sv.im * yi - (dv.re * xr - dv.im * xi);
+    aim += sv.re * yi + sv.im * yr - (dv.re * xi + dv.im * xr);
+  }
+}
+
+template <typename R, typename Rout>
+__global__ void __launch_bounds__(EV_THREADS) k_eval_points(int64_t nt, int64_t np, double k,
+                                                            const double* __restrict__ pts,
+                                                            const double* __restrict__ cent,
+                                                            const double* __restrict__ qpt,
+                                                            const double* __restrict__ nrm,
+                                                            const double* __restrict__ area,
+                                                            const double* __restrict__ hmax,
+                                                            const double* __restrict__ wgt,
+                                                            const typename V4of<R>::T* __restrict__ dens,
+                                                            Rout* __restrict__ out) {
+  typedef typename V4of<R>::T V4;
+  __shared__ V4 s_q[EV_THREADS][3];  // quadrature points relative to the origin, normal in .w
+  __shared__ V4 s_c[EV_THREADS];     // centroid relative to the origin, (4 h)^2 in .w
+  __shared__ V4 s_d[EV_THREADS];     // weighted densities (sigma, tau)
+  const int r = blockIdx.y;
+  const int64_t p0 = blockIdx.x * (int64_t)EV_THREADS, p = p0 + threadIdx.x;
+  const bool live = p < np;
+  const double o[3] = {pts[3 * p0], pts[3 * p0 + 1], pts[3 * p0 + 2]};
+  const int64_t pp = live ? p : p0;
+  const double X[3] = {pts[3 * pp], pts[3 * pp + 1], pts[3 * pp + 2]};
+  const R tx = (R)(X[0] - o[0]), ty = (R)(X[1] - o[1]), tz = (R)(X[2] - o[2]);
+  const V4* dr = dens + (int64_t)r * nt;
+  const R kr = (R)k;
+  double sre = 0.0, sim = 0.0;
+  for (int64_t e0 = 0; e0 < nt; e0 += EV_THREADS) {
+    const int ne = (int)min((int64_t)EV_THREADS, nt - e0);
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      const int64_t j = e0 + threadIdx.x;
+      for (int q = 0; q < 3; ++q) {
+        V4 v;
+        v.x = (R)(qpt[9 * j + 3 * q] - o[0]);
+        v.y = (R)(qpt[9 * j + 3 * q + 1] - o[1]);
+        v.z = (R)(qpt[9 * j + 3 * q + 2] - o[2]);
+        v.w = (R)nrm[3 * j + q];
+        s_q[threadIdx.x][q] = v;
+      }
+      const double h4 = 4.0 * hmax[j];
+      V4 c;
+      c.x = (R)(cent[3 * j] - o[0]);
+      c.y = (R)(cent[3 * j + 1] - o[1]);
+      c.z = (R)(cent[3 * j + 2] - o[2]);
+      c.w = (R)(h4 * h4);
+      s_c[threadIdx.x] = c;
+      s_d[threadIdx.x] = dr[j];
+    }
+    __syncthreads();
+    R are = 0, aim = 0;
+    for (int e = 0; e < ne; ++e) {
+      const V4 c = s_c[e];
+      const R cx = c.x - tx, cy = c.y - ty, cz = c.z - tz;
+      const V4 dd = s_d[e];
+      if (cx * cx + cy * cy + cz * cz < c.w) {
+        eval_near<R>(X, (int)(e0 + e), k, cent, qpt, nrm, area, hmax, wgt, dd, are, aim);
+        continue;
+      }
+      const V4 q0 = s_q[e][0], q1 = s_q[e][1], q2 = s_q[e][2];
+      const R nx = q0.w, ny = q1.w, nz = q2.w;
+      p2p_eval(q0.x - tx, q0.y - ty, q0.z - tz, nx, ny, nz, kr, dd, are, aim);
+      p2p_eval(q1.x - tx, q1.y - ty, q1.z - tz, nx, ny, nz, kr, dd, are, aim);
+      p2p_eval(q2.x - tx, q2.y - ty, q2.z - tz, nx, ny, nz, kr, dd, are, aim);
+    }
+    sre += (double)are;
+    sim += (double)aim;
+  }
+  if (live) {
+    out[2 * ((int64_t)r * np + p)] = (Rout)sre;
+    out[2 * ((int64_t)r * np + p) + 1] = (Rout)sim;
+  }
+}
+
+extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y,
+                               const double* points, int64_t npoints, void* out, int flags, void* stream) {
+  bem_set_error("");
+  if (!h) return bem_fail(BEM_ERR_INVALID_ARG, "handle is NULL");
+  if (nrhs < 1 || nrhs > h->nrhs_max) return bem_fail(BEM_ERR_INVALID_ARG, "nrhs out of [1, max_nrhs]");
+  if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
+  if (!x && !y) return bem_fail(BEM_ERR_INVALID_ARG, "x and y are both NULL");
+  if (!points || !out || npoints < 1) return bem_fail(BEM_ERR_INVALID_ARG, "points and out required, npoints >= 1");
+  if (flags != 0) return bem_fail(BEM_ERR_INVALID_ARG, "flags must be 0");
+  if ((int64_t)(npoints + EV_THREADS - 1) / EV_THREADS > 0x7fffffffLL)
+    return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
+  cudaStream_t s = (cudaStream_t)stream;
+  BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
+  const dim3 grid((unsigned)((npoints + EV_THREADS - 1) / EV_THREADS), nrhs);
+  const int64_t nt = h->nt;
+  if (bem_is_fp64(h)) {
+    if (dtype == BEM_C128)
+      k_eval_points<double, double><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
+                                                                h->area, h->hmax, h->wgt, (const double4*)h->dens,
+                                                                (double*)out);
+    else
+      k_eval_points<double, float><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
+                                                               h->area, h->hmax, h->wgt, (const double4*)h->dens,
+                                                               (float*)out);
+  } else {
+    if (dtype == BEM_C128)
+      k_eval_points<float, double><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
+                                                               h->area, h->hmax, h->wgt, (const float4*)h->dens,
+                                                               (double*)out);
+    else
+      k_eval_points<float, float><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
+                                                              h->area, h->hmax, h->wgt, (const float4*)h->dens,
+                                                              (float*)out);
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
 }
 
 // ------------------------------------------------------------- correction --

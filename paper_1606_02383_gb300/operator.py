@@ -110,6 +110,22 @@ class Operator:
                                        None if ys is None else ys.data_ptr(), z.data_ptr(), flags, _stream()))
         return z
 
+    def eval_points(self, points, x=None, y=None, dtype=None):
+        """u(p) = sum_j S(p, j) y_j - D(p, j) x_j at points [npoints, 3] off the
+        surface (direct sum, the entries' rules).  Returns [nrhs, npoints]."""
+        ref = x if x is not None else y
+        if ref is None:
+            raise ValueError("x and y cannot both be None")
+        dtype = dtype or (ref.dtype if isinstance(ref, torch.Tensor) else torch.complex128)
+        xs, ys = self._prep(x, dtype), self._prep(y, dtype)
+        nrhs = (xs if xs is not None else ys).shape[0]
+        pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        out = torch.empty((nrhs, pts.shape[0]), dtype=dtype, device="cuda")
+        _lib.check(self._lib.bem_eval_points(self._h, nrhs, _dtype_code(out), None if xs is None else xs.data_ptr(),
+                                             None if ys is None else ys.data_ptr(), pts.data_ptr(), pts.shape[0],
+                                             out.data_ptr(), 0, _stream()))
+        return out
+
     def apply_host(self, x=None, y=None, out=None, no_half=False):
         """Same as apply() for host arrays/tensors (pinned is best); copies are inside the call."""
         ref = x if x is not None else y

@@ -1,0 +1,71 @@
+"""Field at off-surface points (bem_eval_points) vs the oracle's eval_points.
+
+The points are a lattice in its natural order around the sphere, plus points
+on rays just off the surface (between 0.3 and 6 longest edges away, so every
+rule R_0, R_1, R_2 is used).  Tolerances as for the apply: 1e-10 relative L2
+in the FP64 modes (same rules, only rounding differs), 1e-5 in the mixed mode.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_02383_gb300 import _lib, inputs
+from paper_1606_02383_gb300.operator import Operator
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def field_points(V, T):
+    g = np.linspace(-1.9, 1.9, 9)
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    lat = lat[np.abs(np.linalg.norm(lat, axis=1) - 1.0) > 0.12]
+    c, _, _, _ = oracle.geometry(V, T)
+    h = np.max(np.linalg.norm(V[T[:, 1]] - V[T[:, 0]], axis=1))
+    rng = np.random.default_rng(4)
+    idx = rng.choice(T.shape[0], 120, replace=False)
+    dirs = c[idx] / np.linalg.norm(c[idx], axis=1, keepdims=True)
+    off = h * np.geomspace(0.3, 6.0, 120) * np.where(np.arange(120) % 2 == 0, 1.0, -1.0)
+    near = c[idx] + dirs * off[:, None]
+    order = np.argsort(np.arctan2(near[:, 1], near[:, 0]))  # neighbours along a curve
+    return np.concatenate([lat, near[order]])
+
+
+@pytest.mark.parametrize("mode,tol", [("direct64", 1e-10), ("fp64", 1e-10), ("mixed", 1e-5)])
+def test_eval_points_matches_oracle(cuda_ok, mode, tol):
+    V, T = inputs.icosphere(3)
+    n, k = T.shape[0], 2.0
+    x = inputs.random_density(n, 2, seed=9, stream=0)
+    y = inputs.random_density(n, 2, seed=9, stream=1)
+    pts = field_points(V, T)
+    ref = oracle.eval_points(V, T, k, pts, x=x, y=y)
+    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    u = op.eval_points(pts, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+    assert u.shape == ref.shape
+    assert rel(u, ref) <= tol
+    # each layer alone, and single precision output
+    us = op.eval_points(pts, None, torch.from_numpy(y).cuda()).cpu().numpy()
+    assert rel(us, oracle.eval_points(V, T, k, pts, y=y)) <= tol
+    u64 = op.eval_points(pts, torch.from_numpy(x.astype(np.complex64)).cuda(),
+                         torch.from_numpy(y.astype(np.complex64)).cuda()).cpu().numpy()
+    assert u64.dtype == np.complex64 and rel(u64, ref) <= max(tol, 2e-6)
+    op.close()
+
+
+def test_eval_points_gauss_identity_and_errors(cuda_ok):
+    """At k -> 0 the double layer of a unit density is -1 inside and 0 outside
+    (the orientation of Section 2.1's normals); bad arguments are rejected."""
+    V, T = inputs.icosphere(3)
+    n = T.shape[0]
+    op = Operator(V, T, 1e-9, mode="direct64")
+    pts = np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1], [2.0, 0.5, 0.0], [0.0, -3.0, 1.0]])
+    u = op.eval_points(pts, torch.ones((1, n), dtype=torch.complex128, device="cuda"), None).cpu().numpy()[0]
+    # u = -D 1: inside D 1 = -1, outside 0
+    assert np.allclose(u[:2], 1.0, atol=2e-3) and np.allclose(u[2:], 0.0, atol=2e-3)
+    with pytest.raises(_lib.BemError):
+        op.eval_points(np.zeros((0, 3)), torch.ones((1, n), dtype=torch.complex128, device="cuda"))
+    op.close()
