@@ -31,6 +31,25 @@ def mie_rigid_sphere_surface(k: float, a: float, cos_theta, nmax: int | None = N
     return p
 
 
+def mie_rigid_sphere_scattered(k: float, a: float, points, nmax: int | None = None):
+    """Scattered pressure outside a rigid sphere of radius a (centred at the
+    origin) for the incident plane wave exp(i k z):
+    p_s(r, theta) = -sum_n (2n+1) i^n [j_n'(ka) / h_n'(ka)] h_n(kr) P_n(cos theta),
+    the outgoing field (h_n = h_n^(1)) that cancels the incident field's
+    normal derivative on r = a."""
+    ka = k * a
+    if nmax is None:
+        nmax = int(ka + 4.0 * ka ** (1.0 / 3.0) + 10)
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1)
+    ct = pts[:, 2] / r
+    p = np.zeros(r.shape, dtype=np.complex128)
+    for n in range(nmax + 1):
+        coef = -(2 * n + 1) * (1j ** n) * sp.spherical_jn(n, ka, True) / _h(n, ka, True)
+        p += coef * _h(n, k * r) * sp.eval_legendre(n, ct)
+    return p
+
+
 def sphere_single_layer_eigenvalue(n: int, k: float, a: float) -> complex:
     """S Y_n = i k a^2 h_n(ka) j_n(ka) Y_n on the sphere of radius a (from the
     addition theorem G = i k sum h_n(k r>) j_n(k r<) sum_m Y_nm Y_nm^*)."""

@@ -69,3 +69,26 @@ def test_eval_points_gauss_identity_and_errors(cuda_ok):
     with pytest.raises(_lib.BemError):
         op.eval_points(np.zeros((0, 3)), torch.ones((1, n), dtype=torch.complex128, device="cuda"))
     op.close()
+
+
+def test_scattered_field_of_the_solved_rigid_sphere(cuda_ok):
+    """End to end: GMRES for the rigid sphere's surface pressure, then the
+    scattered field p_s = D p at exterior points through bem_eval_points
+    (which returns S y - D x), against the Mie series (discretisation error of
+    the 5,120-triangle sphere) and against the oracle's evaluation of the same
+    surface solution (1e-5)."""
+    from oracle import closed_forms as cf
+    V, T = inputs.icosphere(4)
+    k = 2.0
+    c, _, _, _ = oracle.geometry(V, T)
+    op = Operator(V, T, k, p=0, eps=1e-6, mode="mixed")
+    b = torch.from_numpy(inputs.plane_wave(c, k)[None, :]).cuda()
+    p, iters, relres = op.solve(b, tol=1e-8, max_iter=100, restart=100)
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(64, 3))
+    pts = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(1.5, 3.0, size=(64, 1))
+    pts = pts[np.argsort(np.arctan2(pts[:, 1], pts[:, 0]))]
+    ps = -op.eval_points(pts, x=p).cpu().numpy()[0]
+    assert rel(ps, cf.mie_rigid_sphere_scattered(k, 1.0, pts)) < 1e-2
+    assert rel(ps, -oracle.eval_points(V, T, k, pts, x=p.cpu().numpy())[0]) < 1e-5
+    op.close()

@@ -205,6 +205,40 @@ def test_mie_series_truncation_independent():
     assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
 
 
+def test_mie_scattered_field_meets_surface_formula():
+    """On r = a the incident plus scattered closed form equals the surface
+    closed form (the latter simplified through the Wronskian, the former not)."""
+    for k in (0.7, 3.0, 8.0):
+        th = np.linspace(0.05, np.pi - 0.05, 23)
+        pts = np.stack([np.sin(th), 0 * th, np.cos(th)], axis=1)
+        tot = np.exp(1j * k * pts[:, 2]) + cf.mie_rigid_sphere_scattered(k, 1.0, pts)
+        assert _rel(tot, cf.mie_rigid_sphere_surface(k, 1.0, np.cos(th))) < 1e-11
+
+
+def test_offsurface_double_layer_of_the_mie_pressure_is_the_scattered_field():
+    """For a rigid body the exterior representation formula reduces to
+    p_s(x) = (D p)(x), the double layer with the normals pointing into the
+    fluid (its exterior limit D p + p/2 turns p = p_inc + D p into the surface
+    equation (1/2 I - D) p = p_inc).  The oracle's off-surface evaluation,
+    which returns S y - D x, of the exact Mie surface pressure reproduces the
+    Mie scattered field outside the sphere to the discretisation error, which
+    falls as h^2."""
+    k = 2.0
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(24, 3))
+    pts = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(1.5, 3.0, size=(24, 1))
+    ref = cf.mie_rigid_sphere_scattered(k, 1.0, pts)
+    errs = []
+    for lev in (3, 4):
+        V, T = inputs.icosphere(lev)
+        c, _, _, _ = oracle.geometry(V, T)
+        p = cf.mie_rigid_sphere_surface(k, 1.0, c[:, 2] / np.linalg.norm(c, axis=1))[None, :]
+        ps = -oracle.eval_points(V, T, k, pts, x=p)[0]  # -(S y - D x) with y = 0, x = p
+        errs.append(_rel(ps, ref))
+    assert errs[1] < 1e-2
+    assert errs[0] / errs[1] > 2.5
+
+
 # --- vertex / wavenumber gradient (forward-mode duals over every entry) ------
 
 def _loss(V, T, k, g, x, y):
