@@ -225,6 +225,18 @@ int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const voi
                     int64_t npoints, void* out, int flags, void* stream);
 
 /*
+ * bem_point_sources -- b_i = sum_m a_m G(c_i - x_m), G = exp(ikr)/(4 pi r), at
+ * the collocation points c_i (the adjoint right-hand side of Section 2.2:
+ * point sources at the observation points x_m with weights a_m).
+ *   points : [nsrc][3] FP64 (device), off the surface.
+ *   amps   : [nrhs][nsrc] complex128 (device).
+ *   out    : [nrhs][N] complex of dtype (device), caller's element order.
+ * FP64, one thread per element.  Stream-ordered.
+ */
+int bem_point_sources(bem_handle* h, int nrhs, int dtype, int nsrc, const double* points, const double* amps,
+                      void* out, void* stream);
+
+/*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
  * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
  *   b          : right-hand sides [nrhs][N] (device).

@@ -519,6 +519,54 @@ extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x
   return BEM_OK;
 }
 
+// ----------------------------------------------------------- point sources --
+// b_i = sum_m a_m G(c_i - x_m), G = exp(ikr)/(4 pi r): the field of point
+// sources at the collocation points, e.g. the adjoint right-hand side of
+// Section 2.2 with weights a_m at the observation points.  One thread per
+// element, FP64 (a handful of sources), written in the caller's order.
+template <typename Rout>
+__global__ void k_point_sources(int64_t nt, int nrhs, int nsrc, double k, const int* __restrict__ perm,
+                                const double* __restrict__ cent, const double* __restrict__ pts,
+                                const double* __restrict__ amps, Rout* __restrict__ out) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nt) return;
+  const int64_t o = perm[s];
+  const double c0 = cent[3 * s], c1 = cent[3 * s + 1], c2 = cent[3 * s + 2];
+  for (int r = 0; r < nrhs; ++r) {
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < nsrc; ++m) {
+      const double d0 = c0 - pts[3 * m], d1 = c1 - pts[3 * m + 1], d2 = c2 - pts[3 * m + 2];
+      const double d = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      double sn, cs;
+      sincos(k * d, &sn, &cs);
+      const double g = 1.0 / (4.0 * BEM_PI * d);
+      const double ar = amps[2 * ((int64_t)r * nsrc + m)], ai = amps[2 * ((int64_t)r * nsrc + m) + 1];
+      re += g * (ar * cs - ai * sn);
+      im += g * (ar * sn + ai * cs);
+    }
+    out[2 * ((int64_t)r * nt + o)] = (Rout)re;
+    out[2 * ((int64_t)r * nt + o) + 1] = (Rout)im;
+  }
+}
+
+extern "C" int bem_point_sources(bem_handle* h, int nrhs, int dtype, int nsrc, const double* points,
+                                 const double* amps, void* out, void* stream) {
+  bem_set_error("");
+  if (!h) return bem_fail(BEM_ERR_INVALID_ARG, "handle is NULL");
+  if (nrhs < 1 || nsrc < 1 || !points || !amps || !out)
+    return bem_fail(BEM_ERR_INVALID_ARG, "nrhs, nsrc >= 1 and points, amps, out required");
+  if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nt = h->nt;
+  const unsigned g = (unsigned)((nt + 255) / 256);
+  if (dtype == BEM_C128)
+    k_point_sources<double><<<g, 256, 0, s>>>(nt, nrhs, nsrc, h->k, h->perm, h->cent, points, amps, (double*)out);
+  else
+    k_point_sources<float><<<g, 256, 0, s>>>(nt, nrhs, nsrc, h->k, h->perm, h->cent, points, amps, (float*)out);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 // ------------------------------------------------------------- correction --
 // z_i += sum_j C^S_ij sigma_j - C^D_ij tau_j  (values pre-divided by the weight).
 // One warp per row, accumulated in the operator's precision (FP32 in the mixed

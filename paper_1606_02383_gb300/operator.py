@@ -17,6 +17,12 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _raw(t: torch.Tensor) -> torch.Tensor:
+    """Contiguous memory holding the tensor's values: the library reads raw
+    memory, so lazy conjugate / negative views are resolved first."""
+    return t.resolve_conj().resolve_neg().contiguous()
+
+
 def _dtype_code(t: torch.Tensor) -> int:
     if t.dtype == torch.complex128:
         return _lib.BEM_C128
@@ -94,7 +100,8 @@ class Operator:
         t = torch.as_tensor(t)
         if t.dim() == 1:
             t = t[None, :]
-        return t.to(device="cuda", dtype=dtype).contiguous()
+        # the library reads raw memory: lazy conjugate / negative views are resolved
+        return _raw(t.to(device="cuda", dtype=dtype))
 
     def apply(self, x=None, y=None, no_half=False, dtype=None):
         """z = (1/2 I - D) x + S y for device densities [nrhs, n] (or [n])."""
@@ -126,8 +133,39 @@ class Operator:
                                              out.data_ptr(), 0, _stream()))
         return out
 
+    def point_sources(self, points, amps, dtype=torch.complex128):
+        """b_i = sum_m a_m G(c_i - x_m) at the collocation points: points [nsrc, 3],
+        amps [nrhs, nsrc] (or [nsrc]).  Returns [nrhs, N]."""
+        pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        a = torch.as_tensor(amps).to("cuda", torch.complex128)
+        a = _raw(a if a.dim() == 2 else a[None])
+        if a.shape[1] != pts.shape[0]:
+            raise ValueError("amps must be [nrhs, nsrc] with nsrc = len(points)")
+        out = torch.empty((a.shape[0], self.n), dtype=dtype, device="cuda")
+        _lib.check(self._lib.bem_point_sources(self._h, a.shape[0], _dtype_code(out), pts.shape[0], pts.data_ptr(),
+                                               a.data_ptr(), out.data_ptr(), _stream()))
+        return out
+
+    def state_and_adjoint(self, b, observers, incident_at_observers, tol=1e-8, max_iter=200, restart=200):
+        """The chain of Section 2.2 for f = 1/2 |p|^2 summed over observation points:
+        the state solve (1/2 I - D) p = b; the pressure at the observers,
+        p(x_m) = p_inc(x_m) + (D p)(x_m) (the rigid body's representation formula);
+        the adjoint right-hand side sum_m conj(p(x_m)) G(c - x_m); the adjoint
+        solve with the same operator.  Returns a dict with p, p_obs, weights,
+        p_adj, iterations and residuals."""
+        p, it_s, rel_s = self.solve(b, tol=tol, max_iter=max_iter, restart=restart)
+        inc = torch.as_tensor(incident_at_observers).to("cuda", torch.complex128).reshape(1, -1)
+        p_obs = inc - self.eval_points(observers, x=p.to(torch.complex128))
+        weights = torch.conj_physical(p_obs)
+        b_adj = self.point_sources(observers, weights, dtype=p.dtype)
+        p_adj, it_a, rel_a = self.solve(b_adj, tol=tol, max_iter=max_iter, restart=restart)
+        return {"p": p, "p_obs": p_obs, "weights": weights, "p_adj": p_adj, "iterations": (it_s, it_a),
+                "relres": (rel_s, rel_a)}
+
     def apply_host(self, x=None, y=None, out=None, no_half=False):
         """Same as apply() for host arrays/tensors (pinned is best); copies are inside the call."""
+        x = None if x is None else _raw(x)
+        y = None if y is None else _raw(y)
         ref = x if x is not None else y
         nrhs = ref.shape[0] if ref.dim() == 2 else 1
         dtype = ref.dtype
@@ -232,7 +270,7 @@ class BemApplyFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gz):
         x, y = ctx.saved_tensors
-        gz = gz.contiguous()
+        gz = _raw(gz)
         gx, gy = ctx.op.adjoint(gz)
         gk = gv = None
         want_k, want_v = ctx.needs_input_grad[3], len(ctx.needs_input_grad) > 4 and ctx.needs_input_grad[4]
@@ -292,8 +330,8 @@ class Batch:
     def apply(self, x=None, y=None, no_half=False):
         ref = x if x is not None else y
         dtype = ref.dtype
-        xs = None if x is None else (x if x.dim() == 2 else x[None]).to("cuda", dtype).contiguous()
-        ys = None if y is None else (y if y.dim() == 2 else y[None]).to("cuda", dtype).contiguous()
+        xs = None if x is None else _raw((x if x.dim() == 2 else x[None]).to("cuda", dtype))
+        ys = None if y is None else _raw((y if y.dim() == 2 else y[None]).to("cuda", dtype))
         nrhs = (xs if xs is not None else ys).shape[0]
         z = torch.empty((nrhs, self.n), dtype=dtype, device="cuda")
         _lib.check(self._lib.bem_apply_batch(self._h, nrhs, _dtype_code(z), None if xs is None else xs.data_ptr(),
@@ -305,9 +343,9 @@ class Batch:
         """GMRES for (1/2 I - D_p) x_p = b_p on every problem p at once (each with its
         own Krylov space).  b: [nrhs, N_total].  Returns (x, iterations,
         relres[nrhs, number of problems]).  driver as for Operator.solve."""
-        bs = (b if b.dim() == 2 else b[None]).to("cuda").contiguous()
+        bs = _raw((b if b.dim() == 2 else b[None]).to("cuda"))
         nrhs = bs.shape[0]
-        x = torch.zeros_like(bs) if x0 is None else (x0 if x0.dim() == 2 else x0[None]).to("cuda", bs.dtype).clone()
+        x = torch.zeros_like(bs) if x0 is None else _raw((x0 if x0.dim() == 2 else x0[None]).to("cuda", bs.dtype)).clone()
         iters = ctypes.c_int(0)
         nprob = len(self.sizes)
         rel = (ctypes.c_double * (nrhs * nprob))()

@@ -40,3 +40,17 @@ def test_error_paths_without_gpu():
     assert lib.bem_setup(ctypes.byref(mesh), 1.0, 8, 1e-5, None, None, ctypes.byref(h)) == _lib.BEM_ERR_INVALID_ARG
     assert lib.bem_apply(None, 1, _lib.BEM_C128, None, None, None, 0, None) == _lib.BEM_ERR_INVALID_ARG
     assert lib.bem_destroy(None) == _lib.BEM_OK
+
+
+def test_lazy_conjugate_views_are_resolved_before_the_library_reads_memory():
+    """torch.conj gives a view whose raw memory holds the unconjugated values;
+    the binding must hand the library the conjugated numbers."""
+    import torch
+    from paper_1606_02383_gb300.operator import _raw
+    a = torch.tensor([1 + 2j, 3 - 4j], dtype=torch.complex128)
+    r = _raw(torch.conj(a))
+    assert not r.is_conj()
+    raw = torch.view_as_real(r).flatten().tolist()
+    assert raw == [1.0, -2.0, 3.0, 4.0]
+    r = _raw(-torch.conj(a))
+    assert torch.view_as_real(r).flatten().tolist() == [-1.0, 2.0, -3.0, -4.0]

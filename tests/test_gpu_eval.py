@@ -92,3 +92,32 @@ def test_scattered_field_of_the_solved_rigid_sphere(cuda_ok):
     assert rel(ps, cf.mie_rigid_sphere_scattered(k, 1.0, pts)) < 1e-2
     assert rel(ps, -oracle.eval_points(V, T, k, pts, x=p.cpu().numpy())[0]) < 1e-5
     op.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("direct64", 1e-7), ("mixed", 1e-5)])
+def test_state_observation_adjoint_chain(cuda_ok, mode, tol):
+    """Section 2.2's chain for f = 1/2 sum_m |p(x_m)|^2: state solve, the
+    pressure at the observers through the representation formula, the
+    adjoint right-hand side with weights conj(p(x_m)), the adjoint solve;
+    every step against the oracle's dense LU and off-surface evaluation."""
+    V, T = inputs.icosphere(3)
+    k = 2.0
+    c, _, _, _ = oracle.geometry(V, T)
+    obs = np.array([[5.0, 0, 0], [-5.0, 0, 0], [0, 0, 5.0], [0, 0, -5.0]])
+    b = inputs.plane_wave(c, k)[None, :]
+    S, D = oracle.assemble(V, T, k)
+    A = 0.5 * np.eye(T.shape[0]) - D
+    p_ref = oracle.lu_solve(A, b)
+    inc_obs = np.exp(1j * k * obs[:, 2])
+    pobs_ref = inc_obs - oracle.eval_points(V, T, k, obs, x=p_ref)[0]
+    r = np.linalg.norm(c[:, None, :] - obs[None, :, :], axis=2)
+    badj_ref = (np.exp(1j * k * r) / (4 * np.pi * r)) @ np.conj(pobs_ref)
+    padj_ref = oracle.lu_solve(A, badj_ref[None, :])
+    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    out = op.state_and_adjoint(torch.from_numpy(b).cuda(), obs, inc_obs, tol=1e-10 if mode == "direct64" else 1e-8)
+    assert rel(out["p"].cpu().numpy(), p_ref) <= tol
+    assert rel(out["p_obs"].cpu().numpy()[0], pobs_ref) <= tol
+    badj = op.point_sources(obs, np.conj(pobs_ref)).cpu().numpy()[0]
+    assert rel(badj, badj_ref) <= 1e-12
+    assert rel(out["p_adj"].cpu().numpy(), padj_ref) <= tol
+    op.close()
