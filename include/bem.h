@@ -214,13 +214,17 @@ int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, c
  *              the surface.  Consecutive points should be close to each other
  *              (a lattice in its natural order, or points sorted along a
  *              curve): each block of 128 points shares one FP32 origin.
- *   out      : [nrhs][npoints] complex (device, dtype).
- *   flags    : 0.
+ *   out      : [nrhs][npoints] complex (device, dtype); with BEM_EVAL_GRADIENT
+ *              [nrhs][npoints][3]: grad u(p), the gradient with respect to
+ *              the field point (the same rules applied to grad G and
+ *              grad dG/dn_y).
+ *   flags    : 0 or BEM_EVAL_GRADIENT.
  * Cost: a direct sum over all elements for every point (O(npoints N)), in the
  * handle's precision: FP32 sums with FP64 between tiles in the mixed modes,
  * FP64 in the FP64 modes; pairs within 4 h_j take the refined rule from the
  * FP64 geometry.  Stream-ordered; no allocation, no host synchronisation.
  */
+#define BEM_EVAL_GRADIENT 1
 int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
                     int64_t npoints, void* out, int flags, void* stream);
 

@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     assemble,
     entries,
     eval_points,
+    eval_points_grad,
     geometry,
     grad,
     lu_solve,

@@ -256,6 +256,56 @@ static void entry(const tri_t* ti, int64_t i, const tri_t* tj, int64_t j, double
   entry_offsurface(ti->c, tj, k, flags, s, d);
 }
 
+/* ---- gradient of the entries with respect to the field point ------------
+   With d = y - x, r = |d|, F = exp(ikr)(ikr - 1)/(4 pi r^3) and
+   H = exp(ikr)(3 - 3ikr - k^2 r^2)/(4 pi r^5) (dF/dr = -r H):
+     grad_x G          = -F d
+     grad_x dG/dn_y    = -(H (d.n) d + F n)
+   from G = exp(ikr)/(4 pi r) and dG/dn_y = F (d.n). */
+static void kernel_grad_add(const double* x, const double* y, const double* n, double w, double k, cplx gs[3],
+                            cplx gd[3]) {
+  double dv[3];
+  sub3(y, x, dv);
+  double r = norm3(dv);
+  cplx e = cexp(I * k * r);
+  cplx F = e * (I * k * r - 1.0) / (4.0 * OR_PI * r * r * r);
+  cplx H = e * (3.0 - 3.0 * I * k * r - k * k * r * r) / (4.0 * OR_PI * r * r * r * r * r);
+  double dn = dot3(dv, n);
+  for (int c = 0; c < 3; ++c) {
+    gs[c] += -w * F * dv[c];
+    gd[c] += -w * (H * dn * dv[c] + F * n[c]);
+  }
+}
+
+/* the gradient entries under the rule R_L (same pieces and points as rule_rl) */
+static void rule_rl_grad(const double* x, const double* a, const double* b, const double* c, const double* n, int L,
+                         double k, cplx gs[3], cplx gd[3]) {
+  if (L == 0) {
+    double e1[3], e2[3], cr[3];
+    sub3(b, a, e1);
+    sub3(c, a, e2);
+    cross3(e1, e2, cr);
+    double w = 0.5 * norm3(cr) / 3.0;
+    double bary[3][3] = {{2.0 / 3, 1.0 / 6, 1.0 / 6}, {1.0 / 6, 2.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 6, 2.0 / 3}};
+    for (int q = 0; q < 3; ++q) {
+      double y[3];
+      for (int dd = 0; dd < 3; ++dd) y[dd] = bary[q][0] * a[dd] + bary[q][1] * b[dd] + bary[q][2] * c[dd];
+      kernel_grad_add(x, y, n, w, k, gs, gd);
+    }
+    return;
+  }
+  double ab[3], bc[3], ca[3];
+  for (int dd = 0; dd < 3; ++dd) {
+    ab[dd] = 0.5 * (a[dd] + b[dd]);
+    bc[dd] = 0.5 * (b[dd] + c[dd]);
+    ca[dd] = 0.5 * (c[dd] + a[dd]);
+  }
+  rule_rl_grad(x, a, ab, ca, n, L - 1, k, gs, gd);
+  rule_rl_grad(x, ab, b, bc, n, L - 1, k, gs, gd);
+  rule_rl_grad(x, ca, bc, c, n, L - 1, k, gs, gd);
+  rule_rl_grad(x, ab, bc, ca, n, L - 1, k, gs, gd);
+}
+
 /* ---- public API --------------------------------------------------------- */
 
 int oracle_num_threads(void) {
@@ -418,6 +468,48 @@ int oracle_eval_points(const double* V, int64_t nv, const int32_t* T, int64_t nt
         }
       }
       for (int q = 0; q < nrhs; ++q) oc[(int64_t)q * npts + p] = acc[q];
+    }
+    free(acc);
+  }
+  free(tris);
+  return 0;
+}
+
+/* grad u(p) for u(p) = sum_j S(p, j) y_j - D(p, j) x_j (the entries' rules),
+   out [nrhs][npts][3] complex */
+int oracle_eval_points_grad(const double* V, int64_t nv, const int32_t* T, int64_t nt, double k, int flags,
+                            int nrhs, const double* x, const double* y, const double* pts, int64_t npts,
+                            double* out) {
+  (void)nv;
+  tri_t* tris = (tri_t*)malloc(sizeof(tri_t) * (size_t)nt);
+  if (!tris) return 1;
+  for (int64_t j = 0; j < nt; ++j) tri_load(V, T, j, &tris[j]);
+  const cplx* xc = (const cplx*)x;
+  const cplx* yc = (const cplx*)y;
+  cplx* oc = (cplx*)out;
+#pragma omp parallel
+  {
+    cplx* acc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)nrhs);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npts; ++p) {
+      for (int q = 0; q < 3 * nrhs; ++q) acc[q] = 0.0;
+      for (int64_t j = 0; j < nt; ++j) {
+        cplx gs[3] = {0.0, 0.0, 0.0}, gd[3] = {0.0, 0.0, 0.0};
+        const tri_t* tj = &tris[j];
+        if (flags & OR_FLAG_RULE1) {
+          kernel_grad_add(&pts[3 * p], tj->c, tj->n, tj->area, k, gs, gd);
+        } else {
+          int L = choose_level(&pts[3 * p], tj, flags);
+          rule_rl_grad(&pts[3 * p], tj->v[0], tj->v[1], tj->v[2], tj->n, L, k, gs, gd);
+        }
+        for (int q = 0; q < nrhs; ++q)
+          for (int c = 0; c < 3; ++c) {
+            if (yc) acc[3 * q + c] += gs[c] * yc[(int64_t)q * nt + j];
+            if (xc) acc[3 * q + c] -= gd[c] * xc[(int64_t)q * nt + j];
+          }
+      }
+      for (int q = 0; q < nrhs; ++q)
+        for (int c = 0; c < 3; ++c) oc[((int64_t)q * npts + p) * 3 + c] = acc[3 * q + c];
     }
     free(acc);
   }

@@ -39,12 +39,15 @@ def _load():
     lib.oracle_apply_adjoint.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D]
     lib.oracle_eval_points.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D,
                                        _D, _i64, _D]
+    lib.oracle_eval_points_grad.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
+                                            _D, _D, _i64, _D]
     lib.oracle_assemble.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, _D, _D]
     lib.oracle_lu_solve.argtypes = [_i64, _D, ctypes.c_int, _D]
     lib.oracle_grad.argtypes = [_D, _i64, _I32, _i64, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D,
                                 _I64, _i64, _D, _D]
     for f in (lib.oracle_geometry, lib.oracle_entries, lib.oracle_apply, lib.oracle_apply_adjoint,
-              lib.oracle_eval_points, lib.oracle_assemble, lib.oracle_lu_solve, lib.oracle_grad):
+              lib.oracle_eval_points, lib.oracle_eval_points_grad, lib.oracle_assemble, lib.oracle_lu_solve,
+              lib.oracle_grad):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -169,6 +172,21 @@ def eval_points(V, T, k, pts, x=None, y=None, flags=0):
     out = np.empty((nrhs, pts.shape[0]), dtype=np.complex128)
     rc = _load().oracle_eval_points(_dp(V), V.shape[0], T.ctypes.data_as(_I32), nt, float(k), int(flags), nrhs,
                                     _dp(xa), _dp(ya), _dp(pts), pts.shape[0], out.ctypes.data_as(_D))
+    assert rc == 0
+    return out
+
+
+def eval_points_grad(V, T, k, pts, x=None, y=None, flags=0):
+    """grad_p of sum_j S(p,j) y_j - D(p,j) x_j at off-surface points, [nrhs, npts, 3]."""
+    V, T = _mesh(V, T)
+    nt = T.shape[0]
+    xa, nx = _cplx(x, nt)
+    ya, ny = _cplx(y, nt)
+    nrhs = max(nx, ny)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((nrhs, pts.shape[0], 3), dtype=np.complex128)
+    rc = _load().oracle_eval_points_grad(_dp(V), V.shape[0], T.ctypes.data_as(_I32), nt, float(k), int(flags), nrhs,
+                                         _dp(xa), _dp(ya), _dp(pts), pts.shape[0], out.ctypes.data_as(_D))
     assert rc == 0
     return out
 

@@ -32,6 +32,7 @@ BEM_HOST_BUFFERS = 2
 BEM_GMRES_USE_X0 = 1
 BEM_GMRES_HOST_LOOP = 2
 BEM_GMRES_GRAPH_ONLY = 4
+BEM_EVAL_GRADIENT = 1
 
 INFO = {
     "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,

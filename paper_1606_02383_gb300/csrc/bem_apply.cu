@@ -481,6 +481,167 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points(int64_t nt, int64_t 
   }
 }
 
+// Gradient with respect to the field point of one rule point's contribution:
+// with d = y - x, F = exp(ikr)(ikr - 1)/r^3 and H = exp(ikr)(3 - 3ikr - k^2 r^2)/r^5,
+//   grad S-term = -F d sigma,  grad D-term = -(H (d.n) d + F n) tau,
+// so grad u += d (-F sigma + (d.n) H tau) + n F tau  (sigma, tau weighted as
+// in the apply: they carry the point weight and 1/(4 pi)).  Accurate sincos:
+// a field point may be far from the sources.
+template <typename R>
+__device__ __forceinline__ void grad_eval(R dx, R dy, R dz, R nx, R ny, R nz, R k, R sr, R si, R tr, R ti,
+                                          R (&g)[6]) {
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  const R r = sqrt(r2), ir = R(1) / r, ir2 = ir * ir;
+  const R kr = k * r;
+  R sn, cs;
+  if constexpr (sizeof(R) == 4) sincosf(kr, &sn, &cs);
+  else sincos(kr, &sn, &cs);
+  const R ir3 = ir * ir2, ir5 = ir3 * ir2;
+  const R fr = (-cs - kr * sn) * ir3, fi = (kr * cs - sn) * ir3;
+  const R q = R(3) - kr * kr;
+  const R hr = (cs * q + R(3) * kr * sn) * ir5, hi = (sn * q - R(3) * kr * cs) * ir5;
+  const R dn = dx * nx + dy * ny + dz * nz;
+  const R ar = -(fr * sr - fi * si) + dn * (hr * tr - hi * ti);
+  const R ai = -(fr * si + fi * sr) + dn * (hr * ti + hi * tr);
+  const R br = fr * tr - fi * ti, bi = fr * ti + fi * tr;
+  g[0] += ar * dx + br * nx;
+  g[1] += ai * dx + bi * nx;
+  g[2] += ar * dy + br * ny;
+  g[3] += ai * dy + bi * ny;
+  g[4] += ar * dz + br * nz;
+  g[5] += ai * dz + bi * nz;
+}
+
+// the gradient contribution of element j under its refined rule, relative to X
+template <typename R>
+__device__ void grad_near(const double* X, int j, double k, const double* __restrict__ cent,
+                          const double* __restrict__ qpt, const double* __restrict__ nrm,
+                          const double* __restrict__ area, const double* __restrict__ hmax,
+                          const typename V4of<R>::T& dd, R (&g)[6]) {
+  Tri64 t;
+  load_tri64(qpt, nrm, cent, area, hmax, j, t);
+  const double c0 = t.c[0] - X[0], c1 = t.c[1] - X[1], c2 = t.c[2] - X[2];
+  const double dist = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  const int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+  const int npieces = 1 << (2 * L);
+  // each piece carries 1/4^L of the element's weight
+  const R sc = R(1) / npieces;
+  const R sr = dd.x * sc, si = dd.y * sc, tr = dd.z * sc, ti = dd.w * sc;
+  const R nx = (R)t.n[0], ny = (R)t.n[1], nz = (R)t.n[2];
+  for (int piece = 0; piece < npieces; ++piece) {
+    R a[3], b[3], c[3];
+    for (int e = 0; e < 3; ++e) {
+      a[e] = (R)(t.v[0][e] - X[e]);
+      b[e] = (R)(t.v[1][e] - X[e]);
+      c[e] = (R)(t.v[2][e] - X[e]);
+    }
+    int code = piece;
+    for (int lvl = 0; lvl < L; ++lvl) {
+      const int child = code & 3;
+      code >>= 2;
+      R ab[3], bc[3], ca[3];
+      for (int e = 0; e < 3; ++e) {
+        ab[e] = R(0.5) * (a[e] + b[e]);
+        bc[e] = R(0.5) * (b[e] + c[e]);
+        ca[e] = R(0.5) * (c[e] + a[e]);
+      }
+      for (int e = 0; e < 3; ++e) {
+        if (child == 0) {
+          b[e] = ab[e];
+          c[e] = ca[e];
+        } else if (child == 1) {
+          a[e] = ab[e];
+          c[e] = bc[e];
+        } else if (child == 2) {
+          a[e] = ca[e];
+          b[e] = bc[e];
+        } else {
+          a[e] = ab[e];
+          b[e] = bc[e];
+          c[e] = ca[e];
+        }
+      }
+    }
+    const R b0 = R(2) / R(3), b1 = R(1) / R(6);
+    for (int q = 0; q < 3; ++q) {
+      R y[3];
+      for (int e = 0; e < 3; ++e)
+        y[e] = (q == 0 ? b0 : b1) * a[e] + (q == 1 ? b0 : b1) * b[e] + (q == 2 ? b0 : b1) * c[e];
+      grad_eval<R>(y[0], y[1], y[2], nx, ny, nz, (R)k, sr, si, tr, ti, g);
+    }
+  }
+}
+
+// grad u at points off the surface: as k_eval_points, three complex
+// components per point, out [nrhs][np][3]
+template <typename R, typename Rout>
+__global__ void __launch_bounds__(EV_THREADS) k_eval_points_grad(int64_t nt, int64_t np, double k,
+                                                                 const double* __restrict__ pts,
+                                                                 const double* __restrict__ cent,
+                                                                 const double* __restrict__ qpt,
+                                                                 const double* __restrict__ nrm,
+                                                                 const double* __restrict__ area,
+                                                                 const double* __restrict__ hmax,
+                                                                 const typename V4of<R>::T* __restrict__ dens,
+                                                                 Rout* __restrict__ out) {
+  typedef typename V4of<R>::T V4;
+  __shared__ V4 s_q[EV_THREADS][3];
+  __shared__ V4 s_c[EV_THREADS];
+  __shared__ V4 s_d[EV_THREADS];
+  const int r = blockIdx.y;
+  const int64_t p0 = blockIdx.x * (int64_t)EV_THREADS, p = p0 + threadIdx.x;
+  const bool live = p < np;
+  const double o[3] = {pts[3 * p0], pts[3 * p0 + 1], pts[3 * p0 + 2]};
+  const int64_t pp = live ? p : p0;
+  const double X[3] = {pts[3 * pp], pts[3 * pp + 1], pts[3 * pp + 2]};
+  const R tx = (R)(X[0] - o[0]), ty = (R)(X[1] - o[1]), tz = (R)(X[2] - o[2]);
+  const V4* dr = dens + (int64_t)r * nt;
+  const R kr = (R)k;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e0 = 0; e0 < nt; e0 += EV_THREADS) {
+    const int ne = (int)min((int64_t)EV_THREADS, nt - e0);
+    __syncthreads();
+    if (threadIdx.x < ne) {
+      const int64_t j = e0 + threadIdx.x;
+      for (int q = 0; q < 3; ++q) {
+        V4 v;
+        v.x = (R)(qpt[9 * j + 3 * q] - o[0]);
+        v.y = (R)(qpt[9 * j + 3 * q + 1] - o[1]);
+        v.z = (R)(qpt[9 * j + 3 * q + 2] - o[2]);
+        v.w = (R)nrm[3 * j + q];
+        s_q[threadIdx.x][q] = v;
+      }
+      const double h4 = 4.0 * hmax[j];
+      V4 c;
+      c.x = (R)(cent[3 * j] - o[0]);
+      c.y = (R)(cent[3 * j + 1] - o[1]);
+      c.z = (R)(cent[3 * j + 2] - o[2]);
+      c.w = (R)(h4 * h4);
+      s_c[threadIdx.x] = c;
+      s_d[threadIdx.x] = dr[j];
+    }
+    __syncthreads();
+    R g[6] = {0, 0, 0, 0, 0, 0};
+    for (int e = 0; e < ne; ++e) {
+      const V4 c = s_c[e];
+      const R cx = c.x - tx, cy = c.y - ty, cz = c.z - tz;
+      const V4 dd = s_d[e];
+      if (cx * cx + cy * cy + cz * cz < c.w) {
+        grad_near<R>(X, (int)(e0 + e), k, cent, qpt, nrm, area, hmax, dd, g);
+        continue;
+      }
+      const V4 q0 = s_q[e][0], q1 = s_q[e][1], q2 = s_q[e][2];
+      const R nx = q0.w, ny = q1.w, nz = q2.w;
+      grad_eval<R>(q0.x - tx, q0.y - ty, q0.z - tz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g);
+      grad_eval<R>(q1.x - tx, q1.y - ty, q1.z - tz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g);
+      grad_eval<R>(q2.x - tx, q2.y - ty, q2.z - tz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g);
+    }
+    for (int c = 0; c < 6; ++c) acc[c] += (double)g[c];
+  }
+  if (live)
+    for (int c = 0; c < 6; ++c) out[6 * ((int64_t)r * np + p) + c] = (Rout)acc[c];
+}
+
 extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y,
                                const double* points, int64_t npoints, void* out, int flags, void* stream) {
   bem_set_error("");
@@ -489,13 +650,32 @@ extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x
   if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
   if (!x && !y) return bem_fail(BEM_ERR_INVALID_ARG, "x and y are both NULL");
   if (!points || !out || npoints < 1) return bem_fail(BEM_ERR_INVALID_ARG, "points and out required, npoints >= 1");
-  if (flags != 0) return bem_fail(BEM_ERR_INVALID_ARG, "flags must be 0");
+  if (flags & ~BEM_EVAL_GRADIENT) return bem_fail(BEM_ERR_INVALID_ARG, "flags: 0 or BEM_EVAL_GRADIENT");
   if ((int64_t)(npoints + EV_THREADS - 1) / EV_THREADS > 0x7fffffffLL)
     return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
   cudaStream_t s = (cudaStream_t)stream;
   BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
   const dim3 grid((unsigned)((npoints + EV_THREADS - 1) / EV_THREADS), nrhs);
   const int64_t nt = h->nt;
+  if (flags & BEM_EVAL_GRADIENT) {
+    if (bem_is_fp64(h)) {
+      if (dtype == BEM_C128)
+        k_eval_points_grad<double, double><<<grid, EV_THREADS, 0, s>>>(
+            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const double4*)h->dens, (double*)out);
+      else
+        k_eval_points_grad<double, float><<<grid, EV_THREADS, 0, s>>>(
+            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const double4*)h->dens, (float*)out);
+    } else {
+      if (dtype == BEM_C128)
+        k_eval_points_grad<float, double><<<grid, EV_THREADS, 0, s>>>(
+            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const float4*)h->dens, (double*)out);
+      else
+        k_eval_points_grad<float, float><<<grid, EV_THREADS, 0, s>>>(
+            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const float4*)h->dens, (float*)out);
+    }
+    BEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  }
   if (bem_is_fp64(h)) {
     if (dtype == BEM_C128)
       k_eval_points<double, double><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,

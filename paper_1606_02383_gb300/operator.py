@@ -117,9 +117,10 @@ class Operator:
                                        None if ys is None else ys.data_ptr(), z.data_ptr(), flags, _stream()))
         return z
 
-    def eval_points(self, points, x=None, y=None, dtype=None):
+    def eval_points(self, points, x=None, y=None, dtype=None, gradient=False):
         """u(p) = sum_j S(p, j) y_j - D(p, j) x_j at points [npoints, 3] off the
-        surface (direct sum, the entries' rules).  Returns [nrhs, npoints]."""
+        surface (direct sum, the entries' rules).  Returns [nrhs, npoints], or
+        grad u as [nrhs, npoints, 3] with gradient=True."""
         ref = x if x is not None else y
         if ref is None:
             raise ValueError("x and y cannot both be None")
@@ -127,10 +128,11 @@ class Operator:
         xs, ys = self._prep(x, dtype), self._prep(y, dtype)
         nrhs = (xs if xs is not None else ys).shape[0]
         pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
-        out = torch.empty((nrhs, pts.shape[0]), dtype=dtype, device="cuda")
+        shape = (nrhs, pts.shape[0], 3) if gradient else (nrhs, pts.shape[0])
+        out = torch.empty(shape, dtype=dtype, device="cuda")
         _lib.check(self._lib.bem_eval_points(self._h, nrhs, _dtype_code(out), None if xs is None else xs.data_ptr(),
                                              None if ys is None else ys.data_ptr(), pts.data_ptr(), pts.shape[0],
-                                             out.data_ptr(), 0, _stream()))
+                                             out.data_ptr(), _lib.BEM_EVAL_GRADIENT if gradient else 0, _stream()))
         return out
 
     def point_sources(self, points, amps, dtype=torch.complex128):

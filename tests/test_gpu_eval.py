@@ -56,6 +56,22 @@ def test_eval_points_matches_oracle(cuda_ok, mode, tol):
     op.close()
 
 
+@pytest.mark.parametrize("mode,tol", [("direct64", 1e-10), ("fp64", 1e-10), ("mixed", 1e-5)])
+def test_eval_points_gradient_matches_oracle(cuda_ok, mode, tol):
+    """grad u at the same points (every rule used) against the oracle's gradient."""
+    V, T = inputs.icosphere(3)
+    n, k = T.shape[0], 2.0
+    x = inputs.random_density(n, 2, seed=10, stream=0)
+    y = inputs.random_density(n, 2, seed=10, stream=1)
+    pts = field_points(V, T)
+    ref = oracle.eval_points_grad(V, T, k, pts, x=x, y=y)
+    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    g = op.eval_points(pts, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), gradient=True).cpu().numpy()
+    assert g.shape == ref.shape
+    assert rel(g, ref) <= tol
+    op.close()
+
+
 def test_eval_points_gauss_identity_and_errors(cuda_ok):
     """At k -> 0 the double layer of a unit density is -1 inside and 0 outside
     (the orientation of Section 2.1's normals); bad arguments are rejected."""

@@ -239,6 +239,46 @@ def test_offsurface_double_layer_of_the_mie_pressure_is_the_scattered_field():
     assert errs[0] / errs[1] > 2.5
 
 
+def test_offsurface_gradient_matches_central_differences():
+    """grad_p of the off-surface field against central differences of the
+    (pinned) field itself, for both layers, at points where every rule R_0,
+    R_1, R_2 applies (the rule changes only across the 2h / 4h thresholds,
+    which the tiny steps do not cross)."""
+    V, T = inputs.icosphere(2)
+    n, k = T.shape[0], 2.5
+    x = inputs.random_density(n, 1, seed=6, stream=0)
+    y = inputs.random_density(n, 1, seed=6, stream=1)
+    c, _, _, _ = oracle.geometry(V, T)
+    nrm = c / np.linalg.norm(c, axis=1, keepdims=True)
+    pts = np.concatenate([c[[3, 40, 77]] + nrm[[3, 40, 77]] * np.array([[0.13], [0.45], [0.9]]),
+                          np.array([[0.2, -0.1, 0.3], [2.0, 1.0, -0.5]])])
+    g = oracle.eval_points_grad(V, T, k, pts, x=x, y=y)[0]
+    h = 1e-5
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        fd = (oracle.eval_points(V, T, k, pts + e, x=x, y=y)[0] - oracle.eval_points(V, T, k, pts - e, x=x, y=y)[0]) / (2 * h)
+        assert np.max(np.abs(fd - g[:, a])) < 1e-6 * np.max(np.abs(g)), a
+
+
+def test_offsurface_gradient_of_the_mie_field():
+    """grad p_s of the rigid sphere (D p of the exact Mie surface pressure)
+    against the gradient of the Mie scattered-field closed form (central
+    differences of the series), to the discretisation error."""
+    k = 2.0
+    rng = np.random.default_rng(8)
+    d = rng.normal(size=(12, 3))
+    pts = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(1.5, 2.5, size=(12, 1))
+    h = 1e-5
+    ref = np.stack([(cf.mie_rigid_sphere_scattered(k, 1.0, pts + h * np.eye(3)[a]) -
+                     cf.mie_rigid_sphere_scattered(k, 1.0, pts - h * np.eye(3)[a])) / (2 * h) for a in range(3)], axis=1)
+    V, T = inputs.icosphere(4)
+    c, _, _, _ = oracle.geometry(V, T)
+    p = cf.mie_rigid_sphere_surface(k, 1.0, c[:, 2] / np.linalg.norm(c, axis=1))[None, :]
+    g = -oracle.eval_points_grad(V, T, k, pts, x=p)[0]
+    assert _rel(g, ref) < 1e-2
+
+
 # --- vertex / wavenumber gradient (forward-mode duals over every entry) ------
 
 def _loss(V, T, k, g, x, y):
