@@ -241,6 +241,32 @@ int bem_point_sources(bem_handle* h, int nrhs, int dtype, int nsrc, const double
                       void* out, void* stream);
 
 /*
+ * bem_point_source_field -- phi(x) = sum_m a_m G(x - x_m) (and grad phi) at
+ * arbitrary points: the incident field of the adjoint problem of Section 2.2
+ * (point sources at the observation points) anywhere in the fluid.
+ *   src    : [nsrc][3] FP64 (device);  amps : [nrhs][nsrc] complex128 (device).
+ *   points : [npoints][3] FP64 (device), away from the sources.
+ *   flags  : 0, or BEM_EVAL_GRADIENT for (phi, d/dx, d/dy, d/dz) per point.
+ *   out    : complex128 [nrhs][npoints] or [nrhs][npoints][4] (device).
+ * FP64, one thread per point; no handle needed.  Stream-ordered.
+ */
+int bem_point_source_field(int nrhs, int nsrc, const double* src, const double* amps, int64_t npoints,
+                           const double* points, double k, int flags, double* out, void* stream);
+
+/*
+ * bem_topological_derivative -- T(x) = Re[c1 grad p . grad pa - c2 p pa] at
+ * points x from the state field p and the adjoint field pa (Section 2.5, the
+ * topological derivative for an elastic inclusion appearing in the fluid:
+ * c1 = 3 (rho_s - rho_f)/(2 rho_s + rho_f), c2 = rho_f omega^2
+ * (Lambda_s - Lambda_f)/(Lambda_s Lambda_f); sound-hard limit c1 = 3/2).
+ *   state, adjoint : complex128 [npoints][4] (device): the field and its three
+ *                    gradient components at every point.
+ *   T              : FP64 [npoints] (device).
+ */
+int bem_topological_derivative(int64_t npoints, double c1, double c2, const double* state, const double* adjoint,
+                               double* T, void* stream);
+
+/*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
  * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
  *   b          : right-hand sides [nrhs][N] (device).

@@ -46,7 +46,7 @@ INFO_ORDER_OF_LEVEL = 100
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
-           "bem_eval_points", "bem_point_sources")
+           "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative")
 
 
 class BemMesh(ctypes.Structure):
@@ -102,11 +102,13 @@ def load(path: str | None = None):
     lib.bem_peak_probe.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_eval_points.argtypes = [vp, i, i, vp, vp, vp, i64, vp, i, vp]
     lib.bem_point_sources.argtypes = [vp, i, i, i, vp, vp, vp, vp]
+    lib.bem_point_source_field.argtypes = [i, i, vp, vp, i64, vp, ctypes.c_double, i, vp, vp]
+    lib.bem_topological_derivative.argtypes = [i64, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
-              "bem_eval_points", "bem_point_sources"):
+              "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -747,6 +747,80 @@ extern "C" int bem_point_sources(bem_handle* h, int nrhs, int dtype, int nsrc, c
   return BEM_OK;
 }
 
+// ---------------------------------------------- fields at arbitrary points --
+// phi(x) = sum_m a_m G(x - x_m) at points x, with grad phi = sum_m a_m F(r) (x - x_m)
+// (F = exp(ikr)(ikr - 1)/(4 pi r^3), r = |x - x_m|); FP64, one thread per point.
+// out [nrhs][npts] or, with the gradient, [nrhs][npts][4]: (phi, d/dx, d/dy, d/dz).
+__global__ void k_point_source_field(int nrhs, int nsrc, int64_t npts, double k, int grad,
+                                     const double* __restrict__ src, const double* __restrict__ amps,
+                                     const double* __restrict__ pts, double* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const double x0 = pts[3 * p], x1 = pts[3 * p + 1], x2 = pts[3 * p + 2];
+  for (int r = 0; r < nrhs; ++r) {
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int m = 0; m < nsrc; ++m) {
+      const double d0 = x0 - src[3 * m], d1 = x1 - src[3 * m + 1], d2 = x2 - src[3 * m + 2];
+      const double rr = sqrt(d0 * d0 + d1 * d1 + d2 * d2), kr = k * rr;
+      double sn, cs;
+      sincos(kr, &sn, &cs);
+      const double ar = amps[2 * ((int64_t)r * nsrc + m)], ai = amps[2 * ((int64_t)r * nsrc + m) + 1];
+      const double g = 1.0 / (4.0 * BEM_PI * rr);
+      const double er = ar * cs - ai * sn, ei = ar * sn + ai * cs;  // a exp(ikr)
+      v[0] += g * er;
+      v[1] += g * ei;
+      // a F = a exp(ikr)(ikr - 1) / (4 pi r^3)
+      const double f = g / (rr * rr);
+      const double fr = f * (-er - kr * ei), fi = f * (kr * er - ei);
+      v[2] += fr * d0;
+      v[3] += fi * d0;
+      v[4] += fr * d1;
+      v[5] += fi * d1;
+      v[6] += fr * d2;
+      v[7] += fi * d2;
+    }
+    const int w = grad ? 4 : 1;
+    for (int c = 0; c < 2 * w; ++c) out[2 * w * ((int64_t)r * npts + p) + c] = v[c];
+  }
+}
+
+// T(x) = Re[c1 grad p . grad pa - c2 p pa] from the state and adjoint fields
+// (complex128; field and gradient packed as [npts][4] complex)
+__global__ void k_topological_derivative(int64_t npts, double c1, double c2, const double* __restrict__ st,
+                                         const double* __restrict__ ad, double* __restrict__ T) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const double* a = st + 8 * p;
+  const double* b = ad + 8 * p;
+  double gg = 0.0;  // Re(grad p . grad pa)
+  for (int c = 1; c < 4; ++c) gg += a[2 * c] * b[2 * c] - a[2 * c + 1] * b[2 * c + 1];
+  const double pp = a[0] * b[0] - a[1] * b[1];
+  T[p] = c1 * gg - c2 * pp;
+}
+
+extern "C" int bem_point_source_field(int nrhs, int nsrc, const double* src, const double* amps, int64_t npoints,
+                                      const double* points, double k, int flags, double* out, void* stream) {
+  bem_set_error("");
+  if (nrhs < 1 || nsrc < 1 || npoints < 1 || !src || !amps || !points || !out || (flags & ~BEM_EVAL_GRADIENT))
+    return bem_fail(BEM_ERR_INVALID_ARG, "nrhs, nsrc, npoints >= 1; src, amps, points, out required; flags 0 or "
+                                         "BEM_EVAL_GRADIENT");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_point_source_field<<<(unsigned)((npoints + 255) / 256), 256, 0, s>>>(
+      nrhs, nsrc, npoints, k, (flags & BEM_EVAL_GRADIENT) ? 1 : 0, src, amps, points, out);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+extern "C" int bem_topological_derivative(int64_t npoints, double c1, double c2, const double* state,
+                                          const double* adjoint, double* T, void* stream) {
+  bem_set_error("");
+  if (npoints < 1 || !state || !adjoint || !T) return bem_fail(BEM_ERR_INVALID_ARG, "npoints >= 1 and buffers");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_topological_derivative<<<(unsigned)((npoints + 255) / 256), 256, 0, s>>>(npoints, c1, c2, state, adjoint, T);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 // ------------------------------------------------------------- correction --
 // z_i += sum_j C^S_ij sigma_j - C^D_ij tau_j  (values pre-divided by the weight).
 // One warp per row, accumulated in the operator's precision (FP32 in the mixed

@@ -164,6 +164,45 @@ class Operator:
         return {"p": p, "p_obs": p_obs, "weights": weights, "p_adj": p_adj, "iterations": (it_s, it_a),
                 "relres": (rel_s, rel_a)}
 
+    def point_source_field(self, points, sources, amps, gradient=False):
+        """phi(x) = sum_m a_m G(x - x_m) at points [npoints, 3] (with the
+        gradient: [nrhs, npoints, 4] = phi, d/dx, d/dy, d/dz)."""
+        pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        src = torch.as_tensor(sources, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        a = torch.as_tensor(amps).to("cuda", torch.complex128)
+        a = _raw(a if a.dim() == 2 else a[None])
+        shape = (a.shape[0], pts.shape[0], 4) if gradient else (a.shape[0], pts.shape[0])
+        out = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        _lib.check(self._lib.bem_point_source_field(a.shape[0], src.shape[0], src.data_ptr(), a.data_ptr(),
+                                                    pts.shape[0], pts.data_ptr(), float(self.k),
+                                                    _lib.BEM_EVAL_GRADIENT if gradient else 0, out.data_ptr(),
+                                                    _stream()))
+        return out
+
+    def topological_derivative(self, points, chain, observers, incident, c1=1.5, c2=None):
+        """T(x) = Re[c1 grad p . grad pa - c2 p pa] at points in the fluid
+        (Section 2.5), from a state_and_adjoint result `chain` of the rigid
+        body: p = p_inc + D p_surf and pa = phi + D pa_surf, phi the point
+        sources at the observers with the adjoint weights.  incident:
+        [npoints, 4] complex, the incident field and its gradient at the
+        points (the caller's incident wave).  c1 = 3/2 and c2 = k^2 are the
+        sound-hard limit in units rho_f = c_f = 1."""
+        c2 = self.k ** 2 if c2 is None else float(c2)
+        pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        inc = _raw(torch.as_tensor(incident).to("cuda", torch.complex128).reshape(-1, 4))
+
+        def field(surface):  # D surface at the points, with its gradient: [npoints, 4]
+            u = -self.eval_points(pts, x=surface.to(torch.complex128))[0]
+            gu = -self.eval_points(pts, x=surface.to(torch.complex128), gradient=True)[0]
+            return torch.cat([u[:, None], gu], dim=1)
+
+        state = _raw(inc + field(chain["p"]))
+        adj = _raw(self.point_source_field(pts, observers, chain["weights"], gradient=True)[0] + field(chain["p_adj"]))
+        T = torch.empty(pts.shape[0], dtype=torch.float64, device="cuda")
+        _lib.check(self._lib.bem_topological_derivative(pts.shape[0], float(c1), c2, state.data_ptr(), adj.data_ptr(),
+                                                        T.data_ptr(), _stream()))
+        return T
+
     def apply_host(self, x=None, y=None, out=None, no_half=False):
         """Same as apply() for host arrays/tensors (pinned is best); copies are inside the call."""
         x = None if x is None else _raw(x)

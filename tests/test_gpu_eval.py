@@ -137,3 +137,44 @@ def test_state_observation_adjoint_chain(cuda_ok, mode, tol):
     assert rel(badj, badj_ref) <= 1e-12
     assert rel(out["p_adj"].cpu().numpy(), padj_ref) <= tol
     op.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("direct64", 1e-7), ("mixed", 1e-4)])
+def test_topological_derivative_on_a_lattice(cuda_ok, mode, tol):
+    """T(x) = Re[3/2 grad p . grad pa - k^2 p pa] (Section 2.5, sound-hard limit)
+    on lattice points around the rigid sphere, built from the state and adjoint
+    chain, against the same quantity composed from the oracle's LU solutions,
+    off-surface values and gradients."""
+    V, T = inputs.icosphere(3)
+    k = 2.0
+    c, _, _, _ = oracle.geometry(V, T)
+    obs = np.array([[5.0, 0, 0], [-5.0, 0, 0], [0, 0, 5.0], [0, 0, -5.0]])
+    b = inputs.plane_wave(c, k)[None, :]
+    S, D = oracle.assemble(V, T, k)
+    A = 0.5 * np.eye(T.shape[0]) - D
+    p_ref = oracle.lu_solve(A, b)
+    inc_obs = np.exp(1j * k * obs[:, 2])
+    w_ref = np.conj(inc_obs - oracle.eval_points(V, T, k, obs, x=p_ref)[0])
+    r = np.linalg.norm(c[:, None, :] - obs[None, :, :], axis=2)
+    pa_ref = oracle.lu_solve(A, ((np.exp(1j * k * r) / (4 * np.pi * r)) @ w_ref)[None, :])
+    g = np.linspace(-2.0, 2.0, 7)
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    lat = lat[np.linalg.norm(lat, axis=1) > 1.2]
+    # oracle composition
+    inc = np.exp(1j * k * lat[:, 2])
+    inc4 = np.stack([inc, 0 * inc, 0 * inc, 1j * k * inc], axis=1)
+    p_f = inc - oracle.eval_points(V, T, k, lat, x=p_ref)[0]
+    gp_f = inc4[:, 1:] - oracle.eval_points_grad(V, T, k, lat, x=p_ref)[0]
+    d = lat[:, None, :] - obs[None, :, :]
+    rr = np.linalg.norm(d, axis=2)
+    e = np.exp(1j * k * rr) * w_ref[None, :]
+    phi = np.sum(e / (4 * np.pi * rr), axis=1)
+    gphi = np.einsum("pm,pmc->pc", e * (1j * k * rr - 1) / (4 * np.pi * rr ** 3), d)
+    pa_f = phi - oracle.eval_points(V, T, k, lat, x=pa_ref)[0]
+    gpa_f = gphi - oracle.eval_points_grad(V, T, k, lat, x=pa_ref)[0]
+    T_ref = np.real(1.5 * np.sum(gp_f * gpa_f, axis=1) - k * k * p_f * pa_f)
+    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    chain = op.state_and_adjoint(torch.from_numpy(b).cuda(), obs, inc_obs, tol=1e-10 if mode == "direct64" else 1e-8)
+    Tg = op.topological_derivative(lat, chain, obs, inc4).cpu().numpy()
+    assert rel(Tg, T_ref) <= tol
+    op.close()
