@@ -558,6 +558,27 @@ def run_other(args):
                 eval_field = {"points": int(lat.shape[0]), "ms": ev_ms,
                               "point_element_pairs_per_s": lat.shape[0] * n / (ev_ms * 1e-3),
                               "rel_err_vs_oracle_200_points": _rel(fld.cpu().numpy()[0, smp], ev_ref)}
+                # the chain of Section 2.2 and the topological derivative (Section 2.5,
+                # sound-hard limit) on the same lattice: 4 observers at distance 5
+                obs = np.array([[5.0, 0, 0], [-5.0, 0, 0], [0, 0, 5.0], [0, 0, -5.0]])
+                inc_obs = np.exp(1j * k * obs[:, 2])
+                inc = torch.exp(1j * k * latd[:, 2])
+                inc4 = torch.stack([inc, 0 * inc, 0 * inc, 1j * k * inc], dim=1)
+                op.state_and_adjoint(b, obs, inc_obs, tol=1e-6)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                chain = op.state_and_adjoint(b, obs, inc_obs, tol=1e-6)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                Tl = op.topological_derivative(latd, chain, obs, inc4)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                gpa = op.eval_points(latd[smp], x=chain["p_adj"].to(torch.complex128), gradient=True).cpu().numpy()[0]
+                gpa_ref = oracle.eval_points_grad(V, T, k, lat[smp], x=chain["p_adj"].cpu().numpy().astype(np.complex128))[0]
+                eval_field["topological_derivative"] = {
+                    "chain_s": t1 - t0, "lattice_T_s": t2 - t1, "iterations": list(chain["iterations"]),
+                    "T_range": [float(Tl.min()), float(Tl.max())],
+                    "grad_adjoint_field_rel_err_vs_oracle_200_points": _rel(gpa, gpa_ref)}
             res[mode] = {"apply_ms_17rhs": ms, "rhs_matvecs_per_s": 17e3 / ms,
                          "rel_err_S_per_rhs_max": max(_rel(zs[q], ref_s[q]) for q in range(17)),
                          "rel_err_z_per_rhs_max": max(_rel(zd[q], ref_d[q]) for q in range(17)),
