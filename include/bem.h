@@ -301,7 +301,7 @@ int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, 
  * and wavenumber: the state and adjoint solves of Section 2.5 repeated over a
  * population of designs).  Every problem keeps its own octree and operators;
  * a batch apply runs all of them from one captured CUDA graph whose branches
- * (problems spread over 8 forked streams) execute concurrently.
+ * (problems spread over up to 64 forked streams) execute concurrently.
  */
 typedef struct bem_batch bem_batch;
 

@@ -13,7 +13,7 @@
 
 #include "bem_common.cuh"
 
-#define BEM_BATCH_STREAMS 8
+#define BEM_BATCH_STREAMS 64
 
 struct bem_batch {
   std::vector<bem_handle*> h;
@@ -154,11 +154,12 @@ extern "C" int bem_setup_batch(const bem_mesh* meshes, const double* ks, int cou
 // (events) stay off, so that the work can be captured
 static int issue_batch(bem_batch* b, int nrhs, int half, cudaStream_t s) {
   int rc = BEM_OK;
+  const int ns = std::min<int>(BEM_BATCH_STREAMS, (int)b->h.size());  // streams in use
   BEM_CUDA(cudaEventRecord(b->ev_fork, s));
-  for (int i = 0; i < BEM_BATCH_STREAMS; ++i) BEM_CUDA(cudaStreamWaitEvent(b->fork[i], b->ev_fork, 0));
+  for (int i = 0; i < ns; ++i) BEM_CUDA(cudaStreamWaitEvent(b->fork[i], b->ev_fork, 0));
   for (size_t p = 0; p < b->h.size() && rc == BEM_OK; ++p) {
     bem_handle* h = b->h[p];
-    cudaStream_t fs = b->fork[p % BEM_BATCH_STREAMS];
+    cudaStream_t fs = b->fork[p % ns];
     const double* x = b->sx + 2 * nrhs * b->off[p];
     const double* y = b->sy + 2 * nrhs * b->off[p];
     double* z = b->sz + 2 * nrhs * b->off[p];
@@ -171,7 +172,7 @@ static int issue_batch(bem_batch* b, int nrhs, int half, cudaStream_t s) {
   }
   // join every forked stream, also after a failure, so that no stream is left
   // waiting outside a capture that ends
-  for (int i = 0; i < BEM_BATCH_STREAMS; ++i) {
+  for (int i = 0; i < ns; ++i) {
     cudaError_t e = cudaEventRecord(b->ev_join[i], b->fork[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[i], 0);
     if (e != cudaSuccess && rc == BEM_OK) rc = bem_fail(BEM_ERR_CUDA, std::string("batch join: ") + cudaGetErrorString(e));
