@@ -75,6 +75,9 @@ static void free_handle(bem_handle* h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->s_far) cudaStreamDestroy(h->s_far);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   cudaSetDevice(cur);
@@ -150,6 +153,15 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   };
   int rc;
   if ((rc = bem_alloc(h, &h->d_err, 1)) != BEM_OK) return fail(rc);
+  {
+    // the far field's stream (see the apply): the greatest priority
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->s_far, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(bem_fail(BEM_ERR_CUDA, std::string("far-field stream: ") + cudaGetErrorString(e)));
+  }
   if (cudaMemsetAsync(h->d_err, 0, sizeof(int), s) != cudaSuccess) return fail(bem_fail(BEM_ERR_CUDA, "memset"));
 
   // device copy of the mesh

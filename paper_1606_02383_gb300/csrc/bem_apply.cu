@@ -1,6 +1,7 @@
 // bem_apply.cu -- the hot path: z = (1/2 I - D) x + S y  (Section 2.3, step 2(c)).
 //
-// Stages of one apply (all on the caller's stream):
+// Stages of one apply (on the caller's stream, except the far field, which
+// runs on the handle's high-priority stream beside the correction):
 //   prologue  : gather x, y into octree order, weighted by w_j = A_j/(12 pi)
 //   P2P       : regular-rule near field, leaf box against its 27 colleagues,
 //               FP32 (range-reduced sincos) or FP64
@@ -1238,6 +1239,72 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   }
   BEM_CUDA(cudaGetLastError());
   bem_prof_end(h, pr, 1, nl, s);
+  if (!fmm || L < 2) {
+    pr = bem_prof_begin(h, s);
+    nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+      k_correction<V4, R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(
+          nt, r0, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->zn);
+    });
+    BEM_CUDA(cudaGetLastError());
+    bem_prof_end(h, pr, 2, nl, s);
+    BEM_CUDA(cudaMemsetAsync(h->zfar, 0, sizeof(double) * 2 * nt * nrhs, s));
+    return BEM_OK;
+  }
+  auto far = [&](cudaStream_t s) -> int {
+    int pr, nl;
+    // far field
+    size_t esz = 2 * sizeof(R);
+    LevelInfo& lf = h->lev[L];
+    pr = bem_prof_begin(h, s);
+    BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
+    BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
+    if constexpr (sizeof(R) == 4) {
+      nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+        k_p2m_v<decltype(nr)::value><<<dim3(lf.nbox, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
+            lf.nbox, nt, r0, lf.P, lf.start, lf.end, (const float*)h->p2m_rows, (const float4*)dens, lf.exp_base,
+            h->exp_total, (float*)h->Mexp);
+      });
+    } else {
+      nl = 1;
+      k_p2m<R><<<dim3(lf.nbox, nrhs), 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens,
+                                                   lf.exp_base, h->exp_total, (R*)h->Mexp);
+    }
+    BEM_CUDA(cudaGetLastError());
+    bem_prof_end(h, pr, 3, nl, s);
+    nl = 0;
+    pr = bem_prof_begin(h, s);
+    for (int l = L - 1; l >= 2; --l) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s, &nl));
+    bem_prof_end(h, pr, 4, nl, s);
+    nl = 0;
+    pr = bem_prof_begin(h, s);
+    for (int l = 2; l <= L; ++l) BEM_TRY(run_grouped<R>(h, h->m2l[l], h->Mexp, h->Lexp, nrhs, s, &nl));
+    bem_prof_end(h, pr, 5, nl, s);
+    nl = 0;
+    pr = bem_prof_begin(h, s);
+    for (int l = 2; l < L; ++l) BEM_TRY(run_grouped<R>(h, h->l2l[l], h->Lexp, h->Lexp, nrhs, s, &nl));
+    bem_prof_end(h, pr, 6, nl, s);
+    pr = bem_prof_begin(h, s);
+    nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+      const dim3 grid(nblk(nt * 32, 256), nchunk);
+      if constexpr (sizeof(R) == 4 && decltype(nr)::value == 1)
+        k_l2p_f1<<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const float*)h->l2p_rows, (const float*)h->Lexp,
+                                      lf.exp_base, h->exp_total, h->zfar);
+      else
+        k_l2p<R, decltype(nr)::value><<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows,
+                                                           (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
+    });
+    BEM_CUDA(cudaGetLastError());
+    bem_prof_end(h, pr, 7, nl, s);
+    return BEM_OK;
+  };
+  // After the P2P, the far field runs on the handle's high-priority second
+  // stream beside the correction (40,960 short CTAs that would otherwise fill
+  // the SMs ahead of the translation chain's small launches); both join back
+  // into `s`.  The P2P itself stays alone: its long-lived CTAs fill the
+  // registers of every SM, and a far field forked before it waited for them.
+  BEM_CUDA(cudaEventRecord(h->ev_fork, s));
+  BEM_CUDA(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
+  const int rc = far(h->s_far);
   pr = bem_prof_begin(h, s);
   nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
     k_correction<V4, R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(
@@ -1245,53 +1312,10 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   });
   BEM_CUDA(cudaGetLastError());
   bem_prof_end(h, pr, 2, nl, s);
-  if (!fmm || L < 2) {
-    BEM_CUDA(cudaMemsetAsync(h->zfar, 0, sizeof(double) * 2 * nt * nrhs, s));
-    return BEM_OK;
-  }
-  // far field
-  size_t esz = 2 * sizeof(R);
-  LevelInfo& lf = h->lev[L];
-  pr = bem_prof_begin(h, s);
-  BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
-  BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
-  if constexpr (sizeof(R) == 4) {
-    nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-      k_p2m_v<decltype(nr)::value><<<dim3(lf.nbox, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
-          lf.nbox, nt, r0, lf.P, lf.start, lf.end, (const float*)h->p2m_rows, (const float4*)dens, lf.exp_base,
-          h->exp_total, (float*)h->Mexp);
-    });
-  } else {
-    nl = 1;
-    k_p2m<R><<<dim3(lf.nbox, nrhs), 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens,
-                                                 lf.exp_base, h->exp_total, (R*)h->Mexp);
-  }
-  BEM_CUDA(cudaGetLastError());
-  bem_prof_end(h, pr, 3, nl, s);
-  nl = 0;
-  pr = bem_prof_begin(h, s);
-  for (int l = L - 1; l >= 2; --l) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s, &nl));
-  bem_prof_end(h, pr, 4, nl, s);
-  nl = 0;
-  pr = bem_prof_begin(h, s);
-  for (int l = 2; l <= L; ++l) BEM_TRY(run_grouped<R>(h, h->m2l[l], h->Mexp, h->Lexp, nrhs, s, &nl));
-  bem_prof_end(h, pr, 5, nl, s);
-  nl = 0;
-  pr = bem_prof_begin(h, s);
-  for (int l = 2; l < L; ++l) BEM_TRY(run_grouped<R>(h, h->l2l[l], h->Lexp, h->Lexp, nrhs, s, &nl));
-  bem_prof_end(h, pr, 6, nl, s);
-  pr = bem_prof_begin(h, s);
-  nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-    const dim3 grid(nblk(nt * 32, 256), nchunk);
-    if constexpr (sizeof(R) == 4 && decltype(nr)::value == 1)
-      k_l2p_f1<<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const float*)h->l2p_rows, (const float*)h->Lexp,
-                                    lf.exp_base, h->exp_total, h->zfar);
-    else
-      k_l2p<R, decltype(nr)::value><<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows,
-                                                         (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
-  });
-  BEM_CUDA(cudaGetLastError());
-  bem_prof_end(h, pr, 7, nl, s);
+  cudaError_t e = cudaEventRecord(h->ev_join, h->s_far);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
+  BEM_TRY(rc);
+  BEM_CUDA(e);
   return BEM_OK;
 }
 

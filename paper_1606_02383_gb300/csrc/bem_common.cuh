@@ -252,6 +252,9 @@ struct bem_handle {
   void* io_x = nullptr;     // staging for BEM_HOST_BUFFERS: [nrhs_max][nt] complex double each
   void* io_y = nullptr;
   void* io_z = nullptr;
+  // the far field's high-priority stream, forked after the P2P and joined back
+  cudaStream_t s_far = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // profiling
   int prof_on = 0;
   std::vector<ProfRec> prof;
