@@ -351,6 +351,18 @@ def run_ours(args, world, rank, local):
         ops.close()
         also = {"multi_rhs": multi, "gmres_plane_wave": {"ka": ks, "tol": 1e-5, "iterations": iters,
                                                          "relres": float(relres[0]), "seconds": gm_s}}
+        # the conjugate-transpose apply (the autograd backward of an apply)
+        op.adjoint(xd)
+        tot = 0.0
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            op.adjoint(xd)
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        also["adjoint_apply"] = {"ms_per_apply": tot / 10, "applies_per_s": 1e4 / tot}
         # the same sphere at ka = 1 and 5 (mixed), and the all-FP64 FMM at the headline ka:
         # throughput, setup and the error on 500 oracle rows
         import oracle

@@ -13,7 +13,10 @@
 //                every factor transposed: L2P^T (leaf sums of the L2P rows),
 //                L2L^T upward, M2L^T across, M2M^T downward, P2M^T (dot
 //                products with the P2M rows).
+#include <cub/cub.cuh>
+
 #include "bem_common.cuh"
+#include "bem_f32x2.cuh"
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -140,6 +143,71 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
   const V4* dr = dens + (int64_t)r * nt;
   int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
   R ua_re = 0, ua_im = 0, va_re = 0, va_im = 0, ub_re = 0, ub_im = 0, vb_re = 0, vb_im = 0;
+  if constexpr (sizeof(R) == 4) {
+    // packed: the lane's two elements a, b go through one f32x2 instruction
+    // per operation; each source centroid and weight is broadcast once
+    f32x2 px[3], py[3], pz[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      px[q] = pk2(qa[q].x, qb[q].x);
+      py[q] = pk2(qa[q].y, qb[q].y);
+      pz[q] = pk2(qa[q].z, qb[q].z);
+    }
+    const f32x2 pnx = pk2(qa[0].w, qb[0].w), pny = pk2(qa[1].w, qb[1].w), pnz = pk2(qa[2].w, qb[2].w);
+    const f32x2 pk_k = pk2((float)k, (float)k), m1 = pk2(-1.f, -1.f);
+    f32x2 u_re = pk2(0.f, 0.f), u_im = u_re, v_re = u_re, v_im = u_re;
+    for (int slot = 0; slot < 27; ++slot) {
+      int sb = near27[27 * b + slot];
+      if (sb < 0) continue;
+      const float sx = (float)((coord[3 * sb] - bx) * (double)wleaf);
+      const float sy = (float)((coord[3 * sb + 1] - by) * (double)wleaf);
+      const float sz = (float)((coord[3 * sb + 2] - bz) * (double)wleaf);
+      int e1 = bend[sb];
+      for (int e = bstart[sb] + split; e < e1; e += nsplit) {
+        const V4 x = tgt[e];
+        const V4 d = dr[e];
+        const float nxx = -(x.x + sx), nxy = -(x.y + sy), nxz = -(x.z + sz);
+        const f32x2 cx = pk2(nxx, nxx), cy = pk2(nxy, nxy), cz = pk2(nxz, nxz);
+        const f32x2 hre = pk2(d.x, d.x), him = pk2(d.y, d.y), nhre = pk2(-d.x, -d.x), nhim = pk2(-d.y, -d.y);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const f32x2 dx = add2(px[q], cx), dy = add2(py[q], cy), dz = add2(pz[q], cz);
+          const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          float r2a, r2b;
+          upk2(r2, r2a, r2b);
+          const f32x2 ri = pk2(rsqrtf(r2a), rsqrtf(r2b));
+          const f32x2 kr = mul2(pk_k, mul2(r2, ri));
+          float kra, krb, sa, ca, sb_, cb;
+          upk2(kr, kra, krb);
+          __sincosf(kra, &sa, &ca);  // |kr| stays small in the near field
+          __sincosf(krb, &sb_, &cb);
+          const f32x2 gre = mul2(ri, pk2(ca, cb)), gim = mul2(ri, pk2(sa, sb_));
+          const f32x2 ngim = mul2(gim, m1);
+          const f32x2 f = mul2(fma2(dx, pnx, fma2(dy, pny, mul2(dz, pnz))), mul2(ri, ri));
+          // (dre, dim) = f (ikr - 1) (gre + i gim)
+          const f32x2 ndre = mul2(f, fma2(kr, gim, gre));      // -dre
+          const f32x2 dim = mul2(f, fma2(kr, gre, ngim));
+          u_re = fma2(gre, hre, fma2(ngim, him, u_re));
+          u_im = fma2(gre, him, fma2(gim, hre, u_im));
+          v_re = fma2(dim, nhim, fma2(ndre, nhre, v_re));
+          v_im = fma2(dim, hre, fma2(ndre, nhim, v_im));
+        }
+      }
+    }
+    float lo, hi;
+    upk2(u_re, lo, hi);
+    ua_re = lo;
+    ub_re = hi;
+    upk2(u_im, lo, hi);
+    ua_im = lo;
+    ub_im = hi;
+    upk2(v_re, lo, hi);
+    va_re = lo;
+    vb_re = hi;
+    upk2(v_im, lo, hi);
+    va_im = lo;
+    vb_im = hi;
+  } else
   for (int slot = 0; slot < 27; ++slot) {
     int sb = near27[27 * b + slot];
     if (sb < 0) continue;
@@ -215,23 +283,111 @@ __global__ void __launch_bounds__(128) k_p2p_adj_direct(int64_t nt, R k, const t
 }
 
 // correction, transposed: warp per row i, entries scattered into their columns
+// the correction's transpose by counting sort: entries per column, their
+// offsets, then every entry scattered to its column (order within a column
+// follows the atomics)
+__global__ void k_corrT_count(int64_t nnz, const int* __restrict__ col, int* cnt) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nnz) atomicAdd(&cnt[col[e]], 1);
+}
 template <typename V4>
-__global__ void k_corr_adj(int64_t nt, const int* __restrict__ ptr, const int* __restrict__ col,
-                           const V4* __restrict__ val, const V4* __restrict__ dens, double4* __restrict__ uv) {
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  int r = blockIdx.y;
+__global__ void k_corrT_fill(int64_t nt, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const V4* __restrict__ val, const int* __restrict__ ptrT, int* fill, int* rowT,
+                             V4* valT) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= nt) return;
-  V4 h = dens[(int64_t)r * nt + i];
-  double hr = h.x, hi = h.y;
   for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
-    V4 c = val[e];
-    double* t = (double*)(uv + (int64_t)r * nt + col[e]);
-    atomicAdd(t + 0, (double)c.x * hr - (double)c.y * hi);
-    atomicAdd(t + 1, (double)c.x * hi + (double)c.y * hr);
-    atomicAdd(t + 2, (double)c.z * hr - (double)c.w * hi);
-    atomicAdd(t + 3, (double)c.z * hi + (double)c.w * hr);
+    const int j = col[e];
+    const int pos = ptrT[j] + atomicAdd(&fill[j], 1);
+    rowT[pos] = (int)i;
+    valT[pos] = val[e];
   }
+}
+
+// uv_j += sum_i C_ij h_i through the transpose: one warp per column j, the
+// value and row loads of two entries per lane issued before their gathers,
+// accumulated in the operator's precision
+template <typename V4, typename R>
+__global__ void k_corr_adj(int64_t nt, const int* __restrict__ ptrT, const int* __restrict__ rowT,
+                           const V4* __restrict__ valT, const V4* __restrict__ dens, double4* __restrict__ uv) {
+  const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.y;
+  if (j >= nt) return;
+  const V4* dr = dens + (int64_t)r * nt;
+  R ur = 0, ui = 0, vr = 0, vi = 0;
+  const int e1 = ptrT[j + 1];
+  for (int eb = ptrT[j] + lane; eb < e1; eb += 64) {
+    V4 c[2];
+    int ri[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (eb + 32 * u < e1) {
+        c[u] = valT[eb + 32 * u];
+        ri[u] = rowT[eb + 32 * u];
+      }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (eb + 32 * u >= e1) break;
+      const V4 h = dr[ri[u]];
+      ur += c[u].x * h.x - c[u].y * h.y;
+      ui += c[u].x * h.y + c[u].y * h.x;
+      vr += c[u].z * h.x - c[u].w * h.y;
+      vi += c[u].z * h.y + c[u].w * h.x;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ur += __shfl_xor_sync(0xffffffffu, ur, o);
+    ui += __shfl_xor_sync(0xffffffffu, ui, o);
+    vr += __shfl_xor_sync(0xffffffffu, vr, o);
+    vi += __shfl_xor_sync(0xffffffffu, vi, o);
+  }
+  if (lane == 0) {
+    double4* t = uv + (int64_t)r * nt + j;
+    double4 a = *t;
+    a.x += (double)ur;
+    a.y += (double)ui;
+    a.z += (double)vr;
+    a.w += (double)vi;
+    *t = a;
+  }
+}
+
+template <typename V4>
+static int build_corr_transpose(bem_handle* h, cudaStream_t s) {
+  const int64_t nt = h->nt, nnz = h->corr_nnz;
+  BEM_TRY(bem_alloc(h, &h->corrT_ptr, nt + 1));
+  int* rowT;
+  V4* valT;
+  BEM_TRY(bem_alloc(h, &rowT, std::max<int64_t>(nnz, 1)));
+  BEM_TRY(bem_alloc(h, &valT, std::max<int64_t>(nnz, 1)));
+  h->corrT_row = rowT;
+  h->corrT_val = valT;
+  int *cnt = nullptr, *fill = nullptr;
+  void* tmp = nullptr;
+  BEM_CUDA(cudaMallocAsync((void**)&cnt, (nt + 1) * sizeof(int), s));
+  BEM_CUDA(cudaMallocAsync((void**)&fill, nt * sizeof(int), s));
+  BEM_CUDA(cudaMemsetAsync(cnt, 0, (nt + 1) * sizeof(int), s));
+  BEM_CUDA(cudaMemsetAsync(fill, 0, nt * sizeof(int), s));
+  if (nnz > 0) k_corrT_count<<<nblk(nnz, 256), 256, 0, s>>>(nnz, h->corr_col, cnt);
+  size_t tb = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt, h->corrT_ptr, (int)nt + 1, s);
+  BEM_CUDA(cudaMallocAsync(&tmp, tb, s));
+  BEM_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tb, cnt, h->corrT_ptr, (int)nt + 1, s));
+  k_corrT_fill<V4><<<nblk(nt * 32, 256), 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val,
+                                                      h->corrT_ptr, fill, rowT, valT);
+  BEM_CUDA(cudaGetLastError());
+  cudaFreeAsync(tmp, s);
+  cudaFreeAsync(cnt, s);
+  cudaFreeAsync(fill, s);
+  return BEM_OK;
+}
+
+int bem_build_corr_transpose(bem_handle* h, cudaStream_t s) {
+  if (h->corrT_ptr) return BEM_OK;
+  if (bem_is_fp64(h)) return build_corr_transpose<double4>(h, s);
+  return build_corr_transpose<float4>(h, s);
 }
 
 // L2P^T: Lambda_b = sum_{i in b} rows_r[i] h_i  (leaf level)
@@ -303,6 +459,7 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
   bool fmm = bem_is_fmm(h);
   int L = h->L;
+  int pr = bem_prof_begin(h, s);
   if (fmm) {
     LevelInfo& lf = h->lev[L];
     dim3 grid(nblk(h->n_p2p_units, ADJ_WARPS), nrhs);
@@ -313,14 +470,18 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
     k_p2p_adj_direct<R><<<grid, 128, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->uv);
   }
   BEM_CUDA(cudaGetLastError());
+  bem_prof_end(h, pr, 1, 1, s);
+  pr = bem_prof_begin(h, s);
   {
     dim3 grid(nblk(nt * 32, 256), nrhs);
-    k_corr_adj<V4><<<grid, 256, 0, s>>>(nt, h->corr_ptr, h->corr_col, (const V4*)h->corr_val, dens, h->uv);
+    k_corr_adj<V4, R><<<grid, 256, 0, s>>>(nt, h->corrT_ptr, h->corrT_row, (const V4*)h->corrT_val, dens, h->uv);
     BEM_CUDA(cudaGetLastError());
   }
+  bem_prof_end(h, pr, 2, 1, s);
   if (!fmm || L < 2) return BEM_OK;
   size_t esz = 2 * sizeof(R);
   LevelInfo& lf = h->lev[L];
+  pr = bem_prof_begin(h, s);
   BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
   BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
   {
@@ -329,16 +490,27 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
                                     h->exp_total, (R*)h->Lexp);
     BEM_CUDA(cudaGetLastError());
   }
+  bem_prof_end(h, pr, 7, 1, s);
   int nl = 0;
+  pr = bem_prof_begin(h, s);
   for (int l = L - 1; l >= 2; --l) BEM_TRY(bem_run_grouped(h, h->l2l_T[l], h->Lexp, h->Lexp, nrhs, s, &nl));
+  bem_prof_end(h, pr, 6, nl, s);
+  nl = 0;
+  pr = bem_prof_begin(h, s);
   for (int l = 2; l <= L; ++l) BEM_TRY(bem_run_grouped(h, h->m2l_T[l], h->Lexp, h->Mexp, nrhs, s, &nl));
+  bem_prof_end(h, pr, 5, nl, s);
+  nl = 0;
+  pr = bem_prof_begin(h, s);
   for (int l = 2; l < L; ++l) BEM_TRY(bem_run_grouped(h, h->m2m_T[l], h->Mexp, h->Mexp, nrhs, s, &nl));
+  bem_prof_end(h, pr, 4, nl, s);
+  pr = bem_prof_begin(h, s);
   {
     dim3 grid(nblk(nt * 32, 256), nrhs);
     k_p2m_t<R><<<grid, 256, 0, s>>>(nt, lf.P, h->leaf_of, (const R*)h->p2m_rows, (const R*)h->Mexp, lf.exp_base,
                                     h->exp_total, h->uv);
     BEM_CUDA(cudaGetLastError());
   }
+  bem_prof_end(h, pr, 3, 1, s);
   return BEM_OK;
 }
 

@@ -222,6 +222,10 @@ struct bem_handle {
   int* corr_col = nullptr;      // [nnz]
   void* corr_val = nullptr;     // [nnz] of {S, D} complex (float4 or double4)
   int64_t corr_nnz = 0;
+  // the correction's transpose (columns -> rows), built with the adjoint operators
+  int* corrT_ptr = nullptr;     // [nt+1]
+  int* corrT_row = nullptr;     // [nnz]
+  void* corrT_val = nullptr;    // [nnz], same type as corr_val
 
   // far field
   GroupedOp m2m[BEM_MAXLEV + 1];  // index l: child level l+1 -> parent level l
@@ -316,6 +320,7 @@ int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double
               int flags, int* iters_out, double* relres_out, cudaStream_t s);
 int bem_check_device_error(bem_handle* h, cudaStream_t s);
 int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s);
+int bem_build_corr_transpose(bem_handle* h, cudaStream_t s);
 int bem_build_adjoint(bem_handle* h, cudaStream_t s);
 int bem_adjoint_sorted(bem_handle* h, int nrhs, int dtype, const void* g, void* gx, void* gy, int half,
                        cudaStream_t s);

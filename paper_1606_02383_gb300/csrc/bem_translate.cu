@@ -837,6 +837,7 @@ int bem_build_adjoint(bem_handle* h, cudaStream_t s) {
       BEM_TRY(make_transposed(h, h->l2l[l], h->l2l_T[l], l + 1, s));  // children -> parent level
     }
   }
+  BEM_TRY(bem_build_corr_transpose(h, s));
   BEM_CUDA(cudaStreamSynchronize(s));
   h->adj_ready = true;
   return BEM_OK;
