@@ -31,26 +31,32 @@ __global__ void k_grad_prologue(int64_t nt, int nrhs, const int* __restrict__ pe
   }
 }
 
+// sin/cos in the precision of the evaluation
+__device__ __forceinline__ void gsc(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void gsc(double a, double* s, double* c) { sincos(a, s, c); }
+
 // d/dk of one point of weight wq: returns (dS, dD) contributions at target x
-__device__ __forceinline__ void dk_point(const double* x, const double* y, const double* n, double wq, double k,
-                                         zd& ds, zd& dd) {
-  double d0 = y[0] - x[0], d1 = y[1] - x[1], d2 = y[2] - x[2];
-  double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-  double sn, cs;
-  sincos(k * r, &sn, &cs);
-  double c = wq / (4.0 * BEM_PI);
+template <typename R>
+__device__ __forceinline__ void dk_point(const R* x, const R* y, const R* n, R wq, R k, cpx<R>& ds, cpx<R>& dd) {
+  R d0 = y[0] - x[0], d1 = y[1] - x[1], d2 = y[2] - x[2];
+  R r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  R sn, cs;
+  gsc(k * r, &sn, &cs);
+  R c = wq / R(4.0 * BEM_PI);
   // i e^{ikr} = -sin + i cos
   ds.re += c * (-sn);
   ds.im += c * cs;
-  double dn = d0 * n[0] + d1 * n[1] + d2 * n[2];
-  double f = -c * k * dn / r;
+  R dn = d0 * n[0] + d1 * n[1] + d2 * n[2];
+  R f = -c * k * dn / r;
   dd.re += f * cs;
   dd.im += f * sn;
 }
 
-struct GTri {
-  double v[3][3], n[3], c[3], area, h;
+template <typename R>
+struct GTriT {
+  R v[3][3], n[3], c[3], area, h;
 };
+typedef GTriT<double> GTri;
 
 __device__ void gload(const double* __restrict__ qpt, const double* __restrict__ nrm, const double* __restrict__ cent,
                       const double* __restrict__ area, const double* __restrict__ hmax, int j, GTri& t) {
@@ -64,11 +70,12 @@ __device__ void gload(const double* __restrict__ qpt, const double* __restrict__
 }
 
 // d/dk of rule R_L on triangle t (4^L congruent pieces, 3-point rule each)
-__device__ void dk_rule(const double* x, const GTri& t, int L, double k, zd& ds, zd& dd) {
+template <typename R>
+__device__ void dk_rule(const R* x, const GTriT<R>& t, int L, R k, cpx<R>& ds, cpx<R>& dd) {
   int npieces = 1 << (2 * L);
-  double w = t.area / (3.0 * npieces);
+  R w = t.area / (R(3) * npieces);
   for (int piece = 0; piece < npieces; ++piece) {
-    double a[3], b[3], c[3];
+    R a[3], b[3], c[3];
     for (int d = 0; d < 3; ++d) {
       a[d] = t.v[0][d];
       b[d] = t.v[1][d];
@@ -78,11 +85,11 @@ __device__ void dk_rule(const double* x, const GTri& t, int L, double k, zd& ds,
     for (int lvl = 0; lvl < L; ++lvl) {
       int child = code & 3;
       code >>= 2;
-      double ab[3], bc[3], ca[3];
+      R ab[3], bc[3], ca[3];
       for (int d = 0; d < 3; ++d) {
-        ab[d] = 0.5 * (a[d] + b[d]);
-        bc[d] = 0.5 * (b[d] + c[d]);
-        ca[d] = 0.5 * (c[d] + a[d]);
+        ab[d] = R(0.5) * (a[d] + b[d]);
+        bc[d] = R(0.5) * (b[d] + c[d]);
+        ca[d] = R(0.5) * (c[d] + a[d]);
       }
       for (int d = 0; d < 3; ++d) {
         if (child == 0) {
@@ -101,9 +108,9 @@ __device__ void dk_rule(const double* x, const GTri& t, int L, double k, zd& ds,
         }
       }
     }
-    const double b0 = 2.0 / 3.0, b1 = 1.0 / 6.0;
+    const R b0 = R(2) / R(3), b1 = R(1) / R(6);
     for (int q = 0; q < 3; ++q) {
-      double y[3];
+      R y[3];
       for (int d = 0; d < 3; ++d)
         y[d] = (q == 0 ? b0 : b1) * a[d] + (q == 1 ? b0 : b1) * b[d] + (q == 2 ? b0 : b1) * c[d];
       dk_point(x, y, t.n, w, k, ds, dd);
@@ -163,8 +170,10 @@ __device__ zd dk_self(const GTri& t, double k) {
   return (1.0 / (4.0 * BEM_PI)) * acc;
 }
 
-// corrections: (d/dk of the refined / exact entry) - (d/dk of R_0) for every correction pair
-__global__ void k_grad_k_corr(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+// corrections: (d/dk of the refined / exact entry) - (d/dk of R_0) for every
+// correction pair; FP64, except the non-self pairs of the mixed modes (f32),
+// which run in FP32 relative to the target
+__global__ void k_grad_k_corr(int64_t nt, int nrhs, int f32, double k, const double* __restrict__ cent,
                               const double* __restrict__ qpt, const double* __restrict__ nrm,
                               const double* __restrict__ area, const double* __restrict__ hmax,
                               const int* __restrict__ ptr, const int* __restrict__ col, const double4* __restrict__ yx,
@@ -179,6 +188,35 @@ __global__ void k_grad_k_corr(int64_t nt, int nrhs, double k, const double* __re
       GTri t;
       gload(qpt, nrm, cent, area, hmax, j, t);
       zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0), s1 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
+      if (f32 && (int64_t)j != i) {
+        // mixed modes: both rules of a non-self pair in FP32, relative to the target
+        double dd3[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
+        double dist = sqrt(dd3[0] * dd3[0] + dd3[1] * dd3[1] + dd3[2] * dd3[2]);
+        int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+        if (L == 0) continue;
+        GTriT<float> tf;
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) tf.v[a][d] = (float)(t.v[a][d] - x[d]);
+        for (int d = 0; d < 3; ++d) {
+          tf.n[d] = (float)t.n[d];
+          tf.c[d] = (float)(t.c[d] - x[d]);
+        }
+        tf.area = (float)t.area;
+        tf.h = (float)t.h;
+        const float x0[3] = {0.f, 0.f, 0.f};
+        cpx<float> s0f = cmk(0.f, 0.f), d0f = s0f, s1f = s0f, d1f = s0f;
+        dk_rule(x0, tf, 0, (float)k, s0f, d0f);
+        dk_rule(x0, tf, L, (float)k, s1f, d1f);
+        const zd csf = cmk((double)(s1f.re - s0f.re), (double)(s1f.im - s0f.im));
+        const zd cdf = cmk((double)(d1f.re - d0f.re), (double)(d1f.im - d0f.im));
+        for (int r = 0; r < nrhs; ++r) {
+          double4 uy = yx[(int64_t)r * nt + j];
+          zd v = csf * cmk(uy.x, uy.y) - cdf * cmk(uy.z, uy.w);
+          double2 g = gs[(int64_t)r * nt + i];
+          part += g.x * v.re + g.y * v.im;
+        }
+        continue;
+      }
       dk_rule(x, t, 0, k, s0, d0);
       if ((int64_t)j == i) {
         s1 = dk_self(t, k);
@@ -280,7 +318,7 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
   bem_gl_host(32, glx, glw);
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
-  k_grad_k_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
+  k_grad_k_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, bem_is_fp64(h) ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                    h->corr_ptr, h->corr_col, yx, gs, acc);
   BEM_CUDA(cudaGetLastError());
   BEM_CUDA(cudaMemcpyAsync(dk, acc, sizeof(double), cudaMemcpyDeviceToHost, s));

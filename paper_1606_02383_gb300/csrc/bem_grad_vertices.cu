@@ -27,9 +27,10 @@
 //     FP64 in the FP64 modes; otherwise FP32 with block-relative coordinates
 //     and FP64 accumulation after every tile, except pairs closer than 4.5
 //     longest edges, which stay FP64.
-//   corrections (FP64): for every pair of the correction matrix, the
-//     derivative of the refined rule R_L, or of the exact self term, minus
-//     that of R_0.  The exact self term S_ii (D_ii = 0 for every vertex
+//   corrections: for every pair of the correction matrix, the derivative of
+//     the refined rule R_L, or of the exact self term, minus that of R_0; FP64
+//     in the FP64 modes and for the self terms, FP32 relative to the
+//     collocation point for the other pairs of the mixed modes.  The exact self term S_ii (D_ii = 0 for every vertex
 //     position) differentiates in closed radial form: with lambda_a the
 //     barycentric coordinates and polar coordinates (rho, u) about the centroid,
 //       dS_ii/dV_a = (dA/dV_a) S_ii / A
@@ -338,9 +339,11 @@ __global__ void __launch_bounds__(128) k_gv_source(int64_t nt, double k, const d
 }
 
 // ------------------------------------------------------------ corrections --
-struct VTri {
-  double v[3][3], n[3], c[3], area, h;
+template <typename R>
+struct VTriT {
+  R v[3][3], n[3], c[3], area, h;
 };
+typedef VTriT<double> VTri;
 
 __device__ void vload(const double* __restrict__ qpt, const double* __restrict__ nrm, const double* __restrict__ cent,
                       const double* __restrict__ area, const double* __restrict__ hmax, int64_t j, VTri& t) {
@@ -355,47 +358,49 @@ __device__ void vload(const double* __restrict__ qpt, const double* __restrict__
   t.h = hmax[j];
 }
 
-__device__ __forceinline__ void cross(const double* a, const double* b, double* o) {
+template <typename R>
+__device__ __forceinline__ void cross(const R* a, const R* b, R* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 // adds dL/dA (scalar) and dL/dn (vector) of triangle t onto its vertices
-__device__ void map_area_normal(const VTri& t, double gA, const double* gN, double* g9) {
-  double nn = gN[0] * t.n[0] + gN[1] * t.n[1] + gN[2] * t.n[2];
-  double pg[3] = {gN[0] - nn * t.n[0], gN[1] - nn * t.n[1], gN[2] - nn * t.n[2]};
+template <typename R>
+__device__ void map_area_normal(const VTriT<R>& t, R gA, const R* gN, R* g9) {
+  R nn = gN[0] * t.n[0] + gN[1] * t.n[1] + gN[2] * t.n[2];
+  R pg[3] = {gN[0] - nn * t.n[0], gN[1] - nn * t.n[1], gN[2] - nn * t.n[2]};
   for (int a = 0; a < 3; ++a) {
-    const double* b = t.v[(a + 1) % 3];
-    const double* c = t.v[(a + 2) % 3];
-    double e[3] = {b[0] - c[0], b[1] - c[1], b[2] - c[2]};
-    double ea[3], en[3];
+    const R* b = t.v[(a + 1) % 3];
+    const R* c = t.v[(a + 2) % 3];
+    R e[3] = {b[0] - c[0], b[1] - c[1], b[2] - c[2]};
+    R ea[3], en[3];
     cross(e, t.n, ea);
     cross(e, pg, en);
-    for (int d = 0; d < 3; ++d) g9[3 * a + d] += 0.5 * gA * ea[d] + en[d] / (2.0 * t.area);
+    for (int d = 0; d < 3; ++d) g9[3 * a + d] += R(0.5) * gA * ea[d] + en[d] / (R(2) * t.area);
   }
 }
 
 // sign * d/d(geometry) of Re(cy S_ij - cx D_ij) under rule R_L on triangle t:
 // the collocation point's gradient goes to tgt, the vertices' to g9.
-__device__ void rule_grad(const double* x, const VTri& t, int L, double k, zd cy, zd cx, double sign, double* tgt,
-                          double* g9) {
+template <typename R>
+__device__ void rule_grad(const R* x, const VTriT<R>& t, int L, R k, cpx<R> cy, cpx<R> cx, R sign, R* tgt, R* g9) {
   const int npieces = 1 << (2 * L);
-  const double w = t.area / (3.0 * npieces);
-  double gA = 0.0, gN[3] = {0.0, 0.0, 0.0};
-  double g9l[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tl[3] = {0, 0, 0};
+  const R w = t.area / (R(3) * npieces);
+  R gA = 0, gN[3] = {0, 0, 0};
+  R g9l[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tl[3] = {0, 0, 0};
   for (int piece = 0; piece < npieces; ++piece) {
     // barycentric coordinates (rows: the piece's corners, columns: V_0..V_2)
-    double B[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    R B[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     int code = piece;
     for (int lvl = 0; lvl < L; ++lvl) {
       const int child = code & 3;
       code >>= 2;
-      double ab[3], bc[3], ca[3];
+      R ab[3], bc[3], ca[3];
       for (int a = 0; a < 3; ++a) {
-        ab[a] = 0.5 * (B[0][a] + B[1][a]);
-        bc[a] = 0.5 * (B[1][a] + B[2][a]);
-        ca[a] = 0.5 * (B[2][a] + B[0][a]);
+        ab[a] = R(0.5) * (B[0][a] + B[1][a]);
+        bc[a] = R(0.5) * (B[1][a] + B[2][a]);
+        ca[a] = R(0.5) * (B[2][a] + B[0][a]);
       }
       for (int a = 0; a < 3; ++a) {
         if (child == 0) {
@@ -415,20 +420,20 @@ __device__ void rule_grad(const double* x, const VTri& t, int L, double k, zd cy
       }
     }
     for (int q = 0; q < 3; ++q) {
-      double beta[3], d[3];
+      R beta[3], d[3];
       for (int a = 0; a < 3; ++a) {
-        beta[a] = 0.0;
-        for (int c = 0; c < 3; ++c) beta[a] += (c == q ? 2.0 / 3.0 : 1.0 / 6.0) * B[c][a];
+        beta[a] = 0;
+        for (int c = 0; c < 3; ++c) beta[a] += (c == q ? R(2) / R(3) : R(1) / R(6)) * B[c][a];
       }
       for (int dd = 0; dd < 3; ++dd)
         d[dd] = beta[0] * t.v[0][dd] + beta[1] * t.v[1][dd] + beta[2] * t.v[2][dd] - x[dd];
-      zd G, F, H;
+      cpx<R> G, F, H;
       ghf(d[0], d[1], d[2], k, G, F, H);
-      const double dn = d[0] * t.n[0] + d[1] * t.n[1] + d[2] * t.n[2];
-      const zd a = cy * F - dn * (cx * H);
-      const zd b = cx * F;
+      const R dn = d[0] * t.n[0] + d[1] * t.n[1] + d[2] * t.n[2];
+      const cpx<R> a = cy * F - dn * (cx * H);
+      const cpx<R> b = cx * F;
       for (int dd = 0; dd < 3; ++dd) {
-        const double pg = w * (a.re * d[dd] - b.re * t.n[dd]);
+        const R pg = w * (a.re * d[dd] - b.re * t.n[dd]);
         tl[dd] -= pg;
         for (int c = 0; c < 3; ++c) g9l[3 * c + dd] += beta[c] * pg;
         gN[dd] -= w * b.re * d[dd];
@@ -526,8 +531,9 @@ __device__ void self_grad(const VTri& t, double k, zd cy, double* g9) {
 // One warp per row i of the correction matrix: for every (i, j) the refined
 // rule (or, for j == i, the exact self term) minus R_0.  Collocation-point
 // gradients are summed over the warp into gx; vertex gradients of Gamma_j go
-// to gel[j] (9 doubles: V_0, V_1, V_2).
-__global__ void k_gv_corr(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+// to gel[j] (9 doubles: V_0, V_1, V_2).  With f32 (mixed modes) the non-self
+// pairs run in FP32 with the triangle relative to the collocation point.
+__global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double* __restrict__ cent,
                           const double* __restrict__ qpt, const double* __restrict__ nrm,
                           const double* __restrict__ area, const double* __restrict__ hmax,
                           const int* __restrict__ ptr, const int* __restrict__ col, const double4* __restrict__ yx,
@@ -557,6 +563,27 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, double k, const double* __restri
         cx = cx + cg * cmk(v.z, v.w);
       }
       double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
+      if (f32 && j != i) {
+        // mixed modes: both rules of a non-self pair in FP32, the triangle
+        // relative to the collocation point (as the correction values were built)
+        VTriT<float> tf;
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) tf.v[a][d] = (float)(t.v[a][d] - x[d]);
+        for (int d = 0; d < 3; ++d) {
+          tf.n[d] = (float)t.n[d];
+          tf.c[d] = (float)(t.c[d] - x[d]);
+        }
+        tf.area = (float)t.area;
+        tf.h = (float)t.h;
+        const float x0[3] = {0.f, 0.f, 0.f};
+        const cpx<float> cyf = cmk((float)cy.re, (float)cy.im), cxf = cmk((float)cx.re, (float)cx.im);
+        float g9f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, ttf[3] = {0, 0, 0};
+        rule_grad(x0, tf, 0, (float)k, cyf, cxf, -1.0f, ttf, g9f);
+        rule_grad(x0, tf, L, (float)k, cyf, cxf, 1.0f, ttf, g9f);
+        for (int d = 0; d < 3; ++d) tg[d] += (double)ttf[d];
+        for (int m = 0; m < 9; ++m) atomicAdd(&gel[9 * j + m], (double)g9f[m]);
+        continue;
+      }
       rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
       if (j == i) {
         self_grad(t, k, cy, g9);
@@ -640,7 +667,7 @@ int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2*
   bem_gl_host(32, glx, glw);
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
-  k_gv_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
+  k_gv_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, f64 ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                h->corr_ptr, h->corr_col, yx, gs, gx, gel);
   BEM_CUDA(cudaGetLastError());
   k_gv_finish<<<nblk(nt, 128), 128, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->tri, gx, gq, ga, gn,
