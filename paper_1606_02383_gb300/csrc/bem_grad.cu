@@ -185,6 +185,7 @@ __global__ void k_grad_k_corr(int64_t nt, int nrhs, int f32, double k, const dou
     double x[3] = {cent[3 * i], cent[3 * i + 1], cent[3 * i + 2]};
     for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
       int j = col[e];
+      if ((int64_t)j == i) continue;  // the self pair: k_grad_k_self
       GTri t;
       gload(qpt, nrm, cent, area, hmax, j, t);
       zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0), s1 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
@@ -242,6 +243,32 @@ __global__ void k_grad_k_corr(int64_t nt, int nrhs, int f32, double k, const dou
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0 && part != 0.0) atomicAdd(out, part);
+}
+
+// the self pairs: (d/dk of the exact S_ii) - (d/dk of R_0 at the own centroid),
+// one element per thread (their FP64 loops run side by side)
+__global__ void k_grad_k_self(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+                              const double* __restrict__ qpt, const double* __restrict__ nrm,
+                              const double* __restrict__ area, const double* __restrict__ hmax,
+                              const double4* __restrict__ yx, const double2* __restrict__ gs, double* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < nt) {
+    GTri t;
+    gload(qpt, nrm, cent, area, hmax, (int)i, t);
+    const double x[3] = {t.c[0], t.c[1], t.c[2]};
+    zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0);
+    dk_rule(x, t, 0, k, s0, d0);
+    const zd cs = dk_self(t, k) - s0, cd = cmk(0.0, 0.0) - d0;
+    for (int r = 0; r < nrhs; ++r) {
+      const double4 uy = yx[(int64_t)r * nt + i];
+      const zd v = cs * cmk(uy.x, uy.y) - cd * cmk(uy.z, uy.w);
+      const double2 g = gs[(int64_t)r * nt + i];
+      part += g.x * v.re + g.y * v.im;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, part);
 }
 
 void bem_gl_host(int n, double* x, double* w) {
@@ -320,6 +347,9 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_ggl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
   k_grad_k_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, bem_is_fp64(h) ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                    h->corr_ptr, h->corr_col, yx, gs, acc);
+  BEM_CUDA(cudaGetLastError());
+  k_grad_k_self<<<nblk(nt, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs,
+                                               acc);
   BEM_CUDA(cudaGetLastError());
   BEM_CUDA(cudaMemcpyAsync(dk, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
   BEM_CUDA(cudaFreeAsync(yx, s));

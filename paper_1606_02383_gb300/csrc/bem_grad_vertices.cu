@@ -528,8 +528,8 @@ __device__ void self_grad(const VTri& t, double k, zd cy, double* g9) {
     }
 }
 
-// One warp per row i of the correction matrix: for every (i, j) the refined
-// rule (or, for j == i, the exact self term) minus R_0.  Collocation-point
+// One warp per row i of the correction matrix: for every non-self (i, j) the
+// refined rule minus R_0 (the self pairs are k_gv_self's).  Collocation-point
 // gradients are summed over the warp into gx; vertex gradients of Gamma_j go
 // to gel[j] (9 doubles: V_0, V_1, V_2).  With f32 (mixed modes) the non-self
 // pairs run in FP32 with the triangle relative to the collocation point.
@@ -545,15 +545,13 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
     const double x[3] = {cent[3 * i], cent[3 * i + 1], cent[3 * i + 2]};
     for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
       const int64_t j = col[e];
+      if (j == i) continue;  // the self pair: k_gv_self
       VTri t;
       vload(qpt, nrm, cent, area, hmax, j, t);
-      int L = 0;
-      if (j != i) {
-        const double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
-        const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
-        if (L == 0) continue;  // the rules agree: no correction
-      }
+      const double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
+      const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+      const int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
+      if (L == 0) continue;  // the rules agree: no correction
       zd cy = cmk(0.0, 0.0), cx = cmk(0.0, 0.0);
       for (int r = 0; r < nrhs; ++r) {
         const double2 g = gs[(int64_t)r * nt + i];
@@ -563,7 +561,7 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
         cx = cx + cg * cmk(v.z, v.w);
       }
       double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
-      if (f32 && j != i) {
+      if (f32) {
         // mixed modes: both rules of a non-self pair in FP32, the triangle
         // relative to the collocation point (as the correction values were built)
         VTriT<float> tf;
@@ -585,15 +583,8 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
         continue;
       }
       rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
-      if (j == i) {
-        self_grad(t, k, cy, g9);
-        // the collocation point is this triangle's own centroid
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) g9[3 * a + d] += tt[d] / 3.0;
-      } else {
-        rule_grad(x, t, L, k, cy, cx, 1.0, tt, g9);
-        for (int d = 0; d < 3; ++d) tg[d] += tt[d];
-      }
+      rule_grad(x, t, L, k, cy, cx, 1.0, tt, g9);
+      for (int d = 0; d < 3; ++d) tg[d] += tt[d];
       for (int m = 0; m < 9; ++m) atomicAdd(&gel[9 * j + m], g9[m]);
     }
   }
@@ -601,6 +592,36 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
     for (int o = 16; o > 0; o >>= 1) tg[d] += __shfl_xor_sync(0xffffffffu, tg[d], o);
   if (i < nt && lane == 0)
     for (int d = 0; d < 3; ++d) atomicAdd(&gx[3 * i + d], tg[d]);
+}
+
+// the self pairs, one element per thread (their FP64 loops run side by side):
+// the exact self term's vertex gradient minus R_0's, and R_0's collocation
+// gradient spread over the element's own vertices (its centroid is the
+// collocation point).  Runs after k_gv_corr, so gel[j] is updated in place.
+__global__ void k_gv_self(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+                          const double* __restrict__ qpt, const double* __restrict__ nrm,
+                          const double* __restrict__ area, const double* __restrict__ hmax,
+                          const double4* __restrict__ yx, const double2* __restrict__ gs,
+                          double* __restrict__ gel) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  VTri t;
+  vload(qpt, nrm, cent, area, hmax, i, t);
+  const double x[3] = {t.c[0], t.c[1], t.c[2]};
+  zd cy = cmk(0.0, 0.0), cx = cmk(0.0, 0.0);
+  for (int r = 0; r < nrhs; ++r) {
+    const double2 g = gs[(int64_t)r * nt + i];
+    const double4 v = yx[(int64_t)r * nt + i];
+    const zd cg = cmk(g.x, -g.y);
+    cy = cy + cg * cmk(v.x, v.y);
+    cx = cx + cg * cmk(v.z, v.w);
+  }
+  double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
+  rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
+  self_grad(t, k, cy, g9);
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) g9[3 * a + d] += tt[d] / 3.0;
+  for (int m = 0; m < 9; ++m) gel[9 * i + m] += g9[m];
 }
 
 // Per element: regular-rule point, area and normal gradients and the
@@ -669,6 +690,8 @@ int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2*
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
   k_gv_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, f64 ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                h->corr_ptr, h->corr_col, yx, gs, gx, gel);
+  BEM_CUDA(cudaGetLastError());
+  k_gv_self<<<nblk(nt, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gel);
   BEM_CUDA(cudaGetLastError());
   k_gv_finish<<<nblk(nt, 128), 128, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->tri, gx, gq, ga, gn,
                                             gel, dV);
