@@ -55,7 +55,8 @@ typedef enum {
   BEM_ERR_NOT_CONVERGED = 5,   /* GMRES hit max_iter; x holds the last iterate */
   BEM_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
   BEM_ERR_NUMERIC = 7,         /* NaN/Inf detected, or an unusable expansion */
-  BEM_ERR_UNSUPPORTED = 8      /* option combination not available */
+  BEM_ERR_UNSUPPORTED = 8,     /* option combination not available */
+  BEM_ERR_CALLBACK = 9         /* a caller's callback returned non-zero */
 } bem_status;
 
 typedef enum { BEM_C64 = 1, BEM_C128 = 2 } bem_dtype;
@@ -268,7 +269,8 @@ int bem_topological_derivative(int64_t npoints, double c1, double c2, const doub
 
 /*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
- * Eq. (GMRES) without the FEM coupling term; tolerance as in Section 3).
+ * Eq. (GMRES) without the FEM coupling term, i.e. the rigid scatterer;
+ * tolerance as in Section 3).  bem_gmres_solve_coupled adds the term.
  *   b          : right-hand sides [nrhs][N] (device).
  *   x          : in: initial guess if (flags & BEM_GMRES_USE_X0) else ignored;
  *                out: solution [nrhs][N] (device).
@@ -295,6 +297,38 @@ int bem_topological_derivative(int64_t npoints, double c1, double c2, const doub
 #define BEM_GMRES_GRAPH_ONLY 4
 int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter, int restart,
                     int flags, int* iters_out, double* relres_out, void* stream);
+
+/*
+ * bem_coupling_fn -- the caller's coupling map of Eq. (GMRES): on entry `cx`
+ * (the buffer given to bem_gmres_solve_coupled) holds a vector x, complex128
+ * [nrhs][N], written in stream order on `stream`; the callback must leave
+ * y = C x in `cy` in stream order on `stream` (enqueue its work there, or
+ * finish it and synchronise) and return 0.  For the BEM-FEM system of
+ * Section 2.3, C = T (K - rho_s omega^2 M)^{-1} N: N maps the pressure to
+ * nodal loads, the factorised FEM matrix gives the displacement, and T maps
+ * it to the normal-derivative density that the single layer S acts on.
+ * Any non-zero return ends the solve with BEM_ERR_CALLBACK.
+ */
+typedef int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream);
+
+/*
+ * bem_gmres_solve_coupled -- solve (1/2 I - D + S C) x = b (Eq. (GMRES),
+ * Section 2.3) by restarted GMRES.  Every matrix-vector product is step 2 of
+ * the paper's algorithm: the callback computes y = C x (steps 2(a) and 2(b)),
+ * then one FMM apply gives (1/2 I - D) x + S y (step 2(c)).
+ *   cb, cb_ctx : the coupling map (non-NULL) and its context.
+ *   cx, cy     : caller-owned device buffers, complex128 [nrhs][N] each,
+ *                16-byte aligned, not overlapping b, x or each other.  Their
+ *                addresses stay fixed for the whole call, so the callback may
+ *                prepare its work on them once.
+ *   other arguments as for bem_gmres_solve.
+ * The Arnoldi steps run from the host (the callback is arbitrary host code,
+ * which stream capture cannot hold): BEM_GMRES_HOST_LOOP is implied and
+ * BEM_GMRES_GRAPH_ONLY returns BEM_ERR_UNSUPPORTED.
+ */
+int bem_gmres_solve_coupled(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter,
+                            int restart, bem_coupling_fn cb, void* cb_ctx, double* cx, double* cy, int flags,
+                            int* iters_out, double* relres_out, void* stream);
 
 /*
  * Batches of independent problems (many scatterers, each with its own mesh

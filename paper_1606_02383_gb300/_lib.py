@@ -21,6 +21,7 @@ BEM_ERR_NOT_CONVERGED = 5
 BEM_ERR_TIMEOUT = 6
 BEM_ERR_NUMERIC = 7
 BEM_ERR_UNSUPPORTED = 8
+BEM_ERR_CALLBACK = 9
 
 BEM_C64 = 1
 BEM_C128 = 2
@@ -46,7 +47,11 @@ INFO_ORDER_OF_LEVEL = 100
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
-           "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative")
+           "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
+           "bem_gmres_solve_coupled")
+
+# int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
+COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
 
 
 class BemMesh(ctypes.Structure):
@@ -89,6 +94,8 @@ def load(path: str | None = None):
                              vp]
     lib.bem_gmres_solve.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.bem_gmres_solve_coupled.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, COUPLING_FN, vp, vp, vp, i,
+                                            ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_gmres_solve_batch.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
                                           ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
@@ -108,7 +115,8 @@ def load(path: str | None = None):
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
-              "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative"):
+              "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
+              "bem_gmres_solve_coupled"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -340,6 +340,29 @@ int bem_gmres_solve(bem_handle* h, int nrhs, int dtype, const void* b, void* x, 
   return bem_gmres(h, nrhs, dtype, b, x, tol, max_iter, restart, flags, iters_out, relres_out, (cudaStream_t)stream);
 }
 
+int bem_gmres_solve_coupled(bem_handle* h, int nrhs, int dtype, const void* b, void* x, double tol, int max_iter,
+                            int restart, bem_coupling_fn cb, void* cb_ctx, double* cx, double* cy, int flags,
+                            int* iters_out, double* relres_out, void* stream) {
+  g_last_error.clear();
+  BEM_TRY(check_apply_args(h, nrhs, dtype, 0));
+  if (!b || !x || !cb || !cx || !cy) return bem_fail(BEM_ERR_INVALID_ARG, "b, x, cb, cx or cy is NULL");
+  if (((uintptr_t)cx | (uintptr_t)cy) & 15) return bem_fail(BEM_ERR_INVALID_ARG, "cx and cy must be 16-byte aligned");
+  // byte extents: cx, cy complex128; b, x in the caller's dtype
+  const uintptr_t nc = (uintptr_t)nrhs * h->nt * 16, nb = (uintptr_t)nrhs * h->nt * (dtype == BEM_C128 ? 16 : 8);
+  const uintptr_t lo[4] = {(uintptr_t)cx, (uintptr_t)cy, (uintptr_t)b, (uintptr_t)x}, len[4] = {nc, nc, nb, nb};
+  for (int a = 0; a < 2; ++a)
+    for (int o = a + 1; o < 4; ++o)
+      if (lo[a] < lo[o] + len[o] && lo[o] < lo[a] + len[a])
+        return bem_fail(BEM_ERR_INVALID_ARG, "cx or cy overlaps b, x or the other");
+  if (!(tol > 0.0) || max_iter < 1 || restart < 1) return bem_fail(BEM_ERR_INVALID_ARG, "bad tol/max_iter/restart");
+  if (flags & ~(BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY))
+    return bem_fail(BEM_ERR_INVALID_ARG, "flags: BEM_GMRES_USE_X0 | BEM_GMRES_HOST_LOOP | BEM_GMRES_GRAPH_ONLY");
+  if (flags & BEM_GMRES_GRAPH_ONLY)
+    return bem_fail(BEM_ERR_UNSUPPORTED, "a coupled solve runs the host loop: its callback cannot be captured");
+  return bem_gmres_coupled(h, nrhs, dtype, b, x, tol, max_iter, restart, cb, cb_ctx, cx, cy, flags, iters_out,
+                           relres_out, (cudaStream_t)stream);
+}
+
 int bem_info(bem_handle* h, int key, int64_t* value) {
   g_last_error.clear();
   if (!h || !value) return bem_fail(BEM_ERR_INVALID_ARG, "NULL argument");

@@ -313,6 +313,9 @@ typedef int (*bem_gm_apply_fn)(void* ctx, const double* in, double* out, cudaStr
 // capture_apply (nullable) issues the same work as apply on the given stream
 // with nothing that breaks stream capture (no synchronisation, allocation or
 // events); with it the restart cycles run as CUDA graphs.
+int bem_gmres_coupled(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out, double tol, int max_iter,
+                      int restart, bem_coupling_fn cb, void* cb_ctx, double* cx, double* cy, int flags,
+                      int* iters_out, double* relres_out, cudaStream_t s);
 int bem_gmres_core(bem_gm_apply_fn apply, bem_gm_apply_fn capture_apply, void* ctx, int ncol, int64_t M, const int64_t* off, const int64_t* len,
                    int dtype, const void* b, void* x, double tol, int max_iter, int restart, int flags,
                    int* iters_out, double* relres_out, cudaStream_t s);

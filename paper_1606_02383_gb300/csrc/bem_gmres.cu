@@ -799,6 +799,42 @@ int one_op_apply_capture(void* ctx, const double* in, double* out, cudaStream_t 
 }
 }  // namespace
 
+// ------------------------------------------------------ coupled operator --
+// Eq. (GMRES): (1/2 I - D + S C) x.  The caller's callback computes y = C x
+// from the vector copied into its buffer cx (steps 2(a), 2(b)); one FMM apply
+// with both densities gives (1/2 I - D) x + S y (step 2(c)).
+namespace {
+struct CoupledOp {
+  bem_handle* h;
+  int nrhs;
+  bem_coupling_fn cb;
+  void* cb_ctx;
+  double* cx;
+  double* cy;
+};
+int coupled_apply(void* ctx, const double* in, double* out, cudaStream_t s) {
+  CoupledOp* o = (CoupledOp*)ctx;
+  const size_t bytes = (size_t)o->nrhs * o->h->nt * 2 * sizeof(double);
+  BEM_CUDA(cudaMemcpyAsync(o->cx, in, bytes, cudaMemcpyDeviceToDevice, s));
+  const int rc = o->cb(o->cb_ctx, o->nrhs, (void*)s);
+  if (rc != 0) return bem_fail(BEM_ERR_CALLBACK, "coupling callback returned " + std::to_string(rc));
+  BEM_TRY(bem_prologue(o->h, o->nrhs, BEM_C128, in, o->cy, s));
+  BEM_TRY(bem_apply_sorted(o->h, o->nrhs, s));
+  BEM_TRY(bem_epilogue(o->h, o->nrhs, BEM_C128, in, out, 1, s));
+  return BEM_OK;
+}
+}  // namespace
+
+int bem_gmres_coupled(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out, double tol, int max_iter,
+                      int restart, bem_coupling_fn cb, void* cb_ctx, double* cx, double* cy, int flags,
+                      int* iters_out, double* relres_out, cudaStream_t s) {
+  std::vector<int64_t> off(nrhs), len(nrhs, h->nt);
+  for (int r = 0; r < nrhs; ++r) off[r] = (int64_t)r * h->nt;
+  CoupledOp ctx{h, nrhs, cb, cb_ctx, cx, cy};
+  return bem_gmres_core(coupled_apply, nullptr, &ctx, nrhs, (int64_t)nrhs * h->nt, off.data(), len.data(), dtype,
+                        b_in, x_out, tol, max_iter, restart, flags | BEM_GMRES_HOST_LOOP, iters_out, relres_out, s);
+}
+
 // the nrhs right-hand sides of one operator: column r is [r N, (r + 1) N)
 int bem_gmres(bem_handle* h, int nrhs, int dtype, const void* b_in, void* x_out, double tol, int max_iter,
               int restart, int flags, int* iters_out, double* relres_out, cudaStream_t s) {

@@ -266,19 +266,46 @@ class Operator:
             k = torch.tensor(self.k, dtype=torch.float64)
         return BemApplyFn.apply(self, x, y, k, vertices)
 
-    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True, driver="graph"):
+    def solve(self, b, tol=1e-8, max_iter=200, restart=200, x0=None, raise_on_fail=True, driver="graph",
+              coupling=None):
         """GMRES for (1/2 I - D) x = b.  Returns (x, iterations, relres[nrhs]).
         driver: "graph" (each restart cycle one CUDA graph, falling back to the
         host loop if no graph can be built), "graph_only" (no fallback) or
-        "host" (the Arnoldi steps driven from the host)."""
+        "host" (the Arnoldi steps driven from the host).
+
+        coupling: optional callable coupling(cx, cy) for Eq. (GMRES),
+        (1/2 I - D + S C) x = b.  cx and cy are complex128 CUDA tensors
+        [nrhs, N] at fixed addresses; the callable must write C cx into cy in
+        place, on the current stream (e.g. the FEM map T (K - rho_s omega^2
+        M)^{-1} N of Section 2.3).  A coupled solve runs the host loop."""
         bs = self._prep(b, b.dtype)
         nrhs = bs.shape[0]
         x = torch.zeros_like(bs) if x0 is None else self._prep(x0, bs.dtype).clone()
         iters = ctypes.c_int(0)
         rel = (ctypes.c_double * nrhs)()
         flags = (_lib.BEM_GMRES_USE_X0 if x0 is not None else 0) | _gmres_driver_flags(driver)
-        rc = self._lib.bem_gmres_solve(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
-                                       int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
+        if coupling is None:
+            rc = self._lib.bem_gmres_solve(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
+                                           int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
+        else:
+            cx = torch.zeros((nrhs, self.n), dtype=torch.complex128, device="cuda")
+            cy = torch.zeros_like(cx)
+            raised = []
+
+            def _cb(_ctx, _nrhs, _stream_ptr):
+                try:
+                    coupling(cx, cy)
+                    return 0
+                except BaseException as e:  # an exception must not cross the C frames
+                    raised.append(e)
+                    return 1
+
+            fn = _lib.COUPLING_FN(_cb)
+            rc = self._lib.bem_gmres_solve_coupled(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(),
+                                                   float(tol), int(max_iter), int(restart), fn, None, cx.data_ptr(),
+                                                   cy.data_ptr(), flags, ctypes.byref(iters), rel, _stream())
+            if rc == _lib.BEM_ERR_CALLBACK and raised:
+                raise raised[0]
         if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
             _lib.check(rc)
         return x, int(iters.value), np.array(list(rel))

@@ -40,6 +40,10 @@ def test_error_paths_without_gpu():
     assert lib.bem_setup(ctypes.byref(mesh), 1.0, 8, 1e-5, None, None, ctypes.byref(h)) == _lib.BEM_ERR_INVALID_ARG
     assert lib.bem_apply(None, 1, _lib.BEM_C128, None, None, None, 0, None) == _lib.BEM_ERR_INVALID_ARG
     assert lib.bem_destroy(None) == _lib.BEM_OK
+    # the coupled solve checks its arguments before any CUDA call
+    cb = _lib.COUPLING_FN(lambda ctx, nrhs, stream: 0)
+    assert lib.bem_gmres_solve_coupled(None, 1, _lib.BEM_C128, None, None, 1e-8, 10, 10, cb, None, None, None, 0,
+                                       None, None, None) == _lib.BEM_ERR_INVALID_ARG
 
 
 def test_lazy_conjugate_views_are_resolved_before_the_library_reads_memory():
