@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
       pz[q] = pk2(qa[q].z, qb[q].z);
     }
     const f32x2 pnx = pk2(qa[0].w, qb[0].w), pny = pk2(qa[1].w, qb[1].w), pnz = pk2(qa[2].w, qb[2].w);
-    const f32x2 pk_k = pk2((float)k, (float)k), m1 = pk2(-1.f, -1.f);
+    const f32x2 pk_k = pk2((float)k, (float)k);
     f32x2 u_re = pk2(0.f, 0.f), u_im = u_re, v_re = u_re, v_im = u_re;
     for (int slot = 0; slot < 27; ++slot) {
       int sb = near27[27 * b + slot];
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
           __sincosf(kra, &sa, &ca);  // |kr| stays small in the near field
           __sincosf(krb, &sb_, &cb);
           const f32x2 gre = mul2(ri, pk2(ca, cb)), gim = mul2(ri, pk2(sa, sb_));
-          const f32x2 ngim = mul2(gim, m1);
+          const f32x2 ngim = neg2(gim);
           const f32x2 f = mul2(fma2(dx, pnx, fma2(dy, pny, mul2(dz, pnz))), mul2(ri, ri));
           // (dre, dim) = f (ikr - 1) (gre + i gim)
           const f32x2 ndre = mul2(f, fma2(kr, gim, gre));      // -dre

@@ -110,12 +110,12 @@ __device__ __forceinline__ void p2p_eval(double dx, double dy, double dz, double
 // The point kernel of p2p_eval for two targets at once (packed pairs), split
 // into the part every right-hand side shares (g = exp(ikr)/r, f and kr f) and
 // the per-density update.  nt = (-t_a, -t_b) per axis; n as broadcast pairs;
-// k2 = (k, k), m1 = (-1, -1).
+// k2 = (k, k).
 struct P2PPoint {
   f32x2 gre, gim, ngim, f, fk, nfk;
 };
 __device__ __forceinline__ P2PPoint p2p_point_pair(float qx, float qy, float qz, f32x2 ntx, f32x2 nty, f32x2 ntz,
-                                                   f32x2 nx, f32x2 ny, f32x2 nz, f32x2 k2, f32x2 m1) {
+                                                   f32x2 nx, f32x2 ny, f32x2 nz, f32x2 k2) {
   P2PPoint g;
   f32x2 dx = add2(pk2(qx, qx), ntx), dy = add2(pk2(qy, qy), nty), dz = add2(pk2(qz, qz), ntz);
   f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
@@ -129,10 +129,10 @@ __device__ __forceinline__ P2PPoint p2p_point_pair(float qx, float qy, float qz,
   __sincosf(krb, &sb, &cb);
   g.f = mul2(fma2(dx, nx, fma2(dy, ny, mul2(dz, nz))), mul2(ri, ri));
   g.fk = mul2(g.f, kr);
-  g.nfk = mul2(g.fk, m1);
+  g.nfk = neg2(g.fk);
   g.gre = mul2(ri, pk2(ca, cb));
   g.gim = mul2(ri, pk2(sa, sb));
-  g.ngim = mul2(g.gim, m1);
+  g.ngim = neg2(g.gim);
   return g;
 }
 // a += g [sigma + u - i kr u], u = f tau, for the density d = (sigma, tau)
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
   f32x2 are[NR], aim[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) are[j] = aim[j] = pk2(0.f, 0.f);
-  const f32x2 pk_k = pk2(k, k), pk_m1 = pk2(-1.f, -1.f);
+  const f32x2 pk_k = pk2(k, k);
   for (int slot = 0; slot < 27; ++slot) {
     int sb = near27[27 * b + slot];
     if (sb < 0) continue;
@@ -199,13 +199,13 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
 #pragma unroll
       for (int j = 0; j < NR; ++j) d[j] = dr[(int64_t)j * nt + e];
       f32x2 nx = pk2(q0.w, q0.w), ny = pk2(q1.w, q1.w), nz = pk2(q2.w, q2.w);
-      P2PPoint g = p2p_point_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+      P2PPoint g = p2p_point_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, pk_k);
 #pragma unroll
       for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
-      g = p2p_point_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+      g = p2p_point_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, pk_k);
 #pragma unroll
       for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
-      g = p2p_point_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, pk_k, pk_m1);
+      g = p2p_point_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, pk_k);
 #pragma unroll
       for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
     }

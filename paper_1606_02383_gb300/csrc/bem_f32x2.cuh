@@ -22,6 +22,12 @@ __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+// -a: both sign bits flipped by an integer xor (ALU pipe, not the FMA pipe)
+__device__ __forceinline__ f32x2 neg2(f32x2 a) {
+  f32x2 r;
+  asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(r) : "l"(a));
+  return r;
+}
 __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
   f32x2 r;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
