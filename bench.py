@@ -409,10 +409,10 @@ def run_ours(args, world, rank, local):
         work = info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL  # per launch (one launch per apply)
         achieved = work / (per_launch_ms * 1e-3) / 1e12
         # DRAM bytes per launch from an ncu capture of this kernel on the 81,920-triangle
-        # sphere at ka = 10 (dram__bytes_read + write = 6.778624 MB for 263,562,360
+        # sphere at ka = 10 (dram__bytes_read + write = 6.779648 MB for 263,562,360
         # evaluations), scaled by the evaluations of this launch: the traffic is the
         # sources, targets and densities read once, which grow with N as the work does
-        traffic = 6.778624e6 * (info["p2p_pairs"] * 3) / 263562360.0
+        traffic = 6.779648e6 * (info["p2p_pairs"] * 3) / 263562360.0
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
                 "traffic_source": "ncu dram bytes of the same kernel at N = 81,920 (ka = 10), scaled by evaluations",
