@@ -523,6 +523,62 @@ def _resonance_safe_k(k0, radii, width=0.2, nmax=40):
     return float(bk)
 
 
+def isosurface_timings(warm):
+    """The level-set boundary by marching tetrahedra on the device, for the
+    workload's phi on 64^3 and 256^3 grids over [-2,2]^3 at the workload's level.
+    One bem_isosurface call (count, scan, emit; it synchronises) is timed with
+    the output buffers already sized; algorithmic bytes = phi read once +
+    vertices and triangles written."""
+    import ctypes
+    import torch
+    import oracle
+    from paper_1606_02383_gb300 import _lib, inputs
+    from paper_1606_02383_gb300.operator import isosurface
+    lib = _lib.load()
+    hbm = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+    t = inputs.level_set_level()
+    c, w = inputs.level_set_gaussians(0, 20)
+    out = {}
+    for n in (64, 256):
+        x = torch.linspace(-2.0, 2.0, n, dtype=torch.float64, device="cuda")
+        X, Y, Z = torch.meshgrid(x, x, x, indexing="ij")
+        phi = torch.zeros_like(X)
+        for i in range(len(w)):
+            phi += torch.exp(-((X - c[i, 0]) ** 2 + (Y - c[i, 1]) ** 2 + (Z - c[i, 2]) ** 2) / (2.0 * w[i] ** 2))
+        del X, Y, Z
+        h = 4.0 / (n - 1)
+        V, T = isosurface(phi, (-2.0, -2.0, -2.0), h, t)
+        nv, nt = V.shape[0], T.shape[0]
+        lo = (ctypes.c_double * 3)(-2.0, -2.0, -2.0)
+        counts = (ctypes.c_int64 * 2)()
+        s = torch.cuda.current_stream().cuda_stream
+
+        def call():
+            _lib.check(lib.bem_isosurface(n, n, n, phi.data_ptr(), lo, h, t, V.data_ptr(), nv, T.data_ptr(), nt,
+                                          counts, s))
+
+        for _ in range(max(warm, 3)):
+            call()
+        ts = []
+        for _ in range(10):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            call()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        sec = statistics.median(ts)
+        nbytes = 8 * n ** 3 + 24 * nv + 12 * nt
+        row = {"grid": n, "vertices": nv, "triangles": nt, "ms": sec * 1e3, "algorithmic_bytes": nbytes,
+               "achieved_gbs": nbytes / sec / 1e9, "hbm_frac": nbytes / sec / 1e9 / hbm}
+        if n == 64:  # the oracle builds the same mesh in the same order
+            Vr, Tr = oracle.isosurface(phi.cpu().numpy(), (-2.0, -2.0, -2.0), h, t)
+            row["indices_equal_oracle"] = bool(np.array_equal(T.cpu().numpy(), Tr))
+            row["max_abs_vertex_diff_vs_oracle"] = float(np.abs(V.cpu().numpy() - Vr).max())
+        out["grid%d" % n] = row
+        del phi, V, T
+    return out
+
+
 def run_other(args):
     """The configurations besides the headline, one JSON line each."""
     import torch
@@ -741,7 +797,8 @@ def run_other(args):
                                                                       xt.detach(), yt.detach()) - fd) / abs(fd),
                      "dk_rel_err": abs(float(kt.grad) - fd) / abs(fd),
                      "dx_rel_err_vs_oracle": _rel(xt.grad.cpu().numpy(), gx_ref),
-                     "dy_rel_err_vs_oracle": _rel(yt.grad.cpu().numpy(), gy_ref)})
+                     "dy_rel_err_vs_oracle": _rel(yt.grad.cpu().numpy(), gy_ref),
+                     "isosurface": isosurface_timings(warm)})
         del rows, loss
     print(json.dumps(line), flush=True)
 

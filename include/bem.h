@@ -268,6 +268,35 @@ int bem_topological_derivative(int64_t npoints, double c1, double c2, const doub
                                double* T, void* stream);
 
 /*
+ * bem_isosurface -- the boundary {phi = t} of the level-set region {phi > t}
+ * as a closed triangle mesh (Section 2.4: the elastic body is where phi > 0,
+ * the fluid where phi <= 0, and the boundary is phi = 0), by marching
+ * tetrahedra: every grid cube splits into the 6 tetrahedra from its corner
+ * (0,0,0) to (1,1,1) along the 6 axis orders; a tetrahedron with 1 or 3
+ * corners inside gives one triangle, with 2 inside two.  A cut point sits on
+ * its grid edge (a, b), a the lower end, at a + s (b - a) with
+ * s = (t - phi_a) / (phi_b - phi_a) clamped to [0.02, 0.98], and is shared
+ * by every tetrahedron around the edge, so the mesh is closed wherever the
+ * region stays inside the grid.  Triangles face out of the region {phi > t}.
+ *   n0, n1, n2 : grid points per axis (>= 2 each; 7 n0 n1 n2 < 2^31).
+ *   phi        : FP64 [n0][n1][n2] (device); phi[i][j][k] is the value at
+ *                lo + (i, j, k) h.
+ *   lo         : host double[3]; h > 0; t: the level.
+ *   vertices   : device FP64 [max_vertices][3], or NULL to count only.
+ *   triangles  : device int32 [max_triangles][3] (a bem_mesh's layout), or
+ *                NULL to count only.
+ *   counts     : host int64[2]: receives the vertex and triangle counts.
+ * Order: vertices by (grid point, edge direction), triangles by (cube,
+ * tetrahedron, piece) -- the same for every run.  Errors: BEM_ERR_INVALID_ARG
+ * when the output does not fit (counts are filled, nothing is written);
+ * BEM_ERR_NUMERIC when phi holds a NaN or an infinity.  Synchronises
+ * `stream`.  Keeps a grow-only device scratch of about 17 n0 n1 n2 bytes for
+ * later calls; calls from several threads run one at a time.
+ */
+int bem_isosurface(int n0, int n1, int n2, const double* phi, const double* lo, double h, double t, double* vertices,
+                   int64_t max_vertices, int* triangles, int64_t max_triangles, int64_t* counts, void* stream);
+
+/*
  * bem_gmres_solve -- solve (1/2 I - D) x = b by restarted GMRES (Section 2.3,
  * Eq. (GMRES) without the FEM coupling term, i.e. the rigid scatterer;
  * tolerance as in Section 3).  bem_gmres_solve_coupled adds the term.

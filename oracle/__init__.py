@@ -18,3 +18,4 @@ from .oracle import (  # noqa: F401
     lu_solve,
     num_threads,
 )
+from .isosurface import isosurface  # noqa: F401,E402

@@ -48,7 +48,7 @@ EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gm
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-           "bem_gmres_solve_coupled")
+           "bem_gmres_solve_coupled", "bem_isosurface")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -96,6 +96,8 @@ def load(path: str | None = None):
                                     ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_gmres_solve_coupled.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, COUPLING_FN, vp, vp, vp, i,
                                             ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
+    lib.bem_isosurface.argtypes = [i, i, i, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double, vp,
+                                   i64, vp, i64, ctypes.POINTER(i64), vp]
     lib.bem_gmres_solve_batch.argtypes = [vp, i, i, vp, vp, ctypes.c_double, i, i, i, ctypes.POINTER(i),
                                           ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
@@ -116,7 +118,7 @@ def load(path: str | None = None):
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
               "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-              "bem_gmres_solve_coupled"):
+              "bem_gmres_solve_coupled", "bem_isosurface"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -235,21 +235,30 @@ def _marching_tets(phi, lo, h, t):
     return V, F
 
 
-def level_set_mesh(seed: int = 0, n_gauss: int = 20, grid: int = 64, target: int = 30000):
-    """The differentiation workload's surface: the level set of
-    phi(x) = sum_i exp(-|x - c_i|^2 / (2 w_i^2)) (c_i uniform in [-1,1]^3,
-    w_i uniform in [0.2, 0.5]) on a grid^3 lattice over [-2,2]^3, at the
-    iso-level (found by bisection) that gives about `target` triangles."""
+def level_set_gaussians(seed: int = 0, n_gauss: int = 20):
+    """Centres c_i (uniform in [-1,1]^3) and widths w_i (uniform in [0.2, 0.5])
+    of the level-set function phi(x) = sum_i exp(-|x - c_i|^2 / (2 w_i^2))."""
     rng = np.random.Generator(np.random.PCG64([int(seed), 4]))
     c = rng.uniform(-1.0, 1.0, size=(n_gauss, 3))
     w = rng.uniform(0.2, 0.5, size=n_gauss)
+    return c, w
+
+
+def level_set_function(seed: int = 0, n_gauss: int = 20, grid: int = 64):
+    """(phi [grid]^3, lo, h): the level-set function on a grid^3 lattice over [-2,2]^3."""
+    c, w = level_set_gaussians(seed, n_gauss)
     x = np.linspace(-2.0, 2.0, grid)
     X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
     P = np.stack([X, Y, Z], -1)
     phi = np.zeros(X.shape)
     for i in range(n_gauss):
         phi += np.exp(-np.sum((P - c[i]) ** 2, -1) / (2.0 * w[i] ** 2))
-    h = x[1] - x[0]
+    return phi, np.array([-2.0, -2.0, -2.0]), x[1] - x[0]
+
+
+def level_set_level(seed: int = 0, n_gauss: int = 20, grid: int = 64, target: int = 30000):
+    """The iso-level (found by bisection) whose surface has about `target` triangles."""
+    phi, _, _ = level_set_function(seed, n_gauss, grid)
 
     def count(t):  # triangles of the iso-surface at level t, without building it
         n0 = grid
@@ -270,7 +279,17 @@ def level_set_mesh(seed: int = 0, n_gauss: int = 20, grid: int = 64, target: int
             lo_t = mid
         else:
             hi_t = mid
-    V, F = _marching_tets(phi, np.array([-2.0, -2.0, -2.0]), h, 0.5 * (lo_t + hi_t))
+    return 0.5 * (lo_t + hi_t)
+
+
+def level_set_mesh(seed: int = 0, n_gauss: int = 20, grid: int = 64, target: int = 30000):
+    """The differentiation workload's surface: the level set of
+    phi(x) = sum_i exp(-|x - c_i|^2 / (2 w_i^2)) (c_i uniform in [-1,1]^3,
+    w_i uniform in [0.2, 0.5]) on a grid^3 lattice over [-2,2]^3, at the
+    iso-level (found by bisection) that gives about `target` triangles."""
+    phi, lo, h = level_set_function(seed, n_gauss, grid)
+    t = level_set_level(seed, n_gauss, grid, target)
+    V, F = _marching_tets(phi, lo, h, t)
     return np.ascontiguousarray(V), np.ascontiguousarray(F.astype(np.int32))
 
 

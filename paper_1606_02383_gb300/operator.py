@@ -311,6 +311,29 @@ class Operator:
         return x, int(iters.value), np.array(list(rel))
 
 
+def isosurface(phi, lo, h, t=0.0):
+    """The boundary {phi = t} of the level-set region {phi > t} (Section 2.4)
+    as a closed triangle mesh, by marching tetrahedra on the CUDA device.
+
+    phi: FP64 tensor [n0, n1, n2] (moved to the GPU), the value at
+    lo + (i, j, k) h.  Returns (vertices [nv, 3] FP64, triangles [nt, 3] int32),
+    CUDA tensors; triangles face out of {phi > t}, i.e. into the fluid."""
+    lib = _lib.load()
+    ph = phi.to(device="cuda", dtype=torch.float64).contiguous()
+    if ph.dim() != 3:
+        raise ValueError("phi must be [n0, n1, n2]")
+    n0, n1, n2 = ph.shape
+    lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    counts = (ctypes.c_int64 * 2)()
+    _lib.check(lib.bem_isosurface(n0, n1, n2, ph.data_ptr(), lo3, float(h), float(t), None, 0, None, 0, counts,
+                                  _stream()))
+    V = torch.empty((max(int(counts[0]), 1), 3), dtype=torch.float64, device="cuda")
+    T = torch.empty((max(int(counts[1]), 1), 3), dtype=torch.int32, device="cuda")
+    _lib.check(lib.bem_isosurface(n0, n1, n2, ph.data_ptr(), lo3, float(h), float(t), V.data_ptr(), V.shape[0],
+                                  T.data_ptr(), T.shape[0], counts, _stream()))
+    return V[:int(counts[0])], T[:int(counts[1])]
+
+
 def _gmres_driver_flags(driver):
     flags = {"graph": 0, "graph_only": _lib.BEM_GMRES_GRAPH_ONLY, "host": _lib.BEM_GMRES_HOST_LOOP}
     if driver not in flags:
