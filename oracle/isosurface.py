@@ -19,7 +19,8 @@ its definition in plain Python over the cut edges and the mixed cubes:
   quadrilateral cut(a,c), cut(a,d), cut(b,d), cut(b,c), split along its
   first diagonal into (q0, q1, q2) and (q0, q2, q3);
 - a triangle whose normal (B - A) x (C - A) points against
-  mean(outside corners) - mean(inside corners) has its last two vertices
+  mean(outside corners) - mean(inside corners) (taken times nin (4 - nin),
+  an integer vector with the same direction) has its last two vertices
   swapped, so every triangle faces out of {phi > t}.
 
 Output order: vertices by (g, step), triangles by (cube, tetrahedron, piece),
@@ -97,7 +98,9 @@ def isosurface(phi, lo, h, t):
                 c, d = outs
                 q = [edge(a, c), edge(a, d), edge(b, d), edge(b, c)]
                 pieces = [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
-            away = [sum(cs[q][x] for q in outs) / len(outs) - sum(cs[q][x] for q in ins) / len(ins)
+            # nin (4 - nin) (mean(outside corners) - mean(inside corners)): the
+            # positive factor leaves the sign of the test alone
+            away = [float(len(ins) * sum(cs[q][x] for q in outs) - len(outs) * sum(cs[q][x] for q in ins))
                     for x in range(3)]
             for tri in pieces:
                 A, B, C = (verts[v] for v in tri)

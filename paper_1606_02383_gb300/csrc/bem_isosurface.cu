@@ -21,6 +21,7 @@
 
 #include <cub/cub.cuh>
 
+#include <cstring>
 #include <mutex>
 
 #include "bem_common.cuh"
@@ -36,7 +37,18 @@ __constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2,
 struct Grid {
   int n0, n1, n2;
   double lo0, lo1, lo2, h, t;
+  long long tkey;  // order key of t
 };
+
+// An integer key of a double's bits that orders as the doubles do (NaN
+// aside; -0 folds onto +0), so phi > t is decided on the integer pipe:
+// FP64 instructions are slow on this part and cost a whole warp's issue
+// even with one lane active.
+__host__ __device__ __forceinline__ long long order_key(long long bits) {
+  if (bits == (long long)0x8000000000000000ULL) bits = 0;
+  return bits >= 0 ? bits : bits ^ 0x7FFFFFFFFFFFFFFFLL;
+}
+__device__ __forceinline__ bool above(const Grid& G, double f) { return order_key(__double_as_longlong(f)) > G.tkey; }
 
 __device__ __forceinline__ int64_t gidx(const Grid& G, int i, int j, int k) {
   return ((int64_t)i * G.n1 + j) * G.n2 + k;
@@ -54,13 +66,13 @@ __global__ void k_iso_mask(Grid G, const double* __restrict__ phi, unsigned char
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(g % G.n2), j = (int)((g / G.n2) % G.n1), i = (int)(g / ((int64_t)G.n1 * G.n2));
     const double f = phi[g];
-    if (!isfinite(f)) atomicExch(bad, 1);
-    const bool in = f > G.t;
+    if (((__double_as_longlong(f) >> 52) & 0x7FF) == 0x7FF) atomicExch(bad, 1);  // NaN or infinity
+    const bool in = above(G, f);
     unsigned m = 0;
 #pragma unroll
     for (int d = 0; d < 7; ++d) {
       const int a = i + c_dir[d][0], b = j + c_dir[d][1], c = k + c_dir[d][2];
-      if (a < G.n0 && b < G.n1 && c < G.n2 && (phi[gidx(G, a, b, c)] > G.t) != in) m |= 1u << d;
+      if (a < G.n0 && b < G.n1 && c < G.n2 && above(G, phi[gidx(G, a, b, c)]) != in) m |= 1u << d;
     }
     mask[g] = (unsigned char)m;
     vcnt[g] = __popc(m);
@@ -74,7 +86,7 @@ __global__ void k_iso_count(Grid G, const double* __restrict__ phi, int* __restr
     const int k = (int)(c % c2), j = (int)((c / c2) % c1), i = (int)(c / ((int64_t)c1 * c2));
     unsigned in8 = 0;  // bit x | y << 1 | z << 2: the cube corner at that step is inside
     for (int b = 0; b < 8; ++b)
-      if (phi[gidx(G, i + (b & 1), j + ((b >> 1) & 1), k + (b >> 2))] > G.t) in8 |= 1u << b;
+      if (above(G, phi[gidx(G, i + (b & 1), j + ((b >> 1) & 1), k + (b >> 2))])) in8 |= 1u << b;
     int tot = 0;
     if (in8 != 0 && in8 != 255)
       for (int p = 0; p < 6; ++p) {
@@ -139,7 +151,7 @@ __global__ void k_iso_triangles(Grid G, const double* __restrict__ phi, const un
       int nin = 0;
       for (int q = 0; q < 4; ++q) {
         corner(p, q, cv[q]);
-        in[q] = phi[gidx(G, i + cv[q][0], j + cv[q][1], k + cv[q][2])] > G.t;
+        in[q] = above(G, phi[gidx(G, i + cv[q][0], j + cv[q][1], k + cv[q][2])]);
         nin += in[q];
       }
       if (nin == 0 || nin == 4) continue;
@@ -166,10 +178,13 @@ __global__ void k_iso_triangles(Grid G, const double* __restrict__ phi, const un
       }
 #undef ISO_CUT
       // face from the inside corners to the outside ones: the cut plane
-      // separates them, so the sign of this test is never close to zero
-      double away[3] = {0.0, 0.0, 0.0};
+      // separates them, so the sign of this test is never close to zero.
+      // away = nin (4 - nin) (mean of the outside corners - mean of the
+      // inside ones), in integers: the positive factor keeps the sign.
+      int awi[3] = {0, 0, 0};
       for (int q = 0; q < 4; ++q)
-        for (int a = 0; a < 3; ++a) away[a] += in[q] ? -(double)cv[q][a] / nin : (double)cv[q][a] / (4 - nin);
+        for (int a = 0; a < 3; ++a) awi[a] += in[q] ? -(4 - nin) * cv[q][a] : nin * cv[q][a];
+      const double away[3] = {(double)awi[0], (double)awi[1], (double)awi[2]};
       for (int s = 0; s < ntri; ++s) {
         const double* A = V + 3 * (int64_t)tri[s][0];
         const double* B = V + 3 * (int64_t)tri[s][1];
@@ -248,7 +263,9 @@ int bem_isosurface(int n0, int n1, int n2, const double* phi, const double* lo, 
   if (7 * npt >= INT32_MAX || 12 * ncube >= INT32_MAX)
     return bem_fail(BEM_ERR_INVALID_ARG, "grid too large for 32-bit vertex and triangle indices");
   cudaStream_t s = (cudaStream_t)stream;
-  const Grid G{n0, n1, n2, lo[0], lo[1], lo[2], h, t};
+  long long tbits;
+  std::memcpy(&tbits, &t, sizeof(tbits));
+  const Grid G{n0, n1, n2, lo[0], lo[1], lo[2], h, t, order_key(tbits)};
   size_t tb1 = 0, tb2 = 0;
   cub::DeviceScan::ExclusiveSum(nullptr, tb1, (int*)nullptr, (int*)nullptr, (int)npt, s);
   cub::DeviceScan::ExclusiveSum(nullptr, tb2, (int*)nullptr, (int*)nullptr, (int)ncube, s);
