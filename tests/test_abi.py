@@ -44,6 +44,18 @@ def test_error_paths_without_gpu():
     cb = _lib.COUPLING_FN(lambda ctx, nrhs, stream: 0)
     assert lib.bem_gmres_solve_coupled(None, 1, _lib.BEM_C128, None, None, 1e-8, 10, 10, cb, None, None, None, 0,
                                        None, None, None) == _lib.BEM_ERR_INVALID_ARG
+    # the iso-surface checks its grid and level before any CUDA call
+    lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    counts = (ctypes.c_int64 * 2)()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case below fails its argument checks first
+    assert lib.bem_isosurface(4, 4, 4, None, lo, 1.0, 0.0, None, 0, None, 0, counts, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_isosurface(1, 4, 4, fake, lo, 1.0, 0.0, None, 0, None, 0, counts, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_isosurface(4, 4, 4, fake, lo, 0.0, 0.0, None, 0, None, 0, counts, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_isosurface(4, 4, 4, fake, lo, 1.0, float("nan"), None, 0, None, 0, counts,
+                              None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_isosurface(2048, 2048, 2048, fake, lo, 1.0, 0.0, None, 0, None, 0, counts,
+                              None) == _lib.BEM_ERR_INVALID_ARG
+    assert b"32-bit" in lib.bem_last_error()
 
 
 def test_lazy_conjugate_views_are_resolved_before_the_library_reads_memory():
