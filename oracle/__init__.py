@@ -19,3 +19,4 @@ from .oracle import (  # noqa: F401
     num_threads,
 )
 from .isosurface import isosurface  # noqa: F401,E402
+from .topological import point_source_field, topological_derivative  # noqa: F401,E402
