@@ -20,3 +20,4 @@ from .oracle import (  # noqa: F401
 )
 from .isosurface import isosurface  # noqa: F401,E402
 from .topological import point_source_field, topological_derivative  # noqa: F401,E402
+from . import levelset  # noqa: F401,E402
