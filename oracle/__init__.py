@@ -21,3 +21,4 @@ from .oracle import (  # noqa: F401
 from .isosurface import isosurface  # noqa: F401,E402
 from .topological import point_source_field, topological_derivative  # noqa: F401,E402
 from . import levelset  # noqa: F401,E402
+from . import burton_miller  # noqa: F401,E402
