@@ -142,11 +142,19 @@ int bem_apply(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, 
  * on each device instead of the handle's workspaces, and the call makes no
  * cudaMalloc, cudaFree or other allocating call.  The caller still passes x, y
  * and z; the handle comes from bem_setup, which did allocate.
- *  - Limit: the scratch needed is about nrhs * (48 N + 16 E) bytes in the
- *    mixed modes (80 N + 32 E in the FP64 modes), E the number of expansion
- *    coefficients of the tree; a call that needs more than the array returns
- *    BEM_ERR_INVALID_ARG with the byte counts in bem_last_error().  At
- *    N = 327,680 (mixed) one call fits two right-hand sides.
+ *  - nrhs is limited to [1, max_nrhs] as for bem_apply.
+ *  - Limit: the scratch needed is the sum of four areas, each rounded up to
+ *    256 bytes: densities nrhs * 16 N (mixed modes) or nrhs * 32 N (FP64
+ *    modes), near and far sums 2 * nrhs * 16 N, and multipole plus local
+ *    expansions 2 * nrhs * 8 E (mixed) or 2 * nrhs * 16 E (FP64), with E the
+ *    number of expansion coefficients of the tree: about nrhs * (48 N + 16 E)
+ *    bytes in the mixed modes and nrhs * (64 N + 32 E) in the FP64 modes.  A
+ *    call that needs more than the array returns BEM_ERR_INVALID_ARG with the
+ *    byte counts in bem_last_error().  At N = 327,680 (mixed) one call fits
+ *    two right-hand sides.
+ *  - While the call runs, the handle's workspace pointers point into the
+ *    array; no other thread may use the same handle (bem_apply,
+ *    bem_apply_adjoint, bem_eval_points, ...) until the call returns.
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current) and caches it; make that
@@ -457,6 +465,35 @@ int bem_profile_read(bem_handle* h, double* ms, int64_t* launches, int nstages);
  * bem_last_error -- message of the last failing call on this thread ("" if none).
  */
 const char* bem_last_error(void);
+
+/*
+ * bem_sync -- synchronise `stream` and report the device-side problem flags
+ * that kernels of this handle raised since the last synchronising call
+ * (bem_apply, bem_apply_adjoint and bem_eval_points are stream-ordered and
+ * return before their kernels run, so this is where their device-side errors
+ * surface): BEM_ERR_TIMEOUT when a bounded device wait expired, BEM_ERR_NUMERIC
+ * for non-finite values.  The flags are cleared when read.  (Section 8(b) error
+ * contract; the paper has no counterpart.)
+ */
+int bem_sync(bem_handle* h, void* stream);
+
+/*
+ * bem_set_wait_limit -- diagnostic of the bounded-wait path (no counterpart in
+ * the paper).  Every mbarrier wait of the tensor-core translations gives up
+ * after a bounded number of SM clocks, sets a device flag, waits (bounded) for
+ * its own copies and MMAs, frees its tensor memory and returns, so no kernel of
+ * this library can wait forever.
+ *   clocks : bound of the main-loop wait for a translation-matrix stage, in SM
+ *            clocks; <= 0 restores the default 2^31 (about one second).  The
+ *            drain waits at the end of a CTA keep the default bound.
+ *   hold   : != 0 makes every translation CTA withhold its first matrix copy,
+ *            so its first wait expires with nothing in flight; 0 restores the
+ *            normal path.
+ * With hold set, the next FMM apply in the mixed or tf32 mode produces a wrong
+ * far field and bem_sync returns BEM_ERR_TIMEOUT; the handle stays usable.
+ * For tests of the timeout path only.
+ */
+int bem_set_wait_limit(bem_handle* h, long long clocks, int hold);
 
 /*
  * bem_peak_probe -- microbenchmark of a compute pipe, for roofline

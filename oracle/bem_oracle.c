@@ -373,7 +373,7 @@ int oracle_apply(const double* V, int64_t nv, const int32_t* T, int64_t nt, doub
 #pragma omp parallel
   {
     cplx* acc = (cplx*)malloc(sizeof(cplx) * (size_t)nrhs);
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
     for (int64_t r = 0; r < nrows; ++r) {
       int64_t i = rows ? rows[r] : r;
       for (int q = 0; q < nrhs; ++q) acc[q] = 0.0;
@@ -414,7 +414,7 @@ int oracle_apply_adjoint(const double* V, int64_t nv, const int32_t* T, int64_t 
   {
     cplx* ax = (cplx*)malloc(sizeof(cplx) * (size_t)nrhs);
     cplx* ay = (cplx*)malloc(sizeof(cplx) * (size_t)nrhs);
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
     for (int64_t j = 0; j < nt; ++j) {
       for (int q = 0; q < nrhs; ++q) ax[q] = ay[q] = 0.0;
       for (int64_t i = 0; i < nt; ++i) {
@@ -456,7 +456,7 @@ int oracle_eval_points(const double* V, int64_t nv, const int32_t* T, int64_t nt
 #pragma omp parallel
   {
     cplx* acc = (cplx*)malloc(sizeof(cplx) * (size_t)nrhs);
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
     for (int64_t p = 0; p < npts; ++p) {
       for (int q = 0; q < nrhs; ++q) acc[q] = 0.0;
       for (int64_t j = 0; j < nt; ++j) {
@@ -490,7 +490,7 @@ int oracle_eval_points_grad(const double* V, int64_t nv, const int32_t* T, int64
 #pragma omp parallel
   {
     cplx* acc = (cplx*)malloc(sizeof(cplx) * 3 * (size_t)nrhs);
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
     for (int64_t p = 0; p < npts; ++p) {
       for (int q = 0; q < 3 * nrhs; ++q) acc[q] = 0.0;
       for (int64_t j = 0; j < nt; ++j) {

@@ -48,7 +48,7 @@ EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gm
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-           "bem_gmres_solve_coupled", "bem_isosurface")
+           "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -113,12 +113,14 @@ def load(path: str | None = None):
     lib.bem_point_sources.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     lib.bem_point_source_field.argtypes = [i, i, vp, vp, i64, vp, ctypes.c_double, i, vp, vp]
     lib.bem_topological_derivative.argtypes = [i64, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+    lib.bem_sync.argtypes = [vp, vp]
+    lib.bem_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
               "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-              "bem_gmres_solve_coupled", "bem_isosurface"):
+              "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

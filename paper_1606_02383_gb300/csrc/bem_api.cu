@@ -88,6 +88,20 @@ extern "C" {
 
 const char* bem_last_error(void) { return g_last_error.c_str(); }
 
+int bem_sync(bem_handle* h, void* stream) {
+  bem_set_error("");
+  if (!h) return bem_fail(BEM_ERR_INVALID_ARG, "handle is NULL");
+  return bem_check_device_error(h, (cudaStream_t)stream);
+}
+
+int bem_set_wait_limit(bem_handle* h, long long clocks, int hold) {
+  bem_set_error("");
+  if (!h) return bem_fail(BEM_ERR_INVALID_ARG, "handle is NULL");
+  h->tc_wait_limit = clocks > 0 ? clocks : (1LL << 31);
+  h->tc_hold_first_copy = hold ? 1 : 0;
+  return BEM_OK;
+}
+
 int bem_destroy(bem_handle* h) {
   g_last_error.clear();
   free_handle(h);

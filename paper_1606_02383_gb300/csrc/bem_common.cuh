@@ -264,6 +264,11 @@ struct bem_handle {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
   int launches_last_apply = 0;  // kernels launched by the last bem_apply
+  // bound of the tensor-core translations' main-loop matrix-stage wait, in SM
+  // clocks, and the diagnostic that withholds every CTA's first matrix copy so
+  // that this wait expires (bem_set_wait_limit)
+  long long tc_wait_limit = 1LL << 31;
+  int tc_hold_first_copy = 0;
 };
 
 int bem_prof_begin(bem_handle* h, cudaStream_t s);                      // returns a record index or -1

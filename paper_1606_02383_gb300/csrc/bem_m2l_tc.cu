@@ -63,13 +63,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: gives up after about 2^31 SM clocks (about one second)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait: gives up after `limit` SM clocks (default 2^31, about one second)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = (1LL << 31)) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     if (mbar_try(bar, parity)) return true;
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
     const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
     const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep, int R2,
-    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice, int* err) {
+    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice, int* err,
+    long long wait_limit, int hold_first_copy) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -223,7 +224,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   float4 pA[4], pB[4];
   gather(pA, ks0);
   if (nstage > 1) gather(pB, ks0 + 1);
-  if (tid == 0) issue_t(0);
+  // hold_first_copy (diagnostic of the timeout path): stage 0's matrix copy is
+  // never issued, so the first matrix-stage wait expires with nothing in flight
+  if (tid == 0 && !hold_first_copy) issue_t(0);
   auto body = [&](float4(&cur)[4], int it) -> bool {
     const int st = it & 1;
     unsigned char* sEh = smem + st * TC_STAGE_BYTES;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     if (it + 2 < nstage) gather(cur, ks0 + it + 2);
     __syncthreads();
     if (tid == 0) {
-      if (!mbar_wait(smem_u32(&bar_t[st]), (it >> 1) & 1)) {
+      if (!mbar_wait(smem_u32(&bar_t[st]), (it >> 1) & 1, wait_limit)) {
         s_abort = 1;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -511,7 +514,8 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
     k_grouped_tc<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, TC_SMEM, s>>>(
         split ? op.d_tc_jobs_split : op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
         op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, R2, nc, 8 * sl.nbox, (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total,
-        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, split ? op.tc_kslice_split : op.tc_kslice, h->d_err);
+        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, split ? op.tc_kslice_split : op.tc_kslice, h->d_err,
+        h->tc_wait_limit, h->tc_hold_first_copy);
     BEM_CUDA(cudaGetLastError());
     *launches += 2;
   }

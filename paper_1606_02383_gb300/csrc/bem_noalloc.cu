@@ -44,7 +44,7 @@ extern "C" int bem_apply_noalloc(bem_handle* h, int nrhs, int dtype, const void*
                                  int flags, void* stream) {
   bem_set_error("");
   if (!h) return bem_fail(BEM_ERR_INVALID_ARG, "handle is NULL");
-  if (nrhs < 1) return bem_fail(BEM_ERR_INVALID_ARG, "nrhs must be >= 1");
+  if (nrhs < 1 || nrhs > h->nrhs_max) return bem_fail(BEM_ERR_INVALID_ARG, "nrhs out of [1, max_nrhs]");
   if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
   if (flags & ~BEM_APPLY_NO_HALF)
     return bem_fail(BEM_ERR_INVALID_ARG, "bem_apply_noalloc takes device buffers only (flags: BEM_APPLY_NO_HALF)");

@@ -328,6 +328,14 @@ def random_density(n: int, nrhs: int = 1, seed: int = 0, stream: int = 0, dtype=
     return np.ascontiguousarray((re + 1j * im).astype(dtype))
 
 
+def centroids(vertices, triangles):
+    """Triangle centroids [nt, 3] (the collocation points), for building
+    right-hand sides such as a plane wave sampled at the elements."""
+    V = np.asarray(vertices, dtype=np.float64)
+    T = np.asarray(triangles, dtype=np.int64)
+    return V[T].mean(axis=1)
+
+
 def plane_wave(points, k: float, direction=(0.0, 0.0, 1.0)):
     """exp(i k d.x) sampled at the given points (e.g. triangle centroids)."""
     d = np.asarray(direction, dtype=np.float64)

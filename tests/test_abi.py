@@ -70,3 +70,9 @@ def test_lazy_conjugate_views_are_resolved_before_the_library_reads_memory():
     assert raw == [1.0, -2.0, 3.0, 4.0]
     r = _raw(-torch.conj(a))
     assert torch.view_as_real(r).flatten().tolist() == [-1.0, 2.0, -3.0, -4.0]
+
+
+def test_sync_and_wait_limit_reject_null_handles():
+    lib = _lib.load()
+    assert lib.bem_sync(None, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_set_wait_limit(None, 0, 0) == _lib.BEM_ERR_INVALID_ARG

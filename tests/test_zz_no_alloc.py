@@ -50,3 +50,13 @@ def test_noalloc_rejects_oversized_calls(cuda_ok):
     rc = _noalloc(op, x, x, z)
     assert rc == _lib.BEM_ERR_INVALID_ARG
     assert b"scratch bytes" in _lib.load().bem_last_error()
+    # a right-hand side count above the handle's max_nrhs is rejected like
+    # bem_apply rejects it, even where the scratch would fit
+    V, T = inputs.icosphere(2)
+    n = T.shape[0]
+    op = Operator(V, T, 1.0, p=8, mode="mixed", leaf_level=2, max_nrhs=2)
+    x = torch.zeros((3, n), dtype=torch.complex128, device="cuda")
+    z = torch.empty_like(x)
+    rc = _noalloc(op, x, x, z)
+    assert rc == _lib.BEM_ERR_INVALID_ARG
+    assert b"max_nrhs" in _lib.load().bem_last_error()
