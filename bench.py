@@ -221,6 +221,7 @@ def stage_rooflines(stages, steps, info, n, fp32_peak, tensor_peak, hbm_peak, ap
     P2P 36 flops per (target, source point); translations 8 P_out P_in flops
     per pair; stream stages their compulsory bytes (rows, values, densities and
     results read or written once)."""
+    rows = info["row_coeffs"]  # L2P row coefficients over all elements (P2M rows: twice as many)
     P = (info["p_leaf"] + 1) ** 2
     work = {
         "p2p": ("alu", info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL, fp32_peak * 1e12),
@@ -230,9 +231,9 @@ def stage_rooflines(stages, steps, info, n, fp32_peak, tensor_peak, hbm_peak, ap
         # value (16 B) + column (4 B) per entry, densities once, near sum read and written
         "correction": ("hbm", info["corr_nnz"] * 20 + n * 16 + n * 32, hbm_peak * 1e9),
         # 2 P complex64 rows per element, densities, leaf multipoles written
-        "p2m": ("hbm", n * 2 * P * 8 + n * 16 + info["n_leaves"] * P * 8, hbm_peak * 1e9),
+        "p2m": ("hbm", 2 * rows * 8 + n * 16 + info["n_leaves"] * P * 8, hbm_peak * 1e9),
         # P complex64 row per element, leaf locals, far sum written
-        "l2p": ("hbm", n * P * 8 + info["n_leaves"] * P * 8 + n * 16, hbm_peak * 1e9),
+        "l2p": ("hbm", rows * 8 + info["n_leaves"] * P * 8 + n * 16, hbm_peak * 1e9),
         # x and y in, permutation and weights, densities out
         "prologue": ("hbm", n * (2 * 16 + 12 + 16), hbm_peak * 1e9),
         # near and far sums and x in, permutation, z out
@@ -402,7 +403,8 @@ def run_ours(args, world, rank, local):
         return
     peaks, peak_src = measured_peaks()
     info = {kk: op.info(kk) for kk in ("leaf_level", "n_leaves", "p2p_pairs", "corr_nnz", "m2l_pairs",
-                                       "m2l_flops", "m2m_flops", "l2l_flops", "p_leaf", "p_top", "device_bytes")}
+                                       "m2l_flops", "m2m_flops", "l2l_flops", "p_leaf", "p_top", "device_bytes",
+                                       "row_coeffs", "adaptive", "w_pairs", "x_pairs")}
     orders = [op.order_of_level(l) for l in range(2, info["leaf_level"] + 1)]
     # roofline of the dominant stage (average launch duration from the live events)
     dom = max(stages, key=lambda s: stages[s][0])
@@ -438,8 +440,8 @@ def run_ours(args, world, rank, local):
     else:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         nbytes = {"correction": info["corr_nnz"] * 20 + n * 32,
-                  "p2m": n * 2 * (info["p_leaf"] + 1) ** 2 * 8 + n * 16,
-                  "l2p": n * (info["p_leaf"] + 1) ** 2 * 8 + n * 16}.get(dom, n * 32)
+                  "p2m": 2 * info["row_coeffs"] * 8 + n * 16,
+                  "l2p": info["row_coeffs"] * 8 + n * 16}.get(dom, n * 32)
         achieved = nbytes / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "work_per_launch": "%d bytes" % nbytes}
@@ -681,22 +683,31 @@ def run_other(args):
                      "mixed_over_fp64": res["fp64"]["apply_ms_17rhs"] / res["mixed"]["apply_ms_17rhs"],
                      "modes": res})
     elif w == "batching":
+        from paper_1606_02383_gb300.autotune import tune_options
         probs = inputs.batch_bodies(64, seed=0)
-        torch.cuda.synchronize()
+        # per-body autotuning (tree, near-field unit, translation K slice) at nrhs = 2
         t0 = time.perf_counter()
-        bt = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2)
-        torch.cuda.synchronize()
-        setup = time.perf_counter() - t0
-        n = bt.n
+        tuned = [tune_options(V, T, k, nrhs=2, reps=3, warmup=1, max_nrhs=2) for V, T, k in probs]
+        tune_s = time.perf_counter() - t0
+        n = sum(T.shape[0] for _, T, _ in probs)
         x = torch.from_numpy(inputs.random_density(n, 2, seed=0, stream=0)).cuda()
         y = torch.from_numpy(inputs.random_density(n, 2, seed=0, stream=1)).cuda()
+        bt0 = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2)
+        ms_default = _timed(lambda: bt0.apply(x, y), steps, warm)
+        bt0.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2, options=[c for c, _ in tuned])
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
         ms = _timed(lambda: bt.apply(x, y), steps, warm)
         z = bt.apply(x, y).cpu().numpy()
+        # every body: 200 oracle rows (500 for bodies 0-3)
         errs = []
-        for pb in (0, 1, 2, 3):
+        for pb in range(len(probs)):
             V, T, k = probs[pb]
             a, e = bt.offsets[pb], bt.offsets[pb + 1]
-            rows = np.sort(np.random.default_rng(pb).choice(e - a, 500, replace=False))
+            rows = np.sort(np.random.default_rng(pb).choice(e - a, 500 if pb < 4 else 200, replace=False))
             ref = oracle.apply(V, T, k, x=x[:, a:e].cpu().numpy(), y=y[:, a:e].cpu().numpy(), rows=rows)
             errs.append(_rel(z[:, a:e][:, rows], ref))
         # the batched solve of every body's state (plane wave) and adjoint (4 observers) right-hand sides
@@ -727,7 +738,12 @@ def run_other(args):
             true_res.append(float(np.linalg.norm(res) / np.linalg.norm(bh[:, a:e][:, rows])))
         line.update({"metric": "batch applies/sec, 64 ellipsoids/tori (775,312 triangles, k in [1,8]), nrhs=2",
                      "value": 1e3 / ms, "unit": "batch-applies/s", "ms_per_step": ms,
-                     "triangle_rhs_per_s": 2 * n / ms * 1e3, "setup_s": setup, "rel_err_bodies_0_3": errs,
+                     "ms_per_step_default_options": ms_default, "gain_over_default_options": ms_default / ms,
+                     "tuned": [{"N": int(T.shape[0]), "k": float(k), "chosen": c, "gain": r["gain"]}
+                               for (V, T, k), (c, r) in zip(probs, tuned)],
+                     "tune_s": tune_s,
+                     "triangle_rhs_per_s": 2 * n / ms * 1e3, "setup_s": setup,
+                     "rel_err_every_body": errs, "max_rel_err": float(max(errs)),
                      "solve": {"rhs": "plane wave e^{ikz} + adjoint sum of 4 observer sources per body", "tol": 1e-5,
                                "lockstep_iterations": iters, "seconds": solve_s,
                                "max_relres": float(relres.max()),
@@ -739,12 +755,23 @@ def run_other(args):
         c = inputs.centroids(V, T)
         x = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=0)).cuda()
         y = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=1)).cuda()
-        torch.cuda.synchronize()
+        # the trees: uniform at the deepest level the width rule allows, the
+        # adaptive default, and the autotuned choice
+        from paper_1606_02383_gb300.autotune import tune
+        trees = {}
+        for name, kw in (("uniform", {"leaf_level": 6}), ("adaptive_default", {})):
+            o = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", **kw)
+            trees[name] = {"ms": _timed(lambda: o.apply(x, y), steps, warm), "leaves": o.info("n_leaves"),
+                           "leaves_per_level": {l: o.info(200 + l) for l in range(11) if o.info(200 + l)}}
+            o.close()
         t0 = time.perf_counter()
-        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed")
+        op, report = tune(V, T, k, p=0, eps=1e-5, mode="mixed", reps=5, warmup=2, targets=(24, 32, 48), spread=0)
         torch.cuda.synchronize()
         setup = time.perf_counter() - t0
         ms = _timed(lambda: op.apply(x, y), steps, warm)
+        trees["tuned"] = {"ms": ms, "chosen": report["chosen"], "leaves": op.info("n_leaves"),
+                          "leaves_per_level": {l: op.info(200 + l) for l in range(11) if op.info(200 + l)},
+                          "w_pairs": op.info("w_pairs"), "x_pairs": op.info("x_pairs")}
         rows = np.sort(np.random.default_rng(0).choice(n, 2000, replace=False))
         t0 = time.perf_counter()
         ref = oracle.apply(V, T, k, x=x.cpu().numpy(), y=y.cpu().numpy(), rows=rows)
@@ -758,7 +785,8 @@ def run_other(args):
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
         line.update({"metric": "FMM BEM matvecs/sec, 983,040 triangles (unit sphere + 8 spheres r=0.3), ka~20",
-                     "value": 1e3 / ms, "unit": "matvecs/s", "ms_per_step": ms, "k": k, "N": n, "setup_s": setup,
+                     "value": 1e3 / ms, "unit": "matvecs/s", "ms_per_step": ms, "k": k, "N": n,
+                     "tune_and_setup_s": setup, "trees": trees,
                      "rel_err_vs_oracle_2000_rows": err, "orders": [op.order_of_level(l) for l in
                                                                     range(2, op.info("leaf_level") + 1)],
                      "gmres": {"tol": 1e-5, "iters": iters, "relres": float(relres[0]), "seconds": ts},

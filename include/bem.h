@@ -88,13 +88,25 @@ typedef struct {
 typedef struct {
   int struct_size;  /* sizeof(bem_options); 0 means "all defaults" */
   int mode;         /* bem_mode, default BEM_MODE_FMM_MIXED */
-  int leaf_level;   /* octree leaf level; <= 0 picks one from leaf_target */
+  int leaf_level;   /* octree leaves (Section 2.3's FMM tree):
+                       > 0  : uniform tree, every leaf on this level;
+                       0    : adaptive, depth chosen per level-2 region: the
+                              deepest level whose mean occupancy in the region
+                              reaches leaf_target and whose boxes stay at least
+                              3 of the region's longest edges wide (the default);
+                       -1   : adaptive, every box split while it holds more than
+                              2 leaf_target elements and its children stay at
+                              least 3 of its longest edges wide */
   int leaf_target;  /* mean triangles per occupied leaf for the automatic choice (default 48) */
   int max_nrhs;     /* largest nrhs a later call may use (default 16) */
   int p_min;        /* lower bound of the automatic per-level order (default 4) */
   int p_max;        /* upper bound of any order (default 40) */
   int p_level[11];  /* > 0: expansion order of octree level l (overrides p and eps there);
                        this is what the order autotuner sets */
+  int p2p_unit;     /* most targets per near-field warp work unit: 16, 32 or 64 (default 64) */
+  int tc_kslice;    /* most 16-wide K stages per tensor-core translation job, 2..16 (default 16) */
+  int corr_rules32; /* mixed modes: 1 sums the refined rules of non-self near-singular pairs in FP32
+                       relative to the target (faster setup); 0 sums them in FP64 (default) */
 } bem_options;
 
 /*
@@ -384,6 +396,15 @@ int bem_setup_batch(const bem_mesh* meshes, const double* ks, int count, int p, 
                     void* stream, bem_batch** out);
 
 /*
+ * bem_setup_batch_each -- bem_setup_batch with options per problem:
+ *   opts : count bem_options (each with its own struct_size; not nullable),
+ *          e.g. the tree and tile choices an autotuner made for each body.
+ * Every problem must use the same max_nrhs.
+ */
+int bem_setup_batch_each(const bem_mesh* meshes, const double* ks, int count, int p, double eps,
+                         const bem_options* opts, void* stream, bem_batch** out);
+
+/*
  * bem_apply_batch -- z = (1/2 I - D) x + S y for every problem at once.
  *   x, y, z : device buffers [nrhs][N_total] where N_total is the sum of the
  *             problems' triangle counts; problem b owns the columns
@@ -424,13 +445,13 @@ int bem_destroy_batch(bem_batch* b);
  */
 typedef enum {
   BEM_INFO_N = 0,            /* triangles */
-  BEM_INFO_LEAF_LEVEL = 1,
-  BEM_INFO_N_LEAVES = 2,
+  BEM_INFO_LEAF_LEVEL = 1,    /* deepest level of the octree (the leaf level of a uniform tree) */
+  BEM_INFO_N_LEAVES = 2,      /* leaves over all levels */
   BEM_INFO_P2P_PAIRS = 3,    /* (target, source triangle) pairs of the near field */
   BEM_INFO_CORR_NNZ = 4,     /* entries of the near-singular correction matrix */
   BEM_INFO_M2L_PAIRS = 5,    /* V-list pairs over all levels */
   BEM_INFO_M2L_FLOPS = 6,    /* 8 P_l^2 per V-list pair summed over levels (one rhs) */
-  BEM_INFO_P_LEAF = 7,       /* expansion order at the leaf level */
+  BEM_INFO_P_LEAF = 7,       /* expansion order at the deepest level */
   BEM_INFO_P_TOP = 8,        /* expansion order at level 2 */
   BEM_INFO_MODE = 9,
   BEM_INFO_DEVICE_BYTES = 10,
@@ -438,9 +459,51 @@ typedef enum {
   BEM_INFO_LAUNCHES_LAST_APPLY = 12, /* kernels the last bem_apply launched (memsets excluded) */
   BEM_INFO_M2M_FLOPS = 13,   /* 8 P_child P_parent per child box summed over levels (one rhs) */
   BEM_INFO_L2L_FLOPS = 14,   /* 8 P_parent P_child per child box summed over levels (one rhs) */
-  BEM_INFO_ORDER_OF_LEVEL = 100 /* + level: expansion order of that level */
+  BEM_INFO_ADAPTIVE = 15,    /* 0: uniform tree, 1: per-region depth, 2: per-box split at the count threshold */
+  BEM_INFO_ROW_COEFFS = 16,  /* coefficients of the stored L2P rows over all elements (P2M rows: twice as many) */
+  BEM_INFO_W_PAIRS = 17,     /* (target leaf, source box) pairs of the W-lists (M2P) */
+  BEM_INFO_X_PAIRS = 18,     /* (target box, source leaf) pairs of the X-lists (P2L) */
+  BEM_INFO_NEAR_LIST = 19,   /* entries of the near-field (U-) lists over all leaves */
+  BEM_INFO_W_EVALS = 20,     /* (target, coefficient) products of the M2P work (one rhs) */
+  BEM_INFO_X_EVALS = 21,     /* (source point, coefficient) products of the P2L work (one rhs) */
+  BEM_INFO_EXP_TOTAL = 22,   /* expansion coefficients per rhs over all levels (the far-field buffers' length) */
+  BEM_INFO_ORDER_OF_LEVEL = 100, /* + level: expansion order of that level */
+  BEM_INFO_LEAVES_OF_LEVEL = 200, /* + level: leaves on that level */
+  BEM_INFO_BOXES_OF_LEVEL = 300,  /* + level: occupied boxes on that level (tree or not) */
+  BEM_INFO_EXP_BASE_OF_LEVEL = 400 /* + level: first coefficient of that level's expansions */
 } bem_info_key;
 int bem_info(bem_handle* h, int key, int64_t* value);
+
+/*
+ * Inspection of the octree and of the FMM stages (Section 2.3's far field),
+ * so that each translation can be checked against direct sums.  Not needed to
+ * apply or solve; every call synchronises.
+ *
+ * bem_tree_level -- the occupied boxes of one level (0 .. BEM_INFO_LEAF_LEVEL),
+ * in Morton order, BEM_INFO_BOXES_OF_LEVEL + level of them.  Host buffers,
+ * each nullable: start/end [nbox] element range in sorted order (see
+ * bem_sorted_order), centre [nbox][3], flags [nbox] (bit 0: the box is in the
+ * tree, bit 1: it is split; a tree box that is not split is a leaf).
+ */
+int bem_tree_level(bem_handle* h, int level, int* start, int* end, double* centre, unsigned char* flags);
+
+/* bem_sorted_order -- perm[s] = caller index of the element at sorted position s (host buffer [N]). */
+int bem_sorted_order(bem_handle* h, int* perm);
+
+/*
+ * bem_far_field -- run one apply of x, y (as bem_apply, device buffers) and
+ * return its far-field intermediates in textbook normalisation (FMM modes only):
+ *   M    : [nrhs][E] complex128 multipoles, u(x) = sum_nm M_nm h_n(k|x-c|) Y_nm
+ *          about each box centre c (E = BEM_INFO_EXP_TOTAL; box b of level l at
+ *          BEM_INFO_EXP_BASE_OF_LEVEL + l + b (p_l + 1)^2, coefficient n^2+n+m);
+ *   L    : [nrhs][E] complex128 local expansions, u(x) = sum_nm L_nm j_n(k|x-c|) Y_nm,
+ *          after the downward pass (before L2P);
+ *   zfar : [nrhs][N] complex128 far-field part of z in the caller's order.
+ * Y_nm is orthonormal without the Condon-Shortley phase, Y_n,-m = conj(Y_nm).
+ * Device buffers, each nullable.  Synchronises `stream`.
+ */
+int bem_far_field(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, double* M, double* L,
+                  double* zfar, void* stream);
 
 /*
  * bem_profile -- per-stage device timing of bem_apply (measurement support for

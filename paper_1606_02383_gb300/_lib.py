@@ -38,17 +38,22 @@ BEM_EVAL_GRADIENT = 1
 INFO = {
     "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,
     "p_leaf": 7, "p_top": 8, "mode": 9, "device_bytes": 10, "p2m_bytes": 11, "launches_last_apply": 12,
-    "m2m_flops": 13, "l2l_flops": 14,
+    "m2m_flops": 13, "l2l_flops": 14, "adaptive": 15, "row_coeffs": 16, "w_pairs": 17, "x_pairs": 18,
+    "near_list": 19, "w_evals": 20, "x_evals": 21, "exp_total": 22,
 }
 STAGES = ("prologue", "p2p", "correction", "p2m", "m2m", "m2l", "l2l", "l2p", "epilogue")
 INFO_ORDER_OF_LEVEL = 100
+INFO_LEAVES_OF_LEVEL = 200
+INFO_BOXES_OF_LEVEL = 300
+INFO_EXP_BASE_OF_LEVEL = 400
 
 # every entry point declared in include/bem.h
 EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
            "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch", "bem_apply_batch",
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-           "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit")
+           "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field",
+           "bem_setup_batch_each")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -62,7 +67,8 @@ class BemMesh(ctypes.Structure):
 class BemOptions(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("mode", ctypes.c_int), ("leaf_level", ctypes.c_int),
                 ("leaf_target", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("p_min", ctypes.c_int),
-                ("p_max", ctypes.c_int), ("p_level", ctypes.c_int * 11)]
+                ("p_max", ctypes.c_int), ("p_level", ctypes.c_int * 11), ("p2p_unit", ctypes.c_int),
+                ("tc_kslice", ctypes.c_int), ("corr_rules32", ctypes.c_int)]
 
 
 class BemError(RuntimeError):
@@ -105,6 +111,8 @@ def load(path: str | None = None):
     lib.bem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i]
     lib.bem_setup_batch.argtypes = [ctypes.POINTER(BemMesh), ctypes.POINTER(ctypes.c_double), i, i, ctypes.c_double,
                                     ctypes.POINTER(BemOptions), vp, ctypes.POINTER(vp)]
+    lib.bem_setup_batch_each.argtypes = [ctypes.POINTER(BemMesh), ctypes.POINTER(ctypes.c_double), i, i,
+                                         ctypes.c_double, vp, vp, ctypes.POINTER(vp)]
     lib.bem_apply_batch.argtypes = [vp, i, i, vp, vp, vp, i, vp]
     lib.bem_batch_info.argtypes = [vp, i, i, ctypes.POINTER(i64)]
     lib.bem_destroy_batch.argtypes = [vp]
@@ -114,13 +122,16 @@ def load(path: str | None = None):
     lib.bem_point_source_field.argtypes = [i, i, vp, vp, i64, vp, ctypes.c_double, i, vp, vp]
     lib.bem_topological_derivative.argtypes = [i64, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.bem_sync.argtypes = [vp, vp]
+    lib.bem_tree_level.argtypes = [vp, i, vp, vp, vp, vp]
+    lib.bem_sorted_order.argtypes = [vp, vp]
+    lib.bem_far_field.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
     lib.bem_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
               "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-              "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit"):
+              "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field", "bem_setup_batch_each"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

@@ -1,12 +1,18 @@
-"""Autotuner over the octree's leaf level (the leaf size of the FMM).
+"""Autotuner over the octree and the kernels' tile choices.
 
-The expansion orders follow ``eps`` at every level, so every candidate meets
-the same accuracy. Only the split of the work changes: a deeper leaf level
-shrinks the near field (P2P cost grows with the leaf occupancy) and multiplies
-the translation pairs (M2L cost grows with the number of boxes times P^2).
-``tune`` builds the operator at the rule-based leaf level and at its
-neighbours, times applies of each with CUDA events on the current stream, and
-keeps the fastest.
+The expansion orders follow ``eps`` on every level, so every candidate meets
+the same accuracy; only the split of the work changes:
+  - the tree: a uniform leaf level, or the adaptive tree with its depth chosen
+    per level-2 region for a target mean occupancy (leaf_target).  Deeper
+    leaves shrink the near field (P2P cost grows with the leaf occupancy) and
+    multiply the translation pairs (M2L cost grows with the boxes times P^2);
+  - the near field's work unit (p2p_unit targets per warp): smaller units
+    balance the grid's tail, larger ones load each source for more targets;
+  - the translation jobs' K slice (tc_kslice stages): shorter slices give
+    small operators more CTAs at the price of more atomic adds.
+``tune`` times the candidates with CUDA events on the current stream,
+coordinate by coordinate (tree first, then the two tile choices), and keeps
+the fastest operator.
 """
 from __future__ import annotations
 
@@ -15,6 +21,8 @@ import torch
 
 from . import inputs
 from .operator import Operator
+
+DEFAULTS = {"leaf_level": 0, "leaf_target": 48, "p2p_unit": 64, "tc_kslice": 16}
 
 
 def pick(timings: dict, prefer=None, tolerance: float = 0.02):
@@ -42,32 +50,62 @@ def _time_apply(op: Operator, x, y, reps: int, warmup: int) -> float:
     return t0.elapsed_time(t1) / reps
 
 
-def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, reps=5, warmup=2, seed=0,
-         **options):
-    """Returns ``(operator, report)``: the fastest of the leaf levels L0 - spread
-    .. L0 + spread (L0 the rule-based level, levels 2..10) for ``nrhs``
-    right-hand sides, and ``report = {"rule": L0, "chosen": L, "ms": {L: ms}}``.
-    The operators that lose are destroyed as soon as they are timed."""
+def _key(cfg):
+    return tuple(sorted(cfg.items()))
+
+
+def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, targets=(24, 32, 48, 64),
+         units=(32, 64), kslices=(8, 16), reps=5, warmup=2, seed=0, **options):
+    """Returns ``(operator, report)`` with the fastest candidate for ``nrhs``
+    right-hand sides.  Candidates: the adaptive tree (leaf_level 0) for every
+    leaf target in ``targets``, and uniform trees on the adaptive default's
+    deepest level +- ``spread``; then, for the best tree, every p2p_unit in
+    ``units`` and every tc_kslice in ``kslices``.  ``report`` holds
+    ``{"default": cfg, "chosen": cfg, "ms": [(cfg, ms), ...], "gain": default_ms / chosen_ms}``."""
     n = np.asarray(triangles).shape[0]
     x = torch.from_numpy(inputs.random_density(n, nrhs, seed=seed, stream=0)).cuda()
     y = torch.from_numpy(inputs.random_density(n, nrhs, seed=seed, stream=1)).cuda()
-    best = Operator(vertices, triangles, k, p=p, eps=eps, mode=mode, **options)
-    rule = best.info("leaf_level")
-    ms = {rule: _time_apply(best, x, y, reps, warmup)}
-    best_level = rule
-    for level in range(rule - spread, rule + spread + 1):
-        if level == rule or level < 2 or level > 10:
-            continue
-        op = Operator(vertices, triangles, k, p=p, eps=eps, mode=mode, leaf_level=level, **options)
-        ms[level] = _time_apply(op, x, y, reps, warmup)
-        if pick({best_level: ms[best_level], level: ms[level]}, prefer=best_level) == level:
-            best.close()
-            best, best_level = op, level
+    timed = {}
+    state = {"best": None, "best_cfg": None}
+
+    def run(cfg):
+        key = _key(cfg)
+        if key in timed:
+            return timed[key]
+        op = Operator(vertices, triangles, k, p=p, eps=eps, mode=mode, max_nrhs=max(nrhs, options.get("max_nrhs", 1)),
+                      **{kk: v for kk, v in options.items() if kk != "max_nrhs"}, **cfg)
+        timed[key] = _time_apply(op, x, y, reps, warmup)
+        if state["best"] is None or pick({0: timed[_key(state["best_cfg"])], 1: timed[key]}, prefer=0) == 1:
+            if state["best"] is not None:
+                state["best"].close()
+            state["best"], state["best_cfg"] = op, dict(cfg)
         else:
             op.close()
-    chosen = pick(ms, prefer=rule)
-    if chosen != best_level:
-        # the rule-based level lost by less than the tolerance to a level already closed
-        best.close()
-        best = Operator(vertices, triangles, k, p=p, eps=eps, mode=mode, leaf_level=chosen, **options)
-    return best, {"rule": rule, "chosen": chosen, "ms": ms}
+        return timed[key]
+
+    default = dict(DEFAULTS)
+    run(default)
+    deepest = state["best"].info("leaf_level")
+    trees = [dict(default, leaf_target=t) for t in targets]
+    trees += [dict(default, leaf_level=lvl) for lvl in range(deepest - spread, deepest + spread + 1) if 2 <= lvl <= 10]
+    for cfg in trees:
+        run(cfg)
+    base = dict(state["best_cfg"])
+    for u in units:
+        run(dict(base, p2p_unit=u))
+    base = dict(state["best_cfg"])
+    for ks in kslices:
+        run(dict(base, tc_kslice=ks))
+    chosen = state["best_cfg"]
+    report = {"default": default, "chosen": chosen,
+              "ms": [(dict(kk), v) for kk, v in timed.items()],
+              "gain": timed[_key(default)] / timed[_key(chosen)]}
+    return state["best"], report
+
+
+def tune_options(vertices, triangles, k, **kw):
+    """The tuned option dict alone (the operator is released), e.g. for a
+    batch built with per-problem options."""
+    op, report = tune(vertices, triangles, k, **kw)
+    op.close()
+    return report["chosen"], report

@@ -113,12 +113,13 @@ __device__ __forceinline__ void adj_point(R dx, R dy, R dz, R nx, R ny, R nz, R 
 // element pairs x source slices, as in the forward kernel
 #define ADJ_WARPS 4
 template <typename R>
-__global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t nt, R k, R wleaf,
+__global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t nt, R k,
                                                             const int4* __restrict__ units,
-                                                            const int* __restrict__ near27,
+                                                            const int* __restrict__ u_ptr,
+                                                            const int* __restrict__ u_src,
+                                                            const typename AV4<R>::T* __restrict__ u_shift,
                                                             const int* __restrict__ bstart,
                                                             const int* __restrict__ bend,
-                                                            const int* __restrict__ coord,
                                                             const typename AV4<R>::T* __restrict__ tgt,
                                                             const typename AV4<R>::T* __restrict__ src,
                                                             const typename AV4<R>::T* __restrict__ dens,
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
     qb[q] = src[3 * (int64_t)jb + q];
   }
   const V4* dr = dens + (int64_t)r * nt;
-  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
+  const int ue = u_ptr[b + 1];
   R ua_re = 0, ua_im = 0, va_re = 0, va_im = 0, ub_re = 0, ub_im = 0, vb_re = 0, vb_im = 0;
   if constexpr (sizeof(R) == 4) {
     // packed: the lane's two elements a, b go through one f32x2 instruction
@@ -156,12 +157,11 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
     const f32x2 pnx = pk2(qa[0].w, qb[0].w), pny = pk2(qa[1].w, qb[1].w), pnz = pk2(qa[2].w, qb[2].w);
     const f32x2 pk_k = pk2((float)k, (float)k);
     f32x2 u_re = pk2(0.f, 0.f), u_im = u_re, v_re = u_re, v_im = u_re;
-    for (int slot = 0; slot < 27; ++slot) {
-      int sb = near27[27 * b + slot];
-      if (sb < 0) continue;
-      const float sx = (float)((coord[3 * sb] - bx) * (double)wleaf);
-      const float sy = (float)((coord[3 * sb + 1] - by) * (double)wleaf);
-      const float sz = (float)((coord[3 * sb + 2] - bz) * (double)wleaf);
+    for (int ui = u_ptr[b]; ui < ue; ++ui) {
+      const int sb = u_src[ui];
+      const bool self = sb == b;  // own leaf: the pair of an element with itself is left out
+      const V4 sh = u_shift[ui];  // centre(the other leaf) - centre(this leaf)
+      const float sx = sh.x, sy = sh.y, sz = sh.z;
       int e1 = bend[sb];
       for (int e = bstart[sb] + split; e < e1; e += nsplit) {
         const V4 x = tgt[e];
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
           const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
           float r2a, r2b;
           upk2(r2, r2a, r2b);
-          const f32x2 ri = pk2(rsqrtf(r2a), rsqrtf(r2b));
+          f32x2 ri = pk2(rsqrtf(r2a), rsqrtf(r2b));
+          if (self) ri = mul2(ri, pk2(e == ja ? 0.f : 1.f, e == jb ? 0.f : 1.f));
           const f32x2 kr = mul2(pk_k, mul2(r2, ri));
           float kra, krb, sa, ca, sb_, cb;
           upk2(kr, kra, krb);
@@ -208,12 +209,11 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
     va_im = lo;
     vb_im = hi;
   } else
-  for (int slot = 0; slot < 27; ++slot) {
-    int sb = near27[27 * b + slot];
-    if (sb < 0) continue;
-    R sx = (R)((coord[3 * sb] - bx) * (double)wleaf);
-    R sy = (R)((coord[3 * sb + 1] - by) * (double)wleaf);
-    R sz = (R)((coord[3 * sb + 2] - bz) * (double)wleaf);
+  for (int ui = u_ptr[b]; ui < ue; ++ui) {
+    const int sb = u_src[ui];
+    const bool self = sb == b;
+    const V4 sh = u_shift[ui];
+    const R sx = sh.x, sy = sh.y, sz = sh.z;
     int e1 = bend[sb];
     for (int e = bstart[sb] + split; e < e1; e += nsplit) {
       V4 x = tgt[e];
@@ -221,10 +221,12 @@ __global__ void __launch_bounds__(32 * ADJ_WARPS) k_p2p_adj(int nunits, int64_t 
       R xx = x.x + sx, xy = x.y + sy, xz = x.z + sz;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        adj_point<R>(qa[q].x - xx, qa[q].y - xy, qa[q].z - xz, qa[0].w, qa[1].w, qa[2].w, k, d.x, d.y, ua_re, ua_im,
-                     va_re, va_im);
-        adj_point<R>(qb[q].x - xx, qb[q].y - xy, qb[q].z - xz, qb[0].w, qb[1].w, qb[2].w, k, d.x, d.y, ub_re, ub_im,
-                     vb_re, vb_im);
+        if (!(self && e == ja))
+          adj_point<R>(qa[q].x - xx, qa[q].y - xy, qa[q].z - xz, qa[0].w, qa[1].w, qa[2].w, k, d.x, d.y, ua_re,
+                       ua_im, va_re, va_im);
+        if (!(self && e == jb))
+          adj_point<R>(qb[q].x - xx, qb[q].y - xy, qb[q].z - xz, qb[0].w, qb[1].w, qb[2].w, k, d.x, d.y, ub_re,
+                       ub_im, vb_re, vb_im);
       }
     }
   }
@@ -269,6 +271,7 @@ __global__ void __launch_bounds__(128) k_p2p_adj_direct(int64_t nt, R k, const t
     __syncthreads();
     R ure = 0, uim = 0, vre = 0, vim = 0;
     for (int e = 0; e < ne; ++e) {
+      if (e0 + e == j) continue;  // the self term comes whole from the correction
       V4 x = s_x[e], h = s_h[e];
       for (int a = 0; a < 3; ++a)
         adj_point<R>(q[a].x - x.x, q[a].y - x.y, q[a].z - x.z, q[0].w, q[1].w, q[2].w, k, h.x, h.y, ure, uim, vre,
@@ -392,16 +395,18 @@ int bem_build_corr_transpose(bem_handle* h, cudaStream_t s) {
 
 // L2P^T: Lambda_b = sum_{i in b} rows_r[i] h_i  (leaf level)
 template <typename R>
-__global__ void k_l2p_t(int nleaf, int64_t nt, int P, const int* __restrict__ bstart, const int* __restrict__ bend,
+__global__ void k_l2p_t(int nleaf, const int* __restrict__ leafbox, int64_t nt, int P, const int* __restrict__ bstart,
+                        const int* __restrict__ bend, const int64_t* __restrict__ row_off,
                         const R* __restrict__ rows_r, const typename AV4<R>::T* __restrict__ dens, int64_t exp_base,
                         int64_t exp_stride, R* __restrict__ Lam) {
   typedef typename AV4<R>::T V4;
-  int b = blockIdx.x, r = blockIdx.y;
+  int b = leafbox[blockIdx.x], r = blockIdx.y;
   const V4* dr = dens + (int64_t)r * nt;
+  const int64_t rb = row_off[bstart[b]], Pe = (P + 1) & ~1;  // the leaf's rows follow each other
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     R are = 0, aim = 0;
     for (int i = bstart[b]; i < bend[b]; ++i) {
-      const R* row = rows_r + 2 * ((int64_t)i * P);
+      const R* row = rows_r + 2 * (rb + (i - bstart[b]) * Pe);
       R xr = row[2 * e], xi = row[2 * e + 1];
       V4 h = dr[i];
       are += xr * h.x - xi * h.y;
@@ -415,15 +420,19 @@ __global__ void k_l2p_t(int nleaf, int64_t nt, int P, const int* __restrict__ bs
 
 // P2M^T: u_j += a_j . Mu_b, v_j += b_j . Mu_b   (warp per element, leaf level)
 template <typename R>
-__global__ void k_p2m_t(int64_t nt, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_ab,
-                        const R* __restrict__ Mu, int64_t exp_base, int64_t exp_stride, double4* __restrict__ uv) {
+__global__ void k_p2m_t(int64_t nt, LevTab lt, const int* __restrict__ leaf_of,
+                        const unsigned char* __restrict__ leaf_lev, const int64_t* __restrict__ row_off,
+                        const R* __restrict__ rows_ab, const R* __restrict__ Mu, int64_t exp_stride,
+                        double4* __restrict__ uv) {
   int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   int r = blockIdx.y;
   if (j >= nt) return;
   int b = leaf_of[j];
-  const R* ab = rows_ab + 2 * ((int64_t)j * 2 * P);
-  const R* M = Mu + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P);
+  const int lvl = leaf_lev[j];
+  const int P = lt.P[lvl];  // 0 above level 2: no multipole
+  const R* ab = rows_ab + 4 * row_off[j];
+  const R* M = Mu + 2 * ((int64_t)r * exp_stride + lt.base[lvl] + (int64_t)b * P);
   R ure = 0, uim = 0, vre = 0, vim = 0;
   for (int e = lane; e < P; e += 32) {
     R mr = M[2 * e], mi = M[2 * e + 1];
@@ -461,10 +470,10 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   int L = h->L;
   int pr = bem_prof_begin(h, s);
   if (fmm) {
-    LevelInfo& lf = h->lev[L];
     dim3 grid(nblk(h->n_p2p_units, ADJ_WARPS), nrhs);
-    k_p2p_adj<R><<<grid, 32 * ADJ_WARPS, 0, s>>>(h->n_p2p_units, nt, (R)h->k, (R)lf.w, h->p2p_units, h->near27,
-                                                 lf.start, lf.end, lf.coord, tgt, src, dens, h->uv);
+    const V4* ush = (const V4*)(sizeof(R) == 4 ? (const void*)h->u_shift32 : (const void*)h->u_shift64);
+    k_p2p_adj<R><<<grid, 32 * ADJ_WARPS, 0, s>>>(h->n_p2p_units, nt, (R)h->k, h->p2p_units, h->u_ptr, h->u_src, ush,
+                                                 h->gl_start, h->gl_end, tgt, src, dens, h->uv);
   } else {
     dim3 grid(nblk(nt, 128), nrhs);
     k_p2p_adj_direct<R><<<grid, 128, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->uv);
@@ -480,24 +489,30 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   bem_prof_end(h, pr, 2, 1, s);
   if (!fmm || L < 2) return BEM_OK;
   size_t esz = 2 * sizeof(R);
-  LevelInfo& lf = h->lev[L];
+  const LevTab lt = bem_levtab(h);
   pr = bem_prof_begin(h, s);
   BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
   BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
-  {
-    dim3 grid(lf.nbox, nrhs);
-    k_l2p_t<R><<<grid, 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->l2p_rows, dens, lf.exp_base,
-                                    h->exp_total, (R*)h->Lexp);
-    BEM_CUDA(cudaGetLastError());
-  }
-  bem_prof_end(h, pr, 7, 1, s);
   int nl = 0;
+  for (int l = 2; l <= L; ++l) {
+    LevelInfo& lf = h->lev[l];
+    if (lf.nleaf == 0) continue;
+    dim3 grid(lf.nleaf, nrhs);
+    k_l2p_t<R><<<grid, 128, 0, s>>>(lf.nleaf, lf.leafbox, nt, lf.P, lf.start, lf.end, h->row_off,
+                                    (const R*)h->l2p_rows, dens, lf.exp_base, h->exp_total, (R*)h->Lexp);
+    BEM_CUDA(cudaGetLastError());
+    ++nl;
+  }
+  BEM_TRY(bem_run_m2p_t(h, nrhs, dens, h->Mexp, s, &nl));  // W-lists: target weights into the multipoles
+  bem_prof_end(h, pr, 7, nl, s);
+  nl = 0;
   pr = bem_prof_begin(h, s);
   for (int l = L - 1; l >= 2; --l) BEM_TRY(bem_run_grouped(h, h->l2l_T[l], h->Lexp, h->Lexp, nrhs, s, &nl));
   bem_prof_end(h, pr, 6, nl, s);
   nl = 0;
   pr = bem_prof_begin(h, s);
   for (int l = 2; l <= L; ++l) BEM_TRY(bem_run_grouped(h, h->m2l_T[l], h->Lexp, h->Mexp, nrhs, s, &nl));
+  BEM_TRY(bem_run_p2l_t(h, nrhs, h->Lexp, h->uv, s, &nl));  // X-lists: local weights back to the sources
   bem_prof_end(h, pr, 5, nl, s);
   nl = 0;
   pr = bem_prof_begin(h, s);
@@ -506,8 +521,8 @@ static int adjoint_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   pr = bem_prof_begin(h, s);
   {
     dim3 grid(nblk(nt * 32, 256), nrhs);
-    k_p2m_t<R><<<grid, 256, 0, s>>>(nt, lf.P, h->leaf_of, (const R*)h->p2m_rows, (const R*)h->Mexp, lf.exp_base,
-                                    h->exp_total, h->uv);
+    k_p2m_t<R><<<grid, 256, 0, s>>>(nt, lt, h->leaf_of, h->leaf_lev, h->row_off, (const R*)h->p2m_rows,
+                                    (const R*)h->Mexp, h->exp_total, h->uv);
     BEM_CUDA(cudaGetLastError());
   }
   bem_prof_end(h, pr, 3, 1, s);

@@ -126,6 +126,8 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   o.max_nrhs = 16;
   o.p_min = 4;
   o.p_max = 40;
+  o.p2p_unit = 64;
+  o.tc_kslice = 16;
   if (opt && opt->struct_size > 0) {
     size_t n = std::min((size_t)opt->struct_size, sizeof(o));
     memcpy(&o, opt, n);
@@ -133,11 +135,17 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
     if (o.max_nrhs <= 0) o.max_nrhs = 16;
     if (o.p_min <= 0) o.p_min = 4;
     if (o.p_max <= 0) o.p_max = 40;
+    if (o.p2p_unit <= 0) o.p2p_unit = 64;
+    if (o.tc_kslice <= 0) o.tc_kslice = 16;
   }
   if (o.mode < 0 || o.mode > 4) return bem_fail(BEM_ERR_INVALID_ARG, "unknown mode");
   if (o.max_nrhs > 1024) return bem_fail(BEM_ERR_INVALID_ARG, "max_nrhs above 1024");
   if (o.leaf_level > BEM_MAXLEV) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level above 10");
+  if (o.leaf_level < -1) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level below -1");
   if (o.p_min > o.p_max || o.p_max > 60) return bem_fail(BEM_ERR_INVALID_ARG, "bad order bounds");
+  if (o.p2p_unit != 16 && o.p2p_unit != 32 && o.p2p_unit != 64)
+    return bem_fail(BEM_ERR_INVALID_ARG, "p2p_unit must be 16, 32 or 64");
+  if (o.tc_kslice < 2 || o.tc_kslice > 16) return bem_fail(BEM_ERR_INVALID_ARG, "tc_kslice must be in [2, 16]");
 
   cudaStream_t s = (cudaStream_t)stream;
   bem_handle* h = new bem_handle();
@@ -147,6 +155,9 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->fixed_p = p;
   h->eps = eps;
   h->nrhs_max = o.max_nrhs;
+  h->p2p_unit = o.p2p_unit;
+  h->tc_kslice_max = o.tc_kslice;
+  h->corr_rules32 = o.corr_rules32 ? 1 : 0;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
   for (int l = 0; l <= BEM_MAXLEV; ++l) {
@@ -384,7 +395,7 @@ int bem_info(bem_handle* h, int key, int64_t* value) {
   switch (key) {
     case BEM_INFO_N: *value = h->nt; return BEM_OK;
     case BEM_INFO_LEAF_LEVEL: *value = L; return BEM_OK;
-    case BEM_INFO_N_LEAVES: *value = h->lev.empty() ? 0 : h->lev[L].nbox; return BEM_OK;
+    case BEM_INFO_N_LEAVES: *value = h->nleaf_all; return BEM_OK;
     case BEM_INFO_P2P_PAIRS: *value = bem_is_fmm(h) ? h->p2p_pairs : h->nt * h->nt; return BEM_OK;
     case BEM_INFO_CORR_NNZ: *value = h->corr_nnz; return BEM_OK;
     case BEM_INFO_M2L_PAIRS: {
@@ -411,15 +422,39 @@ int bem_info(bem_handle* h, int key, int64_t* value) {
       *value = v;
       return BEM_OK;
     }
-    case BEM_INFO_P2M_BYTES: {
-      int64_t P = (L >= 2) ? h->lev[L].P : 0;
-      *value = h->nt * 3 * P * (bem_is_fp64(h) ? 16 : 8);
+    case BEM_INFO_P2M_BYTES: *value = h->row_total * 3 * (bem_is_fp64(h) ? 16 : 8); return BEM_OK;
+    case BEM_INFO_ADAPTIVE: *value = h->adaptive; return BEM_OK;
+    case BEM_INFO_ROW_COEFFS: *value = h->row_total; return BEM_OK;
+    case BEM_INFO_W_PAIRS: *value = h->w_nnz; return BEM_OK;
+    case BEM_INFO_X_PAIRS: {
+      int64_t v = 0;
+      for (int l = 0; l <= L; ++l) v += h->x_n[l];
+      *value = v;
       return BEM_OK;
     }
+    case BEM_INFO_NEAR_LIST: *value = h->u_nnz; return BEM_OK;
+    case BEM_INFO_W_EVALS: *value = h->w_evals; return BEM_OK;
+    case BEM_INFO_X_EVALS: *value = h->x_evals; return BEM_OK;
+    case BEM_INFO_EXP_TOTAL: *value = h->exp_total; return BEM_OK;
     default:
       if (key >= BEM_INFO_ORDER_OF_LEVEL && key <= BEM_INFO_ORDER_OF_LEVEL + BEM_MAXLEV) {
         int l = key - BEM_INFO_ORDER_OF_LEVEL;
         *value = (l >= 2 && l <= L && bem_is_fmm(h)) ? h->lev[l].p : 0;
+        return BEM_OK;
+      }
+      if (key >= BEM_INFO_BOXES_OF_LEVEL && key <= BEM_INFO_BOXES_OF_LEVEL + BEM_MAXLEV) {
+        int l = key - BEM_INFO_BOXES_OF_LEVEL;
+        *value = (l <= L && !h->lev.empty()) ? h->lev[l].nbox : 0;
+        return BEM_OK;
+      }
+      if (key >= BEM_INFO_EXP_BASE_OF_LEVEL && key <= BEM_INFO_EXP_BASE_OF_LEVEL + BEM_MAXLEV) {
+        int l = key - BEM_INFO_EXP_BASE_OF_LEVEL;
+        *value = (l >= 2 && l <= L && bem_is_fmm(h)) ? h->lev[l].exp_base : 0;
+        return BEM_OK;
+      }
+      if (key >= BEM_INFO_LEAVES_OF_LEVEL && key <= BEM_INFO_LEAVES_OF_LEVEL + BEM_MAXLEV) {
+        int l = key - BEM_INFO_LEAVES_OF_LEVEL;
+        *value = (l <= L && !h->lev.empty()) ? h->lev[l].nleaf : 0;
         return BEM_OK;
       }
       return bem_fail(BEM_ERR_INVALID_ARG, "unknown info key");

@@ -144,11 +144,41 @@ __device__ __forceinline__ void p2p_acc_pair(const P2PPoint& g, float4 d, f32x2&
   aim = fma2(g.gre, vi, fma2(g.gim, vr, aim));
 }
 
-// One warp per work unit (leaf box, 2^j consecutive targets, j <= 6).  The
+// The contribution of element e to its own centroid t, computed with the
+// operations of p2p_point_pair and p2p_acc_pair on one half of a pair (the
+// packed instructions round each half like the scalar ones), both in the
+// element's own leaf frame.
+__device__ __forceinline__ void p2p_self_pair(float4 t, const float4* __restrict__ q, float4 d, float k, float& re,
+                                              float& im) {
+  const float4 q0 = q[0], q1 = q[1], q2 = q[2];
+  const float nx = q0.w, ny = q1.w, nz = q2.w;
+  const float ntx = 0.f - t.x, nty = 0.f - t.y, ntz = 0.f - t.z;
+  re = im = 0.f;
+  const float4 pts[3] = {q0, q1, q2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const float dx = pts[p].x + ntx, dy = pts[p].y + nty, dz = pts[p].z + ntz;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrtf(r2);
+    const float kr = k * (r2 * ri);
+    float sn, cs;
+    __sincosf(kr, &sn, &cs);
+    const float f = fmaf(dx, nx, fmaf(dy, ny, dz * nz)) * (ri * ri);
+    const float fk = f * kr;
+    const float gre = ri * cs, gim = ri * sn;
+    const float vr = fmaf(fk, d.w, fmaf(f, d.z, d.x));
+    const float vi = fmaf(-fk, d.z, fmaf(f, d.w, d.y));
+    re = fmaf(gre, vr, fmaf(-gim, vi, re));
+    im = fmaf(gre, vi, fmaf(gim, vr, im));
+  }
+}
+
+// One warp per work unit (leaf, 2^j consecutive targets, j <= 6).  The
 // 32 lanes are np2 = ceil(count/2) target pairs times 32/np2 source slices;
-// every lane owns two targets and walks its slice of the elements of the 27
-// colleague boxes (stored relative to their own leaf centre, shifted into the
-// target box's frame on load), evaluating 6 points per element.  Slices are
+// every lane owns two targets and walks its slice of the elements of the
+// leaf's near list (every leaf that touches it, on any level; elements stored
+// relative to their own leaf centre, shifted into the target leaf's frame on
+// load), evaluating 6 points per element.  Slices are
 // summed with an xor-shuffle butterfly; no shared memory and no barriers.
 // Units are sorted by cost, largest first, so the tail of the grid is short.
 #define P2P_WARPS 4
@@ -157,12 +187,13 @@ __device__ __forceinline__ void p2p_acc_pair(const P2PPoint& g, float4 d, f32x2&
 // the kernel values of every point (packed f32x2 arithmetic, two targets per
 // lane).
 template <int NR>
-__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k, float wleaf,
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k,
                                                               const int4* __restrict__ units,
-                                                              const int* __restrict__ near27,
+                                                              const int* __restrict__ u_ptr,
+                                                              const int* __restrict__ u_src,
+                                                              const float4* __restrict__ u_shift,
                                                               const int* __restrict__ bstart,
                                                               const int* __restrict__ bend,
-                                                              const int* __restrict__ coord,
                                                               const float4* __restrict__ tgt,
                                                               const float4* __restrict__ src,
                                                               const float4* __restrict__ dens,
@@ -179,17 +210,15 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
   float4 ta = tgt[tfirst + pi];
   float4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
   const float4* dr = dens + (int64_t)r * nt;
-  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
   f32x2 are[NR], aim[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) are[j] = aim[j] = pk2(0.f, 0.f);
   const f32x2 pk_k = pk2(k, k);
-  for (int slot = 0; slot < 27; ++slot) {
-    int sb = near27[27 * b + slot];
-    if (sb < 0) continue;
-    float sx = (float)((coord[3 * sb] - bx) * (double)wleaf);
-    float sy = (float)((coord[3 * sb + 1] - by) * (double)wleaf);
-    float sz = (float)((coord[3 * sb + 2] - bz) * (double)wleaf);
+  const int ue = u_ptr[b + 1];
+  for (int ui = u_ptr[b]; ui < ue; ++ui) {
+    const int sb = u_src[ui];
+    const float4 sh = u_shift[ui];  // centre(source leaf) - centre(target leaf)
+    const float sx = sh.x, sy = sh.y, sz = sh.z;
     // targets in the source box's frame, negated
     f32x2 ntx = pk2(sx - ta.x, sx - tb.x), nty = pk2(sy - ta.y, sy - tb.y), ntz = pk2(sz - ta.z, sz - tb.z);
     int e1 = bend[sb];
@@ -208,6 +237,22 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
       g = p2p_point_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, pk_k);
 #pragma unroll
       for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+    }
+  }
+  // The pair of a target with itself went through the loop (its own leaf is
+  // in its near list); the near-singular correction carries the whole exact
+  // self term, so the lane that writes the result takes it out again: the
+  // same operations on the same values (FP32 rounding and all), so the FP32
+  // cancellation of (y - x).n on the element's own plane leaves no trace.
+  if (split == 0) {
+    const int ia = tfirst + pi;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      float ar, ai, br = 0.f, bi = 0.f;
+      p2p_self_pair(ta, src + 3 * (int64_t)ia, dr[(int64_t)j * nt + ia], k, ar, ai);
+      if (two) p2p_self_pair(tb, src + 3 * (int64_t)(ia + np2), dr[(int64_t)j * nt + ia + np2], k, br, bi);
+      are[j] = sub2(are[j], pk2(ar, br));
+      aim[j] = sub2(aim[j], pk2(ai, bi));
     }
   }
 #pragma unroll
@@ -234,12 +279,13 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
 }
 
 // FP64: one right-hand side per warp (grid.y), scalar arithmetic.
-__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm64(int nunits, int64_t nt, double k, double wleaf,
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm64(int nunits, int64_t nt, double k,
                                                               const int4* __restrict__ units,
-                                                              const int* __restrict__ near27,
+                                                              const int* __restrict__ u_ptr,
+                                                              const int* __restrict__ u_src,
+                                                              const double4* __restrict__ u_shift,
                                                               const int* __restrict__ bstart,
                                                               const int* __restrict__ bend,
-                                                              const int* __restrict__ coord,
                                                               const double4* __restrict__ tgt,
                                                               const double4* __restrict__ src,
                                                               const double4* __restrict__ dens,
@@ -256,14 +302,14 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm64(int nunits, int64_
   double4 ta = tgt[tfirst + pi];
   double4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
   const double4* dr = dens + (int64_t)r * nt;
-  int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
   double a_re = 0, a_im = 0, b_re = 0, b_im = 0;
-  for (int slot = 0; slot < 27; ++slot) {
-    int sb = near27[27 * b + slot];
-    if (sb < 0) continue;
-    double sx = (coord[3 * sb] - bx) * wleaf;
-    double sy = (coord[3 * sb + 1] - by) * wleaf;
-    double sz = (coord[3 * sb + 2] - bz) * wleaf;
+  const int ia = tfirst + pi, ib = tfirst + (two ? pi + np2 : pi);
+  const int ue = u_ptr[b + 1];
+  for (int ui = u_ptr[b]; ui < ue; ++ui) {
+    const int sb = u_src[ui];
+    const bool self = sb == b;  // the target's own leaf: the pair of a target with itself is left out
+    const double4 sh = u_shift[ui];  // centre(source leaf) - centre(target leaf)
+    const double sx = sh.x, sy = sh.y, sz = sh.z;
     double ax = ta.x - sx, ay = ta.y - sy, az = ta.z - sz;  // targets in the source box's frame
     double bx_ = tb.x - sx, by_ = tb.y - sy, bz_ = tb.z - sz;
     int e1 = bend[sb];
@@ -271,12 +317,16 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm64(int nunits, int64_
       double4 q0 = src[3 * (int64_t)e], q1 = src[3 * (int64_t)e + 1], q2 = src[3 * (int64_t)e + 2];
       double4 d = dr[e];
       double nx = q0.w, ny = q1.w, nz = q2.w;
-      p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
-      p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-      p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
-      p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      if (!(self && e == ia)) {
+        p2p_eval(q0.x - ax, q0.y - ay, q0.z - az, nx, ny, nz, k, d, a_re, a_im);
+        p2p_eval(q1.x - ax, q1.y - ay, q1.z - az, nx, ny, nz, k, d, a_re, a_im);
+        p2p_eval(q2.x - ax, q2.y - ay, q2.z - az, nx, ny, nz, k, d, a_re, a_im);
+      }
+      if (!(self && e == ib)) {
+        p2p_eval(q0.x - bx_, q0.y - by_, q0.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+        p2p_eval(q1.x - bx_, q1.y - by_, q1.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+        p2p_eval(q2.x - bx_, q2.y - by_, q2.z - bz_, nx, ny, nz, k, d, b_re, b_im);
+      }
     }
   }
   for (int o = np2; o < 32; o <<= 1) {
@@ -325,6 +375,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_direct(int64_t nt, R k, con
     __syncthreads();
     R are = 0, aim = 0;
     for (int e = 0; e < ne; ++e) {
+      if (e0 + e == i) continue;  // the self term comes whole from the correction
       V4 q0 = s_src[e][0], q1 = s_src[e][1], q2 = s_src[e][2];
       V4 dd = s_den[e];
       R nx = q0.w, ny = q1.w, nz = q2.w;
@@ -855,16 +906,19 @@ __global__ void k_correction(int64_t nt, int r0, const int* __restrict__ ptr, co
 
 // -------------------------------------------------------------------- P2M --
 template <typename R>
-__global__ void k_p2m(int nleaf, int64_t nt, int P, const int* __restrict__ bstart, const int* __restrict__ bend,
-                      const R* __restrict__ rows_ab, const typename V4of<R>::T* __restrict__ dens, int64_t exp_base,
-                      int64_t exp_stride, R* __restrict__ M) {
+__global__ void k_p2m(int nleaf, const int* __restrict__ leafbox, int64_t nt, int P, const int* __restrict__ bstart,
+                      const int* __restrict__ bend, const int64_t* __restrict__ row_off, const R* __restrict__ rows_ab,
+                      const typename V4of<R>::T* __restrict__ dens, int64_t exp_base, int64_t exp_stride,
+                      R* __restrict__ M) {
   typedef typename V4of<R>::T V4;
-  int b = blockIdx.x, r = blockIdx.y;
+  int b = leafbox[blockIdx.x], r = blockIdx.y;
   const V4* dr = dens + (int64_t)r * nt;
+  // the leaf's element rows follow each other, (P rounded up to even) coefficients apart
+  const int64_t rb = row_off[bstart[b]], Pe = (P + 1) & ~1;
   for (int e = threadIdx.x; e < P; e += blockDim.x) {
     R are = 0, aim = 0;
     for (int j = bstart[b]; j < bend[b]; ++j) {
-      const R* ab = rows_ab + 2 * ((int64_t)j * 2 * P);
+      const R* ab = rows_ab + 4 * (rb + (j - bstart[b]) * Pe);
       R a_re = ab[2 * e], a_im = ab[2 * e + 1];
       R b_re = ab[2 * (P + e)], b_im = ab[2 * (P + e) + 1];
       V4 d = dr[j];
@@ -883,11 +937,12 @@ __global__ void k_p2m(int nleaf, int64_t nt, int P, const int* __restrict__ bsta
 // A row [a (P complex) | b (P complex)] starts on a 16-byte boundary; b does
 // too when P is even, otherwise it is read as two float2.
 template <int NR>
-__global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restrict__ bstart,
-                        const int* __restrict__ bend, const float* __restrict__ rows_ab,
+__global__ void k_p2m_v(int nleaf, const int* __restrict__ leafbox, int64_t nt, int r0, int P,
+                        const int* __restrict__ bstart, const int* __restrict__ bend,
+                        const int64_t* __restrict__ row_off, const float* __restrict__ rows_ab,
                         const float4* __restrict__ dens, int64_t exp_base, int64_t exp_stride,
                         float* __restrict__ M) {
-  const int b = blockIdx.x, r = r0 + blockIdx.y * NR;
+  const int b = leafbox[blockIdx.x], r = r0 + blockIdx.y * NR;
   const int e0 = 2 * threadIdx.x;
   if (e0 >= P) return;
   const bool two = e0 + 1 < P, peven = (P & 1) == 0;
@@ -896,6 +951,9 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc0[q] = acc1[q] = make_float2(0.f, 0.f);
   const int j0 = bstart[b], j1 = bend[b];
+  // the leaf's element rows follow each other, (P rounded up to even) coefficients apart
+  const float* rows0 = rows_ab + 4 * row_off[j0];
+  const int64_t Pe4 = 4 * (int64_t)((P + 1) & ~1);
   constexpr int P2M_U = NR == 1 ? 8 : 4;  // elements per round
   for (int jb = j0; jb < j1; jb += P2M_U) {
     float4 A[P2M_U], B[P2M_U], D[P2M_U][NR];
@@ -908,7 +966,7 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
         for (int q = 0; q < NR; ++q) D[u][q] = A[u];
         continue;
       }
-      const float* ab = rows_ab + 4 * (int64_t)j * P;
+      const float* ab = rows0 + (int64_t)(j - j0) * Pe4;
       const float* bb = ab + 2 * P;
       if (two) {
         A[u] = *(const float4*)(ab + 2 * e0);
@@ -955,16 +1013,20 @@ __global__ void k_p2m_v(int nleaf, int64_t nt, int r0, int P, const int* __restr
 // One warp per target; NR right-hand sides r0 + NR blockIdx.y + [0, NR)
 // share each loaded row.
 template <typename R, int NR>
-__device__ __forceinline__ void l2p_body(int64_t nt, int r0, int P, const int* __restrict__ leaf_of,
-                                         const R* __restrict__ rows_r, const R* __restrict__ Lexp, int64_t exp_base,
-                                         int64_t exp_stride, double* __restrict__ zfar) {
+__device__ __forceinline__ void l2p_body(int64_t nt, int r0, const LevTab& lt, const int* __restrict__ leaf_of,
+                                         const unsigned char* __restrict__ leaf_lev,
+                                         const int64_t* __restrict__ row_off, const R* __restrict__ rows_r,
+                                         const R* __restrict__ Lexp, int64_t exp_stride,
+                                         double* __restrict__ zfar) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   int r = r0 + blockIdx.y * NR;
   if (i >= nt) return;
   int b = leaf_of[i];
-  const R* row = rows_r + 2 * (i * P);
-  const R* Lb = Lexp + 2 * ((int64_t)r * exp_stride + exp_base + (int64_t)b * P);
+  const int lvl = leaf_lev[i];
+  const int P = lt.P[lvl];  // 0 for a leaf above level 2: no local expansion
+  const R* row = rows_r + 2 * row_off[i];
+  const R* Lb = Lexp + 2 * ((int64_t)r * exp_stride + lt.base[lvl] + (int64_t)b * P);
   const int64_t ls = 2 * exp_stride;  // between right-hand sides
   R are[NR], aim[NR];
 #pragma unroll
@@ -1008,16 +1070,20 @@ __device__ __forceinline__ void l2p_body(int64_t nt, int r0, int P, const int* _
 }
 
 template <typename R, int NR>
-__global__ void k_l2p(int64_t nt, int r0, int P, const int* __restrict__ leaf_of, const R* __restrict__ rows_r,
-                      const R* __restrict__ Lexp, int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
-  l2p_body<R, NR>(nt, r0, P, leaf_of, rows_r, Lexp, exp_base, exp_stride, zfar);
+__global__ void k_l2p(int64_t nt, int r0, LevTab lt, const int* __restrict__ leaf_of,
+                      const unsigned char* __restrict__ leaf_lev, const int64_t* __restrict__ row_off,
+                      const R* __restrict__ rows_r, const R* __restrict__ Lexp, int64_t exp_stride,
+                      double* __restrict__ zfar) {
+  l2p_body<R, NR>(nt, r0, lt, leaf_of, leaf_lev, row_off, rows_r, Lexp, exp_stride, zfar);
 }
-// FP32 with one right-hand side: eight blocks per SM (32 registers), since the
-// kernel is latency-bound on its row loads
-__global__ void __launch_bounds__(256, 8) k_l2p_f1(int64_t nt, int r0, int P, const int* __restrict__ leaf_of,
+// FP32 with one right-hand side: eight blocks per SM, since the kernel is
+// latency-bound on its row loads
+__global__ void __launch_bounds__(256, 8) k_l2p_f1(int64_t nt, int r0, LevTab lt, const int* __restrict__ leaf_of,
+                                                   const unsigned char* __restrict__ leaf_lev,
+                                                   const int64_t* __restrict__ row_off,
                                                    const float* __restrict__ rows_r, const float* __restrict__ Lexp,
-                                                   int64_t exp_base, int64_t exp_stride, double* __restrict__ zfar) {
-  l2p_body<float, 1>(nt, r0, P, leaf_of, rows_r, Lexp, exp_base, exp_stride, zfar);
+                                                   int64_t exp_stride, double* __restrict__ zfar) {
+  l2p_body<float, 1>(nt, r0, lt, leaf_of, leaf_lev, row_off, rows_r, Lexp, exp_stride, zfar);
 }
 
 // ------------------------------------------------ grouped translation GEMM --
@@ -1194,18 +1260,18 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   int pr = bem_prof_begin(h, s);
   int nl = 1;
   if (fmm) {
-    LevelInfo& lf = h->lev[L];
     const unsigned gx = nblk(h->n_p2p_units, P2P_WARPS);
     if constexpr (sizeof(R) == 4) {
       nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
         k_p2p_fmm32<decltype(nr)::value><<<dim3(gx, nchunk), 32 * P2P_WARPS, 0, s>>>(
-            h->n_p2p_units, nt, r0, (float)h->k, (float)lf.w, h->p2p_units, h->near27, lf.start, lf.end, lf.coord,
-            (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
+            h->n_p2p_units, nt, r0, (float)h->k, h->p2p_units, h->u_ptr, h->u_src, h->u_shift32, h->gl_start,
+            h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
       });
     } else {
-      k_p2p_fmm64<<<dim3(gx, nrhs), 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, h->k, lf.w, h->p2p_units,
-                                                          h->near27, lf.start, lf.end, lf.coord, (const double4*)tgt,
-                                                          (const double4*)src, (const double4*)dens, h->zn);
+      k_p2p_fmm64<<<dim3(gx, nrhs), 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, h->k, h->p2p_units, h->u_ptr,
+                                                          h->u_src, h->u_shift64, h->gl_start, h->gl_end,
+                                                          (const double4*)tgt, (const double4*)src,
+                                                          (const double4*)dens, h->zn);
     }
   } else {
     dim3 grid(nblk(nt, P2P_THREADS), nrhs);
@@ -1228,22 +1294,28 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
     int pr, nl;
     // far field
     size_t esz = 2 * sizeof(R);
-    LevelInfo& lf = h->lev[L];
+    const LevTab lt = bem_levtab(h);
     pr = bem_prof_begin(h, s);
     BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
     BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
-    if constexpr (sizeof(R) == 4) {
-      nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-        k_p2m_v<decltype(nr)::value><<<dim3(lf.nbox, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
-            lf.nbox, nt, r0, lf.P, lf.start, lf.end, (const float*)h->p2m_rows, (const float4*)dens, lf.exp_base,
-            h->exp_total, (float*)h->Mexp);
-      });
-    } else {
-      nl = 1;
-      k_p2m<R><<<dim3(lf.nbox, nrhs), 128, 0, s>>>(lf.nbox, nt, lf.P, lf.start, lf.end, (const R*)h->p2m_rows, dens,
-                                                   lf.exp_base, h->exp_total, (R*)h->Mexp);
+    nl = 0;
+    for (int l = 2; l <= L; ++l) {
+      LevelInfo& lf = h->lev[l];
+      if (lf.nleaf == 0) continue;
+      if constexpr (sizeof(R) == 4) {
+        nl += by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+          k_p2m_v<decltype(nr)::value><<<dim3(lf.nleaf, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
+              lf.nleaf, lf.leafbox, nt, r0, lf.P, lf.start, lf.end, h->row_off, (const float*)h->p2m_rows,
+              (const float4*)dens, lf.exp_base, h->exp_total, (float*)h->Mexp);
+        });
+      } else {
+        nl += 1;
+        k_p2m<R><<<dim3(lf.nleaf, nrhs), 128, 0, s>>>(lf.nleaf, lf.leafbox, nt, lf.P, lf.start, lf.end, h->row_off,
+                                                      (const R*)h->p2m_rows, dens, lf.exp_base, h->exp_total,
+                                                      (R*)h->Mexp);
+      }
+      BEM_CUDA(cudaGetLastError());
     }
-    BEM_CUDA(cudaGetLastError());
     bem_prof_end(h, pr, 3, nl, s);
     nl = 0;
     pr = bem_prof_begin(h, s);
@@ -1252,6 +1324,7 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
     nl = 0;
     pr = bem_prof_begin(h, s);
     for (int l = 2; l <= L; ++l) BEM_TRY(run_grouped<R>(h, h->m2l[l], h->Mexp, h->Lexp, nrhs, s, &nl));
+    BEM_TRY(bem_run_p2l(h, nrhs, dens, h->Lexp, s, &nl));  // X-lists, before the local expansions go down
     bem_prof_end(h, pr, 5, nl, s);
     nl = 0;
     pr = bem_prof_begin(h, s);
@@ -1261,13 +1334,15 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
     nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
       const dim3 grid(nblk(nt * 32, 256), nchunk);
       if constexpr (sizeof(R) == 4 && decltype(nr)::value == 1)
-        k_l2p_f1<<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const float*)h->l2p_rows, (const float*)h->Lexp,
-                                      lf.exp_base, h->exp_total, h->zfar);
+        k_l2p_f1<<<grid, 256, 0, s>>>(nt, r0, lt, h->leaf_of, h->leaf_lev, h->row_off, (const float*)h->l2p_rows,
+                                      (const float*)h->Lexp, h->exp_total, h->zfar);
       else
-        k_l2p<R, decltype(nr)::value><<<grid, 256, 0, s>>>(nt, r0, lf.P, h->leaf_of, (const R*)h->l2p_rows,
-                                                           (const R*)h->Lexp, lf.exp_base, h->exp_total, h->zfar);
+        k_l2p<R, decltype(nr)::value><<<grid, 256, 0, s>>>(nt, r0, lt, h->leaf_of, h->leaf_lev, h->row_off,
+                                                           (const R*)h->l2p_rows, (const R*)h->Lexp, h->exp_total,
+                                                           h->zfar);
     });
     BEM_CUDA(cudaGetLastError());
+    BEM_TRY(bem_run_m2p(h, nrhs, h->Mexp, h->zfar, s, &nl));  // W-lists, added to the far sums
     bem_prof_end(h, pr, 7, nl, s);
     return BEM_OK;
   };

@@ -100,18 +100,24 @@ extern "C" int bem_destroy_batch(bem_batch* b) {
   return BEM_OK;
 }
 
-extern "C" int bem_setup_batch(const bem_mesh* meshes, const double* ks, int count, int p, double eps,
-                               const bem_options* opt, void* stream, bem_batch** out) {
+// opt_stride 0: every problem takes opts[0] (nullable); 1: problem i takes opts[i]
+static int setup_batch(const bem_mesh* meshes, const double* ks, int count, int p, double eps,
+                       const bem_options* opts, int opt_stride, void* stream, bem_batch** out) {
   bem_set_error("");
   if (!out) return bem_fail(BEM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!meshes || !ks || count < 1) return bem_fail(BEM_ERR_INVALID_ARG, "need count >= 1 meshes and wavenumbers");
+  if (opt_stride && !opts) return bem_fail(BEM_ERR_INVALID_ARG, "opts is NULL");
   bem_batch* b = new bem_batch();
   cudaGetDevice(&b->device);
   b->off.push_back(0);
   for (int i = 0; i < count; ++i) {
     bem_handle* h = nullptr;
-    int rc = bem_setup(&meshes[i], ks[i], p, eps, opt, stream, &h);
+    int rc = bem_setup(&meshes[i], ks[i], p, eps, opts ? opts + (size_t)i * opt_stride : nullptr, stream, &h);
+    if (rc == BEM_OK && i > 0 && h->nrhs_max != b->h[0]->nrhs_max) {
+      bem_destroy(h);
+      rc = bem_fail(BEM_ERR_INVALID_ARG, "every problem must use the same max_nrhs");
+    }
     if (rc != BEM_OK) {
       std::string m = "problem " + std::to_string(i) + ": " + bem_last_error();
       free_batch(b);
@@ -147,6 +153,16 @@ extern "C" int bem_setup_batch(const bem_mesh* meshes, const double* ks, int cou
   }
   *out = b;
   return BEM_OK;
+}
+
+extern "C" int bem_setup_batch(const bem_mesh* meshes, const double* ks, int count, int p, double eps,
+                               const bem_options* opt, void* stream, bem_batch** out) {
+  return setup_batch(meshes, ks, count, p, eps, opt, 0, stream, out);
+}
+
+extern "C" int bem_setup_batch_each(const bem_mesh* meshes, const double* ks, int count, int p, double eps,
+                                    const bem_options* opts, void* stream, bem_batch** out) {
+  return setup_batch(meshes, ks, count, p, eps, opts, 1, stream, out);
 }
 
 // the applies of all problems (staging buffers in, staging buffer out),

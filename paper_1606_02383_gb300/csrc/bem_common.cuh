@@ -164,6 +164,20 @@ struct LevelInfo {
   int* parent = nullptr;    // parent box (level l-1), -1 at the root
   int* coord = nullptr;     // [nbox][3] integer box coordinates at this level
   double* centre = nullptr; // [nbox][3]
+  // tree membership (adaptive octree): a box is in the tree when its parent is
+  // an internal tree box; a tree box is a leaf or internal
+  unsigned char* intree = nullptr;    // [nbox]
+  unsigned char* internal = nullptr;  // [nbox]
+  int nleaf = 0;                      // leaves on this level
+  int* leafbox = nullptr;             // [nleaf] box index of every leaf of this level
+  int leaf_g0 = 0;                    // global index of this level's first leaf
+};
+
+// per-level orders and expansion offsets, passed by value to kernels that
+// handle elements or boxes of several levels
+struct LevTab {
+  int P[BEM_MAXLEV + 1];
+  long long base[BEM_MAXLEV + 1];
 };
 
 // one profiled stage of one apply: events recorded on the caller's stream
@@ -181,6 +195,9 @@ struct bem_handle {
   int fixed_p = 0;
   double eps = 1e-5;
   int nrhs_max = 16;
+  int p2p_unit = 64;       // most targets per near-field warp work unit
+  int tc_kslice_max = 16;  // most K stages per tensor-core translation job
+  int corr_rules32 = 0;    // mixed modes: non-self near-singular rules summed in FP32
   int p_min = 4, p_max = 40;
   int p_level[BEM_MAXLEV + 1] = {0};  // explicit per-level orders (0 = automatic)
   int64_t nt = 0, nv = 0;
@@ -210,12 +227,58 @@ struct bem_handle {
   double4* src64 = nullptr;
   double hmax_all = 0.0;
 
-  int* leaf_of = nullptr;       // [nt] leaf box of every sorted element
-  // near field: 27 colleague slots per leaf (-1 = none)
-  int* near27 = nullptr;        // [nleaf][27]
+  // octree leaves.  A fixed leaf level (bem_options.leaf_level > 0) gives a
+  // uniform tree; otherwise boxes are split while they hold more than the
+  // split threshold and their children stay at least 3 longest edges wide, so
+  // leaves sit on several levels.  Global leaf g covers elements
+  // [gl_start[g], gl_end[g]); leaves are numbered level by level.
+  int adaptive = 0;
+  int nleaf_all = 0;
+  int* gl_start = nullptr;      // [nleaf_all]
+  int* gl_end = nullptr;        // [nleaf_all]
+  int* leaf_of = nullptr;       // [nt] box (within its level) of every element's leaf
+  unsigned char* leaf_lev = nullptr;  // [nt] level of every element's leaf
+  int* gleaf_of = nullptr;      // [nt] global leaf of every element
+  // P2M and L2P rows: element j's rows start at coefficient row_off[j] (P of
+  // its leaf level, rounded up to even, per element): P2M at 2 row_off[j],
+  // L2P at row_off[j] (complex units)
+  int64_t* row_off = nullptr;
+  int64_t row_total = 0;
+  // near field (U-lists): for leaf g, entries [u_ptr[g], u_ptr[g+1]): every
+  // leaf adjacent to g (any level, g itself included), with the offset
+  // centre(source leaf) - centre(g)
+  int* u_ptr = nullptr;
+  int* u_src = nullptr;
+  float4* u_shift32 = nullptr;
+  double4* u_shift64 = nullptr;
+  int64_t u_nnz = 0;
   int64_t p2p_pairs = 0;
-  int4* p2p_units = nullptr;    // warp work units (leaf, first target, count), largest first
+  int4* p2p_units = nullptr;    // warp work units (global leaf, first target, count), largest first
   int n_p2p_units = 0;
+  // W-lists (M2P): for leaf g, entries [w_ptr[g], w_ptr[g+1]) name boxes D
+  // (level << 24 | box) finer than g whose multipoles converge at g's targets,
+  // with the offset centre(g) - centre(D); w_leaves lists the leaves whose
+  // W-list is not empty
+  int* w_ptr = nullptr;
+  int* w_src = nullptr;
+  float4* w_shift32 = nullptr;
+  double4* w_shift64 = nullptr;
+  int w_nnz = 0;
+  int* w_leaves = nullptr;
+  int n_w_leaves = 0;
+  // X-lists (P2L), the duals of the W-lists: pairs (box B of level l, source
+  // leaf C) with C's elements expanded about B's centre; offsets centre(C) -
+  // centre(B)
+  int x_n[BEM_MAXLEV + 1] = {0};
+  int* x_dst[BEM_MAXLEV + 1] = {nullptr};
+  int* x_src[BEM_MAXLEV + 1] = {nullptr};
+  float4* x_shift32[BEM_MAXLEV + 1] = {nullptr};
+  double4* x_shift64[BEM_MAXLEV + 1] = {nullptr};
+  int64_t w_tp[BEM_MAXLEV + 1] = {0};  // (target, W box) pairs by the box's level
+  int64_t x_pts[BEM_MAXLEV + 1] = {0}; // (source point, X box) pairs by the box's level
+  int64_t w_evals = 0, x_evals = 0;    // (point, coefficient) products per rhs of the M2P and P2L work
+  int* wx_p = nullptr;                 // [BEM_MAXLEV + 1] order of every level
+  void* wx_a = nullptr;                // [BEM_MAXLEV + 1] k w_l in the operator's precision
 
   // correction CSR over sorted targets; values divided by wgt[j]
   int* corr_ptr = nullptr;      // [nt+1]
@@ -302,6 +365,14 @@ int bem_alloc(bem_handle* h, T** p, size_t count) {
 // ---- stage entry points (defined in the .cu files) ----
 int bem_build_geometry(bem_handle* h, const double* dV, const int32_t* dT, cudaStream_t s);
 int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t s);
+LevTab bem_levtab(const bem_handle* h);
+// W- and X-list work (bem_wx.cu): M2P into the far sums, P2L into the local
+// expansions, and their transposes for the adjoint apply
+int bem_build_wx_tables(bem_handle* h, cudaStream_t s);
+int bem_run_m2p(bem_handle* h, int nrhs, const void* M, double* zfar, cudaStream_t s, int* launches);
+int bem_run_p2l(bem_handle* h, int nrhs, const void* dens, void* Lexp, cudaStream_t s, int* launches);
+int bem_run_m2p_t(bem_handle* h, int nrhs, const void* dens, void* Mu, cudaStream_t s, int* launches);
+int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStream_t s, int* launches);
 int bem_build_correction(bem_handle* h, cudaStream_t s);
 int bem_build_far_field(bem_handle* h, cudaStream_t s);
 int bem_apply_sorted(bem_handle* h, int nrhs, cudaStream_t s);  // dens -> zn, zfar

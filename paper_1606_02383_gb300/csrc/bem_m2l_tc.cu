@@ -457,10 +457,11 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
   int nsm = 0;
   BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
   op.tc_want = 2 * (int64_t)std::max(nsm, 1);
-  int ksplit = TC_KSLICE;
-  if (base > 0 && base * ((nks_max + TC_KSLICE - 1) / TC_KSLICE) < op.tc_want) {
+  const int kmax = std::min(TC_KSLICE, std::max(2, h->tc_kslice_max));
+  int ksplit = kmax;
+  if (base > 0 && base * ((nks_max + kmax - 1) / kmax) < op.tc_want) {
     const int64_t slices = (op.tc_want + base - 1) / base;
-    ksplit = (int)std::max<int64_t>(2, std::min<int64_t>(TC_KSLICE, (nks_max + slices - 1) / slices));
+    ksplit = (int)std::max<int64_t>(2, std::min<int64_t>(kmax, (nks_max + slices - 1) / slices));
   }
   auto make_jobs = [&](int kslice) {
     std::vector<int4> js;
@@ -475,9 +476,9 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
     }
     return js;
   };
-  std::vector<int4> jobs = make_jobs(TC_KSLICE);
-  op.tc_kslice = TC_KSLICE;
-  if (ksplit < TC_KSLICE) {
+  std::vector<int4> jobs = make_jobs(kmax);
+  op.tc_kslice = kmax;
+  if (ksplit < kmax) {
     std::vector<int4> js = make_jobs(ksplit);
     op.tc_kslice_split = ksplit;
     op.n_tc_jobs_split = (int)js.size();

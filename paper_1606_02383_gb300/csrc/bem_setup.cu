@@ -15,11 +15,13 @@
 // by the offset between the two boxes so that each group shares one
 // translation matrix.
 //
-// Near-singular correction: for every target i and source j with j == i or
-// |x_i - c_j| < 4 h_j, C_ij = (entry by the refined rule R_L or the exact self
-// term) - (entry by the regular rule R_0), for S and D, in FP64.  The apply
-// evaluates R_0 for every pair (near field directly, far field by the FMM) and
-// adds C, which reproduces the rule-defined operator.
+// Near-singular correction: for every target i and source j != i with
+// |x_i - c_j| < 4 h_j, C_ij = (entry by the refined rule R_L) - (entry by the
+// regular rule R_0), and C_ii = the exact self term, for S and D, in FP64.
+// The apply evaluates R_0 for every other pair (near field directly, far
+// field by the FMM) and adds C, which reproduces the rule-defined operator;
+// the self pair never passes through the FP32 near field, so its D_ii = 0
+// and S_ii keep FP64 accuracy whatever the size of the leaf box.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -256,18 +258,23 @@ __global__ void k_count_p2p(int nleaf, const int* __restrict__ coll27, const int
   atomicAdd(pairs, (unsigned long long)(ns * (bend[b] - bstart[b])));
 }
 
-// V-list: children of the parent's colleagues not adjacent to b.  pass 0 counts per offset, pass 1 fills.
+// V-list of tree box b: children of the parent's internal colleagues that are
+// not adjacent to b (a leaf colleague has no children in the tree; its
+// elements reach b through the X-lists or the near field).  pass 0 counts per
+// offset, pass 1 fills.
 __global__ void k_vlist(int nbox, const int* __restrict__ coord, const int* __restrict__ parent,
                         const int* __restrict__ pcoll27, const int* __restrict__ pchild0,
-                        const int* __restrict__ pnchild, const int* __restrict__ ccoord, int pass, int* counts,
-                        int* cursor, const int* __restrict__ gstart, int* src_box, int* dst_box) {
+                        const int* __restrict__ pnchild, const int* __restrict__ ccoord,
+                        const unsigned char* __restrict__ intree, const unsigned char* __restrict__ pinternal, int pass,
+                        int* counts, int* cursor, const int* __restrict__ gstart, int* src_box, int* dst_box) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbox) return;
+  if (!intree[b]) return;
   int p = parent[b];
   int bx = coord[3 * b], by = coord[3 * b + 1], bz = coord[3 * b + 2];
   for (int t = 0; t < 27; ++t) {
     int q = pcoll27[27 * p + t];
-    if (q < 0) continue;
+    if (q < 0 || !pinternal[q]) continue;
     int c0 = pchild0[q], nc = pnchild[q];
     for (int c = c0; c < c0 + nc; ++c) {
       int dx = bx - ccoord[3 * c], dy = by - ccoord[3 * c + 1], dz = bz - ccoord[3 * c + 2];
@@ -281,6 +288,36 @@ __global__ void k_vlist(int nbox, const int* __restrict__ coord, const int* __re
         dst_box[pos] = b;
       }
     }
+  }
+}
+
+// longest edge of every box (one block per box)
+__global__ void k_box_hmax(int nbox, const int* __restrict__ bstart, const int* __restrict__ bend,
+                           const double* __restrict__ hmax, double* out) {
+  __shared__ double sm[128];
+  const int b = blockIdx.x;
+  double m = 0.0;
+  for (int i = bstart[b] + threadIdx.x; i < bend[b]; i += blockDim.x) m = fmax(m, hmax[i]);
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = sm[0];
+}
+
+// leaf membership of the elements of one level's leaves (one block per leaf)
+__global__ void k_leaf_mark(int nleaf, const int* __restrict__ leafbox, const int* __restrict__ bstart,
+                            const int* __restrict__ bend, int level, int g0, int* leaf_of, unsigned char* leaf_lev,
+                            int* gleaf_of) {
+  const int i = blockIdx.x;
+  if (i >= nleaf) return;
+  const int b = leafbox[i];
+  for (int e = bstart[b] + threadIdx.x; e < bend[b]; e += blockDim.x) {
+    leaf_of[e] = b;
+    leaf_lev[e] = (unsigned char)level;
+    gleaf_of[e] = g0 + i;
   }
 }
 
@@ -354,14 +391,16 @@ __global__ void k_corr_pairs(int64_t nt, const double* __restrict__ cent, const 
   if (!pass) count[i] = n;
 }
 
-// correction values, one warp per target row; values divided by wgt[j].  In the
-// FP64 modes everything is FP64; in the mixed modes (FP32 values) the rules of
-// non-self pairs are summed in FP32 relative to the target, the self term in FP64.
+// correction values, one warp per target row; values divided by wgt[j].  The
+// rules are summed in FP64 (the near-singular quadrature and the self term),
+// and stored in the operator's precision (float4 in the mixed modes).  With
+// rules32 (an option of the mixed modes) the rules of non-self pairs are
+// summed in FP32 relative to the target instead, for a faster setup.
 template <typename V4>
 __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ cent, const double* __restrict__ qpt,
                               const double* __restrict__ nrm, const double* __restrict__ area,
                               const double* __restrict__ hmax, const double* __restrict__ wgt,
-                              const int* __restrict__ ptr, const int* __restrict__ col, V4* val) {
+                              const int* __restrict__ ptr, const int* __restrict__ col, int rules32, V4* val) {
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x & 31;
   if (i >= nt) return;
@@ -370,7 +409,7 @@ __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ c
     int j = col[e];
     Tri64 t;
     load_tri64(qpt, nrm, cent, area, hmax, j, t);
-    if (sizeof(V4) == sizeof(float4) && (int64_t)j != i) {
+    if (sizeof(V4) == sizeof(float4) && rules32 && (int64_t)j != i) {
       // mixed modes (values stored in FP32): both rules in FP32, target-relative
       double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
       double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
@@ -397,11 +436,13 @@ __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ c
       continue;
     }
     zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0), s1 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
-    rule_refined(x, t, 0, k, s0, d0);  // what the regular rule contributes
     if ((int64_t)j == i) {
+      // the near field leaves the pair of an element with itself out, so the
+      // correction carries the whole exact self term
       s1 = self_single_layer(t, k);
       d1 = cmk(0.0, 0.0);
     } else {
+      rule_refined(x, t, 0, k, s0, d0);  // what the regular rule contributes
       double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
       double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
       int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
@@ -579,13 +620,46 @@ int bem_build_geometry(bem_handle* h, const double* dV, const int32_t* dT, cudaS
   return bem_check_device_error(h, s);
 }
 
+// ---------------------------------------------------------- adaptive tree --
+namespace {
+struct HostLevel {
+  int nbox = 0;
+  std::vector<uint32_t> key;
+  std::vector<int> start, end, parent, child0, nchild, coord, coll;
+  std::vector<double> centre, hm;
+  std::vector<unsigned char> intree, internal;
+};
+
+// boxes (l1, c1) and (l2, c2) from different subtrees touch (share a face,
+// edge or corner): their closed extents, on the finer level's grid, intersect
+bool boxes_touch(int l1, const int* c1, int l2, const int* c2) {
+  const int m = std::max(l1, l2);
+  const int64_t s1 = int64_t(1) << (m - l1), s2 = int64_t(1) << (m - l2);
+  for (int d = 0; d < 3; ++d) {
+    const int64_t lo1 = c1[d] * s1, hi1 = lo1 + s1, lo2 = c2[d] * s2, hi2 = lo2 + s2;
+    if (lo1 > hi2 || lo2 > hi1) return false;
+  }
+  return true;
+}
+}  // namespace
+
+LevTab bem_levtab(const bem_handle* h) {
+  LevTab t;
+  for (int l = 0; l <= BEM_MAXLEV; ++l) {
+    const bool has = l < (int)h->lev.size() && l >= 2 && l <= h->L;
+    t.P[l] = has ? h->lev[l].P : 0;
+    t.base[l] = has ? h->lev[l].exp_base : 0;
+  }
+  return t;
+}
+
 int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t s) {
   int64_t nt = h->nt;
   uint32_t* keys = h->lev[0].key;
   double lo_r[3];
   for (int d = 0; d < 3; ++d) lo_r[d] = h->root_c[d] - 0.5 * h->root_w;
 
-  // occupied boxes per level -> leaf level
+  // occupied boxes per level
   unsigned long long* dcnt;
   BEM_CUDA(cudaMallocAsync((void**)&dcnt, (BEM_MAXLEV + 1) * sizeof(unsigned long long), s));
   BEM_CUDA(cudaMemsetAsync(dcnt, 0, (BEM_MAXLEV + 1) * sizeof(unsigned long long), s));
@@ -594,28 +668,57 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
   BEM_CUDA(cudaMemcpyAsync(cnt, dcnt, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   BEM_CUDA(cudaStreamSynchronize(s));
   BEM_CUDA(cudaFreeAsync(dcnt, s));
-  int L;
-  if (leaf_level > 0) {
-    L = std::min(leaf_level, BEM_MAXLEV);
-  } else {
-    // deepest level whose mean occupancy reaches the target and whose boxes are at
-    // least 3 longest edges wide (quadrature points stay close to their box)
-    L = 0;
-    for (int l = 0; l <= BEM_MAXLEV; ++l) {
-      double wl = h->root_w / (1 << l);
-      if ((double)nt / (double)cnt[l] >= (double)leaf_target && wl >= 3.0 * h->hmax_all) L = l;
+
+  // Uniform tree (leaf_level > 0): every box of that level is a leaf.
+  // Adaptive trees: levels 0 and 1 are always split, and no box is split into
+  // children narrower than 3 of its longest edges (quadrature points stay
+  // close to their box, so expansions about the box centre converge one box
+  // away).  leaf_level = 0: the depth is chosen per level-2 region, the
+  // deepest level whose mean occupancy inside the region reaches leaf_target,
+  // so leaves differ in level only between regions of different density and
+  // the W/X-lists stay short.  leaf_level = -1: each box of level >= 2 is
+  // split while it holds more than `split` elements.  If even level 2 is too
+  // narrow for the longest edge, or the mesh fits one leaf, the tree is the
+  // root alone and everything is near field.
+  const bool adaptive = leaf_level <= 0;
+  const bool regional = leaf_level == 0;
+  const int split = 2 * std::max(leaf_target, 1);
+  h->adaptive = adaptive ? (regional ? 1 : 2) : 0;
+  // regional depth: distinct boxes per (level-2 region, level) from the sorted keys
+  std::vector<int> region_depth;
+  if (regional && !(h->root_w / 4.0 < 3.0 * h->hmax_all || nt <= split)) {
+    std::vector<uint32_t> hk(nt);
+    std::vector<double> hh(nt);
+    BEM_CUDA(cudaMemcpyAsync(hk.data(), keys, nt * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(hh.data(), h->hmax, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    const int R = 2, nreg = 1 << (3 * R);
+    const int shR = 3 * (BEM_MAXLEV - R);
+    std::vector<int64_t> nel(nreg, 0);
+    std::vector<double> hreg(nreg, 0.0);
+    std::vector<std::vector<int64_t>> nbox(BEM_MAXLEV + 1, std::vector<int64_t>(nreg, 0));
+    for (int64_t i = 0; i < nt; ++i) {
+      const int reg = (int)(hk[i] >> shR);
+      ++nel[reg];
+      hreg[reg] = std::max(hreg[reg], hh[i]);
+      for (int l = R; l <= BEM_MAXLEV; ++l) {
+        const int sh = 3 * (BEM_MAXLEV - l);
+        if (i == 0 || (hk[i] >> sh) != (hk[i - 1] >> sh)) ++nbox[l][reg];
+      }
     }
-    if (L == 1) L = 0;  // a level-1 leaf has no far field either; keep the single box
+    region_depth.assign(nreg, R);
+    for (int reg = 0; reg < nreg; ++reg) {
+      if (nel[reg] == 0) continue;
+      for (int l = R; l <= BEM_MAXLEV; ++l)
+        if ((double)nel[reg] >= (double)leaf_target * (double)nbox[l][reg] &&
+            h->root_w / (1 << l) >= 3.0 * hreg[reg])
+          region_depth[reg] = l;
+    }
   }
-  h->L = L;
+  int Lfix = std::min(std::max(leaf_level, 0), BEM_MAXLEV);
+  bool single = false;
+  if (adaptive && (h->root_w / 4.0 < 3.0 * h->hmax_all || nt <= split)) single = true;
 
-  // near-singular search level: widest boxes still >= 4 h_max
-  int Lc = 0;
-  for (int l = 0; l <= L; ++l)
-    if (h->root_w / (1 << l) >= 4.0 * h->hmax_all) Lc = l;
-  h->Lc = Lc;
-
-  // boxes of every level 0..L
   int* flags;
   int* scan;
   BEM_CUDA(cudaMallocAsync((void**)&flags, nt * sizeof(int), s));
@@ -624,8 +727,12 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
   cub::DeviceScan::InclusiveSum(nullptr, tb, flags, scan, (int)nt, s);
   void* tmp;
   BEM_CUDA(cudaMallocAsync(&tmp, tb, s));
-  std::vector<int*> elbox(L + 1);
-  for (int l = 0; l <= L; ++l) {
+  std::vector<int*> elbox(BEM_MAXLEV + 1, nullptr);
+  std::vector<HostLevel> hl(BEM_MAXLEV + 1);
+  double* dhm = nullptr;
+  BEM_CUDA(cudaMallocAsync((void**)&dhm, std::max<unsigned long long>(cnt[BEM_MAXLEV], 1) * sizeof(double), s));
+  int L = 0;
+  for (int l = 0; l <= BEM_MAXLEV; ++l) {
     LevelInfo& lv = h->lev[l];
     lv.nbox = (int)cnt[l];
     lv.w = h->root_w / (1 << l);
@@ -640,13 +747,77 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     BEM_TRY(bem_alloc(h, &lv.parent, lv.nbox));
     BEM_TRY(bem_alloc(h, &lv.child0, lv.nbox));
     BEM_TRY(bem_alloc(h, &lv.nchild, lv.nbox));
+    BEM_TRY(bem_alloc(h, &lv.intree, lv.nbox));
+    BEM_TRY(bem_alloc(h, &lv.internal, lv.nbox));
     k_level_flags<<<nblk(nt, 256), 256, 0, s>>>(keys, nt, sh, flags);
     BEM_CUDA(cub::DeviceScan::InclusiveSum(tmp, tb, flags, scan, (int)nt, s));
     k_level_boxes<<<nblk(nt, 256), 256, 0, s>>>(keys, scan, nt, sh, l, lo_r[0], lo_r[1], lo_r[2], lv.w, elbox[l], bkey,
                                                 lv.start, lv.end, lv.coord, lv.centre);
     BEM_CUDA(cudaGetLastError());
     lv.key = bkey;  // (level 0 held the fine keys until now; `keys` still points at them)
+    k_box_hmax<<<lv.nbox, 128, 0, s>>>(lv.nbox, lv.start, lv.end, h->hmax, dhm);
+    BEM_CUDA(cudaGetLastError());
+    HostLevel& H = hl[l];
+    H.nbox = lv.nbox;
+    H.key.resize(lv.nbox);
+    H.start.resize(lv.nbox);
+    H.end.resize(lv.nbox);
+    H.coord.resize(3 * (size_t)lv.nbox);
+    H.centre.resize(3 * (size_t)lv.nbox);
+    H.hm.resize(lv.nbox);
+    BEM_CUDA(cudaMemcpyAsync(H.key.data(), bkey, lv.nbox * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.start.data(), lv.start, lv.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.end.data(), lv.end, lv.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.coord.data(), lv.coord, 3 * lv.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.centre.data(), lv.centre, 3 * lv.nbox * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.hm.data(), dhm, lv.nbox * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    // parents on the host: the box of level l - 1 whose key is this key's prefix
+    H.parent.assign(lv.nbox, -1);
+    if (l > 0) {
+      const std::vector<uint32_t>& pk = hl[l - 1].key;
+      for (int b = 0; b < lv.nbox; ++b)
+        H.parent[b] = (int)(std::lower_bound(pk.begin(), pk.end(), H.key[b] >> 3) - pk.begin());
+    }
+    // tree membership and leaf decision
+    H.intree.assign(lv.nbox, 0);
+    H.internal.assign(lv.nbox, 0);
+    bool any_internal = false;
+    const double wchild = h->root_w / (1 << (l + 1));
+    for (int b = 0; b < lv.nbox; ++b) {
+      const bool in = (l == 0) || hl[l - 1].internal[H.parent[b]] != 0;
+      H.intree[b] = in ? 1 : 0;
+      if (!in) continue;
+      bool leaf;
+      if (!adaptive)
+        leaf = l >= Lfix;
+      else if (single)
+        leaf = true;
+      else if (l < 2)
+        leaf = false;
+      else if (regional)
+        leaf = l >= region_depth[H.key[b] >> (3 * (l - 2))];
+      else
+        leaf = l == BEM_MAXLEV || (H.end[b] - H.start[b]) <= split || wchild < 3.0 * H.hm[b];
+      H.internal[b] = leaf ? 0 : 1;
+      any_internal = any_internal || !leaf;
+    }
+    BEM_CUDA(cudaMemcpyAsync(lv.intree, H.intree.data(), lv.nbox, cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(lv.internal, H.internal.data(), lv.nbox, cudaMemcpyHostToDevice, s));
+    L = l;
+    if (!any_internal) break;
   }
+  BEM_CUDA(cudaStreamSynchronize(s));
+  BEM_CUDA(cudaFreeAsync(dhm, s));
+  for (int l = L + 1; l <= BEM_MAXLEV; ++l) h->lev[l].nbox = 0;
+  h->L = L;
+
+  // near-singular search level: widest boxes still >= 4 h_max
+  int Lc = 0;
+  for (int l = 0; l <= L; ++l)
+    if (h->root_w / (1 << l) >= 4.0 * h->hmax_all) Lc = l;
+  h->Lc = Lc;
+
   for (int l = 0; l <= L; ++l) {
     LevelInfo& lv = h->lev[l];
     k_level_links<<<nblk(lv.nbox, 128), 128, 0, s>>>(lv.nbox, lv.start, lv.end, l > 0 ? elbox[l - 1] : nullptr,
@@ -654,7 +825,7 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     BEM_CUDA(cudaGetLastError());
   }
 
-  // colleagues on every level (needed for V-lists, near field and correction search)
+  // colleagues on every level (V-lists, the near-field lists, correction search)
   std::vector<int*> coll(L + 1);
   for (int l = 0; l <= L; ++l) {
     BEM_TRY(bem_alloc(h, &coll[l], 27 * (size_t)h->lev[l].nbox));
@@ -662,46 +833,211 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
                                                            coll[l]);
     BEM_CUDA(cudaGetLastError());
   }
-  h->near27 = coll[L];
-  {
-    unsigned long long* dp;
-    BEM_CUDA(cudaMallocAsync((void**)&dp, sizeof(unsigned long long), s));
-    BEM_CUDA(cudaMemsetAsync(dp, 0, sizeof(unsigned long long), s));
-    k_count_p2p<<<nblk(h->lev[L].nbox, 128), 128, 0, s>>>(h->lev[L].nbox, coll[L], h->lev[L].start, h->lev[L].end, dp);
-    unsigned long long v = 0;
-    BEM_CUDA(cudaMemcpyAsync(&v, dp, sizeof(v), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaStreamSynchronize(s));
-    BEM_CUDA(cudaFreeAsync(dp, s));
-    h->p2p_pairs = (int64_t)v;
+  for (int l = 0; l <= L; ++l) {
+    HostLevel& H = hl[l];
+    H.coll.resize(27 * (size_t)H.nbox);
+    H.child0.resize(H.nbox);
+    H.nchild.resize(H.nbox);
+    BEM_CUDA(cudaMemcpyAsync(H.coll.data(), coll[l], H.coll.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.child0.data(), h->lev[l].child0, H.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(H.nchild.data(), h->lev[l].nchild, H.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
   }
-  // P2P warp work units: each leaf's targets cut into 64-target blocks plus the
-  // binary decomposition of the remainder, sorted by cost (targets x near sources)
-  if (bem_is_fmm(h)) {
-    int nl = h->lev[L].nbox;
-    std::vector<int> hs(nl), he(nl), hn(27 * (size_t)nl);
-    BEM_CUDA(cudaMemcpyAsync(hs.data(), h->lev[L].start, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaMemcpyAsync(he.data(), h->lev[L].end, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaMemcpyAsync(hn.data(), coll[L], hn.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA(cudaStreamSynchronize(s));
+
+  // ---- leaves, numbered level by level ----
+  std::vector<int> gl_level, gl_box;
+  for (int l = 0; l <= L; ++l) {
+    LevelInfo& lv = h->lev[l];
+    HostLevel& H = hl[l];
+    std::vector<int> lb;
+    for (int b = 0; b < H.nbox; ++b)
+      if (H.intree[b] && !H.internal[b]) lb.push_back(b);
+    lv.nleaf = (int)lb.size();
+    lv.leaf_g0 = (int)gl_level.size();
+    for (int b : lb) {
+      gl_level.push_back(l);
+      gl_box.push_back(b);
+    }
+    BEM_TRY(bem_alloc(h, &lv.leafbox, std::max<size_t>(lb.size(), 1)));
+    if (!lb.empty())
+      BEM_CUDA(cudaMemcpyAsync(lv.leafbox, lb.data(), lb.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaStreamSynchronize(s));
-    std::vector<std::pair<int64_t, int4>> units;
-    for (int b = 0; b < nl; ++b) {
-      int64_t ns = 0;
+  }
+  const int ng = (int)gl_level.size();
+  h->nleaf_all = ng;
+  std::vector<int> hgs(ng), hge(ng);
+  std::vector<double> hgc(3 * (size_t)ng);
+  std::vector<std::vector<int>> gid(L + 1);
+  for (int l = 0; l <= L; ++l) gid[l].assign(hl[l].nbox, -1);
+  for (int g = 0; g < ng; ++g) {
+    const int l = gl_level[g], b = gl_box[g];
+    hgs[g] = hl[l].start[b];
+    hge[g] = hl[l].end[b];
+    for (int d = 0; d < 3; ++d) hgc[3 * (size_t)g + d] = hl[l].centre[3 * (size_t)b + d];
+    gid[l][b] = g;
+  }
+  BEM_TRY(bem_alloc(h, &h->gl_start, std::max(ng, 1)));
+  BEM_TRY(bem_alloc(h, &h->gl_end, std::max(ng, 1)));
+  double* d_glc;
+  BEM_TRY(bem_alloc(h, &d_glc, 3 * (size_t)std::max(ng, 1)));
+  BEM_CUDA(cudaMemcpyAsync(h->gl_start, hgs.data(), ng * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(h->gl_end, hge.data(), ng * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(d_glc, hgc.data(), hgc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  BEM_TRY(bem_alloc(h, &h->leaf_of, nt));
+  BEM_TRY(bem_alloc(h, &h->leaf_lev, nt));
+  BEM_TRY(bem_alloc(h, &h->gleaf_of, nt));
+  for (int l = 0; l <= L; ++l) {
+    LevelInfo& lv = h->lev[l];
+    if (lv.nleaf == 0) continue;
+    k_leaf_mark<<<lv.nleaf, 128, 0, s>>>(lv.nleaf, lv.leafbox, lv.start, lv.end, l, lv.leaf_g0, h->leaf_of,
+                                         h->leaf_lev, h->gleaf_of);
+    BEM_CUDA(cudaGetLastError());
+  }
+
+  // ---- U-, W- and X-lists on the host ----
+  // For leaf g of level l: U(g) holds every leaf that touches g (g included);
+  // W(g) holds the boxes D below g's colleagues that do not touch g although
+  // their parents do (D's multipole converges on g); X(D) gets g in return
+  // (g's elements expanded about D's centre).  Together with the V-lists of g
+  // and its ancestors this counts every (target, source) pair exactly once.
+  std::vector<int> uptr(ng + 1, 0), usrc, wptr(ng + 1, 0), wsrc;
+  std::vector<double> ushift, wshift;
+  std::vector<std::vector<int>> xdst(L + 1), xsrc(L + 1);
+  std::vector<std::vector<double>> xshift(L + 1);
+  auto push_u = [&](int g, int lsrc, int bsrc) {
+    const int gs = gid[lsrc][bsrc];
+    usrc.push_back(gs);
+    for (int d = 0; d < 3; ++d) ushift.push_back(hgc[3 * (size_t)gs + d] - hgc[3 * (size_t)g + d]);
+  };
+  for (int g = 0; g < ng; ++g) {
+    const int l = gl_level[g], b = gl_box[g];
+    const int* cb = &hl[l].coord[3 * (size_t)b];
+    if (l == 0) push_u(g, l, b);
+    if (l > 0) {
+      // same-level colleagues in slot order (g itself in the middle slot),
+      // and the tree below the internal ones
+      std::vector<std::pair<int, int>> stack;
       for (int t = 0; t < 27; ++t) {
-        int c = hn[27 * (size_t)b + t];
-        if (c >= 0) ns += he[c] - hs[c];
+        if (t == 13) {
+          push_u(g, l, b);
+          continue;
+        }
+        const int c = hl[l].coll[27 * (size_t)b + t];
+        if (c < 0 || !hl[l].intree[c]) continue;
+        if (!hl[l].internal[c])
+          push_u(g, l, c);
+        else
+          stack.push_back({l, c});
       }
-      int t0 = hs[b], nc = he[b] - hs[b];
-      while (nc >= 64) {
-        units.push_back({64 * ns, make_int4(b, t0, 64, 0)});
-        t0 += 64;
-        nc -= 64;
+      while (!stack.empty()) {
+        const auto [m, dbox] = stack.back();
+        stack.pop_back();
+        for (int ch = hl[m].child0[dbox]; ch < hl[m].child0[dbox] + hl[m].nchild[dbox]; ++ch) {
+          if (boxes_touch(m + 1, &hl[m + 1].coord[3 * (size_t)ch], l, cb)) {
+            if (hl[m + 1].internal[ch])
+              stack.push_back({m + 1, ch});
+            else
+              push_u(g, m + 1, ch);
+          } else {
+            wsrc.push_back(((m + 1) << 24) | ch);
+            for (int d = 0; d < 3; ++d)
+              wshift.push_back(hgc[3 * (size_t)g + d] - hl[m + 1].centre[3 * (size_t)ch + d]);
+            xdst[m + 1].push_back(ch);
+            xsrc[m + 1].push_back(g);
+            for (int d = 0; d < 3; ++d)
+              xshift[m + 1].push_back(hgc[3 * (size_t)g + d] - hl[m + 1].centre[3 * (size_t)ch + d]);
+          }
+        }
       }
-      for (int j = 5; j >= 0; --j)
+      // coarser leaves that touch g: colleagues of g's ancestors
+      int a = b;
+      for (int la = l - 1; la >= 0; --la) {
+        a = hl[la + 1].parent[a];
+        for (int t = 0; t < 27; ++t) {
+          if (t == 13) continue;
+          const int c = hl[la].coll[27 * (size_t)a + t];
+          if (c < 0 || !hl[la].intree[c] || hl[la].internal[c]) continue;
+          if (boxes_touch(la, &hl[la].coord[3 * (size_t)c], l, cb)) push_u(g, la, c);
+        }
+      }
+    }
+    uptr[g + 1] = (int)usrc.size();
+    wptr[g + 1] = (int)wsrc.size();
+  }
+  h->u_nnz = (int64_t)usrc.size();
+  h->w_nnz = (int)wsrc.size();
+  BEM_TRY(bem_alloc(h, &h->u_ptr, ng + 1));
+  BEM_TRY(bem_alloc(h, &h->u_src, std::max<size_t>(usrc.size(), 1)));
+  BEM_TRY(bem_alloc(h, &h->w_ptr, ng + 1));
+  BEM_TRY(bem_alloc(h, &h->w_src, std::max<size_t>(wsrc.size(), 1)));
+  BEM_CUDA(cudaMemcpyAsync(h->u_ptr, uptr.data(), (ng + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(h->u_src, usrc.data(), usrc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(h->w_ptr, wptr.data(), (ng + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!wsrc.empty())
+    BEM_CUDA(cudaMemcpyAsync(h->w_src, wsrc.data(), wsrc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  std::vector<int> wl;
+  for (int g = 0; g < ng; ++g)
+    if (wptr[g + 1] > wptr[g]) wl.push_back(g);
+  h->n_w_leaves = (int)wl.size();
+  BEM_TRY(bem_alloc(h, &h->w_leaves, std::max<size_t>(wl.size(), 1)));
+  if (!wl.empty())
+    BEM_CUDA(cudaMemcpyAsync(h->w_leaves, wl.data(), wl.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  // offsets in the operator's precision
+  auto upload_shift = [&](const std::vector<double>& v, float4** f, double4** d) -> int {
+    const size_t n = v.size() / 3;
+    if (bem_is_fp64(h)) {
+      std::vector<double4> o(std::max<size_t>(n, 1));
+      for (size_t i = 0; i < n; ++i) o[i] = make_double4(v[3 * i], v[3 * i + 1], v[3 * i + 2], 0.0);
+      BEM_TRY(bem_alloc(h, d, o.size()));
+      BEM_CUDA(cudaMemcpyAsync(*d, o.data(), o.size() * sizeof(double4), cudaMemcpyHostToDevice, s));
+    } else {
+      std::vector<float4> o(std::max<size_t>(n, 1));
+      for (size_t i = 0; i < n; ++i)
+        o[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f);
+      BEM_TRY(bem_alloc(h, f, o.size()));
+      BEM_CUDA(cudaMemcpyAsync(*f, o.data(), o.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    }
+    BEM_CUDA(cudaStreamSynchronize(s));
+    return BEM_OK;
+  };
+  BEM_TRY(upload_shift(ushift, &h->u_shift32, &h->u_shift64));
+  BEM_TRY(upload_shift(wshift, &h->w_shift32, &h->w_shift64));
+  for (int l = 0; l <= L; ++l) {
+    h->x_n[l] = (int)xdst[l].size();
+    if (xdst[l].empty()) continue;
+    BEM_TRY(bem_alloc(h, &h->x_dst[l], xdst[l].size()));
+    BEM_TRY(bem_alloc(h, &h->x_src[l], xsrc[l].size()));
+    BEM_CUDA(cudaMemcpyAsync(h->x_dst[l], xdst[l].data(), xdst[l].size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(h->x_src[l], xsrc[l].data(), xsrc[l].size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_TRY(upload_shift(xshift[l], &h->x_shift32[l], &h->x_shift64[l]));
+    for (size_t i = 0; i < xsrc[l].size(); ++i) h->x_pts[l] += 3 * (int64_t)(hge[xsrc[l][i]] - hgs[xsrc[l][i]]);
+  }
+  for (int g = 0; g < ng; ++g)
+    for (int e = wptr[g]; e < wptr[g + 1]; ++e) h->w_tp[wsrc[e] >> 24] += hge[g] - hgs[g];
+
+  // ---- P2P work units: each leaf's targets cut into blocks of p2p_unit
+  // targets plus the binary decomposition of the remainder, sorted by cost ----
+  {
+    const int U = h->p2p_unit, ulog = U == 16 ? 4 : (U == 32 ? 5 : 6);
+    std::vector<std::pair<int64_t, int4>> units;
+    int64_t pairs = 0;
+    for (int g = 0; g < ng; ++g) {
+      int64_t ns = 0;
+      for (int e = uptr[g]; e < uptr[g + 1]; ++e) ns += hge[usrc[e]] - hgs[usrc[e]];
+      int t0 = hgs[g], nc = hge[g] - hgs[g];
+      pairs += ns * nc;
+      while (nc >= U) {
+        units.push_back({U * ns, make_int4(g, t0, U, 0)});
+        t0 += U;
+        nc -= U;
+      }
+      for (int j = ulog - 1; j >= 0; --j)
         if (nc & (1 << j)) {
-          units.push_back({(int64_t)(1 << j) * ns, make_int4(b, t0, 1 << j, 0)});
+          units.push_back({(int64_t)(1 << j) * ns, make_int4(g, t0, 1 << j, 0)});
           t0 += 1 << j;
         }
     }
+    h->p2p_pairs = pairs;
     std::stable_sort(units.begin(), units.end(),
                      [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) { return a.first > b.first; });
     std::vector<int4> u4(units.size());
@@ -743,13 +1079,13 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
       BEM_TRY(bem_alloc(h, &v, nnz));
       h->corr_val = v;
       k_corr_values<double4><<<nblk(nt * 32, 128), 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
-                                                                 h->wgt, h->corr_ptr, h->corr_col, v);
+                                                                 h->wgt, h->corr_ptr, h->corr_col, 0, v);
     } else {
       float4* v;
       BEM_TRY(bem_alloc(h, &v, nnz));
       h->corr_val = v;
       k_corr_values<float4><<<nblk(nt * 32, 128), 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
-                                                                h->wgt, h->corr_ptr, h->corr_col, v);
+                                                                h->wgt, h->corr_ptr, h->corr_col, h->corr_rules32, v);
     }
     BEM_CUDA(cudaGetLastError());
     BEM_CUDA(cudaFreeAsync(t2, s));
@@ -758,12 +1094,12 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
 
   // ---- P2P arrays ----
   // FMM: coordinates relative to the element's leaf centre (keeps FP32
-  // differences accurate; the kernel adds the exact box offset).  Direct sums:
-  // one common frame, the root centre.
+  // differences accurate; the kernels add the exact offset between leaf
+  // centres).  Direct sums: one common frame, the root centre.
   bool direct = (h->mode == BEM_MODE_DIRECT_FP64 || h->mode == BEM_MODE_DIRECT_FP32);
   {
-    const int* frame_of = elbox[L];
-    const double* frame_c = h->lev[L].centre;
+    const int* frame_of = h->gleaf_of;
+    const double* frame_c = d_glc;
     double* rc = nullptr;
     int* zero = nullptr;
     if (direct) {
@@ -802,7 +1138,8 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     BEM_CUDA(cudaMemsetAsync(dcnt2, 0, 343 * sizeof(int), s));
     BEM_CUDA(cudaMemsetAsync(dcur, 0, 343 * sizeof(int), s));
     k_vlist<<<nblk(lv.nbox, 128), 128, 0, s>>>(lv.nbox, lv.coord, lv.parent, coll[l - 1], pv.child0, pv.nchild,
-                                               lv.coord, 0, dcnt2, nullptr, nullptr, nullptr, nullptr);
+                                               lv.coord, lv.intree, pv.internal, 0, dcnt2, nullptr, nullptr, nullptr,
+                                               nullptr);
     int hc[343];
     BEM_CUDA(cudaMemcpyAsync(hc, dcnt2, sizeof(hc), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaStreamSynchronize(s));
@@ -829,7 +1166,8 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     dst_box = op.d_dst_off;
     BEM_CUDA(cudaMemcpyAsync(dstart, gs.data(), 344 * sizeof(int), cudaMemcpyHostToDevice, s));
     k_vlist<<<nblk(lv.nbox, 128), 128, 0, s>>>(lv.nbox, lv.coord, lv.parent, coll[l - 1], pv.child0, pv.nchild,
-                                               lv.coord, 1, nullptr, dcur, dstart, src_box, dst_box);
+                                               lv.coord, lv.intree, pv.internal, 1, nullptr, dcur, dstart, src_box,
+                                               dst_box);
     BEM_CUDA(cudaGetLastError());
     BEM_CUDA(cudaStreamSynchronize(s));
     BEM_CUDA(cudaFreeAsync(dcnt2, s));

@@ -293,21 +293,37 @@ __device__ void solid_harmonics(const double* u, const double* dir, int p, zd* S
   }
 }
 
-// one thread per (sorted) element; a: [nt][P] conj rows for S, b: normal-derivative rows, r: L2P rows
+// order, box width and box centres of every leaf level, for the row builder
+struct LevRows {
+  int p[BEM_MAXLEV + 1];
+  double w[BEM_MAXLEV + 1];
+  const double* centre[BEM_MAXLEV + 1];
+};
+
+// one thread per (sorted) element, about the centre of the element's leaf
+// with that leaf level's order; the rows start at complex offsets
+// 2 row_off[j] (a: conj rows for S, then b: normal-derivative rows, P each)
+// and row_off[j] (r: L2P rows).  Elements of leaves above level 2 have none.
 template <typename R, int PM>
-__global__ void k_p2m_l2p_rows(int64_t nt, int p, double k, double w, const double* __restrict__ cent,
+__global__ void k_p2m_l2p_rows(int64_t nt, LevRows lr, double k, const double* __restrict__ cent,
                                const double* __restrict__ qpt, const double* __restrict__ nrm,
-                               const int* __restrict__ leaf_of, const double* __restrict__ bcentre, R* rows_ab,
-                               R* rows_r, double* scratch, int* err) {
+                               const int* __restrict__ leaf_of, const unsigned char* __restrict__ leaf_lev,
+                               const int64_t* __restrict__ row_off, int Pscr, R* rows_ab_base, R* rows_r_base,
+                               double* scratch, int* err) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= nt) return;
+  const int lvl = leaf_lev[j];
+  if (lvl < 2) return;
+  const int p = lr.p[lvl];
+  const double w = lr.w[lvl];
   const int P = (p + 1) * (p + 1);
-  zd* S = (zd*)(scratch + (int64_t)j * 4 * P * 2 + 0);
+  zd* S = (zd*)(scratch + (int64_t)j * 4 * Pscr * 2 + 0);
   zd* dS = S + P;
   zd* A = dS + P;
   zd* B = A + P;
   double jh[PM + 3];
   int b = leaf_of[j];
+  const double* bcentre = lr.centre[lvl];
   double c[3] = {bcentre[3 * b], bcentre[3 * b + 1], bcentre[3 * b + 2]};
   double nn[3] = {nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2]};
   for (int e = 0; e < P; ++e) A[e] = B[e] = cmk(0.0, 0.0);
@@ -334,7 +350,7 @@ __global__ void k_p2m_l2p_rows(int64_t nt, int p, double k, double w, const doub
     }
   }
   zd fac = cmk(0.0, 4.0 * BEM_PI * k);
-  R* ab = rows_ab + 2 * ((int64_t)j * 2 * P);
+  R* ab = rows_ab_base + 4 * row_off[j];
   for (int e = 0; e < P; ++e) {
     zd a = fac * A[e], bb = fac * B[e];
     ab[2 * e] = (R)a.re;
@@ -353,7 +369,7 @@ __global__ void k_p2m_l2p_rows(int64_t nt, int p, double k, double w, const doub
     double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     sph_jhat(k * r, p, jh);
     solid_harmonics<PM>(u, nn, p, S, dS);
-    R* rr = rows_r + 2 * ((int64_t)j * P);
+    R* rr = rows_r_base + 2 * row_off[j];
     for (int n = 0; n <= p; ++n)
       for (int m = -n; m <= n; ++m) {
         int e = IDX(n, m);
@@ -364,10 +380,12 @@ __global__ void k_p2m_l2p_rows(int64_t nt, int p, double k, double w, const doub
   }
 }
 
-__global__ void k_leaf_of(int nleaf, const int* __restrict__ bstart, const int* __restrict__ bend, int* leaf_of) {
-  int b = blockIdx.x;
-  if (b >= nleaf) return;
-  for (int i = bstart[b] + threadIdx.x; i < bend[b]; i += blockDim.x) leaf_of[i] = b;
+// row length of every element: P of its leaf level rounded up to even (0 above level 2)
+__global__ void k_row_len(int64_t nt, const unsigned char* __restrict__ leaf_lev, LevTab lt, int64_t* len) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  const int P = lt.P[leaf_lev[j]];
+  len[j] = (P + 1) & ~1;
 }
 
 __global__ void k_pairs_to_offsets(int np, const int* __restrict__ src_box, const int* __restrict__ dst_box,
@@ -503,15 +521,17 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
     pmax = std::max(pmax, lv.p);
   }
   if (h->exp_total > 2000000000LL) return bem_fail(BEM_ERR_UNSUPPORTED, "expansion storage exceeds 32-bit offsets");
+  BEM_TRY(bem_build_wx_tables(h, s));
+  h->w_evals = h->x_evals = 0;
+  for (int l = 2; l <= L; ++l) {
+    h->w_evals += h->w_tp[l] * h->lev[l].P;
+    h->x_evals += h->x_pts[l] * h->lev[l].P;
+  }
   bool f64 = bem_is_fp64(h);
   size_t csz = f64 ? 2 * sizeof(double) : 2 * sizeof(float);
   int Pm = (pmax + 1) * (pmax + 1);
 
-  // leaf membership (needed by the P2M/L2P rows)
-  BEM_TRY(bem_alloc(h, &h->leaf_of, nt));
-  int* leaf_of = h->leaf_of;
-  k_leaf_of<<<h->lev[L].nbox, 128, 0, s>>>(h->lev[L].nbox, h->lev[L].start, h->lev[L].end, leaf_of);
-  BEM_CUDA(cudaGetLastError());
+  int* leaf_of = h->leaf_of;  // leaf membership (built with the tree)
 
   // ---- groups: M2L (from the V-lists), M2M/L2L (octants) ----
   std::vector<MatJob> mj;
@@ -602,14 +622,39 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
     BEM_CUDA(cudaMallocAsync((void**)&fl, std::max(cv.nbox, 1), s));
     k_octant_pairs<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cv.key, cv.parent, cb, pb, fl);
     BEM_CUDA(cudaGetLastError());
+    // only tree boxes take part (children of internal boxes): compact the pairs
+    int ncp = cv.nbox;
+    {
+      std::vector<int> hcb(cv.nbox), hpb(cv.nbox);
+      std::vector<unsigned char> hfl(cv.nbox), hin(cv.nbox);
+      BEM_CUDA(cudaMemcpyAsync(hcb.data(), cb, cv.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaMemcpyAsync(hpb.data(), pb, cv.nbox * sizeof(int), cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaMemcpyAsync(hfl.data(), fl, cv.nbox, cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaMemcpyAsync(hin.data(), cv.intree, cv.nbox, cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaStreamSynchronize(s));
+      ncp = 0;
+      for (int c = 0; c < cv.nbox; ++c)
+        if (hin[c]) {
+          hcb[ncp] = hcb[c];
+          hpb[ncp] = hpb[c];
+          hfl[ncp] = hfl[c];
+          ++ncp;
+        }
+      if (ncp > 0) {
+        BEM_CUDA(cudaMemcpyAsync(cb, hcb.data(), ncp * sizeof(int), cudaMemcpyHostToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(pb, hpb.data(), ncp * sizeof(int), cudaMemcpyHostToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(fl, hfl.data(), ncp, cudaMemcpyHostToDevice, s));
+      }
+      BEM_CUDA(cudaStreamSynchronize(s));
+    }
     double hw = 0.5 * cv.w;
     double v[3] = {hw, hw, hw};  // canonical c_child - c_parent
     GroupedOp* ops[2] = {&h->m2m[l], &h->l2l[l]};
     for (int which = 0; which < 2; ++which) {
       GroupedOp& op = *ops[which];
-      op.npairs = cv.nbox;
-      op.ngroups = 1;
-      op.pair_start = {0, cv.nbox};
+      op.npairs = ncp;
+      op.ngroups = ncp > 0 ? 1 : 0;
+      op.pair_start = ncp > 0 ? std::vector<int>{0, ncp} : std::vector<int>{0};
       if (which == 0) {
         op.rows = {pv.P};
         op.cols = {cv.P};
@@ -619,17 +664,19 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
         op.cols = {pv.P};
         op.mat_off = {add_mat(2, v, cv.p, pv.p, l + 1, l)};
       }
-      BEM_TRY(bem_alloc(h, &op.d_src_off, std::max(cv.nbox, 1)));
-      BEM_TRY(bem_alloc(h, &op.d_dst_off, std::max(cv.nbox, 1)));
-      BEM_TRY(bem_alloc(h, &op.d_flags, std::max(cv.nbox, 1)));
-      BEM_CUDA(cudaMemcpyAsync(op.d_flags, fl, cv.nbox, cudaMemcpyDeviceToDevice, s));
-      if (which == 0)
-        k_pairs_to_offsets<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, cb, pb, cv.exp_base, cv.P, pv.exp_base, pv.P,
-                                                              op.d_src_off, op.d_dst_off);
-      else
-        k_pairs_to_offsets<<<nblk(cv.nbox, 256), 256, 0, s>>>(cv.nbox, pb, cb, pv.exp_base, pv.P, cv.exp_base, cv.P,
-                                                              op.d_src_off, op.d_dst_off);
-      BEM_CUDA(cudaGetLastError());
+      BEM_TRY(bem_alloc(h, &op.d_src_off, std::max(ncp, 1)));
+      BEM_TRY(bem_alloc(h, &op.d_dst_off, std::max(ncp, 1)));
+      BEM_TRY(bem_alloc(h, &op.d_flags, std::max(ncp, 1)));
+      if (ncp > 0) {
+        BEM_CUDA(cudaMemcpyAsync(op.d_flags, fl, ncp, cudaMemcpyDeviceToDevice, s));
+        if (which == 0)
+          k_pairs_to_offsets<<<nblk(ncp, 256), 256, 0, s>>>(ncp, cb, pb, cv.exp_base, cv.P, pv.exp_base, pv.P,
+                                                            op.d_src_off, op.d_dst_off);
+        else
+          k_pairs_to_offsets<<<nblk(ncp, 256), 256, 0, s>>>(ncp, pb, cb, pv.exp_base, pv.P, cv.exp_base, cv.P,
+                                                            op.d_src_off, op.d_dst_off);
+        BEM_CUDA(cudaGetLastError());
+      }
       BEM_TRY(make_jobs(h, op, s));
     }
     BEM_CUDA(cudaStreamSynchronize(s));
@@ -738,37 +785,68 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
     }
   }
 
-  // ---- P2M / L2P rows at the leaf level ----
-  LevelInfo& lf = h->lev[L];
-  int PL = lf.P;
+  // ---- P2M / L2P rows of every element, about its leaf's centre ----
+  // row offsets: P of the element's leaf level rounded up to even (16-byte
+  // aligned rows), prefix-summed
+  LevRows lr;
+  int PLmax = 0;
+  for (int l = 0; l <= BEM_MAXLEV; ++l) {
+    const bool has = l >= 2 && l <= L;
+    lr.p[l] = has ? h->lev[l].p : 0;
+    lr.w[l] = has ? h->lev[l].w : 0.0;
+    lr.centre[l] = has ? h->lev[l].centre : nullptr;
+    if (has && h->lev[l].nleaf > 0) {
+      if (h->lev[l].p > 60) return bem_fail(BEM_ERR_UNSUPPORTED, "leaf order above 60");
+      PLmax = std::max(PLmax, h->lev[l].P);
+    }
+  }
+  {
+    LevTab lt = bem_levtab(h);
+    int64_t* len;
+    BEM_CUDA(cudaMallocAsync((void**)&len, nt * sizeof(int64_t), s));
+    k_row_len<<<nblk(nt, 256), 256, 0, s>>>(nt, h->leaf_lev, lt, len);
+    BEM_TRY(bem_alloc(h, &h->row_off, nt));
+    size_t tbs = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tbs, len, h->row_off, (int)nt, s);
+    void* tsc;
+    BEM_CUDA(cudaMallocAsync(&tsc, tbs, s));
+    BEM_CUDA(cub::DeviceScan::ExclusiveSum(tsc, tbs, len, h->row_off, (int)nt, s));
+    int64_t last[2] = {0, 0};
+    BEM_CUDA(cudaMemcpyAsync(&last[0], h->row_off + nt - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaMemcpyAsync(&last[1], len + nt - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    h->row_total = last[0] + last[1];
+    BEM_CUDA(cudaFreeAsync(tsc, s));
+    BEM_CUDA(cudaFreeAsync(len, s));
+  }
+  const int64_t rt = std::max<int64_t>(h->row_total, 2);
   if (f64) {
     double *ab, *r;
-    BEM_TRY(bem_alloc(h, &ab, (size_t)nt * 2 * PL * 2));
-    BEM_TRY(bem_alloc(h, &r, (size_t)nt * PL * 2));
+    BEM_TRY(bem_alloc(h, &ab, (size_t)rt * 2 * 2));
+    BEM_TRY(bem_alloc(h, &r, (size_t)rt * 2));
     h->p2m_rows = ab;
     h->l2p_rows = r;
   } else {
     float *ab, *r;
-    BEM_TRY(bem_alloc(h, &ab, (size_t)nt * 2 * PL * 2));
-    BEM_TRY(bem_alloc(h, &r, (size_t)nt * PL * 2));
+    BEM_TRY(bem_alloc(h, &ab, (size_t)rt * 2 * 2));
+    BEM_TRY(bem_alloc(h, &r, (size_t)rt * 2));
     h->p2m_rows = ab;
     h->l2p_rows = r;
   }
   const int64_t chunk = 1 << 16;
   double* scr;
-  BEM_CUDA(cudaMallocAsync((void**)&scr, (size_t)chunk * 4 * PL * 2 * sizeof(double), s));
-  for (int64_t j0 = 0; j0 < nt; j0 += chunk) {
+  BEM_CUDA(cudaMallocAsync((void**)&scr, (size_t)chunk * 4 * std::max(PLmax, 1) * 2 * sizeof(double), s));
+  for (int64_t j0 = 0; j0 < nt && PLmax > 0; j0 += chunk) {
     int64_t cnt = std::min(chunk, nt - j0);
     // the kernel indexes scratch by its own element index, so offset pointers per chunk
-    if (lf.p > 60) return bem_fail(BEM_ERR_UNSUPPORTED, "leaf order above 60");
     if (f64)
       k_p2m_l2p_rows<double, 64><<<nblk(cnt, 64), 64, 0, s>>>(
-          cnt, lf.p, h->k, lf.w, h->cent + 3 * j0, h->qpt + 9 * j0, h->nrm + 3 * j0, leaf_of + j0, lf.centre,
-          (double*)h->p2m_rows + 2 * (j0 * 2 * PL), (double*)h->l2p_rows + 2 * (j0 * PL), scr, h->d_err);
+          cnt, lr, h->k, h->cent + 3 * j0, h->qpt + 9 * j0, h->nrm + 3 * j0, leaf_of + j0, h->leaf_lev + j0,
+          h->row_off + j0, PLmax, (double*)h->p2m_rows, (double*)h->l2p_rows, scr, h->d_err);
     else
       k_p2m_l2p_rows<float, 64><<<nblk(cnt, 64), 64, 0, s>>>(
-          cnt, lf.p, h->k, lf.w, h->cent + 3 * j0, h->qpt + 9 * j0, h->nrm + 3 * j0, leaf_of + j0, lf.centre,
-          (float*)h->p2m_rows + 2 * (j0 * 2 * PL), (float*)h->l2p_rows + 2 * (j0 * PL), scr, h->d_err);
+          cnt, lr, h->k, h->cent + 3 * j0, h->qpt + 9 * j0, h->nrm + 3 * j0, leaf_of + j0, h->leaf_lev + j0,
+          h->row_off + j0, PLmax, (float*)h->p2m_rows, (float*)h->l2p_rows, scr, h->d_err);
     BEM_CUDA(cudaGetLastError());
   }
   BEM_CUDA(cudaStreamSynchronize(s));

@@ -31,26 +31,38 @@ def _dtype_code(t: torch.Tensor) -> int:
     raise TypeError("densities must be complex64 or complex128 tensors")
 
 
+def _options(mode="mixed", leaf_level=0, leaf_target=48, max_nrhs=16, p_min=4, p_max=40, p_level=None, p2p_unit=64,
+             tc_kslice=16, corr_rules32=0):
+    levels = (ctypes.c_int * 11)(*([0] * 11))
+    for lvl, order in (p_level or {}).items():
+        levels[int(lvl)] = int(order)
+    return _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
+                           int(max_nrhs), int(p_min), int(p_max), levels, int(p2p_unit), int(tc_kslice),
+                           int(corr_rules32))
+
+
 class Operator:
     """z = (1/2 I - D) x + S y on a triangle mesh (see include/bem.h).
 
     Parameters: vertices [nv,3] float64, triangles [nt,3] int32 (host arrays),
     wavenumber k, order p (> 0 fixed, 0 = automatic from eps), eps, mode in
-    {"mixed", "fp64", "direct64", "direct32"}, leaf_level (0 = automatic),
-    leaf_target, max_nrhs, p_level ({level: order} overrides).
+    {"mixed", "fp64", "direct64", "direct32"}, leaf_level (> 0 uniform tree
+    with leaves on that level, 0 = adaptive with the depth chosen per level-2
+    region, -1 = adaptive split per box), leaf_target (mean elements per leaf
+    the adaptive trees aim at), max_nrhs, p_level ({level: order} overrides),
+    p2p_unit (most targets per near-field work unit: 16, 32, 64), tc_kslice
+    (most 16-wide K stages per tensor-core translation job, 2..16),
+    corr_rules32 (mixed modes: near-singular rules of non-self pairs in FP32).
     """
 
     def __init__(self, vertices, triangles, k, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48,
-                 max_nrhs=16, p_min=4, p_max=40, p_level=None):
+                 max_nrhs=16, p_min=4, p_max=40, p_level=None, p2p_unit=64, tc_kslice=16, corr_rules32=0):
         lib = _lib.load()
         V = np.ascontiguousarray(vertices, dtype=np.float64)
         T = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
-        levels = (ctypes.c_int * 11)(*([0] * 11))
-        for lvl, order in (p_level or {}).items():
-            levels[int(lvl)] = int(order)
-        opt = _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
-                              int(max_nrhs), int(p_min), int(p_max), levels)
+        opt = _options(mode, leaf_level, leaf_target, max_nrhs, p_min, p_max, p_level, p2p_unit, tc_kslice,
+                       corr_rules32)
         h = ctypes.c_void_p()
         _lib.check(lib.bem_setup(ctypes.byref(mesh), float(k), int(p), float(eps), ctypes.byref(opt), _stream(),
                                  ctypes.byref(h)))
@@ -379,7 +391,8 @@ class Batch:
     along the element axis in problem order: [nrhs, sum N_b].
     """
 
-    def __init__(self, problems, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48, max_nrhs=4):
+    def __init__(self, problems, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48, max_nrhs=4,
+                 options=None):
         lib = _lib.load()
         self._keep = []
         meshes = (_lib.BemMesh * len(problems))()
@@ -390,11 +403,21 @@ class Batch:
             self._keep += [V, T]
             meshes[i] = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
             ks[i] = float(k)
-        opt = _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
-                              int(max_nrhs), 4, 40, (ctypes.c_int * 11)())
         h = ctypes.c_void_p()
-        _lib.check(lib.bem_setup_batch(meshes, ks, len(problems), int(p), float(eps), ctypes.byref(opt), _stream(),
-                                       ctypes.byref(h)))
+        if options is None:
+            opt = _options(mode, leaf_level, leaf_target, max_nrhs)
+            _lib.check(lib.bem_setup_batch(meshes, ks, len(problems), int(p), float(eps), ctypes.byref(opt),
+                                           _stream(), ctypes.byref(h)))
+        else:
+            # per-problem options (e.g. an autotuner's choices): dicts of Operator keywords
+            opts = (_lib.BemOptions * len(problems))()
+            for i, o in enumerate(options):
+                kw = {"mode": mode, "leaf_level": leaf_level, "leaf_target": leaf_target}
+                kw.update(o or {})
+                kw["max_nrhs"] = max_nrhs
+                opts[i] = _options(**kw)
+            _lib.check(lib.bem_setup_batch_each(meshes, ks, len(problems), int(p), float(eps), opts, _stream(),
+                                                ctypes.byref(h)))
         self._h = h
         self._lib = lib
         self.sizes = [int(T.shape[0]) for _, T, _ in problems]

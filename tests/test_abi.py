@@ -76,3 +76,20 @@ def test_sync_and_wait_limit_reject_null_handles():
     lib = _lib.load()
     assert lib.bem_sync(None, None) == _lib.BEM_ERR_INVALID_ARG
     assert lib.bem_set_wait_limit(None, 0, 0) == _lib.BEM_ERR_INVALID_ARG
+
+
+def test_option_checks_without_gpu():
+    """Out-of-range tree and tile options are rejected before any device work."""
+    import numpy as np
+    lib = _lib.load()
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.float64)
+    T = np.array([[0, 1, 2]], dtype=np.int32)
+    mesh = _lib.BemMesh(3, 1, V.ctypes.data, T.ctypes.data, 0)
+    h = ctypes.c_void_p()
+    from paper_1606_02383_gb300.operator import _options
+    for kw, word in (({"leaf_level": -2}, b"leaf_level"), ({"p2p_unit": 48}, b"p2p_unit"),
+                     ({"tc_kslice": 1}, b"tc_kslice"), ({"tc_kslice": 17}, b"tc_kslice")):
+        opt = _options(**kw)
+        rc = lib.bem_setup(ctypes.byref(mesh), 1.0, 8, 1e-5, ctypes.byref(opt), None, ctypes.byref(h))
+        assert rc == _lib.BEM_ERR_INVALID_ARG, kw
+        assert word in lib.bem_last_error(), (kw, lib.bem_last_error())

@@ -1,4 +1,4 @@
-"""Leaf-level autotuner: the selection rule on CPU, the tuned operator on GPU."""
+"""Autotuner over the tree and the tile choices: the selection rule on CPU, the tuned operator on GPU."""
 import numpy as np
 import pytest
 
@@ -31,8 +31,14 @@ def test_tuned_operator_matches_oracle(cuda_ok):
     V, T = inputs.icosphere(4)
     n = T.shape[0]
     op, report = tune(V, T, 5.0, eps=1e-5, reps=3, warmup=1)
-    assert len(report["ms"]) >= 2 and report["chosen"] in report["ms"]
-    assert op.info("leaf_level") == report["chosen"]
+    assert len(report["ms"]) >= 4
+    assert report["gain"] >= 1.0
+    chosen = report["chosen"]
+    assert set(chosen) == {"leaf_level", "leaf_target", "p2p_unit", "tc_kslice"}
+    if chosen["leaf_level"] > 0:
+        assert op.info("leaf_level") == chosen["leaf_level"] and op.info("adaptive") == 0
+    else:
+        assert op.info("adaptive") == 1
     x = inputs.random_density(n, 1, seed=81)
     y = inputs.random_density(n, 1, seed=82)
     z = op.apply(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()

@@ -94,3 +94,32 @@ def test_batch_solve_rejects_bad_arguments(cuda_ok):
     rc = batch._lib.bem_gmres_solve_batch(batch._h, 1, _lib.BEM_C128, b.data_ptr(), None, 1e-6, 10, 10, 0, None, None,
                                           None)
     assert rc == _lib.BEM_ERR_INVALID_ARG
+
+
+def test_uneven_batch_with_per_body_options(cuda_ok):
+    """Bodies spanning the batching workload's size spread (2,000 to 20,000
+    triangles here, ellipsoids and tori, k in [1, 8]), each with its own
+    options (trees, near-field units, K slices as an autotuner would pick
+    them), applied together: every body against the oracle on sampled rows,
+    and against its own single-problem operator."""
+    probs = inputs.batch_bodies(6, seed=3, n_min=2000, n_max=20000)
+    sizes = [T.shape[0] for _, T, _ in probs]
+    assert min(sizes) < 4000 and max(sizes) > 10000, sizes
+    opts = [{"leaf_level": 0, "leaf_target": 32}, {"leaf_level": -1, "leaf_target": 32},
+            {"leaf_level": 0, "leaf_target": 48, "p2p_unit": 32}, {"leaf_level": 3, "tc_kslice": 8},
+            {"leaf_level": 0, "leaf_target": 24, "p2p_unit": 16}, {"leaf_level": 0, "leaf_target": 64}]
+    batch = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2, options=opts)
+    n = batch.n
+    x = inputs.random_density(n, 2, seed=61)
+    y = inputs.random_density(n, 2, seed=62)
+    z = batch.apply(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+    for b, ((V, T, k), o) in enumerate(zip(probs, opts)):
+        a, e = batch.offsets[b], batch.offsets[b + 1]
+        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", max_nrhs=2, **o)
+        zs = op.apply(torch.from_numpy(x[:, a:e]).cuda(), torch.from_numpy(y[:, a:e]).cuda()).cpu().numpy()
+        assert rel(z[:, a:e], zs) <= 1e-6, b
+        rows = np.sort(np.random.default_rng(b).choice(e - a, 300, replace=False))
+        ref = oracle.apply(V, T, k, x=x[:, a:e], y=y[:, a:e], rows=rows)
+        assert rel(z[:, a:e][:, rows], ref) <= 1e-5, (b, sizes[b], o)
+        op.close()
+    batch.close()
