@@ -755,11 +755,13 @@ def run_other(args):
         c = inputs.centroids(V, T)
         x = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=0)).cuda()
         y = torch.from_numpy(inputs.random_density(n, 1, seed=0, stream=1)).cuda()
-        # the trees: uniform at the deepest level the width rule allows, the
-        # adaptive default, and the autotuned choice
+        # the trees: the default uniform rule, the adaptive trees (per-region
+        # depth for two occupancy targets), and the autotuned choice
         from paper_1606_02383_gb300.autotune import tune
         trees = {}
-        for name, kw in (("uniform", {"leaf_level": 6}), ("adaptive_default", {})):
+        for name, kw in (("uniform_default", {}), ("uniform_level7", {"leaf_level": 7}),
+                         ("adaptive_region_target48", {"leaf_level": -1, "leaf_target": 48}),
+                         ("adaptive_region_target24", {"leaf_level": -1, "leaf_target": 24})):
             o = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", **kw)
             trees[name] = {"ms": _timed(lambda: o.apply(x, y), steps, warm), "leaves": o.info("n_leaves"),
                            "leaves_per_level": {l: o.info(200 + l) for l in range(11) if o.info(200 + l)}}

@@ -90,11 +90,15 @@ typedef struct {
   int mode;         /* bem_mode, default BEM_MODE_FMM_MIXED */
   int leaf_level;   /* octree leaves (Section 2.3's FMM tree):
                        > 0  : uniform tree, every leaf on this level;
-                       0    : adaptive, depth chosen per level-2 region: the
+                       0    : uniform tree on the deepest level whose mean
+                              occupancy over the mesh reaches leaf_target and
+                              whose boxes are at least 3 longest edges wide
+                              (the default);
+                       -1   : adaptive, depth chosen per level-2 region: the
                               deepest level whose mean occupancy in the region
                               reaches leaf_target and whose boxes stay at least
-                              3 of the region's longest edges wide (the default);
-                       -1   : adaptive, every box split while it holds more than
+                              3 of the region's longest edges wide;
+                       -2   : adaptive, every box split while it holds more than
                               2 leaf_target elements and its children stay at
                               least 3 of its longest edges wide */
   int leaf_target;  /* mean triangles per occupied leaf for the automatic choice (default 48) */
@@ -107,6 +111,9 @@ typedef struct {
   int tc_kslice;    /* most 16-wide K stages per tensor-core translation job, 2..16 (default 16) */
   int corr_rules32; /* mixed modes: 1 sums the refined rules of non-self near-singular pairs in FP32
                        relative to the target (faster setup); 0 sums them in FP64 (default) */
+  int tc_tf32;      /* mixed mode: 1 runs the tensor-core translations as 3xTF32; 0 (default) as the
+                       two-term FP16 split with power-of-two row scales (same 11-bit mantissa, half
+                       the bytes and twice the tensor rate) */
 } bem_options;
 
 /*
@@ -459,7 +466,7 @@ typedef enum {
   BEM_INFO_LAUNCHES_LAST_APPLY = 12, /* kernels the last bem_apply launched (memsets excluded) */
   BEM_INFO_M2M_FLOPS = 13,   /* 8 P_child P_parent per child box summed over levels (one rhs) */
   BEM_INFO_L2L_FLOPS = 14,   /* 8 P_parent P_child per child box summed over levels (one rhs) */
-  BEM_INFO_ADAPTIVE = 15,    /* 0: uniform tree, 1: per-region depth, 2: per-box split at the count threshold */
+  BEM_INFO_ADAPTIVE = 15,    /* 0: uniform tree, 1: per-region depth (leaf_level -1), 2: per-box split (-2) */
   BEM_INFO_ROW_COEFFS = 16,  /* coefficients of the stored L2P rows over all elements (P2M rows: twice as many) */
   BEM_INFO_W_PAIRS = 17,     /* (target leaf, source box) pairs of the W-lists (M2P) */
   BEM_INFO_X_PAIRS = 18,     /* (target box, source leaf) pairs of the X-lists (P2L) */

@@ -57,10 +57,11 @@ def _key(cfg):
 def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, targets=(24, 32, 48, 64),
          units=(32, 64), kslices=(8, 16), reps=5, warmup=2, seed=0, **options):
     """Returns ``(operator, report)`` with the fastest candidate for ``nrhs``
-    right-hand sides.  Candidates: the adaptive tree (leaf_level 0) for every
-    leaf target in ``targets``, and uniform trees on the adaptive default's
-    deepest level +- ``spread``; then, for the best tree, every p2p_unit in
-    ``units`` and every tc_kslice in ``kslices``.  ``report`` holds
+    right-hand sides.  Candidates: the default uniform tree (leaf_level 0) and
+    uniform trees on its level +- ``spread``, the adaptive tree with its depth
+    chosen per region (leaf_level -1) for every leaf target in ``targets``;
+    then, for the best tree, every p2p_unit in ``units`` and every tc_kslice
+    in ``kslices``.  ``report`` holds
     ``{"default": cfg, "chosen": cfg, "ms": [(cfg, ms), ...], "gain": default_ms / chosen_ms}``."""
     n = np.asarray(triangles).shape[0]
     x = torch.from_numpy(inputs.random_density(n, nrhs, seed=seed, stream=0)).cuda()
@@ -86,8 +87,8 @@ def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, 
     default = dict(DEFAULTS)
     run(default)
     deepest = state["best"].info("leaf_level")
-    trees = [dict(default, leaf_target=t) for t in targets]
-    trees += [dict(default, leaf_level=lvl) for lvl in range(deepest - spread, deepest + spread + 1) if 2 <= lvl <= 10]
+    trees = [dict(default, leaf_level=lvl) for lvl in range(deepest - spread, deepest + spread + 1) if 2 <= lvl <= 10]
+    trees += [dict(default, leaf_level=-1, leaf_target=t) for t in targets]
     for cfg in trees:
         run(cfg)
     base = dict(state["best_cfg"])

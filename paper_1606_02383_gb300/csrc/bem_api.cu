@@ -141,7 +141,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   if (o.mode < 0 || o.mode > 4) return bem_fail(BEM_ERR_INVALID_ARG, "unknown mode");
   if (o.max_nrhs > 1024) return bem_fail(BEM_ERR_INVALID_ARG, "max_nrhs above 1024");
   if (o.leaf_level > BEM_MAXLEV) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level above 10");
-  if (o.leaf_level < -1) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level below -1");
+  if (o.leaf_level < -2) return bem_fail(BEM_ERR_INVALID_ARG, "leaf_level below -2");
   if (o.p_min > o.p_max || o.p_max > 60) return bem_fail(BEM_ERR_INVALID_ARG, "bad order bounds");
   if (o.p2p_unit != 16 && o.p2p_unit != 32 && o.p2p_unit != 64)
     return bem_fail(BEM_ERR_INVALID_ARG, "p2p_unit must be 16, 32 or 64");
@@ -158,6 +158,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->p2p_unit = o.p2p_unit;
   h->tc_kslice_max = o.tc_kslice;
   h->corr_rules32 = o.corr_rules32 ? 1 : 0;
+  h->tc_fp16 = (o.mode == BEM_MODE_FMM_MIXED && o.tc_tf32 == 0) ? 1 : 0;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
   for (int l = 0; l <= BEM_MAXLEV; ++l) {

@@ -145,6 +145,8 @@ struct GroupedOp {
   int64_t tc_want = 0;  // CTAs that give every SM two
   int* d_prep_row = nullptr;            // [npairs] row (flag * nbox + box) of the prepared source
   float* tcA = nullptr;
+  float* tscale = nullptr;  // FP16 split: inverse power-of-two scale of every matrix row, per group at d_tsoff[g]
+  int* d_tsoff = nullptr;
   int64_t* d_tc_off = nullptr;
   int4* d_tc_jobs = nullptr;
   int n_tc_jobs = 0;
@@ -198,6 +200,7 @@ struct bem_handle {
   int p2p_unit = 64;       // most targets per near-field warp work unit
   int tc_kslice_max = 16;  // most K stages per tensor-core translation job
   int corr_rules32 = 0;    // mixed modes: non-self near-singular rules summed in FP32
+  int tc_fp16 = 0;         // mixed mode: translations as the FP16 split (else 3xTF32)
   int p_min = 4, p_max = 40;
   int p_level[BEM_MAXLEV + 1] = {0};  // explicit per-level orders (0 = automatic)
   int64_t nt = 0, nv = 0;
@@ -306,8 +309,10 @@ struct bem_handle {
   GroupedOp m2l_T[BEM_MAXLEV + 1];  // target level-l Lambda -> source level-l Mu (transpose of m2l[l])
   GroupedOp l2l_T[BEM_MAXLEV + 1];  // child level l+1 -> parent level l (transpose of l2l[l])
   void* mats_T = nullptr;
-  float* prep = nullptr;            // reflected, TF32-split source expansions of one level (tensor-core path)
+  float* prep = nullptr;            // reflected, TF32- or FP16-split source expansions of one level (tensor-core path)
   int64_t prep_len = 0;
+  float* prep_scale = nullptr;      // FP16 split: inverse power-of-two scale of every prepared row
+  int64_t prep_scale_len = 0;
   double4* uv = nullptr;            // [nrhs_max][nt]: (u = S^T h, v = D^T h) before the weight, sorted
 
   // workspaces

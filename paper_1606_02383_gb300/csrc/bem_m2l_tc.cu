@@ -21,6 +21,14 @@
 //   - one thread issues 2 k-steps x 3 tcgen05.mma (M=128, N<=256, K=8) and
 //     commits them to an mbarrier that releases the stage (two stages);
 //   - long K is split across CTAs (outputs are accumulated atomically).
+// FP16 split (the default of the mixed mode): the same product with
+// kind::f16 MMAs (K = 16 per instruction, 32 per stage) on a two-term FP16
+// split, A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.  FP16 keeps 11 significant
+// bits like TF32 but only a 5-bit exponent, so every source row (pair) and
+// every matrix row is scaled by a power of two that puts its largest entry
+// in [2^13, 2^14) before the split; the epilogue multiplies the scales back
+// out (exact).  A stage then holds 32 K in the bytes TF32 needs for 16, so the
+// matrices stream half the bytes and the pipeline runs half the stages.
 // In the epilogue every thread owns one pair (its TMEM lane) and adds that
 // pair's outputs to the destination expansion with (re, im) vector atomics,
 // applying the output reflection.  Every wait is bounded (about one second of
@@ -29,6 +37,8 @@
 // returns.
 #include <algorithm>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "bem_common.cuh"
 
@@ -90,6 +100,19 @@ __device__ __forceinline__ uint32_t instr_desc(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
+// instruction descriptor: D = F32, A = B = F16, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t instr_desc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -102,6 +125,23 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
 __device__ __forceinline__ uint32_t core_off(int row, int kk, int rows) {
   int j = kk >> 3, kg = (kk >> 2) & 1, e = kk & 3;
   return (uint32_t)(j * (rows / 8) * 256 + (row >> 3) * 256 + kg * 128 + (row & 7) * 16 + e * 4);
+}
+// the same layout by byte position within a row's 64-byte stage (32 FP16 or 16 TF32)
+__device__ __forceinline__ uint32_t core_off_b(int row, int byte, int rows) {
+  int j = byte >> 5, kg = (byte >> 4) & 1, e = byte & 15;
+  return (uint32_t)(j * (rows / 8) * 256 + (row >> 3) * 256 + kg * 128 + (row & 7) * 16 + e);
+}
+
+// power of two that puts x's magnitude in [2^13, 2^14) (1 for 0), and its inverse
+__host__ __device__ __forceinline__ void f16_scale(float x, float* scale, float* inv) {
+  if (!(x > 0.f) || !isfinite(x)) {
+    *scale = *inv = 1.f;
+    return;
+  }
+  int ex;
+  frexpf(x, &ex);  // x = m 2^ex, m in [0.5, 1)
+  *scale = ldexpf(1.f, 14 - ex);
+  *inv = ldexpf(1.f, ex - 14);
 }
 
 // --------------------------------------------------------- setup packing --
@@ -134,13 +174,60 @@ __global__ void k_tc_pack(const float* __restrict__ T, int Po, int Pi, int nks, 
   (void)nnt;
 }
 
+// FP16 packing: rows scaled by rsc[R] (largest entry in [2^13, 2^14)); per
+// k stage of 32 a block [hi N x 32 | lo N x 32] halves, in the byte layout of
+// the TF32 blocks (64 bytes per row and half).
+__global__ void k_tc_rowscale(const float* __restrict__ T, int Po, int Pi, float* rsc, float* rinv) {
+  // one warp per output coefficient q (real rows 2q, 2q+1 share the entries)
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (q >= Po) return;
+  float m = 0.f;
+  for (int k = lane; k < Pi; k += 32)
+    m = fmaxf(m, fmaxf(fabsf(T[2 * ((int64_t)q * Pi + k)]), fabsf(T[2 * ((int64_t)q * Pi + k) + 1])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    float sc, iv;
+    f16_scale(m, &sc, &iv);
+    rsc[2 * q] = rsc[2 * q + 1] = sc;
+    rinv[2 * q] = rinv[2 * q + 1] = iv;
+  }
+}
+
+__global__ void k_tc_pack16(const float* __restrict__ T, int Po, int Pi, int nks, const float* __restrict__ rsc,
+                            float* out) {
+  int nt = blockIdx.x / nks, ks = blockIdx.x % nks;
+  int N = tc_ntile_width(2 * Po, nt);
+  unsigned char* blk = (unsigned char*)(out + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS) + (int64_t)ks * (2 * N * TC_KS));
+  for (int idx = threadIdx.x; idx < N * 32; idx += blockDim.x) {
+    int row = idx / 32, kk = idx % 32;
+    int R = nt * TC_NMAX + row, C = ks * 32 + kk;
+    int q = R >> 1, k = C >> 1;
+    float v = 0.f;
+    if (q < Po && k < Pi) {
+      float tr = T[2 * ((int64_t)q * Pi + k)], ti = T[2 * ((int64_t)q * Pi + k) + 1];
+      int pr = R & 1, pc = C & 1;
+      v = ((pr == pc) ? tr : (pr == 0 ? -ti : ti)) * rsc[R];
+    }
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    const uint32_t o = core_off_b(row, 2 * kk, N);
+    *(__half*)(blk + o) = hi;
+    *(__half*)(blk + N * 64 + o) = lo;
+  }
+}
+
 // ------------------------------------------------------------------ kernel --
+// F16: the FP16-split form (32 K per stage, scaled rows: escale per prepared
+// source row, tscale per matrix row at tsoff[g]); otherwise TF32 (16 K per
+// stage, nprod = 3 for 3xTF32 or 1 for plain TF32).
+template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
     const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
-    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep, int R2,
-    int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice, int* err,
-    long long wait_limit, int hold_first_copy) {
+    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep,
+    int row_floats, int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice,
+    int* err, long long wait_limit, int hold_first_copy, const float* __restrict__ escale,
+    const float* __restrict__ tscale, const int* __restrict__ tsoff) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_t[2];
   __shared__ __align__(8) uint64_t bar_m[2];
@@ -155,7 +242,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const int g = job.x, p0 = job.y, np = job.z & 255, nt = job.w;
   const int Po = grows[g], Pi = gcols[g];
   const int N = tc_ntile_width(2 * Po, nt);
-  const int nks = (2 * Pi + TC_KS - 1) / TC_KS;
+  constexpr int KSTG = F16 ? 32 : TC_KS;  // K per stage
+  const int nks = (2 * Pi + KSTG - 1) / KSTG;
   const int ks0 = (job.z >> 8) * kslice, ks1 = min(nks, ks0 + kslice);
   const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
   const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
@@ -185,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = instr_desc(N);
+  const uint32_t idesc = F16 ? instr_desc_f16(N) : instr_desc(N);
   int issued_t = 0, committed = 0;  // tracked by thread 0 only
 
   // gather of one E stage from the prepared rows (reflection and hi/lo split
@@ -200,7 +288,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
       const int c = ((item >> 5) & 15) * 8 + (item & 7), quad = (item >> 3) & 3, part = item >> 9;
       const int row = s_src[c];
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (row >= 0) v = *(const float4*)(prep + (int64_t)row * (2 * R2) + ks * (2 * TC_KS) + part * TC_KS + quad * 4);
+      if (row >= 0) v = *(const float4*)(prep + (int64_t)row * row_floats + ks * (2 * TC_KS) + part * TC_KS + quad * 4);
       pre[q] = v;
     }
   };
@@ -255,10 +343,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
           uint64_t al = smem_desc(e1 + j * (TC_M / 8) * 256);
           uint64_t bh = smem_desc(t0 + j * (N / 8) * 256);
           uint64_t bl = smem_desc(t0 + N * TC_KS * 4 + j * (N / 8) * 256);
-          mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
-          if (nprod == 3) {
-            mma_tf32(tmem, ah, bl, idesc, 1u);
-            mma_tf32(tmem, al, bh, idesc, 1u);
+          if constexpr (F16) {
+            mma_f16(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
+            mma_f16(tmem, ah, bl, idesc, 1u);
+            mma_f16(tmem, al, bh, idesc, 1u);
+          } else {
+            mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
+            if (nprod == 3) {
+              mma_tf32(tmem, ah, bl, idesc, 1u);
+              mma_tf32(tmem, al, bh, idesc, 1u);
+            }
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -295,6 +389,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
     // warp w: TMEM lanes (pairs) 32 (w % 4) .. + 31, columns [w/4 * N/2, + N/2)
     const int c = 32 * (warp & 3) + lane;
     const int dof = s_dst[c], fl = s_flg[c];
+    // FP16 split: the pair's source row and each matrix row were scaled by powers of two
+    const float psc = (F16 && s_src[c] >= 0) ? escale[s_src[c]] : 1.f;
+    const float* tsg = F16 ? tscale + tsoff[g] : nullptr;
     const int half = N >> 1;
     const int cbeg = (warp >> 2) * half;
     const bool mflip = ((fl & 1) != 0) != ((fl & 2) != 0);
@@ -319,8 +416,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
       for (int e = 0; e < 4; ++e) {
         const bool neg = ((fl & 1) && (m & 1)) != ((fl & 4) && ((n + m) & 1));
         qi[e] = (dof >= 0 && q < Po) ? (mflip ? n * n + n - m : q) : -1;
-        re[e] = neg ? -__uint_as_float(v[2 * e]) : __uint_as_float(v[2 * e]);
-        im[e] = neg ? -__uint_as_float(v[2 * e + 1]) : __uint_as_float(v[2 * e + 1]);
+        float sc = neg ? -1.f : 1.f;
+        if (F16 && q < Po) sc *= psc * tsg[2 * q];
+        re[e] = sc * __uint_as_float(v[2 * e]);
+        im[e] = sc * __uint_as_float(v[2 * e + 1]);
         ++q;
         if (++m > n) {
           ++n;
@@ -397,6 +496,41 @@ __global__ void k_prep(const float* __restrict__ src, int64_t base, int nbox, in
   *(float4*)(o + TC_KS) = lo;
 }
 
+// FP16 split: one warp per row (rhs r0 + rc, reflection f, box b); the row's
+// largest magnitude (reflections only permute and negate) picks the power-of-
+// two scale; per K stage of 32 the row holds [hi 32 | lo 32] halves (128
+// bytes, as a TF32 stage of 16), and escale[row] keeps the inverse scale.
+__global__ void k_prep16(const float* __restrict__ src, int64_t base, int nbox, int P, int nks, int r0, int nchunk,
+                         int64_t exp_stride, float* __restrict__ out, float* __restrict__ escale) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t per_rhs = (int64_t)8 * nbox;
+  if (row >= nchunk * per_rhs) return;
+  const int rc = (int)(row / per_rhs);
+  const int f = (int)((row % per_rhs) / nbox), b = (int)(row % nbox);
+  const float* sb = src + 2 * ((int64_t)(r0 + rc) * exp_stride + base + (int64_t)b * P);
+  float m = 0.f;
+  for (int kr = lane; kr < 2 * P; kr += 32) m = fmaxf(m, fabsf(sb[kr]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  float sc, iv;
+  f16_scale(m, &sc, &iv);
+  if (lane == 0) escale[row] = iv;
+  __half* o = (__half*)(out + row * (int64_t)(32 * nks));
+  for (int kr = lane; kr < 32 * nks; kr += 32) {
+    float v = 0.f;
+    if (kr < 2 * P) {
+      bool neg;
+      const int ki = reflect_index(kr >> 1, f, &neg);
+      v = sb[2 * ki + (kr & 1)] * sc;
+      if (neg) v = -v;
+    }
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    o[(kr >> 5) * 64 + (kr & 31)] = hi;
+    o[(kr >> 5) * 64 + 32 + (kr & 31)] = lo;
+  }
+}
+
 __global__ void k_prep_rows(int np, const int* __restrict__ src_off, const unsigned char* __restrict__ flags,
                             int64_t base, int P, int nbox, int* rows) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -406,20 +540,35 @@ __global__ void k_prep_rows(int np, const int* __restrict__ src_off, const unsig
 }
 
 // -------------------------------------------------------------------- host --
-static inline int prep_stride(int P) { return ((2 * P + TC_KS - 1) / TC_KS) * TC_KS; }
+
+// K per stage of the handle's translation form: 32 (FP16 split) or 16 (TF32)
+static inline int tc_kstage(const bem_handle* h) { return h->tc_fp16 ? 32 : TC_KS; }
+// floats per prepared source row: stages x 32 floats (hi and lo, 128 bytes)
+static inline int prep_row_floats(const bem_handle* h, int P) {
+  const int ks = tc_kstage(h);
+  return ((2 * P + ks - 1) / ks) * 2 * TC_KS;
+}
 
 int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
   if (op.ngroups == 0) return BEM_OK;
   op.src_level = src_level;
+  const int KSTG = tc_kstage(h);
   {
     LevelInfo& sl = h->lev[src_level];
     const int chunk = std::min(h->nrhs_max, TC_RHS_CHUNK);
-    int64_t need = (int64_t)chunk * 8 * sl.nbox * 2 * prep_stride(sl.P);
+    const int64_t rows = (int64_t)chunk * 8 * sl.nbox;
+    int64_t need = rows * prep_row_floats(h, sl.P);
     if (need > h->prep_len) {
       float* p;
       BEM_TRY(bem_alloc(h, &p, need));  // grows monotonically; older buffers stay in the handle's list
       h->prep = p;
       h->prep_len = need;
+    }
+    if (h->tc_fp16 && rows > h->prep_scale_len) {
+      float* p;
+      BEM_TRY(bem_alloc(h, &p, rows));
+      h->prep_scale = p;
+      h->prep_scale_len = rows;
     }
     BEM_TRY(bem_alloc(h, &op.d_prep_row, std::max(op.npairs, 1)));
     if (op.npairs > 0)
@@ -427,21 +576,40 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
                                                           sl.nbox, op.d_prep_row);
     BEM_CUDA(cudaGetLastError());
   }
-  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   std::vector<int64_t> off(op.ngroups);
+  std::vector<int> toff(op.ngroups);
   int64_t tot = 0;
+  int ttot = 0;
   for (int g = 0; g < op.ngroups; ++g) {
-    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
+    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + KSTG - 1) / KSTG;
     off[g] = tot;
     tot += (int64_t)nnt * nks * 2 * TC_NMAX * TC_KS;
+    toff[g] = ttot;
+    ttot += 2 * op.rows[g];
   }
   BEM_TRY(bem_alloc(h, &op.tcA, std::max<int64_t>(tot, 4)));
+  float* rsc = nullptr;
+  if (h->tc_fp16) {
+    BEM_TRY(bem_alloc(h, &op.tscale, std::max(ttot, 1)));
+    BEM_TRY(bem_alloc(h, &op.d_tsoff, op.ngroups));
+    BEM_CUDA(cudaMemcpyAsync(op.d_tsoff, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMallocAsync((void**)&rsc, std::max(ttot, 1) * sizeof(float), s));
+  }
   for (int g = 0; g < op.ngroups; ++g) {
-    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
-    k_tc_pack<<<nnt * nks, 256, 0, s>>>((const float*)op.mats_base + 2 * op.mat_off[g], op.rows[g], op.cols[g], nks,
-                                        nnt, op.tcA + off[g]);
+    int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX, nks = (2 * op.cols[g] + KSTG - 1) / KSTG;
+    const float* T = (const float*)op.mats_base + 2 * op.mat_off[g];
+    if (h->tc_fp16) {
+      k_tc_rowscale<<<(op.rows[g] + 7) / 8, 256, 0, s>>>(T, op.rows[g], op.cols[g], rsc + toff[g],
+                                                          op.tscale + toff[g]);
+      k_tc_pack16<<<nnt * nks, 256, 0, s>>>(T, op.rows[g], op.cols[g], nks, rsc + toff[g], op.tcA + off[g]);
+    } else {
+      k_tc_pack<<<nnt * nks, 256, 0, s>>>(T, op.rows[g], op.cols[g], nks, nnt, op.tcA + off[g]);
+    }
     BEM_CUDA(cudaGetLastError());
   }
+  if (rsc) BEM_CUDA(cudaFreeAsync(rsc, s));
   // K stages per job: TC_KSLICE.  When the operator has too few (pair tile,
   // row tile) jobs to give every SM two CTAs, a second job list with shorter
   // slices (down to 2 stages) lets the small translations (M2M, L2L, the
@@ -452,23 +620,25 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
   for (int g = 0; g < op.ngroups; ++g) {
     int np = op.pair_start[g + 1] - op.pair_start[g];
     base += (int64_t)((np + TC_M - 1) / TC_M) * ((2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX);
-    nks_max = std::max(nks_max, (2 * op.cols[g] + TC_KS - 1) / TC_KS);
+    nks_max = std::max(nks_max, (2 * op.cols[g] + KSTG - 1) / KSTG);
   }
   int nsm = 0;
   BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
   op.tc_want = 2 * (int64_t)std::max(nsm, 1);
   const int kmax = std::min(TC_KSLICE, std::max(2, h->tc_kslice_max));
   int ksplit = kmax;
+  // (FP16 stages hold twice the K of TF32 ones, so their shortest slice is one stage)
+  const int kmin = h->tc_fp16 ? 1 : 2;
   if (base > 0 && base * ((nks_max + kmax - 1) / kmax) < op.tc_want) {
     const int64_t slices = (op.tc_want + base - 1) / base;
-    ksplit = (int)std::max<int64_t>(2, std::min<int64_t>(kmax, (nks_max + slices - 1) / slices));
+    ksplit = (int)std::max<int64_t>(kmin, std::min<int64_t>(kmax, (nks_max + slices - 1) / slices));
   }
   auto make_jobs = [&](int kslice) {
     std::vector<int4> js;
     for (int g = 0; g < op.ngroups; ++g) {
       int np = op.pair_start[g + 1] - op.pair_start[g];
       int nnt = (2 * op.rows[g] + TC_NMAX - 1) / TC_NMAX;
-      int nks = (2 * op.cols[g] + TC_KS - 1) / TC_KS;
+      int nks = (2 * op.cols[g] + KSTG - 1) / KSTG;
       for (int p0 = 0; p0 < np; p0 += TC_M)
         for (int nt = 0; nt < nnt; ++nt)
           for (int sl = 0; sl * kslice < nks; ++sl)
@@ -499,24 +669,34 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
                        int* launches) {
   if (op.n_tc_jobs == 0) return BEM_OK;
   LevelInfo& sl = h->lev[op.src_level];
-  int R2 = prep_stride(sl.P);
+  const int row_floats = prep_row_floats(h, sl.P);
   const int chunk = std::min(h->nrhs_max, TC_RHS_CHUNK);
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     // up to `chunk` right-hand sides per launch share each matrix stage via L2
     const int nc = std::min(chunk, nrhs - r0);
-    const int64_t n = (int64_t)nc * 8 * sl.nbox * (R2 / 4);
-    k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r0, nc,
-                                                        h->exp_total, h->prep);
+    if (h->tc_fp16) {
+      const int64_t rows = (int64_t)nc * 8 * sl.nbox;
+      k_prep16<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
+          (const float*)src, sl.exp_base, sl.nbox, sl.P, row_floats / (2 * TC_KS), r0, nc, h->exp_total, h->prep,
+          h->prep_scale);
+    } else {
+      const int R2 = row_floats / 2;
+      const int64_t n = (int64_t)nc * 8 * sl.nbox * (R2 / 4);
+      k_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, sl.exp_base, sl.nbox, sl.P, R2, r0, nc,
+                                                          h->exp_total, h->prep);
+    }
     BEM_CUDA(cudaGetLastError());
     // one right-hand side and too few CTAs for the SMs: the job list with
     // shorter K slices (with 2-4 right-hand sides per launch the extra
     // slices' atomics cost more than the added CTAs give back)
     const bool split = nc == 1 && op.n_tc_jobs_split > 0;
-    k_grouped_tc<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, TC_SMEM, s>>>(
+    auto kern = h->tc_fp16 ? k_grouped_tc<true> : k_grouped_tc<false>;
+    kern<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, TC_SMEM, s>>>(
         split ? op.d_tc_jobs_split : op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
-        op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, R2, nc, 8 * sl.nbox, (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total,
-        h->mode == BEM_MODE_FMM_TF32 ? 1 : 3, split ? op.tc_kslice_split : op.tc_kslice, h->d_err,
-        h->tc_wait_limit, h->tc_hold_first_copy);
+        op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, row_floats, nc, 8 * sl.nbox,
+        (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total, h->mode == BEM_MODE_FMM_TF32 ? 1 : 3,
+        split ? op.tc_kslice_split : op.tc_kslice, h->d_err, h->tc_wait_limit, h->tc_hold_first_copy,
+        h->prep_scale, op.tscale, op.d_tsoff);
     BEM_CUDA(cudaGetLastError());
     *launches += 2;
   }

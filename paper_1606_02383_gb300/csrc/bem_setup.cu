@@ -673,15 +673,28 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
   // Adaptive trees: levels 0 and 1 are always split, and no box is split into
   // children narrower than 3 of its longest edges (quadrature points stay
   // close to their box, so expansions about the box centre converge one box
-  // away).  leaf_level = 0: the depth is chosen per level-2 region, the
+  // away).  leaf_level = -1: the depth is chosen per level-2 region, the
   // deepest level whose mean occupancy inside the region reaches leaf_target,
   // so leaves differ in level only between regions of different density and
-  // the W/X-lists stay short.  leaf_level = -1: each box of level >= 2 is
+  // the W/X-lists stay short.  leaf_level = -2: each box of level >= 2 is
   // split while it holds more than `split` elements.  If even level 2 is too
   // narrow for the longest edge, or the mesh fits one leaf, the tree is the
   // root alone and everything is near field.
-  const bool adaptive = leaf_level <= 0;
-  const bool regional = leaf_level == 0;
+  // leaf_level 0: the uniform level the whole mesh's mean occupancy picks
+  // (the deepest level whose mean occupancy reaches leaf_target and whose
+  // boxes are at least 3 longest edges wide; a level-1 leaf has no far field,
+  // so that case keeps the single box)
+  if (leaf_level == 0) {
+    int Lauto = 0;
+    for (int l = 0; l <= BEM_MAXLEV; ++l) {
+      double wl = h->root_w / (1 << l);
+      if ((double)nt / (double)cnt[l] >= (double)leaf_target && wl >= 3.0 * h->hmax_all) Lauto = l;
+    }
+    if (Lauto == 1) Lauto = 0;
+    leaf_level = std::max(Lauto, 0);
+  }
+  const bool adaptive = leaf_level < 0;
+  const bool regional = leaf_level == -1;
   const int split = 2 * std::max(leaf_target, 1);
   h->adaptive = adaptive ? (regional ? 1 : 2) : 0;
   // regional depth: distinct boxes per (level-2 region, level) from the sorted keys
@@ -715,7 +728,7 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
           region_depth[reg] = l;
     }
   }
-  int Lfix = std::min(std::max(leaf_level, 0), BEM_MAXLEV);
+  int Lfix = std::min(std::max(leaf_level, 0), BEM_MAXLEV);  // 0 here: the single root box
   bool single = false;
   if (adaptive && (h->root_w / 4.0 < 3.0 * h->hmax_all || nt <= split)) single = true;
 
@@ -790,7 +803,7 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
       if (!in) continue;
       bool leaf;
       if (!adaptive)
-        leaf = l >= Lfix;
+        leaf = l >= Lfix;  // (Lfix = 0: the root alone)
       else if (single)
         leaf = true;
       else if (l < 2)

@@ -105,9 +105,9 @@ def test_uneven_batch_with_per_body_options(cuda_ok):
     probs = inputs.batch_bodies(6, seed=3, n_min=2000, n_max=20000)
     sizes = [T.shape[0] for _, T, _ in probs]
     assert min(sizes) < 4000 and max(sizes) > 10000, sizes
-    opts = [{"leaf_level": 0, "leaf_target": 32}, {"leaf_level": -1, "leaf_target": 32},
+    opts = [{"leaf_level": -1, "leaf_target": 32}, {"leaf_level": -2, "leaf_target": 32},
             {"leaf_level": 0, "leaf_target": 48, "p2p_unit": 32}, {"leaf_level": 3, "tc_kslice": 8},
-            {"leaf_level": 0, "leaf_target": 24, "p2p_unit": 16}, {"leaf_level": 0, "leaf_target": 64}]
+            {"leaf_level": -1, "leaf_target": 24, "p2p_unit": 16}, {"leaf_level": 0, "leaf_target": 64}]
     batch = Batch(probs, p=0, eps=1e-5, mode="mixed", max_nrhs=2, options=opts)
     n = batch.n
     x = inputs.random_density(n, 2, seed=61)

@@ -70,26 +70,26 @@ def test_every_pair_counted_once(cuda_ok, sphere3_dense, mode, leaf):
     op.close()
 
 
-@pytest.mark.parametrize("mode,leaf,target", [("mixed", 2, 48), ("fp64", 2, 48), ("mixed", -1, 16), ("fp64", -1, 16),
-                                              ("mixed", 0, 16)])
+@pytest.mark.parametrize("mode,leaf,target", [("mixed", 2, 48), ("fp64", 2, 48), ("mixed", -2, 16), ("fp64", -2, 16),
+                                              ("mixed", -1, 16)])
 def test_every_pair_counted_once_two_bodies(cuda_ok, mode, leaf, target):
     """Two bodies of different size and element density in one tree: a unit
     sphere and a sphere of radius 0.3 at a distance, so that the boxes of the
     two differ in occupancy and in their neighbour structure.  With the
-    adaptive trees (leaf_level -1: split per box, 0: depth per region) the
+    adaptive trees (leaf_level -2: split per box, -1: depth per region) the
     leaves sit on several levels, so the near lists join leaves of different
     sizes and the W- and X-lists (M2P, P2L) carry part of the far field."""
-    V1, T1 = inputs.icosphere(3 if leaf < 2 else 2)
-    V2, T2 = inputs.icosphere(3 if leaf < 2 else 2, 0.3, (1.3, 0.4, -0.2))
+    V1, T1 = inputs.icosphere(3 if leaf < 0 else 2)
+    V2, T2 = inputs.icosphere(3 if leaf < 0 else 2, 0.3, (1.3, 0.4, -0.2))
     V, T = inputs.merge_meshes([(V1, T1), (V2, T2)])
     n = T.shape[0]
     S, D = oracle.assemble(V, T, 2.0)
     # p = 20 on the adaptive trees: their M2P and P2L converge more slowly
     op = Operator(V, T, 2.0, p=16 if leaf > 0 else 20, mode=mode, leaf_level=leaf, leaf_target=target,
                   max_nrhs=BATCH)
-    if leaf == -1:
+    if leaf == -2:
         assert op.info("w_pairs") > 0 and op.info("x_pairs") > 0
-    if leaf <= 0:
+    if leaf < 0:
         levels = {l for l in range(11) if op.info(200 + l) > 0}
         assert len(levels) >= 2, levels
     label = "two bodies %s leaf %d" % (mode, leaf)

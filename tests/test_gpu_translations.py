@@ -17,7 +17,7 @@ the regular 3-point rule over the sources each expansion stands for:
             whose leaf does not touch the target's leaf.
 
 The meshes: a uniform tree on a sphere, and an adaptive tree split per box
-(leaf_level = -1) on a unit sphere next to a finer sphere of radius 0.3, which
+(leaf_level = -2) on a unit sphere next to a finer sphere of radius 0.3, which
 has leaves on several levels and therefore W- and X-lists (M2P, P2L).
 """
 import ctypes
@@ -163,7 +163,7 @@ def two_spheres():
 # the orders used (p = 16 on the uniform tree, 20 on the adaptive one, whose
 # M2P and P2L converge more slowly than M2L between same-level boxes)
 CASES = [("uniform sphere", "mixed", 3, 2e-5), ("uniform sphere", "fp64", 3, 5e-6),
-         ("two spheres, split per box", "mixed", -1, 2e-5), ("two spheres, split per box", "fp64", -1, 5e-6)]
+         ("two spheres, split per box", "mixed", -2, 2e-5), ("two spheres, split per box", "fp64", -2, 5e-6)]
 
 
 @pytest.mark.parametrize("name,mode,leaf,tol", CASES)
