@@ -452,20 +452,34 @@ def run_ours(args, world, rank, local):
     # peak: measured BF16 x the nominal TF32/BF16 ratio (1.1 / 2.25); 3xTF32 runs
     # three products per algorithmic flop, so the algorithmic ceiling is a third
     m2l_ms, m2l_launches = stages["m2l"]
-    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
     m2l_achieved = info["m2l_flops"] / (m2l_ms / steps * 1e-3) / 1e12
+    from paper_1606_02383_gb300 import peaks as pk
+    probe_fp32 = pk.measure("fp32")
+    fp16_form = op.info("tc_kind") == 1
+    if fp16_form:
+        # FP16 split: kind::f16 runs at the BF16 rate; three products per algorithmic flop
+        tf32_peak = float(peaks.get("bf16_tflops", 1900.0))
+        probe_tc = pk.measure("fp16")
+        rule = "%s BF16 %.0f TFLOP/s (kind::f16 runs FP16 at the BF16 rate), / 3 for the FP16 split" % (
+            peak_src, tf32_peak)
+        probe_txt = "bem_peak_probe: tcgen05 FP16 MMAs, M=128 N=256 K=16, %.0f TFLOP/s, / 3"
+    else:
+        tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+        probe_tc = pk.measure("tf32")
+        rule = "%s BF16 %.0f TFLOP/s x 1.1/2.25 = TF32 %.0f, / 3 for 3xTF32" % (
+            peak_src, float(peaks.get("bf16_tflops", 1900.0)), tf32_peak)
+        probe_txt = "bem_peak_probe: tcgen05 TF32 MMAs, M=128 N=256 K=8, %.0f TFLOP/s, / 3"
     roof_m2l = {"bound": "tensor", "kernel": "k_grouped_tc (M2L, all levels, with k_prep)",
+                "form": "FP16 split" if fp16_form else "3xTF32",
                 "achieved": m2l_achieved, "peak": tf32_peak / 3.0, "unit": "TFLOP/s",
                 "frac": m2l_achieved / (tf32_peak / 3.0), "traffic": None,
                 "work_per_apply": "%.4g flops (8 P_l^2 per V-list pair)" % info["m2l_flops"],
-                "peak_source": "%s BF16 %.0f TFLOP/s x 1.1/2.25 = TF32 %.0f, / 3 for 3xTF32"
-                               % (peak_src, float(peaks.get("bf16_tflops", 1900.0)), tf32_peak)}
-    # the library's own probes of the FP32 and TF32 pipes, reported beside the
-    # rule-based peaks (derived FP32; measured BF16 x the nominal TF32 ratio)
-    from paper_1606_02383_gb300 import peaks as pk
-    probe_fp32, probe_tf32 = pk.measure("fp32"), pk.measure("tf32")
-    roof_m2l.update({"probe_peak": probe_tf32 / 3.0, "probe_frac": m2l_achieved / (probe_tf32 / 3.0),
-                     "probe": "bem_peak_probe: tcgen05 TF32 MMAs, M=128 N=256 K=8, %.0f TFLOP/s, / 3" % probe_tf32})
+                "peak_source": rule}
+    # the library's own probes of the FP32 and tensor pipes, reported beside the
+    # rule-based peaks (derived FP32; measured BF16 for the tensor pipe)
+    probe_tf32 = probe_tc
+    roof_m2l.update({"probe_peak": probe_tc / 3.0, "probe_frac": m2l_achieved / (probe_tc / 3.0),
+                     "probe": probe_txt % probe_tc})
     # the stricter of the two ceilings is the headline fraction of this stage
     roof_m2l["scaled_frac"] = roof_m2l["frac"]
     if probe_tf32 / 3.0 > roof_m2l["peak"]:

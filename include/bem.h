@@ -474,6 +474,7 @@ typedef enum {
   BEM_INFO_W_EVALS = 20,     /* (target, coefficient) products of the M2P work (one rhs) */
   BEM_INFO_X_EVALS = 21,     /* (source point, coefficient) products of the P2L work (one rhs) */
   BEM_INFO_EXP_TOTAL = 22,   /* expansion coefficients per rhs over all levels (the far-field buffers' length) */
+  BEM_INFO_TC_KIND = 23,     /* tensor-core translations: 0 none (FP64 or direct modes), 1 FP16 split, 2 3xTF32, 3 plain TF32 */
   BEM_INFO_ORDER_OF_LEVEL = 100, /* + level: expansion order of that level */
   BEM_INFO_LEAVES_OF_LEVEL = 200, /* + level: leaves on that level */
   BEM_INFO_BOXES_OF_LEVEL = 300,  /* + level: occupied boxes on that level (tree or not) */
@@ -573,7 +574,9 @@ int bem_set_wait_limit(bem_handle* h, long long clocks, int hold);
  *            thread, 8 blocks of 256 threads per SM);
  *            1 = dense TF32 through tcgen05.mma (M = 128, N = 256, K = 8,
  *            operands resident in shared memory, one TMEM accumulator per CTA,
- *            2 CTAs per SM).
+ *            2 CTAs per SM);
+ *            2 = dense FP16 through tcgen05.mma kind::f16 (K = 16, same shape and
+ *            residency), the rate of the FP16-split translations.
  *   iters  : iterations per thread (0) or MMAs per CTA (1), 1 .. 2^20.
  *   tflops : receives the rate of the second of two launches, in TFLOP/s
  *            (an FMA counts 2 flops).

@@ -39,7 +39,7 @@ INFO = {
     "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,
     "p_leaf": 7, "p_top": 8, "mode": 9, "device_bytes": 10, "p2m_bytes": 11, "launches_last_apply": 12,
     "m2m_flops": 13, "l2l_flops": 14, "adaptive": 15, "row_coeffs": 16, "w_pairs": 17, "x_pairs": 18,
-    "near_list": 19, "w_evals": 20, "x_evals": 21, "exp_total": 22,
+    "near_list": 19, "w_evals": 20, "x_evals": 21, "exp_total": 22, "tc_kind": 23,
 }
 STAGES = ("prologue", "p2p", "correction", "p2m", "m2m", "m2l", "l2l", "l2p", "epilogue")
 INFO_ORDER_OF_LEVEL = 100

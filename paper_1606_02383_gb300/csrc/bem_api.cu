@@ -437,6 +437,9 @@ int bem_info(bem_handle* h, int key, int64_t* value) {
     case BEM_INFO_W_EVALS: *value = h->w_evals; return BEM_OK;
     case BEM_INFO_X_EVALS: *value = h->x_evals; return BEM_OK;
     case BEM_INFO_EXP_TOTAL: *value = h->exp_total; return BEM_OK;
+    case BEM_INFO_TC_KIND:
+      *value = (!bem_is_fmm(h) || bem_is_fp64(h)) ? 0 : (h->mode == BEM_MODE_FMM_TF32 ? 3 : (h->tc_fp16 ? 1 : 2));
+      return BEM_OK;
     default:
       if (key >= BEM_INFO_ORDER_OF_LEVEL && key <= BEM_INFO_ORDER_OF_LEVEL + BEM_MAXLEV) {
         int l = key - BEM_INFO_ORDER_OF_LEVEL;

@@ -711,13 +711,18 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
 // Every CTA issues `iters` back-to-back M = 128, N = 256, K = 8 TF32 MMAs
 // from one thread into one TMEM accumulator, with both operands resident in
 // shared memory, then commits once and waits (bounded) for completion.
+template <bool F16>
 __global__ void __launch_bounds__(128, 1) k_peak_tc(int iters, int* err, float* sink) {
   __shared__ __align__(1024) unsigned char ops[TC_M * 8 * 4 + TC_NMAX * 8 * 4];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5;
-  for (int i = tid; i < (int)(sizeof(ops) / 4); i += blockDim.x) ((float*)ops)[i] = tf32_round(1.0f + 1e-3f * (i & 7));
+  if constexpr (F16) {
+    for (int i = tid; i < (int)(sizeof(ops) / 2); i += blockDim.x) ((__half*)ops)[i] = __float2half_rn(1.0f + 1e-3f * (i & 7));
+  } else {
+    for (int i = tid; i < (int)(sizeof(ops) / 4); i += blockDim.x) ((float*)ops)[i] = tf32_round(1.0f + 1e-3f * (i & 7));
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(TC_NMAX));
@@ -735,8 +740,13 @@ __global__ void __launch_bounds__(128, 1) k_peak_tc(int iters, int* err, float* 
   bool ok = true;
   if (tid == 0) {
     const uint64_t a = smem_desc(smem_u32(ops)), b = smem_desc(smem_u32(ops + TC_M * 8 * 4));
-    const uint32_t idesc = instr_desc(TC_NMAX);
-    for (int i = 0; i < iters; ++i) mma_tf32(tmem, a, b, idesc, i > 0 ? 1u : 0u);
+    const uint32_t idesc = F16 ? instr_desc_f16(TC_NMAX) : instr_desc(TC_NMAX);
+    for (int i = 0; i < iters; ++i) {
+      if constexpr (F16)
+        mma_f16(tmem, a, b, idesc, i > 0 ? 1u : 0u);
+      else
+        mma_tf32(tmem, a, b, idesc, i > 0 ? 1u : 0u);
+    }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar))
                  : "memory");
     ok = mbar_wait(smem_u32(&bar), 0);
@@ -785,13 +795,14 @@ __global__ void __launch_bounds__(256) k_peak_fp32(int iters, float* sink) {
 
 extern "C" int bem_peak_probe(int which, int iters, double* tflops, void* stream) {
   bem_set_error("");
-  if (!tflops || iters < 1 || iters > (1 << 20) || (which != 0 && which != 1))
-    return bem_fail(BEM_ERR_INVALID_ARG, "which must be 0 (FP32) or 1 (TF32), 1 <= iters <= 2^20, tflops non-NULL");
+  if (!tflops || iters < 1 || iters > (1 << 20) || which < 0 || which > 2)
+    return bem_fail(BEM_ERR_INVALID_ARG,
+                    "which must be 0 (FP32), 1 (TF32) or 2 (FP16), 1 <= iters <= 2^20, tflops non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, nsm = 0;
   BEM_CUDA(cudaGetDevice(&dev));
   BEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int blocks = which == 1 ? 2 * nsm : 8 * nsm, threads = which == 1 ? 128 : 256;
+  const int blocks = which >= 1 ? 2 * nsm : 8 * nsm, threads = which >= 1 ? 128 : 256;
   float* sink = nullptr;
   int* err = nullptr;
   BEM_CUDA(cudaMallocAsync((void**)&sink, sizeof(float) * blocks * threads, s));
@@ -807,7 +818,9 @@ extern "C" int bem_peak_probe(int which, int iters, double* tflops, void* stream
     for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up, the second is timed
       BEM_CUDA(cudaEventRecord(e0, s));
       if (which == 1)
-        k_peak_tc<<<blocks, threads, 0, s>>>(iters, err, sink);
+        k_peak_tc<false><<<blocks, threads, 0, s>>>(iters, err, sink);
+      else if (which == 2)
+        k_peak_tc<true><<<blocks, threads, 0, s>>>(iters, err, sink);
       else
         k_peak_fp32<<<blocks, threads, 0, s>>>(iters, sink);
       BEM_CUDA(cudaGetLastError());
@@ -826,8 +839,9 @@ extern "C" int bem_peak_probe(int which, int iters, double* tflops, void* stream
   cudaEventDestroy(e1);
   if (rc != BEM_OK) return rc;
   if (herr) return bem_fail(BEM_ERR_TIMEOUT, "a bounded wait of the tensor-core probe expired");
-  const double flops = which == 1 ? (double)blocks * iters * 2.0 * TC_M * TC_NMAX * 8
-                                  : (double)blocks * threads * iters * 8 * 4;
+  const double flops = which == 1   ? (double)blocks * iters * 2.0 * TC_M * TC_NMAX * 8
+                      : which == 2 ? (double)blocks * iters * 2.0 * TC_M * TC_NMAX * 16
+                                   : (double)blocks * threads * iters * 8 * 4;
   *tflops = flops / (ms * 1e-3) / 1e12;
   return BEM_OK;
 }

@@ -2,7 +2,8 @@
 
 FP32: 152 SMs x 128 lanes x 2 flops x the SM clock (at most about 2.1 GHz)
 bounds the f32x2 FMA rate near 81 TFLOP/s.  TF32: the dense tensor rate is
-about half the BF16 rate (nominal 2.25 PFLOP/s BF16, 1.1 TF32).  Each rate
+about half the BF16 rate (nominal 2.25 PFLOP/s BF16, 1.1 TF32); FP16 runs at
+the BF16 rate, so at most 2.25 PFLOP/s and above the TF32 rate.  Each rate
 must come out positive and below those ceilings, and above a floor that a
 mis-timed or dropped kernel would miss."""
 import pytest
@@ -12,11 +13,13 @@ from paper_1606_02383_gb300 import _lib, peaks
 pytestmark = pytest.mark.gpu
 
 
-def test_fp32_and_tf32_rates_in_range(cuda_ok):
+def test_fp32_tf32_and_fp16_rates_in_range(cuda_ok):
     fp32 = peaks.measure("fp32")
     tf32 = peaks.measure("tf32")
+    fp16 = peaks.measure("fp16")
     assert 30.0 < fp32 < 90.0, fp32
     assert 300.0 < tf32 < 1300.0, tf32
+    assert tf32 < fp16 < 2400.0, (tf32, fp16)
 
 
 def test_probe_rejects_bad_arguments(cuda_ok):
