@@ -238,21 +238,36 @@ int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const void* x, c
  * within 2 h_j of element j's centroid, R_1 within 4 h_j, R_0 beyond; no
  * free term and no self term).
  *   x, y     : densities [nrhs][N] (device, dtype), either may be NULL.
- *   points   : [npoints][3] FP64 coordinates (device).  They must not lie on
- *              the surface.  Consecutive points should be close to each other
- *              (a lattice in its natural order, or points sorted along a
- *              curve): each block of 128 points shares one FP32 origin.
- *   out      : [nrhs][npoints] complex (device, dtype); with BEM_EVAL_GRADIENT
- *              [nrhs][npoints][3]: grad u(p), the gradient with respect to
- *              the field point (the same rules applied to grad G and
- *              grad dG/dn_y).
- *   flags    : 0 or BEM_EVAL_GRADIENT.
- * Cost: a direct sum over all elements for every point (O(npoints N)), in the
- * handle's precision: FP32 sums with FP64 between tiles in the mixed modes,
- * FP64 in the FP64 modes; pairs within 4 h_j take the refined rule from the
- * FP64 geometry.  Stream-ordered; no allocation, no host synchronisation.
+ *   points   : [npoints][3] FP64 coordinates (device), anywhere off the
+ *              surface (inside or outside the tree's root cube).
+ *   out      : [nrhs][npoints][ncomp] complex (device, dtype): ncomp = 1, u(p)
+ *              (flags 0); 3, grad u(p) (BEM_EVAL_GRADIENT); 4, u(p) and
+ *              grad u(p) (BEM_EVAL_VALUE_GRADIENT).  The gradient is with
+ *              respect to the field point (the same rules applied to grad G
+ *              and grad dG/dn_y).
+ *   flags    : at most one of BEM_EVAL_GRADIENT, BEM_EVAL_VALUE_GRADIENT;
+ *              BEM_EVAL_DIRECT takes the direct sum on an FMM handle.
+ * Cost, FMM handles (the default there): the upward pass (P2M, M2M) of the
+ * densities, then for every point a walk of the octree from level 2: a box
+ * that does not touch the point's box on its own level, and lies at least
+ * 4 h_max(box) from the point's finest-level box, is taken through its
+ * multipole (M2P, the handle's orders); a leaf that does is summed element by
+ * element with the rules above; other boxes are opened.  About
+ * O(npoints (189 P log N + near elements)).  Allocates its temporaries
+ * (sorted points, FP64 partial sums: 16 ncomp nrhs npoints bytes and 36
+ * npoints more) stream-ordered and frees them before it returns.
+ * Cost, direct handles or BEM_EVAL_DIRECT: a direct sum over all elements for
+ * every point (O(npoints N)); each block of 128 consecutive points shares one
+ * FP32 origin, so consecutive points should be close to each other (a lattice
+ * in its natural order).  No allocation.
+ * Precision: the handle's (FP32 sums with FP64 between tiles and stages in
+ * the mixed modes, FP64 in the FP64 modes); pairs within 4 h_j take the
+ * refined rule from the FP64 geometry.  Stream-ordered; no host
+ * synchronisation.
  */
 #define BEM_EVAL_GRADIENT 1
+#define BEM_EVAL_VALUE_GRADIENT 2
+#define BEM_EVAL_DIRECT 4
 int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
                     int64_t npoints, void* out, int flags, void* stream);
 
@@ -293,6 +308,53 @@ int bem_point_source_field(int nrhs, int nsrc, const double* src, const double* 
  */
 int bem_topological_derivative(int64_t npoints, double c1, double c2, const double* state, const double* adjoint,
                                double* T, void* stream);
+
+/*
+ * bem_state_adjoint -- the adjoint chain of Section 2.2 for the rigid body and
+ * the cost f = 1/2 sum_m |p(x_m)|^2 over observation points, in one call:
+ *   1. the state solve (1/2 I - D) p = b (GMRES, as bem_gmres_solve);
+ *   2. the pressure at the observers, p(x_m) = p_inc(x_m) + (D p)(x_m) (the
+ *      representation formula, bem_eval_points);
+ *   3. the adjoint weights conj(p(x_m)) and the adjoint right-hand side
+ *      sum_m conj(p(x_m)) G(c_i - x_m) (bem_point_sources);
+ *   4. the adjoint solve with the same operator and settings.
+ *   b            : [N] state right-hand side (device, dtype).
+ *   observers    : [nobs][3] FP64 (device), off the surface.
+ *   incident_obs : complex128 [nobs] (device), p_inc at the observers.
+ *   tol, max_iter, restart, flags : as bem_gmres_solve (without
+ *                  BEM_GMRES_USE_X0: both solves start from zero).
+ *   p, p_adj     : [N] (device, dtype) out: the state and adjoint densities.
+ *   p_obs        : complex128 [nobs] (device) out: p(x_m).
+ *   weights      : complex128 [nobs] (device) out: conj(p(x_m)).
+ *   iters, relres: [2] (host) out: per solve, as bem_gmres_solve.
+ * Returns the first failing step's status (BEM_ERR_NOT_CONVERGED from either
+ * solve, with the outputs of the steps done so far).  Synchronises `stream`
+ * as the solves do; allocates (N + nobs) complex values stream-ordered.
+ */
+int bem_state_adjoint(bem_handle* h, int dtype, const void* b, int nobs, const double* observers,
+                      const double* incident_obs, double tol, int max_iter, int restart, int flags, void* p,
+                      double* p_obs, double* weights, void* p_adj, int* iters, double* relres, void* stream);
+
+/*
+ * bem_topological_field -- the topological derivative T (Section 2.5) at
+ * field points from a bem_state_adjoint result, in one call:
+ *   p  = p_inc + D p_surf            (state field and gradient, bem_eval_points)
+ *   pa = phi + D pa_surf             (adjoint field: phi the point sources at
+ *                                     the observers with the adjoint weights,
+ *                                     bem_point_source_field)
+ *   T  = Re[c1 grad p . grad pa - c2 p pa]   (bem_topological_derivative).
+ *   p, p_adj   : [N] (device, dtype): state and adjoint densities.
+ *   observers, weights : [nobs][3] FP64 and complex128 [nobs] (device).
+ *   points     : [npoints][3] FP64 (device), in the fluid, off the surface.
+ *   incident   : complex128 [npoints][4] (device): p_inc and its gradient.
+ *   c1, c2     : as bem_topological_derivative.
+ *   T          : FP64 [npoints] (device) out.
+ * Allocates 4 npoints complex values in dtype and 2 x 4 npoints complex128
+ * stream-ordered.  Stream-ordered; no host synchronisation.
+ */
+int bem_topological_field(bem_handle* h, int dtype, const void* p, const void* p_adj, int nobs,
+                          const double* observers, const double* weights, int64_t npoints, const double* points,
+                          const double* incident, double c1, double c2, double* T, void* stream);
 
 /*
  * bem_isosurface -- the boundary {phi = t} of the level-set region {phi > t}

@@ -34,6 +34,8 @@ BEM_GMRES_USE_X0 = 1
 BEM_GMRES_HOST_LOOP = 2
 BEM_GMRES_GRAPH_ONLY = 4
 BEM_EVAL_GRADIENT = 1
+BEM_EVAL_VALUE_GRADIENT = 2
+BEM_EVAL_DIRECT = 4
 
 INFO = {
     "n": 0, "leaf_level": 1, "n_leaves": 2, "p2p_pairs": 3, "corr_nnz": 4, "m2l_pairs": 5, "m2l_flops": 6,
@@ -53,7 +55,7 @@ EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gm
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
            "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field",
-           "bem_setup_batch_each")
+           "bem_setup_batch_each", "bem_state_adjoint", "bem_topological_field")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -126,12 +128,17 @@ def load(path: str | None = None):
     lib.bem_sorted_order.argtypes = [vp, vp]
     lib.bem_far_field.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]
     lib.bem_set_wait_limit.argtypes = [vp, ctypes.c_longlong, i]
+    lib.bem_state_adjoint.argtypes = [vp, i, vp, i, vp, vp, ctypes.c_double, i, i, i, vp, vp, vp, vp,
+                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
+    lib.bem_topological_field.argtypes = [vp, i, vp, vp, i, vp, vp, i64, vp, vp, ctypes.c_double, ctypes.c_double,
+                                          vp, vp]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
               "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
-              "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field", "bem_setup_batch_each"):
+              "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field", "bem_setup_batch_each",
+              "bem_state_adjoint", "bem_topological_field"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

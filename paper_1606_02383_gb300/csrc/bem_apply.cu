@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "bem_common.cuh"
+#include "bem_tree_walk.cuh"
 #include "bem_f32x2.cuh"
 #include "bem_rules.cuh"
 
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points(int64_t nt, int64_t 
                                                             const double* __restrict__ hmax,
                                                             const double* __restrict__ wgt,
                                                             const typename V4of<R>::T* __restrict__ dens,
-                                                            Rout* __restrict__ out) {
+                                                            int nc, int c0, Rout* __restrict__ out) {
   typedef typename V4of<R>::T V4;
   __shared__ V4 s_q[EV_THREADS][3];  // quadrature points relative to the origin, normal in .w
   __shared__ V4 s_c[EV_THREADS];     // centroid relative to the origin, (4 h)^2 in .w
@@ -502,8 +503,8 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points(int64_t nt, int64_t 
     sim += (double)aim;
   }
   if (live) {
-    out[2 * ((int64_t)r * np + p)] = (Rout)sre;
-    out[2 * ((int64_t)r * np + p) + 1] = (Rout)sim;
+    out[2 * (((int64_t)r * np + p) * nc + c0)] = (Rout)sre;
+    out[2 * (((int64_t)r * np + p) * nc + c0) + 1] = (Rout)sim;
   }
 }
 
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points_grad(int64_t nt, int
                                                                  const double* __restrict__ area,
                                                                  const double* __restrict__ hmax,
                                                                  const typename V4of<R>::T* __restrict__ dens,
-                                                                 Rout* __restrict__ out) {
+                                                                 int nc, int c0, Rout* __restrict__ out) {
   typedef typename V4of<R>::T V4;
   __shared__ V4 s_q[EV_THREADS][3];
   __shared__ V4 s_c[EV_THREADS];
@@ -665,7 +666,157 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points_grad(int64_t nt, int
     for (int c = 0; c < 6; ++c) acc[c] += (double)g[c];
   }
   if (live)
-    for (int c = 0; c < 6; ++c) out[6 * ((int64_t)r * np + p) + c] = (Rout)acc[c];
+    for (int c = 0; c < 6; ++c) out[2 * (((int64_t)r * np + p) * nc + c0) + c] = (Rout)acc[c];
+}
+
+// ------------------------------------------- near leaves at field points --
+// One thread per field point (in the walk's order): the elements of every
+// near leaf of the point's walk (bem_tree_walk.cuh), each with the rule its
+// distance calls for, as in k_eval_points; then the far part from acc is
+// added and the point's components are written in the caller's order.
+// The stored P2P coordinates are relative to the element's leaf centre, so
+// one FP64 difference per leaf (centre - x) places them relative to x.
+template <typename R, typename Rout, int MODE, int NR>
+__global__ void __launch_bounds__(128) k_evf_near(int64_t np, int r0, int64_t nt, WalkTree wt, double k,
+                                                  const double* __restrict__ pts, const int* __restrict__ tcs,
+                                                  const int* __restrict__ perm, const typename V4of<R>::T* __restrict__ tgt,
+                                                  const typename V4of<R>::T* __restrict__ src,
+                                                  const typename V4of<R>::T* __restrict__ dens,
+                                                  const double* __restrict__ cent, const double* __restrict__ qpt,
+                                                  const double* __restrict__ nrm, const double* __restrict__ area,
+                                                  const double* __restrict__ hmax, const double* __restrict__ wgt,
+                                                  const double* __restrict__ acc, Rout* __restrict__ out) {
+  typedef typename V4of<R>::T V4;
+  constexpr bool VAL = MODE != 1, GRAD = MODE != 0;
+  constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+  const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+  const R kr = (R)k;
+  R are[NR], aim[NR], g[NR][6];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    are[q] = aim[q] = 0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g[q][c] = 0;
+  }
+  tree_walk(wt, t, [&](int kind, int l, int b) {
+    if (kind != 1) return;
+    const double* c = wt.lv[l].centre + 3 * b;
+    const R sx = (R)(c[0] - X[0]), sy = (R)(c[1] - X[1]), sz = (R)(c[2] - X[2]);
+    const int e1 = wt.lv[l].end[b];
+    for (int j = wt.lv[l].start[b]; j < e1; ++j) {
+      const V4 tc = tgt[j];
+      const R cx = tc.x + sx, cy = tc.y + sy, cz = tc.z + sz;
+      const R h4 = (R)(4.0 * hmax[j]);
+      if (cx * cx + cy * cy + cz * cz < h4 * h4) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
+          if (VAL) eval_near<R>(X, j, k, cent, qpt, nrm, area, hmax, wgt, dd, are[q], aim[q]);
+          if (GRAD) grad_near<R>(X, j, k, cent, qpt, nrm, area, hmax, dd, g[q]);
+        }
+        continue;
+      }
+      const V4 q0 = src[3 * (int64_t)j], q1 = src[3 * (int64_t)j + 1], q2 = src[3 * (int64_t)j + 2];
+      const R nx = q0.w, ny = q1.w, nz = q2.w;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
+        if (VAL) {
+          p2p_eval(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+          p2p_eval(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+          p2p_eval(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+        }
+        if (GRAD) {
+          grad_eval<R>(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+          grad_eval<R>(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+          grad_eval<R>(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+        }
+      }
+    }
+  });
+  const int64_t o = perm[i];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const double* a = acc + 2 * (((int64_t)(r0 + q) * np + i) * NC);
+    Rout* w = out + 2 * (((int64_t)(r0 + q) * np + o) * NC);
+    int c0 = 0;
+    if (VAL) {
+      w[0] = (Rout)(a[0] + (double)are[q]);
+      w[1] = (Rout)(a[1] + (double)aim[q]);
+      c0 = 1;
+    }
+    if (GRAD)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) w[2 * c0 + c] = (Rout)(a[2 * c0 + c] + (double)g[q][c]);
+  }
+}
+
+template <typename R, typename Rout, int MODE>
+static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
+                         const int* perm, const double* acc, void* out, cudaStream_t s) {
+  typedef typename V4of<R>::T V4;
+  const V4* tgt = (const V4*)(sizeof(R) == 4 ? (const void*)h->tgt32 : (const void*)h->tgt64);
+  const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
+  const unsigned g = nblk(np, 128);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int rem = nrhs - r0;
+#define EVF_NEAR(NRV)                                                                                          \
+  k_evf_near<R, Rout, MODE, NRV><<<g, 128, 0, s>>>(np, r0, h->nt, wt, h->k, pts, tcs, perm, tgt, src,          \
+                                                   (const V4*)h->dens, h->cent, h->qpt, h->nrm, h->area, h->hmax, \
+                                                   h->wgt, acc, (Rout*)out);                                   \
+  r0 += NRV;
+    if (rem >= 4) {
+      EVF_NEAR(4)
+    } else if (rem >= 2) {
+      EVF_NEAR(2)
+    } else {
+      EVF_NEAR(1)
+    }
+#undef EVF_NEAR
+    BEM_CUDA(cudaGetLastError());
+  }
+  return BEM_OK;
+}
+
+template <typename R, typename Rout>
+static int evf_near_mode(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                         const int* tcs, const int* perm, const double* acc, void* out, cudaStream_t s) {
+  if (mode == 0) return evf_near_impl<R, Rout, 0>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
+  if (mode == 1) return evf_near_impl<R, Rout, 1>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
+  return evf_near_impl<R, Rout, 2>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
+}
+
+int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                 const int* tcs, const int* perm, const double* acc, int dtype, void* out, cudaStream_t s) {
+  if (bem_is_fp64(h))
+    return dtype == BEM_C128 ? evf_near_mode<double, double>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s)
+                             : evf_near_mode<double, float>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s);
+  return dtype == BEM_C128 ? evf_near_mode<float, double>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s)
+                           : evf_near_mode<float, float>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s);
+}
+
+// the direct sum over all elements (mode 0: u, 1: grad u, 2: both)
+template <typename R, typename Rout>
+static int eval_direct(bem_handle* h, int nrhs, int mode, const double* points, int64_t npoints, void* out,
+                       cudaStream_t s) {
+  typedef typename V4of<R>::T V4;
+  const dim3 grid((unsigned)((npoints + EV_THREADS - 1) / EV_THREADS), nrhs);
+  const int nc = mode == 0 ? 1 : (mode == 1 ? 3 : 4);
+  if (mode != 1) {
+    k_eval_points<R, Rout><<<grid, EV_THREADS, 0, s>>>(h->nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area,
+                                                       h->hmax, h->wgt, (const V4*)h->dens, nc, 0, (Rout*)out);
+    BEM_CUDA(cudaGetLastError());
+  }
+  if (mode != 0) {
+    k_eval_points_grad<R, Rout><<<grid, EV_THREADS, 0, s>>>(h->nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
+                                                            h->area, h->hmax, (const V4*)h->dens, nc, mode == 2 ? 1 : 0,
+                                                            (Rout*)out);
+    BEM_CUDA(cudaGetLastError());
+  }
+  return BEM_OK;
 }
 
 extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x, const void* y,
@@ -676,53 +827,22 @@ extern "C" int bem_eval_points(bem_handle* h, int nrhs, int dtype, const void* x
   if (dtype != BEM_C64 && dtype != BEM_C128) return bem_fail(BEM_ERR_INVALID_ARG, "dtype must be BEM_C64 or BEM_C128");
   if (!x && !y) return bem_fail(BEM_ERR_INVALID_ARG, "x and y are both NULL");
   if (!points || !out || npoints < 1) return bem_fail(BEM_ERR_INVALID_ARG, "points and out required, npoints >= 1");
-  if (flags & ~BEM_EVAL_GRADIENT) return bem_fail(BEM_ERR_INVALID_ARG, "flags: 0 or BEM_EVAL_GRADIENT");
+  if (flags & ~(BEM_EVAL_GRADIENT | BEM_EVAL_VALUE_GRADIENT | BEM_EVAL_DIRECT))
+    return bem_fail(BEM_ERR_INVALID_ARG, "flags: BEM_EVAL_GRADIENT or BEM_EVAL_VALUE_GRADIENT, and BEM_EVAL_DIRECT");
+  if ((flags & BEM_EVAL_GRADIENT) && (flags & BEM_EVAL_VALUE_GRADIENT))
+    return bem_fail(BEM_ERR_INVALID_ARG, "BEM_EVAL_GRADIENT and BEM_EVAL_VALUE_GRADIENT exclude each other");
   if ((int64_t)(npoints + EV_THREADS - 1) / EV_THREADS > 0x7fffffffLL)
     return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
+  const int mode = (flags & BEM_EVAL_VALUE_GRADIENT) ? 2 : ((flags & BEM_EVAL_GRADIENT) ? 1 : 0);
   cudaStream_t s = (cudaStream_t)stream;
+  if (bem_is_fmm(h) && h->L >= 2 && !(flags & BEM_EVAL_DIRECT))
+    return bem_eval_fmm(h, nrhs, dtype, x, y, points, npoints, out, mode, s);
   BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
-  const dim3 grid((unsigned)((npoints + EV_THREADS - 1) / EV_THREADS), nrhs);
-  const int64_t nt = h->nt;
-  if (flags & BEM_EVAL_GRADIENT) {
-    if (bem_is_fp64(h)) {
-      if (dtype == BEM_C128)
-        k_eval_points_grad<double, double><<<grid, EV_THREADS, 0, s>>>(
-            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const double4*)h->dens, (double*)out);
-      else
-        k_eval_points_grad<double, float><<<grid, EV_THREADS, 0, s>>>(
-            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const double4*)h->dens, (float*)out);
-    } else {
-      if (dtype == BEM_C128)
-        k_eval_points_grad<float, double><<<grid, EV_THREADS, 0, s>>>(
-            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const float4*)h->dens, (double*)out);
-      else
-        k_eval_points_grad<float, float><<<grid, EV_THREADS, 0, s>>>(
-            nt, npoints, h->k, points, h->cent, h->qpt, h->nrm, h->area, h->hmax, (const float4*)h->dens, (float*)out);
-    }
-    BEM_CUDA(cudaGetLastError());
-    return BEM_OK;
-  }
-  if (bem_is_fp64(h)) {
-    if (dtype == BEM_C128)
-      k_eval_points<double, double><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
-                                                                h->area, h->hmax, h->wgt, (const double4*)h->dens,
-                                                                (double*)out);
-    else
-      k_eval_points<double, float><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
-                                                               h->area, h->hmax, h->wgt, (const double4*)h->dens,
-                                                               (float*)out);
-  } else {
-    if (dtype == BEM_C128)
-      k_eval_points<float, double><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
-                                                               h->area, h->hmax, h->wgt, (const float4*)h->dens,
-                                                               (double*)out);
-    else
-      k_eval_points<float, float><<<grid, EV_THREADS, 0, s>>>(nt, npoints, h->k, points, h->cent, h->qpt, h->nrm,
-                                                              h->area, h->hmax, h->wgt, (const float4*)h->dens,
-                                                              (float*)out);
-  }
-  BEM_CUDA(cudaGetLastError());
-  return BEM_OK;
+  if (bem_is_fp64(h))
+    return dtype == BEM_C128 ? eval_direct<double, double>(h, nrhs, mode, points, npoints, out, s)
+                             : eval_direct<double, float>(h, nrhs, mode, points, npoints, out, s);
+  return dtype == BEM_C128 ? eval_direct<float, double>(h, nrhs, mode, points, npoints, out, s)
+                           : eval_direct<float, float>(h, nrhs, mode, points, npoints, out, s);
 }
 
 // ----------------------------------------------------------- point sources --
@@ -1247,6 +1367,34 @@ static int by_rhs_chunks(int nrhs, F&& f) {
   return (full > 0) + (rem > 0);
 }
 
+// P2M of every leaf level: h->dens into h->Mexp (which the caller zeroed)
+template <typename R>
+static int p2m_impl(bem_handle* h, int nrhs, cudaStream_t s, int* launches) {
+  const int64_t nt = h->nt;
+  const int L = h->L;
+  const typename V4of<R>::T* dens = (const typename V4of<R>::T*)h->dens;
+  int nl = 0;
+  for (int l = 2; l <= L; ++l) {
+    LevelInfo& lf = h->lev[l];
+    if (lf.nleaf == 0) continue;
+    if constexpr (sizeof(R) == 4) {
+      nl += by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+        k_p2m_v<decltype(nr)::value><<<dim3(lf.nleaf, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
+            lf.nleaf, lf.leafbox, nt, r0, lf.P, lf.start, lf.end, h->row_off, (const float*)h->p2m_rows,
+            (const float4*)dens, lf.exp_base, h->exp_total, (float*)h->Mexp);
+      });
+    } else {
+      nl += 1;
+      k_p2m<R><<<dim3(lf.nleaf, nrhs), 128, 0, s>>>(lf.nleaf, lf.leafbox, nt, lf.P, lf.start, lf.end, h->row_off,
+                                                    (const R*)h->p2m_rows, dens, lf.exp_base, h->exp_total,
+                                                    (R*)h->Mexp);
+    }
+    BEM_CUDA(cudaGetLastError());
+  }
+  *launches += nl;
+  return BEM_OK;
+}
+
 template <typename R>
 static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   typedef typename V4of<R>::T V4;
@@ -1299,23 +1447,7 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
     BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, esz * h->exp_total * nrhs, s));
     BEM_CUDA(cudaMemsetAsync(h->Lexp, 0, esz * h->exp_total * nrhs, s));
     nl = 0;
-    for (int l = 2; l <= L; ++l) {
-      LevelInfo& lf = h->lev[l];
-      if (lf.nleaf == 0) continue;
-      if constexpr (sizeof(R) == 4) {
-        nl += by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-          k_p2m_v<decltype(nr)::value><<<dim3(lf.nleaf, nchunk), ((lf.P + 1) / 2 + 31) / 32 * 32, 0, s>>>(
-              lf.nleaf, lf.leafbox, nt, r0, lf.P, lf.start, lf.end, h->row_off, (const float*)h->p2m_rows,
-              (const float4*)dens, lf.exp_base, h->exp_total, (float*)h->Mexp);
-        });
-      } else {
-        nl += 1;
-        k_p2m<R><<<dim3(lf.nleaf, nrhs), 128, 0, s>>>(lf.nleaf, lf.leafbox, nt, lf.P, lf.start, lf.end, h->row_off,
-                                                      (const R*)h->p2m_rows, dens, lf.exp_base, h->exp_total,
-                                                      (R*)h->Mexp);
-      }
-      BEM_CUDA(cudaGetLastError());
-    }
+    BEM_TRY(p2m_impl<R>(h, nrhs, s, &nl));
     bem_prof_end(h, pr, 3, nl, s);
     nl = 0;
     pr = bem_prof_begin(h, s);
@@ -1372,6 +1504,20 @@ int bem_run_grouped(bem_handle* h, GroupedOp& op, const void* src, void* dst, in
                     int* launches) {
   if (bem_is_fp64(h)) return run_grouped<double>(h, op, src, dst, nrhs, s, launches);
   return run_grouped<float>(h, op, src, dst, nrhs, s, launches);
+}
+
+template <typename R>
+static int upward_impl(bem_handle* h, int nrhs, cudaStream_t s) {
+  BEM_CUDA(cudaMemsetAsync(h->Mexp, 0, 2 * sizeof(R) * h->exp_total * nrhs, s));
+  int nl = 0;
+  BEM_TRY(p2m_impl<R>(h, nrhs, s, &nl));
+  for (int l = h->L - 1; l >= 2; --l) BEM_TRY(run_grouped<R>(h, h->m2m[l], h->Mexp, h->Mexp, nrhs, s, &nl));
+  return BEM_OK;
+}
+
+int bem_run_upward(bem_handle* h, int nrhs, cudaStream_t s) {
+  if (bem_is_fp64(h)) return upward_impl<double>(h, nrhs, s);
+  return upward_impl<float>(h, nrhs, s);
 }
 
 int bem_apply_sorted(bem_handle* h, int nrhs, cudaStream_t s) {

@@ -173,6 +173,7 @@ struct LevelInfo {
   int nleaf = 0;                      // leaves on this level
   int* leafbox = nullptr;             // [nleaf] box index of every leaf of this level
   int leaf_g0 = 0;                    // global index of this level's first leaf
+  float* gap2 = nullptr;              // [nbox] (4 h_max(box) / w_L)^2, the off-surface walk's far test
 };
 
 // per-level orders and expansion offsets, passed by value to kernels that
@@ -378,6 +379,20 @@ int bem_run_m2p(bem_handle* h, int nrhs, const void* M, double* zfar, cudaStream
 int bem_run_p2l(bem_handle* h, int nrhs, const void* dens, void* Lexp, cudaStream_t s, int* launches);
 int bem_run_m2p_t(bem_handle* h, int nrhs, const void* dens, void* Mu, cudaStream_t s, int* launches);
 int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStream_t s, int* launches);
+// off-surface evaluation through the tree (bem_eval_fmm.cu): the upward pass
+// alone (P2M, M2M of h->dens into h->Mexp), then per point the far boxes'
+// multipoles (bem_wx.cu) and the near leaves' elements (bem_apply.cu).
+// mode: 0 value, 1 gradient, 2 value and gradient; acc is FP64 complex
+// [nrhs][np][ncomp] in the walk's point order; the near pass adds acc and
+// writes out[r][perm[i]][c] in the caller's dtype.
+struct WalkTree;
+int bem_run_upward(bem_handle* h, int nrhs, cudaStream_t s);
+int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                const int* tcs, double* acc, cudaStream_t s);
+int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                 const int* tcs, const int* perm, const double* acc, int dtype, void* out, cudaStream_t s);
+int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
+                 int64_t np, void* out, int mode, cudaStream_t s);
 int bem_build_correction(bem_handle* h, cudaStream_t s);
 int bem_build_far_field(bem_handle* h, cudaStream_t s);
 int bem_apply_sorted(bem_handle* h, int nrhs, cudaStream_t s);  // dens -> zn, zfar

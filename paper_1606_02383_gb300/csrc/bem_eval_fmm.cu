@@ -1,0 +1,120 @@
+// bem_eval_fmm.cu -- the field (and its gradient) at points off the surface
+// through the FMM (Section 2.3's tree evaluating the representation formula
+// at field points, as the topological derivative of Section 2.5 needs on a
+// lattice):
+//   1. prologue: the weighted densities in tree order;
+//   2. upward pass: P2M of every leaf, M2M up to level 2;
+//   3. the points are sorted along a Morton curve of their level-L boxes
+//      (extended beyond the root cube), so that the threads of a warp walk
+//      nearly the same boxes;
+//   4. far pass: per point, the multipole of every far box of its walk;
+//   5. near pass: per point, the elements of every near leaf of its walk,
+//      plus the far part, written in the caller's point order.
+// Temporary arrays are stream-ordered allocations freed at the end of the call.
+#include <cub/cub.cuh>
+
+#include "bem_common.cuh"
+#include "bem_tree_walk.cuh"
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+WalkTree bem_walk_tree(const bem_handle* h) {
+  WalkTree wt;
+  wt.L = h->L;
+  for (int d = 0; d < 3; ++d) wt.lo[d] = h->root_c[d] - 0.5 * h->root_w;
+  wt.wL = h->root_w / (double)(1 << h->L);
+  for (int l = 0; l <= h->L; ++l) {
+    const LevelInfo& lv = h->lev[l];
+    WalkLevel& w = wt.lv[l];
+    w.coord = lv.coord;
+    w.internal = lv.internal;
+    w.child0 = lv.child0;
+    w.nchild = lv.nchild;
+    w.gap2 = lv.gap2;
+    w.centre = lv.centre;
+    w.start = lv.start;
+    w.end = lv.end;
+    w.nbox = lv.nbox;
+  }
+  return wt;
+}
+
+// spread the low 21 bits of v to every third bit
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1FFFFFULL;
+  v = (v | (v << 32)) & 0x1F00000000FFFFULL;
+  v = (v | (v << 16)) & 0x1F0000FF0000FFULL;
+  v = (v | (v << 8)) & 0x100F00F00F00F00FULL;
+  v = (v | (v << 4)) & 0x10C30C30C30C30C3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+
+__global__ void k_evf_keys(int64_t np, WalkTree wt, const double* __restrict__ pts, unsigned long long* keys,
+                           int* idx) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  int t[3];
+  walk_box_of(wt, pts + 3 * i, t);
+  // coordinates in [-2^20, 2^20 - 1], shifted to [0, 2^21 - 1]
+  keys[i] = (spread3((unsigned long long)(t[0] + WALK_COORD_MAX)) << 2) |
+            (spread3((unsigned long long)(t[1] + WALK_COORD_MAX)) << 1) |
+            spread3((unsigned long long)(t[2] + WALK_COORD_MAX));
+  idx[i] = (int)i;
+}
+
+__global__ void k_evf_gather(int64_t np, WalkTree wt, const int* __restrict__ perm, const double* __restrict__ pts,
+                             double* __restrict__ spts, int* __restrict__ tcs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const int64_t o = perm[i];
+  const double X[3] = {pts[3 * o], pts[3 * o + 1], pts[3 * o + 2]};
+  int t[3];
+  walk_box_of(wt, X, t);
+  for (int a = 0; a < 3; ++a) {
+    spts[3 * i + a] = X[a];
+    tcs[3 * i + a] = t[a];
+  }
+}
+
+int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
+                 int64_t np, void* out, int mode, cudaStream_t s) {
+  if (np > 0x7fffffffLL) return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
+  const WalkTree wt = bem_walk_tree(h);
+  const int nc = mode == 0 ? 1 : (mode == 1 ? 3 : 4);
+  BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
+  BEM_TRY(bem_run_upward(h, nrhs, s));
+  unsigned long long *keys_in = nullptr, *keys = nullptr;
+  int *idx_in = nullptr, *perm = nullptr, *tcs = nullptr;
+  double *spts = nullptr, *acc = nullptr;
+  void* tmp = nullptr;
+  size_t tb = 0;
+  int rc = BEM_OK;
+  auto fail = [&](cudaError_t e) {
+    if (rc == BEM_OK && e != cudaSuccess)
+      rc = bem_fail(e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA, cudaGetErrorString(e));
+    return rc != BEM_OK;
+  };
+  do {
+    if (fail(cudaMallocAsync((void**)&keys_in, np * sizeof(unsigned long long), s))) break;
+    if (fail(cudaMallocAsync((void**)&keys, np * sizeof(unsigned long long), s))) break;
+    if (fail(cudaMallocAsync((void**)&idx_in, np * sizeof(int), s))) break;
+    if (fail(cudaMallocAsync((void**)&perm, np * sizeof(int), s))) break;
+    if (fail(cudaMallocAsync((void**)&tcs, 3 * np * sizeof(int), s))) break;
+    if (fail(cudaMallocAsync((void**)&spts, 3 * np * sizeof(double), s))) break;
+    if (fail(cudaMallocAsync((void**)&acc, 2 * nc * nrhs * np * sizeof(double), s))) break;
+    k_evf_keys<<<nblk(np, 256), 256, 0, s>>>(np, wt, points, keys_in, idx_in);
+    if (fail(cudaGetLastError())) break;
+    if (fail(cub::DeviceRadixSort::SortPairs(nullptr, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
+    if (fail(cudaMallocAsync(&tmp, tb, s))) break;
+    if (fail(cub::DeviceRadixSort::SortPairs(tmp, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
+    k_evf_gather<<<nblk(np, 256), 256, 0, s>>>(np, wt, perm, points, spts, tcs);
+    if (fail(cudaGetLastError())) break;
+    rc = bem_evf_far(h, wt, nrhs, mode, np, spts, tcs, acc, s);
+    if (rc != BEM_OK) break;
+    rc = bem_evf_near(h, wt, nrhs, mode, np, spts, tcs, perm, acc, dtype, out, s);
+  } while (false);
+  for (void* p : {(void*)keys_in, (void*)keys, (void*)idx_in, (void*)perm, (void*)tcs, (void*)spts, (void*)acc, tmp})
+    if (p) cudaFreeAsync(p, s);
+  return rc;
+}

@@ -825,6 +825,22 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
   for (int l = L + 1; l <= BEM_MAXLEV; ++l) h->lev[l].nbox = 0;
   h->L = L;
 
+  // the off-surface walk's far test per box: (4 h_max(box) / w_L)^2
+  {
+    const double wL = h->root_w / (1 << L);
+    for (int l = 0; l <= L; ++l) {
+      LevelInfo& lv = h->lev[l];
+      std::vector<float> g2(lv.nbox);
+      for (int b = 0; b < lv.nbox; ++b) {
+        const double q = 4.0 * hl[l].hm[b] / wL;
+        g2[b] = (float)(q * q);
+      }
+      BEM_TRY(bem_alloc(h, &lv.gap2, lv.nbox));
+      BEM_CUDA(cudaMemcpyAsync(lv.gap2, g2.data(), lv.nbox * sizeof(float), cudaMemcpyHostToDevice, s));
+      BEM_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+
   // near-singular search level: widest boxes still >= 4 h_max
   int Lc = 0;
   for (int l = 0; l <= L; ++l)

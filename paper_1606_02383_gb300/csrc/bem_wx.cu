@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "bem_common.cuh"
+#include "bem_tree_walk.cuh"
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -376,6 +377,191 @@ __global__ void k_p2l_t(int npair, const int* __restrict__ xdst, const int* __re
   }
 }
 
+// --------------------------------------------------- M2P at field points --
+// The multipole of one far box evaluated at one point (the off-surface walk,
+// bem_tree_walk.cuh), for NR right-hand sides at once: the same h^_n, Y_nm
+// recurrences as outgoing_rows, with the pair (n, m), (n, -m) folded into
+// Z = M~_nm Y_nm + M~_n,-m conj(Y_nm), so that
+//   u += sum_n h^_n Z_n,
+//   grad u += (v/|v|) sum_n h^_n'(r) Z_n + sum_n h^_n grad Z_n,
+// grad Z taking grad Y_nm = grad(W_n^m(u_z)) (u_x + i u_y)^m + W_n^m grad (u_x + i u_y)^m
+// with du_a/dv_c = (delta_ac - u_a u_c) / |v| (the chain rule through u = v / |v|).
+template <typename R, bool GRAD, int NR>
+__device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, const R* const (&Md)[NR],
+                                          R (&val)[NR][2], R (&grd)[NR][3][2]) {
+  typedef WxTab<R> T;
+  R hr[WX_T], hi[WX_T], dhr[GRAD ? WX_T : 1], dhi[GRAD ? WX_T : 1];
+  const R r = sqrt(vx * vx + vy * vy + vz * vz);
+  const R ir = R(1) / r;
+  const R x = k * r, ix = ir / k;
+  R sn, cs;
+  sc(x, &sn, &cs);
+  const R a2 = a * a, a3 = a / R(3);
+  hr[0] = sn * ix;
+  hi[0] = -cs * ix;
+  hr[1] = a3 * ((-cs + sn * ix) * ix);
+  hi[1] = a3 * ((-cs * ix - sn) * ix);
+  const R aix = a * ix;
+  for (int n = 1; n < p; ++n) {
+    const R c1 = aix * T::t1(n), c2 = a2 * T::t2(n);
+    hr[n + 1] = c1 * hr[n] - c2 * hr[n - 1];
+    hi[n + 1] = c1 * hi[n] - c2 * hi[n - 1];
+  }
+  const R u[3] = {vx * ir, vy * ir, vz * ir};
+  R dux[3], duy[3], duz[3];
+  if constexpr (GRAD) {
+    const R ka = k * (R(3) / a);
+    dhr[0] = -ka * hr[1];
+    dhi[0] = -ka * hi[1];
+    for (int n = 1; n <= p; ++n) {
+      const R c1 = a * T::t3(n), c2 = R(n + 1) * ix;
+      dhr[n] = k * (c1 * hr[n - 1] - c2 * hr[n]);
+      dhi[n] = k * (c1 * hi[n - 1] - c2 * hi[n]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dux[c] = ((c == 0 ? R(1) : R(0)) - u[0] * u[c]) * ir;
+      duy[c] = ((c == 1 ? R(1) : R(0)) - u[1] * u[c]) * ir;
+      duz[c] = ((c == 2 ? R(1) : R(0)) - u[2] * u[c]) * ir;
+    }
+  }
+  R Ar[NR], Ai[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) Ar[q] = Ai[q] = 0;
+  R pr = 1, pi = 0, dpr[3] = {0, 0, 0}, dpi[3] = {0, 0, 0};
+  for (int m = 0; m <= p; ++m) {
+    if (m > 0) {
+      const R npr = pr * u[0] - pi * u[1], npi = pr * u[1] + pi * u[0];
+      if constexpr (GRAD) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const R ndr = dpr[c] * u[0] - dpi[c] * u[1] + pr * dux[c] - pi * duy[c];
+          const R ndi = dpr[c] * u[1] + dpi[c] * u[0] + pr * duy[c] + pi * dux[c];
+          dpr[c] = ndr;
+          dpi[c] = ndi;
+        }
+      }
+      pr = npr;
+      pi = npi;
+    }
+    R w1 = T::q(m), w2 = 0, dw1[3] = {0, 0, 0}, dw2[3] = {0, 0, 0};
+    const R c1m = T::c1(m);
+    for (int n = m; n <= p; ++n) {
+      R w, dw[3] = {0, 0, 0};
+      if (n == m) {
+        w = w1;
+      } else if (n == m + 1) {
+        w = c1m * u[2] * w1;
+        if constexpr (GRAD)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dw[c] = c1m * (duz[c] * w1 + u[2] * dw1[c]);
+      } else {
+        const R ca = T::ca(n * WX_T + m), cb = T::cb(n * WX_T + m);
+        w = ca * (u[2] * w1 - cb * w2);
+        if constexpr (GRAD)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dw[c] = ca * (duz[c] * w1 + u[2] * dw1[c] - cb * dw2[c]);
+      }
+      if (n > m) {
+        w2 = w1;
+        w1 = w;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dw2[c] = dw1[c];
+          dw1[c] = dw[c];
+        }
+      }
+      const R yr = w * pr, yi = w * pi;
+      const R h_r = hr[n], h_i = hi[n];
+      const int qp = wx_idx(n, m), qm = wx_idx(n, -m);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const R mpr = Md[q][2 * qp], mpi = Md[q][2 * qp + 1];
+        // Z = M+ Y + M- conj(Y)
+        R zr = mpr * yr - mpi * yi, zi = mpr * yi + mpi * yr;
+        R mmr = 0, mmi = 0;
+        if (m > 0) {
+          mmr = Md[q][2 * qm];
+          mmi = Md[q][2 * qm + 1];
+          zr += mmr * yr + mmi * yi;
+          zi += -mmr * yi + mmi * yr;
+        }
+        val[q][0] += h_r * zr - h_i * zi;
+        val[q][1] += h_r * zi + h_i * zr;
+        if constexpr (GRAD) {
+          Ar[q] += dhr[n] * zr - dhi[n] * zi;
+          Ai[q] += dhr[n] * zi + dhi[n] * zr;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const R dyr = dw[c] * pr + w * dpr[c], dyi = dw[c] * pi + w * dpi[c];
+            const R gzr = mpr * dyr - mpi * dyi + (mmr * dyr + mmi * dyi);
+            const R gzi = mpr * dyi + mpi * dyr + (-mmr * dyi + mmi * dyr);
+            grd[q][c][0] += h_r * gzr - h_i * gzi;
+            grd[q][c][1] += h_r * gzi + h_i * gzr;
+          }
+        }
+      }
+    }
+  }
+  if constexpr (GRAD) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        grd[q][c][0] += u[c] * Ar[q];
+        grd[q][c][1] += u[c] * Ai[q];
+      }
+  }
+}
+
+// One thread per field point (in the walk's order): the multipoles of the
+// point's far boxes.  Writes acc[r][i][c] (FP64 complex), c over the
+// components of the mode (0: u; 1: grad u; 2: u, grad u).
+template <typename R, int MODE, int NR>
+__global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt, const double* __restrict__ pts,
+                                                 const int* __restrict__ tcs, LevTab lt, const int* __restrict__ lev_p,
+                                                 const R* __restrict__ lev_a, R k, const R* __restrict__ M,
+                                                 int64_t exp_stride, double* __restrict__ acc) {
+  constexpr bool GRAD = MODE != 0;
+  constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+  const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+  R val[NR][2], grd[NR][3][2];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    val[q][0] = val[q][1] = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) grd[q][c][0] = grd[q][c][1] = 0;
+  }
+  tree_walk(wt, t, [&](int kind, int l, int b) {
+    if (kind != 0) return;
+    const double* c = wt.lv[l].centre + 3 * b;
+    const R vx = (R)(X[0] - c[0]), vy = (R)(X[1] - c[1]), vz = (R)(X[2] - c[2]);
+    const R* Md[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) Md[q] = M + 2 * ((int64_t)(r0 + q) * exp_stride + lt.base[l] + (int64_t)b * lt.P[l]);
+    m2p_point<R, GRAD, NR>(lev_p[l], k, lev_a[l], vx, vy, vz, Md, val, grd);
+  });
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    double* o = acc + 2 * (((int64_t)(r0 + q) * np + i) * NC);
+    int c0 = 0;
+    if (MODE != 1) {
+      o[0] = (double)val[q][0];
+      o[1] = (double)val[q][1];
+      c0 = 1;
+    }
+    if (GRAD)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[2 * (c0 + c)] = (double)grd[q][c][0];
+        o[2 * (c0 + c) + 1] = (double)grd[q][c][1];
+      }
+  }
+}
+
 // -------------------------------------------------------------------- host --
 // orders and k w_l of every level in the operator's precision (setup)
 int bem_build_wx_tables(bem_handle* h, cudaStream_t s) {
@@ -539,4 +725,40 @@ int bem_run_m2p_t(bem_handle* h, int nrhs, const void* dens, void* Mu, cudaStrea
 int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStream_t s, int* launches) {
   return bem_is_fp64(h) ? run_p2l_t<double>(h, nrhs, Lam, uv, s, launches)
                         : run_p2l_t<float>(h, nrhs, Lam, uv, s, launches);
+}
+
+template <typename R, int MODE>
+static int evf_far_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
+                        double* acc, cudaStream_t s) {
+  const LevTab lt = bem_levtab(h);
+  const unsigned g = nblk(np, 128);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int rem = nrhs - r0;
+    if (rem >= 4) {
+      k_evf_far<R, MODE, 4><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
+                                              (const R*)h->Mexp, h->exp_total, acc);
+      r0 += 4;
+    } else if (rem >= 2) {
+      k_evf_far<R, MODE, 2><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
+                                              (const R*)h->Mexp, h->exp_total, acc);
+      r0 += 2;
+    } else {
+      k_evf_far<R, MODE, 1><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
+                                              (const R*)h->Mexp, h->exp_total, acc);
+      r0 += 1;
+    }
+    BEM_CUDA(cudaGetLastError());
+  }
+  return BEM_OK;
+}
+
+int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                const int* tcs, double* acc, cudaStream_t s) {
+  const bool f64 = bem_is_fp64(h);
+  if (mode == 0) return f64 ? evf_far_impl<double, 0>(h, wt, nrhs, np, pts, tcs, acc, s)
+                            : evf_far_impl<float, 0>(h, wt, nrhs, np, pts, tcs, acc, s);
+  if (mode == 1) return f64 ? evf_far_impl<double, 1>(h, wt, nrhs, np, pts, tcs, acc, s)
+                            : evf_far_impl<float, 1>(h, wt, nrhs, np, pts, tcs, acc, s);
+  return f64 ? evf_far_impl<double, 2>(h, wt, nrhs, np, pts, tcs, acc, s)
+             : evf_far_impl<float, 2>(h, wt, nrhs, np, pts, tcs, acc, s);
 }

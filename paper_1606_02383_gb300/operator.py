@@ -132,22 +132,31 @@ class Operator:
                                        None if ys is None else ys.data_ptr(), z.data_ptr(), flags, _stream()))
         return z
 
-    def eval_points(self, points, x=None, y=None, dtype=None, gradient=False):
+    def eval_points(self, points, x=None, y=None, dtype=None, gradient=False, value_and_gradient=False,
+                    direct=False):
         """u(p) = sum_j S(p, j) y_j - D(p, j) x_j at points [npoints, 3] off the
-        surface (direct sum, the entries' rules).  Returns [nrhs, npoints], or
-        grad u as [nrhs, npoints, 3] with gradient=True."""
+        surface.  Returns [nrhs, npoints]; grad u as [nrhs, npoints, 3] with
+        gradient=True; (u, grad u) as [nrhs, npoints, 4] with
+        value_and_gradient=True.  FMM handles walk the octree (multipoles of
+        far boxes, rules on near leaves) unless direct=True asks for the
+        direct sum over all elements."""
         ref = x if x is not None else y
         if ref is None:
             raise ValueError("x and y cannot both be None")
+        if gradient and value_and_gradient:
+            raise ValueError("gradient and value_and_gradient exclude each other")
         dtype = dtype or (ref.dtype if isinstance(ref, torch.Tensor) else torch.complex128)
         xs, ys = self._prep(x, dtype), self._prep(y, dtype)
         nrhs = (xs if xs is not None else ys).shape[0]
         pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
-        shape = (nrhs, pts.shape[0], 3) if gradient else (nrhs, pts.shape[0])
+        nc = 4 if value_and_gradient else (3 if gradient else 1)
+        shape = (nrhs, pts.shape[0], nc) if nc > 1 else (nrhs, pts.shape[0])
         out = torch.empty(shape, dtype=dtype, device="cuda")
+        flags = (_lib.BEM_EVAL_VALUE_GRADIENT if value_and_gradient else 0) | \
+            (_lib.BEM_EVAL_GRADIENT if gradient else 0) | (_lib.BEM_EVAL_DIRECT if direct else 0)
         _lib.check(self._lib.bem_eval_points(self._h, nrhs, _dtype_code(out), None if xs is None else xs.data_ptr(),
                                              None if ys is None else ys.data_ptr(), pts.data_ptr(), pts.shape[0],
-                                             out.data_ptr(), _lib.BEM_EVAL_GRADIENT if gradient else 0, _stream()))
+                                             out.data_ptr(), flags, _stream()))
         return out
 
     def point_sources(self, points, amps, dtype=torch.complex128):
@@ -163,21 +172,35 @@ class Operator:
                                                a.data_ptr(), out.data_ptr(), _stream()))
         return out
 
-    def state_and_adjoint(self, b, observers, incident_at_observers, tol=1e-8, max_iter=200, restart=200):
-        """The chain of Section 2.2 for f = 1/2 |p|^2 summed over observation points:
-        the state solve (1/2 I - D) p = b; the pressure at the observers,
-        p(x_m) = p_inc(x_m) + (D p)(x_m) (the rigid body's representation formula);
-        the adjoint right-hand side sum_m conj(p(x_m)) G(c - x_m); the adjoint
-        solve with the same operator.  Returns a dict with p, p_obs, weights,
-        p_adj, iterations and residuals."""
-        p, it_s, rel_s = self.solve(b, tol=tol, max_iter=max_iter, restart=restart)
-        inc = torch.as_tensor(incident_at_observers).to("cuda", torch.complex128).reshape(1, -1)
-        p_obs = inc - self.eval_points(observers, x=p.to(torch.complex128))
-        weights = torch.conj_physical(p_obs)
-        b_adj = self.point_sources(observers, weights, dtype=p.dtype)
-        p_adj, it_a, rel_a = self.solve(b_adj, tol=tol, max_iter=max_iter, restart=restart)
-        return {"p": p, "p_obs": p_obs, "weights": weights, "p_adj": p_adj, "iterations": (it_s, it_a),
-                "relres": (rel_s, rel_a)}
+    def state_and_adjoint(self, b, observers, incident_at_observers, tol=1e-8, max_iter=200, restart=200,
+                          driver="graph"):
+        """The chain of Section 2.2 for f = 1/2 |p|^2 summed over observation points
+        (one bem_state_adjoint call): the state solve (1/2 I - D) p = b; the
+        pressure at the observers, p(x_m) = p_inc(x_m) + (D p)(x_m) (the rigid
+        body's representation formula); the adjoint right-hand side
+        sum_m conj(p(x_m)) G(c - x_m); the adjoint solve with the same
+        operator.  Returns a dict with p, p_obs, weights, p_adj, iterations and
+        residuals."""
+        bs = self._prep(b, b.dtype)
+        if bs.shape[0] != 1:
+            raise ValueError("the chain takes one right-hand side")
+        obs = torch.as_tensor(observers, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        inc = _raw(torch.as_tensor(incident_at_observers).to("cuda", torch.complex128).reshape(-1))
+        nobs = obs.shape[0]
+        if inc.shape[0] != nobs:
+            raise ValueError("one incident value per observer")
+        p = torch.empty_like(bs)
+        p_adj = torch.empty_like(bs)
+        p_obs = torch.empty((1, nobs), dtype=torch.complex128, device="cuda")
+        weights = torch.empty_like(p_obs)
+        iters = (ctypes.c_int * 2)()
+        rel = (ctypes.c_double * 2)()
+        _lib.check(self._lib.bem_state_adjoint(self._h, _dtype_code(bs), bs.data_ptr(), nobs, obs.data_ptr(),
+                                               inc.data_ptr(), float(tol), int(max_iter), int(restart),
+                                               _gmres_driver_flags(driver), p.data_ptr(), p_obs.data_ptr(),
+                                               weights.data_ptr(), p_adj.data_ptr(), iters, rel, _stream()))
+        return {"p": p, "p_obs": p_obs, "weights": weights, "p_adj": p_adj, "iterations": (iters[0], iters[1]),
+                "relres": (np.array([rel[0]]), np.array([rel[1]]))}
 
     def point_source_field(self, points, sources, amps, gradient=False):
         """phi(x) = sum_m a_m G(x - x_m) at points [npoints, 3] (with the
@@ -198,24 +221,24 @@ class Operator:
         """T(x) = Re[c1 grad p . grad pa - c2 p pa] at points in the fluid
         (Section 2.5), from a state_and_adjoint result `chain` of the rigid
         body: p = p_inc + D p_surf and pa = phi + D pa_surf, phi the point
-        sources at the observers with the adjoint weights.  incident:
-        [npoints, 4] complex, the incident field and its gradient at the
-        points (the caller's incident wave).  c1 = 3/2 and c2 = k^2 are the
-        sound-hard limit in units rho_f = c_f = 1."""
+        sources at the observers with the adjoint weights (one
+        bem_topological_field call).  incident: [npoints, 4] complex, the
+        incident field and its gradient at the points (the caller's incident
+        wave).  c1 = 3/2 and c2 = k^2 are the sound-hard limit in units
+        rho_f = c_f = 1."""
         c2 = self.k ** 2 if c2 is None else float(c2)
         pts = torch.as_tensor(points, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
         inc = _raw(torch.as_tensor(incident).to("cuda", torch.complex128).reshape(-1, 4))
-
-        def field(surface):  # D surface at the points, with its gradient: [npoints, 4]
-            u = -self.eval_points(pts, x=surface.to(torch.complex128))[0]
-            gu = -self.eval_points(pts, x=surface.to(torch.complex128), gradient=True)[0]
-            return torch.cat([u[:, None], gu], dim=1)
-
-        state = _raw(inc + field(chain["p"]))
-        adj = _raw(self.point_source_field(pts, observers, chain["weights"], gradient=True)[0] + field(chain["p_adj"]))
+        obs = torch.as_tensor(observers, dtype=torch.float64).reshape(-1, 3).to("cuda").contiguous()
+        w = _raw(torch.as_tensor(chain["weights"]).to("cuda", torch.complex128).reshape(-1))
+        p = self._prep(chain["p"], chain["p"].dtype)
+        pa = self._prep(chain["p_adj"], p.dtype)
+        if inc.shape[0] != pts.shape[0] or w.shape[0] != obs.shape[0]:
+            raise ValueError("incident must be [npoints, 4] and weights one per observer")
         T = torch.empty(pts.shape[0], dtype=torch.float64, device="cuda")
-        _lib.check(self._lib.bem_topological_derivative(pts.shape[0], float(c1), c2, state.data_ptr(), adj.data_ptr(),
-                                                        T.data_ptr(), _stream()))
+        _lib.check(self._lib.bem_topological_field(self._h, _dtype_code(p), p.data_ptr(), pa.data_ptr(), obs.shape[0],
+                                                   obs.data_ptr(), w.data_ptr(), pts.shape[0], pts.data_ptr(),
+                                                   inc.data_ptr(), float(c1), c2, T.data_ptr(), _stream()))
         return T
 
     def apply_host(self, x=None, y=None, out=None, no_half=False):

@@ -78,6 +78,18 @@ def test_sync_and_wait_limit_reject_null_handles():
     assert lib.bem_set_wait_limit(None, 0, 0) == _lib.BEM_ERR_INVALID_ARG
 
 
+def test_chain_calls_reject_null_handles():
+    lib = _lib.load()
+    it = (ctypes.c_int * 2)()
+    rel = (ctypes.c_double * 2)()
+    assert lib.bem_state_adjoint(None, _lib.BEM_C128, None, 1, None, None, 1e-8, 10, 10, 0, None, None, None, None,
+                                 it, rel, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_topological_field(None, _lib.BEM_C128, None, None, 1, None, None, 1, None, None, 1.5, 1.0, None,
+                                     None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_eval_points(None, 1, _lib.BEM_C128, None, None, None, 1, None,
+                               _lib.BEM_EVAL_GRADIENT | _lib.BEM_EVAL_VALUE_GRADIENT, None) == _lib.BEM_ERR_INVALID_ARG
+
+
 def test_option_checks_without_gpu():
     """Out-of-range tree and tile options are rejected before any device work."""
     import numpy as np

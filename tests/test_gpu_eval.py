@@ -1,9 +1,13 @@
 """Field at off-surface points (bem_eval_points) vs the oracle's eval_points.
 
-The points are a lattice in its natural order around the sphere, plus points
-on rays just off the surface (between 0.3 and 6 longest edges away, so every
-rule R_0, R_1, R_2 is used).  Tolerances as for the apply: 1e-10 relative L2
-in the FP64 modes (same rules, only rounding differs), 1e-5 in the mixed mode.
+The points are a lattice in its natural order around the sphere, points on
+rays just off the surface (between 0.3 and 6 longest edges away, so every
+rule R_0, R_1, R_2 is used), points 50 radii away (outside the tree's root
+cube) and the centre (in an empty box).  Tolerances: the direct sums as the
+apply, 1e-10 relative L2 in the FP64 modes (same rules, only rounding
+differs) and 1e-5 in the mixed mode; the FMM walk (multipoles of far boxes)
+1e-5 in the mixed mode and 1e-8 in the FP64 mode at order 16, where the
+truncation measured 1e-9 (1.6e-10 with leaves on level 2).
 """
 import numpy as np
 import pytest
@@ -32,43 +36,57 @@ def field_points(V, T):
     off = h * np.geomspace(0.3, 6.0, 120) * np.where(np.arange(120) % 2 == 0, 1.0, -1.0)
     near = c[idx] + dirs * off[:, None]
     order = np.argsort(np.arctan2(near[:, 1], near[:, 0]))  # neighbours along a curve
-    return np.concatenate([lat, near[order]])
+    far = rng.normal(size=(20, 3))
+    far = 50.0 * far / np.linalg.norm(far, axis=1, keepdims=True)
+    return np.concatenate([lat, near[order], far, np.zeros((1, 3))])
 
 
-@pytest.mark.parametrize("mode,tol", [("direct64", 1e-10), ("fp64", 1e-10), ("mixed", 1e-5)])
-def test_eval_points_matches_oracle(cuda_ok, mode, tol):
+# (mode, direct sum, order, tolerance)
+EVAL_CASES = [("direct64", False, 10, 1e-10), ("fp64", True, 10, 1e-10), ("mixed", True, 10, 1e-5),
+              ("fp64", False, 16, 1e-8), ("mixed", False, 10, 1e-5)]
+
+
+@pytest.mark.parametrize("mode,direct,p,tol", EVAL_CASES)
+def test_eval_points_matches_oracle(cuda_ok, mode, direct, p, tol):
     V, T = inputs.icosphere(3)
     n, k = T.shape[0], 2.0
     x = inputs.random_density(n, 2, seed=9, stream=0)
     y = inputs.random_density(n, 2, seed=9, stream=1)
     pts = field_points(V, T)
     ref = oracle.eval_points(V, T, k, pts, x=x, y=y)
-    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
-    u = op.eval_points(pts, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()).cpu().numpy()
+    op = Operator(V, T, k, p=p, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    u = op.eval_points(pts, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), direct=direct).cpu().numpy()
     assert u.shape == ref.shape
     assert rel(u, ref) <= tol
     # each layer alone, and single precision output
-    us = op.eval_points(pts, None, torch.from_numpy(y).cuda()).cpu().numpy()
+    us = op.eval_points(pts, None, torch.from_numpy(y).cuda(), direct=direct).cpu().numpy()
     assert rel(us, oracle.eval_points(V, T, k, pts, y=y)) <= tol
     u64 = op.eval_points(pts, torch.from_numpy(x.astype(np.complex64)).cuda(),
-                         torch.from_numpy(y.astype(np.complex64)).cuda()).cpu().numpy()
+                         torch.from_numpy(y.astype(np.complex64)).cuda(), direct=direct).cpu().numpy()
     assert u64.dtype == np.complex64 and rel(u64, ref) <= max(tol, 2e-6)
     op.close()
 
 
-@pytest.mark.parametrize("mode,tol", [("direct64", 1e-10), ("fp64", 1e-10), ("mixed", 1e-5)])
-def test_eval_points_gradient_matches_oracle(cuda_ok, mode, tol):
-    """grad u at the same points (every rule used) against the oracle's gradient."""
+@pytest.mark.parametrize("mode,direct,p,tol", EVAL_CASES)
+def test_eval_points_gradient_matches_oracle(cuda_ok, mode, direct, p, tol):
+    """grad u at the same points (every rule used) against the oracle's
+    gradient; the value-and-gradient layout holds the same numbers."""
     V, T = inputs.icosphere(3)
     n, k = T.shape[0], 2.0
     x = inputs.random_density(n, 2, seed=10, stream=0)
     y = inputs.random_density(n, 2, seed=10, stream=1)
     pts = field_points(V, T)
     ref = oracle.eval_points_grad(V, T, k, pts, x=x, y=y)
-    op = Operator(V, T, k, p=10, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
-    g = op.eval_points(pts, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), gradient=True).cpu().numpy()
+    op = Operator(V, T, k, p=p, mode=mode, leaf_level=0 if mode == "direct64" else 3, max_nrhs=2)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    g = op.eval_points(pts, xd, yd, gradient=True, direct=direct).cpu().numpy()
     assert g.shape == ref.shape
     assert rel(g, ref) <= tol
+    u = op.eval_points(pts, xd, yd, direct=direct).cpu().numpy()
+    ug = op.eval_points(pts, xd, yd, value_and_gradient=True, direct=direct).cpu().numpy()
+    assert ug.shape == (2, pts.shape[0], 4)
+    # the same sums (FP32 contraction may differ between the kernels' variants)
+    assert rel(ug[..., 0], u) <= 1e-6 and rel(ug[..., 1:], g) <= 1e-6
     op.close()
 
 
