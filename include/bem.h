@@ -114,6 +114,14 @@ typedef struct {
   int tc_tf32;      /* mixed mode: 1 runs the tensor-core translations as 3xTF32; 0 (default) as the
                        two-term FP16 split with power-of-two row scales (same 11-bit mantissa, half
                        the bytes and twice the tensor rate) */
+  int tc_pipeline;  /* mixed modes, the tensor-core translation loop: 1 two stages, all threads gather,
+                       synchronise, one thread issues the MMAs; 2 or 4 stages with specialised warps
+                       (cp.async gather warps, a bulk-copy thread and an MMA thread, synchronised by
+                       mbarriers alone; 2 stages leave room for two CTAs per SM); 0 = default (2) */
+  int p2p_ctas;     /* FP32 FMM: > 0 forks the far field before the near field and runs the near field
+                       from this many resident CTAs per SM (a work queue over its units), so that the
+                       far field's kernels share the SMs with it; 0 (default) runs the near field on
+                       the whole grid first and the far field after it */
 } bem_options;
 
 /*

@@ -146,6 +146,9 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   if (o.p2p_unit != 16 && o.p2p_unit != 32 && o.p2p_unit != 64)
     return bem_fail(BEM_ERR_INVALID_ARG, "p2p_unit must be 16, 32 or 64");
   if (o.tc_kslice < 2 || o.tc_kslice > 16) return bem_fail(BEM_ERR_INVALID_ARG, "tc_kslice must be in [2, 16]");
+  if (o.tc_pipeline != 0 && o.tc_pipeline != 1 && o.tc_pipeline != 2 && o.tc_pipeline != 4)
+    return bem_fail(BEM_ERR_INVALID_ARG, "tc_pipeline must be 0, 1, 2 or 4");
+  if (o.p2p_ctas < 0 || o.p2p_ctas > 16) return bem_fail(BEM_ERR_INVALID_ARG, "p2p_ctas must be in [0, 16]");
 
   cudaStream_t s = (cudaStream_t)stream;
   bem_handle* h = new bem_handle();
@@ -159,6 +162,8 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->tc_kslice_max = o.tc_kslice;
   h->corr_rules32 = o.corr_rules32 ? 1 : 0;
   h->tc_fp16 = (o.mode == BEM_MODE_FMM_MIXED && o.tc_tf32 == 0) ? 1 : 0;
+  h->tc_pipeline = o.tc_pipeline == 0 ? BEM_TC_PIPELINE_DEFAULT : o.tc_pipeline;
+  h->p2p_ctas = o.p2p_ctas;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
   for (int l = 0; l <= BEM_MAXLEV; ++l) {
@@ -179,6 +184,9 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   };
   int rc;
   if ((rc = bem_alloc(h, &h->d_err, 1)) != BEM_OK) return fail(rc);
+  if ((rc = bem_alloc(h, &h->p2p_ctr, h->nrhs_max + 2)) != BEM_OK) return fail(rc);
+  if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->nsm < 1)
+    h->nsm = 1;
   {
     // the far field's stream (see the apply): the greatest priority
     int least = 0, greatest = 0;

@@ -187,22 +187,15 @@ __device__ __forceinline__ void p2p_self_pair(float4 t, const float4* __restrict
 // FP32: NR right-hand sides r0 + NR blockIdx.y + [0, NR) per warp, sharing
 // the kernel values of every point (packed f32x2 arithmetic, two targets per
 // lane).
+// one work unit u of the FP32 near field for right-hand sides r .. r + NR - 1
 template <int NR>
-__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k,
-                                                              const int4* __restrict__ units,
-                                                              const int* __restrict__ u_ptr,
-                                                              const int* __restrict__ u_src,
-                                                              const float4* __restrict__ u_shift,
-                                                              const int* __restrict__ bstart,
-                                                              const int* __restrict__ bend,
-                                                              const float4* __restrict__ tgt,
-                                                              const float4* __restrict__ src,
-                                                              const float4* __restrict__ dens,
-                                                              double* __restrict__ zn) {
-  int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
-  if (u >= nunits) return;
+__device__ __forceinline__ void p2p_unit32(int u, int r, int64_t nt, float k, const int4* __restrict__ units,
+                                           const int* __restrict__ u_ptr, const int* __restrict__ u_src,
+                                           const float4* __restrict__ u_shift, const int* __restrict__ bstart,
+                                           const int* __restrict__ bend, const float4* __restrict__ tgt,
+                                           const float4* __restrict__ src, const float4* __restrict__ dens,
+                                           double* __restrict__ zn) {
   int lane = threadIdx.x & 31;
-  int r = r0 + blockIdx.y * NR;
   int4 U = units[u];
   int b = U.x, tfirst = U.y, cnt = U.z;
   int np2 = (cnt + 1) >> 1;  // power of two
@@ -276,6 +269,51 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
         zn[o + 2 * np2 + 1] = (double)b_im;
       }
     }
+  }
+}
+
+
+template <int NR>
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k,
+                                                              const int4* __restrict__ units,
+                                                              const int* __restrict__ u_ptr,
+                                                              const int* __restrict__ u_src,
+                                                              const float4* __restrict__ u_shift,
+                                                              const int* __restrict__ bstart,
+                                                              const int* __restrict__ bend,
+                                                              const float4* __restrict__ tgt,
+                                                              const float4* __restrict__ src,
+                                                              const float4* __restrict__ dens,
+                                                              double* __restrict__ zn) {
+  const int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
+  if (u >= nunits) return;
+  p2p_unit32<NR>(u, r0 + blockIdx.y * NR, nt, k, units, u_ptr, u_src, u_shift, bstart, bend, tgt, src, dens, zn);
+}
+
+// The same work from a fixed number of resident CTAs: every warp takes the
+// next unit (largest first) from a counter per right-hand-side chunk, so the
+// near field can run with a few CTAs per SM and leave room on every SM for
+// the far field's kernels, which run beside it on the far-field stream.
+template <int NR>
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32_q(int nunits, int64_t nt, int r0, float k,
+                                                                int* __restrict__ counter,
+                                                                const int4* __restrict__ units,
+                                                                const int* __restrict__ u_ptr,
+                                                                const int* __restrict__ u_src,
+                                                                const float4* __restrict__ u_shift,
+                                                                const int* __restrict__ bstart,
+                                                                const int* __restrict__ bend,
+                                                                const float4* __restrict__ tgt,
+                                                                const float4* __restrict__ src,
+                                                                const float4* __restrict__ dens,
+                                                                double* __restrict__ zn) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&counter[blockIdx.y], 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nunits) return;
+    p2p_unit32<NR>(u, r0 + blockIdx.y * NR, nt, k, units, u_ptr, u_src, u_shift, bstart, bend, tgt, src, dens, zn);
   }
 }
 
@@ -1404,29 +1442,49 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
   bool fmm = bem_is_fmm(h);
   int L = h->L;
-  // near field
-  int pr = bem_prof_begin(h, s);
-  int nl = 1;
-  if (fmm) {
-    const unsigned gx = nblk(h->n_p2p_units, P2P_WARPS);
-    if constexpr (sizeof(R) == 4) {
-      nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
-        k_p2p_fmm32<decltype(nr)::value><<<dim3(gx, nchunk), 32 * P2P_WARPS, 0, s>>>(
-            h->n_p2p_units, nt, r0, (float)h->k, h->p2p_units, h->u_ptr, h->u_src, h->u_shift32, h->gl_start,
-            h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
-      });
+  // With p2p_ctas > 0 (FP32 FMM) the far field is forked first and the near
+  // field runs beside it from p2p_ctas resident CTAs per SM.
+  const bool overlap = fmm && L >= 2 && sizeof(R) == 4 && h->p2p_ctas > 0;
+  auto near = [&]() -> int {
+    int pr = bem_prof_begin(h, s);
+    int nl = 1;
+    if (fmm) {
+      const unsigned gx = nblk(h->n_p2p_units, P2P_WARPS);
+      if constexpr (sizeof(R) == 4) {
+        if (overlap) {
+          BEM_CUDA(cudaMemsetAsync(h->p2p_ctr, 0, sizeof(int) * (h->nrhs_max + 2), s));
+          const unsigned gq = std::min<unsigned>(gx, (unsigned)(h->p2p_ctas * h->nsm));
+          int c0 = 0;
+          nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+            k_p2p_fmm32_q<decltype(nr)::value><<<dim3(gq, nchunk), 32 * P2P_WARPS, 0, s>>>(
+                h->n_p2p_units, nt, r0, (float)h->k, h->p2p_ctr + c0, h->p2p_units, h->u_ptr, h->u_src,
+                h->u_shift32, h->gl_start, h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens,
+                h->zn);
+            c0 += nchunk;
+          });
+        } else {
+          nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+            k_p2p_fmm32<decltype(nr)::value><<<dim3(gx, nchunk), 32 * P2P_WARPS, 0, s>>>(
+                h->n_p2p_units, nt, r0, (float)h->k, h->p2p_units, h->u_ptr, h->u_src, h->u_shift32, h->gl_start,
+                h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
+          });
+        }
+      } else {
+        k_p2p_fmm64<<<dim3(gx, nrhs), 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, h->k, h->p2p_units, h->u_ptr,
+                                                            h->u_src, h->u_shift64, h->gl_start, h->gl_end,
+                                                            (const double4*)tgt, (const double4*)src,
+                                                            (const double4*)dens, h->zn);
+      }
     } else {
-      k_p2p_fmm64<<<dim3(gx, nrhs), 32 * P2P_WARPS, 0, s>>>(h->n_p2p_units, nt, h->k, h->p2p_units, h->u_ptr,
-                                                          h->u_src, h->u_shift64, h->gl_start, h->gl_end,
-                                                          (const double4*)tgt, (const double4*)src,
-                                                          (const double4*)dens, h->zn);
+      dim3 grid(nblk(nt, P2P_THREADS), nrhs);
+      k_p2p_direct<R><<<grid, P2P_THREADS, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->zn);
     }
-  } else {
-    dim3 grid(nblk(nt, P2P_THREADS), nrhs);
-    k_p2p_direct<R><<<grid, P2P_THREADS, 0, s>>>(nt, (R)h->k, tgt, src, dens, h->zn);
-  }
-  BEM_CUDA(cudaGetLastError());
-  bem_prof_end(h, pr, 1, nl, s);
+    BEM_CUDA(cudaGetLastError());
+    bem_prof_end(h, pr, 1, nl, s);
+    return BEM_OK;
+  };
+  int pr, nl;
+  if (!overlap) BEM_TRY(near());
   if (!fmm || L < 2) {
     pr = bem_prof_begin(h, s);
     nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
@@ -1486,6 +1544,14 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
   BEM_CUDA(cudaEventRecord(h->ev_fork, s));
   BEM_CUDA(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
   const int rc = far(h->s_far);
+  if (overlap) {
+    const int rn = near();
+    if (rn != BEM_OK) {
+      cudaEventRecord(h->ev_join, h->s_far);
+      cudaStreamWaitEvent(s, h->ev_join, 0);
+      return rn;
+    }
+  }
   pr = bem_prof_begin(h, s);
   nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
     k_correction<V4, R, decltype(nr)::value><<<dim3(nblk(nt * 32, 256), nchunk), 256, 0, s>>>(

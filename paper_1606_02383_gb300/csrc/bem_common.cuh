@@ -144,6 +144,8 @@ struct GroupedOp {
   int tc_kslice_split = 16;
   int64_t tc_want = 0;  // CTAs that give every SM two
   int* d_prep_row = nullptr;            // [npairs] row (flag * nbox + box) of the prepared source
+  int* d_prep_list = nullptr;           // [n_prep_list] distinct rows the pairs read (when few)
+  int n_prep_list = 0;
   float* tcA = nullptr;
   float* tscale = nullptr;  // FP16 split: inverse power-of-two scale of every matrix row, per group at d_tsoff[g]
   int* d_tsoff = nullptr;
@@ -151,6 +153,9 @@ struct GroupedOp {
   int4* d_tc_jobs = nullptr;
   int n_tc_jobs = 0;
 };
+
+// translation kernel of the mixed modes when bem_options.tc_pipeline is 0
+#define BEM_TC_PIPELINE_DEFAULT 2
 
 struct LevelInfo {
   int nbox = 0;
@@ -201,7 +206,11 @@ struct bem_handle {
   int p2p_unit = 64;       // most targets per near-field warp work unit
   int tc_kslice_max = 16;  // most K stages per tensor-core translation job
   int corr_rules32 = 0;    // mixed modes: non-self near-singular rules summed in FP32
-  int tc_fp16 = 0;         // mixed mode: translations as the FP16 split (else 3xTF32)
+  int tc_fp16 = 0;   // mixed mode: translations as the FP16 split (else 3xTF32)
+  int tc_pipeline = 1;  // translation kernel: 1 block-synchronous, 2 / 4 warp-specialised stages
+  int p2p_ctas = 0;     // > 0: near field from this many resident CTAs per SM, beside the far field
+  int nsm = 0;          // SMs of the device
+  int* p2p_ctr = nullptr;  // [nrhs_max + 2] unit counters of the resident near field
   int p_min = 4, p_max = 40;
   int p_level[BEM_MAXLEV + 1] = {0};  // explicit per-level orders (0 = automatic)
   int64_t nt = 0, nv = 0;

@@ -216,6 +216,72 @@ __global__ void k_tc_pack16(const float* __restrict__ T, int Po, int Pi, int nks
   }
 }
 
+// Epilogue of one tile: TMEM lanes hold the tile's 128 pairs, columns its N
+// real output rows.  In chunks of 64 columns (32 output coefficients):
+//   1. warp w copies lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31 of
+//      the chunk from tensor memory into a shared tile [pair][column] (rows
+//      padded to 68 floats: the 16-byte stores of 8 consecutive pairs cover
+//      all banks);
+//   2. warp w takes pairs w, w + 8, ...: lane j adds coefficient j of the
+//      chunk, scaled back (FP16 split), reflected and signed as the pair's
+//      flags say, to the pair's destination expansion, so that one warp's
+//      atomics fall on one expansion's consecutive coefficients (a few
+//      32-byte sectors per instruction instead of one sector per lane).
+// `buf` is the kernel's stage memory, free once every copy and MMA is done.
+#define TC_EPI_STRIDE 68
+template <bool F16>
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, unsigned char* buf, const int* s_src,
+                                            const int* s_dst, const int* s_flg, const float* __restrict__ escale,
+                                            const float* __restrict__ tscale, const int* __restrict__ tsoff, int g,
+                                            int Po, int N, int nt, float* __restrict__ D) {
+  float* tile = (float*)buf;
+  const float* tsg = F16 ? tscale + tsoff[g] : nullptr;
+  const int pr = 32 * (warp & 3) + lane;
+  for (int c0 = 0; c0 < N; c0 += 64) {
+    const int ncol = min(64, N - c0);  // a multiple of 16
+    const int cw = 32 * (warp >> 2);   // this warp's columns within the chunk
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+      if (cw + j < ncol) {
+        uint32_t v[8];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cw + j);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float* t = tile + pr * TC_EPI_STRIDE + cw + j;
+        *(float4*)t = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                  __uint_as_float(v[3]));
+        *(float4*)(t + 4) = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
+                                        __uint_as_float(v[7]));
+      }
+    }
+    __syncthreads();
+    // output coefficient of lane j: q = (nt TC_NMAX + c0) / 2 + j = n^2 + n + m
+    const int q = (nt * TC_NMAX + c0) / 2 + lane;
+    const bool live = 2 * lane < ncol && q < Po;
+    int n = (int)sqrtf((float)q);
+    if ((n + 1) * (n + 1) <= q) ++n;
+    if (n * n > q) --n;
+    const int m = q - n * n - n;
+    const float ts = (F16 && live) ? tsg[2 * q] : 1.f;
+    for (int pc = warp; pc < TC_M; pc += 8) {
+      const int dof = s_dst[pc];
+      if (dof < 0) continue;
+      if (live) {
+        const int fl = s_flg[pc];
+        const bool neg = ((fl & 1) && (m & 1)) != ((fl & 4) && ((n + m) & 1));
+        const bool mflip = ((fl & 1) != 0) != ((fl & 2) != 0);
+        float sc = neg ? -1.f : 1.f;
+        if (F16) sc *= escale[s_src[pc]] * ts;
+        const float2 v = *(const float2*)(tile + pc * TC_EPI_STRIDE + 2 * lane);
+        atomicAdd((float2*)(D + 2 * ((int64_t)dof + (mflip ? n * n + n - m : q))), make_float2(sc * v.x, sc * v.y));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ kernel --
 // F16: the FP16-split form (32 K per stage, scaled rows: escale per prepared
 // source row, tscale per matrix row at tsoff[g]); otherwise TF32 (16 K per
@@ -386,65 +452,203 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_grouped_tc(
   const bool ok = !s_abort;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    // warp w: TMEM lanes (pairs) 32 (w % 4) .. + 31, columns [w/4 * N/2, + N/2)
-    const int c = 32 * (warp & 3) + lane;
-    const int dof = s_dst[c], fl = s_flg[c];
-    // FP16 split: the pair's source row and each matrix row were scaled by powers of two
-    const float psc = (F16 && s_src[c] >= 0) ? escale[s_src[c]] : 1.f;
-    const float* tsg = F16 ? tscale + tsoff[g] : nullptr;
-    const int half = N >> 1;
-    const int cbeg = (warp >> 2) * half;
-    const bool mflip = ((fl & 1) != 0) != ((fl & 2) != 0);
-    // output coefficient q = n^2 + n + m, tracked incrementally from the first column
-    int q = (nt * TC_NMAX + cbeg) / 2;
-    int n = (int)sqrtf((float)q);
-    if ((n + 1) * (n + 1) <= q) ++n;
-    if (n * n > q) --n;
-    int m = q - n * n - n;
-    for (int col0 = cbeg; col0 < cbeg + half; col0 += 8) {
-      uint32_t v[8];
-      uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col0;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                   : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      // the 4 coefficients of this load: destination index (after the output
-      // reflection) and signed value; -1 marks padding rows
-      int qi[4];
-      float re[4], im[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const bool neg = ((fl & 1) && (m & 1)) != ((fl & 4) && ((n + m) & 1));
-        qi[e] = (dof >= 0 && q < Po) ? (mflip ? n * n + n - m : q) : -1;
-        float sc = neg ? -1.f : 1.f;
-        if (F16 && q < Po) sc *= psc * tsg[2 * q];
-        re[e] = sc * __uint_as_float(v[2 * e]);
-        im[e] = sc * __uint_as_float(v[2 * e + 1]);
-        ++q;
-        if (++m > n) {
-          ++n;
-          m = -n;
-        }
+    tc_epilogue<F16>(tmem, warp, lane, smem, s_src, s_dst, s_flg, escale, tscale, tsoff, g, Po, N, nt, D);
+  } else if (tid == 0) {
+    atomicOr(err, BEM_DEVERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
+}
+
+// ------------------------------------------------- warp-specialised kernel --
+// The same tile (job, rhs) and the same MMAs as k_grouped_tc, with the stage
+// loop run by three roles on NS shared-memory stages and mbarriers alone:
+//   warps 0-3  gather producers: every thread copies 8 of the stage's 1,024
+//              16-byte pieces of prepared rows into the core-matrix layout with
+//              cp.async (zero-filled for padding pairs); after issuing stage
+//              it it waits for its copies of stage it - LAG, fences them to
+//              the async proxy and arrives on that stage's gather barrier;
+//   warp 4     one thread issues the matrix stage's bulk copy on the matrix
+//              barrier (expected bytes);
+//   warp 5     one thread waits for both barriers of a stage, issues its MMAs
+//              and commits them to the stage's release barrier, which the
+//              producers wait on before they refill the stage (NS stages
+//              ahead).
+// All eight warps then run the epilogue.  Every wait is bounded; on expiry
+// the role records the abort, stops issuing, and the CTA drains its own
+// copies and MMAs before it frees tensor memory.
+#define TC_WS_THREADS 256
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool F16, int NS, int LAG>
+__global__ void __launch_bounds__(TC_WS_THREADS, 1) k_grouped_tc_ws(
+    const int4* __restrict__ jobs, const int* __restrict__ grows, const int* __restrict__ gcols,
+    const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
+    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep,
+    int row_floats, int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice,
+    int* err, long long wait_limit, int hold_first_copy, const float* __restrict__ escale,
+    const float* __restrict__ tscale, const int* __restrict__ tsoff) {
+  static_assert(LAG >= 1 && LAG < NS, "the gather lag must leave the MMAs a stage of slack");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_e[NS], bar_t[NS], bar_r[NS];
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_src[TC_M], s_dst[TC_M], s_flg[TC_M];
+
+  const int4 job = jobs[blockIdx.x / nchunk];
+  const int r = blockIdx.x % nchunk;
+  const int g = job.x, p0 = job.y, np = job.z & 255, nt = job.w;
+  const int Po = grows[g], Pi = gcols[g];
+  const int N = tc_ntile_width(2 * Po, nt);
+  constexpr int KSTG = F16 ? 32 : TC_KS;
+  const int nks = (2 * Pi + KSTG - 1) / KSTG;
+  const int ks0 = (job.z >> 8) * kslice, ks1 = min(nks, ks0 + kslice);
+  const int nstage = ks1 - ks0;
+  const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
+  const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
+  float* D = dst + 2 * (int64_t)r * exp_stride;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid < TC_M) {
+    const bool ok = tid < np;
+    s_src[tid] = ok ? prep_row[p0 + tid] + r * rows_per_rhs : -1;
+    s_dst[tid] = ok ? dst_off[p0 + tid] : -1;
+    s_flg[tid] = ok ? (int)pflags[p0 + tid] : 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TC_NMAX));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    for (int i = 0; i < NS; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_e[i])), "r"(TC_M));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_t[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_r[i])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp < 4) {
+    // ---- gather producers: thread t copies items t + 128 q, q = 0..7 ----
+    int issued = 0;
+    for (int it = 0; it < nstage; ++it) {
+      if (s_abort) break;
+      const int st = it % NS;
+      if (it >= NS && !mbar_wait(smem_u32(&bar_r[st]), ((it / NS) - 1) & 1, wait_limit)) {
+        s_abort = 1;
+        break;
       }
-      // two coefficients that land next to each other on a 16-byte boundary go
-      // as one float4 atomic, the others as float2 atomics
+      unsigned char* sEh = smem + st * TC_STAGE_BYTES;
+      unsigned char* sEl = sEh + TC_EBYTES;
+      const int ks = ks0 + it;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (qi[e] < 0) continue;
-        if (e < 3 && qi[e + 1] >= 0 && (qi[e + 1] == qi[e] + 1 || qi[e + 1] == qi[e] - 1)) {
-          const int lo = min(qi[e], qi[e + 1]);
-          float* a = D + 2 * ((int64_t)dof + lo);
-          if (((uintptr_t)a & 15) == 0) {
-            const bool up = qi[e + 1] > qi[e];
-            atomicAdd((float4*)a, up ? make_float4(re[e], im[e], re[e + 1], im[e + 1])
-                                     : make_float4(re[e + 1], im[e + 1], re[e], im[e]));
-            qi[e + 1] = -1;
-            continue;
-          }
-        }
-        atomicAdd((float2*)(D + 2 * ((int64_t)dof + qi[e])), make_float2(re[e], im[e]));
+      for (int q = 0; q < 8; ++q) {
+        const int item = tid + TC_M * q;  // 0..1023
+        const int c = ((item >> 5) & 15) * 8 + (item & 7), quad = (item >> 3) & 3, part = item >> 9;
+        const int row = s_src[c];
+        const float* src = row >= 0
+                               ? prep + (int64_t)row * row_floats + ks * (2 * TC_KS) + part * TC_KS + quad * 4
+                               : prep;
+        const uint32_t dsm = smem_u32((part ? sEl : sEh) + core_off(c, quad * 4, TC_M));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dsm), "l"(src), "r"(row >= 0 ? 16 : 0)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      ++issued;
+      if (it >= LAG) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&bar_e[(it - LAG) % NS]));
       }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int j = max(0, issued - LAG); j < issued; ++j) mbar_arrive(smem_u32(&bar_e[j % NS]));
+  } else if (warp == 4 && lane == 0) {
+    // ---- matrix producer ----
+    int last = -1;  // last stage whose copy was issued
+    for (int it = 0; it < nstage; ++it) {
+      if (s_abort) break;
+      const int st = it % NS;
+      if (it >= NS && !mbar_wait(smem_u32(&bar_r[st]), ((it / NS) - 1) & 1, wait_limit)) {
+        s_abort = 1;
+        break;
+      }
+      // hold_first_copy (diagnostic of the timeout path): stage 0 is never issued
+      if (it == 0 && hold_first_copy) continue;
+      const uint32_t bar = smem_u32(&bar_t[st]);
+      unsigned char* sT = smem + st * TC_STAGE_BYTES + 2 * TC_EBYTES;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tbytes) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sT)),
+                   "l"(Tg + (int64_t)(ks0 + it) * (2 * N * TC_KS)), "r"(tbytes), "r"(bar)
+                   : "memory");
+      last = it;
+    }
+    // the copies still in flight (at most the last NS issued) must land before the CTA ends
+    for (int j = max(0, last - NS + 1); j <= last; ++j) {
+      if (j == 0 && hold_first_copy) continue;
+      if (!mbar_wait(smem_u32(&bar_t[j % NS]), (j / NS) & 1, wait_limit)) s_abort = 1;
+    }
+  } else if (warp == 5 && lane == 0) {
+    // ---- MMA issuer ----
+    const uint32_t idesc = F16 ? instr_desc_f16(N) : instr_desc(N);
+    int committed = 0;
+    for (int it = 0; it < nstage; ++it) {
+      if (s_abort) break;
+      const int st = it % NS;
+      const uint32_t ph = (it / NS) & 1;
+      if (!mbar_wait(smem_u32(&bar_t[st]), ph, wait_limit) || !mbar_wait(smem_u32(&bar_e[st]), ph, wait_limit)) {
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* sEh = smem + st * TC_STAGE_BYTES;
+      const uint32_t e0 = smem_u32(sEh), e1 = smem_u32(sEh + TC_EBYTES), t0 = smem_u32(sEh + 2 * TC_EBYTES);
+#pragma unroll
+      for (int j = 0; j < TC_KS / 8; ++j) {
+        const uint64_t ah = smem_desc(e0 + j * (TC_M / 8) * 256);
+        const uint64_t al = smem_desc(e1 + j * (TC_M / 8) * 256);
+        const uint64_t bh = smem_desc(t0 + j * (N / 8) * 256);
+        const uint64_t bl = smem_desc(t0 + N * TC_KS * 4 + j * (N / 8) * 256);
+        if constexpr (F16) {
+          mma_f16(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
+          mma_f16(tmem, ah, bl, idesc, 1u);
+          mma_f16(tmem, al, bh, idesc, 1u);
+        } else {
+          mma_tf32(tmem, ah, bh, idesc, (it > 0 || j > 0) ? 1u : 0u);
+          if (nprod == 3) {
+            mma_tf32(tmem, ah, bl, idesc, 1u);
+            mma_tf32(tmem, al, bh, idesc, 1u);
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_r[st]))
+                   : "memory");
+      committed = it + 1;
+    }
+    // the last commit arrives once every MMA issued before it has completed
+    if (committed > 0) {
+      const int last = committed - 1;
+      if (!mbar_wait(smem_u32(&bar_r[last % NS]), (last / NS) & 1, wait_limit)) s_abort = 1;
+    }
+    if (committed < nstage) s_abort = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!s_abort) {
+    tc_epilogue<F16>(tmem, warp, lane, smem, s_src, s_dst, s_flg, escale, tscale, tsoff, g, Po, N, nt, D);
   } else if (tid == 0) {
     atomicOr(err, BEM_DEVERR_TIMEOUT);
   }
@@ -496,10 +700,52 @@ __global__ void k_prep(const float* __restrict__ src, int64_t base, int nbox, in
   *(float4*)(o + TC_KS) = lo;
 }
 
-// FP16 split: one warp per row (rhs r0 + rc, reflection f, box b); the row's
-// largest magnitude (reflections only permute and negate) picks the power-of-
-// two scale; per K stage of 32 the row holds [hi 32 | lo 32] halves (128
-// bytes, as a TF32 stage of 16), and escale[row] keeps the inverse scale.
+// FP16 split: one warp per row (rhs r0 + rc, reflection f, box b): row
+// (rc * 8 + f) * nbox + b.  The expansion's largest magnitude (reflections
+// only permute and negate) picks the power-of-two scale; per K stage of 32
+// the row holds [hi 32 | lo 32] halves (128 bytes, as a TF32 stage of 16),
+// every lane producing 4 consecutive values of a stage (8-byte stores of hi
+// and lo); escale[row] keeps the inverse scale.
+__device__ __forceinline__ void prep16_row(const float* __restrict__ src, int64_t base, int nbox, int P, int nks,
+                                           int r, int f, int b, int64_t row, int lane, int64_t exp_stride,
+                                           float* __restrict__ out, float* __restrict__ escale) {
+  const float* sb = src + 2 * ((int64_t)r * exp_stride + base + (int64_t)b * P);
+  float m = 0.f;
+  for (int kr = lane; kr < 2 * P; kr += 32) m = fmaxf(m, fabsf(sb[kr]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  float sc, iv;
+  f16_scale(m, &sc, &iv);
+  if (lane == 0) escale[row] = iv;
+  const int K = 32 * nks;
+  __half* o = (__half*)(out + row * (int64_t)K);
+  for (int k4 = 4 * lane; k4 < K; k4 += 128) {
+    // values k4 .. k4 + 3: (re, im) of coefficients k4 / 2 and k4 / 2 + 1
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int kc = (k4 >> 1) + e;
+      float2 w = make_float2(0.f, 0.f);
+      if (kc < P) {
+        bool neg;
+        const int ki = reflect_index(kc, f, &neg);
+        w = *(const float2*)(sb + 2 * ki);
+        if (neg) w = make_float2(-w.x, -w.y);
+      }
+      v[2 * e] = w.x * sc;
+      v[2 * e + 1] = w.y * sc;
+    }
+    __half hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      hi[e] = __float2half_rn(v[e]);
+      lo[e] = __float2half_rn(v[e] - __half2float(hi[e]));
+    }
+    __half* d = o + (k4 >> 5) * 64 + (k4 & 31);
+    *(uint2*)d = *(const uint2*)hi;
+    *(uint2*)(d + 32) = *(const uint2*)lo;
+  }
+}
+
 __global__ void k_prep16(const float* __restrict__ src, int64_t base, int nbox, int P, int nks, int r0, int nchunk,
                          int64_t exp_stride, float* __restrict__ out, float* __restrict__ escale) {
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -508,27 +754,22 @@ __global__ void k_prep16(const float* __restrict__ src, int64_t base, int nbox, 
   if (row >= nchunk * per_rhs) return;
   const int rc = (int)(row / per_rhs);
   const int f = (int)((row % per_rhs) / nbox), b = (int)(row % nbox);
-  const float* sb = src + 2 * ((int64_t)(r0 + rc) * exp_stride + base + (int64_t)b * P);
-  float m = 0.f;
-  for (int kr = lane; kr < 2 * P; kr += 32) m = fmaxf(m, fabsf(sb[kr]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  float sc, iv;
-  f16_scale(m, &sc, &iv);
-  if (lane == 0) escale[row] = iv;
-  __half* o = (__half*)(out + row * (int64_t)(32 * nks));
-  for (int kr = lane; kr < 32 * nks; kr += 32) {
-    float v = 0.f;
-    if (kr < 2 * P) {
-      bool neg;
-      const int ki = reflect_index(kr >> 1, f, &neg);
-      v = sb[2 * ki + (kr & 1)] * sc;
-      if (neg) v = -v;
-    }
-    const __half hi = __float2half_rn(v);
-    const __half lo = __float2half_rn(v - __half2float(hi));
-    o[(kr >> 5) * 64 + (kr & 31)] = hi;
-    o[(kr >> 5) * 64 + 32 + (kr & 31)] = lo;
-  }
+  prep16_row(src, base, nbox, P, nks, r0 + rc, f, b, row, lane, exp_stride, out, escale);
+}
+
+// the same for the rows some pair reads (list: rows f * nbox + b of one rhs),
+// when the operator's pairs use few of the 8 reflections of each box (M2M:
+// every child box is read once, with the reflection of its octant)
+__global__ void k_prep16_list(const float* __restrict__ src, int64_t base, int nbox, int P, int nks, int r0,
+                              int nchunk, const int* __restrict__ list, int nlist, int64_t exp_stride,
+                              float* __restrict__ out, float* __restrict__ escale) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)nchunk * nlist) return;
+  const int rc = (int)(w / nlist);
+  const int lr = list[w % nlist];
+  const int f = lr / nbox, b = lr % nbox;
+  prep16_row(src, base, nbox, P, nks, r0 + rc, f, b, (int64_t)rc * 8 * nbox + lr, lane, exp_stride, out, escale);
 }
 
 __global__ void k_prep_rows(int np, const int* __restrict__ src_off, const unsigned char* __restrict__ flags,
@@ -575,9 +816,31 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
       k_prep_rows<<<(op.npairs + 255) / 256, 256, 0, s>>>(op.npairs, op.d_src_off, op.d_flags, sl.exp_base, sl.P,
                                                           sl.nbox, op.d_prep_row);
     BEM_CUDA(cudaGetLastError());
+    // the rows the pairs read: when they are under half of all 8 nbox rows,
+    // the FP16 preparation runs over their list alone
+    if (h->tc_fp16 && op.npairs > 0) {
+      std::vector<int> pr(op.npairs);
+      BEM_CUDA(cudaMemcpyAsync(pr.data(), op.d_prep_row, op.npairs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaStreamSynchronize(s));
+      std::sort(pr.begin(), pr.end());
+      pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+      if (2 * (int64_t)pr.size() < (int64_t)8 * sl.nbox) {
+        op.n_prep_list = (int)pr.size();
+        BEM_TRY(bem_alloc(h, &op.d_prep_list, pr.size()));
+        BEM_CUDA(cudaMemcpyAsync(op.d_prep_list, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      }
+    }
   }
   BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_ws<false, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                4 * TC_STAGE_BYTES));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_ws<true, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                4 * TC_STAGE_BYTES));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_ws<false, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * TC_STAGE_BYTES));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_ws<true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * TC_STAGE_BYTES));
   std::vector<int64_t> off(op.ngroups);
   std::vector<int> toff(op.ngroups);
   int64_t tot = 0;
@@ -674,7 +937,12 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
   for (int r0 = 0; r0 < nrhs; r0 += chunk) {
     // up to `chunk` right-hand sides per launch share each matrix stage via L2
     const int nc = std::min(chunk, nrhs - r0);
-    if (h->tc_fp16) {
+    if (h->tc_fp16 && op.n_prep_list > 0) {
+      const int64_t rows = (int64_t)nc * op.n_prep_list;
+      k_prep16_list<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
+          (const float*)src, sl.exp_base, sl.nbox, sl.P, row_floats / (2 * TC_KS), r0, nc, op.d_prep_list,
+          op.n_prep_list, h->exp_total, h->prep, h->prep_scale);
+    } else if (h->tc_fp16) {
       const int64_t rows = (int64_t)nc * 8 * sl.nbox;
       k_prep16<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
           (const float*)src, sl.exp_base, sl.nbox, sl.P, row_floats / (2 * TC_KS), r0, nc, h->exp_total, h->prep,
@@ -690,8 +958,12 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
     // shorter K slices (with 2-4 right-hand sides per launch the extra
     // slices' atomics cost more than the added CTAs give back)
     const bool split = nc == 1 && op.n_tc_jobs_split > 0;
-    auto kern = h->tc_fp16 ? k_grouped_tc<true> : k_grouped_tc<false>;
-    kern<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, TC_SMEM, s>>>(
+    // tc_pipeline: 1 block-synchronous two-stage loop, 2 / 4 warp-specialised with 2 / 4 stages
+    auto kern = h->tc_pipeline == 4   ? (h->tc_fp16 ? k_grouped_tc_ws<true, 4, 2> : k_grouped_tc_ws<false, 4, 2>)
+                : h->tc_pipeline == 2 ? (h->tc_fp16 ? k_grouped_tc_ws<true, 2, 1> : k_grouped_tc_ws<false, 2, 1>)
+                                      : (h->tc_fp16 ? k_grouped_tc<true> : k_grouped_tc<false>);
+    const size_t smem = h->tc_pipeline == 4 ? 4 * TC_STAGE_BYTES : 2 * TC_STAGE_BYTES;
+    kern<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, smem, s>>>(
         split ? op.d_tc_jobs_split : op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
         op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, row_floats, nc, 8 * sl.nbox,
         (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total, h->mode == BEM_MODE_FMM_TF32 ? 1 : 3,

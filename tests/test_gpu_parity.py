@@ -120,6 +120,32 @@ def test_fmm_auto_order_ka5(cuda_ok):
     assert op.info("leaf_level") >= 2
 
 
+@pytest.mark.parametrize("pipeline,ctas", [(1, 0), (2, 0), (4, 0), (2, 4), (1, 6)])
+def test_translation_loops_and_resident_near_field(cuda_ok, pipeline, ctas):
+    """Every translation loop (1: block-synchronous two stages; 2, 4:
+    warp-specialised stages) and the near field from resident CTAs beside the
+    far field (p2p_ctas) give the same operator: against the oracle at the
+    FMM bar, against each other to FP32 summation order, one and three
+    right-hand sides."""
+    V, T = inputs.icosphere(4)
+    n = T.shape[0]
+    k = 5.0
+    x = inputs.random_density(n, 3, seed=12, stream=0)
+    y = inputs.random_density(n, 3, seed=12, stream=1)
+    ref = oracle.apply(V, T, k, x=x, y=y)
+    op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", leaf_level=4, max_nrhs=3, tc_pipeline=pipeline,
+                  p2p_ctas=ctas)
+    z = op.apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, ref) <= 1e-5
+    z1 = op.apply(dev(x[:1]), dev(y[:1])).cpu().numpy()
+    assert rel(z1, ref[:1]) <= 1e-5
+    base = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", leaf_level=4, max_nrhs=3, tc_pipeline=1)
+    zb = base.apply(dev(x), dev(y)).cpu().numpy()
+    assert rel(z, zb) <= 1e-6
+    op.close()
+    base.close()
+
+
 @pytest.mark.parametrize("mode,tol", [("direct64", 1e-10), ("fp64", 1e-5), ("mixed", 1e-5)])
 @pytest.mark.parametrize("nrhs", [5, 6, 7])
 def test_multi_rhs_chunks(cuda_ok, mode, tol, nrhs):
