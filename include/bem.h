@@ -117,7 +117,10 @@ typedef struct {
   int tc_pipeline;  /* mixed modes, the tensor-core translation loop: 1 two stages, all threads gather,
                        synchronise, one thread issues the MMAs; 2 or 4 stages with specialised warps
                        (cp.async gather warps, a bulk-copy thread and an MMA thread, synchronised by
-                       mbarriers alone; 2 stages leave room for two CTAs per SM); 0 = default (2) */
+                       mbarriers alone; 2 stages leave room for two CTAs per SM); 3 persistent, one CTA
+                       per SM walking the job list on a 3-stage ring with two tensor-memory accumulators
+                       (the epilogue of one job overlaps the next); 0 (default) per operator: 3 for
+                       M2M (few long jobs), 2 for M2L and L2L */
   int p2p_ctas;     /* FP32 FMM: > 0 forks the far field before the near field and runs the near field
                        from this many resident CTAs per SM (a work queue over its units), so that the
                        far field's kernels share the SMs with it; 0 (default) runs the near field on

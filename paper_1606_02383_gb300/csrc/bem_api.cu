@@ -146,8 +146,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   if (o.p2p_unit != 16 && o.p2p_unit != 32 && o.p2p_unit != 64)
     return bem_fail(BEM_ERR_INVALID_ARG, "p2p_unit must be 16, 32 or 64");
   if (o.tc_kslice < 2 || o.tc_kslice > 16) return bem_fail(BEM_ERR_INVALID_ARG, "tc_kslice must be in [2, 16]");
-  if (o.tc_pipeline != 0 && o.tc_pipeline != 1 && o.tc_pipeline != 2 && o.tc_pipeline != 4)
-    return bem_fail(BEM_ERR_INVALID_ARG, "tc_pipeline must be 0, 1, 2 or 4");
+  if (o.tc_pipeline < 0 || o.tc_pipeline > 4) return bem_fail(BEM_ERR_INVALID_ARG, "tc_pipeline must be in [0, 4]");
   if (o.p2p_ctas < 0 || o.p2p_ctas > 16) return bem_fail(BEM_ERR_INVALID_ARG, "p2p_ctas must be in [0, 16]");
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -162,7 +161,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->tc_kslice_max = o.tc_kslice;
   h->corr_rules32 = o.corr_rules32 ? 1 : 0;
   h->tc_fp16 = (o.mode == BEM_MODE_FMM_MIXED && o.tc_tf32 == 0) ? 1 : 0;
-  h->tc_pipeline = o.tc_pipeline == 0 ? BEM_TC_PIPELINE_DEFAULT : o.tc_pipeline;
+  h->tc_pipeline = o.tc_pipeline;
   h->p2p_ctas = o.p2p_ctas;
   h->p_min = o.p_min;
   h->p_max = o.p_max;

@@ -109,6 +109,7 @@ __device__ __forceinline__ int reflect_index(int k, int flags, bool* neg) {
 
 // ------------------------------------------------------------------ handle --
 struct GroupedOp {
+  int upward = 0;  // 1: an M2M (child to parent) operator, few long jobs per level
   // For every pair c of group g, with Q_c the signed permutation of the pair's
   // reflection flags (x, y, z bits):
   //   dst[dst_off[c] + .] += Q_c T_g Q_c src[src_off[c] + .]
@@ -154,8 +155,6 @@ struct GroupedOp {
   int n_tc_jobs = 0;
 };
 
-// translation kernel of the mixed modes when bem_options.tc_pipeline is 0
-#define BEM_TC_PIPELINE_DEFAULT 2
 
 struct LevelInfo {
   int nbox = 0;
@@ -207,7 +206,8 @@ struct bem_handle {
   int tc_kslice_max = 16;  // most K stages per tensor-core translation job
   int corr_rules32 = 0;    // mixed modes: non-self near-singular rules summed in FP32
   int tc_fp16 = 0;   // mixed mode: translations as the FP16 split (else 3xTF32)
-  int tc_pipeline = 1;  // translation kernel: 1 block-synchronous, 2 / 4 warp-specialised stages
+  int tc_pipeline = 0;  // translation kernel: 0 per operator (M2M persistent, others 2 stages),
+                        // 1 block-synchronous, 2 / 4 warp-specialised stages, 3 persistent
   int p2p_ctas = 0;     // > 0: near field from this many resident CTAs per SM, beside the far field
   int nsm = 0;          // SMs of the device
   int* p2p_ctr = nullptr;  // [nrhs_max + 2] unit counters of the resident near field

@@ -657,6 +657,300 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_grouped_tc_ws(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
 }
 
+// ------------------------------------------------------- persistent kernel --
+// One CTA per SM walks the job list (virtual job v = blockIdx.x + i gridDim.x,
+// job v / nchunk, rhs v % nchunk) on one ring of NS stages that runs on
+// across job boundaries, with two tensor-memory accumulators so that the
+// epilogue of job i overlaps the stages of job i + 1.  Roles (320 threads):
+//   warps 0-3  gather producers (as k_grouped_tc_ws; the pair rows of the
+//              current job in shared memory, reloaded between jobs behind a
+//              named barrier of these four warps);
+//   warps 4-7  epilogue: warp w owns tensor-memory lanes 32 (w - 4) .. + 31
+//              and runs tc_epilogue's two steps for its 32 pairs through its
+//              own shared tile, then releases the accumulator;
+//   warp 8     one thread issues the matrix stages' bulk copies;
+//   warp 9     one thread issues the MMAs: it waits for an accumulator to be
+//              released, runs the job's stages into it, and commits it.
+// Every wait is bounded; on expiry the role records the abort and stops, and
+// the CTA drains its copies and MMAs before it frees tensor memory.
+#define TC_P_THREADS 320
+#define TC_P_STAGES 3
+#define TC_P_EPI_BYTES (4 * 32 * TC_EPI_STRIDE * 4)
+#define TC_P_SMEM (TC_P_STAGES * TC_STAGE_BYTES + TC_P_EPI_BYTES)
+
+template <bool F16, int NS, int LAG>
+__global__ void __launch_bounds__(TC_P_THREADS, 1) k_grouped_tc_p(
+    const int4* __restrict__ jobs, int njobs, const int* __restrict__ grows, const int* __restrict__ gcols,
+    const int64_t* __restrict__ tcoff, const float* __restrict__ tcB, const int* __restrict__ prep_row,
+    const int* __restrict__ dst_off, const unsigned char* __restrict__ pflags, const float* __restrict__ prep,
+    int row_floats, int nchunk, int rows_per_rhs, float* __restrict__ dst, int64_t exp_stride, int nprod, int kslice,
+    int* err, long long wait_limit, int hold_first_copy, const float* __restrict__ escale,
+    const float* __restrict__ tscale, const int* __restrict__ tsoff) {
+  static_assert(LAG >= 1 && LAG < NS, "the gather lag must leave the MMAs a stage of slack");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_e[NS], bar_t[NS], bar_r[NS], bar_af[2], bar_ae[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_src[TC_M];
+  constexpr int KSTG = F16 ? 32 : TC_KS;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nvirt = njobs * nchunk;
+  // the job of local index i, and its stage count and tile width
+  auto job_of = [&](int i, int4& J, int& r, int& nstage, int& N) -> bool {
+    const int v = blockIdx.x + i * gridDim.x;
+    if (v >= nvirt) return false;
+    J = jobs[v / nchunk];
+    r = v % nchunk;
+    const int g = J.x;
+    N = tc_ntile_width(2 * grows[g], J.w);
+    const int nks = (2 * gcols[g] + KSTG - 1) / KSTG;
+    const int ks0 = (J.z >> 8) * kslice;
+    nstage = min(nks, ks0 + kslice) - ks0;
+    return true;
+  };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(2 * TC_NMAX));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    for (int i = 0; i < NS; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_e[i])), "r"(TC_M));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_t[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_r[i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_af[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_ae[i])), "r"(TC_M));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp < 4) {
+    // ---- gather producers ----
+    // the job loop is uniform over the four warps (named barriers inside):
+    // after an abort the remaining jobs are walked without issuing
+    int it = 0, issued = 0;
+    int4 J;
+    int r, nstage, N;
+    for (int i = 0; job_of(i, J, r, nstage, N); ++i) {
+      const int p0 = J.y, np = J.z & 255;
+      const int ks0 = (J.z >> 8) * kslice;
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // every producer is done with the last job's rows
+      s_src[tid] = tid < np ? prep_row[p0 + tid] + r * rows_per_rhs : -1;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int k = 0; k < nstage; ++k, ++it) {
+        if (s_abort) break;
+        const int st = it % NS;
+        if (it >= NS && !mbar_wait(smem_u32(&bar_r[st]), ((it / NS) - 1) & 1, wait_limit)) {
+          s_abort = 1;
+          break;
+        }
+        unsigned char* sEh = smem + st * TC_STAGE_BYTES;
+        unsigned char* sEl = sEh + TC_EBYTES;
+        const int ks = ks0 + k;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int item = tid + TC_M * q;
+          const int c = ((item >> 5) & 15) * 8 + (item & 7), quad = (item >> 3) & 3, part = item >> 9;
+          const int row = s_src[c];
+          const float* src = row >= 0
+                                 ? prep + (int64_t)row * row_floats + ks * (2 * TC_KS) + part * TC_KS + quad * 4
+                                 : prep;
+          const uint32_t dsm = smem_u32((part ? sEl : sEh) + core_off(c, quad * 4, TC_M));
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dsm), "l"(src), "r"(row >= 0 ? 16 : 0)
+                       : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        ++issued;
+        if (it >= LAG) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(smem_u32(&bar_e[(it - LAG) % NS]));
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int j = max(0, issued - LAG); j < issued; ++j) mbar_arrive(smem_u32(&bar_e[j % NS]));
+  } else if (warp < 8) {
+    // ---- epilogue warps ----
+    const int ew = warp - 4;  // tensor-memory lane quarter
+    float* tile = (float*)(smem + NS * TC_STAGE_BYTES) + ew * 32 * TC_EPI_STRIDE;
+    int4 J;
+    int r, nstage, N;
+    for (int i = 0;; ++i) {
+      // warp-uniform decisions: the tensor-memory loads and shuffles below
+      // need all 32 lanes
+      const int go = __shfl_sync(0xffffffffu, (!s_abort && job_of(i, J, r, nstage, N)) ? 1 : 0, 0);
+      if (!go) break;
+      job_of(i, J, r, nstage, N);
+      const int a = i & 1;
+      int ok = 1;
+      if (lane == 0 && !mbar_wait(smem_u32(&bar_af[a]), (i >> 1) & 1, wait_limit)) {
+        s_abort = 1;
+        ok = 0;
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int g = J.x, p0 = J.y, np = J.z & 255, nt = J.w;
+      const int Po = grows[g];
+      const float* tsg = F16 ? tscale + tsoff[g] : nullptr;
+      float* D = dst + 2 * (int64_t)r * exp_stride;
+      // this lane's pair (the row of the tile it fills)
+      const int c = 32 * ew + lane;
+      const bool pv = c < np;
+      const int my_dst = pv ? dst_off[p0 + c] : -1;
+      const int my_flg = pv ? (int)pflags[p0 + c] : 0;
+      const float my_sc = (F16 && pv) ? escale[prep_row[p0 + c] + r * rows_per_rhs] : 1.f;
+      for (int c0 = 0; c0 < N; c0 += 64) {
+        const int ncol = min(64, N - c0);
+#pragma unroll
+        for (int j = 0; j < 64; j += 8) {
+          if (j < ncol) {
+            uint32_t v[8];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)(a * TC_NMAX + c0 + j);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float* t = tile + lane * TC_EPI_STRIDE + j;
+            *(float4*)t = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                      __uint_as_float(v[3]));
+            *(float4*)(t + 4) = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
+                                            __uint_as_float(v[7]));
+          }
+        }
+        __syncwarp();
+        const int q = (nt * TC_NMAX + c0) / 2 + lane;
+        const bool live = 2 * lane < ncol && q < Po;
+        int n = (int)sqrtf((float)q);
+        if ((n + 1) * (n + 1) <= q) ++n;
+        if (n * n > q) --n;
+        const int m = q - n * n - n;
+        const float ts = (F16 && live) ? tsg[2 * q] : 1.f;
+        for (int pc = 0; pc < 32; ++pc) {
+          const int dof = __shfl_sync(0xffffffffu, my_dst, pc);
+          const int fl = __shfl_sync(0xffffffffu, my_flg, pc);
+          const float psc = __shfl_sync(0xffffffffu, my_sc, pc);
+          if (dof < 0 || !live) continue;
+          const bool neg = ((fl & 1) && (m & 1)) != ((fl & 4) && ((n + m) & 1));
+          const bool mflip = ((fl & 1) != 0) != ((fl & 2) != 0);
+          float sc = neg ? -1.f : 1.f;
+          if (F16) sc *= psc * ts;
+          const float2 v = *(const float2*)(tile + pc * TC_EPI_STRIDE + 2 * lane);
+          atomicAdd((float2*)(D + 2 * ((int64_t)dof + (mflip ? n * n + n - m : q))),
+                    make_float2(sc * v.x, sc * v.y));
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_ae[a]));
+    }
+  } else if (warp == 8 && lane == 0) {
+    // ---- matrix producer ----
+    int it = 0, last = -1;
+    int4 J;
+    int r, nstage, N;
+    for (int i = 0; !s_abort && job_of(i, J, r, nstage, N); ++i) {
+      const int g = J.x, nt = J.w;
+      const int nks = (2 * gcols[g] + KSTG - 1) / KSTG;
+      const int ks0 = (J.z >> 8) * kslice;
+      const float* Tg = tcB + tcoff[g] + (int64_t)nt * nks * (2 * TC_NMAX * TC_KS);
+      const uint32_t tbytes = (uint32_t)(2 * N * TC_KS * 4);
+      for (int k = 0; k < nstage; ++k, ++it) {
+        if (s_abort) break;
+        const int st = it % NS;
+        if (it >= NS && !mbar_wait(smem_u32(&bar_r[st]), ((it / NS) - 1) & 1, wait_limit)) {
+          s_abort = 1;
+          break;
+        }
+        if (it == 0 && hold_first_copy) continue;  // diagnostic of the timeout path
+        const uint32_t bar = smem_u32(&bar_t[st]);
+        unsigned char* sT = smem + st * TC_STAGE_BYTES + 2 * TC_EBYTES;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tbytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(sT)),
+                     "l"(Tg + (int64_t)(ks0 + k) * (2 * N * TC_KS)), "r"(tbytes), "r"(bar)
+                     : "memory");
+        last = it;
+      }
+    }
+    for (int j = max(0, last - NS + 1); j <= last; ++j) {
+      if (j == 0 && hold_first_copy) continue;
+      if (!mbar_wait(smem_u32(&bar_t[j % NS]), (j / NS) & 1, wait_limit)) s_abort = 1;
+    }
+  } else if (warp == 9 && lane == 0) {
+    // ---- MMA issuer ----
+    int it = 0, lastc = -1;  // stage of the last commit
+    int4 J;
+    int r, nstage, N;
+    for (int i = 0; !s_abort && job_of(i, J, r, nstage, N); ++i) {
+      const int a = i & 1;
+      if (i >= 2 && !mbar_wait(smem_u32(&bar_ae[a]), ((i >> 1) - 1) & 1, wait_limit)) {
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = F16 ? instr_desc_f16(N) : instr_desc(N);
+      const uint32_t acc = tmem + (uint32_t)(a * TC_NMAX);
+      bool done = true;
+      for (int k = 0; k < nstage; ++k, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (s_abort || !mbar_wait(smem_u32(&bar_t[st]), ph, wait_limit) ||
+            !mbar_wait(smem_u32(&bar_e[st]), ph, wait_limit)) {
+          s_abort = 1;
+          done = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* sEh = smem + st * TC_STAGE_BYTES;
+        const uint32_t e0 = smem_u32(sEh), e1 = smem_u32(sEh + TC_EBYTES), t0 = smem_u32(sEh + 2 * TC_EBYTES);
+#pragma unroll
+        for (int j = 0; j < TC_KS / 8; ++j) {
+          const uint64_t ah = smem_desc(e0 + j * (TC_M / 8) * 256);
+          const uint64_t al = smem_desc(e1 + j * (TC_M / 8) * 256);
+          const uint64_t bh = smem_desc(t0 + j * (N / 8) * 256);
+          const uint64_t bl = smem_desc(t0 + N * TC_KS * 4 + j * (N / 8) * 256);
+          if constexpr (F16) {
+            mma_f16(acc, ah, bh, idesc, (k > 0 || j > 0) ? 1u : 0u);
+            mma_f16(acc, ah, bl, idesc, 1u);
+            mma_f16(acc, al, bh, idesc, 1u);
+          } else {
+            mma_tf32(acc, ah, bh, idesc, (k > 0 || j > 0) ? 1u : 0u);
+            if (nprod == 3) {
+              mma_tf32(acc, ah, bl, idesc, 1u);
+              mma_tf32(acc, al, bh, idesc, 1u);
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar_r[st]))
+                     : "memory");
+        lastc = it;
+      }
+      if (!done) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_af[a]))
+                   : "memory");
+    }
+    // the last commit arrives once every MMA issued before it has completed
+    if (lastc >= 0 && !mbar_wait(smem_u32(&bar_r[lastc % NS]), (lastc / NS) & 1, wait_limit)) s_abort = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_abort && tid == 0) atomicOr(err, BEM_DEVERR_TIMEOUT);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_NMAX));
+}
+
 // ------------------------------------------------------ source preparation --
 // For rhs r0 + rc (rc < nchunk), every box of the source level and every
 // reflection f (8), a row of 2 R2 floats: row ((rc * 8 + f) * nbox + b) holds
@@ -841,6 +1135,10 @@ int bem_build_tc(bem_handle* h, GroupedOp& op, int src_level, cudaStream_t s) {
                                 2 * TC_STAGE_BYTES));
   BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_ws<true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 2 * TC_STAGE_BYTES));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_p<false, TC_P_STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TC_P_SMEM));
+  BEM_CUDA(cudaFuncSetAttribute(k_grouped_tc_p<true, TC_P_STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TC_P_SMEM));
   std::vector<int64_t> off(op.ngroups);
   std::vector<int> toff(op.ngroups);
   int64_t tot = 0;
@@ -958,11 +1256,29 @@ int bem_run_grouped_tc(bem_handle* h, GroupedOp& op, const void* src, void* dst,
     // shorter K slices (with 2-4 right-hand sides per launch the extra
     // slices' atomics cost more than the added CTAs give back)
     const bool split = nc == 1 && op.n_tc_jobs_split > 0;
+    // the loop: the handle's choice, or per operator (measured: the persistent
+    // kernel on the few long M2M jobs, two warp-specialised stages elsewhere)
+    const int pipe = h->tc_pipeline > 0 ? h->tc_pipeline : (op.upward ? 3 : 2);
+    if (pipe == 3) {
+      // persistent: one CTA per SM walks the job list
+      const int njobs = split ? op.n_tc_jobs_split : op.n_tc_jobs;
+      const int grid = (int)std::min<int64_t>((int64_t)njobs * nc, std::max(h->nsm, 1));
+      auto pk = h->tc_fp16 ? k_grouped_tc_p<true, TC_P_STAGES, 1> : k_grouped_tc_p<false, TC_P_STAGES, 1>;
+      pk<<<grid, TC_P_THREADS, TC_P_SMEM, s>>>(
+          split ? op.d_tc_jobs_split : op.d_tc_jobs, njobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
+          op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, row_floats, nc, 8 * sl.nbox,
+          (float*)dst + 2 * (int64_t)r0 * h->exp_total, h->exp_total, h->mode == BEM_MODE_FMM_TF32 ? 1 : 3,
+          split ? op.tc_kslice_split : op.tc_kslice, h->d_err, h->tc_wait_limit, h->tc_hold_first_copy,
+          h->prep_scale, op.tscale, op.d_tsoff);
+      BEM_CUDA(cudaGetLastError());
+      *launches += 2;
+      continue;
+    }
     // tc_pipeline: 1 block-synchronous two-stage loop, 2 / 4 warp-specialised with 2 / 4 stages
-    auto kern = h->tc_pipeline == 4   ? (h->tc_fp16 ? k_grouped_tc_ws<true, 4, 2> : k_grouped_tc_ws<false, 4, 2>)
-                : h->tc_pipeline == 2 ? (h->tc_fp16 ? k_grouped_tc_ws<true, 2, 1> : k_grouped_tc_ws<false, 2, 1>)
-                                      : (h->tc_fp16 ? k_grouped_tc<true> : k_grouped_tc<false>);
-    const size_t smem = h->tc_pipeline == 4 ? 4 * TC_STAGE_BYTES : 2 * TC_STAGE_BYTES;
+    auto kern = pipe == 4   ? (h->tc_fp16 ? k_grouped_tc_ws<true, 4, 2> : k_grouped_tc_ws<false, 4, 2>)
+                : pipe == 2 ? (h->tc_fp16 ? k_grouped_tc_ws<true, 2, 1> : k_grouped_tc_ws<false, 2, 1>)
+                            : (h->tc_fp16 ? k_grouped_tc<true> : k_grouped_tc<false>);
+    const size_t smem = pipe == 4 ? 4 * TC_STAGE_BYTES : 2 * TC_STAGE_BYTES;
     kern<<<(split ? op.n_tc_jobs_split : op.n_tc_jobs) * nc, TC_THREADS, smem, s>>>(
         split ? op.d_tc_jobs_split : op.d_tc_jobs, op.d_group_rows, op.d_group_cols, op.d_tc_off, op.tcA,
         op.d_prep_row, op.d_dst_off, op.d_flags, h->prep, row_floats, nc, 8 * sl.nbox,

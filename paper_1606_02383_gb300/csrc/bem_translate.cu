@@ -780,6 +780,7 @@ int bem_build_far_field(bem_handle* h, cudaStream_t s) {
   if (!f64) {
     for (int l = 2; l <= L; ++l) BEM_TRY(bem_build_tc(h, h->m2l[l], l, s));
     for (int l = 2; l < L; ++l) {
+      h->m2m[l].upward = 1;
       BEM_TRY(bem_build_tc(h, h->m2m[l], l + 1, s));
       BEM_TRY(bem_build_tc(h, h->l2l[l], l, s));
     }

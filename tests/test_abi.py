@@ -101,7 +101,7 @@ def test_option_checks_without_gpu():
     from paper_1606_02383_gb300.operator import _options
     for kw, word in (({"leaf_level": -3}, b"leaf_level"), ({"p2p_unit": 48}, b"p2p_unit"),
                      ({"tc_kslice": 1}, b"tc_kslice"), ({"tc_kslice": 17}, b"tc_kslice"),
-                     ({"tc_pipeline": 3}, b"tc_pipeline")):
+                     ({"tc_pipeline": 5}, b"tc_pipeline")):
         opt = _options(**kw)
         rc = lib.bem_setup(ctypes.byref(mesh), 1.0, 8, 1e-5, ctypes.byref(opt), None, ctypes.byref(h))
         assert rc == _lib.BEM_ERR_INVALID_ARG, kw

@@ -120,10 +120,10 @@ def test_fmm_auto_order_ka5(cuda_ok):
     assert op.info("leaf_level") >= 2
 
 
-@pytest.mark.parametrize("pipeline,ctas", [(1, 0), (2, 0), (4, 0), (2, 4), (1, 6)])
+@pytest.mark.parametrize("pipeline,ctas", [(1, 0), (2, 0), (3, 0), (4, 0), (2, 4), (3, 6)])
 def test_translation_loops_and_resident_near_field(cuda_ok, pipeline, ctas):
     """Every translation loop (1: block-synchronous two stages; 2, 4:
-    warp-specialised stages) and the near field from resident CTAs beside the
+    warp-specialised stages; 3: persistent) and the near field from resident CTAs beside the
     far field (p2p_ctas) give the same operator: against the oracle at the
     FMM bar, against each other to FP32 summation order, one and three
     right-hand sides."""

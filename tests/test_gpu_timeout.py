@@ -25,13 +25,16 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def test_expired_wait_reports_timeout_and_handle_recovers(cuda_ok):
+@pytest.mark.parametrize("pipeline", [1, 2, 3, 4])
+def test_expired_wait_reports_timeout_and_handle_recovers(cuda_ok, pipeline):
+    """Every translation loop (block-synchronous, warp-specialised with 2 and
+    4 stages, persistent) takes the same bounded exit."""
     V, T = inputs.icosphere(3)
     n, k = T.shape[0], 1.0
     x = inputs.random_density(n, 1, seed=4, stream=0)
     y = inputs.random_density(n, 1, seed=4, stream=1)
     ref = oracle.apply(V, T, k, x=x, y=y)
-    op = Operator(V, T, k, p=10, mode="mixed", leaf_level=3)
+    op = Operator(V, T, k, p=10, mode="mixed", leaf_level=3, tc_pipeline=pipeline)
     lib = _lib.load()
     xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
 
