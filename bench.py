@@ -418,10 +418,10 @@ def run_ours(args, world, rank, local):
         work = info["p2p_pairs"] * 3 * P2P_FLOPS_PER_EVAL  # per launch (one launch per apply)
         achieved = work / (per_launch_ms * 1e-3) / 1e12
         # DRAM bytes per launch from an ncu capture of this kernel on the 81,920-triangle
-        # sphere at ka = 10 (dram__bytes_read + write = 6.779648 MB for 263,562,360
+        # sphere at ka = 10 (dram__bytes_read + write = 6.980864 MB for 263,562,360
         # evaluations), scaled by the evaluations of this launch: the traffic is the
         # sources, targets and densities read once, which grow with N as the work does
-        traffic = 6.779648e6 * (info["p2p_pairs"] * 3) / 263562360.0
+        traffic = 6.980864e6 * (info["p2p_pairs"] * 3) / 263562360.0
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
                 "traffic_source": "ncu dram bytes of the same kernel at N = 81,920 (ka = 10), scaled by evaluations",
@@ -469,7 +469,7 @@ def run_ours(args, world, rank, local):
         rule = "%s BF16 %.0f TFLOP/s x 1.1/2.25 = TF32 %.0f, / 3 for 3xTF32" % (
             peak_src, float(peaks.get("bf16_tflops", 1900.0)), tf32_peak)
         probe_txt = "bem_peak_probe: tcgen05 TF32 MMAs, M=128 N=256 K=8, %.0f TFLOP/s, / 3"
-    roof_m2l = {"bound": "tensor", "kernel": "k_grouped_tc (M2L, all levels, with k_prep)",
+    roof_m2l = {"bound": "tensor", "kernel": "k_grouped_tc_ws (M2L, all levels, with k_prep16)",
                 "form": "FP16 split" if fp16_form else "3xTF32",
                 "achieved": m2l_achieved, "peak": tf32_peak / 3.0, "unit": "TFLOP/s",
                 "frac": m2l_achieved / (tf32_peak / 3.0), "traffic": None,
