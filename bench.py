@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
-    ap.add_argument("--workload", choices=["headline", "precision", "batching", "large", "differentiation"],
+    ap.add_argument("--workload", choices=["headline", "precision", "batching", "large", "differentiation", "topology"],
                     default="headline", help="headline = the metric above; the others are the remaining "
                     "configurations (one JSON line each, not the headline metric)")
     a = ap.parse_args()
@@ -609,6 +609,89 @@ def isosurface_timings(warm):
     return out
 
 
+def topology_iteration(steps, warm):
+    """One iteration of the optimisation loop of Section 2.5, every step on the
+    GPU through the library: the body {phi > 0} of the differentiation
+    workload's level set on a 64^3 lattice over [-2, 2]^3 (phi = the Gaussian
+    sum minus the workload's level, clamped to [-1, 1]); its boundary
+    (bem_isosurface); the operator on that mesh (k = 3, mixed, eps 1e-5); the
+    state and adjoint chain for f = 1/2 sum |p|^2 at 4 observers 5 away, with
+    a plane-wave incident field; the topological derivative on the lattice
+    nodes in the fluid (phi <= 0; the body side is outside the path and is
+    taken as 0); one level-set step (F scaled by 1 / max |T|); the new
+    boundary.  Each timed iteration starts from the same phi."""
+    import torch
+    from paper_1606_02383_gb300 import inputs
+    from paper_1606_02383_gb300.operator import Operator, isosurface, levelset_step
+    n, k = 64, 3.0
+    phi0, lo, h = inputs.level_set_function(0, 20, n)
+    t = inputs.level_set_level(0, 20, n)
+    phi = torch.from_numpy(np.clip(phi0 - t, -1.0, 1.0)).cuda()
+    x = torch.linspace(-2.0, 2.0, n, dtype=torch.float64, device="cuda")
+    X, Y, Z = torch.meshgrid(x, x, x, indexing="ij")
+    lattice = torch.stack([X, Y, Z], -1).reshape(-1, 3)
+    obs = np.array([[5.0, 0, 0], [-5.0, 0, 0], [0, 0, 5.0], [0, 0, -5.0]])
+    inc_obs = np.exp(1j * k * obs[:, 2])
+    dt, tau, L, phi_bar = 0.1, 1e-3, 4.0, -1.0
+    out = {}
+
+    def iteration():
+        tm = {}
+
+        def mark(name, t0):
+            torch.cuda.synchronize()
+            tm[name] = time.perf_counter() - t0
+            return time.perf_counter()
+
+        t0 = time.perf_counter()
+        Vd, Td = isosurface(phi, (-2.0, -2.0, -2.0), h, 0.0)
+        t0 = mark("isosurface_s", t0)
+        V, T = Vd.cpu().numpy(), Td.cpu().numpy()
+        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", max_nrhs=2)
+        t0 = mark("setup_s", t0)
+        cen = torch.from_numpy(inputs.centroids(V, T)).cuda()
+        b = torch.exp(1j * k * cen[:, 2])[None, :]
+        chain = op.state_and_adjoint(b, obs, inc_obs, tol=1e-6)
+        t0 = mark("chain_s", t0)
+        # lattice nodes in the fluid, a thin band at the boundary left out (the
+        # fields are evaluated off the surface)
+        fluid = (phi.reshape(-1) <= -0.02).nonzero().reshape(-1)
+        pts = lattice[fluid].contiguous()
+        inc = torch.exp(1j * k * pts[:, 2])
+        inc4 = torch.stack([inc, 0 * inc, 0 * inc, 1j * k * inc], dim=1)
+        Tv = op.topological_derivative(pts, chain, obs, inc4)
+        t0 = mark("topological_derivative_s", t0)
+        T_omega = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+        T_omega[fluid] = Tv
+        T_omega = T_omega.reshape(n, n, n)
+        C = 1.0 / float(T_omega.abs().max())
+        new, its, rel = levelset_step(phi, T_omega, torch.zeros_like(T_omega), h, dt, C, tau, L, phi_bar, tol=1e-10)
+        t0 = mark("levelset_step_s", t0)
+        V2, T2 = isosurface(new, (-2.0, -2.0, -2.0), h, 0.0)
+        mark("isosurface_new_s", t0)
+        op.close()
+        return tm, {"triangles": int(T.shape[0]), "fluid_points": int(fluid.numel()),
+                    "iterations_state_adjoint": list(chain["iterations"]), "levelset_cg_iterations": its,
+                    "levelset_relres": rel, "triangles_new": int(T2.shape[0]),
+                    "body_nodes_before": int((phi > 0).sum()), "body_nodes_after": int((new > 0).sum())}
+
+    for _ in range(max(warm, 1)):
+        iteration()
+    times = []
+    info = None
+    for _ in range(steps):
+        tm, info = iteration()
+        times.append(tm)
+    total = [sum(tm.values()) for tm in times]
+    med = statistics.median(total)
+    out.update({"metric": "topology-optimisation iterations/sec (mesh, setup, state+adjoint chain, T on a 64^3 "
+                          "lattice, level-set step, new mesh), 30,004-triangle level-set body, k=3",
+                "value": 1.0 / med, "unit": "iterations/s", "s_per_iteration": med,
+                "stages_s_median": {kk: statistics.median([tm[kk] for tm in times]) for kk in times[0]},
+                "iteration": info})
+    return out
+
+
 def run_other(args):
     """The configurations besides the headline, one JSON line each."""
     import torch
@@ -818,6 +901,8 @@ def run_other(args):
                      "gmres": {"tol": 1e-5, "iters": iters, "relres": float(relres[0]), "seconds": ts},
                      "cpu_baseline": {"value": (2000 / n) / tor, "unit": "matvecs/s", "kind": "oracle",
                                       "cores": oracle.num_threads(), "sample": "2,000 rows, extrapolated"}})
+    elif w == "topology":
+        line.update(topology_iteration(steps, warm))
     else:  # differentiation
         V, T = inputs.level_set_mesh(0)
         n, k = T.shape[0], 3.0

@@ -368,6 +368,29 @@ int bem_topological_field(bem_handle* h, int dtype, const void* p, const void* p
                           const double* incident, double c1, double c2, double* T, void* stream);
 
 /*
+ * bem_levelset_step -- one step of the level-set update of Section 2.4 on a
+ * lattice of n0 x n1 x n2 nodes with spacing h (the lattice that carries phi
+ * and the topological derivatives):
+ *   d phi / dt = F + tau L^2 lap phi,  F = -C T_omega where phi <= 0 (fluid),
+ *   F = C T_omegac where phi > 0 (body),  phi = phi_bar on the lattice boundary,
+ * discretised with Q1 elements on the voxels, implicit in the diffusion and
+ * explicit in F:  (M / dt + tau L^2 K) phi_new = M (phi / dt + F) on the
+ * interior nodes, then phi_new clamped to [-1, 1].  The interior system is
+ * solved by matrix-free conjugate gradients (27-point stencil) in FP64,
+ * starting from phi, to ||r|| <= tol ||rhs||.
+ *   phi, t_omega, t_omegac : FP64 [n0][n1][n2] (device), node (i, j, k) at
+ *                            i n1 n2 + j n2 + k.
+ *   phi_out                : FP64 [n0][n1][n2] (device), may not alias phi.
+ *   iters_out, relres_out  : (host, nullable) CG iterations and final relative residual.
+ * Returns BEM_ERR_NOT_CONVERGED (phi_out holds the last iterate, clamped) when
+ * max_iter is reached.  Allocates 9 n0 n1 n2 doubles stream-ordered and
+ * synchronises `stream` every 8 iterations to read the residual.
+ */
+int bem_levelset_step(int n0, int n1, int n2, const double* phi, const double* t_omega, const double* t_omegac,
+                      double h, double dt, double C, double tau, double L, double phi_bar, double tol, int max_iter,
+                      double* phi_out, int* iters_out, double* relres_out, void* stream);
+
+/*
  * bem_isosurface -- the boundary {phi = t} of the level-set region {phi > t}
  * as a closed triangle mesh (Section 2.4: the elastic body is where phi > 0,
  * the fluid where phi <= 0, and the boundary is phi = 0), by marching

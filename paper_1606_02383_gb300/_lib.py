@@ -55,7 +55,7 @@ EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gm
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
            "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field",
-           "bem_setup_batch_each", "bem_state_adjoint", "bem_topological_field")
+           "bem_setup_batch_each", "bem_state_adjoint", "bem_topological_field", "bem_levelset_step")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -133,13 +133,16 @@ def load(path: str | None = None):
                                       ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double), vp]
     lib.bem_topological_field.argtypes = [vp, i, vp, vp, i, vp, vp, i64, vp, vp, ctypes.c_double, ctypes.c_double,
                                           vp, vp]
+    d = ctypes.c_double
+    lib.bem_levelset_step.argtypes = [i, i, i, vp, vp, vp, d, d, d, d, d, d, d, i, vp, ctypes.POINTER(i),
+                                      ctypes.POINTER(d), vp]
     lib.bem_last_error.restype = ctypes.c_char_p
     for f in ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gmres_solve", "bem_info",
               "bem_profile", "bem_profile_read", "bem_apply_noalloc", "bem_grad", "bem_setup_batch",
               "bem_apply_batch", "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_peak_probe",
               "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
               "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field", "bem_setup_batch_each",
-              "bem_state_adjoint", "bem_topological_field"):
+              "bem_state_adjoint", "bem_topological_field", "bem_levelset_step"):
         getattr(lib, f).restype = i
     _lib = lib
     return lib

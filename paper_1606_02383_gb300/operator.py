@@ -376,6 +376,31 @@ def isosurface(phi, lo, h, t=0.0):
     return V[:int(counts[0])], T[:int(counts[1])]
 
 
+def levelset_step(phi, t_omega, t_omegac, h, dt, C, tau, L, phi_bar, tol=1e-13, max_iter=10000,
+                  raise_on_fail=True):
+    """One step of the level-set update of Section 2.4 (see include/bem.h,
+    bem_levelset_step) on CUDA float64 tensors of the lattice's shape.
+    Returns (phi_new, iterations, relres)."""
+    ph = torch.as_tensor(phi).to("cuda", torch.float64).contiguous()
+    if ph.dim() != 3:
+        raise ValueError("phi must be a 3-D lattice")
+    ti = torch.as_tensor(t_omega).to("cuda", torch.float64).contiguous()
+    to = torch.as_tensor(t_omegac).to("cuda", torch.float64).contiguous()
+    if ti.shape != ph.shape or to.shape != ph.shape:
+        raise ValueError("T_omega and T_omegac must have phi's shape")
+    out = torch.empty_like(ph)
+    lib = _lib.load()
+    iters = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    n0, n1, n2 = ph.shape
+    rc = lib.bem_levelset_step(n0, n1, n2, ph.data_ptr(), ti.data_ptr(), to.data_ptr(), float(h), float(dt), float(C),
+                               float(tau), float(L), float(phi_bar), float(tol), int(max_iter), out.data_ptr(),
+                               ctypes.byref(iters), ctypes.byref(rel), _stream())
+    if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
+        _lib.check(rc)
+    return out, int(iters.value), float(rel.value)
+
+
 def _gmres_driver_flags(driver):
     flags = {"graph": 0, "graph_only": _lib.BEM_GMRES_GRAPH_ONLY, "host": _lib.BEM_GMRES_HOST_LOOP}
     if driver not in flags:

@@ -78,6 +78,16 @@ def test_sync_and_wait_limit_reject_null_handles():
     assert lib.bem_set_wait_limit(None, 0, 0) == _lib.BEM_ERR_INVALID_ARG
 
 
+def test_levelset_step_rejects_bad_arguments():
+    lib = _lib.load()
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    assert lib.bem_levelset_step(0, 4, 4, None, None, None, 0.1, 0.1, 1.0, 1.0, 1.0, -0.5, 1e-10, 10, None,
+                                 ctypes.byref(it), ctypes.byref(rel), None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_levelset_step(4, 4, 4, None, None, None, 0.1, 0.1, 1.0, 1.0, 1.0, -0.5, 1e-10, 10, None,
+                                 ctypes.byref(it), ctypes.byref(rel), None) == _lib.BEM_ERR_INVALID_ARG
+
+
 def test_chain_calls_reject_null_handles():
     lib = _lib.load()
     it = (ctypes.c_int * 2)()
