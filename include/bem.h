@@ -125,6 +125,9 @@ typedef struct {
                        from this many resident CTAs per SM (a work queue over its units), so that the
                        far field's kernels share the SMs with it; 0 (default) runs the near field on
                        the whole grid first and the far field after it */
+  int p2p_stage;    /* FP32 FMM: 1 stages the near list's source elements in shared memory (per warp,
+                       two buffers of 32 elements filled by cp.async while the other is summed);
+                       0 (default) loads them from global memory in the loop */
 } bem_options;
 
 /*

@@ -163,6 +163,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->tc_fp16 = (o.mode == BEM_MODE_FMM_MIXED && o.tc_tf32 == 0) ? 1 : 0;
   h->tc_pipeline = o.tc_pipeline;
   h->p2p_ctas = o.p2p_ctas;
+  h->p2p_stage = o.p2p_stage ? 1 : 0;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
   for (int l = 0; l <= BEM_MAXLEV; ++l) {

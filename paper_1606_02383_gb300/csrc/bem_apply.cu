@@ -187,6 +187,51 @@ __device__ __forceinline__ void p2p_self_pair(float4 t, const float4* __restrict
 // FP32: NR right-hand sides r0 + NR blockIdx.y + [0, NR) per warp, sharing
 // the kernel values of every point (packed f32x2 arithmetic, two targets per
 // lane).
+// The end of a unit: take the self pair back out, sum the slices, write
+template <int NR>
+__device__ __forceinline__ void p2p_finish32(int r, int64_t nt, float k, int tfirst, int pi, int np2, int split,
+                                             bool two, float4 ta, float4 tb, const float4* __restrict__ src,
+                                             const float4* __restrict__ dr, f32x2 (&are)[NR], f32x2 (&aim)[NR],
+                                             double* __restrict__ zn) {
+  // The pair of a target with itself went through the loop (its own leaf is
+  // in its near list); the near-singular correction carries the whole exact
+  // self term, so the lane that writes the result takes it out again: the
+  // same operations on the same values (FP32 rounding and all), so the FP32
+  // cancellation of (y - x).n on the element's own plane leaves no trace.
+  if (split == 0) {
+    const int ia = tfirst + pi;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      float ar, ai, br = 0.f, bi = 0.f;
+      p2p_self_pair(ta, src + 3 * (int64_t)ia, dr[(int64_t)j * nt + ia], k, ar, ai);
+      if (two) p2p_self_pair(tb, src + 3 * (int64_t)(ia + np2), dr[(int64_t)j * nt + ia + np2], k, br, bi);
+      are[j] = sub2(are[j], pk2(ar, br));
+      aim[j] = sub2(aim[j], pk2(ai, bi));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    float a_re, b_re, a_im, b_im;
+    upk2(are[j], a_re, b_re);
+    upk2(aim[j], a_im, b_im);
+    for (int o = np2; o < 32; o <<= 1) {
+      a_re += __shfl_xor_sync(0xffffffffu, a_re, o);
+      a_im += __shfl_xor_sync(0xffffffffu, a_im, o);
+      b_re += __shfl_xor_sync(0xffffffffu, b_re, o);
+      b_im += __shfl_xor_sync(0xffffffffu, b_im, o);
+    }
+    if (split == 0) {
+      int64_t o = 2 * ((int64_t)(r + j) * nt + tfirst + pi);
+      zn[o] = (double)a_re;
+      zn[o + 1] = (double)a_im;
+      if (two) {
+        zn[o + 2 * np2] = (double)b_re;
+        zn[o + 2 * np2 + 1] = (double)b_im;
+      }
+    }
+  }
+}
+
 // one work unit u of the FP32 near field for right-hand sides r .. r + NR - 1
 template <int NR>
 __device__ __forceinline__ void p2p_unit32(int u, int r, int64_t nt, float k, const int4* __restrict__ units,
@@ -233,45 +278,8 @@ __device__ __forceinline__ void p2p_unit32(int u, int r, int64_t nt, float k, co
       for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
     }
   }
-  // The pair of a target with itself went through the loop (its own leaf is
-  // in its near list); the near-singular correction carries the whole exact
-  // self term, so the lane that writes the result takes it out again: the
-  // same operations on the same values (FP32 rounding and all), so the FP32
-  // cancellation of (y - x).n on the element's own plane leaves no trace.
-  if (split == 0) {
-    const int ia = tfirst + pi;
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      float ar, ai, br = 0.f, bi = 0.f;
-      p2p_self_pair(ta, src + 3 * (int64_t)ia, dr[(int64_t)j * nt + ia], k, ar, ai);
-      if (two) p2p_self_pair(tb, src + 3 * (int64_t)(ia + np2), dr[(int64_t)j * nt + ia + np2], k, br, bi);
-      are[j] = sub2(are[j], pk2(ar, br));
-      aim[j] = sub2(aim[j], pk2(ai, bi));
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    float a_re, b_re, a_im, b_im;
-    upk2(are[j], a_re, b_re);
-    upk2(aim[j], a_im, b_im);
-    for (int o = np2; o < 32; o <<= 1) {
-      a_re += __shfl_xor_sync(0xffffffffu, a_re, o);
-      a_im += __shfl_xor_sync(0xffffffffu, a_im, o);
-      b_re += __shfl_xor_sync(0xffffffffu, b_re, o);
-      b_im += __shfl_xor_sync(0xffffffffu, b_im, o);
-    }
-    if (split == 0) {
-      int64_t o = 2 * ((int64_t)(r + j) * nt + tfirst + pi);
-      zn[o] = (double)a_re;
-      zn[o + 1] = (double)a_im;
-      if (two) {
-        zn[o + 2 * np2] = (double)b_re;
-        zn[o + 2 * np2 + 1] = (double)b_im;
-      }
-    }
-  }
+  p2p_finish32<NR>(r, nt, k, tfirst, pi, np2, split, two, ta, tb, src, dr, are, aim, zn);
 }
-
 
 template <int NR>
 __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_t nt, int r0, float k,
@@ -288,6 +296,148 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32(int nunits, int64_
   const int u = blockIdx.x * P2P_WARPS + (threadIdx.x >> 5);
   if (u >= nunits) return;
   p2p_unit32<NR>(u, r0 + blockIdx.y * NR, nt, k, units, u_ptr, u_src, u_shift, bstart, bend, tgt, src, dens, zn);
+}
+
+// The same unit with the near list's source elements staged in shared memory:
+// the list's elements, leaf after leaf, are cut into chunks of 32; lane j of
+// the warp copies element j of a chunk (its three points, its leaf's centre
+// offset and its NR densities, 16-byte cp.async pieces) into one of the
+// warp's two buffers, and the lanes evaluate the other buffer meanwhile, so
+// the loads of chunk c + 1 are in flight while chunk c is summed.
+#define P2P_CH 32
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+template <int NR>
+__device__ __forceinline__ void p2p_unit32_staged(int u, int r, int64_t nt, float k, const int4* __restrict__ units,
+                                                  const int* __restrict__ u_ptr, const int* __restrict__ u_src,
+                                                  const float4* __restrict__ u_shift, const int* __restrict__ bstart,
+                                                  const int* __restrict__ bend, const float4* __restrict__ tgt,
+                                                  const float4* __restrict__ src, const float4* __restrict__ dens,
+                                                  float4* buf, double* __restrict__ zn) {
+  constexpr int REC = 4 + NR;  // q0, q1, q2, leaf offset, densities
+  const int lane = threadIdx.x & 31;
+  const int4 U = units[u];
+  const int b = U.x, tfirst = U.y, cnt = U.z;
+  const int np2 = (cnt + 1) >> 1;  // power of two
+  const int pi = lane & (np2 - 1), split = lane / np2, nsplit = 32 / np2;
+  const bool two = pi + np2 < cnt;
+  const float4 ta = tgt[tfirst + pi];
+  const float4 tb = tgt[tfirst + (two ? pi + np2 : pi)];
+  const float4* dr = dens + (int64_t)r * nt;
+  f32x2 are[NR], aim[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) are[j] = aim[j] = pk2(0.f, 0.f);
+  const f32x2 pk_k = pk2(k, k);
+  const int ub = u_ptr[b], ue = u_ptr[b + 1];
+  // warp-uniform cursor: list entry cu, element ce (ce = bend of entry cu when done)
+  int cu = ub, ce = ub < ue ? bstart[u_src[ub]] : 0;
+  // stage the next chunk into buffer s; returns its element count
+  auto fill = [&](int s) -> int {
+    int li = cu, le = ce, rem = lane;
+    bool found = false;
+    while (li < ue) {
+      const int e1 = bend[u_src[li]];
+      if (le + rem < e1) {
+        le += rem;
+        found = true;
+        break;
+      }
+      rem -= e1 - le;
+      ++li;
+      if (li < ue) le = bstart[u_src[li]];
+    }
+    if (found) {
+      float4* rec = buf + (s * P2P_CH + lane) * REC;
+      const float4* q = src + 3 * (int64_t)le;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + c)), "l"(q + c) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + 3)), "l"(u_shift + li)
+                   : "memory");
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + 4 + j)),
+                     "l"(dr + (int64_t)j * nt + le)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const unsigned got = __ballot_sync(0xffffffffu, found);
+    const int n = __popc(got);
+    // advance the cursor past the chunk: the element after the last lane's
+    if (n == P2P_CH) {
+      int nli = __shfl_sync(0xffffffffu, li, 31), nle = __shfl_sync(0xffffffffu, le, 31) + 1;
+      if (nle >= bend[u_src[nli]]) {
+        ++nli;
+        nle = nli < ue ? bstart[u_src[nli]] : 0;
+      }
+      cu = nli;
+      ce = nle;
+    } else {
+      cu = ue;
+    }
+    return n;
+  };
+  // one cp.async group per chunk slot, empty once the list is exhausted, so
+  // that "all but the newest group landed" always means "chunk c landed"
+  int n0 = fill(0), n1 = 0;
+  if (n0 == P2P_CH)
+    n1 = fill(1);
+  else
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int c = 0; n0 > 0; ++c) {
+    // chunk c (buffer c & 1) has landed once only the next chunk's copies are pending
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+    const float4* cb = buf + (c & 1) * P2P_CH * REC;
+    for (int e = split; e < n0; e += nsplit) {
+      const float4* rec = cb + e * REC;
+      const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], sh = rec[3];
+      float4 d[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) d[j] = rec[4 + j];
+      const f32x2 ntx = pk2(sh.x - ta.x, sh.x - tb.x), nty = pk2(sh.y - ta.y, sh.y - tb.y),
+                  ntz = pk2(sh.z - ta.z, sh.z - tb.z);
+      const f32x2 nx = pk2(q0.w, q0.w), ny = pk2(q1.w, q1.w), nz = pk2(q2.w, q2.w);
+      P2PPoint g = p2p_point_pair(q0.x, q0.y, q0.z, ntx, nty, ntz, nx, ny, nz, pk_k);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+      g = p2p_point_pair(q1.x, q1.y, q1.z, ntx, nty, ntz, nx, ny, nz, pk_k);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+      g = p2p_point_pair(q2.x, q2.y, q2.z, ntx, nty, ntz, nx, ny, nz, pk_k);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) p2p_acc_pair(g, d[j], are[j], aim[j]);
+    }
+    __syncwarp();  // every lane is done with buffer c & 1 before it is refilled
+    n0 = n1;
+    if (n1 == P2P_CH) {
+      n1 = fill(c & 1);  // chunk c + 2
+    } else {
+      n1 = 0;
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  p2p_finish32<NR>(r, nt, k, tfirst, pi, np2, split, two, ta, tb, src, dr, are, aim, zn);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_fmm32_s(int nunits, int64_t nt, int r0, float k,
+                                                                const int4* __restrict__ units,
+                                                                const int* __restrict__ u_ptr,
+                                                                const int* __restrict__ u_src,
+                                                                const float4* __restrict__ u_shift,
+                                                                const int* __restrict__ bstart,
+                                                                const int* __restrict__ bend,
+                                                                const float4* __restrict__ tgt,
+                                                                const float4* __restrict__ src,
+                                                                const float4* __restrict__ dens,
+                                                                double* __restrict__ zn) {
+  extern __shared__ __align__(16) float4 p2p_stage[];
+  const int warp = threadIdx.x >> 5;
+  const int u = blockIdx.x * P2P_WARPS + warp;
+  if (u >= nunits) return;
+  p2p_unit32_staged<NR>(u, r0 + blockIdx.y * NR, nt, k, units, u_ptr, u_src, u_shift, bstart, bend, tgt, src, dens,
+                        p2p_stage + warp * 2 * P2P_CH * (4 + NR), zn);
 }
 
 // The same work from a fixed number of resident CTAs: every warp takes the
@@ -1461,6 +1611,14 @@ static int apply_sorted_impl(bem_handle* h, int nrhs, cudaStream_t s) {
                 h->u_shift32, h->gl_start, h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens,
                 h->zn);
             c0 += nchunk;
+          });
+        } else if (h->p2p_stage) {
+          nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {
+            constexpr int NRV = decltype(nr)::value;
+            const size_t sm = (size_t)P2P_WARPS * 2 * P2P_CH * (4 + NRV) * sizeof(float4);
+            k_p2p_fmm32_s<NRV><<<dim3(gx, nchunk), 32 * P2P_WARPS, sm, s>>>(
+                h->n_p2p_units, nt, r0, (float)h->k, h->p2p_units, h->u_ptr, h->u_src, h->u_shift32, h->gl_start,
+                h->gl_end, (const float4*)tgt, (const float4*)src, (const float4*)dens, h->zn);
           });
         } else {
           nl = by_rhs_chunks(nrhs, [&](auto nr, int r0, int nchunk) {

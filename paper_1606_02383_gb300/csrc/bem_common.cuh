@@ -209,6 +209,7 @@ struct bem_handle {
   int tc_pipeline = 0;  // translation kernel: 0 per operator (M2M persistent, others 2 stages),
                         // 1 block-synchronous, 2 / 4 warp-specialised stages, 3 persistent
   int p2p_ctas = 0;     // > 0: near field from this many resident CTAs per SM, beside the far field
+  int p2p_stage = 0;    // 1: near-list elements staged in shared memory by cp.async chunks
   int nsm = 0;          // SMs of the device
   int* p2p_ctr = nullptr;  // [nrhs_max + 2] unit counters of the resident near field
   int p_min = 4, p_max = 40;

@@ -120,11 +120,13 @@ def test_fmm_auto_order_ka5(cuda_ok):
     assert op.info("leaf_level") >= 2
 
 
-@pytest.mark.parametrize("pipeline,ctas", [(1, 0), (2, 0), (3, 0), (4, 0), (2, 4), (3, 6)])
-def test_translation_loops_and_resident_near_field(cuda_ok, pipeline, ctas):
+@pytest.mark.parametrize("pipeline,ctas,stage", [(1, 0, 0), (2, 0, 0), (3, 0, 0), (4, 0, 0), (2, 4, 0), (3, 6, 0),
+                                                 (0, 0, 1)])
+def test_translation_loops_and_resident_near_field(cuda_ok, pipeline, ctas, stage):
     """Every translation loop (1: block-synchronous two stages; 2, 4:
-    warp-specialised stages; 3: persistent) and the near field from resident CTAs beside the
-    far field (p2p_ctas) give the same operator: against the oracle at the
+    warp-specialised stages; 3: persistent), the near field from resident
+    CTAs beside the far field (p2p_ctas) and the near field with staged
+    sources (p2p_stage) give the same operator: against the oracle at the
     FMM bar, against each other to FP32 summation order, one and three
     right-hand sides."""
     V, T = inputs.icosphere(4)
@@ -134,7 +136,7 @@ def test_translation_loops_and_resident_near_field(cuda_ok, pipeline, ctas):
     y = inputs.random_density(n, 3, seed=12, stream=1)
     ref = oracle.apply(V, T, k, x=x, y=y)
     op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", leaf_level=4, max_nrhs=3, tc_pipeline=pipeline,
-                  p2p_ctas=ctas)
+                  p2p_ctas=ctas, p2p_stage=stage)
     z = op.apply(dev(x), dev(y)).cpu().numpy()
     assert rel(z, ref) <= 1e-5
     z1 = op.apply(dev(x[:1]), dev(y[:1])).cpu().numpy()
