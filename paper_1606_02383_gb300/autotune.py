@@ -9,10 +9,13 @@ the same accuracy; only the split of the work changes:
   - the near field's work unit (p2p_unit targets per warp): smaller units
     balance the grid's tail, larger ones load each source for more targets;
   - the translation jobs' K slice (tc_kslice stages): shorter slices give
-    small operators more CTAs at the price of more atomic adds.
+    small operators more CTAs at the price of more atomic adds;
+  - the translation loop (tc_pipeline: per operator, block-synchronous,
+    two warp-specialised stages, persistent) and the near field's source
+    staging (p2p_stage): which hides latency best depends on the job sizes.
 ``tune`` times the candidates with CUDA events on the current stream,
-coordinate by coordinate (tree first, then the two tile choices), and keeps
-the fastest operator.
+coordinate by coordinate (tree first, then the tile and loop choices), and
+keeps the fastest operator.
 """
 from __future__ import annotations
 
@@ -22,7 +25,7 @@ import torch
 from . import inputs
 from .operator import Operator
 
-DEFAULTS = {"leaf_level": 0, "leaf_target": 48, "p2p_unit": 64, "tc_kslice": 16}
+DEFAULTS = {"leaf_level": 0, "leaf_target": 48, "p2p_unit": 64, "tc_kslice": 16, "tc_pipeline": 0, "p2p_stage": 0}
 
 
 def pick(timings: dict, prefer=None, tolerance: float = 0.02):
@@ -55,13 +58,15 @@ def _key(cfg):
 
 
 def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, targets=(24, 32, 48, 64),
-         units=(32, 64), kslices=(8, 16), reps=5, warmup=2, seed=0, **options):
+         units=(32, 64), kslices=(8, 16), pipelines=(0, 1, 2, 3), stages=(0, 1), reps=5, warmup=2, seed=0,
+         **options):
     """Returns ``(operator, report)`` with the fastest candidate for ``nrhs``
     right-hand sides.  Candidates: the default uniform tree (leaf_level 0) and
     uniform trees on its level +- ``spread``, the adaptive tree with its depth
     chosen per region (leaf_level -1) for every leaf target in ``targets``;
-    then, for the best tree, every p2p_unit in ``units`` and every tc_kslice
-    in ``kslices``.  ``report`` holds
+    then, for the best tree, every p2p_unit in ``units``, every tc_kslice in
+    ``kslices``, every tc_pipeline in ``pipelines`` and every p2p_stage in
+    ``stages`` (mixed mode only for the last two).  ``report`` holds
     ``{"default": cfg, "chosen": cfg, "ms": [(cfg, ms), ...], "gain": default_ms / chosen_ms}``."""
     n = np.asarray(triangles).shape[0]
     x = torch.from_numpy(inputs.random_density(n, nrhs, seed=seed, stream=0)).cuda()
@@ -97,6 +102,13 @@ def tune(vertices, triangles, k, p=0, eps=1e-5, mode="mixed", nrhs=1, spread=1, 
     base = dict(state["best_cfg"])
     for ks in kslices:
         run(dict(base, tc_kslice=ks))
+    if mode == "mixed":
+        base = dict(state["best_cfg"])
+        for pl in pipelines:
+            run(dict(base, tc_pipeline=pl))
+        base = dict(state["best_cfg"])
+        for st in stages:
+            run(dict(base, p2p_stage=st))
     chosen = state["best_cfg"]
     report = {"default": default, "chosen": chosen,
               "ms": [(dict(kk), v) for kk, v in timed.items()],

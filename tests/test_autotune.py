@@ -34,7 +34,7 @@ def test_tuned_operator_matches_oracle(cuda_ok):
     assert len(report["ms"]) >= 4
     assert report["gain"] >= 1.0
     chosen = report["chosen"]
-    assert set(chosen) == {"leaf_level", "leaf_target", "p2p_unit", "tc_kslice"}
+    assert set(chosen) == {"leaf_level", "leaf_target", "p2p_unit", "tc_kslice", "tc_pipeline", "p2p_stage"}
     if chosen["leaf_level"] > 0:
         assert op.info("leaf_level") == chosen["leaf_level"] and op.info("adaptive") == 0
     else:
