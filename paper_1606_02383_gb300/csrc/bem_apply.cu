@@ -858,103 +858,120 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_points_grad(int64_t nt, int
 }
 
 // ------------------------------------------- near leaves at field points --
-// One thread per field point (in the walk's order): the elements of every
-// near leaf of the point's walk (bem_tree_walk.cuh), each with the rule its
-// distance calls for, as in k_eval_points; then the far part from acc is
-// added and the point's components are written in the caller's order.
-// The stored P2P coordinates are relative to the element's leaf centre, so
-// one FP64 difference per leaf (centre - x) places them relative to x.
-template <typename R, typename Rout, int MODE, int NR>
-__global__ void __launch_bounds__(128) k_evf_near(int64_t np, int r0, int64_t nt, WalkTree wt, double k,
+// One warp per field point that has near leaves (the far pass's flag,
+// compacted into near_list): the lanes walk the tree together and split the
+// elements of every near leaf, each with the rule its distance calls for as
+// in k_eval_points; the lanes' sums are reduced and added to the point's FP64
+// far sums.  The stored P2P coordinates are relative to the element's leaf
+// centre, so one FP64 difference per leaf (centre - x) places them relative
+// to x; the target array's .w holds (4 h_j)^2 for the refined-rule test.
+// The warps stride over the list, whose length is read on the device.
+template <typename R, int MODE, int NR>
+__global__ void __launch_bounds__(128) k_evf_near(int r0, int64_t nt, WalkTree wt, double k, int64_t np,
                                                   const double* __restrict__ pts, const int* __restrict__ tcs,
-                                                  const int* __restrict__ perm, const typename V4of<R>::T* __restrict__ tgt,
+                                                  const int* __restrict__ near_list, const int* __restrict__ n_near,
+                                                  const typename V4of<R>::T* __restrict__ tgt,
                                                   const typename V4of<R>::T* __restrict__ src,
                                                   const typename V4of<R>::T* __restrict__ dens,
                                                   const double* __restrict__ cent, const double* __restrict__ qpt,
                                                   const double* __restrict__ nrm, const double* __restrict__ area,
                                                   const double* __restrict__ hmax, const double* __restrict__ wgt,
-                                                  const double* __restrict__ acc, Rout* __restrict__ out) {
+                                                  double* __restrict__ acc) {
   typedef typename V4of<R>::T V4;
   constexpr bool VAL = MODE != 1, GRAD = MODE != 0;
   constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= np) return;
-  const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
-  const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+  const int lane = threadIdx.x & 31;
+  const int64_t nn = *n_near;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const R kr = (R)k;
-  R are[NR], aim[NR], g[NR][6];
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nn; w += nw) {
+    const int64_t i = near_list[w];
+    const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+    const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+    R are[NR], aim[NR], g[NR][6];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    are[q] = aim[q] = 0;
+    for (int q = 0; q < NR; ++q) {
+      are[q] = aim[q] = 0;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) g[q][c] = 0;
-  }
-  tree_walk(wt, t, [&](int kind, int l, int b) {
-    if (kind != 1) return;
-    const double* c = wt.lv[l].centre + 3 * b;
-    const R sx = (R)(c[0] - X[0]), sy = (R)(c[1] - X[1]), sz = (R)(c[2] - X[2]);
-    const int e1 = wt.lv[l].end[b];
-    for (int j = wt.lv[l].start[b]; j < e1; ++j) {
-      const V4 tc = tgt[j];
-      const R cx = tc.x + sx, cy = tc.y + sy, cz = tc.z + sz;
-      const R h4 = (R)(4.0 * hmax[j]);
-      if (cx * cx + cy * cy + cz * cz < h4 * h4) {
+      for (int c = 0; c < 6; ++c) g[q][c] = 0;
+    }
+    tree_walk(wt, t, [&](int kind, int l, int b) {
+      if (kind != 1) return;
+      const double* c = wt.lv[l].centre + 3 * b;
+      const R sx = (R)(c[0] - X[0]), sy = (R)(c[1] - X[1]), sz = (R)(c[2] - X[2]);
+      const int e1 = wt.lv[l].end[b];
+      for (int j = wt.lv[l].start[b] + lane; j < e1; j += 32) {
+        const V4 tc = tgt[j];
+        const R cx = tc.x + sx, cy = tc.y + sy, cz = tc.z + sz;
+        if (cx * cx + cy * cy + cz * cz < tc.w) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
+            if (VAL) eval_near<R>(X, j, k, cent, qpt, nrm, area, hmax, wgt, dd, are[q], aim[q]);
+            if (GRAD) grad_near<R>(X, j, k, cent, qpt, nrm, area, hmax, dd, g[q]);
+          }
+          continue;
+        }
+        const V4 q0 = src[3 * (int64_t)j], q1 = src[3 * (int64_t)j + 1], q2 = src[3 * (int64_t)j + 2];
+        const R nx = q0.w, ny = q1.w, nz = q2.w;
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
           const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
-          if (VAL) eval_near<R>(X, j, k, cent, qpt, nrm, area, hmax, wgt, dd, are[q], aim[q]);
-          if (GRAD) grad_near<R>(X, j, k, cent, qpt, nrm, area, hmax, dd, g[q]);
+          if (VAL) {
+            p2p_eval(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+            p2p_eval(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+            p2p_eval(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+          }
+          if (GRAD) {
+            grad_eval<R>(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+            grad_eval<R>(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+            grad_eval<R>(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+          }
         }
-        continue;
       }
-      const V4 q0 = src[3 * (int64_t)j], q1 = src[3 * (int64_t)j + 1], q2 = src[3 * (int64_t)j + 2];
-      const R nx = q0.w, ny = q1.w, nz = q2.w;
+    });
+    // the lanes' partial sums, reduced in the operator's precision
 #pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
+    for (int q = 0; q < NR; ++q) {
+      for (int o = 16; o > 0; o >>= 1) {
         if (VAL) {
-          p2p_eval(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
-          p2p_eval(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
-          p2p_eval(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd, are[q], aim[q]);
+          are[q] += __shfl_xor_sync(0xffffffffu, are[q], o);
+          aim[q] += __shfl_xor_sync(0xffffffffu, aim[q], o);
         }
-        if (GRAD) {
-          grad_eval<R>(q0.x + sx, q0.y + sy, q0.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
-          grad_eval<R>(q1.x + sx, q1.y + sy, q1.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
-          grad_eval<R>(q2.x + sx, q2.y + sy, q2.z + sz, nx, ny, nz, kr, dd.x, dd.y, dd.z, dd.w, g[q]);
+        if (GRAD)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) g[q][c] += __shfl_xor_sync(0xffffffffu, g[q][c], o);
+      }
+      if (lane == 0) {
+        double* a = acc + 2 * (((int64_t)(r0 + q) * np + i) * NC);
+        int c0 = 0;
+        if (VAL) {
+          a[0] += (double)are[q];
+          a[1] += (double)aim[q];
+          c0 = 1;
         }
+        if (GRAD)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) a[2 * c0 + c] += (double)g[q][c];
       }
     }
-  });
-  const int64_t o = perm[i];
-#pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    const double* a = acc + 2 * (((int64_t)(r0 + q) * np + i) * NC);
-    Rout* w = out + 2 * (((int64_t)(r0 + q) * np + o) * NC);
-    int c0 = 0;
-    if (VAL) {
-      w[0] = (Rout)(a[0] + (double)are[q]);
-      w[1] = (Rout)(a[1] + (double)aim[q]);
-      c0 = 1;
-    }
-    if (GRAD)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) w[2 * c0 + c] = (Rout)(a[2 * c0 + c] + (double)g[q][c]);
   }
 }
 
-template <typename R, typename Rout, int MODE>
+template <typename R, int MODE>
 static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
-                         const int* perm, const double* acc, void* out, cudaStream_t s) {
+                         const int* near_list, const int* n_near, double* acc, cudaStream_t s) {
   typedef typename V4of<R>::T V4;
   const V4* tgt = (const V4*)(sizeof(R) == 4 ? (const void*)h->tgt32 : (const void*)h->tgt64);
   const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
-  const unsigned g = nblk(np, 128);
+  // warps stride over the near list: enough blocks of 4 warps to fill the GPU
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + 3) / 4, (int64_t)h->nsm * 16));
   for (int r0 = 0; r0 < nrhs;) {
     const int rem = nrhs - r0;
 #define EVF_NEAR(NRV)                                                                                          \
-  k_evf_near<R, Rout, MODE, NRV><<<g, 128, 0, s>>>(np, r0, h->nt, wt, h->k, pts, tcs, perm, tgt, src,          \
-                                                   (const V4*)h->dens, h->cent, h->qpt, h->nrm, h->area, h->hmax, \
-                                                   h->wgt, acc, (Rout*)out);                                   \
+  k_evf_near<R, MODE, NRV><<<g, 128, 0, s>>>(r0, h->nt, wt, h->k, np, pts, tcs, near_list, n_near, tgt, src,     \
+                                             (const V4*)h->dens, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->wgt, \
+                                             acc);                                                             \
   r0 += NRV;
     if (rem >= 4) {
       EVF_NEAR(4)
@@ -969,21 +986,39 @@ static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np
   return BEM_OK;
 }
 
-template <typename R, typename Rout>
-static int evf_near_mode(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                         const int* tcs, const int* perm, const double* acc, void* out, cudaStream_t s) {
-  if (mode == 0) return evf_near_impl<R, Rout, 0>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
-  if (mode == 1) return evf_near_impl<R, Rout, 1>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
-  return evf_near_impl<R, Rout, 2>(h, wt, nrhs, np, pts, tcs, perm, acc, out, s);
+int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
+                 const int* tcs, const int* near_list, const int* n_near, double* acc, cudaStream_t s) {
+  const bool f64 = bem_is_fp64(h);
+  if (mode == 0) return f64 ? evf_near_impl<double, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
+                            : evf_near_impl<float, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
+  if (mode == 1) return f64 ? evf_near_impl<double, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
+                            : evf_near_impl<float, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
+  return f64 ? evf_near_impl<double, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
+             : evf_near_impl<float, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
 }
 
-int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                 const int* tcs, const int* perm, const double* acc, int dtype, void* out, cudaStream_t s) {
-  if (bem_is_fp64(h))
-    return dtype == BEM_C128 ? evf_near_mode<double, double>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s)
-                             : evf_near_mode<double, float>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s);
-  return dtype == BEM_C128 ? evf_near_mode<float, double>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s)
-                           : evf_near_mode<float, float>(h, wt, nrhs, mode, np, pts, tcs, perm, acc, out, s);
+// the FP64 sums of every point, back to the caller's order and dtype
+template <typename Rout>
+__global__ void k_evf_out(int64_t n, int64_t np, int nc, const int* __restrict__ perm, const double* __restrict__ acc,
+                          Rout* __restrict__ out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // over nrhs * np * nc complex values
+  if (idx >= n) return;
+  const int64_t c = idx % nc, i = (idx / nc) % np, r = idx / (nc * np);
+  const int64_t o = ((r * np + perm[i]) * nc + c);
+  out[2 * o] = (Rout)acc[2 * idx];
+  out[2 * o + 1] = (Rout)acc[2 * idx + 1];
+}
+
+int bem_evf_out(int nrhs, int mode, int64_t np, const int* perm, const double* acc, int dtype, void* out,
+                cudaStream_t s) {
+  const int nc = mode == 0 ? 1 : (mode == 1 ? 3 : 4);
+  const int64_t n = (int64_t)nrhs * np * nc;
+  if (dtype == BEM_C128)
+    k_evf_out<double><<<nblk(n, 256), 256, 0, s>>>(n, np, nc, perm, acc, (double*)out);
+  else
+    k_evf_out<float><<<nblk(n, 256), 256, 0, s>>>(n, np, nc, perm, acc, (float*)out);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
 }
 
 // the direct sum over all elements (mode 0: u, 1: grad u, 2: both)

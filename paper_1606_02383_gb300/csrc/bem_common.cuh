@@ -393,14 +393,18 @@ int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStr
 // alone (P2M, M2M of h->dens into h->Mexp), then per point the far boxes'
 // multipoles (bem_wx.cu) and the near leaves' elements (bem_apply.cu).
 // mode: 0 value, 1 gradient, 2 value and gradient; acc is FP64 complex
-// [nrhs][np][ncomp] in the walk's point order; the near pass adds acc and
-// writes out[r][perm[i]][c] in the caller's dtype.
+// [nrhs][np][ncomp] in the walk's point order: the far pass writes it and
+// flags the points with near leaves, the near pass (one warp per flagged
+// point) adds to it, and bem_evf_out writes out[r][perm[i]][c] in the
+// caller's dtype.
 struct WalkTree;
 int bem_run_upward(bem_handle* h, int nrhs, cudaStream_t s);
 int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                const int* tcs, double* acc, cudaStream_t s);
+                const int* tcs, double* acc, int* nearflag, cudaStream_t s);
 int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                 const int* tcs, const int* perm, const double* acc, int dtype, void* out, cudaStream_t s);
+                 const int* tcs, const int* near_list, const int* n_near, double* acc, cudaStream_t s);
+int bem_evf_out(int nrhs, int mode, int64_t np, const int* perm, const double* acc, int dtype, void* out,
+                cudaStream_t s);
 int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
                  int64_t np, void* out, int mode, cudaStream_t s);
 int bem_build_correction(bem_handle* h, cudaStream_t s);

@@ -8,8 +8,9 @@
 //      (extended beyond the root cube), so that the threads of a warp walk
 //      nearly the same boxes;
 //   4. far pass: per point, the multipole of every far box of its walk;
-//   5. near pass: per point, the elements of every near leaf of its walk,
-//      plus the far part, written in the caller's point order.
+//   5. near pass: one warp per point whose walk has near leaves (flagged by
+//      the far pass, compacted), the lanes splitting the leaves' elements;
+//   6. the FP64 sums written in the caller's point order and dtype.
 // Temporary arrays are stream-ordered allocations freed at the end of the call.
 #include <cub/cub.cuh>
 
@@ -85,10 +86,10 @@ int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* 
   BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
   BEM_TRY(bem_run_upward(h, nrhs, s));
   unsigned long long *keys_in = nullptr, *keys = nullptr;
-  int *idx_in = nullptr, *perm = nullptr, *tcs = nullptr;
+  int *idx_in = nullptr, *perm = nullptr, *tcs = nullptr, *nearflag = nullptr, *near_list = nullptr, *n_near = nullptr;
   double *spts = nullptr, *acc = nullptr;
-  void* tmp = nullptr;
-  size_t tb = 0;
+  void *tmp = nullptr, *tmp2 = nullptr;
+  size_t tb = 0, tb2 = 0;
   int rc = BEM_OK;
   auto fail = [&](cudaError_t e) {
     if (rc == BEM_OK && e != cudaSuccess)
@@ -103,6 +104,9 @@ int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* 
     if (fail(cudaMallocAsync((void**)&tcs, 3 * np * sizeof(int), s))) break;
     if (fail(cudaMallocAsync((void**)&spts, 3 * np * sizeof(double), s))) break;
     if (fail(cudaMallocAsync((void**)&acc, 2 * nc * nrhs * np * sizeof(double), s))) break;
+    if (fail(cudaMallocAsync((void**)&nearflag, np * sizeof(int), s))) break;
+    if (fail(cudaMallocAsync((void**)&near_list, np * sizeof(int), s))) break;
+    if (fail(cudaMallocAsync((void**)&n_near, sizeof(int), s))) break;
     k_evf_keys<<<nblk(np, 256), 256, 0, s>>>(np, wt, points, keys_in, idx_in);
     if (fail(cudaGetLastError())) break;
     if (fail(cub::DeviceRadixSort::SortPairs(nullptr, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
@@ -110,11 +114,19 @@ int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* 
     if (fail(cub::DeviceRadixSort::SortPairs(tmp, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
     k_evf_gather<<<nblk(np, 256), 256, 0, s>>>(np, wt, perm, points, spts, tcs);
     if (fail(cudaGetLastError())) break;
-    rc = bem_evf_far(h, wt, nrhs, mode, np, spts, tcs, acc, s);
+    rc = bem_evf_far(h, wt, nrhs, mode, np, spts, tcs, acc, nearflag, s);
     if (rc != BEM_OK) break;
-    rc = bem_evf_near(h, wt, nrhs, mode, np, spts, tcs, perm, acc, dtype, out, s);
+    // the points whose walk has near leaves, in walk order (idx_in still
+    // holds 0 .. np - 1: the sort wrote its output to perm)
+    if (fail(cub::DeviceSelect::Flagged(nullptr, tb2, idx_in, nearflag, near_list, n_near, (int)np, s))) break;
+    if (fail(cudaMallocAsync(&tmp2, tb2, s))) break;
+    if (fail(cub::DeviceSelect::Flagged(tmp2, tb2, idx_in, nearflag, near_list, n_near, (int)np, s))) break;
+    rc = bem_evf_near(h, wt, nrhs, mode, np, spts, tcs, near_list, n_near, acc, s);
+    if (rc != BEM_OK) break;
+    rc = bem_evf_out(nrhs, mode, np, perm, acc, dtype, out, s);
   } while (false);
-  for (void* p : {(void*)keys_in, (void*)keys, (void*)idx_in, (void*)perm, (void*)tcs, (void*)spts, (void*)acc, tmp})
+  for (void* p : {(void*)keys_in, (void*)keys, (void*)idx_in, (void*)perm, (void*)tcs, (void*)spts, (void*)acc,
+                  (void*)nearflag, (void*)near_list, (void*)n_near, tmp, tmp2})
     if (p) cudaFreeAsync(p, s);
   return rc;
 }

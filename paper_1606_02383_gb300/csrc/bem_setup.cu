@@ -466,8 +466,9 @@ __global__ void k_corr_values(int64_t nt, double k, const double* __restrict__ c
 // P2P arrays: sources relative to their leaf centre, normal components in .w
 template <typename V4, typename R>
 __global__ void k_p2p_arrays(int64_t nt, const double* __restrict__ cent, const double* __restrict__ qpt,
-                             const double* __restrict__ nrm, const int* __restrict__ elbox,
-                             const double* __restrict__ bcentre, int relative, V4* tgt, V4* src) {
+                             const double* __restrict__ nrm, const double* __restrict__ hmax,
+                             const int* __restrict__ elbox, const double* __restrict__ bcentre, int relative, V4* tgt,
+                             V4* src) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nt) return;
   double o[3] = {0, 0, 0};
@@ -479,7 +480,7 @@ __global__ void k_p2p_arrays(int64_t nt, const double* __restrict__ cent, const 
   t.x = (R)(cent[3 * s] - o[0]);
   t.y = (R)(cent[3 * s + 1] - o[1]);
   t.z = (R)(cent[3 * s + 2] - o[2]);
-  t.w = (R)0;
+  t.w = (R)(16.0 * hmax[s] * hmax[s]);  // (4 h)^2: within it a field point needs the refined rule
   tgt[s] = t;
   for (int q = 0; q < 3; ++q) {
     V4 v;
@@ -1142,13 +1143,13 @@ int bem_build_tree(bem_handle* h, int leaf_level, int leaf_target, cudaStream_t 
     if (bem_is_fp64(h)) {
       BEM_TRY(bem_alloc(h, &h->tgt64, nt));
       BEM_TRY(bem_alloc(h, &h->src64, 3 * nt));
-      k_p2p_arrays<double4, double><<<nblk(nt, 256), 256, 0, s>>>(nt, h->cent, h->qpt, h->nrm, frame_of, frame_c, 1,
-                                                                  h->tgt64, h->src64);
+      k_p2p_arrays<double4, double><<<nblk(nt, 256), 256, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->hmax, frame_of,
+                                                                  frame_c, 1, h->tgt64, h->src64);
     } else {
       BEM_TRY(bem_alloc(h, &h->tgt32, nt));
       BEM_TRY(bem_alloc(h, &h->src32, 3 * nt));
-      k_p2p_arrays<float4, float><<<nblk(nt, 256), 256, 0, s>>>(nt, h->cent, h->qpt, h->nrm, frame_of, frame_c, 1,
-                                                                h->tgt32, h->src32);
+      k_p2p_arrays<float4, float><<<nblk(nt, 256), 256, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->hmax, frame_of,
+                                                                frame_c, 1, h->tgt32, h->src32);
     }
     BEM_CUDA(cudaGetLastError());
     BEM_CUDA(cudaStreamSynchronize(s));

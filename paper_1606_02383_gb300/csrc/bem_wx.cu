@@ -516,16 +516,19 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
 
 // One thread per field point (in the walk's order): the multipoles of the
 // point's far boxes.  Writes acc[r][i][c] (FP64 complex), c over the
-// components of the mode (0: u; 1: grad u; 2: u, grad u).
+// components of the mode (0: u; 1: grad u; 2: u, grad u), and nearflag[i]:
+// whether the point's walk has near leaves.
 template <typename R, int MODE, int NR>
 __global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt, const double* __restrict__ pts,
                                                  const int* __restrict__ tcs, LevTab lt, const int* __restrict__ lev_p,
                                                  const R* __restrict__ lev_a, R k, const R* __restrict__ M,
-                                                 int64_t exp_stride, double* __restrict__ acc) {
+                                                 int64_t exp_stride, double* __restrict__ acc,
+                                                 int* __restrict__ nearflag) {
   constexpr bool GRAD = MODE != 0;
   constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= np) return;
+  bool near = false;
   const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
   const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
   R val[NR][2], grd[NR][3][2];
@@ -536,7 +539,10 @@ __global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt
     for (int c = 0; c < 3; ++c) grd[q][c][0] = grd[q][c][1] = 0;
   }
   tree_walk(wt, t, [&](int kind, int l, int b) {
-    if (kind != 0) return;
+    if (kind != 0) {
+      near = true;
+      return;
+    }
     const double* c = wt.lv[l].centre + 3 * b;
     const R vx = (R)(X[0] - c[0]), vy = (R)(X[1] - c[1]), vz = (R)(X[2] - c[2]);
     const R* Md[NR];
@@ -544,6 +550,7 @@ __global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt
     for (int q = 0; q < NR; ++q) Md[q] = M + 2 * ((int64_t)(r0 + q) * exp_stride + lt.base[l] + (int64_t)b * lt.P[l]);
     m2p_point<R, GRAD, NR>(lev_p[l], k, lev_a[l], vx, vy, vz, Md, val, grd);
   });
+  if (r0 == 0) nearflag[i] = near ? 1 : 0;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
     double* o = acc + 2 * (((int64_t)(r0 + q) * np + i) * NC);
@@ -729,22 +736,22 @@ int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStr
 
 template <typename R, int MODE>
 static int evf_far_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
-                        double* acc, cudaStream_t s) {
+                        double* acc, int* nearflag, cudaStream_t s) {
   const LevTab lt = bem_levtab(h);
   const unsigned g = nblk(np, 128);
   for (int r0 = 0; r0 < nrhs;) {
     const int rem = nrhs - r0;
     if (rem >= 4) {
       k_evf_far<R, MODE, 4><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc);
+                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
       r0 += 4;
     } else if (rem >= 2) {
       k_evf_far<R, MODE, 2><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc);
+                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
       r0 += 2;
     } else {
       k_evf_far<R, MODE, 1><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc);
+                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
       r0 += 1;
     }
     BEM_CUDA(cudaGetLastError());
@@ -753,12 +760,12 @@ static int evf_far_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np,
 }
 
 int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                const int* tcs, double* acc, cudaStream_t s) {
+                const int* tcs, double* acc, int* nearflag, cudaStream_t s) {
   const bool f64 = bem_is_fp64(h);
-  if (mode == 0) return f64 ? evf_far_impl<double, 0>(h, wt, nrhs, np, pts, tcs, acc, s)
-                            : evf_far_impl<float, 0>(h, wt, nrhs, np, pts, tcs, acc, s);
-  if (mode == 1) return f64 ? evf_far_impl<double, 1>(h, wt, nrhs, np, pts, tcs, acc, s)
-                            : evf_far_impl<float, 1>(h, wt, nrhs, np, pts, tcs, acc, s);
-  return f64 ? evf_far_impl<double, 2>(h, wt, nrhs, np, pts, tcs, acc, s)
-             : evf_far_impl<float, 2>(h, wt, nrhs, np, pts, tcs, acc, s);
+  if (mode == 0) return f64 ? evf_far_impl<double, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
+                            : evf_far_impl<float, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
+  if (mode == 1) return f64 ? evf_far_impl<double, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
+                            : evf_far_impl<float, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
+  return f64 ? evf_far_impl<double, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
+             : evf_far_impl<float, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
 }
