@@ -614,14 +614,16 @@ def topology_iteration(steps, warm):
     GPU through the library: the body {phi > 0} of the differentiation
     workload's level set on a 64^3 lattice over [-2, 2]^3 (phi = the Gaussian
     sum minus the workload's level, clamped to [-1, 1]); its boundary
-    (bem_isosurface); the operator on that mesh (k = 3, mixed, eps 1e-5); the
-    state and adjoint chain for f = 1/2 sum |p|^2 at 4 observers 5 away, with
-    a plane-wave incident field; the topological derivative on the lattice
-    nodes in the fluid (phi <= 0; the body side is outside the path and is
-    taken as 0); one level-set step (F scaled by 1 / max |T|); the new
+    (bem_isosurface); the operator on that mesh (k = 3, mixed, eps 1e-5, with
+    options tuned once on the first mesh); the state and adjoint chain for
+    f = 1/2 sum |p|^2 at 4 observers 5 away, with a plane-wave incident field;
+    the topological derivative on the lattice nodes in the fluid (phi <= -0.02:
+    a thin band at the boundary left out; the body side is outside the path and
+    is taken as 0); one level-set step (F scaled by 1 / max |T|); the new
     boundary.  Each timed iteration starts from the same phi."""
     import torch
     from paper_1606_02383_gb300 import inputs
+    from paper_1606_02383_gb300.autotune import tune_options
     from paper_1606_02383_gb300.operator import Operator, isosurface, levelset_step
     n, k = 64, 3.0
     phi0, lo, h = inputs.level_set_function(0, 20, n)
@@ -634,6 +636,13 @@ def topology_iteration(steps, warm):
     inc_obs = np.exp(1j * k * obs[:, 2])
     dt, tau, L, phi_bar = 0.1, 1e-3, 4.0, -1.0
     out = {}
+    # the operator's options, tuned once on the first mesh and kept for every
+    # iteration (the level-set meshes change little from one step to the next)
+    Vd0, Td0 = isosurface(phi, (-2.0, -2.0, -2.0), h, 0.0)
+    t_tune = time.perf_counter()
+    opts, rep = tune_options(Vd0.cpu().numpy(), Td0.cpu().numpy(), k, nrhs=1, reps=3, warmup=1, max_nrhs=2)
+    out["tuned_options"] = {"chosen": opts, "gain_over_default": rep["gain"], "tune_s": time.perf_counter() - t_tune}
+    opts = {kk: v for kk, v in opts.items() if kk != "max_nrhs"}
 
     def iteration():
         tm = {}
@@ -647,7 +656,7 @@ def topology_iteration(steps, warm):
         Vd, Td = isosurface(phi, (-2.0, -2.0, -2.0), h, 0.0)
         t0 = mark("isosurface_s", t0)
         V, T = Vd.cpu().numpy(), Td.cpu().numpy()
-        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", max_nrhs=2)
+        op = Operator(V, T, k, p=0, eps=1e-5, mode="mixed", max_nrhs=2, **opts)
         t0 = mark("setup_s", t0)
         cen = torch.from_numpy(inputs.centroids(V, T)).cuda()
         b = torch.exp(1j * k * cen[:, 2])[None, :]
