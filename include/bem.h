@@ -128,6 +128,10 @@ typedef struct {
   int p2p_stage;    /* FP32 FMM: 1 stages the near list's source elements in shared memory (per warp,
                        two buffers of 32 elements filled by cp.async while the other is summed);
                        0 (default) loads them from global memory in the loop */
+  int grad_direct;  /* FMM modes: 1 sums the regular-rule part of the vertex gradient (bem_grad) directly
+                       over all pairs, O(N^2); 0 (default) through the octree: the target side by the
+                       walk of bem_eval_points at the centroids, the source side by a walk at the
+                       quadrature points over the multipoles of point charges at the centroids */
 } bem_options;
 
 /*

@@ -72,7 +72,7 @@ class BemOptions(ctypes.Structure):
                 ("p_max", ctypes.c_int), ("p_level", ctypes.c_int * 11), ("p2p_unit", ctypes.c_int),
                 ("tc_kslice", ctypes.c_int), ("corr_rules32", ctypes.c_int), ("tc_tf32", ctypes.c_int),
                 ("tc_pipeline", ctypes.c_int), ("p2p_ctas", ctypes.c_int),
-                ("p2p_stage", ctypes.c_int)]
+                ("p2p_stage", ctypes.c_int), ("grad_direct", ctypes.c_int)]
 
 
 class BemError(RuntimeError):

@@ -164,6 +164,7 @@ int bem_setup(const bem_mesh* mesh, double k, int p, double eps, const bem_optio
   h->tc_pipeline = o.tc_pipeline;
   h->p2p_ctas = o.p2p_ctas;
   h->p2p_stage = o.p2p_stage ? 1 : 0;
+  h->grad_direct = o.grad_direct ? 1 : 0;
   h->p_min = o.p_min;
   h->p_max = o.p_max;
   for (int l = 0; l <= BEM_MAXLEV; ++l) {

@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(128) k_evf_near(int r0, int64_t nt, WalkTree w
                                                   const double* __restrict__ cent, const double* __restrict__ qpt,
                                                   const double* __restrict__ nrm, const double* __restrict__ area,
                                                   const double* __restrict__ hmax, const double* __restrict__ wgt,
-                                                  double* __restrict__ acc) {
+                                                  int refine, double* __restrict__ acc) {
   typedef typename V4of<R>::T V4;
   constexpr bool VAL = MODE != 1, GRAD = MODE != 0;
   constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(128) k_evf_near(int r0, int64_t nt, WalkTree w
       for (int j = wt.lv[l].start[b] + lane; j < e1; j += 32) {
         const V4 tc = tgt[j];
         const R cx = tc.x + sx, cy = tc.y + sy, cz = tc.z + sz;
-        if (cx * cx + cy * cy + cz * cz < tc.w) {
+        if (refine && cx * cx + cy * cy + cz * cz < tc.w) {
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
             const V4 dd = dens[(int64_t)(r0 + q) * nt + j];
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(128) k_evf_near(int r0, int64_t nt, WalkTree w
 
 template <typename R, int MODE>
 static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
-                         const int* near_list, const int* n_near, double* acc, cudaStream_t s) {
+                         const int* near_list, const int* n_near, double* acc, int refine, cudaStream_t s) {
   typedef typename V4of<R>::T V4;
   const V4* tgt = (const V4*)(sizeof(R) == 4 ? (const void*)h->tgt32 : (const void*)h->tgt64);
   const V4* src = (const V4*)(sizeof(R) == 4 ? (const void*)h->src32 : (const void*)h->src64);
@@ -971,7 +971,7 @@ static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np
 #define EVF_NEAR(NRV)                                                                                          \
   k_evf_near<R, MODE, NRV><<<g, 128, 0, s>>>(r0, h->nt, wt, h->k, np, pts, tcs, near_list, n_near, tgt, src,     \
                                              (const V4*)h->dens, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->wgt, \
-                                             acc);                                                             \
+                                             refine, acc);                                                     \
   r0 += NRV;
     if (rem >= 4) {
       EVF_NEAR(4)
@@ -987,14 +987,17 @@ static int evf_near_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np
 }
 
 int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                 const int* tcs, const int* near_list, const int* n_near, double* acc, cudaStream_t s) {
+                 const int* tcs, const int* near_list, const int* n_near, double* acc, int refine,
+                 cudaStream_t s) {
   const bool f64 = bem_is_fp64(h);
-  if (mode == 0) return f64 ? evf_near_impl<double, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
-                            : evf_near_impl<float, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
-  if (mode == 1) return f64 ? evf_near_impl<double, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
-                            : evf_near_impl<float, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
-  return f64 ? evf_near_impl<double, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s)
-             : evf_near_impl<float, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, s);
+  if (mode == 0)
+    return f64 ? evf_near_impl<double, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s)
+               : evf_near_impl<float, 0>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s);
+  if (mode == 1)
+    return f64 ? evf_near_impl<double, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s)
+               : evf_near_impl<float, 1>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s);
+  return f64 ? evf_near_impl<double, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s)
+             : evf_near_impl<float, 2>(h, wt, nrhs, np, pts, tcs, near_list, n_near, acc, refine, s);
 }
 
 // the FP64 sums of every point, back to the caller's order and dtype

@@ -210,6 +210,7 @@ struct bem_handle {
                         // 1 block-synchronous, 2 / 4 warp-specialised stages, 3 persistent
   int p2p_ctas = 0;     // > 0: near field from this many resident CTAs per SM, beside the far field
   int p2p_stage = 0;    // 1: near-list elements staged in shared memory by cp.async chunks
+  int grad_direct = 0;  // 1: the vertex gradient's regular rule as an all-pairs sum on FMM handles
   int nsm = 0;          // SMs of the device
   int* p2p_ctr = nullptr;  // [nrhs_max + 2] unit counters of the resident near field
   int p_min = 4, p_max = 40;
@@ -396,13 +397,25 @@ int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStr
 // [nrhs][np][ncomp] in the walk's point order: the far pass writes it and
 // flags the points with near leaves, the near pass (one warp per flagged
 // point) adds to it, and bem_evf_out writes out[r][perm[i]][c] in the
-// caller's dtype.
+// caller's dtype.  refine = 0 sums every near element with the regular
+// 3-point rule R_0 (the vertex gradient's target side), 1 with the rule its
+// distance calls for.
 struct WalkTree;
 int bem_run_upward(bem_handle* h, int nrhs, cudaStream_t s);
 int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                const int* tcs, double* acc, int* nearflag, cudaStream_t s);
+                const int* tcs, double* acc, int* nearflag, int team, cudaStream_t s);
 int bem_evf_near(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                 const int* tcs, const int* near_list, const int* n_near, double* acc, cudaStream_t s);
+                 const int* tcs, const int* near_list, const int* n_near, double* acc, int refine,
+                 cudaStream_t s);
+// The far pass of the vertex gradient's source side: the multipoles in h->Mexp
+// are those of point charges at the centroids; at every walk point (a
+// quadrature point of element perm[i] / 3, normal n) it writes FP64 complex
+// acc[r][i][8] = (psi, grad psi, n.grad psi, (Hess psi) n) of the far boxes,
+// the second derivatives by dual numbers along n.  team: lanes per point (a
+// power of two up to 32) that share the point's far boxes; bem_evf_far takes
+// the same (1 for the off-surface evaluation).
+int bem_gvf_far(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
+                const int* perm, int team, double* acc, cudaStream_t s);
 int bem_evf_out(int nrhs, int mode, int64_t np, const int* perm, const double* acc, int dtype, void* out,
                 cudaStream_t s);
 int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,

@@ -78,6 +78,54 @@ __global__ void k_evf_gather(int64_t np, WalkTree wt, const int* __restrict__ pe
   }
 }
 
+static int walk_fail(cudaError_t e) {
+  return bem_fail(e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA, cudaGetErrorString(e));
+}
+#define WALK_CUDA(call)                      \
+  do {                                       \
+    const cudaError_t e_ = (call);           \
+    if (e_ != cudaSuccess) return walk_fail(e_); \
+  } while (0)
+
+int bem_walk_order(const WalkTree& wt, int64_t np, const double* points, WalkOrder& wo, cudaStream_t s) {
+  if (np > 0x7fffffffLL) return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
+  WALK_CUDA(cudaMallocAsync((void**)&wo.keys_in, np * sizeof(unsigned long long), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.keys, np * sizeof(unsigned long long), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.idx_in, np * sizeof(int), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.perm, np * sizeof(int), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.tcs, 3 * np * sizeof(int), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.spts, 3 * np * sizeof(double), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.nearflag, np * sizeof(int), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.near_list, np * sizeof(int), s));
+  WALK_CUDA(cudaMallocAsync((void**)&wo.n_near, sizeof(int), s));
+  k_evf_keys<<<nblk(np, 256), 256, 0, s>>>(np, wt, points, wo.keys_in, wo.idx_in);
+  WALK_CUDA(cudaGetLastError());
+  size_t tb = 0;
+  WALK_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, wo.keys_in, wo.keys, wo.idx_in, wo.perm, (int)np, 0, 63, s));
+  WALK_CUDA(cudaMallocAsync(&wo.tmp, tb, s));
+  WALK_CUDA(cub::DeviceRadixSort::SortPairs(wo.tmp, tb, wo.keys_in, wo.keys, wo.idx_in, wo.perm, (int)np, 0, 63, s));
+  k_evf_gather<<<nblk(np, 256), 256, 0, s>>>(np, wt, wo.perm, points, wo.spts, wo.tcs);
+  WALK_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+int bem_walk_near_list(int64_t np, WalkOrder& wo, cudaStream_t s) {
+  // the points whose walk has near leaves, in walk order (idx_in still holds
+  // 0 .. np - 1: the sort wrote its output to perm)
+  size_t tb2 = 0;
+  WALK_CUDA(cub::DeviceSelect::Flagged(nullptr, tb2, wo.idx_in, wo.nearflag, wo.near_list, wo.n_near, (int)np, s));
+  WALK_CUDA(cudaMallocAsync(&wo.tmp2, tb2, s));
+  WALK_CUDA(cub::DeviceSelect::Flagged(wo.tmp2, tb2, wo.idx_in, wo.nearflag, wo.near_list, wo.n_near, (int)np, s));
+  return BEM_OK;
+}
+
+void bem_walk_free(WalkOrder& wo, cudaStream_t s) {
+  for (void* p : {(void*)wo.keys_in, (void*)wo.keys, (void*)wo.idx_in, (void*)wo.perm, (void*)wo.tcs,
+                  (void*)wo.spts, (void*)wo.nearflag, (void*)wo.near_list, (void*)wo.n_near, wo.tmp, wo.tmp2})
+    if (p) cudaFreeAsync(p, s);
+  wo = WalkOrder();
+}
+
 int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* y, const double* points,
                  int64_t np, void* out, int mode, cudaStream_t s) {
   if (np > 0x7fffffffLL) return bem_fail(BEM_ERR_INVALID_ARG, "too many points for one call");
@@ -85,48 +133,23 @@ int bem_eval_fmm(bem_handle* h, int nrhs, int dtype, const void* x, const void* 
   const int nc = mode == 0 ? 1 : (mode == 1 ? 3 : 4);
   BEM_TRY(bem_prologue(h, nrhs, dtype, x, y, s));
   BEM_TRY(bem_run_upward(h, nrhs, s));
-  unsigned long long *keys_in = nullptr, *keys = nullptr;
-  int *idx_in = nullptr, *perm = nullptr, *tcs = nullptr, *nearflag = nullptr, *near_list = nullptr, *n_near = nullptr;
-  double *spts = nullptr, *acc = nullptr;
-  void *tmp = nullptr, *tmp2 = nullptr;
-  size_t tb = 0, tb2 = 0;
+  WalkOrder wo;
+  double* acc = nullptr;
   int rc = BEM_OK;
-  auto fail = [&](cudaError_t e) {
-    if (rc == BEM_OK && e != cudaSuccess)
-      rc = bem_fail(e == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA, cudaGetErrorString(e));
-    return rc != BEM_OK;
-  };
   do {
-    if (fail(cudaMallocAsync((void**)&keys_in, np * sizeof(unsigned long long), s))) break;
-    if (fail(cudaMallocAsync((void**)&keys, np * sizeof(unsigned long long), s))) break;
-    if (fail(cudaMallocAsync((void**)&idx_in, np * sizeof(int), s))) break;
-    if (fail(cudaMallocAsync((void**)&perm, np * sizeof(int), s))) break;
-    if (fail(cudaMallocAsync((void**)&tcs, 3 * np * sizeof(int), s))) break;
-    if (fail(cudaMallocAsync((void**)&spts, 3 * np * sizeof(double), s))) break;
-    if (fail(cudaMallocAsync((void**)&acc, 2 * nc * nrhs * np * sizeof(double), s))) break;
-    if (fail(cudaMallocAsync((void**)&nearflag, np * sizeof(int), s))) break;
-    if (fail(cudaMallocAsync((void**)&near_list, np * sizeof(int), s))) break;
-    if (fail(cudaMallocAsync((void**)&n_near, sizeof(int), s))) break;
-    k_evf_keys<<<nblk(np, 256), 256, 0, s>>>(np, wt, points, keys_in, idx_in);
-    if (fail(cudaGetLastError())) break;
-    if (fail(cub::DeviceRadixSort::SortPairs(nullptr, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
-    if (fail(cudaMallocAsync(&tmp, tb, s))) break;
-    if (fail(cub::DeviceRadixSort::SortPairs(tmp, tb, keys_in, keys, idx_in, perm, (int)np, 0, 63, s))) break;
-    k_evf_gather<<<nblk(np, 256), 256, 0, s>>>(np, wt, perm, points, spts, tcs);
-    if (fail(cudaGetLastError())) break;
-    rc = bem_evf_far(h, wt, nrhs, mode, np, spts, tcs, acc, nearflag, s);
-    if (rc != BEM_OK) break;
-    // the points whose walk has near leaves, in walk order (idx_in still
-    // holds 0 .. np - 1: the sort wrote its output to perm)
-    if (fail(cub::DeviceSelect::Flagged(nullptr, tb2, idx_in, nearflag, near_list, n_near, (int)np, s))) break;
-    if (fail(cudaMallocAsync(&tmp2, tb2, s))) break;
-    if (fail(cub::DeviceSelect::Flagged(tmp2, tb2, idx_in, nearflag, near_list, n_near, (int)np, s))) break;
-    rc = bem_evf_near(h, wt, nrhs, mode, np, spts, tcs, near_list, n_near, acc, s);
-    if (rc != BEM_OK) break;
-    rc = bem_evf_out(nrhs, mode, np, perm, acc, dtype, out, s);
+    const cudaError_t e = cudaMallocAsync((void**)&acc, 2 * nc * nrhs * np * sizeof(double), s);
+    if (e != cudaSuccess) {
+      rc = walk_fail(e);
+      break;
+    }
+    if ((rc = bem_walk_order(wt, np, points, wo, s)) != BEM_OK) break;
+    if ((rc = bem_evf_far(h, wt, nrhs, mode, np, wo.spts, wo.tcs, acc, wo.nearflag, 1, s)) != BEM_OK) break;
+    if ((rc = bem_walk_near_list(np, wo, s)) != BEM_OK) break;
+    if ((rc = bem_evf_near(h, wt, nrhs, mode, np, wo.spts, wo.tcs, wo.near_list, wo.n_near, acc, 1, s)) != BEM_OK)
+      break;
+    rc = bem_evf_out(nrhs, mode, np, wo.perm, acc, dtype, out, s);
   } while (false);
-  for (void* p : {(void*)keys_in, (void*)keys, (void*)idx_in, (void*)perm, (void*)tcs, (void*)spts, (void*)acc,
-                  (void*)nearflag, (void*)near_list, (void*)n_near, tmp, tmp2})
-    if (p) cudaFreeAsync(p, s);
+  if (acc) cudaFreeAsync(acc, s);
+  bem_walk_free(wo, s);
   return rc;
 }

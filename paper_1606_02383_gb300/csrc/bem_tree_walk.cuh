@@ -9,7 +9,9 @@
 //   far   D does not touch the point's box at level l (t >> (L - l)), and the
 //         gap between the point's level-L box and D is at least 4 h_max(D),
 //         so no element of D needs the near-singular rule at x: the multipole
-//         of D is evaluated at x (M2P);
+//         of D is evaluated at x (M2P).  (WalkTree.gap_scale2 scales the
+//         squared gap: the vertex gradient, regular rule only, asks for one
+//         h_max);
 //   near  otherwise, if D is a leaf: its elements are summed directly, each
 //         with the rule its distance calls for;
 //   open  otherwise: D's children are walked.
@@ -37,12 +39,33 @@ struct WalkTree {
   int L = 0;
   double lo[3] = {0, 0, 0};  // corner of the root cube
   double wL = 0;             // width of a level-L box
+  float gap_scale2 = 1.0f;   // the far test's gap in units of 4 h_max(D), squared
 };
+
+// Field points in walk order (bem_eval_fmm.cu): sorted along a Morton curve of
+// their level-L boxes.  perm[i] is the caller's index of walk point i, spts and
+// tcs its coordinates and box; nearflag / near_list / n_near the points whose
+// walk has near leaves, filled by the far pass and bem_walk_near_list.
+struct WalkOrder {
+  unsigned long long *keys_in = nullptr, *keys = nullptr;
+  int *idx_in = nullptr, *perm = nullptr, *tcs = nullptr, *nearflag = nullptr, *near_list = nullptr,
+      *n_near = nullptr;
+  double* spts = nullptr;
+  void *tmp = nullptr, *tmp2 = nullptr;
+};
+WalkTree bem_walk_tree(const bem_handle* h);
+// allocates wo's arrays (stream-ordered) and sorts the np points; on failure
+// the arrays allocated so far stay in wo for bem_walk_free
+int bem_walk_order(const WalkTree& wt, int64_t np, const double* points, WalkOrder& wo, cudaStream_t s);
+int bem_walk_near_list(int64_t np, WalkOrder& wo, cudaStream_t s);
+void bem_walk_free(WalkOrder& wo, cudaStream_t s);
 
 // stack bound: one level-2 box, then at most 7 pending siblings on each of
 // the levels 3 .. 10 and the 8 children of the box being opened
 #define WALK_STACK 72
 #define WALK_COORD_MAX (1 << 20)
+// far boxes a lane of a walking team lists before it evaluates them
+#define WALK_OWN 48
 
 // the level-L box of a point (clamped far outside: such a point stays far
 // from every box)
@@ -79,7 +102,7 @@ __device__ __forceinline__ void tree_walk(const WalkTree& wt, const int* t, Visi
         if (t[a] - hi > g) g = t[a] - hi;
         g2 += g * g;
       }
-      if (!adj && (float)g2 >= lv.gap2[b]) {
+      if (!adj && (float)g2 >= wt.gap_scale2 * lv.gap2[b]) {
         visit(0, l, b);
         continue;
       }

@@ -378,6 +378,48 @@ __global__ void k_p2l_t(int npair, const int* __restrict__ xdst, const int* __re
 }
 
 // --------------------------------------------------- M2P at field points --
+// Forward-mode dual numbers v + d e (e^2 = 0): run through the M2P below with
+// the point moved along a direction n (d of the coordinates = n), the value
+// comes out with its derivative along n and the gradient with (Hess u) n.
+template <typename R>
+struct Dual {
+  R v, d;
+  __device__ __forceinline__ Dual() {}
+  __device__ __forceinline__ Dual(R a) : v(a), d(R(0)) {}
+  __device__ __forceinline__ Dual(R a, R b) : v(a), d(b) {}
+  friend __device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+  friend __device__ __forceinline__ Dual operator+(Dual a, R b) { return Dual(a.v + b, a.d); }
+  friend __device__ __forceinline__ Dual operator+(R a, Dual b) { return Dual(a + b.v, b.d); }
+  friend __device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+  friend __device__ __forceinline__ Dual operator-(Dual a, R b) { return Dual(a.v - b, a.d); }
+  friend __device__ __forceinline__ Dual operator-(R a, Dual b) { return Dual(a - b.v, -b.d); }
+  friend __device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+  friend __device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.v * b.d + a.d * b.v); }
+  friend __device__ __forceinline__ Dual operator*(Dual a, R b) { return Dual(a.v * b, a.d * b); }
+  friend __device__ __forceinline__ Dual operator*(R a, Dual b) { return Dual(a * b.v, a * b.d); }
+  friend __device__ __forceinline__ Dual operator/(Dual a, R b) { return Dual(a.v / b, a.d / b); }
+  friend __device__ __forceinline__ Dual operator/(R a, Dual b) {
+    const R q = a / b.v;
+    return Dual(q, -q * b.d / b.v);
+  }
+  __device__ __forceinline__ Dual& operator+=(Dual b) {
+    v += b.v;
+    d += b.d;
+    return *this;
+  }
+  friend __device__ __forceinline__ Dual sqrt(Dual a) {
+    const R r = sqrt(a.v);
+    return Dual(r, a.d / (R(2) * r));
+  }
+};
+template <typename R>
+__device__ __forceinline__ void sc(Dual<R> x, Dual<R>* s, Dual<R>* c) {
+  R sn, cs;
+  sc(x.v, &sn, &cs);
+  *s = Dual<R>(sn, cs * x.d);
+  *c = Dual<R>(cs, -sn * x.d);
+}
+
 // The multipole of one far box evaluated at one point (the off-surface walk,
 // bem_tree_walk.cuh), for NR right-hand sides at once: the same h^_n, Y_nm
 // recurrences as outgoing_rows, with the pair (n, m), (n, -m) folded into
@@ -386,35 +428,38 @@ __global__ void k_p2l_t(int npair, const int* __restrict__ xdst, const int* __re
 //   grad u += (v/|v|) sum_n h^_n'(r) Z_n + sum_n h^_n grad Z_n,
 // grad Z taking grad Y_nm = grad(W_n^m(u_z)) (u_x + i u_y)^m + W_n^m grad (u_x + i u_y)^m
 // with du_a/dv_c = (delta_ac - u_a u_c) / |v| (the chain rule through u = v / |v|).
-template <typename R, bool GRAD, int NR>
-__device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, const R* const (&Md)[NR],
-                                          R (&val)[NR][2], R (&grd)[NR][3][2]) {
+// D is the number type of everything that depends on the point: R, or Dual<R>.
+template <typename R, typename D, bool GRAD, int NR>
+__device__ __forceinline__ void m2p_point_t(int p, R k, R a, D vx, D vy, D vz, const R* const (&Md)[NR],
+                                            D (&val)[NR][2], D (&grd)[NR][3][2]) {
   typedef WxTab<R> T;
-  R hr[WX_T], hi[WX_T], dhr[GRAD ? WX_T : 1], dhi[GRAD ? WX_T : 1];
-  const R r = sqrt(vx * vx + vy * vy + vz * vz);
-  const R ir = R(1) / r;
-  const R x = k * r, ix = ir / k;
-  R sn, cs;
+  D hr[WX_T], hi[WX_T], dhr[GRAD ? WX_T : 1], dhi[GRAD ? WX_T : 1];
+  const D r = sqrt(vx * vx + vy * vy + vz * vz);
+  const D ir = R(1) / r;
+  const D x = k * r, ix = ir / k;
+  D sn, cs;
   sc(x, &sn, &cs);
   const R a2 = a * a, a3 = a / R(3);
   hr[0] = sn * ix;
   hi[0] = -cs * ix;
   hr[1] = a3 * ((-cs + sn * ix) * ix);
   hi[1] = a3 * ((-cs * ix - sn) * ix);
-  const R aix = a * ix;
+  const D aix = a * ix;
   for (int n = 1; n < p; ++n) {
-    const R c1 = aix * T::t1(n), c2 = a2 * T::t2(n);
+    const D c1 = aix * T::t1(n);
+    const R c2 = a2 * T::t2(n);
     hr[n + 1] = c1 * hr[n] - c2 * hr[n - 1];
     hi[n + 1] = c1 * hi[n] - c2 * hi[n - 1];
   }
-  const R u[3] = {vx * ir, vy * ir, vz * ir};
-  R dux[3], duy[3], duz[3];
+  const D u[3] = {vx * ir, vy * ir, vz * ir};
+  D dux[3], duy[3], duz[3];
   if constexpr (GRAD) {
     const R ka = k * (R(3) / a);
     dhr[0] = -ka * hr[1];
     dhi[0] = -ka * hi[1];
     for (int n = 1; n <= p; ++n) {
-      const R c1 = a * T::t3(n), c2 = R(n + 1) * ix;
+      const R c1 = a * T::t3(n);
+      const D c2 = R(n + 1) * ix;
       dhr[n] = k * (c1 * hr[n - 1] - c2 * hr[n]);
       dhi[n] = k * (c1 * hi[n - 1] - c2 * hi[n]);
     }
@@ -425,18 +470,20 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
       duz[c] = ((c == 2 ? R(1) : R(0)) - u[2] * u[c]) * ir;
     }
   }
-  R Ar[NR], Ai[NR];
+  D Ar[NR], Ai[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) Ar[q] = Ai[q] = 0;
-  R pr = 1, pi = 0, dpr[3] = {0, 0, 0}, dpi[3] = {0, 0, 0};
+  for (int q = 0; q < NR; ++q) Ar[q] = Ai[q] = D(R(0));
+  D pr = D(R(1)), pi = D(R(0)), dpr[3], dpi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dpr[c] = dpi[c] = D(R(0));
   for (int m = 0; m <= p; ++m) {
     if (m > 0) {
-      const R npr = pr * u[0] - pi * u[1], npi = pr * u[1] + pi * u[0];
+      const D npr = pr * u[0] - pi * u[1], npi = pr * u[1] + pi * u[0];
       if constexpr (GRAD) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const R ndr = dpr[c] * u[0] - dpi[c] * u[1] + pr * dux[c] - pi * duy[c];
-          const R ndi = dpr[c] * u[1] + dpi[c] * u[0] + pr * duy[c] + pi * dux[c];
+          const D ndr = dpr[c] * u[0] - dpi[c] * u[1] + pr * dux[c] - pi * duy[c];
+          const D ndi = dpr[c] * u[1] + dpi[c] * u[0] + pr * duy[c] + pi * dux[c];
           dpr[c] = ndr;
           dpi[c] = ndi;
         }
@@ -444,14 +491,18 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
       pr = npr;
       pi = npi;
     }
-    R w1 = T::q(m), w2 = 0, dw1[3] = {0, 0, 0}, dw2[3] = {0, 0, 0};
+    D w1 = D(T::q(m)), w2 = D(R(0)), dw1[3], dw2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dw1[c] = dw2[c] = D(R(0));
     const R c1m = T::c1(m);
     for (int n = m; n <= p; ++n) {
-      R w, dw[3] = {0, 0, 0};
+      D w, dw[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dw[c] = D(R(0));
       if (n == m) {
         w = w1;
       } else if (n == m + 1) {
-        w = c1m * u[2] * w1;
+        w = (c1m * u[2]) * w1;
         if constexpr (GRAD)
 #pragma unroll
           for (int c = 0; c < 3; ++c) dw[c] = c1m * (duz[c] * w1 + u[2] * dw1[c]);
@@ -471,20 +522,20 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
           dw1[c] = dw[c];
         }
       }
-      const R yr = w * pr, yi = w * pi;
-      const R h_r = hr[n], h_i = hi[n];
+      const D yr = w * pr, yi = w * pi;
+      const D h_r = hr[n], h_i = hi[n];
       const int qp = wx_idx(n, m), qm = wx_idx(n, -m);
 #pragma unroll
       for (int q = 0; q < NR; ++q) {
         const R mpr = Md[q][2 * qp], mpi = Md[q][2 * qp + 1];
         // Z = M+ Y + M- conj(Y)
-        R zr = mpr * yr - mpi * yi, zi = mpr * yi + mpi * yr;
+        D zr = mpr * yr - mpi * yi, zi = mpr * yi + mpi * yr;
         R mmr = 0, mmi = 0;
         if (m > 0) {
           mmr = Md[q][2 * qm];
           mmi = Md[q][2 * qm + 1];
-          zr += mmr * yr + mmi * yi;
-          zi += -mmr * yi + mmi * yr;
+          zr = zr + (mmr * yr + mmi * yi);
+          zi = zi + (-mmr * yi + mmi * yr);
         }
         val[q][0] += h_r * zr - h_i * zi;
         val[q][1] += h_r * zi + h_i * zr;
@@ -493,9 +544,9 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
           Ai[q] += dhr[n] * zi + dhi[n] * zr;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const R dyr = dw[c] * pr + w * dpr[c], dyi = dw[c] * pi + w * dpi[c];
-            const R gzr = mpr * dyr - mpi * dyi + (mmr * dyr + mmi * dyi);
-            const R gzi = mpr * dyi + mpi * dyr + (-mmr * dyi + mmi * dyr);
+            const D dyr = dw[c] * pr + w * dpr[c], dyi = dw[c] * pi + w * dpi[c];
+            const D gzr = mpr * dyr - mpi * dyi + (mmr * dyr + mmi * dyi);
+            const D gzi = mpr * dyi + mpi * dyr + (-mmr * dyi + mmi * dyr);
             grd[q][c][0] += h_r * gzr - h_i * gzi;
             grd[q][c][1] += h_r * gzi + h_i * gzr;
           }
@@ -513,24 +564,51 @@ __device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, con
       }
   }
 }
+template <typename R, bool GRAD, int NR>
+__device__ __forceinline__ void m2p_point(int p, R k, R a, R vx, R vy, R vz, const R* const (&Md)[NR],
+                                          R (&val)[NR][2], R (&grd)[NR][3][2]) {
+  m2p_point_t<R, R, GRAD, NR>(p, k, a, vx, vy, vz, Md, val, grd);
+}
 
-// One thread per field point (in the walk's order): the multipoles of the
-// point's far boxes.  Writes acc[r][i][c] (FP64 complex), c over the
-// components of the mode (0: u; 1: grad u; 2: u, grad u), and nearflag[i]:
-// whether the point's walk has near leaves.
+// Teams of `team` consecutive lanes (a power of two, at most 32) per field
+// point (in the walk's order): the lanes of a team walk the tree together,
+// each keeping a list of the far boxes it takes (the c-th far box goes to lane
+// c mod team; beyond WALK_OWN of them a lane evaluates at once), evaluate
+// their lists side by side after the walk, then sum their parts over the
+// team.  team = 1 for dense point sets;
+// larger teams keep the GPU full when the points are few (the vertex
+// gradient's on-surface points).  Lanes past the last point walk nothing but
+// take part in the team sums.
+template <int NV>
+__device__ __forceinline__ void team_sum(float (&v)[NV], int team) {
+  for (int o = team >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+}
+template <int NV>
+__device__ __forceinline__ void team_sum(double (&v)[NV], int team) {
+  for (int o = team >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+}
+
+// The multipoles of the point's far boxes.  Writes acc[r][i][c] (FP64
+// complex), c over the components of the mode (0: u; 1: grad u; 2: u, grad u),
+// and nearflag[i]: whether the point's walk has near leaves.
 template <typename R, int MODE, int NR>
-__global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt, const double* __restrict__ pts,
-                                                 const int* __restrict__ tcs, LevTab lt, const int* __restrict__ lev_p,
+__global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, int team, WalkTree wt,
+                                                 const double* __restrict__ pts, const int* __restrict__ tcs,
+                                                 LevTab lt, const int* __restrict__ lev_p,
                                                  const R* __restrict__ lev_a, R k, const R* __restrict__ M,
                                                  int64_t exp_stride, double* __restrict__ acc,
                                                  int* __restrict__ nearflag) {
   constexpr bool GRAD = MODE != 0;
   constexpr int NC = MODE == 0 ? 1 : (MODE == 1 ? 3 : 4);
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= np) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = gt / team;
+  const int tl = (int)(gt & (team - 1));
+  const bool live = i < np;
   bool near = false;
-  const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
-  const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
   R val[NR][2], grd[NR][3][2];
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
@@ -538,18 +616,61 @@ __global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt
 #pragma unroll
     for (int c = 0; c < 3; ++c) grd[q][c][0] = grd[q][c][1] = 0;
   }
-  tree_walk(wt, t, [&](int kind, int l, int b) {
-    if (kind != 0) {
-      near = true;
-      return;
-    }
-    const double* c = wt.lv[l].centre + 3 * b;
-    const R vx = (R)(X[0] - c[0]), vy = (R)(X[1] - c[1]), vz = (R)(X[2] - c[2]);
-    const R* Md[NR];
+  if (live) {
+    const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+    const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+    auto m2p = [&](int l, int b) {
+      const double* c = wt.lv[l].centre + 3 * b;
+      const R vx = (R)(X[0] - c[0]), vy = (R)(X[1] - c[1]), vz = (R)(X[2] - c[2]);
+      const R* Md[NR];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) Md[q] = M + 2 * ((int64_t)(r0 + q) * exp_stride + lt.base[l] + (int64_t)b * lt.P[l]);
-    m2p_point<R, GRAD, NR>(lev_p[l], k, lev_a[l], vx, vy, vz, Md, val, grd);
-  });
+      for (int q = 0; q < NR; ++q)
+        Md[q] = M + 2 * ((int64_t)(r0 + q) * exp_stride + lt.base[l] + (int64_t)b * lt.P[l]);
+      m2p_point<R, GRAD, NR>(lev_p[l], k, lev_a[l], vx, vy, vz, Md, val, grd);
+    };
+    int own[WALK_OWN], no = 0, cnt = 0;
+    tree_walk(wt, t, [&](int kind, int l, int b) {
+      if (kind != 0) {
+        near = true;
+        return;
+      }
+      if (team == 1) {
+        m2p(l, b);
+        return;
+      }
+      if ((cnt++ & (team - 1)) != tl) return;
+      if (no < WALK_OWN)
+        own[no++] = (l << 24) | b;
+      else
+        m2p(l, b);
+    });
+    for (int u = 0; u < no; ++u) m2p(own[u] >> 24, own[u] & 0xFFFFFF);
+  }
+  if (team > 1) {
+    R v[NR * 8];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      v[8 * q] = val[q][0];
+      v[8 * q + 1] = val[q][1];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[8 * q + 2 + 2 * c] = grd[q][c][0];
+        v[8 * q + 3 + 2 * c] = grd[q][c][1];
+      }
+    }
+    team_sum(v, team);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      val[q][0] = v[8 * q];
+      val[q][1] = v[8 * q + 1];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        grd[q][c][0] = v[8 * q + 2 + 2 * c];
+        grd[q][c][1] = v[8 * q + 3 + 2 * c];
+      }
+    }
+  }
+  if (!live || tl != 0) return;
   if (r0 == 0) nearflag[i] = near ? 1 : 0;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
@@ -566,6 +687,83 @@ __global__ void __launch_bounds__(128) k_evf_far(int64_t np, int r0, WalkTree wt
         o[2 * (c0 + c)] = (double)grd[q][c][0];
         o[2 * (c0 + c) + 1] = (double)grd[q][c][1];
       }
+  }
+}
+
+// The vertex gradient's source side, far boxes: a team of lanes per walk point
+// (as in k_evf_far), a quadrature point of element j = perm[i] / 3.  The
+// multipoles are those of the point charges conj(g_i) at the centroids, so the
+// walk sums psi(y) = sum_i conj(g_i) G(y - x_i); with the point moved along
+// the normal n_j as a dual number it returns psi, n.grad psi, grad psi and
+// (Hess psi) n.  Writes acc[r][i][0..7] (FP64 complex) = psi, grad psi (3),
+// n.grad psi, (Hess psi) n (3).
+template <typename R, int NR>
+__global__ void __launch_bounds__(128) k_gvf_far(int64_t np, int r0, int team, WalkTree wt,
+                                                 const double* __restrict__ pts, const int* __restrict__ tcs,
+                                                 const int* __restrict__ perm, const double* __restrict__ nrm,
+                                                 LevTab lt, const int* __restrict__ lev_p,
+                                                 const R* __restrict__ lev_a, R k, const R* __restrict__ M,
+                                                 int64_t exp_stride, double* __restrict__ acc) {
+  typedef Dual<R> D;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = gt / team;
+  const int tl = (int)(gt & (team - 1));
+  const bool live = i < np;
+  D val[NR][2], grd[NR][3][2];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    val[q][0] = val[q][1] = D(R(0));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) grd[q][c][0] = grd[q][c][1] = D(R(0));
+  }
+  if (live) {
+    const double X[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+    const int t[3] = {tcs[3 * i], tcs[3 * i + 1], tcs[3 * i + 2]};
+    const int64_t j = perm[i] / 3;
+    const R n[3] = {(R)nrm[3 * j], (R)nrm[3 * j + 1], (R)nrm[3 * j + 2]};
+    auto m2p = [&](int l, int b) {
+      const double* c = wt.lv[l].centre + 3 * b;
+      const D vx((R)(X[0] - c[0]), n[0]), vy((R)(X[1] - c[1]), n[1]), vz((R)(X[2] - c[2]), n[2]);
+      const R* Md[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        Md[q] = M + 2 * ((int64_t)(r0 + q) * exp_stride + lt.base[l] + (int64_t)b * lt.P[l]);
+      m2p_point_t<R, D, true, NR>(lev_p[l], k, lev_a[l], vx, vy, vz, Md, val, grd);
+    };
+    int own[WALK_OWN], no = 0, cnt = 0;
+    tree_walk(wt, t, [&](int kind, int l, int b) {
+      if (kind != 0) return;
+      if ((cnt++ & (team - 1)) != tl) return;
+      if (no < WALK_OWN)
+        own[no++] = (l << 24) | b;
+      else
+        m2p(l, b);
+    });
+    for (int u = 0; u < no; ++u) m2p(own[u] >> 24, own[u] & 0xFFFFFF);
+  }
+  // component order of acc: psi, grad psi (3), n.grad psi, (Hess psi) n (3)
+  R v[NR * 16];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    v[16 * q] = val[q][0].v;
+    v[16 * q + 1] = val[q][1].v;
+    v[16 * q + 8] = val[q][0].d;
+    v[16 * q + 9] = val[q][1].d;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[16 * q + 2 + 2 * c] = grd[q][c][0].v;
+      v[16 * q + 3 + 2 * c] = grd[q][c][1].v;
+      v[16 * q + 10 + 2 * c] = grd[q][c][0].d;
+      v[16 * q + 11 + 2 * c] = grd[q][c][1].d;
+    }
+  }
+  team_sum(v, team);
+  if (!live || tl != 0) return;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    double* o = acc + 16 * ((int64_t)(r0 + q) * np + i);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = (double)v[16 * q + c];
   }
 }
 
@@ -736,36 +934,67 @@ int bem_run_p2l_t(bem_handle* h, int nrhs, const void* Lam, double4* uv, cudaStr
 
 template <typename R, int MODE>
 static int evf_far_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
-                        double* acc, int* nearflag, cudaStream_t s) {
+                        double* acc, int* nearflag, int team, cudaStream_t s) {
   const LevTab lt = bem_levtab(h);
-  const unsigned g = nblk(np, 128);
+  const unsigned g = nblk(np * team, 128);
   for (int r0 = 0; r0 < nrhs;) {
     const int rem = nrhs - r0;
+#define EVF_FAR(NRV)                                                                                       \
+  k_evf_far<R, MODE, NRV><<<g, 128, 0, s>>>(np, r0, team, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a,   \
+                                            (R)h->k, (const R*)h->Mexp, h->exp_total, acc, nearflag);      \
+  r0 += NRV;
     if (rem >= 4) {
-      k_evf_far<R, MODE, 4><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
-      r0 += 4;
+      EVF_FAR(4)
     } else if (rem >= 2) {
-      k_evf_far<R, MODE, 2><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
-      r0 += 2;
+      EVF_FAR(2)
     } else {
-      k_evf_far<R, MODE, 1><<<g, 128, 0, s>>>(np, r0, wt, pts, tcs, lt, h->wx_p, (const R*)h->wx_a, (R)h->k,
-                                              (const R*)h->Mexp, h->exp_total, acc, nearflag);
-      r0 += 1;
+      EVF_FAR(1)
     }
+#undef EVF_FAR
     BEM_CUDA(cudaGetLastError());
   }
   return BEM_OK;
 }
 
 int bem_evf_far(bem_handle* h, const WalkTree& wt, int nrhs, int mode, int64_t np, const double* pts,
-                const int* tcs, double* acc, int* nearflag, cudaStream_t s) {
+                const int* tcs, double* acc, int* nearflag, int team, cudaStream_t s) {
+  if (team < 1 || team > 32 || (team & (team - 1))) return bem_fail(BEM_ERR_INVALID_ARG, "bad walk team size");
   const bool f64 = bem_is_fp64(h);
-  if (mode == 0) return f64 ? evf_far_impl<double, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
-                            : evf_far_impl<float, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
-  if (mode == 1) return f64 ? evf_far_impl<double, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
-                            : evf_far_impl<float, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
-  return f64 ? evf_far_impl<double, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s)
-             : evf_far_impl<float, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, s);
+  if (mode == 0) return f64 ? evf_far_impl<double, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s)
+                            : evf_far_impl<float, 0>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s);
+  if (mode == 1) return f64 ? evf_far_impl<double, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s)
+                            : evf_far_impl<float, 1>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s);
+  return f64 ? evf_far_impl<double, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s)
+             : evf_far_impl<float, 2>(h, wt, nrhs, np, pts, tcs, acc, nearflag, team, s);
+}
+
+template <typename R>
+static int gvf_far_impl(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
+                        const int* perm, int team, double* acc, cudaStream_t s) {
+  const LevTab lt = bem_levtab(h);
+  const unsigned g = nblk(np * team, 128);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int rem = nrhs - r0;
+#define GVF_FAR(NRV)                                                                                          \
+  k_gvf_far<R, NRV><<<g, 128, 0, s>>>(np, r0, team, wt, pts, tcs, perm, h->nrm, lt, h->wx_p, (const R*)h->wx_a, \
+                                      (R)h->k, (const R*)h->Mexp, h->exp_total, acc);                          \
+  r0 += NRV;
+    if (rem >= 4) {
+      GVF_FAR(4)
+    } else if (rem >= 2) {
+      GVF_FAR(2)
+    } else {
+      GVF_FAR(1)
+    }
+#undef GVF_FAR
+    BEM_CUDA(cudaGetLastError());
+  }
+  return BEM_OK;
+}
+
+int bem_gvf_far(bem_handle* h, const WalkTree& wt, int nrhs, int64_t np, const double* pts, const int* tcs,
+                const int* perm, int team, double* acc, cudaStream_t s) {
+  if (team < 1 || team > 32 || (team & (team - 1))) return bem_fail(BEM_ERR_INVALID_ARG, "bad walk team size");
+  return bem_is_fp64(h) ? gvf_far_impl<double>(h, wt, nrhs, np, pts, tcs, perm, team, acc, s)
+                        : gvf_far_impl<float>(h, wt, nrhs, np, pts, tcs, perm, team, acc, s);
 }

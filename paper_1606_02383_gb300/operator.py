@@ -32,13 +32,14 @@ def _dtype_code(t: torch.Tensor) -> int:
 
 
 def _options(mode="mixed", leaf_level=0, leaf_target=48, max_nrhs=16, p_min=4, p_max=40, p_level=None, p2p_unit=64,
-             tc_kslice=16, corr_rules32=0, tc_tf32=0, tc_pipeline=0, p2p_ctas=0, p2p_stage=0):
+             tc_kslice=16, corr_rules32=0, tc_tf32=0, tc_pipeline=0, p2p_ctas=0, p2p_stage=0, grad_direct=0):
     levels = (ctypes.c_int * 11)(*([0] * 11))
     for lvl, order in (p_level or {}).items():
         levels[int(lvl)] = int(order)
     return _lib.BemOptions(ctypes.sizeof(_lib.BemOptions), _lib.MODES[mode], int(leaf_level), int(leaf_target),
                            int(max_nrhs), int(p_min), int(p_max), levels, int(p2p_unit), int(tc_kslice),
-                           int(corr_rules32), int(tc_tf32), int(tc_pipeline), int(p2p_ctas), int(p2p_stage))
+                           int(corr_rules32), int(tc_tf32), int(tc_pipeline), int(p2p_ctas), int(p2p_stage),
+                           int(grad_direct))
 
 
 class Operator:
@@ -59,18 +60,20 @@ class Operator:
     block-synchronous, 2 or 4 warp-specialised stages, 0 the default),
     p2p_ctas (FP32 FMM: > 0 runs the near field from this many resident CTAs
     per SM beside the far field, which starts first), p2p_stage (FP32 FMM:
-    the near list's source elements staged in shared memory by cp.async).
+    the near list's source elements staged in shared memory by cp.async),
+    grad_direct (FMM modes: the vertex gradient's regular rule summed over all
+    pairs instead of through the octree).
     """
 
     def __init__(self, vertices, triangles, k, p=0, eps=1e-5, mode="mixed", leaf_level=0, leaf_target=48,
                  max_nrhs=16, p_min=4, p_max=40, p_level=None, p2p_unit=64, tc_kslice=16, corr_rules32=0,
-                 tc_tf32=0, tc_pipeline=0, p2p_ctas=0, p2p_stage=0):
+                 tc_tf32=0, tc_pipeline=0, p2p_ctas=0, p2p_stage=0, grad_direct=0):
         lib = _lib.load()
         V = np.ascontiguousarray(vertices, dtype=np.float64)
         T = np.ascontiguousarray(triangles, dtype=np.int32)
         mesh = _lib.BemMesh(V.shape[0], T.shape[0], V.ctypes.data, T.ctypes.data, 0)
         opt = _options(mode, leaf_level, leaf_target, max_nrhs, p_min, p_max, p_level, p2p_unit, tc_kslice,
-                       corr_rules32, tc_tf32, tc_pipeline, p2p_ctas, p2p_stage)
+                       corr_rules32, tc_tf32, tc_pipeline, p2p_ctas, p2p_stage, grad_direct)
         h = ctypes.c_void_p()
         _lib.check(lib.bem_setup(ctypes.byref(mesh), float(k), int(p), float(eps), ctypes.byref(opt), _stream(),
                                  ctypes.byref(h)))

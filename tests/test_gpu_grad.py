@@ -68,12 +68,17 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("mesh", ["icosphere3_jittered", "level_set_slivers"])
-@pytest.mark.parametrize("mode,p,leaf,tol", [("direct64", 0, 0, 1e-10), ("mixed", 10, 3, 1e-5)])
-def test_vertex_gradient_matches_oracle(cuda_ok, mesh, mode, p, leaf, tol):
+@pytest.mark.parametrize("mode,p,leaf,direct,tol", [("direct64", 0, 0, 0, 1e-10), ("mixed", 10, 3, 1, 1e-5),
+                                                    ("mixed", 10, 3, 0, 1e-4), ("fp64", 16, 3, 0, 2e-6)])
+def test_vertex_gradient_matches_oracle(cuda_ok, mesh, mode, p, leaf, direct, tol):
     """Every vertex: GPU dL/dV against the oracle's dual-number gradient.  FP64
-    direct differs only by rounding; the mixed modes sum the regular rule in FP32
-    (block-relative coordinates, FP64 between tiles) and keep the corrections in
-    FP64, which gives about 1e-6."""
+    direct differs only by rounding.  With direct = 1 the mixed mode sums the
+    regular rule over all pairs in FP32 (block-relative coordinates split into
+    high and low parts, FP64 between tiles) and keeps the corrections in FP64,
+    which gives about 1e-6.  Through the tree (direct = 0) the far boxes add the
+    truncation of their expansions, first and second derivatives included:
+    measured 2e-5 (mixed, p = 10) and 1e-6 (FP64, p = 16) on the jittered
+    sphere, whose leaves are only about 1.5 longest edges wide."""
     if mesh == "icosphere3_jittered":
         V, T = _jittered(3)
     else:
@@ -82,27 +87,55 @@ def test_vertex_gradient_matches_oracle(cuda_ok, mesh, mode, p, leaf, tol):
     k = 2.7
     x, y, g = (inputs.random_density(n, 2, seed=s) for s in (51, 52, 53))
     dV_ref, dk_ref = oracle.grad(V, T, k, g, x, y)
-    op = Operator(V, T, k, p=p, mode=mode, leaf_level=leaf)
+    op = Operator(V, T, k, p=p, mode=mode, leaf_level=leaf, grad_direct=direct)
     dV, dk = op.grad(dev(g), dev(x), dev(y))
     assert _rel(dV, dV_ref) <= tol, _rel(dV, dV_ref)
     assert abs(dk - dk_ref) <= max(tol, 1e-9) * abs(dk_ref)
 
 
-def test_vertex_gradient_sampled_at_30k(cuda_ok):
+@pytest.mark.parametrize("direct,tol", [(1, 1e-5), (0, 1e-4)])
+def test_vertex_gradient_sampled_at_30k(cuda_ok, direct, tol):
     """The 30,000-triangle level-set surface of the differentiation workload
-    (k = 3, mixed FMM): sampled vertices against the oracle, which differentiates
-    only the pairs that touch them."""
+    (k = 3, mixed FMM, orders from eps = 1e-5): sampled vertices against the
+    oracle, which differentiates only the pairs that touch them.  Through the
+    tree (direct = 0) the far boxes' expansions, differentiated twice, add
+    their truncation (measured 3e-5 on these vertices)."""
     V, T = inputs.level_set_mesh(seed=0)
     n = T.shape[0]
     k = 3.0
     x, y, g = (inputs.random_density(n, 1, seed=s) for s in (61, 62, 63))
-    op = Operator(V, T, k, mode="mixed")
+    op = Operator(V, T, k, mode="mixed", grad_direct=direct)
     dV, dk = op.grad(dev(g), dev(x), dev(y), k=False)
     assert dk is None
     rng = np.random.default_rng(7)
     sel = rng.choice(V.shape[0], 6, replace=False)
     ref, _ = oracle.grad(V, T, k, g, x, y, vertices=sel)
-    assert _rel(dV[sel], ref) <= 1e-5, _rel(dV[sel], ref)
+    assert _rel(dV[sel], ref) <= tol, _rel(dV[sel], ref)
+
+
+@pytest.mark.parametrize("mode,p,leaf,tol", [("mixed", 12, -2, 3e-5), ("mixed", 12, -1, 3e-5),
+                                           ("fp64", 18, -2, 3e-8)])
+def test_vertex_gradient_tree_against_all_pairs(cuda_ok, mode, p, leaf, tol):
+    """The tree's regular-rule sums against the all-pairs sums of the same
+    handle (grad_direct = 1), on adaptive trees with five right-hand sides
+    (the far and near passes in chunks of 4 and 1); dL/dk is unaffected."""
+    V1, T1 = inputs.icosphere(3)
+    V2, T2 = inputs.icosphere(3, 0.3, (1.3, 0.4, -0.2))
+    V, T = inputs.merge_meshes([(V1, T1), (V2, T2)])
+    n = T.shape[0]
+    k = 3.3
+    x, y, g = (inputs.random_density(n, 5, seed=s) for s in (81, 82, 83))
+    common = dict(p=p, mode=mode, leaf_level=leaf, leaf_target=16, max_nrhs=5)
+    op = Operator(V, T, k, **common)
+    levels = {l for l in range(11) if op.info(200 + l) > 0}
+    assert len(levels) >= 2, levels
+    ref = Operator(V, T, k, grad_direct=1, **common)
+    dV, dk = op.grad(dev(g), dev(x), dev(y))
+    dV_ref, dk_ref = ref.grad(dev(g), dev(x), dev(y))
+    assert _rel(dV, dV_ref) <= tol, _rel(dV, dV_ref)
+    assert abs(dk - dk_ref) <= 1e-6 * abs(dk_ref)
+    op.close()
+    ref.close()
 
 
 def test_vertex_gradient_autograd(cuda_ok):
