@@ -75,6 +75,11 @@ __device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F,
   ghfr(d0, d1, d2, k, G, F, H, r);
 }
 
+// 1 / sqrt(x): the hardware reciprocal square root in FP32 (2 ulp), exact
+// division in FP64
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+
 // ------------------------------------------------------ regular rule R_0 --
 // In the FP32 passes every coordinate relative to the block's reference point
 // is held as a high FP32 part and the FP32 rounding of the rest, and a
@@ -152,17 +157,27 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
               d1 += s_ql[e][3 * q + 1] - xl[1];
               d2 += s_ql[e][3 * q + 2] - xl[2];
             }
-            cpx<R> G, F, H;
-            R rr;
-            ghfr(d0, d1, d2, kk, G, F, H, rr);
             const R dn = d0 * n0 + d1 * n1 + d2 * n2;
-            const cpx<R> a = dn * (H * wx) - F * wy;
-            const cpx<R> b = F * wx;
-            KT = KT + G * (cmk(-rr * wy.im, rr * wy.re) + (kk * dn) * wx);
             if constexpr (GX) {
+              cpx<R> G, F, H;
+              R rr;
+              ghfr(d0, d1, d2, kk, G, F, H, rr);
+              const cpx<R> a = dn * (H * wx) - F * wy;
+              const cpx<R> b = F * wx;
+              KT = KT + G * (cmk(-rr * wy.im, rr * wy.re) + (kk * dn) * wx);
               T0 = T0 + d0 * a + n0 * b;
               T1 = T1 + d1 * a + n1 * b;
               T2 = T2 + d2 * a + n2 * b;
+            } else {
+              // dL/dk alone: G (i r w y + k (d.n) w x) = E (i w y + (k d.n / r) w x),
+              // E = exp(ikr) (the 1/(4 pi) is applied to the sum)
+              const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              const R ir = inv_sqrt(r2), rr = r2 * ir;
+              R sn, cs;
+              sc(kk * rr, &sn, &cs);
+              const R tk = kk * dn * ir;
+              const cpx<R> v = cmk(tk * wx.re - wy.im, tk * wx.im + wy.re);
+              KT = KT + cmk(cs * v.re - sn * v.im, cs * v.im + sn * v.re);
             }
           }
         }
@@ -172,8 +187,9 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
         acc[3] += T1.im;
         acc[4] += T2.re;
         acc[5] += T2.im;
-        kacc[0] += KT.re;
-        kacc[1] += KT.im;
+        const double kf = GX ? 1.0 : 1.0 / (4.0 * BEM_PI);
+        kacc[0] += kf * KT.re;
+        kacc[1] += kf * KT.im;
       }
     }
   }
@@ -423,7 +439,8 @@ __device__ zd moment0(double a, double sn, double cs) {
     return acc;
   }
   // (cs - 1 + i sn) / (i a) = (sn - i (cs - 1)) / a
-  return cmk(sn / a, (1.0 - cs) / a);
+  const double ia = 1.0 / a;
+  return cmk(sn * ia, (1.0 - cs) * ia);
 }
 
 // d/dV of Re(cy S_ii) for the exact self term (closed radial form, file
@@ -467,16 +484,18 @@ __device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) 
     const double half = 0.5 * plen;
     for (int pn = 0; pn < npan; ++pn) {
       const double u = u0 + plen * (pn + 0.5) + half * xq;
-      const double ch = cosh(u), sh = sinh(u);
+      // cosh and sinh from one exponential, and one reciprocal of cosh
+      const double eu = exp(u), ieu = 1.0 / eu;
+      const double ch = 0.5 * (eu + ieu), sh = 0.5 * (eu - ieu), ich = 1.0 / ch;
       const double R = dist * ch;
-      const double wq = half * wgl / ch;  // d phi = du / cosh(u)
+      const double wq = half * wgl * ich;  // d phi = du / cosh(u)
       double sn, cs;
       sincos(k * R, &sn, &cs);
       const zd m0 = moment0(k * R, sn, cs);
       S = S + (wq * R) * m0;
       const zd K = R * (cmk(cs, sn) - 2.0 * m0);
       double dir[3];
-      for (int d = 0; d < 3; ++d) dir[d] = (fh[d] + sh * tv[d]) / ch;
+      for (int d = 0; d < 3; ++d) dir[d] = (fh[d] + sh * tv[d]) * ich;
       for (int va = 0; va < 3; ++va) {
         const double s = dir[0] * gl[va][0] + dir[1] * gl[va][1] + dir[2] * gl[va][2];
         for (int d = 0; d < 3; ++d) J[va][d] = J[va][d] + (wq * s * dir[d]) * K;
