@@ -123,7 +123,8 @@ __device__ zd moment1(double a) {
   if (fabs(a) < 0.5) {
     // sum_n (i a)^n / (n! (n + 2))
     zd acc = cmk(0.0, 0.0), term = cmk(1.0, 0.0);  // (i a)^n / n!
-    for (int n = 0; n < 30; ++n) {
+#pragma unroll
+    for (int n = 0; n < 30; ++n) {  // unrolled: the reciprocals fold to constants
       acc = acc + (1.0 / (n + 2.0)) * term;
       term = (1.0 / (n + 1.0)) * (term * cmk(0.0, a));
     }
@@ -143,8 +144,11 @@ __constant__ double c_ggl_w[32];
 
 // dS_ii/dk = (1/4 pi) sum_edges int (int_0^rho i t e^{ikt} dt) dphi, with
 // tan(phi) = sinh(u): rho = d cosh(u), dphi = du / cosh(u)
-__device__ zd dk_self(const GTri& t, double k) {
+__device__ zd dk_self(const GTri& t, double k, int lane) {
+  // the 32 Gauss-Legendre points of each edge split over the lanes of a warp;
+  // every lane returns the warp's sum
   zd acc = cmk(0.0, 0.0);
+  const double xq = c_ggl_x[lane], wgl = c_ggl_w[lane];
   for (int e = 0; e < 3; ++e) {
     const double* a = t.v[e];
     const double* b = t.v[(e + 1) % 3];
@@ -157,15 +161,16 @@ __device__ zd dk_self(const GTri& t, double k) {
     double dist = sqrt(fx[0] * fx[0] + fx[1] * fx[1] + fx[2] * fx[2]);
     double u0 = asinh(-pr / dist), u1 = asinh((len - pr) / dist);
     double half = 0.5 * (u1 - u0), mid = 0.5 * (u1 + u0);
-    for (int q = 0; q < 32; ++q) {
-      double u = mid + half * c_ggl_x[q];
-      double ch = cosh(u);
-      double rho = dist * ch;
-      zd m = moment1(k * rho);          // int_0^1 s e^{i k rho s} ds
-      zd inner = (rho * rho) * (cmk(0.0, 1.0) * m);  // i rho^2 m
-      double wq = half * c_ggl_w[q] / ch;
-      acc = acc + wq * inner;
-    }
+    const double u = mid + half * xq;
+    const double eu = exp(u), ch = 0.5 * (eu + 1.0 / eu), ich = 1.0 / ch;
+    const double rho = dist * ch;
+    const zd m = moment1(k * rho);                       // int_0^1 s e^{i k rho s} ds
+    const zd inner = (rho * rho) * (cmk(0.0, 1.0) * m);  // i rho^2 m
+    acc = acc + (half * wgl * ich) * inner;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
   }
   return (1.0 / (4.0 * BEM_PI)) * acc;
 }
@@ -219,9 +224,7 @@ __global__ void k_grad_k_corr(int64_t nt, int nrhs, int f32, double k, const dou
         continue;
       }
       dk_rule(x, t, 0, k, s0, d0);
-      if ((int64_t)j == i) {
-        s1 = dk_self(t, k);
-      } else {
+      {
         double dd[3] = {t.c[0] - x[0], t.c[1] - x[1], t.c[2] - x[2]};
         double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
         int L = dist < 2.0 * t.h ? 2 : (dist < 4.0 * t.h ? 1 : 0);
@@ -251,24 +254,35 @@ __global__ void k_grad_k_self(int64_t nt, int nrhs, double k, const double* __re
                               const double* __restrict__ qpt, const double* __restrict__ nrm,
                               const double* __restrict__ area, const double* __restrict__ hmax,
                               const double4* __restrict__ yx, const double2* __restrict__ gs, double* out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // one warp per element (the lanes split the exact term's quadrature)
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   double part = 0.0;
   if (i < nt) {
     GTri t;
     gload(qpt, nrm, cent, area, hmax, (int)i, t);
-    const double x[3] = {t.c[0], t.c[1], t.c[2]};
-    zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0);
-    dk_rule(x, t, 0, k, s0, d0);
-    const zd cs = dk_self(t, k) - s0, cd = cmk(0.0, 0.0) - d0;
-    for (int r = 0; r < nrhs; ++r) {
-      const double4 uy = yx[(int64_t)r * nt + i];
-      const zd v = cs * cmk(uy.x, uy.y) - cd * cmk(uy.z, uy.w);
-      const double2 g = gs[(int64_t)r * nt + i];
-      part += g.x * v.re + g.y * v.im;
+    const zd se = dk_self(t, k, lane);
+    if (lane == 0) {
+      const double x[3] = {t.c[0], t.c[1], t.c[2]};
+      zd s0 = cmk(0.0, 0.0), d0 = cmk(0.0, 0.0);
+      dk_rule(x, t, 0, k, s0, d0);
+      const zd cs = se - s0, cd = cmk(0.0, 0.0) - d0;
+      for (int r = 0; r < nrhs; ++r) {
+        const double4 uy = yx[(int64_t)r * nt + i];
+        const zd v = cs * cmk(uy.x, uy.y) - cd * cmk(uy.z, uy.w);
+        const double2 g = gs[(int64_t)r * nt + i];
+        part += g.x * v.re + g.y * v.im;
+      }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(out, part);
+  // one atomic add per block of four elements
+  __shared__ double s_part[4];
+  if (lane == 0) s_part[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double sum = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+    if (sum != 0.0) atomicAdd(out, sum);
+  }
 }
 
 void bem_gl_host(int n, double* x, double* w) {
@@ -348,7 +362,7 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
   k_grad_k_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, bem_is_fp64(h) ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
                                                    h->corr_ptr, h->corr_col, yx, gs, acc);
   BEM_CUDA(cudaGetLastError());
-  k_grad_k_self<<<nblk(nt, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs,
+  k_grad_k_self<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs,
                                                acc);
   BEM_CUDA(cudaGetLastError());
   BEM_CUDA(cudaMemcpyAsync(dk, acc, sizeof(double), cudaMemcpyDeviceToHost, s));

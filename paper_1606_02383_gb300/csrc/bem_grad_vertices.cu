@@ -432,7 +432,8 @@ __constant__ double c_vgl_w[32];
 __device__ zd moment0(double a, double sn, double cs) {
   if (fabs(a) < 0.5) {
     zd acc = cmk(0.0, 0.0), term = cmk(1.0, 0.0);  // (ia)^n / n!
-    for (int n = 0; n < 24; ++n) {
+#pragma unroll
+    for (int n = 0; n < 24; ++n) {  // unrolled: the reciprocals fold to constants
       acc = acc + (1.0 / (n + 1.0)) * term;
       term = (1.0 / (n + 1.0)) * (term * cmk(0.0, a));
     }
