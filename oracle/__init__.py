@@ -22,3 +22,4 @@ from .isosurface import isosurface  # noqa: F401,E402
 from .topological import point_source_field, topological_derivative  # noqa: F401,E402
 from . import levelset  # noqa: F401,E402
 from . import burton_miller  # noqa: F401,E402
+from . import fem  # noqa: F401,E402
