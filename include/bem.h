@@ -490,6 +490,73 @@ int bem_gmres_solve_coupled(bem_handle* h, int nrhs, int dtype, const void* b, v
                             int* iters_out, double* relres_out, void* stream);
 
 /*
+ * The elastic body of Section 2.3 (the FEM half of the coupled solver).
+ *
+ * bem_fem_setup -- P1 tetrahedra of the body Omega^c: K - rho_s omega^2 M is
+ * assembled and factorised on the GPU (step 1 of the paper's algorithm).
+ *   nodes  : [n_nodes][3] FP64 node coordinates (host).
+ *   tets   : [n_tets][4] int32 node indices (host), either orientation.
+ *   tris   : [n_tris][3] int32 node indices (host): the boundary faces of the
+ *            tetrahedra, i.e. the BEM mesh, ordered so that the normal points
+ *            out of the body (the BEM operator of the same triangles and the
+ *            same node array gives S and D of Eq. (GMRES)).
+ *   lambda, mu : Lame constants (mu > 0, 3 lambda + 2 mu > 0); rho_s, rho_f:
+ *            solid and fluid densities; omega: angular frequency.
+ *   flags  : BEM_FEM_KEEP_MATRIX keeps a copy of the assembled matrix for
+ *            bem_fem_matrix.
+ * Element matrices as in the Galerkin form of Section 2.3 with the isotropic
+ * C_ijkl: K_e[(a,i),(b,k)] = V (lambda g_ai g_bk + mu g_ak g_bi + mu delta_ik
+ * g_a.g_b), M_e = delta_ik V (1 + delta_ab) / 20; degrees of freedom 3 a + i.
+ * The matrix is held dense (FP64, (3 n_nodes)^2 * 8 bytes, at most 60,000
+ * degrees of freedom) and factorised by LU with partial pivoting; the paper
+ * uses a sparse multifrontal solver.  Fails with BEM_ERR_INVALID_ARG on a
+ * node index out of range, a degenerate tetrahedron or triangle, or a
+ * singular matrix (omega^2 an eigenvalue of the free body).
+ */
+typedef struct bem_fem bem_fem;
+#define BEM_FEM_KEEP_MATRIX 1
+int bem_fem_setup(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets, const int32_t* tris,
+                  int64_t n_tris, double lambda, double mu, double rho_s, double rho_f, double omega, int flags,
+                  void* stream, bem_fem** out);
+int bem_fem_destroy(bem_fem* f);
+
+/* u = (K - rho_s omega^2 M)^{-1} b for nrhs (1..64) real columns b, u
+ * [nrhs][3 n_nodes] (device, FP64), in stream order. */
+int bem_fem_solve(bem_fem* f, int nrhs, const double* b, double* u, void* stream);
+
+/*
+ * bem_fem_couple -- y = C x, the coupling map of Eq. (GMRES) (steps 2(a) and
+ * 2(b) of the paper's algorithm), for complex element pressures x and
+ * densities y [nrhs][n_tris] (nrhs 1..32) in dtype (device), in stream order:
+ *   C = rho_f omega^2 Avg (K - rho_s omega^2 M)^{-1} (-N),
+ * N[(a,i), j] = n_ji A_j / 3 the load of a unit pressure on triangle j (the
+ * traction is -p n by the boundary condition t_i + p n_i = 0), Avg[j, (a,i)]
+ * = n_ji / 3 the element mean of u.n: the single layer then takes
+ * q = rho_f omega^2 u.n as its density, so (1/2 I - D + S C) p = p_src.
+ */
+int bem_fem_couple(bem_fem* f, int nrhs, int dtype, const void* x, void* y, void* stream);
+
+/* bem_fem_bind / bem_fem_coupling -- the coupling map as a bem_coupling_fn:
+ * bind the complex128 buffers cx, cy given to bem_gmres_solve_coupled, then
+ * pass bem_fem_coupling with ctx = f, so that the whole coupled solve runs in
+ * the library. */
+int bem_fem_bind(bem_fem* f, const void* cx, void* cy);
+int bem_fem_coupling(void* ctx, int nrhs, void* stream);
+
+/* the assembled K - rho_s omega^2 M, column-major [3 n_nodes][3 n_nodes] FP64,
+ * into a host or device buffer (requires BEM_FEM_KEEP_MATRIX). */
+int bem_fem_matrix(bem_fem* f, double* out, void* stream);
+
+enum {
+  BEM_FEM_INFO_DOF = 0,   /* 3 n_nodes */
+  BEM_FEM_INFO_NODES = 1,
+  BEM_FEM_INFO_TETS = 2,
+  BEM_FEM_INFO_TRIS = 3,
+  BEM_FEM_INFO_BYTES = 4  /* device bytes held */
+};
+int bem_fem_info(bem_fem* f, int key, int64_t* value);
+
+/*
  * Batches of independent problems (many scatterers, each with its own mesh
  * and wavenumber: the state and adjoint solves of Section 2.5 repeated over a
  * population of designs).  Every problem keeps its own octree and operators;

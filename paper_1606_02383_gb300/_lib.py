@@ -44,6 +44,8 @@ INFO = {
     "near_list": 19, "w_evals": 20, "x_evals": 21, "exp_total": 22, "tc_kind": 23,
 }
 STAGES = ("prologue", "p2p", "correction", "p2m", "m2m", "m2l", "l2l", "l2p", "epilogue")
+FEM_INFO = {"dof": 0, "nodes": 1, "tets": 2, "tris": 3, "device_bytes": 4}
+BEM_FEM_KEEP_MATRIX = 1
 INFO_ORDER_OF_LEVEL = 100
 INFO_LEAVES_OF_LEVEL = 200
 INFO_BOXES_OF_LEVEL = 300
@@ -55,7 +57,9 @@ EXPORTS = ("bem_setup", "bem_destroy", "bem_apply", "bem_apply_adjoint", "bem_gm
            "bem_batch_info", "bem_destroy_batch", "bem_gmres_solve_batch", "bem_last_error", "bem_peak_probe",
            "bem_eval_points", "bem_point_sources", "bem_point_source_field", "bem_topological_derivative",
            "bem_gmres_solve_coupled", "bem_isosurface", "bem_sync", "bem_set_wait_limit", "bem_tree_level", "bem_sorted_order", "bem_far_field",
-           "bem_setup_batch_each", "bem_state_adjoint", "bem_topological_field", "bem_levelset_step")
+           "bem_setup_batch_each", "bem_state_adjoint", "bem_topological_field", "bem_levelset_step",
+           "bem_fem_setup", "bem_fem_destroy", "bem_fem_solve", "bem_fem_couple", "bem_fem_bind", "bem_fem_coupling",
+           "bem_fem_matrix", "bem_fem_info")
 
 # int (*bem_coupling_fn)(void* ctx, int nrhs, void* stream)
 COUPLING_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
@@ -126,6 +130,15 @@ def load(path: str | None = None):
     lib.bem_point_source_field.argtypes = [i, i, vp, vp, i64, vp, ctypes.c_double, i, vp, vp]
     lib.bem_topological_derivative.argtypes = [i64, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     lib.bem_sync.argtypes = [vp, vp]
+    lib.bem_fem_setup.argtypes = [vp, i64, vp, i64, vp, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, i, vp, ctypes.POINTER(vp)]
+    lib.bem_fem_destroy.argtypes = [vp]
+    lib.bem_fem_solve.argtypes = [vp, i, vp, vp, vp]
+    lib.bem_fem_couple.argtypes = [vp, i, i, vp, vp, vp]
+    lib.bem_fem_bind.argtypes = [vp, vp, vp]
+    lib.bem_fem_coupling.argtypes = [vp, i, vp]
+    lib.bem_fem_matrix.argtypes = [vp, vp, vp]
+    lib.bem_fem_info.argtypes = [vp, i, ctypes.POINTER(i64)]
     lib.bem_tree_level.argtypes = [vp, i, vp, vp, vp, vp]
     lib.bem_sorted_order.argtypes = [vp, vp]
     lib.bem_far_field.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp]

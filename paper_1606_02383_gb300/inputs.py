@@ -14,6 +14,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "voxel_body",
+    "voxel_ball",
     "icosphere",
     "ellipsoid",
     "torus",
@@ -341,3 +343,65 @@ def plane_wave(points, k: float, direction=(0.0, 0.0, 1.0)):
     d = np.asarray(direction, dtype=np.float64)
     d = d / np.linalg.norm(d)
     return np.exp(1j * float(k) * (np.asarray(points) @ d))
+
+
+def voxel_body(mask, h: float = 1.0, origin=(0.0, 0.0, 0.0), jitter: float = 0.0, seed: int = 0):
+    """Tetrahedra of the voxels where mask is true, for the elastic body of the
+    coupled problem: every voxel is split into the six tetrahedra around its
+    main diagonal (the same split in every voxel, so faces match), and the
+    boundary faces (those of one tetrahedron only) form the surface mesh,
+    normals out of the body.  Returns (nodes [n, 3] float64, tets [m, 4] int32
+    with positive volume, tris [t, 3] int32); the surface uses the body's node
+    numbering, so nodes and tris also make the BEM mesh.  jitter > 0 moves
+    every node by up to jitter h per coordinate (seeded): on the exact lattice
+    many centroid distances equal 2 or 4 longest edges, the thresholds of the
+    near-singular rules, where two correct evaluations may pick different
+    rules; moved nodes leave no such ties."""
+    mask = np.asarray(mask, dtype=bool)
+    n0, n1, n2 = mask.shape
+    corner = np.zeros((n0 + 1, n1 + 1, n2 + 1), dtype=bool)
+    for d0 in (0, 1):
+        for d1 in (0, 1):
+            for d2 in (0, 1):
+                corner[d0:d0 + n0, d1:d1 + n1, d2:d2 + n2] |= mask
+    ids = -np.ones(corner.shape, dtype=np.int64)
+    pts = np.argwhere(corner)
+    ids[tuple(pts.T)] = np.arange(pts.shape[0])
+    nodes = np.asarray(origin, dtype=np.float64) + h * pts.astype(np.float64)
+    if jitter > 0:
+        nodes = nodes + jitter * h * np.random.default_rng(seed).uniform(-1.0, 1.0, nodes.shape)
+    vox = np.argwhere(mask)
+    unit = np.eye(3, dtype=np.int64)
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        c0 = vox
+        c1 = c0 + unit[perm[0]]
+        c2 = c1 + unit[perm[1]]
+        c3 = c2 + unit[perm[2]]
+        tets.append(np.stack([ids[tuple(c.T)] for c in (c0, c1, c2, c3)], axis=1))
+    tets = np.concatenate(tets)
+    P = nodes[tets]
+    vol = np.einsum("ij,ij->i", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    flip = vol < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    # the four faces of every tetrahedron with the opposite corner
+    fidx = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    faces = tets[:, fidx].reshape(-1, 3)
+    opp = tets[:, [0, 1, 2, 3]].reshape(-1)
+    key = np.sort(faces, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    once = cnt[inv.ravel()] == 1
+    faces, opp = faces[once], opp[once]
+    a, b, c = nodes[faces[:, 0]], nodes[faces[:, 1]], nodes[faces[:, 2]]
+    inward = np.einsum("ij,ij->i", np.cross(b - a, c - a), a - nodes[opp]) < 0
+    faces[inward, 1], faces[inward, 2] = faces[inward, 2].copy(), faces[inward, 1].copy()
+    return nodes, tets.astype(np.int32), faces.astype(np.int32)
+
+
+def voxel_ball(n: int, radius: float, h: float = 1.0, jitter: float = 0.0, seed: int = 0):
+    """The voxels of an n^3 lattice (spacing h, centred on the origin) whose
+    centres lie within radius of the origin, as voxel_body's (nodes, tets, tris)."""
+    g = (np.arange(n) - (n - 1) / 2.0) * h
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    mask = X ** 2 + Y ** 2 + Z ** 2 <= radius * radius
+    return voxel_body(mask, h, origin=(-0.5 * n * h,) * 3, jitter=jitter, seed=seed)

@@ -319,8 +319,9 @@ class Operator:
         host loop if no graph can be built), "graph_only" (no fallback) or
         "host" (the Arnoldi steps driven from the host).
 
-        coupling: optional callable coupling(cx, cy) for Eq. (GMRES),
-        (1/2 I - D + S C) x = b.  cx and cy are complex128 CUDA tensors
+        coupling: optional FemBody (the library's elastic body: the whole
+        coupled solve runs in native code) or callable coupling(cx, cy) for
+        Eq. (GMRES), (1/2 I - D + S C) x = b.  cx and cy are complex128 CUDA tensors
         [nrhs, N] at fixed addresses; the callable must write C cx into cy in
         place, on the current stream (e.g. the FEM map T (K - rho_s omega^2
         M)^{-1} N of Section 2.3).  A coupled solve runs the host loop."""
@@ -333,6 +334,17 @@ class Operator:
         if coupling is None:
             rc = self._lib.bem_gmres_solve(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(), float(tol),
                                            int(max_iter), int(restart), flags, ctypes.byref(iters), rel, _stream())
+        elif isinstance(coupling, FemBody):
+            # the library's own coupling map: the whole solve stays in native code
+            cx = torch.zeros((nrhs, self.n), dtype=torch.complex128, device="cuda")
+            cy = torch.zeros_like(cx)
+            _lib.check(self._lib.bem_fem_bind(coupling._f, cx.data_ptr(), cy.data_ptr()))
+            fn = _lib.COUPLING_FN(ctypes.cast(self._lib.bem_fem_coupling, ctypes.c_void_p).value)
+            rc = self._lib.bem_gmres_solve_coupled(self._h, nrhs, _dtype_code(bs), bs.data_ptr(), x.data_ptr(),
+                                                   float(tol), int(max_iter), int(restart), fn, coupling._f,
+                                                   cx.data_ptr(), cy.data_ptr(), flags, ctypes.byref(iters), rel,
+                                                   _stream())
+            self._lib.bem_fem_bind(coupling._f, None, None)
         else:
             cx = torch.zeros((nrhs, self.n), dtype=torch.complex128, device="cuda")
             cy = torch.zeros_like(cx)
@@ -355,6 +367,73 @@ class Operator:
         if rc != _lib.BEM_OK and (raise_on_fail or rc != _lib.BEM_ERR_NOT_CONVERGED):
             _lib.check(rc)
         return x, int(iters.value), np.array(list(rel))
+
+
+class FemBody:
+    """The elastic body of Section 2.3 on the GPU (see bem_fem_setup in
+    include/bem.h): P1 tetrahedra, K - rho_s omega^2 M assembled and
+    factorised once, and the coupling map C = rho_f omega^2 Avg
+    (K - rho_s omega^2 M)^{-1} (-N) of Eq. (GMRES).  tris are the boundary
+    faces (the BEM mesh, normals out of the body) over the same node array.
+    Pass the body as Operator.solve(coupling=body)."""
+
+    def __init__(self, nodes, tets, tris, lam, mu, rho_s, rho_f, omega, keep_matrix=False):
+        lib = _lib.load()
+        X = np.ascontiguousarray(nodes, dtype=np.float64)
+        Tt = np.ascontiguousarray(tets, dtype=np.int32)
+        Tr = np.ascontiguousarray(tris, dtype=np.int32)
+        f = ctypes.c_void_p()
+        _lib.check(lib.bem_fem_setup(X.ctypes.data, X.shape[0], Tt.ctypes.data, Tt.shape[0], Tr.ctypes.data,
+                                     Tr.shape[0], float(lam), float(mu), float(rho_s), float(rho_f), float(omega),
+                                     _lib.BEM_FEM_KEEP_MATRIX if keep_matrix else 0, _stream(), ctypes.byref(f)))
+        self._f = f
+        self._lib = lib
+        self.n_dof = 3 * X.shape[0]
+        self.n_tris = Tr.shape[0]
+
+    def close(self):
+        if getattr(self, "_f", None):
+            self._lib.bem_fem_destroy(self._f)
+            self._f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, key):
+        v = ctypes.c_int64()
+        _lib.check(self._lib.bem_fem_info(self._f, _lib.FEM_INFO[key], ctypes.byref(v)))
+        return int(v.value)
+
+    def solve(self, b):
+        """(K - rho_s omega^2 M)^{-1} b for real b [m, n_dof] (or [n_dof])."""
+        bb = torch.as_tensor(b, dtype=torch.float64).to("cuda").contiguous()
+        one = bb.dim() == 1
+        bb = bb.reshape(-1, self.n_dof)
+        u = torch.empty_like(bb)
+        _lib.check(self._lib.bem_fem_solve(self._f, bb.shape[0], bb.data_ptr(), u.data_ptr(), _stream()))
+        return u[0] if one else u
+
+    def couple(self, x):
+        """C x for complex element pressures x [nrhs, n_tris] (or [n_tris])."""
+        xx = torch.as_tensor(x).to("cuda")
+        if not xx.is_complex():
+            xx = xx.to(torch.complex128)
+        xx = xx.contiguous()
+        one = xx.dim() == 1
+        xx = xx.reshape(-1, self.n_tris)
+        y = torch.empty_like(xx)
+        _lib.check(self._lib.bem_fem_couple(self._f, xx.shape[0], _dtype_code(xx), xx.data_ptr(), y.data_ptr(),
+                                            _stream()))
+        return y[0] if one else y
+
+    def matrix(self):
+        """The assembled K - rho_s omega^2 M (dense FP64, needs keep_matrix=True)."""
+        out = torch.empty((self.n_dof, self.n_dof), dtype=torch.float64, device="cuda")
+        _lib.check(self._lib.bem_fem_matrix(self._f, out.data_ptr(), _stream()))
+        return out.T  # stored column-major
 
 
 def isosurface(phi, lo, h, t=0.0):

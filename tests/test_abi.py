@@ -44,6 +44,24 @@ def test_error_paths_without_gpu():
     cb = _lib.COUPLING_FN(lambda ctx, nrhs, stream: 0)
     assert lib.bem_gmres_solve_coupled(None, 1, _lib.BEM_C128, None, None, 1e-8, 10, 10, cb, None, None, None, 0,
                                        None, None, None) == _lib.BEM_ERR_INVALID_ARG
+    # the elastic body checks its arguments before any CUDA call
+    out = ctypes.c_void_p()
+    assert lib.bem_fem_setup(None, 8, None, 1, None, 1, 2.0, 1.0, 1.0, 1.0, 1.0, 0, None,
+                             ctypes.byref(out)) == _lib.BEM_ERR_INVALID_ARG
+    import numpy as _np
+    X = _np.zeros((4, 3))
+    tet = _np.array([[0, 1, 2, 4]], dtype=_np.int32)  # node 4 of 4: out of range
+    tri = _np.array([[0, 1, 2]], dtype=_np.int32)
+    assert lib.bem_fem_setup(X.ctypes.data, 4, tet.ctypes.data, 1, tri.ctypes.data, 1, 2.0, 1.0, 1.0, 1.0, 1.0, 0,
+                             None, ctypes.byref(out)) == _lib.BEM_ERR_INVALID_ARG
+    tet[0, 3] = 3
+    assert lib.bem_fem_setup(X.ctypes.data, 4, tet.ctypes.data, 1, tri.ctypes.data, 1, 2.0, -1.0, 1.0, 1.0, 1.0, 0,
+                             None, ctypes.byref(out)) == _lib.BEM_ERR_INVALID_ARG  # mu <= 0
+    assert lib.bem_fem_solve(None, 1, None, None, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_fem_couple(None, 1, _lib.BEM_C128, None, None, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_fem_coupling(None, 1, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_fem_matrix(None, None, None) == _lib.BEM_ERR_INVALID_ARG
+    assert lib.bem_fem_destroy(None) == _lib.BEM_OK
     # the iso-surface checks its grid and level before any CUDA call
     lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
     counts = (ctypes.c_int64 * 2)()
