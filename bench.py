@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
-    ap.add_argument("--workload", choices=["headline", "precision", "batching", "large", "differentiation", "topology"],
+    ap.add_argument("--workload", choices=["headline", "precision", "batching", "large", "differentiation", "topology",
+                                           "coupled"],
                     default="headline", help="headline = the metric above; the others are the remaining "
                     "configurations (one JSON line each, not the headline metric)")
     a = ap.parse_args()
@@ -701,6 +702,63 @@ def topology_iteration(steps, warm):
     return out
 
 
+def coupled_solve(steps, warm):
+    """Eq. (GMRES) of Section 2.3 with the elastic body on the GPU: a voxel ball
+    (20 voxels across, Kuhn tetrahedra, jittered nodes) of lambda = 2, mu = 1,
+    rho_s = 2 in a fluid of rho_f = Lambda_f = 1 at omega = 2 (k_f = 2, ka = 1),
+    plane-wave incidence.  Step 1 (assembly and LU of K - rho_s omega^2 M) and
+    the BEM setup are timed once; a step is one coupled GMRES solve to 1e-6
+    from x = 0, each iteration one coupling map and one FMM apply."""
+    import time
+
+    import torch
+    import oracle
+    from oracle import fem as ofem
+    from paper_1606_02383_gb300 import inputs
+    from paper_1606_02383_gb300.operator import FemBody, Operator
+
+    lam, mu, rho_s, rho_f, omega = 2.0, 1.0, 2.0, 1.0, 2.0
+    k = omega
+    nodes, tets, tris = inputs.voxel_ball(20, 0.5, 0.0525, jitter=0.05, seed=20)
+    c = inputs.centroids(nodes, tris)
+    b = inputs.plane_wave(c, k)[None]
+    bd = torch.from_numpy(b).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    body = FemBody(nodes, tets, tris, lam, mu, rho_s, rho_f, omega)
+    torch.cuda.synchronize()
+    t_fem = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op = Operator(nodes, tris, k, p=0, eps=1e-6, mode="mixed")
+    torch.cuda.synchronize()
+    t_bem = time.perf_counter() - t0
+    xc = torch.randn(1, tris.shape[0], dtype=torch.complex128, device="cuda")
+    ms_couple = _timed(lambda: body.couple(xc), steps, warm)
+    ms_apply = _timed(lambda: op.apply(xc, xc), steps, warm)
+    res = {}
+
+    def solve():
+        res["x"], res["it"], res["rel"] = op.solve(bd, tol=1e-6, max_iter=200, restart=60, coupling=body)
+
+    ms = _timed(solve, steps, warm)
+    # the oracle: dense S, D and the FEM's dense coupling matrix, one LU of Eq. (GMRES)
+    S, D = oracle.assemble(nodes, tris, k)
+    C = ofem.Body(nodes, tets, tris, lam, mu, rho_s, rho_f, omega).matrix()
+    ref = oracle.lu_solve(0.5 * np.eye(tris.shape[0]) - D + S @ C, b)
+    ref0 = oracle.lu_solve(0.5 * np.eye(tris.shape[0]) - D, b)
+    n = 3 * nodes.shape[0]
+    return {"metric": "coupled BEM-FEM solves/sec (Eq. (GMRES) to 1e-6, elastic voxel ball, %d tetrahedra, "
+                      "%d boundary triangles, %d FEM unknowns, ka=1)" % (tets.shape[0], tris.shape[0], n),
+            "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "gmres_iters": int(res["it"]),
+            "relres": float(res["rel"][0]), "rel_err_vs_oracle_dense_lu": _rel(res["x"].cpu().numpy(), ref),
+            "elastic_term_share": _rel(ref0, ref),
+            "fem_assembly_and_lu_s": t_fem, "bem_setup_s": t_bem, "couple_ms": ms_couple, "apply_ms": ms_apply,
+            "lu_hbm_bytes_model": (n ** 3 / 3.0) * 16.0,
+            "lu_achieved_gbs_model": (n ** 3 / 3.0) * 16.0 / t_fem / 1e9,
+            "config": {"workload": "coupled", "fem_dof": n, "tets": int(tets.shape[0]),
+                       "tris": int(tris.shape[0])}}
+
+
 def run_other(args):
     """The configurations besides the headline, one JSON line each."""
     import torch
@@ -912,6 +970,8 @@ def run_other(args):
                                       "cores": oracle.num_threads(), "sample": "2,000 rows, extrapolated"}})
     elif w == "topology":
         line.update(topology_iteration(steps, warm))
+    elif w == "coupled":
+        line.update(coupled_solve(steps, warm))
     else:  # differentiation
         V, T = inputs.level_set_mesh(0)
         n, k = T.shape[0], 3.0

@@ -218,23 +218,13 @@ __global__ void __launch_bounds__(FEM_SUB) k_fem_diag_inv(int64_t n, const doubl
 __global__ void __launch_bounds__(256) k_fem_step(int64_t n, int64_t k0, int nb, int64_t r0, int64_t r1, int ncol,
                                                   const double* __restrict__ A, const double* __restrict__ Dk,
                                                   double* __restrict__ In, double* __restrict__ Out) {
-  extern __shared__ double s_y[];  // [ncol][FEM_SUB] right-hand sides, [ncol][FEM_SUB] solutions, [8][32]
+  extern __shared__ double s_y[];  // [ncol][FEM_SUB] right-hand sides, [ncol][FEM_SUB] solutions, [8][32],
+                                   // then Dk as [FEM_SUB][FEM_SUB + 1]
   double* s_s = s_y + ncol * FEM_SUB;
   double* s_p = s_s + ncol * FEM_SUB;
-  for (int t = threadIdx.x; t < ncol * FEM_SUB; t += blockDim.x) {
-    const int c = t / FEM_SUB, j = t % FEM_SUB;
-    s_y[t] = j < nb ? In[(int64_t)c * n + k0 + j] : 0.0;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < ncol * FEM_SUB; t += blockDim.x) {
-    const int c = t / FEM_SUB, r = t % FEM_SUB;
-    double v = 0.0;
-    for (int j = 0; j < FEM_SUB; ++j) v += Dk[r * FEM_SUB + j] * s_y[c * FEM_SUB + j];
-    s_s[t] = v;
-    if (blockIdx.x == 0 && r < nb) Out[(int64_t)c * n + k0 + r] = v;
-  }
-  __syncthreads();
+  double* s_d = s_p + 8 * 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // this CTA's rows of the step's columns first: their loads overlap the rest
   const int64_t i = r0 + blockIdx.x * (int64_t)32 + lane;
   const bool live = i < r1;
   double a[FEM_SUB / 8];
@@ -243,6 +233,26 @@ __global__ void __launch_bounds__(256) k_fem_step(int64_t n, int64_t k0, int nb,
     const int j = w + 8 * u;
     a[u] = (live && j < nb) ? A[(k0 + j) * n + i] : 0.0;
   }
+  for (int t = threadIdx.x; t < ncol * FEM_SUB; t += blockDim.x) {
+    const int c = t / FEM_SUB, j = t % FEM_SUB;
+    s_y[t] = j < nb ? In[(int64_t)c * n + k0 + j] : 0.0;
+  }
+  for (int t = threadIdx.x; t < FEM_SUB * FEM_SUB; t += blockDim.x)
+    s_d[(t / FEM_SUB) * (FEM_SUB + 1) + t % FEM_SUB] = Dk[t];
+  __syncthreads();
+  // the step's solution from shared memory (rows of Dk at a stride of 65:
+  // consecutive threads, consecutive rows, no bank conflicts)
+  for (int o = threadIdx.x; o < ncol * FEM_SUB; o += blockDim.x) {
+    const int c = o / FEM_SUB, r = o % FEM_SUB;
+    const double* d = s_d + r * (FEM_SUB + 1);
+    const double* y = s_y + c * FEM_SUB;
+    double v = 0.0;
+#pragma unroll 16
+    for (int j = 0; j < FEM_SUB; ++j) v += d[j] * y[j];
+    s_s[o] = v;
+    if (blockIdx.x == 0 && r < nb) Out[(int64_t)c * n + k0 + r] = v;
+  }
+  __syncthreads();
   for (int c = 0; c < ncol; ++c) {
     double acc = 0.0;
 #pragma unroll
@@ -315,7 +325,7 @@ static void fem_free(bem_fem* f) {
 // FEM_SUB rows and direction.
 static int fem_substitute(bem_fem* f, int ncol, double* Y, double* X, cudaStream_t s) {
   const int64_t n = f->n, nbk = (n + FEM_SUB - 1) / FEM_SUB;
-  const size_t sh = sizeof(double) * (2 * (size_t)ncol * FEM_SUB + 8 * 32);
+  const size_t sh = sizeof(double) * (2 * (size_t)ncol * FEM_SUB + 8 * 32 + FEM_SUB * (FEM_SUB + 1));
   for (int64_t b = 0; b < nbk; ++b) {  // L z = P y: Y -> X
     const int64_t k0 = b * FEM_SUB, r0 = k0 + FEM_SUB;
     const int nb = (int)std::min<int64_t>(FEM_SUB, n - k0);
@@ -447,9 +457,9 @@ int bem_fem_setup(const double* nodes, int64_t n_nodes, const int32_t* tets, int
     }
     if (cu(cudaGetLastError())) break;
     k_fem_diag_inv<<<(unsigned)nbk, FEM_SUB, 0, s>>>(n, f->A, f->dinv);
-    // the substitution steps hold two [64 columns][FEM_SUB] tiles at most
+    // the substitution steps hold two [64 columns][FEM_SUB] tiles at most and a diagonal block
     if (cu(cudaFuncSetAttribute(k_fem_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * (2 * 64 * FEM_SUB + 8 * 32)))))
+                                (int)(sizeof(double) * (2 * 64 * FEM_SUB + 8 * 32 + FEM_SUB * (FEM_SUB + 1))))))
       break;
     if (cu(cudaGetLastError())) break;
     std::vector<int> piv(n), perm(n);
