@@ -1097,23 +1097,26 @@ int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2*
   // the regular rule through the tree on FMM handles (unless the all-pairs
   // sums are asked for); dL/dk's regular part stays an all-pairs sum
   const bool tree = dvertices && bem_is_fmm(h) && h->L >= 2 && !h->grad_direct;
+  // the all-pairs target pass sums the centroid gradients only when the
+  // vertices are asked for without the tree; otherwise dL/dk's part alone
+  const bool gxpass = dvertices && !tree;
   int64_t ct = 0, cs = 0;
-  if (!tree || dk) {
-    const void* ft = f64 ? (tree ? (const void*)k_gv_target<double, false> : (const void*)k_gv_target<double, true>)
-                         : (tree ? (const void*)k_gv_target<float, false> : (const void*)k_gv_target<float, true>);
+  if (gxpass || dk) {
+    const void* ft = f64 ? (gxpass ? (const void*)k_gv_target<double, true> : (const void*)k_gv_target<double, false>)
+                         : (gxpass ? (const void*)k_gv_target<float, true> : (const void*)k_gv_target<float, false>);
     const dim3 gt = chunked(ft, nt, ct);
 #define GV_TARGET(RT, GXV) \
   k_gv_target<RT, GXV><<<gt, 128, 0, s>>>(nt, h->k, h->cent, h->qpt, h->nrm, h->area, yx, gs, ct, gx, dk)
     if (f64) {
-      if (tree)
-        GV_TARGET(double, false);
-      else
+      if (gxpass)
         GV_TARGET(double, true);
-    } else {
-      if (tree)
-        GV_TARGET(float, false);
       else
+        GV_TARGET(double, false);
+    } else {
+      if (gxpass)
         GV_TARGET(float, true);
+      else
+        GV_TARGET(float, false);
     }
 #undef GV_TARGET
     BEM_CUDA(cudaGetLastError());
