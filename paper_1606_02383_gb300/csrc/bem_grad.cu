@@ -9,9 +9,11 @@
 // For an upstream gradient g (PyTorch convention for complex outputs) the loss
 // derivative is dk = sum_rhs Re < g, (dA/dk) u >.  The regular rule R_0 over
 // all pairs is summed by the target-major pass of the vertex gradient
-// (bem_grad_vertices.cu: FP64 in the FP64 modes, FP32 with FP64 near pairs
-// otherwise); the near-singular / self corrections add, in FP64, d/dk of
-// (rule R_L or exact) - R_0 for the pairs of the correction matrix.
+// (bem_grad_vertices.cu: FP64 in the FP64 modes, FP32 with split coordinates
+// otherwise); the near-singular / self corrections add d/dk of (rule R_L or
+// exact) - R_0 for the pairs of the correction matrix: here when dL/dk alone
+// is asked for, otherwise inside the vertex gradient's correction and self
+// kernels on the same quadrature points.
 #include "bem_common.cuh"
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -345,10 +347,12 @@ extern "C" int bem_grad(bem_handle* h, int nrhs, int dtype, const void* g, const
     k_grad_prologue<float><<<nblk(nt, 256), 256, 0, s>>>(nt, nrhs, h->perm, (const float*)g, (const float*)x,
                                                          (const float*)y, yx, gs);
   BEM_CUDA(cudaGetLastError());
-  // regular rule over all pairs: vertex terms and the regular part of dL/dk in
-  // one target-major pass (plus the source-major pass for the vertices)
+  // the regular rule (vertex terms, and dL/dk's regular part); with the
+  // vertices asked for, the correction and self kernels of the vertex
+  // gradient add dL/dk's corrections on the same quadrature points too
   BEM_TRY(bem_grad_vertices(h, nrhs, yx, gs, dvertices, dk ? acc : nullptr, s));
-  if (!dk) {
+  if (!dk || dvertices) {
+    if (dk) BEM_CUDA(cudaMemcpyAsync(dk, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaFreeAsync(yx, s));
     BEM_CUDA(cudaFreeAsync(gs, s));
     BEM_CUDA(cudaFreeAsync(acc, s));

@@ -75,11 +75,6 @@ __device__ __forceinline__ void ghf(R d0, R d1, R d2, R k, cpx<R>& G, cpx<R>& F,
   ghfr(d0, d1, d2, k, G, F, H, r);
 }
 
-// 1 / sqrt(x): the hardware reciprocal square root in FP32 (2 ulp), exact
-// division in FP64
-__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
-
 // ------------------------------------------------------ regular rule R_0 --
 // In the FP32 passes every coordinate relative to the block's reference point
 // is held as a high FP32 part and the FP32 rounding of the rest, and a
@@ -95,7 +90,8 @@ __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
 // thread per target, sources streamed through shared memory; coordinates are
 // taken relative to the block's first centroid before rounding to R.  Block z
 // takes the sources [z chunk, (z + 1) chunk) and adds its partial sums.  With
-// GX false only the regular part of dL/dk is summed (the tree gives gx).
+// GX false only the regular part of dL/dk is summed (the tree gives gx, or
+// only dL/dk is asked for), with the same arithmetic.
 template <typename R, bool GX>
 __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const double* __restrict__ cent,
                                                    const double* __restrict__ qpt, const double* __restrict__ nrm,
@@ -158,26 +154,17 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
               d2 += s_ql[e][3 * q + 2] - xl[2];
             }
             const R dn = d0 * n0 + d1 * n1 + d2 * n2;
+            cpx<R> G, F, H;
+            R rr;
+            ghfr(d0, d1, d2, kk, G, F, H, rr);
+            // d/dk: G (i r w y + k (d.n) w x)
+            KT = KT + G * (cmk(-rr * wy.im, rr * wy.re) + (kk * dn) * wx);
             if constexpr (GX) {
-              cpx<R> G, F, H;
-              R rr;
-              ghfr(d0, d1, d2, kk, G, F, H, rr);
               const cpx<R> a = dn * (H * wx) - F * wy;
               const cpx<R> b = F * wx;
-              KT = KT + G * (cmk(-rr * wy.im, rr * wy.re) + (kk * dn) * wx);
               T0 = T0 + d0 * a + n0 * b;
               T1 = T1 + d1 * a + n1 * b;
               T2 = T2 + d2 * a + n2 * b;
-            } else {
-              // dL/dk alone: G (i r w y + k (d.n) w x) = E (i w y + (k d.n / r) w x),
-              // E = exp(ikr) (the 1/(4 pi) is applied to the sum)
-              const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
-              const R ir = inv_sqrt(r2), rr = r2 * ir;
-              R sn, cs;
-              sc(kk * rr, &sn, &cs);
-              const R tk = kk * dn * ir;
-              const cpx<R> v = cmk(tk * wx.re - wy.im, tk * wx.im + wy.re);
-              KT = KT + cmk(cs * v.re - sn * v.im, cs * v.im + sn * v.re);
             }
           }
         }
@@ -187,9 +174,8 @@ __global__ void __launch_bounds__(128) k_gv_target(int64_t nt, double k, const d
         acc[3] += T1.im;
         acc[4] += T2.re;
         acc[5] += T2.im;
-        const double kf = GX ? 1.0 : 1.0 / (4.0 * BEM_PI);
-        kacc[0] += kf * KT.re;
-        kacc[1] += kf * KT.im;
+        kacc[0] += KT.re;
+        kacc[1] += KT.im;
       }
     }
   }
@@ -361,9 +347,12 @@ __device__ void map_area_normal(const VTriT<R>& t, R gA, const R* gN, R* g9) {
 }
 
 // sign * d/d(geometry) of Re(cy S_ij - cx D_ij) under rule R_L on triangle t:
-// the collocation point's gradient goes to tgt, the vertices' to g9.
+// the collocation point's gradient goes to tgt, the vertices' to g9.  With kd
+// non-null the same points also add sign * (dS_ij/dk, dD_ij/dk) to kd[0],
+// kd[1]: w i r G and -w k (d.n) G per point.
 template <typename R>
-__device__ void rule_grad(const R* x, const VTriT<R>& t, int L, R k, cpx<R> cy, cpx<R> cx, R sign, R* tgt, R* g9) {
+__device__ void rule_grad(const R* x, const VTriT<R>& t, int L, R k, cpx<R> cy, cpx<R> cx, R sign, R* tgt, R* g9,
+                          cpx<R>* kd = nullptr) {
   const int npieces = 1 << (2 * L);
   const R w = t.area / (R(3) * npieces);
   R gA = 0, gN[3] = {0, 0, 0};
@@ -407,8 +396,14 @@ __device__ void rule_grad(const R* x, const VTriT<R>& t, int L, R k, cpx<R> cy, 
       for (int dd = 0; dd < 3; ++dd)
         d[dd] = beta[0] * t.v[0][dd] + beta[1] * t.v[1][dd] + beta[2] * t.v[2][dd] - x[dd];
       cpx<R> G, F, H;
-      ghf(d[0], d[1], d[2], k, G, F, H);
+      R rr;
+      ghfr(d[0], d[1], d[2], k, G, F, H, rr);
       const R dn = d[0] * t.n[0] + d[1] * t.n[1] + d[2] * t.n[2];
+      if (kd) {
+        const R wr = sign * w * rr, wk = -sign * w * k * dn;
+        kd[0] = kd[0] + cmk(-wr * G.im, wr * G.re);
+        kd[1] = kd[1] + wk * G;
+      }
       const cpx<R> a = cy * F - dn * (cx * H);
       const cpx<R> b = cx * F;
       for (int dd = 0; dd < 3; ++dd) {
@@ -428,26 +423,33 @@ __device__ void rule_grad(const R* x, const VTriT<R>& t, int L, R k, cpx<R> cy, 
 __constant__ double c_vgl_x[32];
 __constant__ double c_vgl_w[32];
 
-// int_0^1 exp(i a s) ds = (exp(ia) - 1)/(ia), given sn = sin a, cs = cos a
-__device__ zd moment0(double a, double sn, double cs) {
+// m0 = int_0^1 exp(i a s) ds = (exp(ia) - 1)/(ia) and m1 = int_0^1 s exp(i a s) ds
+// = exp(ia)/(ia) + (exp(ia) - 1)/a^2, given sn = sin a, cs = cos a; below
+// |a| = 0.5 by their power series sum_n (ia)^n / n! / (n + 1) and / (n + 2)
+__device__ void moments01(double a, double sn, double cs, zd& m0, zd& m1) {
   if (fabs(a) < 0.5) {
-    zd acc = cmk(0.0, 0.0), term = cmk(1.0, 0.0);  // (ia)^n / n!
+    zd a0 = cmk(0.0, 0.0), a1 = a0, term = cmk(1.0, 0.0);  // (ia)^n / n!
 #pragma unroll
-    for (int n = 0; n < 24; ++n) {  // unrolled: the reciprocals fold to constants
-      acc = acc + (1.0 / (n + 1.0)) * term;
+    for (int n = 0; n < 30; ++n) {  // unrolled: the reciprocals fold to constants
+      a0 = a0 + (1.0 / (n + 1.0)) * term;
+      a1 = a1 + (1.0 / (n + 2.0)) * term;
       term = (1.0 / (n + 1.0)) * (term * cmk(0.0, a));
     }
-    return acc;
+    m0 = a0;
+    m1 = a1;
+    return;
   }
-  // (cs - 1 + i sn) / (i a) = (sn - i (cs - 1)) / a
-  const double ia = 1.0 / a;
-  return cmk(sn * ia, (1.0 - cs) * ia);
+  const double ia = 1.0 / a, ia2 = ia * ia;
+  m0 = cmk(sn * ia, (1.0 - cs) * ia);
+  m1 = cmk(sn * ia + (cs - 1.0) * ia2, -cs * ia + sn * ia2);
 }
 
 // d/dV of Re(cy S_ii) for the exact self term (closed radial form, file
 // header), the 32 Gauss-Legendre points of every panel split over the lanes of
-// a warp; every lane returns the warp's sum in g9 (added).
-__device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) {
+// a warp; every lane returns the warp's sum in g9 (added).  With dks non-null
+// the same points give dS_ii/dk = (1/4 pi) sum_edges int R^2 i m1(k R) dphi
+// (m1 = int_0^1 s exp(i k R s) ds), returned in *dks on every lane.
+__device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9, zd* dks = nullptr) {
   double gl[3][3];  // grad lambda_a = (e_a x n) / (2A), e_a = V_{a+1} - V_{a+2}
   double dA[3][3];  // dA/dV_a = (1/2) e_a x n
   for (int a = 0; a < 3; ++a) {
@@ -460,7 +462,7 @@ __device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) 
       dA[a][d] = 0.5 * en[d];
     }
   }
-  zd S = cmk(0.0, 0.0);
+  zd S = cmk(0.0, 0.0), SK = cmk(0.0, 0.0);
   zd J[3][3];
   for (int a = 0; a < 3; ++a)
     for (int d = 0; d < 3; ++d) J[a][d] = cmk(0.0, 0.0);
@@ -492,8 +494,10 @@ __device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) 
       const double wq = half * wgl * ich;  // d phi = du / cosh(u)
       double sn, cs;
       sincos(k * R, &sn, &cs);
-      const zd m0 = moment0(k * R, sn, cs);
+      zd m0, m1;
+      moments01(k * R, sn, cs, m0, m1);
       S = S + (wq * R) * m0;
+      SK = SK + (wq * R * R) * cmk(-m1.im, m1.re);  // i R^2 m1
       const zd K = R * (cmk(cs, sn) - 2.0 * m0);
       double dir[3];
       for (int d = 0; d < 3; ++d) dir[d] = (fh[d] + sh * tv[d]) * ich;
@@ -506,6 +510,8 @@ __device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) 
   for (int o = 16; o > 0; o >>= 1) {
     S.re += __shfl_xor_sync(0xffffffffu, S.re, o);
     S.im += __shfl_xor_sync(0xffffffffu, S.im, o);
+    SK.re += __shfl_xor_sync(0xffffffffu, SK.re, o);
+    SK.im += __shfl_xor_sync(0xffffffffu, SK.im, o);
     for (int va = 0; va < 3; ++va)
       for (int d = 0; d < 3; ++d) {
         J[va][d].re += __shfl_xor_sync(0xffffffffu, J[va][d].re, o);
@@ -518,10 +524,13 @@ __device__ void self_grad(const VTri& t, double k, zd cy, int lane, double* g9) 
       const zd dS = (c4 * dA[va][d] / t.area) * S + c4 * J[va][d];
       g9[3 * va + d] += (cy * dS).re;
     }
+  if (dks) *dks = c4 * SK;
 }
 
 // One warp per row i of the correction matrix: for every non-self (i, j) the
-// refined rule minus R_0 (the self pairs are k_gv_self's).  Collocation-point
+// refined rule minus R_0 (the self pairs are k_gv_self's); with dk non-null
+// the same points give the pair's d/dk of (refined rule - R_0), added to *dk
+// as Re((dS/dk) cy - (dD/dk) cx).  Launched with 128 threads.  Collocation-point
 // gradients are summed over the warp into gx; vertex gradients of Gamma_j go
 // to gel[j] (9 doubles: V_0, V_1, V_2).  With f32 (mixed modes) the non-self
 // pairs run in FP32 with the triangle relative to the collocation point.
@@ -529,10 +538,12 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
                           const double* __restrict__ qpt, const double* __restrict__ nrm,
                           const double* __restrict__ area, const double* __restrict__ hmax,
                           const int* __restrict__ ptr, const int* __restrict__ col, const double4* __restrict__ yx,
-                          const double2* __restrict__ gs, double* __restrict__ gx, double* __restrict__ gel) {
+                          const double2* __restrict__ gs, double* __restrict__ gx, double* __restrict__ gel,
+                          double* __restrict__ dk) {
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   double tg[3] = {0.0, 0.0, 0.0};
+  double dkp = 0.0;  // Re((dS/dk) cy - (dD/dk) cx) of the row's corrections, with dk
   if (i < nt) {
     const double x[3] = {cent[3 * i], cent[3 * i + 1], cent[3 * i + 2]};
     for (int e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
@@ -568,14 +579,18 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
         const float x0[3] = {0.f, 0.f, 0.f};
         const cpx<float> cyf = cmk((float)cy.re, (float)cy.im), cxf = cmk((float)cx.re, (float)cx.im);
         float g9f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, ttf[3] = {0, 0, 0};
-        rule_grad(x0, tf, 0, (float)k, cyf, cxf, -1.0f, ttf, g9f);
-        rule_grad(x0, tf, L, (float)k, cyf, cxf, 1.0f, ttf, g9f);
+        cpx<float> kd[2] = {cmk(0.f, 0.f), cmk(0.f, 0.f)};
+        rule_grad(x0, tf, 0, (float)k, cyf, cxf, -1.0f, ttf, g9f, dk ? kd : nullptr);
+        rule_grad(x0, tf, L, (float)k, cyf, cxf, 1.0f, ttf, g9f, dk ? kd : nullptr);
+        dkp += (double)kd[0].re * cy.re - (double)kd[0].im * cy.im - ((double)kd[1].re * cx.re - (double)kd[1].im * cx.im);
         for (int d = 0; d < 3; ++d) tg[d] += (double)ttf[d];
         for (int m = 0; m < 9; ++m) atomicAdd(&gel[9 * j + m], (double)g9f[m]);
         continue;
       }
-      rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
-      rule_grad(x, t, L, k, cy, cx, 1.0, tt, g9);
+      zd kd[2] = {cmk(0.0, 0.0), cmk(0.0, 0.0)};
+      rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9, dk ? kd : nullptr);
+      rule_grad(x, t, L, k, cy, cx, 1.0, tt, g9, dk ? kd : nullptr);
+      dkp += (kd[0] * cy).re - (kd[1] * cx).re;
       for (int d = 0; d < 3; ++d) tg[d] += tt[d];
       for (int m = 0; m < 9; ++m) atomicAdd(&gel[9 * j + m], g9[m]);
     }
@@ -584,39 +599,67 @@ __global__ void k_gv_corr(int64_t nt, int nrhs, int f32, double k, const double*
     for (int o = 16; o > 0; o >>= 1) tg[d] += __shfl_xor_sync(0xffffffffu, tg[d], o);
   if (i < nt && lane == 0)
     for (int d = 0; d < 3; ++d) atomicAdd(&gx[3 * i + d], tg[d]);
+  if (dk) {
+    // one atomic add per block of four rows
+    for (int o = 16; o > 0; o >>= 1) dkp += __shfl_xor_sync(0xffffffffu, dkp, o);
+    __shared__ double s_dk[4];
+    if (lane == 0) s_dk[threadIdx.x >> 5] = dkp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double sum = s_dk[0] + s_dk[1] + s_dk[2] + s_dk[3];
+      if (sum != 0.0) atomicAdd(dk, sum);
+    }
+  }
 }
 
 // the self pairs, one warp per element (the lanes split the Gauss-Legendre
 // points of the exact term): the exact self term's vertex gradient minus
 // R_0's, and R_0's collocation gradient spread over the element's own vertices
 // (its centroid is the collocation point).  Runs after k_gv_corr, so gel[j] is
-// updated in place.
-__global__ void k_gv_self(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
-                          const double* __restrict__ qpt, const double* __restrict__ nrm,
-                          const double* __restrict__ area, const double* __restrict__ hmax,
-                          const double4* __restrict__ yx, const double2* __restrict__ gs,
-                          double* __restrict__ gel) {
+// updated in place.  With dk non-null the same quadrature gives the self
+// pair's d/dk of (exact - R_0), added to *dk.  Launched with 128 threads.
+__global__ void __launch_bounds__(128) k_gv_self(int64_t nt, int nrhs, double k, const double* __restrict__ cent,
+                                                 const double* __restrict__ qpt, const double* __restrict__ nrm,
+                                                 const double* __restrict__ area, const double* __restrict__ hmax,
+                                                 const double4* __restrict__ yx, const double2* __restrict__ gs,
+                                                 double* __restrict__ gel, double* __restrict__ dk) {
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (i >= nt) return;  // the whole warp: i is the same on every lane
-  VTri t;
-  vload(qpt, nrm, cent, area, hmax, i, t);
-  const double x[3] = {t.c[0], t.c[1], t.c[2]};
-  zd cy = cmk(0.0, 0.0), cx = cmk(0.0, 0.0);
-  for (int r = 0; r < nrhs; ++r) {
-    const double2 g = gs[(int64_t)r * nt + i];
-    const double4 v = yx[(int64_t)r * nt + i];
-    const zd cg = cmk(g.x, -g.y);
-    cy = cy + cg * cmk(v.x, v.y);
-    cx = cx + cg * cmk(v.z, v.w);
+  double part = 0.0;  // Re((dS_ii/dk - R_0's) cy - (-R_0's dD/dk) cx), with dk
+  if (i < nt) {  // the whole warp: i is the same on every lane
+    VTri t;
+    vload(qpt, nrm, cent, area, hmax, i, t);
+    const double x[3] = {t.c[0], t.c[1], t.c[2]};
+    zd cy = cmk(0.0, 0.0), cx = cmk(0.0, 0.0);
+    for (int r = 0; r < nrhs; ++r) {
+      const double2 g = gs[(int64_t)r * nt + i];
+      const double4 v = yx[(int64_t)r * nt + i];
+      const zd cg = cmk(g.x, -g.y);
+      cy = cy + cg * cmk(v.x, v.y);
+      cx = cx + cg * cmk(v.z, v.w);
+    }
+    double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
+    zd dks = cmk(0.0, 0.0);
+    self_grad(t, k, cy, lane, g9, dk ? &dks : nullptr);
+    if (lane == 0) {
+      zd kd[2] = {cmk(0.0, 0.0), cmk(0.0, 0.0)};
+      rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9, dk ? kd : nullptr);  // kd = (-s0, -d0)
+      for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) g9[3 * a + d] += tt[d] / 3.0;
+      for (int m = 0; m < 9; ++m) gel[9 * i + m] += g9[m];
+      part = ((dks + kd[0]) * cy).re - (kd[1] * cx).re;
+    }
   }
-  double g9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, tt[3] = {0, 0, 0};
-  self_grad(t, k, cy, lane, g9);
-  if (lane != 0) return;
-  rule_grad(x, t, 0, k, cy, cx, -1.0, tt, g9);
-  for (int a = 0; a < 3; ++a)
-    for (int d = 0; d < 3; ++d) g9[3 * a + d] += tt[d] / 3.0;
-  for (int m = 0; m < 9; ++m) gel[9 * i + m] += g9[m];
+  if (dk) {
+    // one atomic add per block of four elements
+    __shared__ double s_dk[4];
+    if (lane == 0) s_dk[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double sum = s_dk[0] + s_dk[1] + s_dk[2] + s_dk[3];
+      if (sum != 0.0) atomicAdd(dk, sum);
+    }
+  }
 }
 
 // Per element: regular-rule point, area and normal gradients and the
@@ -1143,9 +1186,10 @@ int bem_grad_vertices(bem_handle* h, int nrhs, const double4* yx, const double2*
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_x, glx, sizeof(glx), 0, cudaMemcpyHostToDevice, s));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_vgl_w, glw, sizeof(glw), 0, cudaMemcpyHostToDevice, s));
   k_gv_corr<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, f64 ? 0 : 1, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax,
-                                               h->corr_ptr, h->corr_col, yx, gs, gx, gel);
+                                               h->corr_ptr, h->corr_col, yx, gs, gx, gel, dk);
   BEM_CUDA(cudaGetLastError());
-  k_gv_self<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gel);
+  k_gv_self<<<nblk(nt * 32, 128), 128, 0, s>>>(nt, nrhs, h->k, h->cent, h->qpt, h->nrm, h->area, h->hmax, yx, gs, gel,
+                                               dk);
   BEM_CUDA(cudaGetLastError());
   k_gv_finish<<<nblk(nt, 128), 128, 0, s>>>(nt, h->cent, h->qpt, h->nrm, h->area, h->hmax, h->tri, gx, gq, ga, gn,
                                             gel, dV);
