@@ -147,3 +147,22 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     u = -p0 * nodes / (3 * lam + 2 * mu)
     wrong_load = N @ np.full(tris.shape[0], p0)  # the other sign
     assert np.abs(K @ u.ravel() - wrong_load).max() > 0.5 * np.abs(wrong_load).max()
+
+
+@pytest.mark.parametrize("mask", [np.ones((2, 3, 1), bool), _sphere_mask(7, 3.1)])
+def test_shared_voxel_generator_matches_the_oracle_mesher(mask):
+    """inputs.voxel_body (the seeded generator both sides take their bodies
+    from) gives the oracle mesher's nodes, tetrahedra and boundary faces (up to
+    order), and its jittered nodes keep every tetrahedron positive."""
+    from paper_1606_02383_gb300 import inputs
+    a = inputs.voxel_body(mask, 0.3, (0.1, -0.2, 0.4))
+    b = fem.voxel_tets(mask, 0.3, (0.1, -0.2, 0.4))
+    assert np.array_equal(a[0], b[0])
+    assert sorted(map(tuple, np.sort(a[1], axis=1))) == sorted(map(tuple, np.sort(b[1], axis=1)))
+    # faces equal as oriented triangles: the same cyclic order
+    def canon(t):
+        k = int(np.argmin(t))
+        return tuple(int(v) for v in np.roll(t, -k))
+    assert sorted(canon(t) for t in a[2]) == sorted(canon(t) for t in b[2])
+    nodes, tets, _ = inputs.voxel_body(mask, 0.3, jitter=0.05, seed=1)
+    assert min(fem.shape_gradients(nodes[t])[0] for t in tets) > 0
