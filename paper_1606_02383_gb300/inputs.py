@@ -14,6 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "ball_tets",
     "voxel_body",
     "voxel_ball",
     "icosphere",
@@ -405,3 +406,40 @@ def voxel_ball(n: int, radius: float, h: float = 1.0, jitter: float = 0.0, seed:
     X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
     mask = X ** 2 + Y ** 2 + Z ** 2 <= radius * radius
     return voxel_body(mask, h, origin=(-0.5 * n * h,) * 3, jitter=jitter, seed=seed)
+
+
+def ball_tets(level: int, radius: float = 1.0, layers: int = 4):
+    """Tetrahedra of a ball whose boundary is the level-`level` icosphere: the
+    icosphere scaled to radii radius m / layers (m = 1 .. layers) and the
+    centre; the centre and the innermost sphere's triangles make one
+    tetrahedron each, and the prism between two spheres over a triangle with
+    surface vertices a < b < c (a', b', c' one sphere out) is cut into
+    (a, b, c, c'), (a, b, b', c'), (a, a', b', c'): every side face takes the
+    diagonal from its lower-index inner vertex to its higher-index outer one,
+    so neighbouring prisms match.  Returns (nodes, tets with positive volume,
+    tris: the outer icosphere, normals out of the ball)."""
+    Vs, Ts = icosphere(level, 1.0)
+    nv = Vs.shape[0]
+    nodes = [np.zeros((1, 3))]
+    for m in range(1, layers + 1):
+        nodes.append(Vs * (radius * m / layers))
+    nodes = np.concatenate(nodes)
+
+    def node(m, i):  # layer m (1-based) copy of surface vertex i
+        return 1 + (m - 1) * nv + i
+
+    tets = []
+    for t in Ts:
+        a, b, c = sorted(int(v) for v in t)
+        tets.append([0, node(1, a), node(1, b), node(1, c)])
+        for m in range(1, layers):
+            A, B, C = node(m, a), node(m, b), node(m, c)
+            A2, B2, C2 = node(m + 1, a), node(m + 1, b), node(m + 1, c)
+            tets += [[A, B, C, C2], [A, B, B2, C2], [A, A2, B2, C2]]
+    tets = np.asarray(tets, dtype=np.int64)
+    P = nodes[tets]
+    vol = np.einsum("ij,ij->i", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    flip = vol < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    tris = (1 + (layers - 1) * nv + Ts).astype(np.int32)
+    return nodes, tets.astype(np.int32), tris
